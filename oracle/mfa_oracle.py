@@ -1,0 +1,549 @@
+"""Plain FP64 CPU oracle for the domain-decomposed MFA encoder.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import or call this
+module; only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
+baseline / reference arm use it.  It shares no code with the CUDA library.
+
+Paper: Mahadevan, Lenz, Grindeanu, Peterka, "Parallel Domain Decomposition
+Techniques Applied to Multivariate Functional Approximation of Discrete Data"
+(arXiv 2210.06528).
+
+What it computes, in the paper's order (Algorithm 1):
+  * Sec. 2.1, Eq. (nurbs-basis) with W = 1: B-spline basis N_{i,p} by the
+    Cox-de Boor recurrence, and its exact derivatives by the same recurrence.
+  * Sec. 2.1, Eq. (minimization-problem): the unconstrained local LSQ fit,
+    solved through the normal equations with a Cholesky factorisation
+    (Sec. 2.3.1).  On a tensor grid the normal matrix is the Kronecker product
+    of per-axis Gram matrices, so the solve is applied one axis at a time.
+  * Sec. 2.2 (floating interior knots, Delta / delta layers, Eq. vecp-layout)
+    and Sec. 2.3 (Eq. nonlinear-residuals, RAS with w_i = 1/n_s): the outer
+    additive-Schwarz loop.  Iteration 0 is the decoupled unconstrained solve
+    of every subdomain; iteration k >= 1 re-solves every subdomain with its
+    frame control points (those it sees in its overlap but does not own) held
+    at the lagged global iterate, which is the Schur-complement decoupling of
+    Eq. (global-system) with the constraint imposed exactly; the new global
+    iterate averages every owned copy with weight 1/n_s.
+  * Algorithm 1, "update local error": decode R P and the residual Q - R P.
+
+Readings where the paper is silent (all are listed in the design doc):
+  * data parameters u_k = k / (M - 1) on every axis; M = 1 gives u = 0;
+  * global knots clamped and uniform: nspans spans, n = nspans + p control
+    points; subdomain interfaces sit on breakpoints, so interior knots float;
+  * subdomain cores are contiguous span ranges [a, b); a core owns the control
+    points whose support meets it, U = [a, b + p);
+  * the overlap delta extends the core by delta spans per interior side: the
+    window is [a - delta, b + delta) clipped to [0, nspans); the data of a
+    subdomain are the points whose parameter lies in the CLOSED window
+    interval, decided with exact integer arithmetic;
+  * L = all control points touching the window = [w0, w1 + p); the frame is
+    F = L minus U (tensor product: any axis index outside U);
+  * the converged state is the fixed point of the averaged re-solve map.
+
+Array convention: a d-dimensional grid array has numpy shape
+(M_{d-1}, ..., M_1, M_0), C order, so grid axis 0 is the fastest-varying
+index in memory.  ``_np_axis(a, d)`` converts grid axis a to numpy axis.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional, Sequence
+
+import numpy as np
+import scipy.linalg
+
+# ---------------------------------------------------------------------------
+# Sec. 2.1: knots, parameters and the Cox-de Boor basis
+# ---------------------------------------------------------------------------
+
+
+def clamped_uniform_knots(nspans: int, p: int) -> np.ndarray:
+    """Clamped uniform knot vector with ``nspans`` spans: p+1 zeros, the
+    interior breakpoints i/nspans, p+1 ones (Sec. 2.1; global ends clamped,
+    Sec. 2.2; interior knots single, i.e. floating at interfaces)."""
+    interior = [i / nspans for i in range(1, nspans)]
+    return np.array([0.0] * (p + 1) + interior + [1.0] * (p + 1), dtype=np.float64)
+
+
+def grid_params(M: int) -> np.ndarray:
+    """Uniform data parameters u_k = k/(M-1) (reading: the paper does not fix
+    the parameterisation).  A single point sits at u = 0."""
+    if M == 1:
+        return np.zeros(1)
+    return np.arange(M, dtype=np.float64) / (M - 1)
+
+
+def _degree0(t: np.ndarray, u: np.ndarray, side: str) -> np.ndarray:
+    """N_{i,0}(u): indicator of [t_i, t_{i+1}) ('right') or (t_i, t_{i+1}]
+    ('left', the left-sided limit).  With side 'right' the global end u = t[-1]
+    is assigned to the last non-empty interval, with side 'left' the global
+    start u = t[0] to the first one, so the basis is defined on the closed
+    parameter interval."""
+    m = len(t) - 1
+    N = np.zeros((len(u), m))
+    for i in range(m):
+        if side == "right":
+            N[:, i] = (t[i] <= u) & (u < t[i + 1])
+        else:
+            N[:, i] = (t[i] < u) & (u <= t[i + 1])
+    nonempty = [i for i in range(m) if t[i] < t[i + 1]]
+    if side == "right":
+        N[u == t[-1], nonempty[-1]] = 1.0
+    else:
+        N[u == t[0], nonempty[0]] = 1.0
+    return N
+
+
+def basis_matrix(t: np.ndarray, p: int, u, deriv: int = 0, side: str = "right") -> np.ndarray:
+    """Dense collocation matrix D[k, i] = d^deriv/du^deriv N_{i,p}(u_k).
+
+    Cox-de Boor recurrence (Sec. 2.1, Eq. nurbs-basis with W = 1):
+        N_{i,q}(u) = (u - t_i)/(t_{i+q} - t_i) N_{i,q-1}(u)
+                   + (t_{i+q+1} - u)/(t_{i+q+1} - t_{i+1}) N_{i+1,q-1}(u),
+    with a term dropped when its denominator is zero.  Derivatives use the
+    same recurrence on the derivative (Sec. 2.1 notes exact derivatives follow
+    from it):
+        N^{(r)}_{i,q} = q/(t_{i+q} - t_i) N^{(r-1)}_{i,q-1}
+                      - q/(t_{i+q+1} - t_{i+1}) N^{(r-1)}_{i+1,q-1}.
+    The matrix has len(t) - p - 1 columns.
+    """
+    u = np.atleast_1d(np.asarray(u, dtype=np.float64))
+    t = np.asarray(t, dtype=np.float64)
+    if deriv > p:
+        return np.zeros((len(u), len(t) - p - 1))
+    if deriv == 0:
+        N = _degree0(t, u, side)
+        for q in range(1, p + 1):
+            cols = N.shape[1] - 1
+            Nq = np.zeros((len(u), cols))
+            for i in range(cols):
+                d1 = t[i + q] - t[i]
+                d2 = t[i + q + 1] - t[i + 1]
+                if d1 > 0:
+                    Nq[:, i] += (u - t[i]) / d1 * N[:, i]
+                if d2 > 0:
+                    Nq[:, i] += (t[i + q + 1] - u) / d2 * N[:, i + 1]
+            N = Nq
+        return N
+    lower = basis_matrix(t, p - 1, u, deriv - 1, side)  # columns: len(t) - p
+    cols = lower.shape[1] - 1
+    D = np.zeros((len(u), cols))
+    for i in range(cols):
+        d1 = t[i + p] - t[i]
+        d2 = t[i + p + 1] - t[i + 1]
+        if d1 > 0:
+            D[:, i] += p / d1 * lower[:, i]
+        if d2 > 0:
+            D[:, i] -= p / d2 * lower[:, i + 1]
+    return D
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.2: subdomain layout along one axis
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class AxisPiece:
+    """One subdomain's index sets along one grid axis (Sec. 2.2, Eq. vecp-layout).
+
+    core  [a, b)          : owned knot spans (Omega_i)
+    window[w0, w1)        : core plus delta spans per interior side (delta_i)
+    pts   [k0, k1]        : data points in the closed window interval
+    U     [a, b + p)      : owned control points, P(Omega) and P(Delta)
+    L     [w0, w1 + p)    : every control point touching the window
+    """
+
+    a: int
+    b: int
+    w0: int
+    w1: int
+    k0: int
+    k1: int
+    p: int
+
+    @property
+    def U(self) -> range:
+        return range(self.a, self.b + self.p)
+
+    @property
+    def L(self) -> range:
+        return range(self.w0, self.w1 + self.p)
+
+    @property
+    def pts(self) -> range:
+        return range(self.k0, self.k1 + 1)
+
+
+def even_cores(nspans: int, nsub: int) -> List[int]:
+    """Split nspans into nsub contiguous cores; the +1 spans of an uneven split
+    go to the first subdomains (reading)."""
+    base, extra = divmod(nspans, nsub)
+    return [base + (1 if s < extra else 0) for s in range(nsub)]
+
+
+def axis_pieces(M: int, nspans: int, p: int, core_spans: Sequence[int], delta: int) -> List[AxisPiece]:
+    """Index sets of every subdomain along one axis.
+
+    Window membership of data point k (parameter k/(M-1)) in the closed
+    interval [w0/nspans, w1/nspans] is decided exactly:
+        w0 * (M-1) <= k * nspans <= w1 * (M-1).
+    """
+    assert sum(core_spans) == nspans
+    pieces = []
+    a = 0
+    for c in core_spans:
+        b = a + c
+        w0 = max(a - delta, 0)
+        w1 = min(b + delta, nspans)
+        if M == 1:
+            k0 = k1 = 0
+        else:
+            ks = [k for k in range(M) if w0 * (M - 1) <= k * nspans <= w1 * (M - 1)]
+            k0, k1 = ks[0], ks[-1]
+        pieces.append(AxisPiece(a, b, w0, w1, k0, k1, p))
+        a = b
+    return pieces
+
+
+# ---------------------------------------------------------------------------
+# Tensor helpers (plain numpy; grid axis a <-> numpy axis d-1-a)
+# ---------------------------------------------------------------------------
+
+
+def _np_axis(a: int, d: int) -> int:
+    return d - 1 - a
+
+
+def apply_along_axis(T: np.ndarray, mat: np.ndarray, a: int) -> np.ndarray:
+    """Contract grid axis a of tensor T with matrix ``mat``: out_i = sum_j mat[i, j] T_j."""
+    d = T.ndim
+    ax = _np_axis(a, d)
+    out = np.tensordot(mat, T, axes=([1], [ax]))  # new axis first
+    return np.moveaxis(out, 0, ax)
+
+
+def box(T: np.ndarray, ranges: Sequence[range]) -> np.ndarray:
+    """Sub-array of T selected by one index range per grid axis."""
+    d = T.ndim
+    sl = [None] * d
+    for a, r in enumerate(ranges):
+        sl[_np_axis(a, d)] = slice(r.start, r.stop)
+    return T[tuple(sl)]
+
+
+def _box_slices(ranges: Sequence[range], d: int):
+    sl = [None] * d
+    for a, r in enumerate(ranges):
+        sl[_np_axis(a, d)] = slice(r.start, r.stop)
+    return tuple(sl)
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.1 / 2.3.1: separable least squares through the normal equations
+# ---------------------------------------------------------------------------
+
+
+class NotSPDError(RuntimeError):
+    pass
+
+
+def cholesky_solve(A: np.ndarray, rhs: np.ndarray) -> np.ndarray:
+    """Solve A X = rhs with a Cholesky factorisation (Sec. 2.3.1)."""
+    try:
+        c = scipy.linalg.cho_factor(A, lower=True, check_finite=True)
+    except np.linalg.LinAlgError as e:  # not positive definite
+        raise NotSPDError(str(e)) from e
+    return scipy.linalg.cho_solve(c, rhs)
+
+
+def separable_lsq(Qbox: np.ndarray, mats: Sequence[np.ndarray]) -> np.ndarray:
+    """argmin_P || Q - (N_{d-1} x ... x N_0) P ||_2 for a tensor-grid box.
+
+    The normal matrix of the Kronecker collocation matrix is the Kronecker
+    product of the per-axis Gram matrices N_a^T N_a, so the normal equations
+    (Eq. minimization-problem) are solved by projecting every axis with N_a^T
+    and then applying (N_a^T N_a)^{-1} on every axis, axis 0 first.
+    """
+    T = Qbox
+    for a, N in enumerate(mats):
+        T = apply_along_axis(T, N.T, a)
+    for a, N in enumerate(mats):
+        A = N.T @ N
+        T = apply_along_axis(T, cholesky_solve(A, np.eye(A.shape[0])), a)
+    return T
+
+
+def decode_box(P: np.ndarray, mats: Sequence[np.ndarray]) -> np.ndarray:
+    """Tensor-product decode R P = (N_{d-1} x ... x N_0) P (Algorithm 1 error step)."""
+    T = P
+    for a, N in enumerate(mats):
+        T = apply_along_axis(T, N, a)
+    return T
+
+
+# ---------------------------------------------------------------------------
+# Problem description
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class Problem:
+    """A gridded MFA problem in the adopted reading.
+
+    npts[a], nspans[a], cores[a] (list of core span counts), delta[a] per grid
+    axis a = 0..d-1, one degree p for all axes.
+    """
+
+    p: int
+    npts: List[int]
+    nspans: List[int]
+    cores: List[List[int]]
+    delta: List[int]
+
+    @property
+    def d(self) -> int:
+        return len(self.npts)
+
+    def ncp(self) -> List[int]:
+        return [s + self.p for s in self.nspans]
+
+    def knots(self, a: int) -> np.ndarray:
+        return clamped_uniform_knots(self.nspans[a], self.p)
+
+    def params(self, a: int) -> np.ndarray:
+        return grid_params(self.npts[a])
+
+    def basis(self, a: int) -> np.ndarray:
+        return basis_matrix(self.knots(a), self.p, self.params(a))
+
+    def pieces(self, a: int) -> List[AxisPiece]:
+        return axis_pieces(self.npts[a], self.nspans[a], self.p, self.cores[a], self.delta[a])
+
+    def subdomains(self):
+        """All subdomains as tuples of AxisPiece, axis 0 varying fastest."""
+        per_axis = [self.pieces(a) for a in range(self.d)]
+        out = []
+        for idx in np.ndindex(*[len(x) for x in reversed(per_axis)]):
+            s = tuple(per_axis[a][idx[self.d - 1 - a]] for a in range(self.d))
+            out.append(s)
+        return out
+
+
+def make_problem(p, npts, nspans, nsub, delta, cores=None) -> Problem:
+    d = len(npts)
+    if cores is None:
+        cores = [even_cores(nspans[a], nsub[a]) for a in range(d)]
+    if isinstance(delta, int):
+        delta = [delta] * d
+    return Problem(p, list(npts), list(nspans), [list(c) for c in cores], list(delta))
+
+
+# ---------------------------------------------------------------------------
+# The plain definition: global LSQ fit (N = 1)
+# ---------------------------------------------------------------------------
+
+
+def global_fit(prob: Problem, Q: np.ndarray) -> np.ndarray:
+    """argmin_P ||Q - R P|| over the whole grid (Eq. minimization-problem, N = 1)."""
+    return separable_lsq(np.asarray(Q, np.float64), [prob.basis(a) for a in range(prob.d)])
+
+
+def decode_grid(prob: Problem, P: np.ndarray) -> np.ndarray:
+    """Decode the global control points on the full data grid."""
+    return decode_box(P, [prob.basis(a) for a in range(prob.d)])
+
+
+# ---------------------------------------------------------------------------
+# Sec. 2.3 / Algorithm 1: overlapping additive Schwarz
+# ---------------------------------------------------------------------------
+
+
+@dataclass
+class SchwarzState:
+    P: np.ndarray                      # current global iterate P^k
+    copies: list                       # per-subdomain owned copies (arrays over U_s)
+    frames: list                       # per-subdomain L_s arrays used in the last solve
+    k: int = 0
+    history: list = field(default_factory=list)
+
+
+def _local_mats(prob: Problem, s, Nglob, cols: str):
+    mats = []
+    for a, pc in enumerate(s):
+        rows = pc.pts
+        cr = pc.L if cols == "L" else pc.U
+        mats.append(Nglob[a][rows.start:rows.stop, cr.start:cr.stop])
+    return mats
+
+
+def average_copies(prob: Problem, subs, copies) -> tuple:
+    """Uniformly weighted average of every owned copy, w = 1/n_s (Sec. 2.3.2).
+
+    Returns (P, spread) where spread[g] = max copy - min copy of CP g."""
+    shape = tuple(reversed(prob.ncp()))
+    acc = np.zeros(shape)
+    cnt = np.zeros(shape)
+    hi = np.full(shape, -np.inf)
+    lo = np.full(shape, np.inf)
+    for s, c in zip(subs, copies):
+        sl = _box_slices([pc.U for pc in s], prob.d)
+        acc[sl] += c
+        cnt[sl] += 1
+        hi[sl] = np.maximum(hi[sl], c)
+        lo[sl] = np.minimum(lo[sl], c)
+    if np.any(cnt == 0):
+        raise ValueError("a control point is owned by no subdomain")
+    return acc / cnt, hi - lo
+
+
+def multiplicity(prob: Problem) -> np.ndarray:
+    """n_s(g): number of subdomains owning control point g."""
+    shape = tuple(reversed(prob.ncp()))
+    cnt = np.zeros(shape, dtype=np.int64)
+    for s in prob.subdomains():
+        cnt[_box_slices([pc.U for pc in s], prob.d)] += 1
+    return cnt
+
+
+def schwarz_initial(prob: Problem, Q: np.ndarray) -> SchwarzState:
+    """Iteration 0 of Algorithm 1: every subdomain solves the unconstrained
+    local LSQ on its window data with all of L_s free (Eq. minimization-problem);
+    the owned part U_s of each local solution is kept and averaged."""
+    Q = np.asarray(Q, np.float64)
+    Nglob = [prob.basis(a) for a in range(prob.d)]
+    subs = prob.subdomains()
+    copies, frames = [], []
+    for s in subs:
+        mats = _local_mats(prob, s, Nglob, "L")
+        PL = separable_lsq(box(Q, [pc.pts for pc in s]), mats)
+        frames.append(PL)
+        u_in_l = [range(pc.a - pc.w0, pc.a - pc.w0 + len(pc.U)) for pc in s]
+        copies.append(box(PL, u_in_l).copy())
+    P, spread = average_copies(prob, subs, copies)
+    st = SchwarzState(P=P, copies=copies, frames=frames, k=0)
+    st.history.append({"k": 0, "spread": float(spread.max(initial=0.0))})
+    return st
+
+
+def schwarz_step(prob: Problem, Q: np.ndarray, st: SchwarzState) -> SchwarzState:
+    """One outer iteration k >= 1 of Algorithm 1.
+
+    Exchange: each subdomain reads its frame F_s = L_s minus U_s from the
+    lagged global iterate P^{k-1} (the dequeued constraints P_i(Delta u delta)).
+    Constrain: the frame is held fixed, its decoded contribution is moved to
+    the right-hand side, and the owned points U_s are re-solved by LSQ on the
+    window data -- the Schur-complement decoupling with lagged neighbour
+    values (Sec. 2.2, Eq. global-system; jump terms of Eq. nonlinear-residuals
+    driven to zero at the fixed point).
+    Update: P^k averages all owned copies with w = 1/n_s (Sec. 2.3.2).
+    """
+    Q = np.asarray(Q, np.float64)
+    Nglob = [prob.basis(a) for a in range(prob.d)]
+    subs = prob.subdomains()
+    copies, frames = [], []
+    for s in subs:
+        Lr = [pc.L for pc in s]
+        PF = box(st.P, Lr).copy()
+        u_in_l = [range(pc.a - pc.w0, pc.a - pc.w0 + len(pc.U)) for pc in s]
+        PF[_box_slices(u_in_l, prob.d)] = 0.0
+        matsL = _local_mats(prob, s, Nglob, "L")
+        R = box(Q, [pc.pts for pc in s]) - decode_box(PF, matsL)
+        PU = separable_lsq(R, _local_mats(prob, s, Nglob, "U"))
+        full = PF.copy()
+        full[_box_slices(u_in_l, prob.d)] = PU
+        frames.append(full)
+        copies.append(PU)
+    P, spread = average_copies(prob, subs, copies)
+    dP = float(np.max(np.abs(P - st.P)))
+    pmax = float(np.max(np.abs(P)))
+    new = SchwarzState(P=P, copies=copies, frames=frames, k=st.k + 1, history=list(st.history))
+    new.history.append({"k": new.k, "dP_rel": dP / pmax if pmax > 0 else 0.0,
+                        "spread": float(spread.max(initial=0.0))})
+    return new
+
+
+def residual_stats(prob: Problem, Q: np.ndarray, P: np.ndarray) -> dict:
+    """Decoded error E = Q - R P over the full grid: RMS and max |E|."""
+    E = np.asarray(Q, np.float64) - decode_grid(prob, P)
+    return {"rms": float(np.sqrt(np.mean(E * E))), "max": float(np.max(np.abs(E)))}
+
+
+def schwarz_solve(prob: Problem, Q: np.ndarray, max_iters: int = 200, tol_dP: float = 0.0,
+                  tol_rms_stall: float = 0.0, keep_iterates: bool = False) -> dict:
+    """Algorithm 1 to convergence.
+
+    Stops after iteration k >= 1 when dP_rel = max|P^k - P^{k-1}| / max|P^k|
+    <= tol_dP, or (if tol_rms_stall > 0) when the decoded RMS changes by at
+    most tol_rms_stall * RMS_k, or at max_iters.
+    """
+    st = schwarz_initial(prob, Q)
+    iterates = [st.P.copy()] if keep_iterates else None
+    rms_prev = residual_stats(prob, Q, st.P)["rms"] if tol_rms_stall > 0 else None
+    converged = False
+    while st.k < max_iters:
+        st = schwarz_step(prob, Q, st)
+        if keep_iterates:
+            iterates.append(st.P.copy())
+        h = st.history[-1]
+        if h["dP_rel"] <= tol_dP:
+            converged = True
+            break
+        if tol_rms_stall > 0:
+            rms = residual_stats(prob, Q, st.P)["rms"]
+            h["rms"] = rms
+            if abs(rms - rms_prev) <= tol_rms_stall * rms:
+                converged = True
+                break
+            rms_prev = rms
+    return {"P": st.P, "state": st, "iters": st.k, "converged": converged,
+            "iterates": iterates, "history": st.history}
+
+
+# ---------------------------------------------------------------------------
+# Continuity diagnostics (Sec. 2.2: C^0 .. C^{p-1} at interfaces)
+# ---------------------------------------------------------------------------
+
+
+def interface_jumps_1d(prob: Problem, st: SchwarzState, max_order: Optional[int] = None) -> np.ndarray:
+    """1-D: jumps of derivative orders 0..max_order between neighbouring local
+    splines at each interface breakpoint.  The local spline of subdomain s is
+    the one it solved last (owned copy plus the frame it held); the left one is
+    evaluated as a left limit, the right one as a right limit.
+    Returns an array [n_interfaces, max_order + 1]."""
+    assert prob.d == 1
+    p = prob.p
+    if max_order is None:
+        max_order = p
+    t = prob.knots(0)
+    pieces = prob.pieces(0)
+    out = []
+    for i in range(len(pieces) - 1):
+        left, right = pieces[i], pieces[i + 1]
+        tau = left.b / prob.nspans[0]
+        row = []
+        for r in range(max_order + 1):
+            DL = basis_matrix(t, p, [tau], r, side="left")[0]
+            DR = basis_matrix(t, p, [tau], r, side="right")[0]
+            vL = DL[left.L.start:left.L.stop] @ st.frames[i]
+            vR = DR[right.L.start:right.L.stop] @ st.frames[i + 1]
+            row.append(abs(vL - vR))
+        out.append(row)
+    return np.array(out)
+
+
+def scattered_decode(prob: Problem, P: np.ndarray, u: np.ndarray, deriv=None) -> np.ndarray:
+    """Evaluate the global tensor spline (or a mixed partial derivative with
+    per-axis orders ``deriv``) at parameter points u[k, a] in [0,1]^d, one point
+    at a time through dense basis rows."""
+    d = prob.d
+    u = np.atleast_2d(np.asarray(u, np.float64))
+    deriv = [0] * d if deriv is None else list(deriv)
+    out = np.empty(len(u))
+    for k in range(len(u)):
+        T = P
+        for a in range(d):
+            row = basis_matrix(prob.knots(a), prob.p, [u[k, a]], deriv[a])  # (1, n_a)
+            T = apply_along_axis(T, row, a)
+        out[k] = float(np.asarray(T).reshape(-1)[0])
+    return out
