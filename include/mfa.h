@@ -1,0 +1,184 @@
+/*
+ * mfa.h -- C ABI of the GB300 library for domain-decomposed multivariate
+ * functional approximation (MFA): tensor-product B-spline least-squares fits
+ * of gridded data, split into overlapping subdomains and made continuous by an
+ * overlapping additive-Schwarz iteration.
+ *
+ * Method: Mahadevan, Lenz, Grindeanu, Peterka, "Parallel Domain Decomposition
+ * Techniques Applied to Multivariate Functional Approximation of Discrete
+ * Data", arXiv 2210.06528.  Section references below are to that paper.
+ *
+ * Conventions shared by every call:
+ *  - Grids are stored with grid axis 0 fastest in memory: value (i0,i1,i2) of
+ *    a grid with npts = (M0,M1,M2) sits at offset i0 + M0*(i1 + M1*i2).
+ *    Control points use the same convention with n_a = nspans_a + degree.
+ *  - Knots on axis a are clamped and uniform with nspans_a spans; the data
+ *    parameters are u_k = k/(M_a - 1).  Physical coordinates map affinely from
+ *    [lo_a, hi_a] to [0, 1].
+ *  - Ownership: the caller owns every pointer it passes (q, pts, out, host_out);
+ *    the library reads or writes them only inside the call's stream work and
+ *    keeps none of them.  Host buffers are copied synchronously with respect
+ *    to the host before the call returns; device buffers must stay valid
+ *    until the handle's stream has passed the call (mfa_sync).  The library
+ *    owns mfa_model and mfa_handle objects until mfa_free / mfa_destroy.
+ *  - Errors: argument and layout errors return synchronously with no state
+ *    changed.  Errors found on the device (non-positive pivot, non-finite
+ *    input) are recorded in a device status word and returned by the next
+ *    call that synchronises (mfa_schwarz_iterate, mfa_residual, mfa_get_ctrl,
+ *    mfa_sync).  No call traps or aborts the process.
+ *  - Threading: a handle and its models are not thread-safe; use one handle
+ *    per host thread.  Every call is enqueued on the handle's stream.
+ */
+#ifndef MFA_GB300_H
+#define MFA_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mfa_handle mfa_handle; /* device, stream, workspace pool */
+typedef struct mfa_model mfa_model;   /* a fitted MFA, device resident  */
+
+enum {
+  MFA_OK = 0,
+  MFA_NOT_CONVERGED = 1,   /* warning: max_iters reached before the tolerance */
+  MFA_ERR_ARG = -1,        /* bad pointer, dtype, size or flag */
+  MFA_ERR_LAYOUT = -2,     /* layout rejected (core < degree spans, data too sparse, ...) */
+  MFA_ERR_OOM = -3,        /* device allocation failed */
+  MFA_ERR_CUDA = -4,       /* a CUDA runtime call failed */
+  MFA_ERR_NOT_SPD = -5,    /* a local normal matrix had a non-positive Cholesky pivot */
+  MFA_ERR_DIVERGED = -6,   /* the Schwarz update grew for 8 iterations in a row */
+  MFA_ERR_NONFINITE = -7,  /* the input data held NaN or Inf */
+  MFA_ERR_UNSUPPORTED = -8 /* valid request outside what this build implements */
+};
+
+enum { MFA_F32 = 0, MFA_F64 = 1 };
+
+/* Arithmetic of the fit.
+ * MFA_PREC_FP64 : every step in FP64 (the plain method).
+ * MFA_PREC_MIXED: data passes (projection, decode, residual) and the
+ *                 control-point iteration in FP32; Gram matrices and their
+ *                 Cholesky factors in FP64; residual reductions in FP64. */
+enum { MFA_PREC_FP64 = 0, MFA_PREC_MIXED = 1 };
+
+#define MFA_MAX_DIM 3
+#define MFA_MAX_DEGREE 7
+
+/* Problem layout (Sec. 2.2, Eq. vecp-layout; Algorithm 1 parameters N, p).
+ *   dim          1..3
+ *   degree       p, 1..MFA_MAX_DEGREE, same on every axis
+ *   npts[a]      data points M_a on axis a (>= 1; axes >= dim are ignored)
+ *   nspans[a]    global knot spans; n_a = nspans[a] + degree control points
+ *   nsub[a]      subdomains along axis a (N = product)
+ *   core_spans[a] NULL for an even split (the first nspans % nsub cores get
+ *                one span more) or an array of nsub[a] span counts summing to
+ *                nspans[a]; every core needs >= degree spans
+ *   overlap[a]   delta, extra knot spans shared per interior side (Sec. 2.2,
+ *                "Augmenting Knot Spans with Overlap"), >= 0
+ *   precision    MFA_PREC_FP64 or MFA_PREC_MIXED
+ *   lo[a], hi[a] physical extent of axis a (used by scattered decode)     */
+typedef struct {
+  int32_t dim;
+  int32_t degree;
+  int64_t npts[3];
+  int32_t nspans[3];
+  int32_t nsub[3];
+  const int32_t* core_spans[3];
+  int32_t overlap[3];
+  int32_t precision;
+  double lo[3];
+  double hi[3];
+} mfa_layout;
+
+/* Convergence and error metrics (Algorithm 1: "update local error",
+ * "check convergence metrics").
+ *   iters        Schwarz iterations done on this model (0 right after encode)
+ *   dP_rel       max|P^k - P^{k-1}| / max|P^k| of the last iteration
+ *   jump_max     largest spread (max - min) among the owned copies of any
+ *                shared control point: the jump residual F_ij of
+ *                Eq. (nonlinear-residuals) measured in control-point space
+ *   rms_decoded, maxabs_decoded   RMS and max |Q - R P| over all data
+ *   data_range   max(Q) - min(Q)                                           */
+typedef struct {
+  int32_t iters;
+  int32_t status;
+  double dP_rel;
+  double jump_max;
+  double rms_decoded;
+  double maxabs_decoded;
+  double data_range;
+} mfa_report;
+
+/* Create a handle bound to CUDA device `device` and stream `cuda_stream`
+ * (a cudaStream_t, or NULL for the legacy default stream).  The handle owns a
+ * stream-ordered memory pool for models and scratch.  Returns MFA_OK. */
+int mfa_create(int device, void* cuda_stream, mfa_handle** out);
+
+/* Release the handle and its pool.  Models must be freed first. */
+int mfa_destroy(mfa_handle* h);
+
+/* Setup and iteration 0 of Algorithm 1 (Sec. 2.4): build the subdomain
+ * layout, evaluate the Cox-de Boor basis of every axis (Sec. 2.1, Eq.
+ * nurbs-basis, W = 1), assemble and Cholesky-factor the banded per-axis
+ * normal matrices of every subdomain window (Sec. 2.3.1), project the window
+ * data onto every subdomain's control points (N^T Q), solve the decoupled
+ * unconstrained local LSQ problems (Eq. minimization-problem) and average the
+ * owned copies with weight 1/n_s (Sec. 2.3.2) into the global iterate P^0.
+ *   q            grid of prod(npts) values, dtype q_dtype (MFA_F32/MFA_F64),
+ *                on the device if q_on_device, else in host memory
+ *   out          receives a new model (free with mfa_free)
+ * Asynchronous on the handle's stream except for host input copies. */
+int mfa_encode(mfa_handle* h, const mfa_layout* layout, const void* q, int q_dtype,
+               int q_on_device, mfa_model** out);
+
+/* Outer iterations k >= 1 of Algorithm 1 (Sec. 2.3.2): exchange the frame
+ * control points of every subdomain from the lagged global iterate (a device
+ * gather), re-solve every subdomain with its frame held fixed (the Schur
+ * decoupling of Eq. global-system, done in control-point space without
+ * re-reading the data), and average the owned copies into P^k.  Stops after
+ * an iteration with dP_rel <= tol_dP or after max_iters iterations.
+ * Returns MFA_OK when the tolerance was met, MFA_NOT_CONVERGED when
+ * max_iters ran out (tol_dP <= 0 always runs max_iters), or an error.
+ * `rep` (may be NULL) receives iters, dP_rel, jump_max. */
+int mfa_schwarz_iterate(mfa_handle* h, mfa_model* m, int32_t max_iters, double tol_dP,
+                        mfa_report* rep);
+
+/* Decode the global MFA (Algorithm 1 error step, R P; Sec. 2.1 derivatives).
+ *   pts == NULL  full data grid: writes prod(npts) values in grid layout
+ *   pts != NULL  npts_q scattered points, row-major [npts_q][dim] physical
+ *                coordinates (clamped to [lo, hi])
+ *   deriv        NULL for values, else per-axis derivative orders (each
+ *                0..degree) of the mixed partial derivative with respect to
+ *                the physical coordinates
+ *   out          dtype out_dtype, on the device if out_on_device            */
+int mfa_decode(mfa_handle* h, const mfa_model* m, const double* pts, int64_t npts_q,
+               const int32_t* deriv, void* out, int out_dtype, int out_on_device);
+
+/* Decoded error E = Q - R P over the full grid (Algorithm 1 "update local
+ * error"): fills rep->rms_decoded, maxabs_decoded, data_range.  Synchronous. */
+int mfa_residual(mfa_handle* h, const mfa_model* m, const void* q, int q_dtype,
+                 int q_on_device, mfa_report* rep);
+
+/* Copy the global control points (FP64, grid layout, prod(n_a) values) to
+ * host memory; cap is the capacity of host_out in values.  Synchronous. */
+int mfa_get_ctrl(mfa_handle* h, const mfa_model* m, double* host_out, int64_t cap);
+
+/* Number of global control points of a model (prod n_a), or < 0 on error. */
+int64_t mfa_num_ctrl(const mfa_model* m);
+
+/* Free a model (stream-ordered on the stream of the handle that made it). */
+int mfa_free(mfa_model* m);
+
+/* Wait for the handle's stream; return and clear the device status word. */
+int mfa_sync(mfa_handle* h);
+
+/* Static text for a status code. */
+const char* mfa_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFA_GB300_H */

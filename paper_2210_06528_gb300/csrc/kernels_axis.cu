@@ -1,0 +1,323 @@
+// Batched one-axis tensor operations over every subdomain at once.
+// Every launch covers all subdomains: blockIdx.y selects the subdomain, the x
+// dimension covers its output elements.  The per-subdomain operand views are
+// built once on the host (AxisOp tables) and kept on the device.
+#include "mfa_internal.cuh"
+
+namespace mfa {
+
+template <typename T>
+__device__ __forceinline__ const T* basis_vals(const AxisDev& ax);
+template <>
+__device__ __forceinline__ const double* basis_vals<double>(const AxisDev& ax) { return ax.vals_d; }
+template <>
+__device__ __forceinline__ const float* basis_vals<float>(const AxisDev& ax) { return ax.vals_f; }
+
+template <typename T>
+__device__ __forceinline__ const T* fac_L(const AxisDev& ax);
+template <>
+__device__ __forceinline__ const double* fac_L<double>(const AxisDev& ax) { return ax.facL_d; }
+template <>
+__device__ __forceinline__ const float* fac_L<float>(const AxisDev& ax) { return ax.facL_f; }
+template <typename T>
+__device__ __forceinline__ const T* fac_U(const AxisDev& ax);
+template <>
+__device__ __forceinline__ const double* fac_U<double>(const AxisDev& ax) { return ax.facU_d; }
+template <>
+__device__ __forceinline__ const float* fac_U<float>(const AxisDev& ax) { return ax.facU_f; }
+
+__device__ __forceinline__ void unflatten(long long idx, const int* n, int* o) {
+  o[0] = (int)(idx % n[0]);
+  long long r = idx / n[0];
+  o[1] = (int)(r % n[1]);
+  o[2] = (int)(r / n[1]);
+}
+
+__device__ __forceinline__ bool finite_val(float x) { return isfinite(x); }
+__device__ __forceinline__ bool finite_val(double x) { return isfinite(x); }
+
+// Projection along one axis: out[l] = sum_k N_{c0+l}(u_{k}) in[k - k0] over
+// the points k of the window that lie in the support of control point c0+l,
+// i.e. whose span is in [c0+l-p, c0+l] (the N^T Q assembly of the normal
+// equations, Eq. minimization-problem).  When reading raw data the kernel also
+// flags non-finite input.
+template <typename T, typename TIn>
+__global__ void k_contract(LayoutDev L, int axis, const AxisOp* ops, const TIn* __restrict__ in,
+                           T* __restrict__ out, int* status) {
+  const AxisOp op = ops[blockIdx.y];
+  const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nout) return;
+  int o[3];
+  unflatten(idx, op.out.n, o);
+  const AxisDev& ax = L.ax[axis];
+  const int p = ax.p, w = p + 1;
+  const int g = op.c0 + o[axis];
+  int lo = g - p < 0 ? 0 : g - p;
+  int hi = g + 1 > ax.nspans ? ax.nspans : g + 1;
+  int kb = ax.span_start[lo], ke = ax.span_start[hi];
+  if (kb < op.k0) kb = op.k0;
+  if (ke > op.kend) ke = op.kend;
+  long long base = op.in.off;
+  for (int a = 0; a < 3; ++a)
+    if (a != axis) base += (long long)o[a] * op.in.st[a];
+  const long long sk = op.in.st[axis];
+  const T* v = basis_vals<T>(ax);
+  T acc = 0;
+  bool bad = false;
+  for (int k = kb; k < ke; ++k) {
+    const TIn x = in[base + (long long)(k - op.k0) * sk];
+    bad |= !finite_val(x);
+    acc += v[(long long)k * w + (g - ax.span[k])] * (T)x;
+  }
+  if (bad && status) atomicExch(status, MFA_ERR_NONFINITE);
+  const View& ov = op.out;
+  out[ov.off + o[0] * ov.st[0] + o[1] * ov.st[1] + o[2] * ov.st[2]] = acc;
+}
+
+// Decode along one axis: out[k] = sum_r N_{span(k)+r}(u_k) in[span(k)+r-c0],
+// terms whose control point lies outside the input range are zero (R P,
+// Algorithm 1 error step).
+template <typename T>
+__device__ __forceinline__ T expand_one(const AxisDev& ax, const AxisOp& op, int axis, const int* o,
+                                        const T* __restrict__ in) {
+  const int p = ax.p, w = p + 1;
+  const int k = op.k0 + o[axis];
+  const int j = ax.span[k];
+  long long base = op.in.off;
+  for (int a = 0; a < 3; ++a)
+    if (a != axis) base += (long long)o[a] * op.in.st[a];
+  const long long sc = op.in.st[axis];
+  const T* v = basis_vals<T>(ax) + (long long)k * w;
+  T acc = 0;
+  for (int r = 0; r <= p; ++r) {
+    const int c = j + r - op.c0;
+    if (c < 0 || c >= op.in.n[axis]) continue;
+    acc += v[r] * in[base + (long long)c * sc];
+  }
+  return acc;
+}
+
+template <typename T>
+__global__ void k_expand(LayoutDev L, int axis, const AxisOp* ops, const T* __restrict__ in, T* __restrict__ out) {
+  const AxisOp op = ops[blockIdx.y];
+  const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nout; idx += stride) {
+    int o[3];
+    unflatten(idx, op.out.n, o);
+    const T val = expand_one<T>(L.ax[axis], op, axis, o, in);
+    const View& ov = op.out;
+    out[ov.off + o[0] * ov.st[0] + o[1] * ov.st[1] + o[2] * ov.st[2]] = val;
+  }
+}
+
+// Final decode axis fused with the residual E = Q - R P: per-block partial
+// sums of E^2 (FP64), max |E|, min Q and max Q.  Q shares the output layout.
+template <typename T, typename TQ>
+__global__ void k_expand_residual(LayoutDev L, int axis, const AxisOp* opp, const T* __restrict__ in,
+                                  const TQ* __restrict__ q, double* partials) {
+  const AxisOp op = *opp;
+  const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  double s2 = 0.0, emax = 0.0, qmin = INFINITY, qmax = -INFINITY;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nout; idx += stride) {
+    int o[3];
+    unflatten(idx, op.out.n, o);
+    const T val = expand_one<T>(L.ax[axis], op, axis, o, in);
+    const double qv = (double)q[idx];
+    const double e = qv - (double)val;
+    s2 += e * e;
+    emax = fmax(emax, fabs(e));
+    qmin = fmin(qmin, qv);
+    qmax = fmax(qmax, qv);
+  }
+  __shared__ double sh[4][32];
+  for (int off = 16; off > 0; off >>= 1) {
+    s2 += __shfl_down_sync(0xffffffffu, s2, off);
+    emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, off));
+    qmin = fmin(qmin, __shfl_down_sync(0xffffffffu, qmin, off));
+    qmax = fmax(qmax, __shfl_down_sync(0xffffffffu, qmax, off));
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    sh[0][wid] = s2;
+    sh[1][wid] = emax;
+    sh[2][wid] = qmin;
+    sh[3][wid] = qmax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    double a = 0.0, b = 0.0, c = INFINITY, d = -INFINITY;
+    for (int i = 0; i < nw; ++i) {
+      a += sh[0][i];
+      b = fmax(b, sh[1][i]);
+      c = fmin(c, sh[2][i]);
+      d = fmax(d, sh[3][i]);
+    }
+    partials[4 * blockIdx.x + 0] = a;
+    partials[4 * blockIdx.x + 1] = b;
+    partials[4 * blockIdx.x + 2] = c;
+    partials[4 * blockIdx.x + 3] = d;
+  }
+}
+
+// Fixed-order final reduction of the per-block partials (deterministic).
+__global__ void k_reduce_partials(const double* partials, int nblocks, double* result) {
+  __shared__ double sh[4][256];
+  double a = 0.0, b = 0.0, c = INFINITY, d = -INFINITY;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+    a += partials[4 * i];
+    b = fmax(b, partials[4 * i + 1]);
+    c = fmin(c, partials[4 * i + 2]);
+    d = fmax(d, partials[4 * i + 3]);
+  }
+  sh[0][threadIdx.x] = a;
+  sh[1][threadIdx.x] = b;
+  sh[2][threadIdx.x] = c;
+  sh[3][threadIdx.x] = d;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
+      sh[1][threadIdx.x] = fmax(sh[1][threadIdx.x], sh[1][threadIdx.x + s]);
+      sh[2][threadIdx.x] = fmin(sh[2][threadIdx.x], sh[2][threadIdx.x + s]);
+      sh[3][threadIdx.x] = fmax(sh[3][threadIdx.x], sh[3][threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int i = 0; i < 4; ++i) result[i] = sh[i][0];
+}
+
+// Banded matrix-vector product along one axis with the output restricted to
+// the owned rows: out[i] = sum_c A_L(oU+i, c) in[c], |oU+i-c| <= p.  This is
+// the coupling G = N_U^T N_L of the Schur-decoupled local problem.
+template <typename T>
+__global__ void k_band_apply(LayoutDev L, int axis, const AxisOp* ops, const T* __restrict__ in, T* __restrict__ out) {
+  const AxisOp op = ops[blockIdx.y];
+  const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nout) return;
+  int o[3];
+  unflatten(idx, op.out.n, o);
+  const AxisDev& ax = L.ax[axis];
+  const int p = ax.p, w = p + 1;
+  const AxisSub sb = ax.subs[op.sa];
+  const double* A = ax.AL + (long long)sb.bandL * w;
+  const int r = op.oU + o[axis];
+  const int nL = op.in.n[axis];
+  long long base = op.in.off;
+  for (int a = 0; a < 3; ++a)
+    if (a != axis) base += (long long)o[a] * op.in.st[a];
+  const long long sc = op.in.st[axis];
+  T acc = 0;
+  const int c_lo = r - p < 0 ? 0 : r - p;
+  const int c_hi = r + p > nL - 1 ? nL - 1 : r + p;
+  for (int c = c_lo; c <= c_hi; ++c) {
+    const double a = c >= r ? A[(long long)r * w + (c - r)] : A[(long long)c * w + (r - c)];
+    acc += (T)a * in[base + (long long)c * sc];
+  }
+  const View& ov = op.out;
+  out[ov.off + o[0] * ov.st[0] + o[1] * ov.st[1] + o[2] * ov.st[2]] = acc;
+}
+
+// In-place banded Cholesky solve along one axis, one thread per fibre
+// (Sec. 2.3.1): forward L y = c, then backward L^T x = y.
+template <typename T>
+__global__ void k_band_solve(LayoutDev L, int axis, bool useU, const AxisOp* ops, T* x) {
+  const AxisOp op = ops[blockIdx.y];
+  const View& v = op.out;
+  const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
+  const long long nf = (long long)v.n[a1] * v.n[a2];
+  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const int i1 = (int)(f % v.n[a1]), i2 = (int)(f / v.n[a1]);
+  const AxisDev& ax = L.ax[axis];
+  const int p = ax.p, w = p + 1;
+  const AxisSub sb = ax.subs[op.sa];
+  const T* F = useU ? fac_U<T>(ax) + (long long)sb.bandU * w : fac_L<T>(ax) + (long long)sb.bandL * w;
+  const int n = v.n[axis];
+  T* base = x + v.off + (long long)i1 * v.st[a1] + (long long)i2 * v.st[a2];
+  const long long s = v.st[axis];
+  for (int i = 0; i < n; ++i) {
+    T acc = base[i * s];
+    for (int e = 1; e <= p && e <= i; ++e) acc -= F[i * w + e] * base[(i - e) * s];
+    base[i * s] = acc * F[i * w];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    T acc = base[i * s];
+    for (int e = 1; e <= p && i + e < n; ++e) acc -= F[(i + e) * w + e] * base[(i + e) * s];
+    base[i * s] = acc * F[i * w];
+  }
+}
+
+template <typename T, typename TIn>
+void launch_contract(const LayoutDev& L, int axis, const AxisOp* ops, int nops, int max_out, const TIn* in, T* out,
+                     int* status, cudaStream_t st) {
+  dim3 grid((max_out + 127) / 128, nops);
+  k_contract<T, TIn><<<grid, 128, 0, st>>>(L, axis, ops, in, out, status);
+}
+
+template <typename T>
+void launch_expand(const LayoutDev& L, int axis, const AxisOp* ops, int nops, long long max_out, const T* in, T* out,
+                   cudaStream_t st) {
+  long long blocks = (max_out + 255) / 256;
+  if (blocks > 65535) blocks = 65535;
+  dim3 grid((unsigned)blocks, nops);
+  k_expand<T><<<grid, 256, 0, st>>>(L, axis, ops, in, out);
+}
+
+template <typename T, typename TQ>
+void launch_expand_residual(const LayoutDev& L, int axis, const AxisOp* op, long long nout, const T* in, const TQ* q,
+                            double* partials, int nblocks, cudaStream_t st) {
+  k_expand_residual<T, TQ><<<nblocks, 256, 0, st>>>(L, axis, op, in, q, partials);
+}
+
+void launch_reduce_partials(const double* partials, int nblocks, double* result, cudaStream_t st) {
+  k_reduce_partials<<<1, 256, 0, st>>>(partials, nblocks, result);
+}
+
+template <typename T>
+void launch_band_apply(const LayoutDev& L, int axis, const AxisOp* ops, int nops, int max_out, const T* in, T* out,
+                       cudaStream_t st) {
+  dim3 grid((max_out + 127) / 128, nops);
+  k_band_apply<T><<<grid, 128, 0, st>>>(L, axis, ops, in, out);
+}
+
+template <typename T>
+void launch_band_solve(const LayoutDev& L, int axis, bool useU, const AxisOp* ops, int nops, int max_fibres, T* x,
+                       cudaStream_t st) {
+  dim3 grid((max_fibres + 63) / 64, nops);
+  k_band_solve<T><<<grid, 64, 0, st>>>(L, axis, useU, ops, x);
+}
+
+template void launch_contract<double, double>(const LayoutDev&, int, const AxisOp*, int, int, const double*, double*,
+                                              int*, cudaStream_t);
+template void launch_contract<double, float>(const LayoutDev&, int, const AxisOp*, int, int, const float*, double*,
+                                             int*, cudaStream_t);
+template void launch_contract<float, float>(const LayoutDev&, int, const AxisOp*, int, int, const float*, float*, int*,
+                                            cudaStream_t);
+template void launch_contract<float, double>(const LayoutDev&, int, const AxisOp*, int, int, const double*, float*,
+                                             int*, cudaStream_t);
+template void launch_expand<double>(const LayoutDev&, int, const AxisOp*, int, long long, const double*, double*,
+                                    cudaStream_t);
+template void launch_expand<float>(const LayoutDev&, int, const AxisOp*, int, long long, const float*, float*,
+                                   cudaStream_t);
+template void launch_expand_residual<double, double>(const LayoutDev&, int, const AxisOp*, long long, const double*,
+                                                     const double*, double*, int, cudaStream_t);
+template void launch_expand_residual<double, float>(const LayoutDev&, int, const AxisOp*, long long, const double*,
+                                                    const float*, double*, int, cudaStream_t);
+template void launch_expand_residual<float, float>(const LayoutDev&, int, const AxisOp*, long long, const float*,
+                                                   const float*, double*, int, cudaStream_t);
+template void launch_expand_residual<float, double>(const LayoutDev&, int, const AxisOp*, long long, const float*,
+                                                    const double*, double*, int, cudaStream_t);
+template void launch_band_apply<double>(const LayoutDev&, int, const AxisOp*, int, int, const double*, double*,
+                                        cudaStream_t);
+template void launch_band_apply<float>(const LayoutDev&, int, const AxisOp*, int, int, const float*, float*,
+                                       cudaStream_t);
+template void launch_band_solve<double>(const LayoutDev&, int, bool, const AxisOp*, int, int, double*, cudaStream_t);
+template void launch_band_solve<float>(const LayoutDev&, int, bool, const AxisOp*, int, int, float*, cudaStream_t);
+
+}  // namespace mfa

@@ -1,0 +1,151 @@
+// Setup kernels (Algorithm 1 "Setup"): Cox-de Boor basis tables, banded
+// per-axis Gram matrices of every subdomain window and their Cholesky factors.
+// All three are tiny (per-axis work, O(M_a p^2)); they run in FP64.
+#include "mfa_internal.cuh"
+
+namespace mfa {
+
+// Knot t_i of the clamped uniform knot vector with `nspans` spans, degree p.
+__device__ __forceinline__ double knot_at(int i, int p, int nspans) {
+  if (i <= p) return 0.0;
+  if (i >= nspans + p) return 1.0;
+  return (double)(i - p) / (double)nspans;
+}
+
+// Basis values N_{j+r,p}(u), r = 0..p, on knot span j (global span index) by
+// the Cox-de Boor recurrence (Sec. 2.1, Eq. nurbs-basis with W = 1), raising
+// the degree from 0 to p on the p+1 functions that are nonzero on the span.
+// Writing i = j + p for the knot index of the span's left end, degree q keeps
+// Nq[r] = N_{i-q+r,q} for r = 0..q and
+//   Nq[r] = (u - t_{i-q+r}) / (t_{i+r} - t_{i-q+r}) * N_{q-1}[r-1]
+//         + (t_{i+r+1} - u) / (t_{i+r+1} - t_{i-q+r+1}) * N_{q-1}[r].
+// Both denominators are positive on a non-empty span.
+__device__ void cox_de_boor(int j, double u, int p, int nspans, double* N) {
+  const int i = j + p;
+  N[0] = 1.0;
+  for (int q = 1; q <= p; ++q) {
+    double carry = 0.0;  // contribution of N_{q-1}[r-1] to Nq[r]
+    for (int r = 0; r < q; ++r) {
+      const double tl = knot_at(i - q + r + 1, p, nspans);
+      const double tr = knot_at(i + r + 1, p, nspans);
+      const double w = N[r] / (tr - tl);
+      const double right = (tr - u) * w;            // N_{q-1}[r] -> Nq[r]
+      const double left_next = (u - tl) * w;        // N_{q-1}[r] -> Nq[r+1]
+      N[r] = carry + right;
+      carry = left_next;
+    }
+    N[q] = carry;
+  }
+}
+
+__global__ void k_basis(int M, int nspans, int p, int* span, double* vd, float* vf) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= M) return;
+  // span index: largest j with j/nspans <= k/(M-1), exact in integers
+  int j = 0;
+  double u = 0.0;
+  if (M > 1) {
+    long long num = (long long)k * nspans;
+    j = (int)(num / (M - 1));
+    if (j > nspans - 1) j = nspans - 1;
+    u = (double)k / (double)(M - 1);
+  }
+  double N[MFA_MAX_DEGREE + 1];
+  cox_de_boor(j, u, p, nspans, N);
+  span[k] = j;
+  for (int r = 0; r <= p; ++r) {
+    vd[(long long)k * (p + 1) + r] = N[r];
+    vf[(long long)k * (p + 1) + r] = (float)N[r];
+  }
+}
+
+void launch_basis(const AxisDev& ax, int* span, double* vd, float* vf, cudaStream_t st) {
+  int threads = 128;
+  int blocks = (ax.M + threads - 1) / threads;
+  k_basis<<<blocks, threads, 0, st>>>(ax.M, ax.nspans, ax.p, span, vd, vf);
+}
+
+// Gram band of one window: A_L = N_L^T N_L summed over the window's points
+// (the normal matrix of Eq. minimization-problem along one axis).  Each data
+// point touches the p+1 control points of its span; the point sitting on the
+// window's closing breakpoint has a zero last value whose index lies past L
+// and is skipped.  One thread per piece; serial FP64 sums.
+__global__ void k_gram(AxisDev ax, double* AL) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= ax.S) return;
+  const AxisSub sb = ax.subs[s];
+  const int p = ax.p, w = p + 1;
+  double* A = AL + (long long)sb.bandL * w;
+  for (int i = 0; i < sb.nL * w; ++i) A[i] = 0.0;
+  for (int k = sb.k0; k < sb.k0 + sb.m; ++k) {
+    const int j = ax.span[k];
+    const double* v = ax.vals_d + (long long)k * w;
+    for (int r = 0; r <= p; ++r) {
+      const int l = j + r - sb.l0;
+      if (l < 0 || l >= sb.nL) continue;
+      for (int r2 = r; r2 <= p; ++r2) {
+        const int l2 = j + r2 - sb.l0;
+        if (l2 >= sb.nL) continue;
+        A[l * w + (r2 - r)] += v[r] * v[r2];
+      }
+    }
+  }
+}
+
+void launch_gram(const AxisDev& ax, double* AL, cudaStream_t st) {
+  k_gram<<<(ax.S + 63) / 64, 64, 0, st>>>(ax, AL);
+}
+
+// Banded Cholesky A = L L^T of the n x n principal block of A_L starting at
+// row `o` (Sec. 2.3.1: Cholesky on the normal equations).  Row-oriented:
+//   L(i,j) = (A(j,i) - sum_{k<j} L(i,k) L(j,k)) / L(j,j),  i-p <= j < i
+//   L(i,i) = sqrt(A(i,i) - sum_{k<i} L(i,k)^2).
+// A pivot that is not positive, or falls below 1e-13 of its diagonal entry,
+// marks the status word MFA_ERR_NOT_SPD and the factor is left unusable.
+__device__ void band_cholesky(const double* A, int o, int n, int p, double* F, float* Ff, int* status) {
+  const int w = p + 1;
+  for (int i = 0; i < n; ++i) {
+    for (int e = p; e >= 1; --e) {
+      const int j = i - e;
+      if (j < 0) continue;
+      double s = A[(long long)(o + j) * w + e];
+      for (int f = e + 1; f <= p; ++f) {
+        if (i - f < 0) continue;
+        s -= F[i * w + f] * F[j * w + (f - e)];
+      }
+      F[i * w + e] = s * F[j * w];
+    }
+    const double aii = A[(long long)(o + i) * w];
+    double dsum = aii;
+    for (int e = 1; e <= p; ++e)
+      if (i - e >= 0) dsum -= F[i * w + e] * F[i * w + e];
+    if (!(dsum > 1e-13 * aii) || !(aii > 0.0)) {
+      atomicExch(status, MFA_ERR_NOT_SPD);
+      dsum = 1.0;
+    }
+    F[i * w] = 1.0 / sqrt(dsum);
+  }
+  for (int i = 0; i < n * w; ++i) Ff[i] = (float)F[i];
+}
+
+__global__ void k_chol(AxisDev ax, const double* AL, double* fLd, float* fLf, double* fUd, float* fUf,
+                       int* status) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * ax.S) return;
+  const int s = t >> 1;
+  const AxisSub sb = ax.subs[s];
+  const int w = ax.p + 1;
+  const double* A = AL + (long long)sb.bandL * w;
+  if ((t & 1) == 0)
+    band_cholesky(A, 0, sb.nL, ax.p, fLd + (long long)sb.bandL * w, fLf + (long long)sb.bandL * w, status);
+  else
+    band_cholesky(A, sb.oU, sb.nU, ax.p, fUd + (long long)sb.bandU * w, fUf + (long long)sb.bandU * w, status);
+}
+
+void launch_chol(const AxisDev& ax, const double* AL, double* fLd, float* fLf, double* fUd, float* fUf,
+                 int* status, cudaStream_t st) {
+  int n = 2 * ax.S;
+  k_chol<<<(n + 63) / 64, 64, 0, st>>>(ax, AL, fLd, fLf, fUd, fUf, status);
+}
+
+}  // namespace mfa

@@ -1,0 +1,941 @@
+// C ABI of the MFA library: layout builder, device tables, the launch
+// sequences of encode (setup + iteration 0), the Schwarz loop, decode and
+// residual.  See include/mfa.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mfa_internal.cuh"
+
+using namespace mfa;
+
+// ---------------------------------------------------------------------------
+// handle and model
+// ---------------------------------------------------------------------------
+
+struct mfa_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+  int* d_status = nullptr;
+  unsigned long long* d_metrics = nullptr;  // [4]
+  double* d_partials = nullptr;             // [4 * kResidualBlocks]
+  double* d_result = nullptr;               // [4]
+  double* h_pinned = nullptr;               // [16] readback
+  void* ws = nullptr;                       // growable scratch
+  size_t ws_size = 0;
+  int live_models = 0;
+};
+
+struct mfa_model {
+  mfa_handle* h = nullptr;
+  int prec = MFA_PREC_FP64;
+  int dim = 1;
+  int degree = 1;
+  double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
+  AxisHost axh[3];
+  LayoutDev L{};
+  int nsub = 1;
+  long long sizeL = 0, sizeS1 = 0, sizeS2 = 0;
+  int maxL = 0, maxU = 0, maxS1 = 0, maxS2 = 0;
+  int maxOut[3] = {0, 0, 0};      // projection stage output sizes
+  int maxApply[3] = {0, 0, 0};    // band-apply output sizes
+  int maxFibL[3] = {0, 0, 0};     // fibres per solve, L boxes
+  int maxFibU[3] = {0, 0, 0};
+  void* arena = nullptr;          // device tables
+  void* big = nullptr;            // B_L, X, P, Pprev, S1, S2
+  // device pointers inside the arena
+  long long *offL = nullptr, *offS1 = nullptr, *offS2 = nullptr;
+  AxisOp* ops = nullptr;  // [kOpKinds][nsub]
+  // big buffers
+  void *BL = nullptr, *X = nullptr, *P = nullptr, *Pprev = nullptr, *S1 = nullptr, *S2 = nullptr;
+  int iters = 0;
+  int grow_streak = 0;
+  double last_dP = 0.0;
+  double last_jump = 0.0;
+};
+
+namespace {
+
+// op table rows
+enum OpKind { OP_PROJ0 = 0, OP_PROJ1, OP_PROJ2, OP_SOLVEL0, OP_SOLVEL1, OP_SOLVEL2, OP_APPLY0, OP_APPLY1, OP_APPLY2,
+              OP_SOLVEU0, OP_SOLVEU1, OP_SOLVEU2, OP_DEC0, OP_DEC1, OP_DEC2, kOpKinds };
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return MFA_OK;
+  if (e == cudaErrorMemoryAllocation) return MFA_ERR_OOM;
+  return MFA_ERR_CUDA;
+}
+
+int pool_alloc(mfa_handle* h, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  cudaError_t e = cudaMallocFromPoolAsync(p, bytes, h->pool, h->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? MFA_ERR_OOM : MFA_ERR_CUDA;
+  }
+  return MFA_OK;
+}
+
+void pool_free(mfa_handle* h, void* p) {
+  if (p) cudaFreeAsync(p, h->stream);
+}
+
+int ensure_ws(mfa_handle* h, size_t bytes) {
+  if (h->ws_size >= bytes) return MFA_OK;
+  pool_free(h, h->ws);
+  h->ws = nullptr;
+  h->ws_size = 0;
+  int rc = pool_alloc(h, &h->ws, bytes);
+  if (rc == MFA_OK) h->ws_size = bytes;
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// layout builder (Sec. 2.2): cores, windows, data ranges, U/L sets, owners
+// ---------------------------------------------------------------------------
+
+// Does control point g have a nonzero basis value at data point k?  Exact in
+// integers: the open support (t_{g-p}, t_{g+1}) in parameter space, plus the
+// clamped end values N_0(0) = N_{n-1}(1) = 1.
+bool in_open_support(long long k, int g, int p, int nspans, long long M) {
+  const int n = nspans + p;
+  if (M == 1) return true;
+  if (g == 0 && k == 0) return true;
+  if (g == n - 1 && k == M - 1) return true;
+  const long long lo = std::max(g - p, 0), hi = std::min(g + 1, nspans);
+  const long long x = k * nspans;
+  return lo * (M - 1) < x && x < hi * (M - 1);
+}
+
+// Schoenberg-Whitney condition for the window's collocation matrix: a
+// strictly increasing assignment of data points to the L control points with
+// nonzero basis value.  Greedy in control-point order.
+bool schoenberg_whitney(const AxisHost& ax, const AxisSub& sb) {
+  long long next = sb.k0;
+  for (int l = 0; l < sb.nL; ++l) {
+    const int g = sb.l0 + l;
+    bool found = false;
+    for (long long k = next; k < sb.k0 + sb.m; ++k) {
+      if (in_open_support(k, g, ax.p, ax.nspans, ax.M)) {
+        next = k + 1;
+        found = true;
+        break;
+      }
+    }
+    if (!found) return false;
+  }
+  return true;
+}
+
+int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int32_t* core, int delta) {
+  if (M < 1 || M > (1LL << 30)) return MFA_ERR_ARG;
+  if (nspans < 1 || nsub < 1 || nsub > nspans || delta < 0) return MFA_ERR_LAYOUT;
+  ax.M = (int)M;
+  ax.nspans = nspans;
+  ax.p = p;
+  ax.n = nspans + p;
+  ax.S = nsub;
+  std::vector<int> cs(nsub);
+  if (core) {
+    long long tot = 0;
+    for (int s = 0; s < nsub; ++s) {
+      cs[s] = core[s];
+      tot += core[s];
+    }
+    if (tot != nspans) return MFA_ERR_LAYOUT;
+  } else {
+    for (int s = 0; s < nsub; ++s) cs[s] = nspans / nsub + (s < nspans % nsub ? 1 : 0);
+  }
+  ax.subs.clear();
+  int a = 0, bandL = 0, bandU = 0;
+  for (int s = 0; s < nsub; ++s) {
+    if (cs[s] < std::max(p, 1)) return MFA_ERR_LAYOUT;  // cores need >= p spans
+    AxisSub sb{};
+    sb.a = a;
+    sb.b = a + cs[s];
+    sb.w0 = std::max(sb.a - delta, 0);
+    sb.w1 = std::min(sb.b + delta, nspans);
+    // closed window [w0/nspans, w1/nspans]: w0 (M-1) <= k nspans <= w1 (M-1)
+    if (M == 1) {
+      sb.k0 = 0;
+      sb.m = 1;
+    } else {
+      const long long k0 = (sb.w0 * (M - 1) + nspans - 1) / nspans;  // ceil
+      const long long k1 = (sb.w1 * (M - 1)) / nspans;                 // floor
+      if (k1 < k0) return MFA_ERR_LAYOUT;
+      sb.k0 = (int)k0;
+      sb.m = (int)(k1 - k0 + 1);
+    }
+    sb.l0 = sb.w0;
+    sb.nL = sb.w1 + p - sb.w0;
+    sb.oU = sb.a - sb.w0;
+    sb.nU = sb.b + p - sb.a;
+    sb.bandL = bandL;
+    sb.bandU = bandU;
+    bandL += sb.nL;
+    bandU += sb.nU;
+    if (!schoenberg_whitney(ax, sb)) return MFA_ERR_LAYOUT;
+    ax.subs.push_back(sb);
+    a = sb.b;
+  }
+  ax.bandL_rows = bandL;
+  ax.bandU_rows = bandU;
+  // owners of every global control point (1 or 2 per axis since cores >= p)
+  ax.own_first.assign(ax.n, -1);
+  ax.own_count.assign(ax.n, 0);
+  for (int s = 0; s < nsub; ++s) {
+    const AxisSub& sb = ax.subs[s];
+    for (int g = sb.a; g < sb.b + p; ++g) {
+      if (ax.own_first[g] < 0) ax.own_first[g] = s;
+      ax.own_count[g]++;
+    }
+  }
+  for (int g = 0; g < ax.n; ++g)
+    if (ax.own_count[g] < 1 || ax.own_count[g] > 2) return MFA_ERR_LAYOUT;
+  // first data point of every span (span of point k = floor(k nspans / (M-1)), capped)
+  ax.span_start.assign(nspans + 1, (int)M);
+  int j = 0;
+  for (long long k = 0; k < M; ++k) {
+    long long sk = (M == 1) ? 0 : (k * nspans) / (M - 1);
+    if (sk > nspans - 1) sk = nspans - 1;
+    while (j <= sk) ax.span_start[j++] = (int)k;
+  }
+  return MFA_OK;
+}
+
+}  // namespace
+
+namespace {
+
+// Byte sizes of the element type the model computes in.
+inline size_t elem_size(int prec) { return prec == MFA_PREC_FP64 ? sizeof(double) : sizeof(float); }
+
+View make_view(long long off, int n0, int n1, int n2, long long s0, long long s1, long long s2) {
+  View v;
+  v.off = off;
+  v.n[0] = n0;
+  v.n[1] = n1;
+  v.n[2] = n2;
+  v.st[0] = s0;
+  v.st[1] = s1;
+  v.st[2] = s2;
+  return v;
+}
+
+View contiguous(long long off, int n0, int n1, int n2) {
+  return make_view(off, n0, n1, n2, 1, n0, (long long)n0 * n1);
+}
+
+// Build every per-subdomain op table and the buffer offsets of a model.
+// Buffers per subdomain s: B_L and X are L-shaped (nL0 x nL1 x nL2) at offL[s];
+// S1 holds the first projection stage (nL0 x m1 x m2) and later the band-apply
+// ping buffer; S2 holds the second stage (nL0 x nL1 x m2) and the pong buffer.
+void build_ops(mfa_model* md, std::vector<AxisOp>& ops, std::vector<long long>& offL, std::vector<long long>& offS1,
+               std::vector<long long>& offS2) {
+  const int S0 = md->axh[0].S, S1 = md->axh[1].S, S2 = md->axh[2].S;
+  const int ns = S0 * S1 * S2;
+  ops.assign((size_t)kOpKinds * ns, AxisOp{});
+  offL.assign(ns, 0);
+  offS1.assign(ns, 0);
+  offS2.assign(ns, 0);
+  long long aL = 0, a1 = 0, a2 = 0;
+  const long long M0 = md->axh[0].M, M1 = md->axh[1].M;
+  for (int s = 0; s < ns; ++s) {
+    const int sa[3] = {s % S0, (s / S0) % S1, s / (S0 * S1)};
+    const AxisSub b[3] = {md->axh[0].subs[sa[0]], md->axh[1].subs[sa[1]], md->axh[2].subs[sa[2]]};
+    const int nL[3] = {b[0].nL, b[1].nL, b[2].nL}, nU[3] = {b[0].nU, b[1].nU, b[2].nU};
+    const int m[3] = {b[0].m, b[1].m, b[2].m};
+    const long long szL = (long long)nL[0] * nL[1] * nL[2];
+    const long long sz1 = std::max((long long)nL[0] * m[1] * m[2], szL);
+    const long long sz2 = std::max((long long)nL[0] * nL[1] * m[2], szL);
+    offL[s] = aL;
+    offS1[s] = a1;
+    offS2[s] = a2;
+    aL += szL;
+    a1 += sz1;
+    a2 += sz2;
+    md->maxL = std::max<long long>(md->maxL, szL);
+    md->maxU = std::max(md->maxU, nU[0] * nU[1] * nU[2]);
+    auto at = [&](int kind) -> AxisOp& { return ops[(size_t)kind * ns + s]; };
+    // projection stages: Q window -> S1 -> S2 -> B_L, skipping padded axes
+    {
+      const int d = md->dim;
+      View in = make_view((long long)b[0].k0 + M0 * ((long long)b[1].k0 + M1 * b[2].k0), m[0], m[1], m[2], 1, M0,
+                          M0 * M1);
+      int cur[3] = {m[0], m[1], m[2]};
+      for (int a = 0; a < d; ++a) {
+        cur[a] = nL[a];
+        const long long off = (a == d - 1) ? offL[s] : (a == 0 ? offS1[s] : offS2[s]);
+        View out = contiguous(off, cur[0], cur[1], cur[2]);
+        AxisOp& op = at(OP_PROJ0 + a);
+        op.in = in;
+        op.out = out;
+        op.k0 = b[a].k0;
+        op.kend = b[a].k0 + b[a].m;
+        op.c0 = b[a].l0;
+        op.sa = sa[a];
+        md->maxOut[a] = std::max<long long>(md->maxOut[a], (long long)cur[0] * cur[1] * cur[2]);
+        in = out;
+      }
+    }
+    // iteration-0 solves over the L box of X, and U-box solves of later iterations
+    for (int a = 0; a < 3; ++a) {
+      AxisOp& opL = at(OP_SOLVEL0 + a);
+      opL.out = contiguous(offL[s], nL[0], nL[1], nL[2]);
+      opL.sa = sa[a];
+      AxisOp& opU = at(OP_SOLVEU0 + a);
+      opU.out = make_view(offL[s] + b[0].oU + (long long)nL[0] * (b[1].oU + (long long)nL[1] * b[2].oU), nU[0], nU[1],
+                          nU[2], 1, nL[0], (long long)nL[0] * nL[1]);
+      opU.sa = sa[a];
+      const int o1 = a == 0 ? 1 : 0, o2 = a == 2 ? 1 : 2;
+      md->maxFibL[a] = std::max(md->maxFibL[a], nL[o1] * nL[o2]);
+      md->maxFibU[a] = std::max(md->maxFibU[a], nU[o1] * nU[o2]);
+    }
+    // band applies: Pt (L box, in S2) -> S1 -> S2 -> S1 (ping-pong), rows restricted to U
+    {
+      int cur[3] = {nL[0], nL[1], nL[2]};
+      View in = contiguous(offS2[s], cur[0], cur[1], cur[2]);
+      for (int a = 0; a < md->dim; ++a) {
+        cur[a] = nU[a];
+        const long long off = (a % 2 == 0) ? offS1[s] : offS2[s];
+        View out = contiguous(off, cur[0], cur[1], cur[2]);
+        AxisOp& op = at(OP_APPLY0 + a);
+        op.in = in;
+        op.out = out;
+        op.sa = sa[a];
+        op.oU = b[a].oU;
+        md->maxApply[a] = std::max<long long>(md->maxApply[a], (long long)cur[0] * cur[1] * cur[2]);
+        in = out;
+      }
+    }
+  }
+  md->sizeL = aL;
+  md->sizeS1 = a1;
+  md->sizeS2 = a2;
+  // global decode stages (one op each): P (n0 x n1 x n2) -> ... -> grid (M0 x M1 x M2)
+  {
+    int cur[3] = {md->axh[0].n, md->axh[1].n, md->axh[2].n};
+    long long off = 0;
+    View in = contiguous(0, cur[0], cur[1], cur[2]);
+    for (int a = 0; a < md->dim; ++a) {
+      cur[a] = md->axh[a].M;
+      View out = contiguous(off, cur[0], cur[1], cur[2]);
+      AxisOp& op = ops[(size_t)(OP_DEC0 + a) * ns];
+      op.in = in;
+      op.out = out;
+      op.k0 = 0;
+      op.kend = md->axh[a].M;
+      op.c0 = 0;
+      op.sa = 0;
+      in = out;
+    }
+  }
+}
+
+struct Arena {
+  size_t used = 0;
+  template <typename T>
+  size_t take(size_t count) {
+    size_t off = used;
+    used = align256(used + count * sizeof(T));
+    return off;
+  }
+};
+
+template <typename T>
+T* at_off(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+
+// Launch the projection N^T Q (all subdomains) and iteration 0.
+template <typename T, typename TQ>
+void run_encode(mfa_model* md, const TQ* q) {
+  mfa_handle* h = md->h;
+  const LayoutDev& L = md->L;
+  const int ns = md->nsub;
+  T* BL = (T*)md->BL;
+  T* X = (T*)md->X;
+  T* S1 = (T*)md->S1;
+  T* S2 = (T*)md->S2;
+  auto opsk = [&](int kind) { return md->ops + (size_t)kind * ns; };
+  // projection: stage a reads the previous stage (the data for a = 0)
+  for (int a = 0; a < md->dim; ++a) {
+    T* out = (a == md->dim - 1) ? BL : (a == 0 ? S1 : S2);
+    if (a == 0)
+      launch_contract<T, TQ>(L, 0, opsk(OP_PROJ0), ns, md->maxOut[0], q, out, h->d_status, h->stream);
+    else
+      launch_contract<T, T>(L, a, opsk(OP_PROJ0 + a), ns, md->maxOut[a], a == 1 ? S1 : S2, out, nullptr, h->stream);
+  }
+  // iteration 0: unconstrained local solves on the L boxes
+  cudaMemcpyAsync(X, BL, md->sizeL * sizeof(T), cudaMemcpyDeviceToDevice, h->stream);
+  for (int a = 0; a < md->dim; ++a)
+    launch_band_solve<T>(L, a, false, opsk(OP_SOLVEL0 + a), ns, md->maxFibL[a], X, h->stream);
+  cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
+  launch_average<T>(L, md->offL, X, (T*)md->P, nullptr, h->d_metrics, h->stream);
+}
+
+// One Schwarz iteration k >= 1 in control-point space.
+template <typename T>
+void run_step(mfa_model* md) {
+  mfa_handle* h = md->h;
+  const LayoutDev& L = md->L;
+  const int ns = md->nsub;
+  T* S1 = (T*)md->S1;
+  T* S2 = (T*)md->S2;
+  auto opsk = [&](int kind) { return md->ops + (size_t)kind * ns; };
+  std::swap(md->P, md->Pprev);  // Pprev <- P^{k-1}
+  launch_frame_gather<T>(L, md->offS2, md->maxL, (const T*)md->Pprev, S2, h->stream);
+  for (int a = 0; a < md->dim; ++a) {
+    const T* in = (a % 2 == 0) ? S2 : S1;
+    T* out = (a % 2 == 0) ? S1 : S2;
+    launch_band_apply<T>(L, a, opsk(OP_APPLY0 + a), ns, md->maxApply[a], in, out, h->stream);
+  }
+  const T* Y = (md->dim % 2 == 1) ? S1 : S2;
+  const long long* offY = (md->dim % 2 == 1) ? md->offS1 : md->offS2;
+  launch_rhs_finalize<T>(L, md->offL, offY, md->maxU, (const T*)md->BL, Y, (T*)md->X, h->stream);
+  for (int a = 0; a < md->dim; ++a)
+    launch_band_solve<T>(L, a, true, opsk(OP_SOLVEU0 + a), ns, md->maxFibU[a], (T*)md->X, h->stream);
+  cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
+  launch_average<T>(L, md->offL, (const T*)md->X, (T*)md->P, (const T*)md->Pprev, h->d_metrics, h->stream);
+}
+
+// Global grid decode; the last axis either writes `out` (type T) or is fused
+// with the residual against q.
+template <typename T, typename TQ>
+int run_decode_grid(mfa_model* md, T* out, const TQ* q) {
+  mfa_handle* h = md->h;
+  const LayoutDev& L = md->L;
+  const int ns = md->nsub;
+  const int d = md->dim;
+  // scratch for intermediate stages
+  long long sz[3] = {0, 0, 0};
+  {
+    long long cur[3] = {md->axh[0].n, md->axh[1].n, md->axh[2].n};
+    for (int a = 0; a < d; ++a) {
+      cur[a] = md->axh[a].M;
+      sz[a] = cur[0] * cur[1] * cur[2];
+    }
+  }
+  size_t need = 0;
+  if (d >= 2) need += align256(sz[0] * sizeof(T));
+  if (d >= 3) need += align256(sz[1] * sizeof(T));
+  int rc = ensure_ws(h, std::max<size_t>(need, 256));
+  if (rc != MFA_OK) return rc;
+  T* bufA = (T*)h->ws;
+  T* bufB = (T*)((char*)h->ws + align256(sz[0] * sizeof(T)));
+  const T* in = (const T*)md->P;
+  for (int a = 0; a < d; ++a) {
+    const AxisOp* op = md->ops + (size_t)(OP_DEC0 + a) * ns;
+    const bool last = a == d - 1;
+    if (last) {
+      if (q) {
+        launch_expand_residual<T, TQ>(L, a, op, sz[a], in, q, h->d_partials, kResidualBlocks, h->stream);
+        launch_reduce_partials(h->d_partials, kResidualBlocks, h->d_result, h->stream);
+      } else {
+        launch_expand<T>(L, a, op, 1, sz[a], in, out, h->stream);
+      }
+    } else {
+      T* o = (a == 0) ? bufA : bufB;
+      launch_expand<T>(L, a, op, 1, sz[a], in, o, h->stream);
+      in = o;
+    }
+  }
+  return MFA_OK;
+}
+
+int read_status(mfa_handle* h) {
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(h->h_pinned, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::memcpy(&st, h->h_pinned, sizeof(int));
+  if (st != 0) cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream);
+  return st;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char* mfa_status_string(int s) {
+  switch (s) {
+    case MFA_OK: return "ok";
+    case MFA_NOT_CONVERGED: return "not converged (max_iters reached)";
+    case MFA_ERR_ARG: return "invalid argument";
+    case MFA_ERR_LAYOUT: return "invalid layout";
+    case MFA_ERR_OOM: return "device out of memory";
+    case MFA_ERR_CUDA: return "CUDA error";
+    case MFA_ERR_NOT_SPD: return "local normal matrix not positive definite";
+    case MFA_ERR_DIVERGED: return "Schwarz iteration diverged";
+    case MFA_ERR_NONFINITE: return "non-finite input data";
+    case MFA_ERR_UNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+  }
+}
+
+int mfa_create(int device, void* cuda_stream, mfa_handle** out) {
+  if (!out) return MFA_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return MFA_ERR_ARG;
+  }
+  DeviceGuard g(device);
+  mfa_handle* h = new (std::nothrow) mfa_handle();
+  if (!h) return MFA_ERR_OOM;
+  h->device = device;
+  h->stream = (cudaStream_t)cuda_stream;
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  cudaError_t e = cudaMemPoolCreate(&h->pool, &props);
+  if (e == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    e = cudaMemPoolSetAttribute(h->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_status, 256);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_metrics, 256);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_partials, 4 * sizeof(double) * kResidualBlocks);
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_result, 256);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_pinned, 256);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, 256, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    mfa_destroy(h);
+    return cuda_status(e);
+  }
+  *out = h;
+  return MFA_OK;
+}
+
+int mfa_destroy(mfa_handle* h) {
+  if (!h) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  cudaStreamSynchronize(h->stream);
+  if (h->ws) cudaFreeAsync(h->ws, h->stream);
+  cudaStreamSynchronize(h->stream);
+  if (h->pool) cudaMemPoolDestroy(h->pool);
+  cudaFree(h->d_status);
+  cudaFree(h->d_metrics);
+  cudaFree(h->d_partials);
+  cudaFree(h->d_result);
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  delete h;
+  return MFA_OK;
+}
+
+int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype, int q_on_device, mfa_model** out) {
+  if (!h || !lay || !q || !out) return MFA_ERR_ARG;
+  *out = nullptr;
+  if (lay->dim < 1 || lay->dim > MFA_MAX_DIM) return MFA_ERR_ARG;
+  if (lay->degree < 1 || lay->degree > MFA_MAX_DEGREE) return MFA_ERR_ARG;
+  if (q_dtype != MFA_F32 && q_dtype != MFA_F64) return MFA_ERR_ARG;
+  if (lay->precision != MFA_PREC_FP64 && lay->precision != MFA_PREC_MIXED) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  mfa_model* md = new (std::nothrow) mfa_model();
+  if (!md) return MFA_ERR_OOM;
+  md->h = h;
+  md->prec = lay->precision;
+  md->dim = lay->dim;
+  md->degree = lay->degree;
+  long long npts_total = 1;
+  for (int a = 0; a < 3; ++a) {
+    int rc;
+    if (a < lay->dim) {
+      if (lay->npts[a] < 1) {
+        delete md;
+        return MFA_ERR_ARG;
+      }
+      rc = build_axis(md->axh[a], lay->npts[a], lay->nspans[a], lay->degree, lay->nsub[a], lay->core_spans[a],
+                      lay->overlap[a]);
+      md->lo[a] = lay->lo[a];
+      md->hi[a] = lay->hi[a];
+      npts_total *= lay->npts[a];
+    } else {
+      rc = build_axis(md->axh[a], 1, 1, 0, 1, nullptr, 0);
+    }
+    if (rc != MFA_OK) {
+      delete md;
+      return rc;
+    }
+  }
+  if (npts_total > (1LL << 40)) {
+    delete md;
+    return MFA_ERR_ARG;
+  }
+  md->nsub = md->axh[0].S * md->axh[1].S * md->axh[2].S;
+  std::vector<AxisOp> ops;
+  std::vector<long long> offL, offS1, offS2;
+  build_ops(md, ops, offL, offS1, offS2);
+  const int ns = md->nsub;
+  // ---- device tables in one arena
+  Arena ar;
+  size_t o_span[3], o_vd[3], o_vf[3], o_ss[3], o_subs[3], o_of[3], o_oc[3], o_AL[3], o_fLd[3], o_fLf[3], o_fUd[3],
+      o_fUf[3];
+  for (int a = 0; a < 3; ++a) {
+    const AxisHost& ax = md->axh[a];
+    const int w = ax.p + 1;
+    o_span[a] = ar.take<int>(ax.M);
+    o_vd[a] = ar.take<double>((size_t)ax.M * w);
+    o_vf[a] = ar.take<float>((size_t)ax.M * w);
+    o_ss[a] = ar.take<int>(ax.nspans + 1);
+    o_subs[a] = ar.take<AxisSub>(ax.S);
+    o_of[a] = ar.take<int>(ax.n);
+    o_oc[a] = ar.take<int>(ax.n);
+    o_AL[a] = ar.take<double>((size_t)ax.bandL_rows * w);
+    o_fLd[a] = ar.take<double>((size_t)ax.bandL_rows * w);
+    o_fLf[a] = ar.take<float>((size_t)ax.bandL_rows * w);
+    o_fUd[a] = ar.take<double>((size_t)ax.bandU_rows * w);
+    o_fUf[a] = ar.take<float>((size_t)ax.bandU_rows * w);
+  }
+  const size_t o_offL = ar.take<long long>(ns), o_offS1 = ar.take<long long>(ns), o_offS2 = ar.take<long long>(ns);
+  const size_t o_ops = ar.take<AxisOp>(ops.size());
+  const size_t tables_bytes = ar.used;
+  // host staging image of the uploaded tables
+  std::vector<char> img(tables_bytes, 0);
+  for (int a = 0; a < 3; ++a) {
+    const AxisHost& ax = md->axh[a];
+    std::memcpy(img.data() + o_ss[a], ax.span_start.data(), sizeof(int) * ax.span_start.size());
+    std::memcpy(img.data() + o_subs[a], ax.subs.data(), sizeof(AxisSub) * ax.subs.size());
+    std::memcpy(img.data() + o_of[a], ax.own_first.data(), sizeof(int) * ax.n);
+    std::memcpy(img.data() + o_oc[a], ax.own_count.data(), sizeof(int) * ax.n);
+  }
+  std::memcpy(img.data() + o_offL, offL.data(), sizeof(long long) * ns);
+  std::memcpy(img.data() + o_offS1, offS1.data(), sizeof(long long) * ns);
+  std::memcpy(img.data() + o_offS2, offS2.data(), sizeof(long long) * ns);
+  std::memcpy(img.data() + o_ops, ops.data(), sizeof(AxisOp) * ops.size());
+  // big buffers
+  const size_t es = elem_size(md->prec);
+  Arena bg;
+  const size_t o_BL = bg.take<char>(md->sizeL * es), o_X = bg.take<char>(md->sizeL * es);
+  const long long ncp = (long long)md->axh[0].n * md->axh[1].n * md->axh[2].n;
+  const size_t o_P = bg.take<char>(ncp * es), o_Pp = bg.take<char>(ncp * es);
+  const size_t o_S1 = bg.take<char>(md->sizeS1 * es), o_S2 = bg.take<char>(md->sizeS2 * es);
+  // host data staging: the data are copied into the pool before use
+  const size_t qbytes = (size_t)npts_total * (q_dtype == MFA_F64 ? 8 : 4);
+  const size_t o_Q = q_on_device ? 0 : bg.take<char>(qbytes);
+  int rc = pool_alloc(h, &md->arena, tables_bytes);
+  if (rc == MFA_OK) rc = pool_alloc(h, &md->big, bg.used);
+  if (rc != MFA_OK) {
+    pool_free(h, md->arena);
+    pool_free(h, md->big);
+    delete md;
+    return rc;
+  }
+  cudaError_t e = cudaMemcpyAsync(md->arena, img.data(), tables_bytes, cudaMemcpyHostToDevice, h->stream);
+  // device layout struct
+  LayoutDev& L = md->L;
+  L.dim = md->dim;
+  L.nsub = ns;
+  for (int a = 0; a < 3; ++a) {
+    const AxisHost& ax = md->axh[a];
+    L.S[a] = ax.S;
+    L.ncp[a] = ax.n;
+    L.M[a] = ax.M;
+    AxisDev& d = L.ax[a];
+    d.M = ax.M;
+    d.nspans = ax.nspans;
+    d.p = ax.p;
+    d.n = ax.n;
+    d.S = ax.S;
+    d.span = at_off<int>(md->arena, o_span[a]);
+    d.vals_d = at_off<double>(md->arena, o_vd[a]);
+    d.vals_f = at_off<float>(md->arena, o_vf[a]);
+    d.span_start = at_off<int>(md->arena, o_ss[a]);
+    d.subs = at_off<AxisSub>(md->arena, o_subs[a]);
+    d.own_first = at_off<int>(md->arena, o_of[a]);
+    d.own_count = at_off<int>(md->arena, o_oc[a]);
+    d.AL = at_off<double>(md->arena, o_AL[a]);
+    d.facL_d = at_off<double>(md->arena, o_fLd[a]);
+    d.facL_f = at_off<float>(md->arena, o_fLf[a]);
+    d.facU_d = at_off<double>(md->arena, o_fUd[a]);
+    d.facU_f = at_off<float>(md->arena, o_fUf[a]);
+  }
+  md->offL = at_off<long long>(md->arena, o_offL);
+  md->offS1 = at_off<long long>(md->arena, o_offS1);
+  md->offS2 = at_off<long long>(md->arena, o_offS2);
+  md->ops = at_off<AxisOp>(md->arena, o_ops);
+  md->BL = at_off<char>(md->big, o_BL);
+  md->X = at_off<char>(md->big, o_X);
+  md->P = at_off<char>(md->big, o_P);
+  md->Pprev = at_off<char>(md->big, o_Pp);
+  md->S1 = at_off<char>(md->big, o_S1);
+  md->S2 = at_off<char>(md->big, o_S2);
+  // setup kernels: basis tables, Gram bands, Cholesky factors (FP64)
+  for (int a = 0; a < 3; ++a) {
+    AxisDev& d = L.ax[a];
+    launch_basis(d, const_cast<int*>(d.span), const_cast<double*>(d.vals_d), const_cast<float*>(d.vals_f), h->stream);
+  }
+  for (int a = 0; a < 3; ++a) launch_gram(L.ax[a], const_cast<double*>(L.ax[a].AL), h->stream);
+  for (int a = 0; a < 3; ++a)
+    launch_chol(L.ax[a], L.ax[a].AL, const_cast<double*>(L.ax[a].facL_d), const_cast<float*>(L.ax[a].facL_f),
+                const_cast<double*>(L.ax[a].facU_d), const_cast<float*>(L.ax[a].facU_f), h->d_status, h->stream);
+  const void* qd = q;
+  if (!q_on_device) {
+    // host data: copy and wait, so the caller may reuse its buffer on return
+    void* qbuf = at_off<char>(md->big, o_Q);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(qbuf, q, qbytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    qd = qbuf;
+  }
+  if (md->prec == MFA_PREC_FP64) {
+    if (q_dtype == MFA_F64)
+      run_encode<double, double>(md, (const double*)qd);
+    else
+      run_encode<double, float>(md, (const float*)qd);
+  } else {
+    if (q_dtype == MFA_F64)
+      run_encode<float, double>(md, (const double*)qd);
+    else
+      run_encode<float, float>(md, (const float*)qd);
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    pool_free(h, md->arena);
+    pool_free(h, md->big);
+    delete md;
+    return cuda_status(e);
+  }
+  md->iters = 0;
+  h->live_models++;
+  *out = md;
+  return MFA_OK;
+}
+
+int mfa_schwarz_iterate(mfa_handle* h, mfa_model* md, int32_t max_iters, double tol_dP, mfa_report* rep) {
+  if (!h || !md || md->h != h || max_iters < 0) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  int status = read_status(h);  // surfaces encode-time device errors
+  if (status < 0) return status;
+  int rc = MFA_NOT_CONVERGED;
+  for (int it = 0; it < max_iters; ++it) {
+    if (md->prec == MFA_PREC_FP64)
+      run_step<double>(md);
+    else
+      run_step<float>(md);
+    cudaError_t e = cudaMemcpyAsync(h->h_pinned, h->d_metrics, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    unsigned long long bits[3];
+    std::memcpy(bits, h->h_pinned, sizeof(bits));
+    double v[3];
+    std::memcpy(v, bits, sizeof(v));
+    const double dP = v[1] > 0 ? v[0] / v[1] : 0.0;
+    md->iters++;
+    if (md->iters > 1 && dP > md->last_dP && dP > 0)
+      md->grow_streak++;
+    else
+      md->grow_streak = 0;
+    md->last_dP = dP;
+    md->last_jump = v[2];
+    if (!std::isfinite(dP) || md->grow_streak >= 8) {
+      rc = MFA_ERR_DIVERGED;
+      break;
+    }
+    if (tol_dP > 0 && dP <= tol_dP) {
+      rc = MFA_OK;
+      break;
+    }
+  }
+  if (max_iters == 0) rc = MFA_OK;
+  status = read_status(h);
+  if (status < 0) rc = status;
+  if (rep) {
+    rep->iters = md->iters;
+    rep->status = rc;
+    rep->dP_rel = md->last_dP;
+    rep->jump_max = md->last_jump;
+  }
+  return rc;
+}
+
+int mfa_decode(mfa_handle* h, const mfa_model* mdc, const double* pts, int64_t npts_q, const int32_t* deriv, void* out,
+               int out_dtype, int out_on_device) {
+  mfa_model* md = const_cast<mfa_model*>(mdc);
+  if (!h || !md || md->h != h || !out) return MFA_ERR_ARG;
+  if (out_dtype != MFA_F32 && out_dtype != MFA_F64) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  int der[3] = {0, 0, 0};
+  if (deriv)
+    for (int a = 0; a < md->dim; ++a) {
+      if (deriv[a] < 0 || deriv[a] > md->degree) return MFA_ERR_ARG;
+      der[a] = deriv[a];
+    }
+  const size_t osz = out_dtype == MFA_F64 ? 8 : 4;
+  if (pts) {
+    if (npts_q < 0) return MFA_ERR_ARG;
+    if (npts_q == 0) return MFA_OK;
+    // scattered points: copy coordinates (host) to the workspace
+    const size_t pbytes = (size_t)npts_q * md->dim * sizeof(double);
+    const size_t obytes = out_on_device ? 0 : (size_t)npts_q * osz;
+    int rc = ensure_ws(h, align256(pbytes) + align256(obytes) + 256);
+    if (rc != MFA_OK) return rc;
+    double* dpts = (double*)h->ws;
+    void* dout = out_on_device ? out : (void*)((char*)h->ws + align256(pbytes));
+    cudaError_t e = cudaMemcpyAsync(dpts, pts, pbytes, cudaMemcpyDefault, h->stream);
+    if (md->prec == MFA_PREC_FP64)
+      launch_decode_points<double>(md->L, md->lo, md->hi, dpts, npts_q, der, (const double*)md->P, dout, out_dtype,
+                                   h->stream);
+    else
+      launch_decode_points<float>(md->L, md->lo, md->hi, dpts, npts_q, der, (const float*)md->P, dout, out_dtype,
+                                  h->stream);
+    if (e == cudaSuccess && !out_on_device)
+      e = cudaMemcpyAsync(out, dout, (size_t)npts_q * osz, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return cuda_status(e);
+  }
+  // full grid
+  if (der[0] || der[1] || der[2]) return MFA_ERR_UNSUPPORTED;
+  const long long n = (long long)md->axh[0].M * md->axh[1].M * md->axh[2].M;
+  const bool native = (md->prec == MFA_PREC_FP64) == (out_dtype == MFA_F64);
+  if (native && out_on_device) {
+    int rc = md->prec == MFA_PREC_FP64 ? run_decode_grid<double, double>(md, (double*)out, nullptr)
+                                       : run_decode_grid<float, float>(md, (float*)out, nullptr);
+    if (rc != MFA_OK) return rc;
+    return cuda_status(cudaGetLastError());
+  }
+  // decode into a pool buffer of the model's type, then convert / copy out
+  const size_t es = elem_size(md->prec);
+  void* tmp = nullptr;
+  int rc = pool_alloc(h, &tmp, n * es + (native ? 0 : n * osz));
+  if (rc != MFA_OK) return rc;
+  rc = md->prec == MFA_PREC_FP64 ? run_decode_grid<double, double>(md, (double*)tmp, nullptr)
+                                 : run_decode_grid<float, float>(md, (float*)tmp, nullptr);
+  cudaError_t e = cudaSuccess;
+  void* src = tmp;
+  if (rc == MFA_OK && !native) {
+    void* conv = (char*)tmp + n * es;
+    if (out_dtype == MFA_F64)
+      launch_cast<float>((const float*)tmp, (double*)conv, n, h->stream);
+    else
+      rc = MFA_ERR_UNSUPPORTED;  // FP64 model decoded to FP32 output: not offered
+    src = conv;
+  }
+  if (rc == MFA_OK) {
+    if (out_on_device)
+      e = cudaMemcpyAsync(out, src, n * osz, cudaMemcpyDeviceToDevice, h->stream);
+    else
+      e = cudaMemcpyAsync(out, src, n * osz, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess && !out_on_device) e = cudaStreamSynchronize(h->stream);
+  }
+  pool_free(h, tmp);
+  if (rc != MFA_OK) return rc;
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return cuda_status(e);
+}
+
+int mfa_residual(mfa_handle* h, const mfa_model* mdc, const void* q, int q_dtype, int q_on_device, mfa_report* rep) {
+  mfa_model* md = const_cast<mfa_model*>(mdc);
+  if (!h || !md || md->h != h || !q || !rep) return MFA_ERR_ARG;
+  if (q_dtype != MFA_F32 && q_dtype != MFA_F64) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  const long long n = (long long)md->axh[0].M * md->axh[1].M * md->axh[2].M;
+  const size_t qb = (size_t)n * (q_dtype == MFA_F64 ? 8 : 4);
+  void* qtmp = nullptr;
+  const void* qd = q;
+  cudaError_t e = cudaSuccess;
+  if (!q_on_device) {
+    int rc = pool_alloc(h, &qtmp, qb);
+    if (rc != MFA_OK) return rc;
+    e = cudaMemcpyAsync(qtmp, q, qb, cudaMemcpyHostToDevice, h->stream);
+    qd = qtmp;
+  }
+  int rc;
+  if (md->prec == MFA_PREC_FP64)
+    rc = q_dtype == MFA_F64 ? run_decode_grid<double, double>(md, nullptr, (const double*)qd)
+                            : run_decode_grid<double, float>(md, nullptr, (const float*)qd);
+  else
+    rc = q_dtype == MFA_F64 ? run_decode_grid<float, double>(md, nullptr, (const double*)qd)
+                            : run_decode_grid<float, float>(md, nullptr, (const float*)qd);
+  if (rc == MFA_OK && e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h_pinned, h->d_result, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (qtmp) pool_free(h, qtmp);
+  if (rc != MFA_OK) return rc;
+  if (e != cudaSuccess) return cuda_status(e);
+  double r[4];
+  std::memcpy(r, h->h_pinned, sizeof(r));
+  rep->rms_decoded = std::sqrt(r[0] / (double)n);
+  rep->maxabs_decoded = r[1];
+  rep->data_range = r[3] - r[2];
+  rep->iters = md->iters;
+  rep->dP_rel = md->last_dP;
+  rep->jump_max = md->last_jump;
+  int st = read_status(h);
+  rep->status = st;
+  return st < 0 ? st : MFA_OK;
+}
+
+int64_t mfa_num_ctrl(const mfa_model* md) {
+  if (!md) return MFA_ERR_ARG;
+  return (int64_t)md->axh[0].n * md->axh[1].n * md->axh[2].n;
+}
+
+int mfa_get_ctrl(mfa_handle* h, const mfa_model* mdc, double* host_out, int64_t cap) {
+  mfa_model* md = const_cast<mfa_model*>(mdc);
+  if (!h || !md || md->h != h || !host_out) return MFA_ERR_ARG;
+  const long long n = mfa_num_ctrl(md);
+  if (cap < n) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  int rc = ensure_ws(h, n * sizeof(double));
+  if (rc != MFA_OK) return rc;
+  if (md->prec == MFA_PREC_FP64)
+    launch_cast<double>((const double*)md->P, (double*)h->ws, n, h->stream);
+  else
+    launch_cast<float>((const float*)md->P, (double*)h->ws, n, h->stream);
+  cudaError_t e = cudaMemcpyAsync(host_out, h->ws, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = read_status(h);
+  return st < 0 ? st : MFA_OK;
+}
+
+int mfa_free(mfa_model* md) {
+  if (!md) return MFA_ERR_ARG;
+  mfa_handle* h = md->h;
+  DeviceGuard g(h->device);
+  pool_free(h, md->arena);
+  pool_free(h, md->big);
+  h->live_models--;
+  delete md;
+  return MFA_OK;
+}
+
+int mfa_sync(mfa_handle* h) {
+  if (!h) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  return read_status(h);
+}
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+// Internal declarations of the MFA library: device layout tables, batched
+// per-subdomain tensor views and the kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "mfa.h"
+
+namespace mfa {
+
+// One subdomain along one grid axis (Sec. 2.2, Eq. vecp-layout):
+//   core spans [a, b), window spans [w0, w1) = core + overlap per interior side,
+//   data points [k0, k0 + m) with parameter in the closed window interval,
+//   L = [l0, l0 + nL) control points touching the window,
+//   U = [l0 + oU, l0 + oU + nU) owned control points (support meets the core).
+struct AxisSub {
+  int a, b, w0, w1;
+  int k0, m;
+  int l0, nL;
+  int oU, nU;
+  int bandL;  // first row of this piece in the per-axis L band arrays
+  int bandU;  // first row of this piece in the per-axis U band arrays
+};
+
+// Per-axis device tables.
+struct AxisDev {
+  int M, nspans, p, n, S;
+  const int* span;          // [M] knot span of every data point
+  const double* vals_d;     // [M * (p+1)] N_{span+r,p}(u_k), r = 0..p
+  const float* vals_f;      // same, rounded to FP32
+  const int* span_start;    // [nspans + 1] first point whose span is >= j
+  const AxisSub* subs;      // [S]
+  const int* own_first;     // [n] first subdomain-axis index owning CP g
+  const int* own_count;     // [n] number of owners (1 or 2)
+  const double* AL;         // Gram band rows of every piece, upper storage: A(i, i+e) at [i*(p+1)+e]
+  const double* facL_d;     // Cholesky band of A_L: [i*(p+1)] = 1/L(i,i), [i*(p+1)+e] = L(i,i-e)
+  const float* facL_f;
+  const double* facU_d;     // Cholesky band of A_U (owned rows only)
+  const float* facU_f;
+};
+
+struct LayoutDev {
+  int dim;
+  int nsub;
+  int S[3];
+  long long ncp[3];    // n_a (1 for axes >= dim)
+  long long M[3];
+  AxisDev ax[3];
+};
+
+// A strided 3-D view: element (i0,i1,i2) at off + i0*st[0] + i1*st[1] + i2*st[2].
+struct View {
+  long long off;
+  long long st[3];
+  int n[3];
+};
+
+// One subdomain's operand description for an operation along one axis.
+struct AxisOp {
+  View in, out;
+  int k0;    // global index of point 0 on the point-indexed side of the axis
+  int kend;  // one past the last point that may contribute (contract)
+  int c0;    // global index of CP 0 on the CP-indexed side of the axis
+  int sa;    // subdomain-axis index along the op axis
+  int oU;    // row offset of the output inside L (band apply), 0 otherwise
+};
+
+// Host-side mirror of one axis.
+struct AxisHost {
+  int M = 1, nspans = 1, p = 0, n = 1, S = 1;
+  std::vector<AxisSub> subs;
+  std::vector<int> own_first, own_count, span_start;
+  int bandL_rows = 0, bandU_rows = 0;
+};
+
+// ---------------------------------------------------------------------------
+// kernel launchers (kernels_*.cu)
+// ---------------------------------------------------------------------------
+void launch_basis(const AxisDev& ax, int* span, double* vd, float* vf, cudaStream_t st);
+void launch_gram(const AxisDev& ax, double* AL, cudaStream_t st);
+void launch_chol(const AxisDev& ax, const double* AL, double* fLd, float* fLf, double* fUd, float* fUf,
+                 int* status, cudaStream_t st);
+
+template <typename T, typename TIn>
+void launch_contract(const LayoutDev& L, int axis, const AxisOp* ops, int nops, int max_out,
+                     const TIn* in, T* out, int* status, cudaStream_t st);
+template <typename T>
+void launch_expand(const LayoutDev& L, int axis, const AxisOp* ops, int nops, long long max_out,
+                   const T* in, T* out, cudaStream_t st);
+template <typename T, typename TQ>
+void launch_expand_residual(const LayoutDev& L, int axis, const AxisOp* op, long long nout, const T* in,
+                            const TQ* q, double* partials, int nblocks, cudaStream_t st);
+template <typename T>
+void launch_band_apply(const LayoutDev& L, int axis, const AxisOp* ops, int nops, int max_out,
+                       const T* in, T* out, cudaStream_t st);
+template <typename T>
+void launch_band_solve(const LayoutDev& L, int axis, bool useU, const AxisOp* ops, int nops, int max_fibres,
+                       T* x, cudaStream_t st);
+template <typename T>
+void launch_frame_gather(const LayoutDev& L, const long long* offL, int maxL, const T* P, T* Pt, cudaStream_t st);
+template <typename T>
+void launch_rhs_finalize(const LayoutDev& L, const long long* offL, const long long* offY, int maxU,
+                         const T* BL, const T* Y, T* X, cudaStream_t st);
+template <typename T>
+void launch_average(const LayoutDev& L, const long long* offL, const T* X, T* P, const T* Pprev,
+                    unsigned long long* metrics, cudaStream_t st);
+template <typename T>
+void launch_decode_points(const LayoutDev& L, const double* lo, const double* hi, const double* pts, long long npts,
+                          const int* deriv, const T* P, void* out, int out_dtype, cudaStream_t st);
+void launch_reduce_partials(const double* partials, int nblocks, double* result, cudaStream_t st);
+template <typename T>
+void launch_cast(const T* in, double* out, long long n, cudaStream_t st);
+
+constexpr int kResidualBlocks = 1216;  // 8 x 152 SMs
+
+}  // namespace mfa

@@ -1,0 +1,298 @@
+"""Thin ctypes binding of the MFA C ABI (include/mfa.h).
+
+Argument marshalling only: every step of the fit runs in the CUDA library.
+Loading fails loudly when the library has not been built; there is no CPU
+path.  PyTorch supplies device memory (tensor data pointers) and streams.
+
+Function names match the C entry points; ``Handle`` and ``Model`` wrap them.
+Grid arrays use the library's layout: shape (M_{d-1}, ..., M_0), C order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+MFA_OK = 0
+MFA_NOT_CONVERGED = 1
+MFA_ERR_ARG = -1
+MFA_ERR_LAYOUT = -2
+MFA_ERR_OOM = -3
+MFA_ERR_CUDA = -4
+MFA_ERR_NOT_SPD = -5
+MFA_ERR_DIVERGED = -6
+MFA_ERR_NONFINITE = -7
+MFA_ERR_UNSUPPORTED = -8
+MFA_F32, MFA_F64 = 0, 1
+MFA_PREC_FP64, MFA_PREC_MIXED = 0, 1
+
+EXPORTED = ["mfa_create", "mfa_destroy", "mfa_encode", "mfa_schwarz_iterate", "mfa_decode", "mfa_residual",
+            "mfa_get_ctrl", "mfa_num_ctrl", "mfa_free", "mfa_sync", "mfa_status_string"]
+
+
+class mfa_layout(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("degree", ctypes.c_int32), ("npts", ctypes.c_int64 * 3),
+                ("nspans", ctypes.c_int32 * 3), ("nsub", ctypes.c_int32 * 3),
+                ("core_spans", ctypes.POINTER(ctypes.c_int32) * 3), ("overlap", ctypes.c_int32 * 3),
+                ("precision", ctypes.c_int32), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+
+
+class mfa_report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("dP_rel", ctypes.c_double),
+                ("jump_max", ctypes.c_double), ("rms_decoded", ctypes.c_double),
+                ("maxabs_decoded", ctypes.c_double), ("data_range", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class MFAError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)} ({code})")
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load the built library (``__graft_entry__.build()`` or
+    ``python -m paper_2210_06528_gb300.build`` makes it)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"MFA CUDA library not built: {path} is missing (run the build first)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.mfa_create.argtypes = [ctypes.c_int, P, ctypes.POINTER(P)]
+    lib.mfa_destroy.argtypes = [P]
+    lib.mfa_encode.argtypes = [P, ctypes.POINTER(mfa_layout), P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(P)]
+    lib.mfa_schwarz_iterate.argtypes = [P, P, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(mfa_report)]
+    lib.mfa_decode.argtypes = [P, P, P, ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int]
+    lib.mfa_residual.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(mfa_report)]
+    lib.mfa_get_ctrl.argtypes = [P, P, P, ctypes.c_int64]
+    lib.mfa_num_ctrl.argtypes = [P]
+    lib.mfa_num_ctrl.restype = ctypes.c_int64
+    lib.mfa_free.argtypes = [P]
+    lib.mfa_sync.argtypes = [P]
+    lib.mfa_status_string.argtypes = [ctypes.c_int]
+    lib.mfa_status_string.restype = ctypes.c_char_p
+    for name in ["mfa_create", "mfa_destroy", "mfa_encode", "mfa_schwarz_iterate", "mfa_decode", "mfa_residual",
+                 "mfa_get_ctrl", "mfa_free", "mfa_sync"]:
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load().mfa_status_string(int(code)).decode()
+
+
+def _check(rc: int, where: str, ok=(MFA_OK,)) -> int:
+    if rc not in ok:
+        raise MFAError(rc, where)
+    return rc
+
+
+# ---------------------------------------------------------------------------
+# C-named wrappers (argument marshalling only)
+# ---------------------------------------------------------------------------
+
+def make_layout(dim, degree, npts, nspans, nsub, overlap, precision=MFA_PREC_FP64, core_spans=None, lo=None,
+                hi=None):
+    """Build an mfa_layout; the returned object keeps the core arrays alive."""
+    lay = mfa_layout()
+    lay.dim = dim
+    lay.degree = degree
+    keep = []
+    for a in range(3):
+        lay.npts[a] = int(npts[a]) if a < dim else 1
+        lay.nspans[a] = int(nspans[a]) if a < dim else 1
+        lay.nsub[a] = int(nsub[a]) if a < dim else 1
+        lay.overlap[a] = int(overlap[a] if not np.isscalar(overlap) else overlap) if a < dim else 0
+        lay.lo[a] = float(lo[a]) if lo is not None and a < dim else 0.0
+        lay.hi[a] = float(hi[a]) if hi is not None and a < dim else 1.0
+        if core_spans is not None and a < dim and core_spans[a] is not None:
+            arr = (ctypes.c_int32 * len(core_spans[a]))(*[int(c) for c in core_spans[a]])
+            keep.append(arr)
+            lay.core_spans[a] = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32))
+        else:
+            lay.core_spans[a] = ctypes.POINTER(ctypes.c_int32)()
+    lay.precision = precision
+    lay._keep = keep
+    return lay
+
+
+def mfa_create(device: int = 0, stream: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(load().mfa_create(device, ctypes.c_void_p(stream), ctypes.byref(h)), "mfa_create")
+    return h.value
+
+
+def mfa_destroy(h: int) -> None:
+    _check(load().mfa_destroy(ctypes.c_void_p(h)), "mfa_destroy")
+
+
+def mfa_encode(h: int, layout: mfa_layout, q_ptr: int, q_dtype: int, q_on_device: bool) -> int:
+    m = ctypes.c_void_p()
+    _check(load().mfa_encode(ctypes.c_void_p(h), ctypes.byref(layout), ctypes.c_void_p(q_ptr), q_dtype,
+                             int(q_on_device), ctypes.byref(m)), "mfa_encode")
+    return m.value
+
+
+def mfa_schwarz_iterate(h: int, m: int, max_iters: int, tol_dP: float):
+    rep = mfa_report()
+    rc = load().mfa_schwarz_iterate(ctypes.c_void_p(h), ctypes.c_void_p(m), int(max_iters), float(tol_dP),
+                                    ctypes.byref(rep))
+    _check(rc, "mfa_schwarz_iterate", ok=(MFA_OK, MFA_NOT_CONVERGED))
+    return rc, rep
+
+
+def mfa_decode(h: int, m: int, pts_ptr: int, npts_q: int, deriv, out_ptr: int, out_dtype: int,
+               out_on_device: bool) -> None:
+    d = None
+    if deriv is not None:
+        d = (ctypes.c_int32 * 3)(*(list(deriv) + [0] * (3 - len(deriv))))
+    _check(load().mfa_decode(ctypes.c_void_p(h), ctypes.c_void_p(m), ctypes.c_void_p(pts_ptr), int(npts_q),
+                             ctypes.cast(d, ctypes.c_void_p) if d is not None else None, ctypes.c_void_p(out_ptr),
+                             out_dtype, int(out_on_device)), "mfa_decode")
+
+
+def mfa_residual(h: int, m: int, q_ptr: int, q_dtype: int, q_on_device: bool) -> mfa_report:
+    rep = mfa_report()
+    _check(load().mfa_residual(ctypes.c_void_p(h), ctypes.c_void_p(m), ctypes.c_void_p(q_ptr), q_dtype,
+                               int(q_on_device), ctypes.byref(rep)), "mfa_residual")
+    return rep
+
+
+def mfa_num_ctrl(m: int) -> int:
+    return int(load().mfa_num_ctrl(ctypes.c_void_p(m)))
+
+
+def mfa_get_ctrl(h: int, m: int) -> np.ndarray:
+    n = mfa_num_ctrl(m)
+    out = np.empty(n, dtype=np.float64)
+    _check(load().mfa_get_ctrl(ctypes.c_void_p(h), ctypes.c_void_p(m), out.ctypes.data, n), "mfa_get_ctrl")
+    return out
+
+
+def mfa_free(m: int) -> None:
+    _check(load().mfa_free(ctypes.c_void_p(m)), "mfa_free")
+
+
+def mfa_sync(h: int) -> int:
+    return load().mfa_sync(ctypes.c_void_p(h))
+
+
+# ---------------------------------------------------------------------------
+# convenience classes
+# ---------------------------------------------------------------------------
+
+def _ptr_dtype(q):
+    """(pointer, dtype code, on_device, keepalive) for a torch tensor or numpy array."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(q, torch.Tensor):
+        if not q.is_contiguous():
+            q = q.contiguous()
+        if q.dtype == torch.float32:
+            code = MFA_F32
+        elif q.dtype == torch.float64:
+            code = MFA_F64
+        else:
+            raise TypeError("data must be float32 or float64")
+        return q.data_ptr(), code, q.is_cuda, q
+    a = np.ascontiguousarray(q)
+    if a.dtype == np.float32:
+        code = MFA_F32
+    elif a.dtype == np.float64:
+        code = MFA_F64
+    else:
+        raise TypeError("data must be float32 or float64")
+    return a.ctypes.data, code, False, a
+
+
+class Handle:
+    """A library handle on one device and stream (default: torch's current stream)."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.device = device
+        self.stream = stream
+        self.h = mfa_create(device, stream)
+
+    def encode(self, q, layout: mfa_layout) -> "Model":
+        ptr, code, dev, keep = _ptr_dtype(q)
+        m = mfa_encode(self.h, layout, ptr, code, dev)
+        return Model(self, m, layout)
+
+    def sync(self) -> int:
+        return mfa_sync(self.h)
+
+    def close(self):
+        if self.h:
+            mfa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Model:
+    """A fitted MFA resident on the device."""
+
+    def __init__(self, handle: Handle, m: int, layout: mfa_layout):
+        self.handle = handle
+        self.m = m
+        self.dim = layout.dim
+        self.degree = layout.degree
+        self.npts = [int(layout.npts[a]) for a in range(self.dim)]
+        self.ncp = [int(layout.nspans[a]) + layout.degree for a in range(self.dim)]
+
+    def iterate(self, max_iters: int, tol_dP: float = 0.0):
+        return mfa_schwarz_iterate(self.handle.h, self.m, max_iters, tol_dP)
+
+    def ctrl(self) -> np.ndarray:
+        return mfa_get_ctrl(self.handle.h, self.m).reshape(tuple(reversed(self.ncp)))
+
+    def residual(self, q) -> mfa_report:
+        ptr, code, dev, keep = _ptr_dtype(q)
+        return mfa_residual(self.handle.h, self.m, ptr, code, dev)
+
+    def decode_grid(self, out):
+        """Decode on the full data grid into ``out`` (torch tensor or numpy array)."""
+        ptr, code, dev, keep = _ptr_dtype(out)
+        mfa_decode(self.handle.h, self.m, 0, 0, None, ptr, code, dev)
+        return out
+
+    def decode_points(self, pts, out, deriv: Optional[Sequence[int]] = None):
+        """Decode at scattered physical points pts[k, a] (host or device FP64)."""
+        pptr, pcode, pdev, pkeep = _ptr_dtype(pts)
+        if pcode != MFA_F64:
+            raise TypeError("points must be float64")
+        optr, ocode, odev, okeep = _ptr_dtype(out)
+        n = pts.shape[0]
+        mfa_decode(self.handle.h, self.m, pptr, n, deriv, optr, ocode, odev)
+        return out
+
+    def free(self):
+        if self.m:
+            mfa_free(self.m)
+            self.m = None

@@ -1,0 +1,247 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle.
+
+FP64 path: every iterate's control points agree with the oracle's to a
+relative difference <= 1e-9 (max |dP| / max |P|).
+Mixed path: decoded RMS within 1% of the oracle's and max |decoded difference|
+<= 1e-5 of the data range.
+"""
+import numpy as np
+import pytest
+
+from mfa_cases import TOL_FP64, GpuRun, oracle_problem, rel_diff
+from oracle import mfa_oracle as O
+from paper_2210_06528_gb300 import inputs, mfa
+
+pytestmark = pytest.mark.gpu
+
+
+def _iterate_parity(Q, p, nspans, nsub, delta, iters, cores=None, on_device=True):
+    prob = oracle_problem(Q, p, nspans, nsub, delta, cores)
+    g = GpuRun(Q, p, nspans, nsub, delta, cores=cores, on_device=on_device)
+    try:
+        st = O.schwarz_initial(prob, Q)
+        assert rel_diff(g.ctrl(), st.P) <= TOL_FP64, "iteration 0"
+        for k in range(1, iters + 1):
+            st = O.schwarz_step(prob, Q, st)
+            rc, rep = g.iterate(1)
+            assert rep.iters == k
+            assert rel_diff(g.ctrl(), st.P) <= TOL_FP64, f"iteration {k}"
+            h = st.history[-1]
+            assert abs(rep.dP_rel - h["dP_rel"]) <= 1e-11 + 1e-6 * h["dP_rel"]
+            assert abs(rep.jump_max - h["spread"]) <= 1e-11 * max(np.abs(st.P).max(), 1) + 1e-6 * h["spread"]
+        res = g.residual()
+        ref = O.residual_stats(prob, Q, st.P)
+        assert abs(res.rms_decoded - ref["rms"]) <= 1e-8 * max(ref["rms"], 1e-12) + 1e-13
+        assert abs(res.maxabs_decoded - ref["max"]) <= 1e-8 * max(ref["max"], 1e-12) + 1e-13
+        assert abs(res.data_range - (Q.max() - Q.min())) <= 1e-12 * (Q.max() - Q.min())
+        D = g.decode_grid()
+        Dref = O.decode_grid(prob, st.P)
+        assert np.abs(D - Dref).max() <= 1e-10 * max(np.abs(Dref).max(), 1)
+    finally:
+        g.close()
+
+
+def test_config1_sinc_1d_fp64_full():
+    """1-D plain method: 1024 points of sin(x)/x on [-4pi, 4pi], p=3, 4 subdomains
+    of 32 core spans, overlap 2, Schwarz to dP_rel <= 1e-10."""
+    Q = inputs.sinc_1d(1024)
+    prob = oracle_problem(Q, 3, [128], [4], 2)
+    ref = O.schwarz_solve(prob, Q, max_iters=200, tol_dP=1e-10, keep_iterates=True)
+    g = GpuRun(Q, 3, [128], [4], 2)
+    try:
+        assert rel_diff(g.ctrl(), ref["iterates"][0]) <= TOL_FP64
+        rc, rep = g.iterate(200, 1e-10)
+        assert rc == mfa.MFA_OK
+        assert rep.iters == ref["iters"]
+        assert rel_diff(g.ctrl(), ref["P"]) <= TOL_FP64
+        res = g.residual()
+        oref = O.residual_stats(prob, Q, ref["P"])
+        assert abs(res.rms_decoded - oref["rms"]) <= 1e-6 * oref["rms"]
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("p,delta", [(1, 0), (1, 1), (2, 1), (3, 0), (3, 2), (3, 3), (4, 2), (5, 1), (5, 6)])
+def test_1d_iterates(p, delta):
+    M = 301  # ragged: 301 points over 60 spans
+    Q = inputs.asymmetric_sinc_1d(M)
+    _iterate_parity(Q, p, [60], [4], delta, iters=4)
+
+
+def test_1d_uneven_cores_and_host_input():
+    Q = inputs.symmetric_sinc_1d(257)
+    _iterate_parity(Q, 3, [50], [4], 2, iters=3, cores=[[9, 17, 4, 20]], on_device=False)
+
+
+@pytest.mark.parametrize("p,delta,nsub", [(2, 1, (3, 2)), (3, 2, (2, 3)), (3, 0, (4, 4)), (3, 3, (3, 3)),
+                                          (4, 4, (2, 2))])
+def test_2d_iterates(p, delta, nsub):
+    Q = inputs.paper_2d(97)  # 97 x 97 grid (ragged against the spans)
+    _iterate_parity(Q, p, [30, 27], list(nsub), delta, iters=3)
+
+
+def test_2d_rectangular_noise():
+    Q = inputs.random_field((83, 61), seed=11)
+    _iterate_parity(Q, 2, [26, 18], [3, 2], 1, iters=3)
+
+
+@pytest.mark.parametrize("p,delta,nsub", [(2, 1, (2, 2, 2)), (3, 2, (3, 2, 2)), (3, 0, (2, 2, 2)),
+                                          (3, 3, (2, 2, 2))])
+def test_3d_iterates(p, delta, nsub):
+    Q = inputs.paper_3d(29)
+    _iterate_parity(Q, p, [12, 11, 10], list(nsub), delta, iters=2)
+
+
+def test_3d_anisotropic_fp32_input():
+    Q = inputs.gauss_3d((37, 29, 23), seed=3, dtype=np.float32)
+    Qd = Q.astype(np.float64)
+    prob = oracle_problem(Qd, 3, [12, 9, 7], [2, 2, 1], 2)
+    g = GpuRun(Q, 3, [12, 9, 7], [2, 2, 1], 2)
+    try:
+        st = O.schwarz_initial(prob, Qd)
+        assert rel_diff(g.ctrl(), st.P) <= TOL_FP64
+        for _ in range(3):
+            st = O.schwarz_step(prob, Qd, st)
+            g.iterate(1)
+            assert rel_diff(g.ctrl(), st.P) <= TOL_FP64
+    finally:
+        g.close()
+
+
+def test_single_subdomain_equals_global_fit():
+    Q = inputs.paper_2d(64)
+    g = GpuRun(Q, 3, [20, 17], [1, 1], 2)
+    try:
+        prob = oracle_problem(Q, 3, [20, 17], [1, 1], 2)
+        Pg = O.global_fit(prob, Q)
+        assert rel_diff(g.ctrl(), Pg) <= TOL_FP64
+        rc, rep = g.iterate(3, 1e-14)
+        assert rep.dP_rel <= 1e-14
+        assert rel_diff(g.ctrl(), Pg) <= TOL_FP64
+    finally:
+        g.close()
+
+
+def test_overlap_ge_p_converges_to_global_fit():
+    Q = inputs.asymmetric_sinc_1d(400)
+    prob = oracle_problem(Q, 3, [80], [5], 3)
+    Pg = O.global_fit(prob, Q)
+    g = GpuRun(Q, 3, [80], [5], 3)
+    try:
+        rc, rep = g.iterate(300, 1e-14)
+        assert rc == mfa.MFA_OK
+        assert rel_diff(g.ctrl(), Pg) <= 1e-9
+        assert rep.jump_max <= 1e-10
+    finally:
+        g.close()
+
+
+def test_polynomial_reproduction_on_gpu():
+    Q = inputs.tensor_polynomial((45, 38), 3, seed=2)
+    g = GpuRun(Q, 3, [14, 12], [3, 3], 1)
+    try:
+        res = g.residual()
+        assert res.maxabs_decoded <= 1e-10 * res.data_range
+        rc, rep = g.iterate(1)
+        assert rep.dP_rel <= 1e-12
+    finally:
+        g.close()
+
+
+def test_scattered_decode_and_derivatives():
+    Q = inputs.paper_2d(50)
+    lo, hi = [-4.0, -4.0], [4.0, 4.0]
+    prob = oracle_problem(Q, 3, [16, 15], [2, 2], 3)
+    ref = O.schwarz_solve(prob, Q, max_iters=50, tol_dP=1e-13)
+    g = GpuRun(Q, 3, [16, 15], [2, 2], 3, lo=lo, hi=hi)
+    try:
+        g.iterate(50, 1e-13)
+        u = inputs.uniform_points(500, 2, seed=9)
+        u[:3] = [[0, 0], [1, 1], [0.5, 1.0]]
+        x = np.asarray(lo) + u * (np.asarray(hi) - np.asarray(lo))
+        for der in [(0, 0), (1, 0), (0, 2), (1, 1), (3, 2)]:
+            out = np.empty(len(u))
+            g.model.decode_points(np.ascontiguousarray(x), out, der)
+            oref = O.scattered_decode(prob, ref["P"], u, der) / (8.0 ** sum(der))
+            scale = max(np.abs(oref).max(), 1e-12)
+            assert np.abs(out - oref).max() <= 1e-8 * scale, der
+    finally:
+        g.close()
+
+
+def test_mixed_precision_2d_noise():
+    """FP32 data passes and control-point iteration; FP64 Gram/Cholesky."""
+    Q = inputs.sinc_2d(256, noise=1e-3, seed=0, dtype=np.float32)
+    Qd = Q.astype(np.float64)
+    prob = oracle_problem(Qd, 3, [64, 64], [4, 4], 2)
+    ref = O.schwarz_solve(prob, Qd, max_iters=30, tol_dP=1e-7)
+    g = GpuRun(Q, 3, [64, 64], [4, 4], 2, precision=mfa.MFA_PREC_MIXED)
+    try:
+        g.iterate(30, 1e-6)
+        res = g.residual()
+        oref = O.residual_stats(prob, Qd, ref["P"])
+        rng = float(Qd.max() - Qd.min())
+        assert abs(res.rms_decoded - oref["rms"]) <= 0.01 * oref["rms"]
+        D = g.decode_grid(np.float64)
+        Dref = O.decode_grid(prob, ref["P"])
+        assert np.abs(D - Dref).max() <= 1e-5 * rng
+    finally:
+        g.close()
+
+
+# ---------------------------------------------------------------------------
+# error paths (host-detected, or reported by the device status word)
+# ---------------------------------------------------------------------------
+
+def test_layout_rejections():
+    h = mfa.Handle(0)
+    try:
+        Q = np.zeros(100)
+        import torch
+        q = torch.zeros(100, dtype=torch.float64, device="cuda")
+        bad = [
+            dict(p=3, nspans=[20], nsub=[10], delta=1),      # cores of 2 spans < p
+            dict(p=3, nspans=[200], nsub=[2], delta=1),      # more CPs than points: Schoenberg-Whitney fails
+        ]
+        for b in bad:
+            lay = mfa.make_layout(1, b["p"], [100], b["nspans"], b["nsub"], [b["delta"]])
+            with pytest.raises(mfa.MFAError) as e:
+                h.encode(q, lay)
+            assert e.value.code == mfa.MFA_ERR_LAYOUT
+        lay = mfa.make_layout(1, 3, [100], [20], [2], [1], core_spans=[[5, 14]])  # does not sum to nspans
+        with pytest.raises(mfa.MFAError):
+            h.encode(q, lay)
+        lay = mfa.make_layout(1, 9, [100], [20], [2], [1])  # degree above the maximum
+        with pytest.raises(mfa.MFAError) as e:
+            h.encode(q, lay)
+        assert e.value.code == mfa.MFA_ERR_ARG
+        lay = mfa.make_layout(1, 3, [0], [20], [2], [1])  # empty grid
+        with pytest.raises(mfa.MFAError) as e:
+            h.encode(q, lay)
+        assert e.value.code == mfa.MFA_ERR_ARG
+        del Q
+    finally:
+        h.close()
+
+
+def test_nonfinite_input_reported():
+    import torch
+    Q = inputs.asymmetric_sinc_1d(200)
+    Q[77] = np.nan
+    h = mfa.Handle(0)
+    try:
+        q = torch.from_numpy(Q).cuda()
+        lay = mfa.make_layout(1, 3, [200], [40], [2], [1])
+        m = h.encode(q, lay)
+        with pytest.raises(mfa.MFAError) as e:
+            m.iterate(1)
+        assert e.value.code == mfa.MFA_ERR_NONFINITE
+        m.free()
+        # the handle stays usable
+        Q[77] = 0.0
+        m = h.encode(torch.from_numpy(Q).cuda(), lay)
+        rc, rep = m.iterate(2)
+        assert np.isfinite(rep.dP_rel)
+        m.free()
+    finally:
+        h.close()
