@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Throughput of the Schwarz-converged MFA encode on GB300.
+
+One step = mfa_encode (setup, projection, iteration 0) + mfa_schwarz_iterate
+to the stopping tolerance + mfa_residual (decoded RMS / max error), on one
+batch of synthetic data already resident in HBM.  ``value`` is data points
+per second over the whole job; ``e2e`` is the same metric through the C ABI
+with pinned host buffers (host->device copies of the data and the read-back
+of the control points inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference] [--workload 3d|2d|1d]
+
+With N > 1 (torchrun), every rank fits its own replica (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
+same workload on the host cores (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2210_06528_gb300 import inputs  # noqa: E402
+
+METRIC = "encode pts/s (Schwarz-converged) + decode pts/s vs plain GPU; serve p50/p99"
+
+WORKLOADS = {
+    # BASELINE 3-D workload: 512^3 FP32 grid of 16 seeded Gaussians + sin(6 pi x) cos(4 pi y) z,
+    # p = 3, 8x8x8 subdomains of 24 core spans (192 spans, 195 control points per axis), overlap 2.
+    "3d": dict(name="3d_512^3_gauss16_p3_8x8x8sub_24spans_overlap2_mixed", npts=(512, 512, 512), p=3,
+               nspans=(192, 192, 192), nsub=(8, 8, 8), delta=2, precision="mixed", tol=1e-6, max_iters=50,
+               sample=dict(npts=(128, 128, 128), nspans=(48, 48, 48), nsub=(2, 2, 2))),
+    # BASELINE 2-D workload: 1024^2 sinc(x) sinc(y) + N(0, 1e-3), p = 3, 4x4 subdomains of 64 core spans.
+    "2d": dict(name="2d_1024^2_sinc_noise1e-3_p3_4x4sub_64spans_overlap2_mixed", npts=(1024, 1024), p=3,
+               nspans=(256, 256), nsub=(4, 4), delta=2, precision="mixed", tol=1e-6, max_iters=50,
+               sample=dict(npts=(512, 512), nspans=(128, 128), nsub=(2, 2))),
+    # BASELINE 1-D workload: 1024 points of sin(x)/x, p = 3, 4 subdomains of 32 core spans, FP64.
+    "1d": dict(name="1d_1024_sinc_p3_4sub_32spans_overlap2_fp64", npts=(1024,), p=3, nspans=(128,), nsub=(4,),
+               delta=2, precision="fp64", tol=1e-10, max_iters=200,
+               sample=dict(npts=(1024,), nspans=(128,), nsub=(4,))),
+}
+
+
+def make_data(wl, npts, seed=0):
+    d = len(npts)
+    if d == 3:
+        return inputs.gauss_3d(tuple(npts), seed=seed, dtype=np.float32)
+    if d == 2:
+        return inputs.sinc_2d(npts[0], noise=1e-3, seed=seed, dtype=np.float32)
+    return inputs.sinc_1d(npts[0])
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_step(wl):
+    """One oracle run on the bounded sample of the workload; returns (points, seconds)."""
+    from oracle import mfa_oracle as O
+    smp = wl["sample"]
+    Q = make_data(wl, smp["npts"]).astype(np.float64)
+    prob = O.make_problem(wl["p"], list(smp["npts"]), list(smp["nspans"]), list(smp["nsub"]), wl["delta"])
+    t0 = time.perf_counter()
+    res = O.schwarz_solve(prob, Q, max_iters=wl["max_iters"], tol_dP=wl["tol"])
+    O.residual_stats(prob, Q, res["P"])
+    dt = time.perf_counter() - t0
+    return int(np.prod(smp["npts"])), dt
+
+
+def sample_desc(wl):
+    smp = wl["sample"]
+    return (f"{'x'.join(map(str, smp['npts']))} grid, {'x'.join(map(str, smp['nsub']))} subdomains with the "
+            f"workload's per-subdomain shape (p={wl['p']}, overlap {wl['delta']}, same points per span), "
+            f"oracle Schwarz to dP_rel <= {wl['tol']:g} + residual, FP64 numpy")
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def cpu_baseline(wl, budget_s=20.0):
+    pts, dt = oracle_sample_step(wl)  # first run includes imports / page-in
+    n, tot = 0, 0.0
+    while tot < budget_s and n < 50:
+        p2, d2 = oracle_sample_step(wl)
+        n += 1
+        tot += d2
+    return {"value": pts * n / tot, "unit": "pts/s", "cores": host_cores(), "kind": "oracle",
+            "sample": sample_desc(wl) + f", {n} runs"}
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_sample_step(wl)
+    times = []
+    pts = 0
+    for _ in range(args.steps):
+        pts, dt = oracle_sample_step(wl)
+        times.append(dt)
+    t = sum(times) / len(times)
+    value = pts / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "sample": sample_desc(wl)},
+            "cpu_baseline": {"value": value, "unit": "pts/s", "cores": host_cores(), "kind": "oracle",
+                             "sample": sample_desc(wl)},
+            "e2e": {"value": value, "unit": "pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def algorithmic_bytes(cls_name, wl, qbytes, model_info):
+    """Algorithmic bytes of one launch of a kernel class (what the method must
+    move): the data-reading kernels read every data value once."""
+    if cls_name in ("project_data", "residual"):
+        return qbytes
+    return None
+
+
+def run_gb300(args, wl):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2210_06528_gb300 import mfa
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    npts = wl["npts"]
+    Qnp = make_data(wl, npts, seed=rank)
+    q_dev = torch.from_numpy(Qnp).cuda()
+    q_host = torch.from_numpy(Qnp).pin_memory()
+    del Qnp
+    qbytes = q_dev.numel() * q_dev.element_size()
+    M = q_dev.numel()
+    prec = mfa.MFA_PREC_MIXED if wl["precision"] == "mixed" else mfa.MFA_PREC_FP64
+    d = len(npts)
+    lay = mfa.make_layout(d, wl["p"], npts, wl["nspans"], wl["nsub"], [wl["delta"]] * d, prec)
+    h = mfa.Handle(local)
+    stream = torch.cuda.current_stream()
+
+    iters_seen = []
+
+    def step(q):
+        m = h.encode(q, lay)
+        rc, rep = m.iterate(wl["max_iters"], wl["tol"])
+        res = m.residual(q)
+        iters_seen.append(rep.iters)
+        m.free()
+        return rep, res
+
+    for _ in range(args.warmup):
+        rep, res = step(q_dev)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident data
+    mfa.mfa_trace_enable(h.h, True)
+    iters_seen.clear()
+    clk = ClockSampler(local)
+    clk.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rep, res = step(q_dev)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    t_ms = e0.elapsed_time(e1) / args.steps
+    trace = mfa.trace_table(h.h)
+    mfa.mfa_trace_enable(h.h, False)
+    if world > 1:
+        tt = torch.tensor([t_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+    value = world * M / (t_ms * 1e-3)
+
+    # ---- decode throughput (grid decode into a device buffer)
+    m = h.encode(q_dev, lay)
+    m.iterate(wl["max_iters"], wl["tol"])
+    out = torch.empty_like(q_dev)
+    for _ in range(2):
+        m.decode_grid(out)
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    for _ in range(args.steps):
+        m.decode_grid(out)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    dec_ms = d0.elapsed_time(d1) / args.steps
+    ncp = mfa.mfa_num_ctrl(m.m)
+    m.free()
+    del out
+
+    # ---- end to end through the C ABI with pinned host buffers
+    def step_e2e():
+        m = h.encode(q_host, lay)  # host -> device copy inside
+        m.iterate(wl["max_iters"], wl["tol"])
+        m.residual(q_host)  # second host -> device copy of the data
+        P = m.ctrl()  # device -> host read of the control points
+        m.free()
+        return P
+
+    step_e2e()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        tt = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": world * M / e2e_s, "unit": "pts/s", "h2d_bytes_per_step": 2 * qbytes,
+           "d2h_bytes_per_step": ncp * 8}
+
+    # ---- roofline of the dominant kernel class
+    peak, peak_kind = load_peaks()
+    launches = sum(n for (_, n) in trace.values())
+    dom = max(trace.items(), key=lambda kv: kv[1][0]) if trace else None
+    roof = None
+    kernels = {k: {"ms_total": v[0], "launches": v[1], "ms_per_launch": v[0] / max(v[1], 1)} for k, v in trace.items()}
+    hbm_classes = {k: v for k, v in trace.items() if algorithmic_bytes(k, wl, qbytes, None)}
+    if hbm_classes:
+        name = max(hbm_classes.items(), key=lambda kv: kv[1][0])[0]
+        ms_per = trace[name][0] / trace[name][1]
+        ab = algorithmic_bytes(name, wl, qbytes, None)
+        achieved = ab / (ms_per * 1e-3) / 1e9
+        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": ab, "ms_per_launch": ms_per}
+    if rank != 0:
+        return
+    cpu = cpu_baseline(wl, budget_s=args.cpu_budget) if world == 1 and not args.no_cpu else None
+    line = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == mfa.MFA_PREC_MIXED else "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "points": M, "control_points": ncp, "precision": wl["precision"],
+                       "stop": f"dP_rel <= {wl['tol']:g}", "schwarz_iters": sorted(set(iters_seen)),
+                       "l2": "inputs larger than L2" if qbytes > 129e6 else "inputs smaller than L2",
+                       "parallelism": f"replicas x{world}"},
+            "decode_pts_per_s": world * M / (dec_ms * 1e-3), "decode_ms": dec_ms,
+            "roofline": roof, "dominant_kernel": dom[0] if dom else None, "kernels": kernels,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clocks,
+            "rms_decoded": res.rms_decoded, "maxabs_decoded": res.maxabs_decoded}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_gb300(args, wl)
+
+
+if __name__ == "__main__":
+    main()

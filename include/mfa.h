@@ -177,6 +177,21 @@ int mfa_sync(mfa_handle* h);
 /* Static text for a status code. */
 const char* mfa_status_string(int status);
 
+/* Tracing (per-phase timing of Algorithm 1's steps, as in the paper's
+ * setup / solve / iterate / decode breakdown, Sec. 3.2.4).  When enabled,
+ * every kernel launch of the handle is bracketed by CUDA events on the
+ * handle's stream and its duration is added to its kernel class.  Launch
+ * counts are kept whether or not timing is enabled.
+ *   mfa_trace_enable  enable (1) / disable (0) event timing; resets totals
+ *   mfa_trace_read    synchronises the stream, then returns the total
+ *                     milliseconds and launch count of kernel class `cls`
+ *                     since the last reset (cls in 0..MFA_TRACE_CLASSES-1)
+ *   mfa_trace_name    static name of a kernel class                        */
+#define MFA_TRACE_CLASSES 16
+int mfa_trace_enable(mfa_handle* h, int enable);
+int mfa_trace_read(mfa_handle* h, int32_t cls, double* total_ms, int64_t* launches);
+const char* mfa_trace_name(int32_t cls);
+
 #ifdef __cplusplus
 }
 #endif

@@ -30,6 +30,13 @@ struct mfa_handle {
   void* ws = nullptr;                       // growable scratch
   size_t ws_size = 0;
   int live_models = 0;
+  // tracing: per-class CUDA-event timing and launch counts
+  bool trace_on = false;
+  double trace_ms[MFA_TRACE_CLASSES] = {};
+  long long trace_n[MFA_TRACE_CLASSES] = {};
+  std::vector<cudaEvent_t> ev;               // event pool, used in pairs
+  std::vector<std::pair<int, int>> pending;  // (class, first event index)
+  int ev_next = 0;
 };
 
 struct mfa_model {
@@ -109,6 +116,73 @@ int ensure_ws(mfa_handle* h, size_t bytes) {
   if (rc == MFA_OK) h->ws_size = bytes;
   return rc;
 }
+
+// ---------------------------------------------------------------------------
+// tracing
+// ---------------------------------------------------------------------------
+
+enum TraceClass {
+  TR_SETUP = 0,        // basis tables, Gram bands, Cholesky factors
+  TR_PROJECT_DATA,     // first projection stage: reads the data
+  TR_PROJECT_REDUCED,  // later projection stages on reduced arrays
+  TR_SOLVE_L,          // iteration-0 banded solves
+  TR_AVERAGE,          // 1/n_s averaging + metrics
+  TR_FRAME_GATHER,     // Schwarz exchange
+  TR_BAND_APPLY,       // coupling product G P_F
+  TR_RHS_FINALIZE,     // B_U - G P_F
+  TR_SOLVE_U,          // owned-box banded solves
+  TR_DECODE_STAGE,     // intermediate decode stages
+  TR_RESIDUAL,         // last decode stage fused with the residual + reduction
+  TR_DECODE_OUT,       // last decode stage writing the output grid
+  TR_DECODE_POINTS,    // scattered decode
+  TR_MISC,             // casts
+  TR_REDUCE,           // final fixed-order reduction of residual partials
+  TR_UNUSED15
+};
+
+const char* kTraceNames[MFA_TRACE_CLASSES] = {
+    "setup_basis_gram_chol", "project_data", "project_reduced", "solve_iter0", "average", "frame_gather",
+    "band_apply", "rhs_finalize", "solve_owned", "decode_stage", "residual", "decode_out", "decode_points",
+    "cast", "reduce", "unused15"};
+
+void trace_flush(mfa_handle* h) {
+  if (h->pending.empty()) {
+    h->ev_next = 0;
+    return;
+  }
+  cudaEventSynchronize(h->ev[h->pending.back().second + 1]);
+  for (auto& pr : h->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[pr.second], h->ev[pr.second + 1]) == cudaSuccess)
+      h->trace_ms[pr.first] += ms;
+  }
+  cudaGetLastError();
+  h->pending.clear();
+  h->ev_next = 0;
+}
+
+int trace_begin(mfa_handle* h) {
+  if (!h->trace_on) return -1;
+  if (h->ev_next + 2 > (int)h->ev.size()) trace_flush(h);
+  const int i = h->ev_next;
+  cudaEventRecord(h->ev[i], h->stream);
+  return i;
+}
+
+void trace_end(mfa_handle* h, int cls, int i) {
+  h->trace_n[cls]++;
+  if (i < 0) return;
+  cudaEventRecord(h->ev[i + 1], h->stream);
+  h->pending.push_back({cls, i});
+  h->ev_next = i + 2;
+}
+
+#define TRACED(h, cls, stmt)        \
+  do {                              \
+    const int _ti = trace_begin(h); \
+    stmt;                           \
+    trace_end(h, cls, _ti);         \
+  } while (0)
 
 // ---------------------------------------------------------------------------
 // layout builder (Sec. 2.2): cores, windows, data ranges, U/L sets, owners
@@ -382,16 +456,19 @@ void run_encode(mfa_model* md, const TQ* q) {
   for (int a = 0; a < md->dim; ++a) {
     T* out = (a == md->dim - 1) ? BL : (a == 0 ? S1 : S2);
     if (a == 0)
-      launch_contract<T, TQ>(L, 0, opsk(OP_PROJ0), ns, md->maxOut[0], q, out, h->d_status, h->stream);
+      TRACED(h, TR_PROJECT_DATA,
+             (launch_contract<T, TQ>(L, 0, opsk(OP_PROJ0), ns, md->maxOut[0], q, out, h->d_status, h->stream)));
     else
-      launch_contract<T, T>(L, a, opsk(OP_PROJ0 + a), ns, md->maxOut[a], a == 1 ? S1 : S2, out, nullptr, h->stream);
+      TRACED(h, TR_PROJECT_REDUCED,
+             (launch_contract<T, T>(L, a, opsk(OP_PROJ0 + a), ns, md->maxOut[a], a == 1 ? S1 : S2, out, nullptr,
+                                    h->stream)));
   }
   // iteration 0: unconstrained local solves on the L boxes
   cudaMemcpyAsync(X, BL, md->sizeL * sizeof(T), cudaMemcpyDeviceToDevice, h->stream);
   for (int a = 0; a < md->dim; ++a)
-    launch_band_solve<T>(L, a, false, opsk(OP_SOLVEL0 + a), ns, md->maxFibL[a], X, h->stream);
+    TRACED(h, TR_SOLVE_L, launch_band_solve<T>(L, a, false, opsk(OP_SOLVEL0 + a), ns, md->maxFibL[a], X, h->stream));
   cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
-  launch_average<T>(L, md->offL, X, (T*)md->P, nullptr, h->d_metrics, h->stream);
+  TRACED(h, TR_AVERAGE, launch_average<T>(L, md->offL, X, (T*)md->P, nullptr, h->d_metrics, h->stream));
 }
 
 // One Schwarz iteration k >= 1 in control-point space.
@@ -404,19 +481,22 @@ void run_step(mfa_model* md) {
   T* S2 = (T*)md->S2;
   auto opsk = [&](int kind) { return md->ops + (size_t)kind * ns; };
   std::swap(md->P, md->Pprev);  // Pprev <- P^{k-1}
-  launch_frame_gather<T>(L, md->offS2, md->maxL, (const T*)md->Pprev, S2, h->stream);
+  TRACED(h, TR_FRAME_GATHER, launch_frame_gather<T>(L, md->offS2, md->maxL, (const T*)md->Pprev, S2, h->stream));
   for (int a = 0; a < md->dim; ++a) {
     const T* in = (a % 2 == 0) ? S2 : S1;
     T* out = (a % 2 == 0) ? S1 : S2;
-    launch_band_apply<T>(L, a, opsk(OP_APPLY0 + a), ns, md->maxApply[a], in, out, h->stream);
+    TRACED(h, TR_BAND_APPLY, launch_band_apply<T>(L, a, opsk(OP_APPLY0 + a), ns, md->maxApply[a], in, out, h->stream));
   }
   const T* Y = (md->dim % 2 == 1) ? S1 : S2;
   const long long* offY = (md->dim % 2 == 1) ? md->offS1 : md->offS2;
-  launch_rhs_finalize<T>(L, md->offL, offY, md->maxU, (const T*)md->BL, Y, (T*)md->X, h->stream);
+  TRACED(h, TR_RHS_FINALIZE,
+         launch_rhs_finalize<T>(L, md->offL, offY, md->maxU, (const T*)md->BL, Y, (T*)md->X, h->stream));
   for (int a = 0; a < md->dim; ++a)
-    launch_band_solve<T>(L, a, true, opsk(OP_SOLVEU0 + a), ns, md->maxFibU[a], (T*)md->X, h->stream);
+    TRACED(h, TR_SOLVE_U,
+           launch_band_solve<T>(L, a, true, opsk(OP_SOLVEU0 + a), ns, md->maxFibU[a], (T*)md->X, h->stream));
   cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
-  launch_average<T>(L, md->offL, (const T*)md->X, (T*)md->P, (const T*)md->Pprev, h->d_metrics, h->stream);
+  TRACED(h, TR_AVERAGE,
+         launch_average<T>(L, md->offL, (const T*)md->X, (T*)md->P, (const T*)md->Pprev, h->d_metrics, h->stream));
 }
 
 // Global grid decode; the last axis either writes `out` (type T) or is fused
@@ -449,14 +529,15 @@ int run_decode_grid(mfa_model* md, T* out, const TQ* q) {
     const bool last = a == d - 1;
     if (last) {
       if (q) {
-        launch_expand_residual<T, TQ>(L, a, op, sz[a], in, q, h->d_partials, kResidualBlocks, h->stream);
-        launch_reduce_partials(h->d_partials, kResidualBlocks, h->d_result, h->stream);
+        TRACED(h, TR_RESIDUAL,
+               (launch_expand_residual<T, TQ>(L, a, op, sz[a], in, q, h->d_partials, kResidualBlocks, h->stream)));
+        TRACED(h, TR_REDUCE, launch_reduce_partials(h->d_partials, kResidualBlocks, h->d_result, h->stream));
       } else {
-        launch_expand<T>(L, a, op, 1, sz[a], in, out, h->stream);
+        TRACED(h, TR_DECODE_OUT, launch_expand<T>(L, a, op, 1, sz[a], in, out, h->stream));
       }
     } else {
       T* o = (a == 0) ? bufA : bufB;
-      launch_expand<T>(L, a, op, 1, sz[a], in, o, h->stream);
+      TRACED(h, TR_DECODE_STAGE, launch_expand<T>(L, a, op, 1, sz[a], in, o, h->stream));
       in = o;
     }
   }
@@ -547,6 +628,7 @@ int mfa_destroy(mfa_handle* h) {
   cudaFree(h->d_partials);
   cudaFree(h->d_result);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
   return MFA_OK;
 }
@@ -691,12 +773,16 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
   // setup kernels: basis tables, Gram bands, Cholesky factors (FP64)
   for (int a = 0; a < 3; ++a) {
     AxisDev& d = L.ax[a];
-    launch_basis(d, const_cast<int*>(d.span), const_cast<double*>(d.vals_d), const_cast<float*>(d.vals_f), h->stream);
+    TRACED(h, TR_SETUP,
+           launch_basis(d, const_cast<int*>(d.span), const_cast<double*>(d.vals_d), const_cast<float*>(d.vals_f),
+                        h->stream));
   }
-  for (int a = 0; a < 3; ++a) launch_gram(L.ax[a], const_cast<double*>(L.ax[a].AL), h->stream);
+  for (int a = 0; a < 3; ++a) TRACED(h, TR_SETUP, launch_gram(L.ax[a], const_cast<double*>(L.ax[a].AL), h->stream));
   for (int a = 0; a < 3; ++a)
-    launch_chol(L.ax[a], L.ax[a].AL, const_cast<double*>(L.ax[a].facL_d), const_cast<float*>(L.ax[a].facL_f),
-                const_cast<double*>(L.ax[a].facU_d), const_cast<float*>(L.ax[a].facU_f), h->d_status, h->stream);
+    TRACED(h, TR_SETUP,
+           launch_chol(L.ax[a], L.ax[a].AL, const_cast<double*>(L.ax[a].facL_d), const_cast<float*>(L.ax[a].facL_f),
+                       const_cast<double*>(L.ax[a].facU_d), const_cast<float*>(L.ax[a].facU_f), h->d_status,
+                       h->stream));
   const void* qd = q;
   if (!q_on_device) {
     // host data: copy and wait, so the caller may reuse its buffer on return
@@ -802,11 +888,13 @@ int mfa_decode(mfa_handle* h, const mfa_model* mdc, const double* pts, int64_t n
     void* dout = out_on_device ? out : (void*)((char*)h->ws + align256(pbytes));
     cudaError_t e = cudaMemcpyAsync(dpts, pts, pbytes, cudaMemcpyDefault, h->stream);
     if (md->prec == MFA_PREC_FP64)
-      launch_decode_points<double>(md->L, md->lo, md->hi, dpts, npts_q, der, (const double*)md->P, dout, out_dtype,
-                                   h->stream);
+      TRACED(h, TR_DECODE_POINTS,
+             launch_decode_points<double>(md->L, md->lo, md->hi, dpts, npts_q, der, (const double*)md->P, dout,
+                                          out_dtype, h->stream));
     else
-      launch_decode_points<float>(md->L, md->lo, md->hi, dpts, npts_q, der, (const float*)md->P, dout, out_dtype,
-                                  h->stream);
+      TRACED(h, TR_DECODE_POINTS,
+             launch_decode_points<float>(md->L, md->lo, md->hi, dpts, npts_q, der, (const float*)md->P, dout,
+                                         out_dtype, h->stream));
     if (e == cudaSuccess && !out_on_device)
       e = cudaMemcpyAsync(out, dout, (size_t)npts_q * osz, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -835,7 +923,7 @@ int mfa_decode(mfa_handle* h, const mfa_model* mdc, const double* pts, int64_t n
   if (rc == MFA_OK && !native) {
     void* conv = (char*)tmp + n * es;
     if (out_dtype == MFA_F64)
-      launch_cast<float>((const float*)tmp, (double*)conv, n, h->stream);
+      TRACED(h, TR_MISC, launch_cast<float>((const float*)tmp, (double*)conv, n, h->stream));
     else
       rc = MFA_ERR_UNSUPPORTED;  // FP64 model decoded to FP32 output: not offered
     src = conv;
@@ -909,9 +997,9 @@ int mfa_get_ctrl(mfa_handle* h, const mfa_model* mdc, double* host_out, int64_t 
   int rc = ensure_ws(h, n * sizeof(double));
   if (rc != MFA_OK) return rc;
   if (md->prec == MFA_PREC_FP64)
-    launch_cast<double>((const double*)md->P, (double*)h->ws, n, h->stream);
+    TRACED(h, TR_MISC, launch_cast<double>((const double*)md->P, (double*)h->ws, n, h->stream));
   else
-    launch_cast<float>((const float*)md->P, (double*)h->ws, n, h->stream);
+    TRACED(h, TR_MISC, launch_cast<float>((const float*)md->P, (double*)h->ws, n, h->stream));
   cudaError_t e = cudaMemcpyAsync(host_out, h->ws, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_status(e);
@@ -928,6 +1016,37 @@ int mfa_free(mfa_model* md) {
   h->live_models--;
   delete md;
   return MFA_OK;
+}
+
+int mfa_trace_enable(mfa_handle* h, int enable) {
+  if (!h) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  trace_flush(h);
+  if (enable && h->ev.empty()) {
+    h->ev.resize(4096);
+    for (auto& e : h->ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return MFA_ERR_CUDA;
+  }
+  h->trace_on = enable != 0;
+  for (int i = 0; i < MFA_TRACE_CLASSES; ++i) {
+    h->trace_ms[i] = 0.0;
+    h->trace_n[i] = 0;
+  }
+  return MFA_OK;
+}
+
+int mfa_trace_read(mfa_handle* h, int32_t cls, double* total_ms, int64_t* launches) {
+  if (!h || cls < 0 || cls >= MFA_TRACE_CLASSES) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  trace_flush(h);
+  if (total_ms) *total_ms = h->trace_ms[cls];
+  if (launches) *launches = h->trace_n[cls];
+  return MFA_OK;
+}
+
+const char* mfa_trace_name(int32_t cls) {
+  if (cls < 0 || cls >= MFA_TRACE_CLASSES) return "invalid";
+  return kTraceNames[cls];
 }
 
 int mfa_sync(mfa_handle* h) {

@@ -30,8 +30,7 @@ MFA_ERR_UNSUPPORTED = -8
 MFA_F32, MFA_F64 = 0, 1
 MFA_PREC_FP64, MFA_PREC_MIXED = 0, 1
 
-EXPORTED = ["mfa_create", "mfa_destroy", "mfa_encode", "mfa_schwarz_iterate", "mfa_decode", "mfa_residual",
-            "mfa_get_ctrl", "mfa_num_ctrl", "mfa_free", "mfa_sync", "mfa_status_string"]
+MFA_TRACE_CLASSES = 16
 
 
 class mfa_layout(ctypes.Structure):
@@ -87,6 +86,12 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_sync.argtypes = [P]
     lib.mfa_status_string.argtypes = [ctypes.c_int]
     lib.mfa_status_string.restype = ctypes.c_char_p
+    lib.mfa_trace_enable.argtypes = [P, ctypes.c_int]
+    lib.mfa_trace_enable.restype = ctypes.c_int
+    lib.mfa_trace_read.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
+    lib.mfa_trace_read.restype = ctypes.c_int
+    lib.mfa_trace_name.argtypes = [ctypes.c_int32]
+    lib.mfa_trace_name.restype = ctypes.c_char_p
     for name in ["mfa_create", "mfa_destroy", "mfa_encode", "mfa_schwarz_iterate", "mfa_decode", "mfa_residual",
                  "mfa_get_ctrl", "mfa_free", "mfa_sync"]:
         getattr(lib, name).restype = ctypes.c_int
@@ -192,6 +197,31 @@ def mfa_free(m: int) -> None:
 
 def mfa_sync(h: int) -> int:
     return load().mfa_sync(ctypes.c_void_p(h))
+
+
+def mfa_trace_enable(h: int, enable: bool) -> None:
+    _check(load().mfa_trace_enable(ctypes.c_void_p(h), int(enable)), "mfa_trace_enable")
+
+
+def mfa_trace_read(h: int, cls: int):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load().mfa_trace_read(ctypes.c_void_p(h), int(cls), ctypes.byref(ms), ctypes.byref(n)), "mfa_trace_read")
+    return ms.value, n.value
+
+
+def mfa_trace_name(cls: int) -> str:
+    return load().mfa_trace_name(int(cls)).decode()
+
+
+def trace_table(h: int) -> dict:
+    """{class name: (total ms, launches)} for every kernel class."""
+    out = {}
+    for c in range(MFA_TRACE_CLASSES):
+        ms, n = mfa_trace_read(h, c)
+        if n:
+            out[mfa_trace_name(c)] = (ms, n)
+    return out
 
 
 # ---------------------------------------------------------------------------
