@@ -177,6 +177,48 @@ int mfa_sync(mfa_handle* h);
 /* Static text for a status code. */
 const char* mfa_status_string(int status);
 
+/* Grid decode that allocates nothing.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory at the point where they decode: for example
+ * an analysis or visualisation plugin running inside a simulation that has
+ * already reserved the whole device through its own memory pool (so a new
+ * allocation would fail or break the host application's budget), or a loop
+ * that must not stall because cudaMalloc / cudaFree may synchronise the
+ * device.  Such a caller passes its own input and output buffers and the
+ * call uses no other memory than one fixed scratch array.
+ *
+ * Decodes the tensor-product B-spline with clamped uniform knots (nspans[a]
+ * spans, degree `degree`) on its full data grid u_k = k/(npts[a]-1), the same
+ * values as mfa_decode with pts == NULL.
+ *   dim, degree, npts[dim], nspans[dim]  as in mfa_layout
+ *   ctrl    device pointer, prod(nspans[a] + degree) FP64 control points,
+ *           grid layout (axis 0 fastest)
+ *   out     device pointer, prod(npts[a]) FP64 values, grid layout
+ *   cuda_stream  stream of the current device on which the work is queued
+ * Runs on the calling thread's current device, which must own ctrl, out and
+ * the stream.  Asynchronous; the caller owns ctrl and out.
+ *
+ * Memory: basis tables and the intermediate arrays between axes live in one
+ * static device array of MFA_NOALLOC_SCRATCH_BYTES (32 MiB) compiled into the
+ * library; every GPU that loads the library holds it until the process
+ * exits.  The call never calls cudaMalloc, cudaFree or any allocating
+ * routine.  A request whose basis tables and intermediates exceed the array
+ * returns MFA_ERR_UNSUPPORTED before any work is queued (roughly: 2-D grids
+ * up to npts[0] * (nspans[1] + degree) of 4M values, 3-D grids whose
+ * npts[0]*npts[1]*(nspans[2]+degree) stays near 3M values).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the array and it
+ * keeps the last call's contents (every element a call reads was written by
+ * that call first, so nothing needs clearing); calls whose GPU work overlaps
+ * in time, on different streams or from different host threads, race on the
+ * array and must be serialised by the caller.
+ * Returns MFA_OK, MFA_ERR_ARG, MFA_ERR_UNSUPPORTED or MFA_ERR_CUDA. */
+#define MFA_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int mfa_decode_grid_noalloc(int32_t dim, int32_t degree, const int64_t* npts, const int32_t* nspans,
+                            const double* ctrl, double* out, void* cuda_stream);
+
 /* Tracing (per-phase timing of Algorithm 1's steps, as in the paper's
  * setup / solve / iterate / decode breakdown, Sec. 3.2.4).  When enabled,
  * every kernel launch of the handle is bracketed by CUDA events on the

@@ -86,6 +86,9 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_sync.argtypes = [P]
     lib.mfa_status_string.argtypes = [ctypes.c_int]
     lib.mfa_status_string.restype = ctypes.c_char_p
+    lib.mfa_decode_grid_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                            ctypes.POINTER(ctypes.c_int32), P, P, P]
+    lib.mfa_decode_grid_noalloc.restype = ctypes.c_int
     lib.mfa_trace_enable.argtypes = [P, ctypes.c_int]
     lib.mfa_trace_enable.restype = ctypes.c_int
     lib.mfa_trace_read.argtypes = [P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)]
@@ -197,6 +200,16 @@ def mfa_free(m: int) -> None:
 
 def mfa_sync(h: int) -> int:
     return load().mfa_sync(ctypes.c_void_p(h))
+
+
+def mfa_decode_grid_noalloc(dim: int, degree: int, npts, nspans, ctrl_ptr: int, out_ptr: int, stream: int = 0) -> None:
+    """Grid decode into caller-owned device buffers using only the library's
+    fixed static scratch (no allocation); see include/mfa.h."""
+    n = (ctypes.c_int64 * 3)(*[int(x) for x in npts] + [1] * (3 - len(npts)))
+    s = (ctypes.c_int32 * 3)(*[int(x) for x in nspans] + [1] * (3 - len(nspans)))
+    _check(load().mfa_decode_grid_noalloc(int(dim), int(degree), n, s, ctypes.c_void_p(ctrl_ptr),
+                                          ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream)),
+           "mfa_decode_grid_noalloc")
 
 
 def mfa_trace_enable(h: int, enable: bool) -> None:
