@@ -39,7 +39,7 @@ WORKLOADS = {
     # BASELINE 3-D workload: 512^3 FP32 grid of 16 seeded Gaussians + sin(6 pi x) cos(4 pi y) z,
     # p = 3, 8x8x8 subdomains of 24 core spans (192 spans, 195 control points per axis), overlap 2.
     "3d": dict(name="3d_512^3_gauss16_p3_8x8x8sub_24spans_overlap2_mixed", npts=(512, 512, 512), p=3,
-               nspans=(192, 192, 192), nsub=(8, 8, 8), delta=2, precision="mixed", tol=1e-6, max_iters=50,
+               nspans=(192, 192, 192), nsub=(8, 8, 8), delta=2, precision="mixed", tol=1e-7, max_iters=50,
                sample=dict(npts=(128, 128, 128), nspans=(48, 48, 48), nsub=(2, 2, 2))),
     # BASELINE 2-D workload: 1024^2 sinc(x) sinc(y) + N(0, 1e-3), p = 3, 4x4 subdomains of 64 core spans.
     "2d": dict(name="2d_1024^2_sinc_noise1e-3_p3_4x4sub_64spans_overlap2_mixed", npts=(1024, 1024), p=3,

@@ -151,7 +151,7 @@ extern "C" int mfa_decode_grid_noalloc(int32_t dim, int32_t degree, const int64_
     int* sp = reinterpret_cast<int*>(base + off_span[a]);
     double* vd = reinterpret_cast<double*>(base + off_vd[a]);
     float* vf = reinterpret_cast<float*>(base + off_vf[a]);
-    mfa::launch_basis(ax, sp, vd, vf, st);
+    mfa::launch_basis(ax, sp, vd, vf, nullptr, st);
     span[a] = sp;
     vals[a] = vd;
   }

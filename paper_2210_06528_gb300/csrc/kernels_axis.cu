@@ -12,6 +12,8 @@ template <>
 __device__ __forceinline__ const double* basis_vals<double>(const AxisDev& ax) { return ax.vals_d; }
 template <>
 __device__ __forceinline__ const float* basis_vals<float>(const AxisDev& ax) { return ax.vals_f; }
+template <>
+__device__ __forceinline__ const ff* basis_vals<ff>(const AxisDev& ax) { return ax.vals_ff; }
 
 template <typename T>
 __device__ __forceinline__ const T* fac_L(const AxisDev& ax);
@@ -19,12 +21,16 @@ template <>
 __device__ __forceinline__ const double* fac_L<double>(const AxisDev& ax) { return ax.facL_d; }
 template <>
 __device__ __forceinline__ const float* fac_L<float>(const AxisDev& ax) { return ax.facL_f; }
+template <>
+__device__ __forceinline__ const ff* fac_L<ff>(const AxisDev& ax) { return ax.facL_ff; }
 template <typename T>
 __device__ __forceinline__ const T* fac_U(const AxisDev& ax);
 template <>
 __device__ __forceinline__ const double* fac_U<double>(const AxisDev& ax) { return ax.facU_d; }
 template <>
 __device__ __forceinline__ const float* fac_U<float>(const AxisDev& ax) { return ax.facU_f; }
+template <>
+__device__ __forceinline__ const ff* fac_U<ff>(const AxisDev& ax) { return ax.facU_ff; }
 
 __device__ __forceinline__ void unflatten(long long idx, const int* n, int* o) {
   o[0] = (int)(idx % n[0]);
@@ -35,6 +41,7 @@ __device__ __forceinline__ void unflatten(long long idx, const int* n, int* o) {
 
 __device__ __forceinline__ bool finite_val(float x) { return isfinite(x); }
 __device__ __forceinline__ bool finite_val(double x) { return isfinite(x); }
+__device__ __forceinline__ bool finite_val(ff x) { return isfinite(x.hi); }
 
 // Projection along one axis: out[l] = sum_k N_{c0+l}(u_{k}) in[k - k0] over
 // the points k of the window that lie in the support of control point c0+l,
@@ -98,8 +105,8 @@ __device__ __forceinline__ T expand_one(const AxisDev& ax, const AxisOp& op, int
   return acc;
 }
 
-template <typename T>
-__global__ void k_expand(LayoutDev L, int axis, const AxisOp* ops, const T* __restrict__ in, T* __restrict__ out) {
+template <typename T, typename TOut>
+__global__ void k_expand(LayoutDev L, int axis, const AxisOp* ops, const T* __restrict__ in, TOut* __restrict__ out) {
   const AxisOp op = ops[blockIdx.y];
   const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -108,7 +115,7 @@ __global__ void k_expand(LayoutDev L, int axis, const AxisOp* ops, const T* __re
     unflatten(idx, op.out.n, o);
     const T val = expand_one<T>(L.ax[axis], op, axis, o, in);
     const View& ov = op.out;
-    out[ov.off + o[0] * ov.st[0] + o[1] * ov.st[1] + o[2] * ov.st[2]] = val;
+    out[ov.off + o[0] * ov.st[0] + o[1] * ov.st[1] + o[2] * ov.st[2]] = (TOut)val;
   }
 }
 
@@ -260,13 +267,13 @@ void launch_contract(const LayoutDev& L, int axis, const AxisOp* ops, int nops, 
   k_contract<T, TIn><<<grid, 128, 0, st>>>(L, axis, ops, in, out, status);
 }
 
-template <typename T>
-void launch_expand(const LayoutDev& L, int axis, const AxisOp* ops, int nops, long long max_out, const T* in, T* out,
-                   cudaStream_t st) {
+template <typename T, typename TOut>
+void launch_expand(const LayoutDev& L, int axis, const AxisOp* ops, int nops, long long max_out, const T* in,
+                   TOut* out, cudaStream_t st) {
   long long blocks = (max_out + 255) / 256;
   if (blocks > 65535) blocks = 65535;
   dim3 grid((unsigned)blocks, nops);
-  k_expand<T><<<grid, 256, 0, st>>>(L, axis, ops, in, out);
+  k_expand<T, TOut><<<grid, 256, 0, st>>>(L, axis, ops, in, out);
 }
 
 template <typename T, typename TQ>
@@ -293,31 +300,28 @@ void launch_band_solve(const LayoutDev& L, int axis, bool useU, const AxisOp* op
   k_band_solve<T><<<grid, 64, 0, st>>>(L, axis, useU, ops, x);
 }
 
-template void launch_contract<double, double>(const LayoutDev&, int, const AxisOp*, int, int, const double*, double*,
-                                              int*, cudaStream_t);
-template void launch_contract<double, float>(const LayoutDev&, int, const AxisOp*, int, int, const float*, double*,
-                                             int*, cudaStream_t);
-template void launch_contract<float, float>(const LayoutDev&, int, const AxisOp*, int, int, const float*, float*, int*,
-                                            cudaStream_t);
-template void launch_contract<float, double>(const LayoutDev&, int, const AxisOp*, int, int, const double*, float*,
-                                             int*, cudaStream_t);
-template void launch_expand<double>(const LayoutDev&, int, const AxisOp*, int, long long, const double*, double*,
+#define MFA_INST_T(T)                                                                                        \
+  template void launch_band_apply<T>(const LayoutDev&, int, const AxisOp*, int, int, const T*, T*, cudaStream_t);   \
+  template void launch_band_solve<T>(const LayoutDev&, int, bool, const AxisOp*, int, int, T*, cudaStream_t);      \
+  template void launch_contract<T, float>(const LayoutDev&, int, const AxisOp*, int, int, const float*, T*, int*,  \
+                                          cudaStream_t);                                                           \
+  template void launch_contract<T, double>(const LayoutDev&, int, const AxisOp*, int, int, const double*, T*, int*, \
+                                           cudaStream_t);                                                          \
+  template void launch_expand_residual<T, float>(const LayoutDev&, int, const AxisOp*, long long, const T*,        \
+                                                 const float*, double*, int, cudaStream_t);                        \
+  template void launch_expand_residual<T, double>(const LayoutDev&, int, const AxisOp*, long long, const T*,       \
+                                                  const double*, double*, int, cudaStream_t);                      \
+  template void launch_expand<T, float>(const LayoutDev&, int, const AxisOp*, int, long long, const T*, float*,    \
+                                        cudaStream_t);                                                             \
+  template void launch_expand<T, double>(const LayoutDev&, int, const AxisOp*, int, long long, const T*, double*,  \
+                                         cudaStream_t);
+
+MFA_INST_T(double)
+MFA_INST_T(float)
+MFA_INST_T(ff)
+template void launch_expand<ff, ff>(const LayoutDev&, int, const AxisOp*, int, long long, const ff*, ff*,
                                     cudaStream_t);
-template void launch_expand<float>(const LayoutDev&, int, const AxisOp*, int, long long, const float*, float*,
-                                   cudaStream_t);
-template void launch_expand_residual<double, double>(const LayoutDev&, int, const AxisOp*, long long, const double*,
-                                                     const double*, double*, int, cudaStream_t);
-template void launch_expand_residual<double, float>(const LayoutDev&, int, const AxisOp*, long long, const double*,
-                                                    const float*, double*, int, cudaStream_t);
-template void launch_expand_residual<float, float>(const LayoutDev&, int, const AxisOp*, long long, const float*,
-                                                   const float*, double*, int, cudaStream_t);
-template void launch_expand_residual<float, double>(const LayoutDev&, int, const AxisOp*, long long, const float*,
-                                                    const double*, double*, int, cudaStream_t);
-template void launch_band_apply<double>(const LayoutDev&, int, const AxisOp*, int, int, const double*, double*,
-                                        cudaStream_t);
-template void launch_band_apply<float>(const LayoutDev&, int, const AxisOp*, int, int, const float*, float*,
-                                       cudaStream_t);
-template void launch_band_solve<double>(const LayoutDev&, int, bool, const AxisOp*, int, int, double*, cudaStream_t);
-template void launch_band_solve<float>(const LayoutDev&, int, bool, const AxisOp*, int, int, float*, cudaStream_t);
+template void launch_contract<ff, ff>(const LayoutDev&, int, const AxisOp*, int, int, const ff*, ff*, int*,
+                                      cudaStream_t);
 
 }  // namespace mfa

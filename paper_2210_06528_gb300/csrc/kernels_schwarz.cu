@@ -245,36 +245,33 @@ void launch_decode_points(const LayoutDev& L, const double* lo, const double* hi
                                                        deriv[0], deriv[1], deriv[2], P, out, out_dtype);
 }
 
-template <typename T>
-__global__ void k_cast(const T* in, double* out, long long n) {
+template <typename TIn, typename TOut>
+__global__ void k_cast(const TIn* in, TOut* out, long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (double)in[i];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (TOut)in[i];
 }
 
-template <typename T>
-void launch_cast(const T* in, double* out, long long n, cudaStream_t st) {
+template <typename TIn, typename TOut>
+void launch_cast(const TIn* in, TOut* out, long long n, cudaStream_t st) {
   long long blocks = (n + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   if (blocks < 1) blocks = 1;
-  k_cast<T><<<(unsigned)blocks, 256, 0, st>>>(in, out, n);
+  k_cast<TIn, TOut><<<(unsigned)blocks, 256, 0, st>>>(in, out, n);
 }
 
-template void launch_frame_gather<double>(const LayoutDev&, const long long*, int, const double*, double*,
-                                          cudaStream_t);
-template void launch_frame_gather<float>(const LayoutDev&, const long long*, int, const float*, float*, cudaStream_t);
-template void launch_rhs_finalize<double>(const LayoutDev&, const long long*, const long long*, int, const double*,
-                                          const double*, double*, cudaStream_t);
-template void launch_rhs_finalize<float>(const LayoutDev&, const long long*, const long long*, int, const float*,
-                                         const float*, float*, cudaStream_t);
-template void launch_average<double>(const LayoutDev&, const long long*, const double*, double*, const double*,
-                                     unsigned long long*, cudaStream_t);
-template void launch_average<float>(const LayoutDev&, const long long*, const float*, float*, const float*,
-                                    unsigned long long*, cudaStream_t);
-template void launch_decode_points<double>(const LayoutDev&, const double*, const double*, const double*, long long,
-                                           const int*, const double*, void*, int, cudaStream_t);
-template void launch_decode_points<float>(const LayoutDev&, const double*, const double*, const double*, long long,
-                                          const int*, const float*, void*, int, cudaStream_t);
-template void launch_cast<double>(const double*, double*, long long, cudaStream_t);
-template void launch_cast<float>(const float*, double*, long long, cudaStream_t);
+#define MFA_INST_S(T)                                                                                       \
+  template void launch_frame_gather<T>(const LayoutDev&, const long long*, int, const T*, T*, cudaStream_t);     \
+  template void launch_rhs_finalize<T>(const LayoutDev&, const long long*, const long long*, int, const T*,      \
+                                       const T*, T*, cudaStream_t);                                              \
+  template void launch_average<T>(const LayoutDev&, const long long*, const T*, T*, const T*, unsigned long long*, \
+                                  cudaStream_t);                                                                  \
+  template void launch_decode_points<T>(const LayoutDev&, const double*, const double*, const double*, long long, \
+                                        const int*, const T*, void*, int, cudaStream_t);                          \
+  template void launch_cast<T, double>(const T*, double*, long long, cudaStream_t);                              \
+  template void launch_cast<T, float>(const T*, float*, long long, cudaStream_t);
+
+MFA_INST_S(double)
+MFA_INST_S(float)
+MFA_INST_S(ff)
 
 }  // namespace mfa

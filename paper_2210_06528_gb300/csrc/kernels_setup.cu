@@ -38,7 +38,7 @@ __device__ void cox_de_boor(int j, double u, int p, int nspans, double* N) {
   }
 }
 
-__global__ void k_basis(int M, int nspans, int p, int* span, double* vd, float* vf) {
+__global__ void k_basis(int M, int nspans, int p, int* span, double* vd, float* vf, ff* vff) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= M) return;
   // span index: largest j with j/nspans <= k/(M-1), exact in integers
@@ -56,13 +56,14 @@ __global__ void k_basis(int M, int nspans, int p, int* span, double* vd, float* 
   for (int r = 0; r <= p; ++r) {
     vd[(long long)k * (p + 1) + r] = N[r];
     vf[(long long)k * (p + 1) + r] = (float)N[r];
+    if (vff) vff[(long long)k * (p + 1) + r] = ff(N[r]);
   }
 }
 
-void launch_basis(const AxisDev& ax, int* span, double* vd, float* vf, cudaStream_t st) {
+void launch_basis(const AxisDev& ax, int* span, double* vd, float* vf, ff* vff, cudaStream_t st) {
   int threads = 128;
   int blocks = (ax.M + threads - 1) / threads;
-  k_basis<<<blocks, threads, 0, st>>>(ax.M, ax.nspans, ax.p, span, vd, vf);
+  k_basis<<<blocks, threads, 0, st>>>(ax.M, ax.nspans, ax.p, span, vd, vf, vff);
 }
 
 // Gram band of one window: A_L = N_L^T N_L summed over the window's points
@@ -102,7 +103,7 @@ void launch_gram(const AxisDev& ax, double* AL, cudaStream_t st) {
 //   L(i,i) = sqrt(A(i,i) - sum_{k<i} L(i,k)^2).
 // A pivot that is not positive, or falls below 1e-13 of its diagonal entry,
 // marks the status word MFA_ERR_NOT_SPD and the factor is left unusable.
-__device__ void band_cholesky(const double* A, int o, int n, int p, double* F, float* Ff, int* status) {
+__device__ void band_cholesky(const double* A, int o, int n, int p, double* F, float* Ff, ff* Fff, int* status) {
   const int w = p + 1;
   for (int i = 0; i < n; ++i) {
     for (int e = p; e >= 1; --e) {
@@ -125,11 +126,14 @@ __device__ void band_cholesky(const double* A, int o, int n, int p, double* F, f
     }
     F[i * w] = 1.0 / sqrt(dsum);
   }
-  for (int i = 0; i < n * w; ++i) Ff[i] = (float)F[i];
+  for (int i = 0; i < n * w; ++i) {
+    Ff[i] = (float)F[i];
+    Fff[i] = ff(F[i]);
+  }
 }
 
-__global__ void k_chol(AxisDev ax, const double* AL, double* fLd, float* fLf, double* fUd, float* fUf,
-                       int* status) {
+__global__ void k_chol(AxisDev ax, const double* AL, double* fLd, float* fLf, ff* fLff, double* fUd, float* fUf,
+                       ff* fUff, int* status) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 2 * ax.S) return;
   const int s = t >> 1;
@@ -137,15 +141,17 @@ __global__ void k_chol(AxisDev ax, const double* AL, double* fLd, float* fLf, do
   const int w = ax.p + 1;
   const double* A = AL + (long long)sb.bandL * w;
   if ((t & 1) == 0)
-    band_cholesky(A, 0, sb.nL, ax.p, fLd + (long long)sb.bandL * w, fLf + (long long)sb.bandL * w, status);
+    band_cholesky(A, 0, sb.nL, ax.p, fLd + (long long)sb.bandL * w, fLf + (long long)sb.bandL * w,
+                  fLff + (long long)sb.bandL * w, status);
   else
-    band_cholesky(A, sb.oU, sb.nU, ax.p, fUd + (long long)sb.bandU * w, fUf + (long long)sb.bandU * w, status);
+    band_cholesky(A, sb.oU, sb.nU, ax.p, fUd + (long long)sb.bandU * w, fUf + (long long)sb.bandU * w,
+                  fUff + (long long)sb.bandU * w, status);
 }
 
-void launch_chol(const AxisDev& ax, const double* AL, double* fLd, float* fLf, double* fUd, float* fUf,
-                 int* status, cudaStream_t st) {
+void launch_chol(const AxisDev& ax, const double* AL, double* fLd, float* fLf, ff* fLff, double* fUd, float* fUf,
+                 ff* fUff, int* status, cudaStream_t st) {
   int n = 2 * ax.S;
-  k_chol<<<(n + 63) / 64, 64, 0, st>>>(ax, AL, fLd, fLf, fUd, fUf, status);
+  k_chol<<<(n + 63) / 64, 64, 0, st>>>(ax, AL, fLd, fLf, fLff, fUd, fUf, fUff, status);
 }
 
 }  // namespace mfa

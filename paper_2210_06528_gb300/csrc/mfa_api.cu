@@ -302,7 +302,7 @@ int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int
 namespace {
 
 // Byte sizes of the element type the model computes in.
-inline size_t elem_size(int prec) { return prec == MFA_PREC_FP64 ? sizeof(double) : sizeof(float); }
+inline size_t elem_size(int prec) { return prec == MFA_PREC_FP64 ? sizeof(double) : sizeof(ff); }
 
 View make_view(long long off, int n0, int n1, int n2, long long s0, long long s1, long long s2) {
   View v;
@@ -501,8 +501,8 @@ void run_step(mfa_model* md) {
 
 // Global grid decode; the last axis either writes `out` (type T) or is fused
 // with the residual against q.
-template <typename T, typename TQ>
-int run_decode_grid(mfa_model* md, T* out, const TQ* q) {
+template <typename T, typename TQ, typename TOut>
+int run_decode_grid(mfa_model* md, TOut* out, const TQ* q) {
   mfa_handle* h = md->h;
   const LayoutDev& L = md->L;
   const int ns = md->nsub;
@@ -533,11 +533,11 @@ int run_decode_grid(mfa_model* md, T* out, const TQ* q) {
                (launch_expand_residual<T, TQ>(L, a, op, sz[a], in, q, h->d_partials, kResidualBlocks, h->stream)));
         TRACED(h, TR_REDUCE, launch_reduce_partials(h->d_partials, kResidualBlocks, h->d_result, h->stream));
       } else {
-        TRACED(h, TR_DECODE_OUT, launch_expand<T>(L, a, op, 1, sz[a], in, out, h->stream));
+        TRACED(h, TR_DECODE_OUT, (launch_expand<T, TOut>(L, a, op, 1, sz[a], in, out, h->stream)));
       }
     } else {
       T* o = (a == 0) ? bufA : bufB;
-      TRACED(h, TR_DECODE_STAGE, launch_expand<T>(L, a, op, 1, sz[a], in, o, h->stream));
+      TRACED(h, TR_DECODE_STAGE, (launch_expand<T, T>(L, a, op, 1, sz[a], in, o, h->stream)));
       in = o;
     }
   }
@@ -679,14 +679,15 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
   const int ns = md->nsub;
   // ---- device tables in one arena
   Arena ar;
-  size_t o_span[3], o_vd[3], o_vf[3], o_ss[3], o_subs[3], o_of[3], o_oc[3], o_AL[3], o_fLd[3], o_fLf[3], o_fUd[3],
-      o_fUf[3];
+  size_t o_span[3], o_vd[3], o_vf[3], o_vff[3], o_ss[3], o_subs[3], o_of[3], o_oc[3], o_AL[3], o_fLd[3], o_fLf[3],
+      o_fLff[3], o_fUd[3], o_fUf[3], o_fUff[3];
   for (int a = 0; a < 3; ++a) {
     const AxisHost& ax = md->axh[a];
     const int w = ax.p + 1;
     o_span[a] = ar.take<int>(ax.M);
     o_vd[a] = ar.take<double>((size_t)ax.M * w);
     o_vf[a] = ar.take<float>((size_t)ax.M * w);
+    o_vff[a] = ar.take<ff>((size_t)ax.M * w);
     o_ss[a] = ar.take<int>(ax.nspans + 1);
     o_subs[a] = ar.take<AxisSub>(ax.S);
     o_of[a] = ar.take<int>(ax.n);
@@ -694,8 +695,10 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
     o_AL[a] = ar.take<double>((size_t)ax.bandL_rows * w);
     o_fLd[a] = ar.take<double>((size_t)ax.bandL_rows * w);
     o_fLf[a] = ar.take<float>((size_t)ax.bandL_rows * w);
+    o_fLff[a] = ar.take<ff>((size_t)ax.bandL_rows * w);
     o_fUd[a] = ar.take<double>((size_t)ax.bandU_rows * w);
     o_fUf[a] = ar.take<float>((size_t)ax.bandU_rows * w);
+    o_fUff[a] = ar.take<ff>((size_t)ax.bandU_rows * w);
   }
   const size_t o_offL = ar.take<long long>(ns), o_offS1 = ar.take<long long>(ns), o_offS2 = ar.take<long long>(ns);
   const size_t o_ops = ar.take<AxisOp>(ops.size());
@@ -750,6 +753,7 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
     d.span = at_off<int>(md->arena, o_span[a]);
     d.vals_d = at_off<double>(md->arena, o_vd[a]);
     d.vals_f = at_off<float>(md->arena, o_vf[a]);
+    d.vals_ff = at_off<ff>(md->arena, o_vff[a]);
     d.span_start = at_off<int>(md->arena, o_ss[a]);
     d.subs = at_off<AxisSub>(md->arena, o_subs[a]);
     d.own_first = at_off<int>(md->arena, o_of[a]);
@@ -757,8 +761,10 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
     d.AL = at_off<double>(md->arena, o_AL[a]);
     d.facL_d = at_off<double>(md->arena, o_fLd[a]);
     d.facL_f = at_off<float>(md->arena, o_fLf[a]);
+    d.facL_ff = at_off<ff>(md->arena, o_fLff[a]);
     d.facU_d = at_off<double>(md->arena, o_fUd[a]);
     d.facU_f = at_off<float>(md->arena, o_fUf[a]);
+    d.facU_ff = at_off<ff>(md->arena, o_fUff[a]);
   }
   md->offL = at_off<long long>(md->arena, o_offL);
   md->offS1 = at_off<long long>(md->arena, o_offS1);
@@ -775,13 +781,14 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
     AxisDev& d = L.ax[a];
     TRACED(h, TR_SETUP,
            launch_basis(d, const_cast<int*>(d.span), const_cast<double*>(d.vals_d), const_cast<float*>(d.vals_f),
-                        h->stream));
+                        const_cast<ff*>(d.vals_ff), h->stream));
   }
   for (int a = 0; a < 3; ++a) TRACED(h, TR_SETUP, launch_gram(L.ax[a], const_cast<double*>(L.ax[a].AL), h->stream));
   for (int a = 0; a < 3; ++a)
     TRACED(h, TR_SETUP,
            launch_chol(L.ax[a], L.ax[a].AL, const_cast<double*>(L.ax[a].facL_d), const_cast<float*>(L.ax[a].facL_f),
-                       const_cast<double*>(L.ax[a].facU_d), const_cast<float*>(L.ax[a].facU_f), h->d_status,
+                       const_cast<ff*>(L.ax[a].facL_ff), const_cast<double*>(L.ax[a].facU_d),
+                       const_cast<float*>(L.ax[a].facU_f), const_cast<ff*>(L.ax[a].facU_ff), h->d_status,
                        h->stream));
   const void* qd = q;
   if (!q_on_device) {
@@ -798,9 +805,9 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
       run_encode<double, float>(md, (const float*)qd);
   } else {
     if (q_dtype == MFA_F64)
-      run_encode<float, double>(md, (const double*)qd);
+      run_encode<ff, double>(md, (const double*)qd);
     else
-      run_encode<float, float>(md, (const float*)qd);
+      run_encode<ff, float>(md, (const float*)qd);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -825,7 +832,7 @@ int mfa_schwarz_iterate(mfa_handle* h, mfa_model* md, int32_t max_iters, double 
     if (md->prec == MFA_PREC_FP64)
       run_step<double>(md);
     else
-      run_step<float>(md);
+      run_step<ff>(md);
     cudaError_t e = cudaMemcpyAsync(h->h_pinned, h->d_metrics, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                     h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -893,8 +900,8 @@ int mfa_decode(mfa_handle* h, const mfa_model* mdc, const double* pts, int64_t n
                                           out_dtype, h->stream));
     else
       TRACED(h, TR_DECODE_POINTS,
-             launch_decode_points<float>(md->L, md->lo, md->hi, dpts, npts_q, der, (const float*)md->P, dout,
-                                         out_dtype, h->stream));
+             launch_decode_points<ff>(md->L, md->lo, md->hi, dpts, npts_q, der, (const ff*)md->P, dout, out_dtype,
+                                      h->stream));
     if (e == cudaSuccess && !out_on_device)
       e = cudaMemcpyAsync(out, dout, (size_t)npts_q * osz, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -904,38 +911,26 @@ int mfa_decode(mfa_handle* h, const mfa_model* mdc, const double* pts, int64_t n
   // full grid
   if (der[0] || der[1] || der[2]) return MFA_ERR_UNSUPPORTED;
   const long long n = (long long)md->axh[0].M * md->axh[1].M * md->axh[2].M;
-  const bool native = (md->prec == MFA_PREC_FP64) == (out_dtype == MFA_F64);
-  if (native && out_on_device) {
-    int rc = md->prec == MFA_PREC_FP64 ? run_decode_grid<double, double>(md, (double*)out, nullptr)
-                                       : run_decode_grid<float, float>(md, (float*)out, nullptr);
-    if (rc != MFA_OK) return rc;
-    return cuda_status(cudaGetLastError());
-  }
-  // decode into a pool buffer of the model's type, then convert / copy out
-  const size_t es = elem_size(md->prec);
+  void* dst = out;
   void* tmp = nullptr;
-  int rc = pool_alloc(h, &tmp, n * es + (native ? 0 : n * osz));
-  if (rc != MFA_OK) return rc;
-  rc = md->prec == MFA_PREC_FP64 ? run_decode_grid<double, double>(md, (double*)tmp, nullptr)
-                                 : run_decode_grid<float, float>(md, (float*)tmp, nullptr);
+  if (!out_on_device) {
+    int rc = pool_alloc(h, &tmp, n * osz);
+    if (rc != MFA_OK) return rc;
+    dst = tmp;
+  }
+  int rc;
+  if (md->prec == MFA_PREC_FP64)
+    rc = out_dtype == MFA_F64 ? run_decode_grid<double, double, double>(md, (double*)dst, (const double*)nullptr)
+                              : run_decode_grid<double, double, float>(md, (float*)dst, (const double*)nullptr);
+  else
+    rc = out_dtype == MFA_F64 ? run_decode_grid<ff, double, double>(md, (double*)dst, (const double*)nullptr)
+                              : run_decode_grid<ff, double, float>(md, (float*)dst, (const double*)nullptr);
   cudaError_t e = cudaSuccess;
-  void* src = tmp;
-  if (rc == MFA_OK && !native) {
-    void* conv = (char*)tmp + n * es;
-    if (out_dtype == MFA_F64)
-      TRACED(h, TR_MISC, launch_cast<float>((const float*)tmp, (double*)conv, n, h->stream));
-    else
-      rc = MFA_ERR_UNSUPPORTED;  // FP64 model decoded to FP32 output: not offered
-    src = conv;
+  if (rc == MFA_OK && !out_on_device) {
+    e = cudaMemcpyAsync(out, dst, n * osz, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   }
-  if (rc == MFA_OK) {
-    if (out_on_device)
-      e = cudaMemcpyAsync(out, src, n * osz, cudaMemcpyDeviceToDevice, h->stream);
-    else
-      e = cudaMemcpyAsync(out, src, n * osz, cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess && !out_on_device) e = cudaStreamSynchronize(h->stream);
-  }
-  pool_free(h, tmp);
+  if (tmp) pool_free(h, tmp);
   if (rc != MFA_OK) return rc;
   if (e == cudaSuccess) e = cudaGetLastError();
   return cuda_status(e);
@@ -959,11 +954,11 @@ int mfa_residual(mfa_handle* h, const mfa_model* mdc, const void* q, int q_dtype
   }
   int rc;
   if (md->prec == MFA_PREC_FP64)
-    rc = q_dtype == MFA_F64 ? run_decode_grid<double, double>(md, nullptr, (const double*)qd)
-                            : run_decode_grid<double, float>(md, nullptr, (const float*)qd);
+    rc = q_dtype == MFA_F64 ? run_decode_grid<double, double, double>(md, nullptr, (const double*)qd)
+                            : run_decode_grid<double, float, double>(md, nullptr, (const float*)qd);
   else
-    rc = q_dtype == MFA_F64 ? run_decode_grid<float, double>(md, nullptr, (const double*)qd)
-                            : run_decode_grid<float, float>(md, nullptr, (const float*)qd);
+    rc = q_dtype == MFA_F64 ? run_decode_grid<ff, double, ff>(md, nullptr, (const double*)qd)
+                            : run_decode_grid<ff, float, ff>(md, nullptr, (const float*)qd);
   if (rc == MFA_OK && e == cudaSuccess)
     e = cudaMemcpyAsync(h->h_pinned, h->d_result, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -997,9 +992,9 @@ int mfa_get_ctrl(mfa_handle* h, const mfa_model* mdc, double* host_out, int64_t 
   int rc = ensure_ws(h, n * sizeof(double));
   if (rc != MFA_OK) return rc;
   if (md->prec == MFA_PREC_FP64)
-    TRACED(h, TR_MISC, launch_cast<double>((const double*)md->P, (double*)h->ws, n, h->stream));
+    TRACED(h, TR_MISC, (launch_cast<double, double>((const double*)md->P, (double*)h->ws, n, h->stream)));
   else
-    TRACED(h, TR_MISC, launch_cast<float>((const float*)md->P, (double*)h->ws, n, h->stream));
+    TRACED(h, TR_MISC, (launch_cast<ff, double>((const ff*)md->P, (double*)h->ws, n, h->stream)));
   cudaError_t e = cudaMemcpyAsync(host_out, h->ws, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) return cuda_status(e);

@@ -7,6 +7,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "ff.cuh"
 #include "mfa.h"
 
 namespace mfa {
@@ -31,6 +32,7 @@ struct AxisDev {
   const int* span;          // [M] knot span of every data point
   const double* vals_d;     // [M * (p+1)] N_{span+r,p}(u_k), r = 0..p
   const float* vals_f;      // same, rounded to FP32
+  const ff* vals_ff;        // same, as float-float pairs
   const int* span_start;    // [nspans + 1] first point whose span is >= j
   const AxisSub* subs;      // [S]
   const int* own_first;     // [n] first subdomain-axis index owning CP g
@@ -38,8 +40,10 @@ struct AxisDev {
   const double* AL;         // Gram band rows of every piece, upper storage: A(i, i+e) at [i*(p+1)+e]
   const double* facL_d;     // Cholesky band of A_L: [i*(p+1)] = 1/L(i,i), [i*(p+1)+e] = L(i,i-e)
   const float* facL_f;
+  const ff* facL_ff;
   const double* facU_d;     // Cholesky band of A_U (owned rows only)
   const float* facU_f;
+  const ff* facU_ff;
 };
 
 struct LayoutDev {
@@ -79,17 +83,17 @@ struct AxisHost {
 // ---------------------------------------------------------------------------
 // kernel launchers (kernels_*.cu)
 // ---------------------------------------------------------------------------
-void launch_basis(const AxisDev& ax, int* span, double* vd, float* vf, cudaStream_t st);
+void launch_basis(const AxisDev& ax, int* span, double* vd, float* vf, ff* vff, cudaStream_t st);
 void launch_gram(const AxisDev& ax, double* AL, cudaStream_t st);
-void launch_chol(const AxisDev& ax, const double* AL, double* fLd, float* fLf, double* fUd, float* fUf,
-                 int* status, cudaStream_t st);
+void launch_chol(const AxisDev& ax, const double* AL, double* fLd, float* fLf, ff* fLff, double* fUd, float* fUf,
+                 ff* fUff, int* status, cudaStream_t st);
 
 template <typename T, typename TIn>
 void launch_contract(const LayoutDev& L, int axis, const AxisOp* ops, int nops, int max_out,
                      const TIn* in, T* out, int* status, cudaStream_t st);
-template <typename T>
+template <typename T, typename TOut = T>
 void launch_expand(const LayoutDev& L, int axis, const AxisOp* ops, int nops, long long max_out,
-                   const T* in, T* out, cudaStream_t st);
+                   const T* in, TOut* out, cudaStream_t st);
 template <typename T, typename TQ>
 void launch_expand_residual(const LayoutDev& L, int axis, const AxisOp* op, long long nout, const T* in,
                             const TQ* q, double* partials, int nblocks, cudaStream_t st);
@@ -111,8 +115,8 @@ template <typename T>
 void launch_decode_points(const LayoutDev& L, const double* lo, const double* hi, const double* pts, long long npts,
                           const int* deriv, const T* P, void* out, int out_dtype, cudaStream_t st);
 void launch_reduce_partials(const double* partials, int nblocks, double* result, cudaStream_t st);
-template <typename T>
-void launch_cast(const T* in, double* out, long long n, cudaStream_t st);
+template <typename TIn, typename TOut>
+void launch_cast(const TIn* in, TOut* out, long long n, cudaStream_t st);
 
 constexpr int kResidualBlocks = 1216;  // 8 x 152 SMs
 
