@@ -41,6 +41,11 @@ WORKLOADS = {
     "3d": dict(name="3d_512^3_gauss16_p3_8x8x8sub_24spans_overlap2_mixed", npts=(512, 512, 512), p=3,
                nspans=(192, 192, 192), nsub=(8, 8, 8), delta=2, precision="mixed", tol=1e-7, max_iters=50,
                sample=dict(npts=(128, 128, 128), nspans=(48, 48, 48), nsub=(2, 2, 2))),
+    # Profiling-size case of the 3-D workload: 384^3 (226 MB, larger than L2), 6x6x6 subdomains of the
+    # same per-subdomain shape; used for ncu captures, not a bench line.
+    "3d384": dict(name="3d_384^3_gauss16_p3_6x6x6sub_24spans_overlap2_mixed", npts=(384, 384, 384), p=3,
+                  nspans=(144, 144, 144), nsub=(6, 6, 6), delta=2, precision="mixed", tol=1e-7, max_iters=50,
+                  sample=dict(npts=(128, 128, 128), nspans=(48, 48, 48), nsub=(2, 2, 2))),
     # BASELINE 2-D workload: 1024^2 sinc(x) sinc(y) + N(0, 1e-3), p = 3, 4x4 subdomains of 64 core spans.
     "2d": dict(name="2d_1024^2_sinc_noise1e-3_p3_4x4sub_64spans_overlap2_mixed", npts=(1024, 1024), p=3,
                nspans=(256, 256), nsub=(4, 4), delta=2, precision="mixed", tol=1e-6, max_iters=50,

@@ -1,0 +1,581 @@
+// Fused 3-D kernels for the data passes of the encode (Algorithm 1 setup and
+// error steps), specialised on the degree P.
+//
+// Accumulation: `AccFF` keeps float-float sums (products formed exactly with
+// FMA, sums compensated).  The kernels read the data once per subdomain window
+// and stream it through shared memory.
+#include <algorithm>
+
+#include "mfa_internal.cuh"
+
+namespace mfa {
+
+// ---------------------------------------------------------------------------
+// accumulation policies
+// ---------------------------------------------------------------------------
+
+struct AccFF {
+  using V = ff;
+  __device__ static V zero() { return ff(0.f, 0.f); }
+  // acc += (nh + nl) * x, x a float: the product hi part is exact with its FMA
+  // error term; the sum uses TwoSum and keeps the low word unnormalised
+  // (renormalised by finish()).
+  __device__ __forceinline__ static void add_f(V& acc, float nh, float nl, float x) {
+    const float p = __fmul_rn(nh, x);
+    float e = __fmaf_rn(nh, x, -p);
+    e = __fmaf_rn(nl, x, e);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, err));
+  }
+  // acc += (nh + nl) * (x.hi + x.lo)
+  __device__ __forceinline__ static void add_v(V& acc, float nh, float nl, V x) {
+    const float p = __fmul_rn(nh, x.hi);
+    float e = __fmaf_rn(nh, x.hi, -p);
+    e = __fmaf_rn(nh, x.lo, e);
+    e = __fmaf_rn(nl, x.hi, e);
+    const float s = __fadd_rn(acc.hi, p);
+    const float bb = __fsub_rn(s, acc.hi);
+    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, err));
+  }
+  __device__ __forceinline__ static V finish(V a) { return fast_two_sum(a.hi, a.lo); }
+};
+
+template <typename TQ>
+__device__ __forceinline__ float to_f(TQ x) {
+  return (float)x;
+}
+
+// ---------------------------------------------------------------------------
+// Projection B_L = (N_z^T x N_y^T x N_x^T) Q over every window (the N^T Q
+// assembly of the local normal equations, Eq. minimization-problem).
+//
+// One CTA per subdomain streams its window in batches of ZB z-planes:
+//   stage 1 (x): one thread per data row; a sliding window of P+1
+//                accumulators walks the row, each point adding its P+1 basis
+//                products; a control point is emitted when the span moves
+//                past it.
+//   stage 2 (y): one thread per (plane, x-control point, chunk of y-control
+//                points), same sliding window down the column.
+//   stage 3 (z): every thread owns NPAIR (x,y) control-point pairs and keeps
+//                a ring of P+1 accumulators per pair across the planes; a
+//                z-control point is written to B_L when the planes' span
+//                moves past it.
+// Every product is (basis hi + lo) x value with an exact FMA product and a
+// compensated (TwoSum) accumulation.
+// ---------------------------------------------------------------------------
+
+struct Proj3dArgs {
+  LayoutDev L;
+  const long long* offL;
+  int zb;     // planes per batch
+  int nch2;   // y-chunks per column in stage 2
+};
+
+template <int P, int NT, int NPAIR, typename TQ>
+__global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* __restrict__ Q, ff* __restrict__ BL,
+                                                         int* status) {
+  constexpr int W = P + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const LayoutDev& L = A.L;
+  const int s = blockIdx.x;
+  const int s0 = s % L.S[0], s1 = (s / L.S[0]) % L.S[1], s2 = s / (L.S[0] * L.S[1]);
+  const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];
+  const int m0 = bx.m, m1 = by.m, m2 = bz.m;
+  const int n0 = bx.nL, n1 = by.nL, n2 = bz.nL;
+  const int zb = A.zb;
+  const long long M0 = L.M[0], M01 = L.M[0] * L.M[1];
+
+  // shared: basis x and y as hi/lo rows of W values, local spans, stage-1 and
+  // stage-2 outputs of the current batch of planes
+  float* bxh = reinterpret_cast<float*>(smem);     // [m0][W]
+  float* bxl = bxh + m0 * W;                        // [m0][W]
+  float* byh = bxl + m0 * W;                        // [m1][W]
+  float* byl = byh + m1 * W;                        // [m1][W]
+  int* spx = reinterpret_cast<int*>(byl + m1 * W);  // [m0]
+  int* spy = spx + m0;                              // [m1]
+  size_t off = (size_t)(2 * W * (m0 + m1)) * 4 + (size_t)(m0 + m1) * 4;
+  off = (off + 15) & ~size_t(15);
+  ff* T1 = reinterpret_cast<ff*>(smem + off);       // [zb][m1][n0]
+  off += (size_t)zb * m1 * n0 * sizeof(ff);
+  ff* T2 = reinterpret_cast<ff*>(smem + off);       // [zb][n1][n0]
+
+  const ff* vx = L.ax[0].vals_ff;
+  const ff* vy = L.ax[1].vals_ff;
+  const ff* vz = L.ax[2].vals_ff;
+  for (int i = threadIdx.x; i < m0; i += NT) {
+    const int k = bx.k0 + i;
+    spx[i] = L.ax[0].span[k] - bx.l0;
+#pragma unroll
+    for (int r = 0; r < W; ++r) {
+      const ff v = vx[(long long)k * W + r];
+      bxh[i * W + r] = v.hi;
+      bxl[i * W + r] = v.lo;
+    }
+  }
+  for (int i = threadIdx.x; i < m1; i += NT) {
+    const int k = by.k0 + i;
+    spy[i] = L.ax[1].span[k] - by.l0;
+#pragma unroll
+    for (int r = 0; r < W; ++r) {
+      const ff v = vy[(long long)k * W + r];
+      byh[i * W + r] = v.hi;
+      byl[i * W + r] = v.lo;
+    }
+  }
+
+  ff ring[NPAIR][W];
+#pragma unroll
+  for (int i = 0; i < NPAIR; ++i)
+#pragma unroll
+    for (int r = 0; r < W; ++r) ring[i][r] = ff(0.f, 0.f);
+  const int npairs = n0 * n1;
+  ff* out = BL + A.offL[s];
+  int curz = L.ax[2].span[bz.k0] - bz.l0;  // z-control point held in ring slot 0
+  bool bad = false;
+  const TQ* qwin = Q + (long long)bx.k0 + M0 * by.k0 + M01 * bz.k0;
+  __syncthreads();
+
+  for (int z0 = 0; z0 < m2; z0 += zb) {
+    const int nz = min(zb, m2 - z0);
+    // ---- stage 1: one data row per thread, read straight from global memory
+    for (int t = threadIdx.x; t < nz * m1; t += NT) {
+      const int zz = t / m1, y = t - zz * m1;
+      const TQ* q = qwin + M01 * (z0 + zz) + M0 * y;
+      ff* o = T1 + t * n0;
+      ff win[W];
+#pragma unroll
+      for (int r = 0; r < W; ++r) win[r] = ff(0.f, 0.f);
+      int cur = spx[0];
+      for (int k = 0; k < m0; ++k) {
+        const float x = to_f<TQ>(__ldg(q + k));
+        bad |= !isfinite(x);
+        const int sk = spx[k];
+        while (cur < sk) {
+          if (cur >= 0 && cur < n0) o[cur] = AccFF::finish(win[0]);
+#pragma unroll
+          for (int r = 0; r < P; ++r) win[r] = win[r + 1];
+          win[P] = ff(0.f, 0.f);
+          ++cur;
+        }
+#pragma unroll
+        for (int r = 0; r < W; ++r) AccFF::add_f(win[r], bxh[k * W + r], bxl[k * W + r], x);
+      }
+#pragma unroll
+      for (int r = 0; r < W; ++r)
+        if (cur + r >= 0 && cur + r < n0) o[cur + r] = AccFF::finish(win[r]);
+    }
+    __syncthreads();
+    // ---- stage 2: columns along y, chunked over the y-control points
+    {
+      const int nch = A.nch2;
+      const int csz = (n1 + nch - 1) / nch;
+      const int* ss = L.ax[1].span_start;
+      for (int t = threadIdx.x; t < nz * n0 * nch; t += NT) {
+        const int zz = t / (n0 * nch);
+        const int rem = t - zz * n0 * nch;
+        const int ch = rem / n0, lx = rem - ch * n0;
+        const int c0 = ch * csz, c1 = min(n1, c0 + csz);
+        if (c0 >= c1) continue;
+        // rows whose span reaches control points [c0, c1): span in [c0-P, c1-1]
+        const int gs0 = max(by.l0 + c0 - P, 0), gs1 = min(by.l0 + c1, L.ax[1].nspans);
+        const int y0 = max(ss[gs0] - by.k0, 0), y1 = min(ss[gs1] - by.k0, m1);
+        const ff* col = T1 + zz * m1 * n0 + lx;
+        ff* o = T2 + zz * n1 * n0 + lx;
+        ff win[W];
+#pragma unroll
+        for (int r = 0; r < W; ++r) win[r] = ff(0.f, 0.f);
+        int cur = y0 < m1 ? spy[y0] : c1;
+        for (int y = y0; y < y1; ++y) {
+          const int sy = spy[y];
+          while (cur < sy) {
+            if (cur >= c0 && cur < c1) o[cur * n0] = AccFF::finish(win[0]);
+#pragma unroll
+            for (int r = 0; r < P; ++r) win[r] = win[r + 1];
+            win[P] = ff(0.f, 0.f);
+            ++cur;
+          }
+          const ff x = col[y * n0];
+#pragma unroll
+          for (int r = 0; r < W; ++r) AccFF::add_v(win[r], byh[y * W + r], byl[y * W + r], x);
+        }
+#pragma unroll
+        for (int r = 0; r < W; ++r)
+          if (cur + r >= c0 && cur + r < c1) o[(cur + r) * n0] = AccFF::finish(win[r]);
+      }
+    }
+    __syncthreads();
+    // ---- stage 3: accumulate the planes into the z ring
+    for (int zz = 0; zz < nz; ++zz) {
+      const int kz = bz.k0 + z0 + zz;
+      const int sz = L.ax[2].span[kz] - bz.l0;
+      while (curz < sz) {
+#pragma unroll
+        for (int i = 0; i < NPAIR; ++i) {
+          const int q = threadIdx.x + i * NT;
+          if (q < npairs && curz >= 0 && curz < n2) out[(long long)curz * npairs + q] = AccFF::finish(ring[i][0]);
+#pragma unroll
+          for (int r = 0; r < P; ++r) ring[i][r] = ring[i][r + 1];
+          ring[i][P] = ff(0.f, 0.f);
+        }
+        ++curz;
+      }
+      float nzh[W], nzl[W];
+#pragma unroll
+      for (int r = 0; r < W; ++r) {
+        const ff v = vz[(long long)kz * W + r];
+        nzh[r] = v.hi;
+        nzl[r] = v.lo;
+      }
+      const ff* t2 = T2 + zz * npairs;
+#pragma unroll
+      for (int i = 0; i < NPAIR; ++i) {
+        const int q = threadIdx.x + i * NT;
+        if (q < npairs) {
+          const ff x = t2[q];
+#pragma unroll
+          for (int r = 0; r < W; ++r) AccFF::add_v(ring[i][r], nzh[r], nzl[r], x);
+        }
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < NPAIR; ++i) {
+    const int q = threadIdx.x + i * NT;
+#pragma unroll
+    for (int r = 0; r < W; ++r)
+      if (q < npairs && curz + r >= 0 && curz + r < n2)
+        out[(long long)(curz + r) * npairs + q] = AccFF::finish(ring[i][r]);
+  }
+  if (bad && status) atomicExch(status, MFA_ERR_NONFINITE);
+}
+
+template <int P>
+size_t proj3d_smem(int m0, int m1, int n0, int n1, int zb) {
+  constexpr int W = P + 1;
+  size_t off = (size_t)(2 * W * (m0 + m1)) * 4 + (size_t)(m0 + m1) * 4;
+  off = (off + 15) & ~size_t(15);
+  off += (size_t)zb * m1 * n0 * sizeof(ff);
+  off += (size_t)zb * n1 * n0 * sizeof(ff);
+  return off;
+}
+
+constexpr int kProjThreads = 256;
+
+// Returns false when the fused kernel does not cover this layout (the caller
+// then runs the generic per-axis kernels).
+template <typename TQ>
+bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, int maxm1, int maxn0, int maxn1,
+                         const TQ* Q, ff* BL, int* status, cudaStream_t st) {
+  const int P = L.ax[0].p;
+  if (L.dim != 3 || L.ax[1].p != P || L.ax[2].p != P) return false;
+  const int npairs = maxn0 * maxn1;
+  Proj3dArgs A;
+  A.L = L;
+  A.offL = offL;
+  // planes per batch: fill the stage-1 rows onto the threads
+  A.zb = std::max(1, std::min(4, kProjThreads / std::max(maxm1, 1)));
+  size_t smem = 0;
+  auto pick = [&](auto kernel, size_t sm) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    A.nch2 = std::max(1, kProjThreads / std::max(1, A.zb * maxn0));
+    kernel<<<L.nsub, kProjThreads, sm, st>>>(A, Q, BL, status);
+  };
+#define MFA_PROJ_CASE(PP)                                                  \
+  case PP: {                                                               \
+    smem = proj3d_smem<PP>(maxm0, maxm1, maxn0, maxn1, A.zb);              \
+    while (smem > 110 * 1024 && A.zb > 1) {                                \
+      A.zb--;                                                              \
+      smem = proj3d_smem<PP>(maxm0, maxm1, maxn0, maxn1, A.zb);            \
+    }                                                                      \
+    if (smem > 200 * 1024) return false;                                   \
+    if (npairs <= 4 * kProjThreads)                                        \
+      pick(k_project3d_ff<PP, kProjThreads, 4, TQ>, smem);                 \
+    else if (npairs <= 8 * kProjThreads)                                   \
+      pick(k_project3d_ff<PP, kProjThreads, 8, TQ>, smem);                 \
+    else                                                                   \
+      return false;                                                        \
+    return true;                                                           \
+  }
+  switch (P) {
+    MFA_PROJ_CASE(2)
+    MFA_PROJ_CASE(3)
+    MFA_PROJ_CASE(4)
+    MFA_PROJ_CASE(5)
+    default:
+      return false;
+  }
+#undef MFA_PROJ_CASE
+}
+
+template bool launch_project3d_ff<float>(const LayoutDev&, const long long*, int, int, int, int, const float*, ff*,
+                                         int*, cudaStream_t);
+template bool launch_project3d_ff<double>(const LayoutDev&, const long long*, int, int, int, int, const double*, ff*,
+                                          int*, cudaStream_t);
+
+}  // namespace mfa
+
+namespace mfa {
+
+// ---------------------------------------------------------------------------
+// value policies shared by the fused decode: V = ff (compensated) or float
+// ---------------------------------------------------------------------------
+
+template <typename V>
+struct Val;
+
+template <>
+struct Val<ff> {
+  __device__ __forceinline__ static ff zero() { return ff(0.f, 0.f); }
+  __device__ __forceinline__ static void add(ff& acc, float nh, float nl, ff x) { AccFF::add_v(acc, nh, nl, x); }
+  __device__ __forceinline__ static ff finish(ff a) { return AccFF::finish(a); }
+  __device__ __forceinline__ static float hi(ff a) { return a.hi; }
+  __device__ __forceinline__ static float lo(ff a) { return a.lo; }
+  __device__ __forceinline__ static const ff* vals(const AxisDev& ax) { return ax.vals_ff; }
+};
+
+template <>
+struct Val<float> {
+  __device__ __forceinline__ static float zero() { return 0.f; }
+  __device__ __forceinline__ static void add(float& acc, float nh, float, float x) { acc = fmaf(nh, x, acc); }
+  __device__ __forceinline__ static float finish(float a) { return a; }
+  __device__ __forceinline__ static float hi(float a) { return a; }
+  __device__ __forceinline__ static float lo(float) { return 0.f; }
+  __device__ __forceinline__ static const ff* vals(const AxisDev& ax) { return ax.vals_ff; }
+};
+
+// ---------------------------------------------------------------------------
+// Grid decode R P (Algorithm 1 error step) on tiles of TX x TY x TZ points,
+// fused with either the residual E = Q - R P (per-CTA partial sums of E^2,
+// max |E|, min Q, max Q) or a write of the decoded values.
+//
+// Per tile: load the (spans + P) control-point block, expand along z, then y,
+// then x; every output sums P+1 basis products with the basis held as hi/lo
+// floats (float-float sums for V = ff).
+// ---------------------------------------------------------------------------
+
+constexpr int kDecTX = 64, kDecTY = 8, kDecTZ = 8, kDecThreads = 256;
+
+template <int P, typename V, typename TQ, typename TOut, bool RESID>
+__global__ void __launch_bounds__(kDecThreads) k_decode3d(LayoutDev L, const V* __restrict__ Pc,
+                                                          const TQ* __restrict__ Q, TOut* __restrict__ out,
+                                                          double* __restrict__ partials) {
+  constexpr int W = P + 1;
+  constexpr int CX = (kDecTX * 1) + P + 1;  // generous bound on control points per tile row
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int ntx = (int)((L.M[0] + kDecTX - 1) / kDecTX), nty = (int)((L.M[1] + kDecTY - 1) / kDecTY);
+  const int tile = blockIdx.x;
+  const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+  const int x0 = tx * kDecTX, y0 = ty * kDecTY, z0 = tz * kDecTZ;
+  const int x1 = min(x0 + kDecTX, (int)L.M[0]), y1 = min(y0 + kDecTY, (int)L.M[1]), z1 = min(z0 + kDecTZ, (int)L.M[2]);
+  const int nx = x1 - x0, ny = y1 - y0, nz = z1 - z0;
+  const AxisDev &ax = L.ax[0], &ay = L.ax[1], &az = L.ax[2];
+  const int cx0 = ax.span[x0], cy0 = ay.span[y0], cz0 = az.span[z0];
+  const int ncx = ax.span[x1 - 1] + W - cx0, ncy = ay.span[y1 - 1] + W - cy0, ncz = az.span[z1 - 1] + W - cz0;
+  (void)CX;
+
+  // shared: basis of the tile's points (hi/lo), local spans, control block,
+  // z-expanded and y-expanded blocks
+  float* nxh = reinterpret_cast<float*>(smem);  // [TX][W]
+  float* nxl = nxh + kDecTX * W;
+  float* nyh = nxl + kDecTX * W;                // [TY][W]
+  float* nyl = nyh + kDecTY * W;
+  float* nzh = nyl + kDecTY * W;                // [TZ][W]
+  float* nzl = nzh + kDecTZ * W;
+  int* sx = reinterpret_cast<int*>(nzl + kDecTZ * W);
+  int* sy = sx + kDecTX;
+  int* sz = sy + kDecTY;
+  size_t off = (size_t)(2 * W * (kDecTX + kDecTY + kDecTZ)) * 4 + (size_t)(kDecTX + kDecTY + kDecTZ) * 4;
+  off = (off + 15) & ~size_t(15);
+  V* Pb = reinterpret_cast<V*>(smem + off);  // [ncz][ncy][ncx]
+  off += (size_t)ncz * ncy * ncx * sizeof(V);
+  V* Tz = reinterpret_cast<V*>(smem + off);  // [nz][ncy][ncx]
+  off += (size_t)kDecTZ * ncy * ncx * sizeof(V);
+  V* Ty = reinterpret_cast<V*>(smem + off);  // [nz][ny][ncx]
+
+  const ff* vx = ax.vals_ff;
+  const ff* vy = ay.vals_ff;
+  const ff* vz = az.vals_ff;
+  for (int i = threadIdx.x; i < nx * W; i += kDecThreads) {
+    const int k = i / W, r = i - k * W;
+    const ff v = vx[(long long)(x0 + k) * W + r];
+    nxh[k * W + r] = v.hi;
+    nxl[k * W + r] = v.lo;
+    if (r == 0) sx[k] = ax.span[x0 + k] - cx0;
+  }
+  for (int i = threadIdx.x; i < ny * W; i += kDecThreads) {
+    const int k = i / W, r = i - k * W;
+    const ff v = vy[(long long)(y0 + k) * W + r];
+    nyh[k * W + r] = v.hi;
+    nyl[k * W + r] = v.lo;
+    if (r == 0) sy[k] = ay.span[y0 + k] - cy0;
+  }
+  for (int i = threadIdx.x; i < nz * W; i += kDecThreads) {
+    const int k = i / W, r = i - k * W;
+    const ff v = vz[(long long)(z0 + k) * W + r];
+    nzh[k * W + r] = v.hi;
+    nzl[k * W + r] = v.lo;
+    if (r == 0) sz[k] = az.span[z0 + k] - cz0;
+  }
+  // control-point block
+  const long long n0 = L.ncp[0], n01 = L.ncp[0] * L.ncp[1];
+  const int nb = ncz * ncy * ncx;
+  for (int i = threadIdx.x; i < nb; i += kDecThreads) {
+    const int cx = i % ncx, r2 = i / ncx;
+    const int cy = r2 % ncy, cz = r2 / ncy;
+    Pb[i] = Pc[(long long)(cx0 + cx) + n0 * (cy0 + cy) + n01 * (cz0 + cz)];
+  }
+  __syncthreads();
+  // z expansion: Tz[z][cy][cx]
+  const int nzc = nz * ncy * ncx;
+  for (int i = threadIdx.x; i < nzc; i += kDecThreads) {
+    const int cx = i % ncx, r2 = i / ncx;
+    const int cy = r2 % ncy, z = r2 / ncy;
+    const V* src = Pb + (sz[z] * ncy + cy) * ncx + cx;
+    V acc = Val<V>::zero();
+#pragma unroll
+    for (int r = 0; r < W; ++r) Val<V>::add(acc, nzh[z * W + r], nzl[z * W + r], src[r * ncy * ncx]);
+    Tz[i] = Val<V>::finish(acc);
+  }
+  __syncthreads();
+  // y expansion: Ty[z][y][cx]
+  const int nyc = nz * ny * ncx;
+  for (int i = threadIdx.x; i < nyc; i += kDecThreads) {
+    const int cx = i % ncx, r2 = i / ncx;
+    const int y = r2 % ny, z = r2 / ny;
+    const V* src = Tz + (z * ncy + sy[y]) * ncx + cx;
+    V acc = Val<V>::zero();
+#pragma unroll
+    for (int r = 0; r < W; ++r) Val<V>::add(acc, nyh[y * W + r], nyl[y * W + r], src[r * ncx]);
+    Ty[i] = Val<V>::finish(acc);
+  }
+  __syncthreads();
+  // x expansion of every point of the tile, then residual or output
+  float s2 = 0.f, emax = 0.f, qmin = INFINITY, qmax = -INFINITY;
+  const long long M0 = L.M[0], M01 = L.M[0] * L.M[1];
+  const int npt = nz * ny * nx;
+  for (int i = threadIdx.x; i < npt; i += kDecThreads) {
+    const int x = i % nx, r2 = i / nx;
+    const int y = r2 % ny, z = r2 / ny;
+    const V* src = Ty + (z * ny + y) * ncx + sx[x];
+    V acc = Val<V>::zero();
+#pragma unroll
+    for (int r = 0; r < W; ++r) Val<V>::add(acc, nxh[x * W + r], nxl[x * W + r], src[r]);
+    acc = Val<V>::finish(acc);
+    const long long g = (long long)(x0 + x) + M0 * (y0 + y) + M01 * (z0 + z);
+    if constexpr (RESID) {
+      const float q = (float)Q[g];
+      // E = q - (hi + lo): q - hi is exact when the fit is close (Sterbenz)
+      const float e = __fsub_rn(__fsub_rn(q, Val<V>::hi(acc)), Val<V>::lo(acc));
+      s2 = fmaf(e, e, s2);
+      emax = fmaxf(emax, fabsf(e));
+      qmin = fminf(qmin, q);
+      qmax = fmaxf(qmax, q);
+    } else {
+      out[g] = (TOut)((double)Val<V>::hi(acc) + (double)Val<V>::lo(acc));
+    }
+  }
+  if constexpr (RESID) {
+    // block reduction in FP64 (few operations per block) into this tile's slot
+    double ds2 = s2;
+    double demax = emax, dqmin = qmin, dqmax = qmax;
+    for (int o = 16; o > 0; o >>= 1) {
+      ds2 += __shfl_down_sync(0xffffffffu, ds2, o);
+      demax = fmax(demax, __shfl_down_sync(0xffffffffu, demax, o));
+      dqmin = fmin(dqmin, __shfl_down_sync(0xffffffffu, dqmin, o));
+      dqmax = fmax(dqmax, __shfl_down_sync(0xffffffffu, dqmax, o));
+    }
+    __shared__ double red[4][kDecThreads / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+      red[0][wid] = ds2;
+      red[1][wid] = demax;
+      red[2][wid] = dqmin;
+      red[3][wid] = dqmax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0, b = 0.0, c = INFINITY, d = -INFINITY;
+      for (int w = 0; w < kDecThreads / 32; ++w) {
+        a += red[0][w];
+        b = fmax(b, red[1][w]);
+        c = fmin(c, red[2][w]);
+        d = fmax(d, red[3][w]);
+      }
+      partials[4 * (long long)tile + 0] = a;
+      partials[4 * (long long)tile + 1] = b;
+      partials[4 * (long long)tile + 2] = c;
+      partials[4 * (long long)tile + 3] = d;
+    }
+  }
+}
+
+template <int P, typename V>
+size_t decode3d_smem(int ncx, int ncy, int ncz) {
+  constexpr int W = P + 1;
+  size_t off = (size_t)(2 * W * (kDecTX + kDecTY + kDecTZ)) * 4 + (size_t)(kDecTX + kDecTY + kDecTZ) * 4;
+  off = (off + 15) & ~size_t(15);
+  off += (size_t)ncz * ncy * ncx * sizeof(V);
+  off += (size_t)kDecTZ * ncy * ncx * sizeof(V);
+  off += (size_t)kDecTZ * kDecTY * ncx * sizeof(V);
+  return off;
+}
+
+long long decode3d_tiles(const LayoutDev& L) {
+  return ((L.M[0] + kDecTX - 1) / kDecTX) * ((L.M[1] + kDecTY - 1) / kDecTY) * ((L.M[2] + kDecTZ - 1) / kDecTZ);
+}
+
+// Bound on the control points a tile of `t` consecutive points touches.
+static int tile_cps(const AxisDev& ax, int t) {
+  // t points cover at most ceil((t-1) * nspans / (M-1)) + 1 spans
+  const long long M = ax.M;
+  if (M <= 1) return ax.p + 1;
+  const long long spans = ((long long)(t - 1) * ax.nspans + (M - 2)) / (M - 1) + 1;
+  return (int)std::min<long long>(spans + ax.p, ax.n);
+}
+
+template <typename V, typename TQ, typename TOut, bool RESID>
+bool launch_decode3d(const LayoutDev& L, const V* P, const TQ* Q, TOut* out, double* partials, cudaStream_t st) {
+  const int p = L.ax[0].p;
+  if (L.dim != 3 || L.ax[1].p != p || L.ax[2].p != p) return false;
+  const int ncx = tile_cps(L.ax[0], kDecTX), ncy = tile_cps(L.ax[1], kDecTY), ncz = tile_cps(L.ax[2], kDecTZ);
+  const long long tiles = decode3d_tiles(L);
+  if (tiles > (1LL << 31) - 1) return false;
+  auto go = [&](auto kernel, size_t smem) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kernel<<<(unsigned)tiles, kDecThreads, smem, st>>>(L, P, Q, out, partials);
+  };
+#define MFA_DEC_CASE(PP)                                                    \
+  case PP: {                                                                \
+    const size_t sm = decode3d_smem<PP, V>(ncx, ncy, ncz);                  \
+    if (sm > 200 * 1024) return false;                                      \
+    go(k_decode3d<PP, V, TQ, TOut, RESID>, sm);                             \
+    return true;                                                            \
+  }
+  switch (p) {
+    MFA_DEC_CASE(2)
+    MFA_DEC_CASE(3)
+    MFA_DEC_CASE(4)
+    MFA_DEC_CASE(5)
+    default:
+      return false;
+  }
+#undef MFA_DEC_CASE
+}
+
+template bool launch_decode3d<ff, float, float, true>(const LayoutDev&, const ff*, const float*, float*, double*,
+                                                      cudaStream_t);
+template bool launch_decode3d<ff, double, float, true>(const LayoutDev&, const ff*, const double*, float*, double*,
+                                                       cudaStream_t);
+template bool launch_decode3d<ff, float, float, false>(const LayoutDev&, const ff*, const float*, float*, double*,
+                                                       cudaStream_t);
+template bool launch_decode3d<ff, float, double, false>(const LayoutDev&, const ff*, const float*, double*, double*,
+                                                        cudaStream_t);
+
+}  // namespace mfa

@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "mfa_internal.cuh"
@@ -50,6 +51,7 @@ struct mfa_model {
   int nsub = 1;
   long long sizeL = 0, sizeS1 = 0, sizeS2 = 0;
   int maxL = 0, maxU = 0, maxS1 = 0, maxS2 = 0;
+  int maxm[3] = {0, 0, 0}, maxnL[3] = {0, 0, 0};  // largest window points / L per axis
   int maxOut[3] = {0, 0, 0};      // projection stage output sizes
   int maxApply[3] = {0, 0, 0};    // band-apply output sizes
   int maxFibL[3] = {0, 0, 0};     // fibres per solve, L boxes
@@ -61,6 +63,7 @@ struct mfa_model {
   AxisOp* ops = nullptr;  // [kOpKinds][nsub]
   // big buffers
   void *BL = nullptr, *X = nullptr, *P = nullptr, *Pprev = nullptr, *S1 = nullptr, *S2 = nullptr;
+  bool use_fused = true;  // fused 3-D kernels where they cover the layout
   int iters = 0;
   int grow_streak = 0;
   double last_dP = 0.0;
@@ -349,6 +352,10 @@ void build_ops(mfa_model* md, std::vector<AxisOp>& ops, std::vector<long long>& 
     a1 += sz1;
     a2 += sz2;
     md->maxL = std::max<long long>(md->maxL, szL);
+    for (int a = 0; a < 3; ++a) {
+      md->maxm[a] = std::max(md->maxm[a], m[a]);
+      md->maxnL[a] = std::max(md->maxnL[a], nL[a]);
+    }
     md->maxU = std::max(md->maxU, nU[0] * nU[1] * nU[2]);
     auto at = [&](int kind) -> AxisOp& { return ops[(size_t)kind * ns + s]; };
     // projection stages: Q window -> S1 -> S2 -> B_L, skipping padded axes
@@ -452,8 +459,17 @@ void run_encode(mfa_model* md, const TQ* q) {
   T* S1 = (T*)md->S1;
   T* S2 = (T*)md->S2;
   auto opsk = [&](int kind) { return md->ops + (size_t)kind * ns; };
-  // projection: stage a reads the previous stage (the data for a = 0)
-  for (int a = 0; a < md->dim; ++a) {
+  // projection: the fused 3-D kernel when it covers the layout, else one
+  // launch per axis where stage a reads the previous stage (the data for a = 0)
+  bool fused = false;
+  if constexpr (std::is_same<T, ff>::value) {
+    if (md->dim == 3 && md->use_fused) {
+      TRACED(h, TR_PROJECT_DATA,
+             fused = launch_project3d_ff<TQ>(L, md->offL, md->maxm[0], md->maxm[1], md->maxnL[0], md->maxnL[1], q, BL,
+                                              h->d_status, h->stream));
+    }
+  }
+  for (int a = 0; a < md->dim && !fused; ++a) {
     T* out = (a == md->dim - 1) ? BL : (a == 0 ? S1 : S2);
     if (a == 0)
       TRACED(h, TR_PROJECT_DATA,
@@ -507,6 +523,29 @@ int run_decode_grid(mfa_model* md, TOut* out, const TQ* q) {
   const LayoutDev& L = md->L;
   const int ns = md->nsub;
   const int d = md->dim;
+  // fused 3-D tiles: one kernel, residual partials per tile
+  if constexpr (std::is_same<T, ff>::value) {
+    if (d == 3 && md->use_fused) {
+      bool fused = false;
+      if (q) {
+        const long long tiles = decode3d_tiles(L);
+        int rc = ensure_ws(h, (size_t)tiles * 4 * sizeof(double));
+        if (rc != MFA_OK) return rc;
+        double* part = (double*)h->ws;
+        TRACED(h, TR_RESIDUAL,
+               fused = (launch_decode3d<ff, TQ, float, true>(L, (const ff*)md->P, q, nullptr, part, h->stream)));
+        if (fused) {
+          TRACED(h, TR_REDUCE, launch_reduce_partials(part, (int)tiles, h->d_result, h->stream));
+          return MFA_OK;
+        }
+      } else if constexpr (!std::is_same<TOut, ff>::value) {
+        TRACED(h, TR_DECODE_OUT,
+               fused = (launch_decode3d<ff, float, TOut, false>(L, (const ff*)md->P, (const float*)nullptr, out,
+                                                                 nullptr, h->stream)));
+        if (fused) return MFA_OK;
+      }
+    }
+  }
   // scratch for intermediate stages
   long long sz[3] = {0, 0, 0};
   {

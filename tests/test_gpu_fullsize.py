@@ -62,3 +62,17 @@ def test_fullsize_2d_1024_mixed():
     """2-D workload: 1024^2 sinc(x)sinc(y) + N(0,1e-3), 4x4 subdomains of 64 core spans."""
     Q = inputs.sinc_2d(1024, noise=1e-3, seed=0, dtype=np.float32)
     _mixed_case(Q, 3, [256, 256], [4, 4], 2, 1e-6)
+
+
+@pytest.mark.parametrize("p,delta,nsub,nspans,npts", [
+    (2, 1, (2, 3, 2), (14, 16, 12), (41, 47, 35)),
+    (3, 0, (2, 2, 2), (12, 12, 12), (37, 33, 35)),
+    (4, 3, (2, 2, 1), (12, 10, 8), (45, 40, 31)),
+    (5, 2, (2, 1, 2), (14, 8, 12), (50, 33, 46)),
+    (3, 6, (3, 2, 2), (15, 12, 12), (43, 38, 37)),
+])
+def test_mixed_3d_degrees_and_overlaps(p, delta, nsub, nspans, npts):
+    """Mixed path in 3-D (fused projection) across degrees, overlaps, ragged
+    grids and uneven splits: control points within 1e-9 of the oracle."""
+    Q = inputs.gauss_3d(npts, seed=p, dtype=np.float32)
+    _mixed_case(Q, p, list(nspans), list(nsub), delta, 1e-9, max_iters=60)
