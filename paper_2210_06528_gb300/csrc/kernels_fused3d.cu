@@ -579,3 +579,394 @@ template bool launch_decode3d<ff, float, double, false>(const LayoutDev&, const 
                                                         cudaStream_t);
 
 }  // namespace mfa
+
+namespace mfa {
+
+// ---------------------------------------------------------------------------
+// Schwarz step k >= 1 in defect-correction form (Sec. 2.3.2; the Schur
+// decoupling of Eq. global-system):
+//   r_s   = B_U - A_L[U, :] P^{k-1}|_L      (residual of the local normal equations)
+//   c_s   = (A_U,0 x A_U,1 x A_U,2)^{-1} r_s (banded Cholesky solves)
+//   X_s   = P^{k-1}|_U + c_s
+// which equals A_U^{-1} (B_U - A_L[U, F] P_F) because A_L[U, U] = A_U.  All
+// of it runs in float-float.
+//
+// One CTA per subdomain: the L box of P^{k-1} streams through shared memory
+// plane by plane along z (the next plane is fetched into registers while the
+// current one is processed); per plane the x and y band products run in
+// shared memory and the z band product accumulates in a register ring of 2P+1
+// owned z-points per owned (x, y) pair.  The residual box stays in shared
+// memory for the three fibre solves.
+// ---------------------------------------------------------------------------
+
+struct Step3dArgs {
+  LayoutDev L;
+  const long long* offL;
+};
+
+template <int P>
+__device__ __forceinline__ void load_band_rows(const AxisDev& ax, const AxisSub& b, float* h, float* l) {
+  // full band rows of A_L for the owned rows: row u holds A(oU+u, oU+u-P+e), e = 0..2P
+  constexpr int B = 2 * P + 1;
+  const double* A = ax.AL + (long long)b.bandL * (P + 1);
+  for (int i = threadIdx.x; i < b.nU * B; i += blockDim.x) {
+    const int u = i / B, e = i - u * B;
+    const int r = b.oU + u, c = r - P + e;
+    double v = 0.0;
+    if (c >= 0 && c < b.nL) v = c >= r ? A[(long long)r * (P + 1) + (c - r)] : A[(long long)c * (P + 1) + (r - c)];
+    const ff f(v);
+    h[i] = f.hi;
+    l[i] = f.lo;
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void load_factor(const AxisDev& ax, const AxisSub& b, float* h, float* l) {
+  constexpr int W = P + 1;
+  const ff* F = ax.facU_ff + (long long)b.bandU * W;
+  for (int i = threadIdx.x; i < b.nU * W; i += blockDim.x) {
+    h[i] = F[i].hi;
+    l[i] = F[i].lo;
+  }
+}
+
+// In-place banded Cholesky solve of one fibre in float-float: L y = c, L^T x = y.
+// F rows hold 1/L(i,i) at [i*W] and L(i,i-e) at [i*W+e].
+template <int P>
+__device__ __forceinline__ void solve_fibre_ff(ff* x, int n, int s, const float* Fh, const float* Fl) {
+  constexpr int W = P + 1;
+  for (int i = 0; i < n; ++i) {
+    ff acc = x[i * s];
+#pragma unroll
+    for (int e = 1; e <= P; ++e)
+      if (i - e >= 0) AccFF::add_v(acc, -Fh[i * W + e], -Fl[i * W + e], x[(i - e) * s]);
+    x[i * s] = AccFF::finish(acc) * ff(Fh[i * W], Fl[i * W]);
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    ff acc = x[i * s];
+#pragma unroll
+    for (int e = 1; e <= P; ++e)
+      if (i + e < n) AccFF::add_v(acc, -Fh[(i + e) * W + e], -Fl[(i + e) * W + e], x[(i + e) * s]);
+    x[i * s] = AccFF::finish(acc) * ff(Fh[i * W], Fl[i * W]);
+  }
+}
+
+template <int P, int NT, int NPAIR, int NPRE>
+__global__ void __launch_bounds__(NT, 1) k_schwarz3d_ff(Step3dArgs A, const ff* __restrict__ Pg,
+                                                         const ff* __restrict__ BL, ff* __restrict__ X) {
+  constexpr int W = P + 1, B = 2 * P + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const LayoutDev& L = A.L;
+  const int s = blockIdx.x;
+  const int s0 = s % L.S[0], s1 = (s / L.S[0]) % L.S[1], s2 = s / (L.S[0] * L.S[1]);
+  const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];
+  const int nL0 = bx.nL, nL1 = by.nL, nL2 = bz.nL;
+  const int nU0 = bx.nU, nU1 = by.nU, nU2 = bz.nU;
+  const int oU0 = bx.oU, oU1 = by.oU, oU2 = bz.oU;
+  const long long n0 = L.ncp[0], n01 = L.ncp[0] * L.ncp[1];
+
+  float* axh = reinterpret_cast<float*>(smem);  // [nU0][B]
+  float* axl = axh + nU0 * B;
+  float* ayh = axl + nU0 * B;                    // [nU1][B]
+  float* ayl = ayh + nU1 * B;
+  float* azh = ayl + nU1 * B;                    // [nU2][B]
+  float* azl = azh + nU2 * B;
+  float* fxh = azl + nU2 * B;                    // [nU][W] factors of A_U per axis
+  float* fxl = fxh + nU0 * W;
+  float* fyh = fxl + nU0 * W;
+  float* fyl = fyh + nU1 * W;
+  float* fzh = fyl + nU1 * W;
+  float* fzl = fzh + nU2 * W;
+  size_t off = (size_t)(2 * B * (nU0 + nU1 + nU2) + 2 * W * (nU0 + nU1 + nU2)) * 4;
+  off = (off + 15) & ~size_t(15);
+  ff* Pp = reinterpret_cast<ff*>(smem + off);    // [nL1][nL0]
+  off += (size_t)nL1 * nL0 * sizeof(ff);
+  ff* Y1 = reinterpret_cast<ff*>(smem + off);    // [nL1][nU0]
+  off += (size_t)nL1 * nU0 * sizeof(ff);
+  ff* Y2 = reinterpret_cast<ff*>(smem + off);    // [nU1][nU0]
+  off += (size_t)nU1 * nU0 * sizeof(ff);
+  ff* R = reinterpret_cast<ff*>(smem + off);     // [nU2][nU1][nU0]
+
+  load_band_rows<P>(L.ax[0], bx, axh, axl);
+  load_band_rows<P>(L.ax[1], by, ayh, ayl);
+  load_band_rows<P>(L.ax[2], bz, azh, azl);
+  load_factor<P>(L.ax[0], bx, fxh, fxl);
+  load_factor<P>(L.ax[1], by, fyh, fyl);
+  load_factor<P>(L.ax[2], bz, fzh, fzl);
+
+  const int npairs = nU0 * nU1;
+  const int nplane = nL1 * nL0;
+  ff ring[NPAIR][B];
+#pragma unroll
+  for (int i = 0; i < NPAIR; ++i)
+#pragma unroll
+    for (int j = 0; j < B; ++j) ring[i][j] = ff(0.f, 0.f);
+  const ff* bl = BL + A.offL[s];
+  const ff* pg = Pg + (long long)bx.l0 + n0 * by.l0 + n01 * bz.l0;
+
+  // planes that reach an owned z-point through the band
+  const int lz_lo = max(0, oU2 - P), lz_hi = min(nL2 - 1, oU2 + nU2 - 1 + P);
+  ff pre[NPRE];
+  auto fetch = [&](int lz) {
+#pragma unroll
+    for (int k = 0; k < NPRE; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < nplane) {
+        const int ly = i / nL0, lx = i - ly * nL0;
+        pre[k] = pg[lx + n0 * ly + n01 * lz];
+      }
+    }
+  };
+  fetch(lz_lo);
+  for (int lz = lz_lo; lz <= lz_hi; ++lz) {
+#pragma unroll
+    for (int k = 0; k < NPRE; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < nplane) Pp[i] = pre[k];
+    }
+    __syncthreads();
+    if (lz < lz_hi) fetch(lz + 1);
+    // x band product, owned x rows
+    for (int i = threadIdx.x; i < nL1 * nU0; i += NT) {
+      const int ly = i / nU0, ux = i - ly * nU0;
+      const int c0 = oU0 + ux - P;
+      ff acc(0.f, 0.f);
+#pragma unroll
+      for (int e = 0; e < B; ++e) {
+        const int c = c0 + e;
+        if (c >= 0 && c < nL0) AccFF::add_v(acc, axh[ux * B + e], axl[ux * B + e], Pp[ly * nL0 + c]);
+      }
+      Y1[i] = AccFF::finish(acc);
+    }
+    __syncthreads();
+    // y band product, owned y rows
+    for (int i = threadIdx.x; i < nU1 * nU0; i += NT) {
+      const int uy = i / nU0, ux = i - uy * nU0;
+      const int c0 = oU1 + uy - P;
+      ff acc(0.f, 0.f);
+#pragma unroll
+      for (int e = 0; e < B; ++e) {
+        const int c = c0 + e;
+        if (c >= 0 && c < nL1) AccFF::add_v(acc, ayh[uy * B + e], ayl[uy * B + e], Y1[c * nU0 + ux]);
+      }
+      Y2[i] = AccFF::finish(acc);
+    }
+    __syncthreads();
+    // z band product into the ring: slot j holds owned z-point uz = lz - oU2 - P + j
+    const int uzb = lz - oU2 - P;
+#pragma unroll
+    for (int i = 0; i < NPAIR; ++i) {
+      const int q = threadIdx.x + i * NT;
+      if (q < npairs) {
+        const ff y2 = Y2[q];
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+          const int uz = uzb + j;
+          if (uz >= 0 && uz < nU2) AccFF::add_v(ring[i][j], azh[uz * B + (2 * P - j)], azl[uz * B + (2 * P - j)], y2);
+        }
+        // slot 0 is complete: residual r = B_U - (A x A x A) P
+        if (uzb >= 0 && uzb < nU2) {
+          const int ux = q % nU0, uy = q / nU0;
+          const ff b = bl[(oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uzb))];
+          R[(uzb * nU1 + uy) * nU0 + ux] = b - AccFF::finish(ring[i][0]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < B - 1; ++j) ring[i][j] = ring[i][j + 1];
+      ring[i][B - 1] = ff(0.f, 0.f);
+    }
+    __syncthreads();
+  }
+  // owned z-points whose band ended with the last plane
+  {
+    const int uzb = lz_hi + 1 - oU2 - P;  // z-point now in slot 0
+#pragma unroll
+    for (int i = 0; i < NPAIR; ++i) {
+      const int q = threadIdx.x + i * NT;
+      if (q >= npairs) continue;
+      const int ux = q % nU0, uy = q / nU0;
+#pragma unroll
+      for (int j = 0; j < B; ++j) {
+        const int uz = uzb + j;
+        if (uz >= 0 && uz < nU2) {
+          const ff b = bl[(oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uz))];
+          R[(uz * nU1 + uy) * nU0 + ux] = b - AccFF::finish(ring[i][j]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // correction c = A_U^{-1} r, one fibre per thread and axis
+  for (int f = threadIdx.x; f < nU1 * nU2; f += NT) solve_fibre_ff<P>(R + f * nU0, nU0, 1, fxh, fxl);
+  __syncthreads();
+  for (int f = threadIdx.x; f < nU0 * nU2; f += NT) {
+    const int ux = f % nU0, uz = f / nU0;
+    solve_fibre_ff<P>(R + uz * nU1 * nU0 + ux, nU1, nU0, fyh, fyl);
+  }
+  __syncthreads();
+  for (int f = threadIdx.x; f < nU0 * nU1; f += NT) solve_fibre_ff<P>(R + f, nU2, nU0 * nU1, fzh, fzl);
+  __syncthreads();
+  // owned copy X_s = P^{k-1}|_U + c_s
+  ff* xo = X + A.offL[s];
+  const int nUall = nU0 * nU1 * nU2;
+  for (int i = threadIdx.x; i < nUall; i += NT) {
+    const int ux = i % nU0, r2 = i / nU0;
+    const int uy = r2 % nU1, uz = r2 / nU1;
+    const ff pv = pg[(oU0 + ux) + n0 * (oU1 + uy) + n01 * (oU2 + uz)];
+    xo[(oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uz))] = pv + R[i];
+  }
+}
+
+template <int P>
+size_t step3d_smem(int nL0, int nL1, int nU0, int nU1, int nU2) {
+  constexpr int W = P + 1, B = 2 * P + 1;
+  size_t off = (size_t)(2 * B * (nU0 + nU1 + nU2) + 2 * W * (nU0 + nU1 + nU2)) * 4;
+  off = (off + 15) & ~size_t(15);
+  off += (size_t)nL1 * nL0 * sizeof(ff) + (size_t)nL1 * nU0 * sizeof(ff) + (size_t)nU1 * nU0 * sizeof(ff);
+  off += (size_t)nU0 * nU1 * nU2 * sizeof(ff);
+  return off;
+}
+
+constexpr int kStepThreads = 512;
+
+bool launch_schwarz3d_ff(const LayoutDev& L, const long long* offL, const int* maxnL, const int* maxnU, const ff* P,
+                         const ff* BL, ff* X, cudaStream_t st) {
+  const int p = L.ax[0].p;
+  if (L.dim != 3 || L.ax[1].p != p || L.ax[2].p != p) return false;
+  Step3dArgs A;
+  A.L = L;
+  A.offL = offL;
+  const int npairs = maxnU[0] * maxnU[1];
+  const int nplane = maxnL[0] * maxnL[1];
+  if (npairs > 2 * kStepThreads || nplane > 4 * kStepThreads) return false;
+  auto go = [&](auto kernel, size_t sm) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    kernel<<<L.nsub, kStepThreads, sm, st>>>(A, P, BL, X);
+  };
+#define MFA_STEP_CASE(PP)                                                                      \
+  case PP: {                                                                                   \
+    const size_t sm = step3d_smem<PP>(maxnL[0], maxnL[1], maxnU[0], maxnU[1], maxnU[2]);       \
+    if (sm > 220 * 1024) return false;                                                         \
+    if (nplane <= 2 * kStepThreads)                                                            \
+      go(k_schwarz3d_ff<PP, kStepThreads, 2, 2>, sm);                                          \
+    else                                                                                       \
+      go(k_schwarz3d_ff<PP, kStepThreads, 2, 4>, sm);                                          \
+    return true;                                                                               \
+  }
+  switch (p) {
+    MFA_STEP_CASE(2)
+    MFA_STEP_CASE(3)
+    MFA_STEP_CASE(4)
+    MFA_STEP_CASE(5)
+    default:
+      return false;
+  }
+#undef MFA_STEP_CASE
+}
+
+// ---------------------------------------------------------------------------
+// Update (Sec. 2.3.2) in float-float: P^k(g) = (1/n_s) sum of the owned copies
+// of g in a fixed order; metrics max|P^k - P^{k-1}|, max|P^k| and the copy
+// spread are formed from float-float differences, so no FP64 arithmetic runs.
+// One thread per control point on a 3-D grid (no index divisions).
+// ---------------------------------------------------------------------------
+
+__constant__ float c_inv_hi[9], c_inv_lo[9];  // 1/n as float-float, n = 1..8
+
+__device__ __forceinline__ void atomic_max_f(unsigned long long* addr, float v) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong((double)v));
+}
+
+__global__ void __launch_bounds__(128) k_average_ff(LayoutDev L, const long long* __restrict__ offL,
+                                                    const ff* __restrict__ X, ff* __restrict__ P,
+                                                    const ff* __restrict__ Pprev, unsigned long long* metrics) {
+  const int g0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g1 = blockIdx.y, g2 = blockIdx.z;
+  float dmax = 0.f, pmax = 0.f, spread = 0.f;
+  if (g0 < (int)L.ncp[0]) {
+    const int f0 = L.ax[0].own_first[g0], c0n = L.ax[0].own_count[g0];
+    const int f1 = L.ax[1].own_first[g1], c1n = L.ax[1].own_count[g1];
+    const int f2 = L.ax[2].own_first[g2], c2n = L.ax[2].own_count[g2];
+    ff sum(0.f, 0.f), first(0.f, 0.f);
+    float dlo = 0.f, dhi = 0.f;
+    int cnt = 0;
+    for (int c2 = 0; c2 < c2n; ++c2) {
+      const AxisSub b2 = L.ax[2].subs[f2 + c2];
+      for (int c1 = 0; c1 < c1n; ++c1) {
+        const AxisSub b1 = L.ax[1].subs[f1 + c1];
+        for (int c0 = 0; c0 < c0n; ++c0) {
+          const AxisSub b0 = L.ax[0].subs[f0 + c0];
+          const int s = (f0 + c0) + L.S[0] * ((f1 + c1) + L.S[1] * (f2 + c2));
+          const int li = (g0 - b0.l0) + b0.nL * ((g1 - b1.l0) + b1.nL * (g2 - b2.l0));
+          const ff v = X[offL[s] + li];
+          sum = sum + v;
+          if (cnt == 0) {
+            first = v;
+          } else {
+            const ff d = v - first;
+            const float df = d.hi + d.lo;
+            dlo = fminf(dlo, df);
+            dhi = fmaxf(dhi, df);
+          }
+          ++cnt;
+        }
+      }
+    }
+    const ff pn = cnt == 1 ? sum : sum * ff(c_inv_hi[cnt], c_inv_lo[cnt]);
+    const long long g = (long long)g0 + L.ncp[0] * ((long long)g1 + L.ncp[1] * g2);
+    P[g] = pn;
+    pmax = fabsf(pn.hi);
+    spread = dhi - dlo;
+    if (Pprev) {
+      const ff d = pn - Pprev[g];
+      dmax = fabsf(d.hi + d.lo);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dmax = fmaxf(dmax, __shfl_down_sync(0xffffffffu, dmax, o));
+    pmax = fmaxf(pmax, __shfl_down_sync(0xffffffffu, pmax, o));
+    spread = fmaxf(spread, __shfl_down_sync(0xffffffffu, spread, o));
+  }
+  __shared__ float red[3][4];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = dmax;
+    red[1][wid] = pmax;
+    red[2][wid] = spread;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float a = red[0][0], b = red[1][0], c = red[2][0];
+    for (int w = 1; w < 4; ++w) {
+      a = fmaxf(a, red[0][w]);
+      b = fmaxf(b, red[1][w]);
+      c = fmaxf(c, red[2][w]);
+    }
+    atomic_max_f(&metrics[0], a);
+    atomic_max_f(&metrics[1], b);
+    atomic_max_f(&metrics[2], c);
+  }
+}
+
+void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev,
+                       unsigned long long* metrics, cudaStream_t st) {
+  static bool init[64] = {};  // reciprocal table in constant memory, set once per device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !init[dev]) {
+    float h[9] = {0}, l[9] = {0};
+    for (int n = 1; n <= 8; ++n) {
+      const ff v(1.0 / n);
+      h[n] = v.hi;
+      l[n] = v.lo;
+    }
+    cudaMemcpyToSymbol(c_inv_hi, h, sizeof(h));
+    cudaMemcpyToSymbol(c_inv_lo, l, sizeof(l));
+    init[dev] = true;
+  }
+  dim3 grid((unsigned)((L.ncp[0] + 127) / 128), (unsigned)L.ncp[1], (unsigned)L.ncp[2]);
+  k_average_ff<<<grid, 128, 0, st>>>(L, offL, X, P, Pprev, metrics);
+}
+
+}  // namespace mfa

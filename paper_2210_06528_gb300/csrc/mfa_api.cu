@@ -51,7 +51,7 @@ struct mfa_model {
   int nsub = 1;
   long long sizeL = 0, sizeS1 = 0, sizeS2 = 0;
   int maxL = 0, maxU = 0, maxS1 = 0, maxS2 = 0;
-  int maxm[3] = {0, 0, 0}, maxnL[3] = {0, 0, 0};  // largest window points / L per axis
+  int maxm[3] = {0, 0, 0}, maxnL[3] = {0, 0, 0}, maxnU[3] = {0, 0, 0};  // largest window points / L / U per axis
   int maxOut[3] = {0, 0, 0};      // projection stage output sizes
   int maxApply[3] = {0, 0, 0};    // band-apply output sizes
   int maxFibL[3] = {0, 0, 0};     // fibres per solve, L boxes
@@ -355,6 +355,7 @@ void build_ops(mfa_model* md, std::vector<AxisOp>& ops, std::vector<long long>& 
     for (int a = 0; a < 3; ++a) {
       md->maxm[a] = std::max(md->maxm[a], m[a]);
       md->maxnL[a] = std::max(md->maxnL[a], nL[a]);
+      md->maxnU[a] = std::max(md->maxnU[a], nU[a]);
     }
     md->maxU = std::max(md->maxU, nU[0] * nU[1] * nU[2]);
     auto at = [&](int kind) -> AxisOp& { return ops[(size_t)kind * ns + s]; };
@@ -484,6 +485,12 @@ void run_encode(mfa_model* md, const TQ* q) {
   for (int a = 0; a < md->dim; ++a)
     TRACED(h, TR_SOLVE_L, launch_band_solve<T>(L, a, false, opsk(OP_SOLVEL0 + a), ns, md->maxFibL[a], X, h->stream));
   cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
+  if constexpr (std::is_same<T, ff>::value) {
+    if (md->use_fused) {
+      TRACED(h, TR_AVERAGE, launch_average_ff(L, md->offL, X, (ff*)md->P, nullptr, h->d_metrics, h->stream));
+      return;
+    }
+  }
   TRACED(h, TR_AVERAGE, launch_average<T>(L, md->offL, X, (T*)md->P, nullptr, h->d_metrics, h->stream));
 }
 
@@ -497,6 +504,21 @@ void run_step(mfa_model* md) {
   T* S2 = (T*)md->S2;
   auto opsk = [&](int kind) { return md->ops + (size_t)kind * ns; };
   std::swap(md->P, md->Pprev);  // Pprev <- P^{k-1}
+  if constexpr (std::is_same<T, ff>::value) {
+    if (md->dim == 3 && md->use_fused) {
+      bool fused = false;
+      TRACED(h, TR_SOLVE_U,
+             fused = launch_schwarz3d_ff(L, md->offL, md->maxnL, md->maxnU, (const ff*)md->Pprev, (const ff*)md->BL,
+                                         (ff*)md->X, h->stream));
+      if (fused) {
+        cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
+        TRACED(h, TR_AVERAGE,
+               launch_average_ff(L, md->offL, (const ff*)md->X, (ff*)md->P, (const ff*)md->Pprev, h->d_metrics,
+                                 h->stream));
+        return;
+      }
+    }
+  }
   TRACED(h, TR_FRAME_GATHER, launch_frame_gather<T>(L, md->offS2, md->maxL, (const T*)md->Pprev, S2, h->stream));
   for (int a = 0; a < md->dim; ++a) {
     const T* in = (a % 2 == 0) ? S2 : S1;

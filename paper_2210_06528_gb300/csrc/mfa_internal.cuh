@@ -125,6 +125,10 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
 template <typename V, typename TQ, typename TOut, bool RESID>
 bool launch_decode3d(const LayoutDev& L, const V* P, const TQ* Q, TOut* out, double* partials, cudaStream_t st);
 long long decode3d_tiles(const LayoutDev& L);
+bool launch_schwarz3d_ff(const LayoutDev& L, const long long* offL, const int* maxnL, const int* maxnU, const ff* P,
+                         const ff* BL, ff* X, cudaStream_t st);
+void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev,
+                       unsigned long long* metrics, cudaStream_t st);
 
 constexpr int kResidualBlocks = 1216;  // 8 x 152 SMs
 
