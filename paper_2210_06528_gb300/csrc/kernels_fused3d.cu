@@ -143,6 +143,7 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
   for (int z0 = 0; z0 < m2; z0 += zb) {
     const int nz = min(zb, m2 - z0);
     // ---- stage 1: one data row per thread, read straight from global memory
+    // with an 8-deep register prefetch ring
     for (int t = threadIdx.x; t < nz * m1; t += NT) {
       const int zz = t / m1, y = t - zz * m1;
       const TQ* q = qwin + M01 * (z0 + zz) + M0 * y;
@@ -151,19 +152,39 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
 #pragma unroll
       for (int r = 0; r < W; ++r) win[r] = ff(0.f, 0.f);
       int cur = spx[0];
-      for (int k = 0; k < m0; ++k) {
-        const float x = to_f<TQ>(__ldg(q + k));
-        bad |= !isfinite(x);
-        const int sk = spx[k];
-        while (cur < sk) {
-          if (cur >= 0 && cur < n0) o[cur] = AccFF::finish(win[0]);
+      constexpr int D = 8;
+      float buf[D];
 #pragma unroll
-          for (int r = 0; r < P; ++r) win[r] = win[r + 1];
-          win[P] = ff(0.f, 0.f);
-          ++cur;
+      for (int j = 0; j < D; ++j) buf[j] = j < m0 ? to_f<TQ>(__ldg(q + j)) : 0.f;
+      for (int kb = 0; kb < m0; kb += D) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          const int k = kb + j;
+          if (k < m0) {
+            const float x = buf[j];
+            if (k + D < m0) buf[j] = to_f<TQ>(__ldg(q + k + D));
+            bad |= !isfinite(x);
+            const int sk = spx[k];
+            while (cur < sk) {
+              if (cur >= 0 && cur < n0) o[cur] = AccFF::finish(win[0]);
+#pragma unroll
+              for (int r = 0; r < P; ++r) win[r] = win[r + 1];
+              win[P] = ff(0.f, 0.f);
+              ++cur;
+            }
+            if constexpr (W == 4) {
+              const float4 nh = reinterpret_cast<const float4*>(bxh)[k];
+              const float4 nl = reinterpret_cast<const float4*>(bxl)[k];
+              AccFF::add_f(win[0], nh.x, nl.x, x);
+              AccFF::add_f(win[1], nh.y, nl.y, x);
+              AccFF::add_f(win[2], nh.z, nl.z, x);
+              AccFF::add_f(win[3], nh.w, nl.w, x);
+            } else {
+#pragma unroll
+              for (int r = 0; r < W; ++r) AccFF::add_f(win[r], bxh[k * W + r], bxl[k * W + r], x);
+            }
+          }
         }
-#pragma unroll
-        for (int r = 0; r < W; ++r) AccFF::add_f(win[r], bxh[k * W + r], bxl[k * W + r], x);
       }
 #pragma unroll
       for (int r = 0; r < W; ++r)
@@ -874,31 +895,28 @@ bool launch_schwarz3d_ff(const LayoutDev& L, const long long* offL, const int* m
 
 __constant__ float c_inv_hi[9], c_inv_lo[9];  // 1/n as float-float, n = 1..8
 
-__device__ __forceinline__ void atomic_max_f(unsigned long long* addr, float v) {
-  atomicMax(addr, (unsigned long long)__double_as_longlong((double)v));
-}
-
 __global__ void __launch_bounds__(128) k_average_ff(LayoutDev L, const long long* __restrict__ offL,
                                                     const ff* __restrict__ X, ff* __restrict__ P,
-                                                    const ff* __restrict__ Pprev, unsigned long long* metrics) {
+                                                    const ff* __restrict__ Pprev, float* __restrict__ part) {
   const int g0 = blockIdx.x * blockDim.x + threadIdx.x;
   const int g1 = blockIdx.y, g2 = blockIdx.z;
   float dmax = 0.f, pmax = 0.f, spread = 0.f;
   if (g0 < (int)L.ncp[0]) {
-    const int f0 = L.ax[0].own_first[g0], c0n = L.ax[0].own_count[g0];
-    const int f1 = L.ax[1].own_first[g1], c1n = L.ax[1].own_count[g1];
-    const int f2 = L.ax[2].own_first[g2], c2n = L.ax[2].own_count[g2];
+    const int4 o0 = L.ax[0].own_tab[g0], o1 = L.ax[1].own_tab[g1], o2 = L.ax[2].own_tab[g2];
+    const int sa0[2] = {o0.x, o0.z}, li0[2] = {o0.y, o0.w};
+    const int sa1[2] = {o1.x, o1.z}, li1[2] = {o1.y, o1.w};
+    const int sa2[2] = {o2.x, o2.z}, li2[2] = {o2.y, o2.w};
+    const int c0n = o0.z < 0 ? 1 : 2, c1n = o1.z < 0 ? 1 : 2, c2n = o2.z < 0 ? 1 : 2;
     ff sum(0.f, 0.f), first(0.f, 0.f);
     float dlo = 0.f, dhi = 0.f;
     int cnt = 0;
     for (int c2 = 0; c2 < c2n; ++c2) {
-      const AxisSub b2 = L.ax[2].subs[f2 + c2];
       for (int c1 = 0; c1 < c1n; ++c1) {
-        const AxisSub b1 = L.ax[1].subs[f1 + c1];
+        const int nL1 = L.ax[1].nL_tab[sa1[c1]];
         for (int c0 = 0; c0 < c0n; ++c0) {
-          const AxisSub b0 = L.ax[0].subs[f0 + c0];
-          const int s = (f0 + c0) + L.S[0] * ((f1 + c1) + L.S[1] * (f2 + c2));
-          const int li = (g0 - b0.l0) + b0.nL * ((g1 - b1.l0) + b1.nL * (g2 - b2.l0));
+          const int nL0 = L.ax[0].nL_tab[sa0[c0]];
+          const int s = sa0[c0] + L.S[0] * (sa1[c1] + L.S[1] * sa2[c2]);
+          const int li = li0[c0] + nL0 * (li1[c1] + nL1 * li2[c2]);
           const ff v = X[offL[s] + li];
           sum = sum + v;
           if (cnt == 0) {
@@ -943,13 +961,54 @@ __global__ void __launch_bounds__(128) k_average_ff(LayoutDev L, const long long
       b = fmaxf(b, red[1][w]);
       c = fmaxf(c, red[2][w]);
     }
-    atomic_max_f(&metrics[0], a);
-    atomic_max_f(&metrics[1], b);
-    atomic_max_f(&metrics[2], c);
+    const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+    part[3 * blk + 0] = a;
+    part[3 * blk + 1] = b;
+    part[3 * blk + 2] = c;
   }
 }
 
-void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev,
+// Maxima of the per-block metric partials into metrics[0..2] (bit patterns of
+// non-negative doubles, the same format the host reads).
+__global__ void k_metrics_reduce(const float* __restrict__ part, long long nblk, unsigned long long* metrics) {
+  float a = 0.f, b = 0.f, c = 0.f;
+  for (long long i = threadIdx.x; i < nblk; i += blockDim.x) {
+    a = fmaxf(a, part[3 * i]);
+    b = fmaxf(b, part[3 * i + 1]);
+    c = fmaxf(c, part[3 * i + 2]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmaxf(a, __shfl_down_sync(0xffffffffu, a, o));
+    b = fmaxf(b, __shfl_down_sync(0xffffffffu, b, o));
+    c = fmaxf(c, __shfl_down_sync(0xffffffffu, c, o));
+  }
+  __shared__ float red[3][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = a;
+    red[1][wid] = b;
+    red[2][wid] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      a = fmaxf(a, red[0][w]);
+      b = fmaxf(b, red[1][w]);
+      c = fmaxf(c, red[2][w]);
+    }
+    a = fmaxf(a, red[0][0]);
+    b = fmaxf(b, red[1][0]);
+    c = fmaxf(c, red[2][0]);
+    metrics[0] = (unsigned long long)__double_as_longlong((double)a);
+    metrics[1] = (unsigned long long)__double_as_longlong((double)b);
+    metrics[2] = (unsigned long long)__double_as_longlong((double)c);
+  }
+}
+
+long long average_ff_blocks(const LayoutDev& L) { return ((L.ncp[0] + 127) / 128) * L.ncp[1] * L.ncp[2]; }
+
+// `part` holds 3 floats per block of the launch (average_ff_blocks).
+void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev, float* part,
                        unsigned long long* metrics, cudaStream_t st) {
   static bool init[64] = {};  // reciprocal table in constant memory, set once per device
   int dev = 0;
@@ -966,7 +1025,129 @@ void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, f
     init[dev] = true;
   }
   dim3 grid((unsigned)((L.ncp[0] + 127) / 128), (unsigned)L.ncp[1], (unsigned)L.ncp[2]);
-  k_average_ff<<<grid, 128, 0, st>>>(L, offL, X, P, Pprev, metrics);
+  k_average_ff<<<grid, 128, 0, st>>>(L, offL, X, P, Pprev, part);
+  k_metrics_reduce<<<1, 1024, 0, st>>>(part, average_ff_blocks(L), metrics);
+}
+
+}  // namespace mfa
+
+namespace mfa {
+
+// ---------------------------------------------------------------------------
+// Iteration 0 (Algorithm 1: decoupled unconstrained local solves):
+// X_s = (A_L,0 x A_L,1 x A_L,2)^{-1} B_L in float-float.  Pass 1 solves the x
+// and y fibres of one z-plane of one subdomain in shared memory; pass 2 solves
+// the z fibres in place, one fibre per thread (coalesced across x).
+// ---------------------------------------------------------------------------
+
+template <int P>
+__global__ void __launch_bounds__(128) k_iter0_xy_ff(LayoutDev L, const long long* __restrict__ offL,
+                                                     const ff* __restrict__ BL, ff* __restrict__ X) {
+  constexpr int W = P + 1;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int s = blockIdx.x, lz = blockIdx.y;
+  const int s0 = s % L.S[0], s1 = (s / L.S[0]) % L.S[1], s2 = s / (L.S[0] * L.S[1]);
+  const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];
+  if (lz >= bz.nL) return;
+  const int nL0 = bx.nL, nL1 = by.nL;
+  float* fxh = reinterpret_cast<float*>(smem);
+  float* fxl = fxh + nL0 * W;
+  float* fyh = fxl + nL0 * W;
+  float* fyl = fyh + nL1 * W;
+  size_t off = (size_t)2 * W * (nL0 + nL1) * 4;
+  off = (off + 15) & ~size_t(15);
+  ff* T = reinterpret_cast<ff*>(smem + off);  // [nL1][nL0]
+  const ff* Fx = L.ax[0].facL_ff + (long long)bx.bandL * W;
+  const ff* Fy = L.ax[1].facL_ff + (long long)by.bandL * W;
+  for (int i = threadIdx.x; i < nL0 * W; i += blockDim.x) {
+    fxh[i] = Fx[i].hi;
+    fxl[i] = Fx[i].lo;
+  }
+  for (int i = threadIdx.x; i < nL1 * W; i += blockDim.x) {
+    fyh[i] = Fy[i].hi;
+    fyl[i] = Fy[i].lo;
+  }
+  const long long base = offL[s] + (long long)lz * nL0 * nL1;
+  for (int i = threadIdx.x; i < nL0 * nL1; i += blockDim.x) T[i] = BL[base + i];
+  __syncthreads();
+  for (int f = threadIdx.x; f < nL1; f += blockDim.x) solve_fibre_ff<P>(T + f * nL0, nL0, 1, fxh, fxl);
+  __syncthreads();
+  for (int f = threadIdx.x; f < nL0; f += blockDim.x) solve_fibre_ff<P>(T + f, nL1, nL0, fyh, fyl);
+  __syncthreads();
+  for (int i = threadIdx.x; i < nL0 * nL1; i += blockDim.x) X[base + i] = T[i];
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_iter0_z_ff(LayoutDev L, const long long* __restrict__ offL,
+                                                    ff* __restrict__ X) {
+  constexpr int W = P + 1;
+  const int s = blockIdx.y;
+  const int s0 = s % L.S[0], s1 = (s / L.S[0]) % L.S[1], s2 = s / (L.S[0] * L.S[1]);
+  const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];
+  const int nf = bx.nL * by.nL;
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= nf) return;
+  const int n = bz.nL;
+  const long long st = nf;
+  ff* x = X + offL[s] + f;
+  const ff* F = L.ax[2].facL_ff + (long long)bz.bandL * W;
+  ff win[P];  // the last P solved values, win[0] the most recent
+#pragma unroll
+  for (int e = 0; e < P; ++e) win[e] = ff(0.f, 0.f);
+  for (int i = 0; i < n; ++i) {
+    ff acc = x[i * st];
+#pragma unroll
+    for (int e = 1; e <= P; ++e)
+      if (i - e >= 0) {
+        const ff Fe = F[i * W + e];
+        AccFF::add_v(acc, -Fe.hi, -Fe.lo, win[e - 1]);
+      }
+    const ff y = AccFF::finish(acc) * F[i * W];
+    x[i * st] = y;
+#pragma unroll
+    for (int e = P - 1; e > 0; --e) win[e] = win[e - 1];
+    win[0] = y;
+  }
+#pragma unroll
+  for (int e = 0; e < P; ++e) win[e] = ff(0.f, 0.f);
+  for (int i = n - 1; i >= 0; --i) {
+    ff acc = x[i * st];
+#pragma unroll
+    for (int e = 1; e <= P; ++e)
+      if (i + e < n) {
+        const ff Fe = F[(i + e) * W + e];
+        AccFF::add_v(acc, -Fe.hi, -Fe.lo, win[e - 1]);
+      }
+    const ff v = AccFF::finish(acc) * F[i * W];
+    x[i * st] = v;
+#pragma unroll
+    for (int e = P - 1; e > 0; --e) win[e] = win[e - 1];
+    win[0] = v;
+  }
+}
+
+// Returns the number of kernels launched (0 when not covered).
+int launch_iter0_3d_ff(const LayoutDev& L, const long long* offL, const int* maxnL, const ff* BL, ff* X,
+                       cudaStream_t st) {
+  const int p = L.ax[0].p;
+  if (L.dim != 3 || L.ax[1].p != p || L.ax[2].p != p) return 0;
+  const size_t smem = (((size_t)2 * (p + 1) * (maxnL[0] + maxnL[1]) * 4 + 15) & ~size_t(15)) +
+                      (size_t)maxnL[0] * maxnL[1] * sizeof(ff);
+  if (smem > 200 * 1024) return 0;
+  dim3 g1(L.nsub, maxnL[2]);
+  dim3 g2((maxnL[0] * maxnL[1] + 127) / 128, L.nsub);
+  auto go = [&](auto kxy, auto kz) {
+    cudaFuncSetAttribute(kxy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kxy<<<g1, 128, smem, st>>>(L, offL, BL, X);
+    kz<<<g2, 128, 0, st>>>(L, offL, X);
+  };
+  switch (p) {
+    case 2: go(k_iter0_xy_ff<2>, k_iter0_z_ff<2>); return 2;
+    case 3: go(k_iter0_xy_ff<3>, k_iter0_z_ff<3>); return 2;
+    case 4: go(k_iter0_xy_ff<4>, k_iter0_z_ff<4>); return 2;
+    case 5: go(k_iter0_xy_ff<5>, k_iter0_z_ff<5>); return 2;
+    default: return 0;
+  }
 }
 
 }  // namespace mfa

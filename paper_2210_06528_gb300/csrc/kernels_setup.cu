@@ -155,3 +155,160 @@ void launch_chol(const AxisDev& ax, const double* AL, double* fLd, float* fLf, f
 }
 
 }  // namespace mfa
+
+namespace mfa {
+
+// ---------------------------------------------------------------------------
+// Batched setup: one launch evaluates the basis of every axis; one launch
+// assembles the Gram band of every piece of every axis (one CTA per piece,
+// one thread per band entry) and factors it in shared memory.
+// ---------------------------------------------------------------------------
+
+struct SetupArgs {
+  AxisDev ax[3];
+  int naxes;
+  int* span[3];
+  double* vd[3];
+  float* vf[3];
+  ff* vff[3];
+  double* AL[3];
+  double *fLd[3], *fUd[3];
+  float *fLf[3], *fUf[3];
+  ff *fLff[3], *fUff[3];
+};
+
+__global__ void k_basis_all(SetupArgs A) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  int a = 0;
+  while (a < A.naxes && k >= A.ax[a].M) {
+    k -= A.ax[a].M;
+    ++a;
+  }
+  if (a >= A.naxes) return;
+  const AxisDev& ax = A.ax[a];
+  const int M = ax.M, nspans = ax.nspans, p = ax.p;
+  int j = 0;
+  double u = 0.0;
+  if (M > 1) {
+    j = (int)(((long long)k * nspans) / (M - 1));
+    if (j > nspans - 1) j = nspans - 1;
+    u = (double)k / (double)(M - 1);
+  }
+  double N[MFA_MAX_DEGREE + 1];
+  cox_de_boor(j, u, p, nspans, N);
+  A.span[a][k] = j;
+  for (int r = 0; r <= p; ++r) {
+    A.vd[a][(long long)k * (p + 1) + r] = N[r];
+    A.vf[a][(long long)k * (p + 1) + r] = (float)N[r];
+    A.vff[a][(long long)k * (p + 1) + r] = ff(N[r]);
+  }
+}
+
+// Banded Cholesky of the n x n block of A (upper band storage, row stride w)
+// starting at row o; writes the factor (1/L(i,i) at [i*w], L(i,i-e) at
+// [i*w+e]) in FP64, FP32 and float-float.  Same recurrence as band_cholesky.
+__device__ void band_cholesky_smem(const double* A, int o, int n, int p, double* F, double* Fd, float* Ff, ff* Fff,
+                                   int* status) {
+  const int w = p + 1;
+  for (int i = 0; i < n; ++i) {
+    for (int e = p; e >= 1; --e) {
+      const int j = i - e;
+      if (j < 0) continue;
+      double s = A[(o + j) * w + e];
+      for (int f = e + 1; f <= p; ++f) {
+        if (i - f < 0) continue;
+        s -= F[i * w + f] * F[j * w + (f - e)];
+      }
+      F[i * w + e] = s * F[j * w];
+    }
+    const double aii = A[(o + i) * w];
+    double dsum = aii;
+    for (int e = 1; e <= p; ++e)
+      if (i - e >= 0) dsum -= F[i * w + e] * F[i * w + e];
+    if (!(dsum > 1e-13 * aii) || !(aii > 0.0)) {
+      atomicExch(status, MFA_ERR_NOT_SPD);
+      dsum = 1.0;
+    }
+    F[i * w] = 1.0 / sqrt(dsum);
+  }
+  for (int i = 0; i < n * w; ++i) {
+    Fd[i] = F[i];
+    Ff[i] = (float)F[i];
+    Fff[i] = ff(F[i]);
+  }
+}
+
+__global__ void k_gram_chol_all(SetupArgs A, int* status) {
+  extern __shared__ double sh[];
+  int b = blockIdx.x, a = 0;
+  while (a < A.naxes && b >= A.ax[a].S) {
+    b -= A.ax[a].S;
+    ++a;
+  }
+  if (a >= A.naxes) return;
+  const AxisDev& ax = A.ax[a];
+  const AxisSub sb = ax.subs[b];
+  const int p = ax.p, w = p + 1, nL = sb.nL;
+  double* As = sh;            // [nL][w]
+  double* F = sh + nL * w;    // [nL][w] scratch factor
+  // A(l, l+e) = sum over window points of N_g N_{g+e}, g = l0 + l, on spans [g+e-p, g]
+  for (int t = threadIdx.x; t < nL * w; t += blockDim.x) {
+    const int l = t / w, e = t - l * w;
+    const int g = sb.l0 + l;
+    double acc = 0.0;
+    if (l + e < nL) {
+      const int jlo = max(g + e - p, 0), jhi = min(g, ax.nspans - 1);
+      if (jlo <= jhi) {
+        int kb = ax.span_start[jlo], ke = ax.span_start[jhi + 1];
+        kb = max(kb, sb.k0);
+        ke = min(ke, sb.k0 + sb.m);
+        for (int k = kb; k < ke; ++k) {
+          const int r = g - ax.span[k];
+          const double* v = A.vd[a] + (long long)k * w;
+          acc += v[r] * v[r + e];
+        }
+      }
+    }
+    As[t] = acc;
+    A.AL[a][(long long)sb.bandL * w + t] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    band_cholesky_smem(As, 0, nL, p, F, A.fLd[a] + (long long)sb.bandL * w, A.fLf[a] + (long long)sb.bandL * w,
+                       A.fLff[a] + (long long)sb.bandL * w, status);
+  } else if (threadIdx.x == 32) {
+    // the owned block needs its own scratch: reuse the upper half of F's space
+    double* FU = F + (size_t)nL * w;
+    band_cholesky_smem(As, sb.oU, sb.nU, p, FU, A.fUd[a] + (long long)sb.bandU * w, A.fUf[a] + (long long)sb.bandU * w,
+                       A.fUff[a] + (long long)sb.bandU * w, status);
+  }
+}
+
+void launch_setup_all(const AxisDev* ax, int naxes, int maxnL, int* status, cudaStream_t st) {
+  SetupArgs A{};
+  A.naxes = naxes;
+  int totalM = 0, totalS = 0, maxw = 1;
+  for (int a = 0; a < naxes; ++a) {
+    A.ax[a] = ax[a];
+    A.span[a] = const_cast<int*>(ax[a].span);
+    A.vd[a] = const_cast<double*>(ax[a].vals_d);
+    A.vf[a] = const_cast<float*>(ax[a].vals_f);
+    A.vff[a] = const_cast<ff*>(ax[a].vals_ff);
+    A.AL[a] = const_cast<double*>(ax[a].AL);
+    A.fLd[a] = const_cast<double*>(ax[a].facL_d);
+    A.fLf[a] = const_cast<float*>(ax[a].facL_f);
+    A.fLff[a] = const_cast<ff*>(ax[a].facL_ff);
+    A.fUd[a] = const_cast<double*>(ax[a].facU_d);
+    A.fUf[a] = const_cast<float*>(ax[a].facU_f);
+    A.fUff[a] = const_cast<ff*>(ax[a].facU_ff);
+    totalM += ax[a].M;
+    totalS += ax[a].S;
+    maxw = ax[a].p + 1 > maxw ? ax[a].p + 1 : maxw;
+  }
+  k_basis_all<<<(totalM + 127) / 128, 128, 0, st>>>(A);
+  // shared: Gram band, L-factor and U-factor scratch of the largest piece
+  const size_t smem = (size_t)3 * maxnL * maxw * sizeof(double);
+  k_gram_chol_all<<<totalS, 128, smem, st>>>(A, status);
+}
+
+}  // namespace mfa

@@ -63,6 +63,7 @@ struct mfa_model {
   AxisOp* ops = nullptr;  // [kOpKinds][nsub]
   // big buffers
   void *BL = nullptr, *X = nullptr, *P = nullptr, *Pprev = nullptr, *S1 = nullptr, *S2 = nullptr;
+  float* part = nullptr;  // per-block metric partials of the float-float average
   bool use_fused = true;  // fused 3-D kernels where they cover the layout
   int iters = 0;
   int grow_streak = 0;
@@ -172,8 +173,8 @@ int trace_begin(mfa_handle* h) {
   return i;
 }
 
-void trace_end(mfa_handle* h, int cls, int i) {
-  h->trace_n[cls]++;
+void trace_end(mfa_handle* h, int cls, int i, int nlaunch = 1) {
+  h->trace_n[cls] += nlaunch;
   if (i < 0) return;
   cudaEventRecord(h->ev[i + 1], h->stream);
   h->pending.push_back({cls, i});
@@ -185,6 +186,14 @@ void trace_end(mfa_handle* h, int cls, int i) {
     const int _ti = trace_begin(h); \
     stmt;                           \
     trace_end(h, cls, _ti);         \
+  } while (0)
+
+// same, for a call that launches `n` kernels
+#define TRACED_N(h, cls, n, stmt)     \
+  do {                                \
+    const int _ti = trace_begin(h);   \
+    stmt;                             \
+    trace_end(h, cls, _ti, (n));      \
   } while (0)
 
 // ---------------------------------------------------------------------------
@@ -289,6 +298,18 @@ int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int
   }
   for (int g = 0; g < ax.n; ++g)
     if (ax.own_count[g] < 1 || ax.own_count[g] > 2) return MFA_ERR_LAYOUT;
+  ax.own_tab.assign(ax.n, int4{0, 0, -1, 0});
+  for (int g = 0; g < ax.n; ++g) {
+    const int f = ax.own_first[g];
+    ax.own_tab[g].x = f;
+    ax.own_tab[g].y = g - ax.subs[f].l0;
+    if (ax.own_count[g] == 2) {
+      ax.own_tab[g].z = f + 1;
+      ax.own_tab[g].w = g - ax.subs[f + 1].l0;
+    }
+  }
+  ax.nL_tab.resize(nsub);
+  for (int s = 0; s < nsub; ++s) ax.nL_tab[s] = ax.subs[s].nL;
   // first data point of every span (span of point k = floor(k nspans / (M-1)), capped)
   ax.span_start.assign(nspans + 1, (int)M);
   int j = 0;
@@ -481,13 +502,22 @@ void run_encode(mfa_model* md, const TQ* q) {
                                     h->stream)));
   }
   // iteration 0: unconstrained local solves on the L boxes
-  cudaMemcpyAsync(X, BL, md->sizeL * sizeof(T), cudaMemcpyDeviceToDevice, h->stream);
-  for (int a = 0; a < md->dim; ++a)
+  int it0 = 0;
+  if constexpr (std::is_same<T, ff>::value) {
+    if (md->dim == 3 && md->use_fused) {
+      const int _ti = trace_begin(h);
+      it0 = launch_iter0_3d_ff(L, md->offL, md->maxnL, BL, X, h->stream);
+      trace_end(h, TR_SOLVE_L, _ti, it0);
+    }
+  }
+  if (!it0) cudaMemcpyAsync(X, BL, md->sizeL * sizeof(T), cudaMemcpyDeviceToDevice, h->stream);
+  for (int a = 0; a < md->dim && !it0; ++a)
     TRACED(h, TR_SOLVE_L, launch_band_solve<T>(L, a, false, opsk(OP_SOLVEL0 + a), ns, md->maxFibL[a], X, h->stream));
   cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
   if constexpr (std::is_same<T, ff>::value) {
     if (md->use_fused) {
-      TRACED(h, TR_AVERAGE, launch_average_ff(L, md->offL, X, (ff*)md->P, nullptr, h->d_metrics, h->stream));
+      TRACED_N(h, TR_AVERAGE, 2,
+               launch_average_ff(L, md->offL, X, (ff*)md->P, nullptr, md->part, h->d_metrics, h->stream));
       return;
     }
   }
@@ -511,10 +541,9 @@ void run_step(mfa_model* md) {
              fused = launch_schwarz3d_ff(L, md->offL, md->maxnL, md->maxnU, (const ff*)md->Pprev, (const ff*)md->BL,
                                          (ff*)md->X, h->stream));
       if (fused) {
-        cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
-        TRACED(h, TR_AVERAGE,
-               launch_average_ff(L, md->offL, (const ff*)md->X, (ff*)md->P, (const ff*)md->Pprev, h->d_metrics,
-                                 h->stream));
+        TRACED_N(h, TR_AVERAGE, 2,
+                 launch_average_ff(L, md->offL, (const ff*)md->X, (ff*)md->P, (const ff*)md->Pprev, md->part,
+                                   h->d_metrics, h->stream));
         return;
       }
     }
@@ -741,7 +770,7 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
   // ---- device tables in one arena
   Arena ar;
   size_t o_span[3], o_vd[3], o_vf[3], o_vff[3], o_ss[3], o_subs[3], o_of[3], o_oc[3], o_AL[3], o_fLd[3], o_fLf[3],
-      o_fLff[3], o_fUd[3], o_fUf[3], o_fUff[3];
+      o_fLff[3], o_fUd[3], o_fUf[3], o_fUff[3], o_ot[3], o_nlt[3];
   for (int a = 0; a < 3; ++a) {
     const AxisHost& ax = md->axh[a];
     const int w = ax.p + 1;
@@ -753,6 +782,8 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
     o_subs[a] = ar.take<AxisSub>(ax.S);
     o_of[a] = ar.take<int>(ax.n);
     o_oc[a] = ar.take<int>(ax.n);
+    o_ot[a] = ar.take<int4>(ax.n);
+    o_nlt[a] = ar.take<int>(ax.S);
     o_AL[a] = ar.take<double>((size_t)ax.bandL_rows * w);
     o_fLd[a] = ar.take<double>((size_t)ax.bandL_rows * w);
     o_fLf[a] = ar.take<float>((size_t)ax.bandL_rows * w);
@@ -772,6 +803,8 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
     std::memcpy(img.data() + o_subs[a], ax.subs.data(), sizeof(AxisSub) * ax.subs.size());
     std::memcpy(img.data() + o_of[a], ax.own_first.data(), sizeof(int) * ax.n);
     std::memcpy(img.data() + o_oc[a], ax.own_count.data(), sizeof(int) * ax.n);
+    std::memcpy(img.data() + o_ot[a], ax.own_tab.data(), sizeof(int4) * ax.n);
+    std::memcpy(img.data() + o_nlt[a], ax.nL_tab.data(), sizeof(int) * ax.S);
   }
   std::memcpy(img.data() + o_offL, offL.data(), sizeof(long long) * ns);
   std::memcpy(img.data() + o_offS1, offS1.data(), sizeof(long long) * ns);
@@ -784,6 +817,7 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
   const long long ncp = (long long)md->axh[0].n * md->axh[1].n * md->axh[2].n;
   const size_t o_P = bg.take<char>(ncp * es), o_Pp = bg.take<char>(ncp * es);
   const size_t o_S1 = bg.take<char>(md->sizeS1 * es), o_S2 = bg.take<char>(md->sizeS2 * es);
+  const size_t o_part = bg.take<float>(3 * (size_t)(((md->axh[0].n + 127) / 128) * md->axh[1].n * md->axh[2].n));
   // host data staging: the data are copied into the pool before use
   const size_t qbytes = (size_t)npts_total * (q_dtype == MFA_F64 ? 8 : 4);
   const size_t o_Q = q_on_device ? 0 : bg.take<char>(qbytes);
@@ -819,6 +853,8 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
     d.subs = at_off<AxisSub>(md->arena, o_subs[a]);
     d.own_first = at_off<int>(md->arena, o_of[a]);
     d.own_count = at_off<int>(md->arena, o_oc[a]);
+    d.own_tab = at_off<int4>(md->arena, o_ot[a]);
+    d.nL_tab = at_off<int>(md->arena, o_nlt[a]);
     d.AL = at_off<double>(md->arena, o_AL[a]);
     d.facL_d = at_off<double>(md->arena, o_fLd[a]);
     d.facL_f = at_off<float>(md->arena, o_fLf[a]);
@@ -837,20 +873,13 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
   md->Pprev = at_off<char>(md->big, o_Pp);
   md->S1 = at_off<char>(md->big, o_S1);
   md->S2 = at_off<char>(md->big, o_S2);
-  // setup kernels: basis tables, Gram bands, Cholesky factors (FP64)
-  for (int a = 0; a < 3; ++a) {
-    AxisDev& d = L.ax[a];
-    TRACED(h, TR_SETUP,
-           launch_basis(d, const_cast<int*>(d.span), const_cast<double*>(d.vals_d), const_cast<float*>(d.vals_f),
-                        const_cast<ff*>(d.vals_ff), h->stream));
+  md->part = at_off<float>(md->big, o_part);
+  // setup kernels: basis tables, Gram bands, Cholesky factors (FP64), all axes per launch
+  {
+    int maxnL = 1;
+    for (int a = 0; a < 3; ++a) maxnL = std::max(maxnL, md->maxnL[a]);
+    TRACED_N(h, TR_SETUP, 2, launch_setup_all(L.ax, 3, maxnL, h->d_status, h->stream));
   }
-  for (int a = 0; a < 3; ++a) TRACED(h, TR_SETUP, launch_gram(L.ax[a], const_cast<double*>(L.ax[a].AL), h->stream));
-  for (int a = 0; a < 3; ++a)
-    TRACED(h, TR_SETUP,
-           launch_chol(L.ax[a], L.ax[a].AL, const_cast<double*>(L.ax[a].facL_d), const_cast<float*>(L.ax[a].facL_f),
-                       const_cast<ff*>(L.ax[a].facL_ff), const_cast<double*>(L.ax[a].facU_d),
-                       const_cast<float*>(L.ax[a].facU_f), const_cast<ff*>(L.ax[a].facU_ff), h->d_status,
-                       h->stream));
   const void* qd = q;
   if (!q_on_device) {
     // host data: copy and wait, so the caller may reuse its buffer on return

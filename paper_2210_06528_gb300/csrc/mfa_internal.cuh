@@ -37,6 +37,8 @@ struct AxisDev {
   const AxisSub* subs;      // [S]
   const int* own_first;     // [n] first subdomain-axis index owning CP g
   const int* own_count;     // [n] number of owners (1 or 2)
+  const int4* own_tab;      // [n] {first owner, g - l0 in it, second owner or -1, g - l0 in it}
+  const int* nL_tab;        // [S] L size of every piece
   const double* AL;         // Gram band rows of every piece, upper storage: A(i, i+e) at [i*(p+1)+e]
   const double* facL_d;     // Cholesky band of A_L: [i*(p+1)] = 1/L(i,i), [i*(p+1)+e] = L(i,i-e)
   const float* facL_f;
@@ -76,7 +78,8 @@ struct AxisOp {
 struct AxisHost {
   int M = 1, nspans = 1, p = 0, n = 1, S = 1;
   std::vector<AxisSub> subs;
-  std::vector<int> own_first, own_count, span_start;
+  std::vector<int> own_first, own_count, span_start, nL_tab;
+  std::vector<int4> own_tab;
   int bandL_rows = 0, bandU_rows = 0;
 };
 
@@ -85,6 +88,7 @@ struct AxisHost {
 // ---------------------------------------------------------------------------
 void launch_basis(const AxisDev& ax, int* span, double* vd, float* vf, ff* vff, cudaStream_t st);
 void launch_gram(const AxisDev& ax, double* AL, cudaStream_t st);
+void launch_setup_all(const AxisDev* ax, int naxes, int maxnL, int* status, cudaStream_t st);
 void launch_chol(const AxisDev& ax, const double* AL, double* fLd, float* fLf, ff* fLff, double* fUd, float* fUf,
                  ff* fUff, int* status, cudaStream_t st);
 
@@ -127,7 +131,10 @@ bool launch_decode3d(const LayoutDev& L, const V* P, const TQ* Q, TOut* out, dou
 long long decode3d_tiles(const LayoutDev& L);
 bool launch_schwarz3d_ff(const LayoutDev& L, const long long* offL, const int* maxnL, const int* maxnU, const ff* P,
                          const ff* BL, ff* X, cudaStream_t st);
-void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev,
+int launch_iter0_3d_ff(const LayoutDev& L, const long long* offL, const int* maxnL, const ff* BL, ff* X,
+                       cudaStream_t st);
+long long average_ff_blocks(const LayoutDev& L);
+void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev, float* part,
                        unsigned long long* metrics, cudaStream_t st);
 
 constexpr int kResidualBlocks = 1216;  // 8 x 152 SMs
