@@ -604,20 +604,22 @@ template bool launch_decode3d<ff, float, double, false>(const LayoutDev&, const 
 namespace mfa {
 
 // ---------------------------------------------------------------------------
-// Schwarz step k >= 1 in defect-correction form (Sec. 2.3.2; the Schur
-// decoupling of Eq. global-system):
-//   r_s   = B_U - A_L[U, :] P^{k-1}|_L      (residual of the local normal equations)
-//   c_s   = (A_U,0 x A_U,1 x A_U,2)^{-1} r_s (banded Cholesky solves)
-//   X_s   = P^{k-1}|_U + c_s
-// which equals A_U^{-1} (B_U - A_L[U, F] P_F) because A_L[U, U] = A_U.  All
-// of it runs in float-float.
+// Schwarz step k >= 1 as iterative refinement of every subdomain's own copy
+// (Sec. 2.3.2; the Schur decoupling of Eq. global-system):
+//   Z_s   = (X_s^{k-1} on U, P^{k-1} on the frame F)     the local spline
+//   r_s   = B_U - A_L[U, :] Z_s                          float-float residual
+//   X_s^k = X_s^{k-1} + (A_U,0 x A_U,1 x A_U,2)^{-1} r_s  FP32 correction
+// In exact arithmetic X_s^k = A_U^{-1} (B_U - A_L[U, F] P_F^{k-1}), the
+// constrained local solve.  The residual is taken against the subdomain's own
+// previous copy, so it vanishes as the iteration converges and the FP32
+// correction leaves no rounding floor (mixed-precision iterative refinement).
 //
-// One CTA per subdomain: the L box of P^{k-1} streams through shared memory
-// plane by plane along z (the next plane is fetched into registers while the
-// current one is processed); per plane the x and y band products run in
-// shared memory and the z band product accumulates in a register ring of 2P+1
-// owned z-points per owned (x, y) pair.  The residual box stays in shared
-// memory for the three fibre solves.
+// One CTA per subdomain: Z_s streams through shared memory plane by plane
+// along z (the next plane is fetched into registers while the current one is
+// processed); per plane the x and y band products run in shared memory and the
+// z band product accumulates in a register ring of 2P+1 owned z-points per
+// owned (x, y) pair.  The residual box (FP32) stays in shared memory for the
+// three fibre solves.
 // ---------------------------------------------------------------------------
 
 struct Step3dArgs {
@@ -641,18 +643,29 @@ __device__ __forceinline__ void load_band_rows(const AxisDev& ax, const AxisSub&
   }
 }
 
+// In-place FP32 banded Cholesky solve of one fibre: L y = c, L^T x = y.
+// F rows hold 1/L(i,i) at [i*W] and L(i,i-e) at [i*W+e].
 template <int P>
-__device__ __forceinline__ void load_factor(const AxisDev& ax, const AxisSub& b, float* h, float* l) {
+__device__ __forceinline__ void solve_fibre(float* x, int n, int s, const float* F) {
   constexpr int W = P + 1;
-  const ff* F = ax.facU_ff + (long long)b.bandU * W;
-  for (int i = threadIdx.x; i < b.nU * W; i += blockDim.x) {
-    h[i] = F[i].hi;
-    l[i] = F[i].lo;
+  for (int i = 0; i < n; ++i) {
+    float acc = x[i * s];
+#pragma unroll
+    for (int e = 1; e <= P; ++e)
+      if (i - e >= 0) acc = fmaf(-F[i * W + e], x[(i - e) * s], acc);
+    x[i * s] = acc * F[i * W];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    float acc = x[i * s];
+#pragma unroll
+    for (int e = 1; e <= P; ++e)
+      if (i + e < n) acc = fmaf(-F[(i + e) * W + e], x[(i + e) * s], acc);
+    x[i * s] = acc * F[i * W];
   }
 }
 
-// In-place banded Cholesky solve of one fibre in float-float: L y = c, L^T x = y.
-// F rows hold 1/L(i,i) at [i*W] and L(i,i-e) at [i*W+e].
+// The same solve in float-float (iteration 0 uses it on the ill-conditioned
+// window blocks).
 template <int P>
 __device__ __forceinline__ void solve_fibre_ff(ff* x, int n, int s, const float* Fh, const float* Fl) {
   constexpr int W = P + 1;
@@ -673,7 +686,7 @@ __device__ __forceinline__ void solve_fibre_ff(ff* x, int n, int s, const float*
 }
 
 template <int P, int NT, int NPAIR, int NPRE>
-__global__ void __launch_bounds__(NT, 1) k_schwarz3d_ff(Step3dArgs A, const ff* __restrict__ Pg,
+__global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* __restrict__ Pg,
                                                          const ff* __restrict__ BL, ff* __restrict__ X) {
   constexpr int W = P + 1, B = 2 * P + 1;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -692,13 +705,10 @@ __global__ void __launch_bounds__(NT, 1) k_schwarz3d_ff(Step3dArgs A, const ff* 
   float* ayl = ayh + nU1 * B;
   float* azh = ayl + nU1 * B;                    // [nU2][B]
   float* azl = azh + nU2 * B;
-  float* fxh = azl + nU2 * B;                    // [nU][W] factors of A_U per axis
-  float* fxl = fxh + nU0 * W;
-  float* fyh = fxl + nU0 * W;
-  float* fyl = fyh + nU1 * W;
-  float* fzh = fyl + nU1 * W;
-  float* fzl = fzh + nU2 * W;
-  size_t off = (size_t)(2 * B * (nU0 + nU1 + nU2) + 2 * W * (nU0 + nU1 + nU2)) * 4;
+  float* fx = azl + nU2 * B;                     // [nU][W] FP32 factors of A_U per axis
+  float* fy = fx + nU0 * W;
+  float* fz = fy + nU1 * W;
+  size_t off = (size_t)(2 * B * (nU0 + nU1 + nU2) + W * (nU0 + nU1 + nU2)) * 4;
   off = (off + 15) & ~size_t(15);
   ff* Pp = reinterpret_cast<ff*>(smem + off);    // [nL1][nL0]
   off += (size_t)nL1 * nL0 * sizeof(ff);
@@ -706,14 +716,14 @@ __global__ void __launch_bounds__(NT, 1) k_schwarz3d_ff(Step3dArgs A, const ff* 
   off += (size_t)nL1 * nU0 * sizeof(ff);
   ff* Y2 = reinterpret_cast<ff*>(smem + off);    // [nU1][nU0]
   off += (size_t)nU1 * nU0 * sizeof(ff);
-  ff* R = reinterpret_cast<ff*>(smem + off);     // [nU2][nU1][nU0]
+  float* R = reinterpret_cast<float*>(smem + off);  // [nU2][nU1][nU0]
 
   load_band_rows<P>(L.ax[0], bx, axh, axl);
   load_band_rows<P>(L.ax[1], by, ayh, ayl);
   load_band_rows<P>(L.ax[2], bz, azh, azl);
-  load_factor<P>(L.ax[0], bx, fxh, fxl);
-  load_factor<P>(L.ax[1], by, fyh, fyl);
-  load_factor<P>(L.ax[2], bz, fzh, fzl);
+  for (int i = threadIdx.x; i < nU0 * W; i += NT) fx[i] = L.ax[0].facU_f[(long long)bx.bandU * W + i];
+  for (int i = threadIdx.x; i < nU1 * W; i += NT) fy[i] = L.ax[1].facU_f[(long long)by.bandU * W + i];
+  for (int i = threadIdx.x; i < nU2 * W; i += NT) fz[i] = L.ax[2].facU_f[(long long)bz.bandU * W + i];
 
   const int npairs = nU0 * nU1;
   const int nplane = nL1 * nL0;
@@ -723,18 +733,21 @@ __global__ void __launch_bounds__(NT, 1) k_schwarz3d_ff(Step3dArgs A, const ff* 
 #pragma unroll
     for (int j = 0; j < B; ++j) ring[i][j] = ff(0.f, 0.f);
   const ff* bl = BL + A.offL[s];
+  ff* xs = X + A.offL[s];
   const ff* pg = Pg + (long long)bx.l0 + n0 * by.l0 + n01 * bz.l0;
 
   // planes that reach an owned z-point through the band
   const int lz_lo = max(0, oU2 - P), lz_hi = min(nL2 - 1, oU2 + nU2 - 1 + P);
   ff pre[NPRE];
   auto fetch = [&](int lz) {
+    const bool zin = lz >= oU2 && lz < oU2 + nU2;
 #pragma unroll
     for (int k = 0; k < NPRE; ++k) {
       const int i = threadIdx.x + k * NT;
       if (i < nplane) {
         const int ly = i / nL0, lx = i - ly * nL0;
-        pre[k] = pg[lx + n0 * ly + n01 * lz];
+        const bool own = zin && ly >= oU1 && ly < oU1 + nU1 && lx >= oU0 && lx < oU0 + nU0;
+        pre[k] = own ? xs[(long long)lz * nplane + i] : pg[lx + n0 * ly + n01 * lz];
       }
     }
   };
@@ -785,11 +798,12 @@ __global__ void __launch_bounds__(NT, 1) k_schwarz3d_ff(Step3dArgs A, const ff* 
           const int uz = uzb + j;
           if (uz >= 0 && uz < nU2) AccFF::add_v(ring[i][j], azh[uz * B + (2 * P - j)], azl[uz * B + (2 * P - j)], y2);
         }
-        // slot 0 is complete: residual r = B_U - (A x A x A) P
+        // slot 0 is complete: residual r = B_U - (A x A x A) Z
         if (uzb >= 0 && uzb < nU2) {
           const int ux = q % nU0, uy = q / nU0;
           const ff b = bl[(oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uzb))];
-          R[(uzb * nU1 + uy) * nU0 + ux] = b - AccFF::finish(ring[i][0]);
+          const ff r = b - AccFF::finish(ring[i][0]);
+          R[(uzb * nU1 + uy) * nU0 + ux] = r.hi + r.lo;
         }
       }
 #pragma unroll
@@ -811,44 +825,44 @@ __global__ void __launch_bounds__(NT, 1) k_schwarz3d_ff(Step3dArgs A, const ff* 
         const int uz = uzb + j;
         if (uz >= 0 && uz < nU2) {
           const ff b = bl[(oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uz))];
-          R[(uz * nU1 + uy) * nU0 + ux] = b - AccFF::finish(ring[i][j]);
+          const ff r = b - AccFF::finish(ring[i][j]);
+          R[(uz * nU1 + uy) * nU0 + ux] = r.hi + r.lo;
         }
       }
     }
   }
   __syncthreads();
-  // correction c = A_U^{-1} r, one fibre per thread and axis
-  for (int f = threadIdx.x; f < nU1 * nU2; f += NT) solve_fibre_ff<P>(R + f * nU0, nU0, 1, fxh, fxl);
+  // correction c = A_U^{-1} r in FP32, one fibre per thread and axis
+  for (int f = threadIdx.x; f < nU1 * nU2; f += NT) solve_fibre<P>(R + f * nU0, nU0, 1, fx);
   __syncthreads();
   for (int f = threadIdx.x; f < nU0 * nU2; f += NT) {
     const int ux = f % nU0, uz = f / nU0;
-    solve_fibre_ff<P>(R + uz * nU1 * nU0 + ux, nU1, nU0, fyh, fyl);
+    solve_fibre<P>(R + uz * nU1 * nU0 + ux, nU1, nU0, fy);
   }
   __syncthreads();
-  for (int f = threadIdx.x; f < nU0 * nU1; f += NT) solve_fibre_ff<P>(R + f, nU2, nU0 * nU1, fzh, fzl);
+  for (int f = threadIdx.x; f < nU0 * nU1; f += NT) solve_fibre<P>(R + f, nU2, nU0 * nU1, fz);
   __syncthreads();
-  // owned copy X_s = P^{k-1}|_U + c_s
-  ff* xo = X + A.offL[s];
+  // refined copy X_s^k = X_s^{k-1} + c_s
   const int nUall = nU0 * nU1 * nU2;
   for (int i = threadIdx.x; i < nUall; i += NT) {
     const int ux = i % nU0, r2 = i / nU0;
     const int uy = r2 % nU1, uz = r2 / nU1;
-    const ff pv = pg[(oU0 + ux) + n0 * (oU1 + uy) + n01 * (oU2 + uz)];
-    xo[(oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uz))] = pv + R[i];
+    const long long li = (oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uz));
+    xs[li] = xs[li] + ff(R[i]);
   }
 }
 
 template <int P>
 size_t step3d_smem(int nL0, int nL1, int nU0, int nU1, int nU2) {
   constexpr int W = P + 1, B = 2 * P + 1;
-  size_t off = (size_t)(2 * B * (nU0 + nU1 + nU2) + 2 * W * (nU0 + nU1 + nU2)) * 4;
+  size_t off = (size_t)(2 * B * (nU0 + nU1 + nU2) + W * (nU0 + nU1 + nU2)) * 4;
   off = (off + 15) & ~size_t(15);
   off += (size_t)nL1 * nL0 * sizeof(ff) + (size_t)nL1 * nU0 * sizeof(ff) + (size_t)nU1 * nU0 * sizeof(ff);
-  off += (size_t)nU0 * nU1 * nU2 * sizeof(ff);
+  off += (size_t)nU0 * nU1 * nU2 * sizeof(float);
   return off;
 }
 
-constexpr int kStepThreads = 512;
+constexpr int kStepThreads = 256;
 
 bool launch_schwarz3d_ff(const LayoutDev& L, const long long* offL, const int* maxnL, const int* maxnU, const ff* P,
                          const ff* BL, ff* X, cudaStream_t st) {
@@ -859,7 +873,7 @@ bool launch_schwarz3d_ff(const LayoutDev& L, const long long* offL, const int* m
   A.offL = offL;
   const int npairs = maxnU[0] * maxnU[1];
   const int nplane = maxnL[0] * maxnL[1];
-  if (npairs > 2 * kStepThreads || nplane > 4 * kStepThreads) return false;
+  if (npairs > 3 * kStepThreads || nplane > 4 * kStepThreads) return false;
   auto go = [&](auto kernel, size_t sm) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -869,10 +883,7 @@ bool launch_schwarz3d_ff(const LayoutDev& L, const long long* offL, const int* m
   case PP: {                                                                                   \
     const size_t sm = step3d_smem<PP>(maxnL[0], maxnL[1], maxnU[0], maxnU[1], maxnU[2]);       \
     if (sm > 220 * 1024) return false;                                                         \
-    if (nplane <= 2 * kStepThreads)                                                            \
-      go(k_schwarz3d_ff<PP, kStepThreads, 2, 2>, sm);                                          \
-    else                                                                                       \
-      go(k_schwarz3d_ff<PP, kStepThreads, 2, 4>, sm);                                          \
+    go(k_schwarz3d_ff<PP, kStepThreads, 3, 4>, sm);                                            \
     return true;                                                                               \
   }
   switch (p) {
@@ -903,25 +914,28 @@ __global__ void __launch_bounds__(128) k_average_ff(LayoutDev L, const long long
   float dmax = 0.f, pmax = 0.f, spread = 0.f;
   if (g0 < (int)L.ncp[0]) {
     const int4 o0 = L.ax[0].own_tab[g0], o1 = L.ax[1].own_tab[g1], o2 = L.ax[2].own_tab[g2];
-    const int sa0[2] = {o0.x, o0.z}, li0[2] = {o0.y, o0.w};
-    const int sa1[2] = {o1.x, o1.z}, li1[2] = {o1.y, o1.w};
-    const int sa2[2] = {o2.x, o2.z}, li2[2] = {o2.y, o2.w};
-    const int c0n = o0.z < 0 ? 1 : 2, c1n = o1.z < 0 ? 1 : 2, c2n = o2.z < 0 ? 1 : 2;
     ff sum(0.f, 0.f), first(0.f, 0.f);
     float dlo = 0.f, dhi = 0.f;
     int cnt = 0;
-    for (int c2 = 0; c2 < c2n; ++c2) {
-      for (int c1 = 0; c1 < c1n; ++c1) {
-        const int nL1 = L.ax[1].nL_tab[sa1[c1]];
-        for (int c0 = 0; c0 < c0n; ++c0) {
-          const int nL0 = L.ax[0].nL_tab[sa0[c0]];
-          const int s = sa0[c0] + L.S[0] * (sa1[c1] + L.S[1] * sa2[c2]);
-          const int li = li0[c0] + nL0 * (li1[c1] + nL1 * li2[c2]);
+#pragma unroll
+    for (int c2 = 0; c2 < 2; ++c2) {
+      const int sa2 = c2 ? o2.z : o2.x, li2 = c2 ? o2.w : o2.y;
+#pragma unroll
+      for (int c1 = 0; c1 < 2; ++c1) {
+        const int sa1 = c1 ? o1.z : o1.x, li1 = c1 ? o1.w : o1.y;
+#pragma unroll
+        for (int c0 = 0; c0 < 2; ++c0) {
+          const int sa0 = c0 ? o0.z : o0.x, li0 = c0 ? o0.w : o0.y;
+          if (sa0 < 0 || sa1 < 0 || sa2 < 0) continue;
+          const int nL0 = L.ax[0].nL_tab[sa0], nL1 = L.ax[1].nL_tab[sa1];
+          const int s = sa0 + L.S[0] * (sa1 + L.S[1] * sa2);
+          const int li = li0 + nL0 * (li1 + nL1 * li2);
           const ff v = X[offL[s] + li];
-          sum = sum + v;
           if (cnt == 0) {
+            sum = v;
             first = v;
           } else {
+            sum = sum + v;
             const ff d = v - first;
             const float df = d.hi + d.lo;
             dlo = fminf(dlo, df);
@@ -969,10 +983,11 @@ __global__ void __launch_bounds__(128) k_average_ff(LayoutDev L, const long long
 }
 
 // Maxima of the per-block metric partials into metrics[0..2] (bit patterns of
-// non-negative doubles, the same format the host reads).
+// non-negative doubles, the same format the host reads; metrics must start at
+// zero).  A few hundred blocks, one atomic per block and metric.
 __global__ void k_metrics_reduce(const float* __restrict__ part, long long nblk, unsigned long long* metrics) {
   float a = 0.f, b = 0.f, c = 0.f;
-  for (long long i = threadIdx.x; i < nblk; i += blockDim.x) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nblk; i += (long long)gridDim.x * blockDim.x) {
     a = fmaxf(a, part[3 * i]);
     b = fmaxf(b, part[3 * i + 1]);
     c = fmaxf(c, part[3 * i + 2]);
@@ -982,7 +997,7 @@ __global__ void k_metrics_reduce(const float* __restrict__ part, long long nblk,
     b = fmaxf(b, __shfl_down_sync(0xffffffffu, b, o));
     c = fmaxf(c, __shfl_down_sync(0xffffffffu, c, o));
   }
-  __shared__ float red[3][32];
+  __shared__ float red[3][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     red[0][wid] = a;
@@ -999,9 +1014,9 @@ __global__ void k_metrics_reduce(const float* __restrict__ part, long long nblk,
     a = fmaxf(a, red[0][0]);
     b = fmaxf(b, red[1][0]);
     c = fmaxf(c, red[2][0]);
-    metrics[0] = (unsigned long long)__double_as_longlong((double)a);
-    metrics[1] = (unsigned long long)__double_as_longlong((double)b);
-    metrics[2] = (unsigned long long)__double_as_longlong((double)c);
+    atomicMax(&metrics[0], (unsigned long long)__double_as_longlong((double)a));
+    atomicMax(&metrics[1], (unsigned long long)__double_as_longlong((double)b));
+    atomicMax(&metrics[2], (unsigned long long)__double_as_longlong((double)c));
   }
 }
 
@@ -1026,7 +1041,8 @@ void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, f
   }
   dim3 grid((unsigned)((L.ncp[0] + 127) / 128), (unsigned)L.ncp[1], (unsigned)L.ncp[2]);
   k_average_ff<<<grid, 128, 0, st>>>(L, offL, X, P, Pprev, part);
-  k_metrics_reduce<<<1, 1024, 0, st>>>(part, average_ff_blocks(L), metrics);
+  cudaMemsetAsync(metrics, 0, 3 * sizeof(unsigned long long), st);
+  k_metrics_reduce<<<152, 256, 0, st>>>(part, average_ff_blocks(L), metrics);
 }
 
 }  // namespace mfa
@@ -1040,15 +1056,18 @@ namespace mfa {
 // the z fibres in place, one fibre per thread (coalesced across x).
 // ---------------------------------------------------------------------------
 
+constexpr int kIt0Planes = 4;
+
 template <int P>
 __global__ void __launch_bounds__(128) k_iter0_xy_ff(LayoutDev L, const long long* __restrict__ offL,
                                                      const ff* __restrict__ BL, ff* __restrict__ X) {
   constexpr int W = P + 1;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int s = blockIdx.x, lz = blockIdx.y;
+  const int s = blockIdx.x, lz0 = blockIdx.y * kIt0Planes;
   const int s0 = s % L.S[0], s1 = (s / L.S[0]) % L.S[1], s2 = s / (L.S[0] * L.S[1]);
   const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];
-  if (lz >= bz.nL) return;
+  if (lz0 >= bz.nL) return;
+  const int npl = min(kIt0Planes, bz.nL - lz0);
   const int nL0 = bx.nL, nL1 = by.nL;
   float* fxh = reinterpret_cast<float*>(smem);
   float* fxl = fxh + nL0 * W;
@@ -1056,7 +1075,7 @@ __global__ void __launch_bounds__(128) k_iter0_xy_ff(LayoutDev L, const long lon
   float* fyl = fyh + nL1 * W;
   size_t off = (size_t)2 * W * (nL0 + nL1) * 4;
   off = (off + 15) & ~size_t(15);
-  ff* T = reinterpret_cast<ff*>(smem + off);  // [nL1][nL0]
+  ff* T = reinterpret_cast<ff*>(smem + off);  // [npl][nL1][nL0]
   const ff* Fx = L.ax[0].facL_ff + (long long)bx.bandL * W;
   const ff* Fy = L.ax[1].facL_ff + (long long)by.bandL * W;
   for (int i = threadIdx.x; i < nL0 * W; i += blockDim.x) {
@@ -1067,14 +1086,18 @@ __global__ void __launch_bounds__(128) k_iter0_xy_ff(LayoutDev L, const long lon
     fyh[i] = Fy[i].hi;
     fyl[i] = Fy[i].lo;
   }
-  const long long base = offL[s] + (long long)lz * nL0 * nL1;
-  for (int i = threadIdx.x; i < nL0 * nL1; i += blockDim.x) T[i] = BL[base + i];
+  const int npp = nL0 * nL1;
+  const long long base = offL[s] + (long long)lz0 * npp;
+  for (int i = threadIdx.x; i < npl * npp; i += blockDim.x) T[i] = BL[base + i];
   __syncthreads();
-  for (int f = threadIdx.x; f < nL1; f += blockDim.x) solve_fibre_ff<P>(T + f * nL0, nL0, 1, fxh, fxl);
+  for (int f = threadIdx.x; f < npl * nL1; f += blockDim.x) solve_fibre_ff<P>(T + f * nL0, nL0, 1, fxh, fxl);
   __syncthreads();
-  for (int f = threadIdx.x; f < nL0; f += blockDim.x) solve_fibre_ff<P>(T + f, nL1, nL0, fyh, fyl);
+  for (int f = threadIdx.x; f < npl * nL0; f += blockDim.x) {
+    const int pl = f / nL0, x = f - pl * nL0;
+    solve_fibre_ff<P>(T + pl * npp + x, nL1, nL0, fyh, fyl);
+  }
   __syncthreads();
-  for (int i = threadIdx.x; i < nL0 * nL1; i += blockDim.x) X[base + i] = T[i];
+  for (int i = threadIdx.x; i < npl * npp; i += blockDim.x) X[base + i] = T[i];
 }
 
 template <int P>
@@ -1132,9 +1155,9 @@ int launch_iter0_3d_ff(const LayoutDev& L, const long long* offL, const int* max
   const int p = L.ax[0].p;
   if (L.dim != 3 || L.ax[1].p != p || L.ax[2].p != p) return 0;
   const size_t smem = (((size_t)2 * (p + 1) * (maxnL[0] + maxnL[1]) * 4 + 15) & ~size_t(15)) +
-                      (size_t)maxnL[0] * maxnL[1] * sizeof(ff);
+                      (size_t)kIt0Planes * maxnL[0] * maxnL[1] * sizeof(ff);
   if (smem > 200 * 1024) return 0;
-  dim3 g1(L.nsub, maxnL[2]);
+  dim3 g1(L.nsub, (maxnL[2] + kIt0Planes - 1) / kIt0Planes);
   dim3 g2((maxnL[0] * maxnL[1] + 127) / 128, L.nsub);
   auto go = [&](auto kxy, auto kz) {
     cudaFuncSetAttribute(kxy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
