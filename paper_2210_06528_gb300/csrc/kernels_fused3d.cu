@@ -74,7 +74,35 @@ struct Proj3dArgs {
   const long long* offL;
   int zb;     // planes per batch
   int nch2;   // y-chunks per column in stage 2
+  int ldq;    // row pitch (floats) of the staged data, odd
 };
+
+__device__ __forceinline__ void cp_async_f32(float* dst, const float* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Stage planes z0 .. z0+nz-1 of the window into Qs [nz][m1][ldq] with
+// coalesced copies: each warp copies whole rows, lanes along x.
+template <typename TQ>
+__device__ __forceinline__ void stage_planes(float* Qs, const TQ* qwin, long long M0, long long M01, int z0, int nz,
+                                             int m0, int m1, int ldq) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int row = warp; row < nz * m1; row += nwarp) {
+    const int zz = row / m1, y = row - zz * m1;
+    const TQ* src = qwin + M01 * (z0 + zz) + M0 * y;
+    float* dst = Qs + row * ldq;
+    for (int x = lane; x < m0; x += 32) {
+      if constexpr (sizeof(TQ) == 4)
+        cp_async_f32(dst + x, reinterpret_cast<const float*>(src) + x);
+      else
+        dst[x] = (float)src[x];
+    }
+  }
+  cp_async_commit();
+}
 
 template <int P, int NT, int NPAIR, typename TQ>
 __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* __restrict__ Q, ff* __restrict__ BL,
@@ -87,11 +115,13 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
   const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];
   const int m0 = bx.m, m1 = by.m, m2 = bz.m;
   const int n0 = bx.nL, n1 = by.nL, n2 = bz.nL;
-  const int zb = A.zb;
+  const int zb = A.zb, ldq = A.ldq;
   const long long M0 = L.M[0], M01 = L.M[0] * L.M[1];
 
-  // shared: basis x and y as hi/lo rows of W values, local spans, stage-1 and
-  // stage-2 outputs of the current batch of planes
+  // shared: basis x and y as hi/lo rows of W values, local spans, staged data
+  // rows (overwritten in place by the stage-1 output: control point c of a row
+  // lands on floats 2c, 2c+1, behind every point still to be read when there
+  // are at least two points per span), stage-2 output
   float* bxh = reinterpret_cast<float*>(smem);     // [m0][W]
   float* bxl = bxh + m0 * W;                        // [m0][W]
   float* byh = bxl + m0 * W;                        // [m1][W]
@@ -100,8 +130,9 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
   int* spy = spx + m0;                              // [m1]
   size_t off = (size_t)(2 * W * (m0 + m1)) * 4 + (size_t)(m0 + m1) * 4;
   off = (off + 15) & ~size_t(15);
-  ff* T1 = reinterpret_cast<ff*>(smem + off);       // [zb][m1][n0]
-  off += (size_t)zb * m1 * n0 * sizeof(ff);
+  float* Qs = reinterpret_cast<float*>(smem + off);  // [zb][m1][ldq]; row t's stage-1 output as ff at Qs + t*ldq
+  off += (size_t)zb * m1 * ldq * 4;
+  off = (off + 15) & ~size_t(15);
   ff* T2 = reinterpret_cast<ff*>(smem + off);       // [zb][n1][n0]
 
   const ff* vx = L.ax[0].vals_ff;
@@ -138,57 +169,54 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
   int curz = L.ax[2].span[bz.k0] - bz.l0;  // z-control point held in ring slot 0
   bool bad = false;
   const TQ* qwin = Q + (long long)bx.k0 + M0 * by.k0 + M01 * bz.k0;
-  __syncthreads();
+  stage_planes<TQ>(Qs, qwin, M0, M01, 0, min(zb, m2), m0, m1, ldq);
 
   for (int z0 = 0; z0 < m2; z0 += zb) {
     const int nz = min(zb, m2 - z0);
-    // ---- stage 1: one data row per thread, read straight from global memory
-    // with an 8-deep register prefetch ring
+    cp_async_wait_all();
+    __syncthreads();
+    // ---- stage 1: one staged row per thread, sliding window of P+1
+    // accumulators; the output overwrites the consumed part of the row
     for (int t = threadIdx.x; t < nz * m1; t += NT) {
-      const int zz = t / m1, y = t - zz * m1;
-      const TQ* q = qwin + M01 * (z0 + zz) + M0 * y;
-      ff* o = T1 + t * n0;
+      const float* q = Qs + t * ldq;
+      float* o = Qs + t * ldq;  // output of control point c at o[2c] (hi), o[2c+1] (lo); 4-byte aligned only
       ff win[W];
 #pragma unroll
       for (int r = 0; r < W; ++r) win[r] = ff(0.f, 0.f);
       int cur = spx[0];
-      constexpr int D = 8;
-      float buf[D];
-#pragma unroll
-      for (int j = 0; j < D; ++j) buf[j] = j < m0 ? to_f<TQ>(__ldg(q + j)) : 0.f;
-      for (int kb = 0; kb < m0; kb += D) {
-#pragma unroll
-        for (int j = 0; j < D; ++j) {
-          const int k = kb + j;
-          if (k < m0) {
-            const float x = buf[j];
-            if (k + D < m0) buf[j] = to_f<TQ>(__ldg(q + k + D));
-            bad |= !isfinite(x);
-            const int sk = spx[k];
-            while (cur < sk) {
-              if (cur >= 0 && cur < n0) o[cur] = AccFF::finish(win[0]);
-#pragma unroll
-              for (int r = 0; r < P; ++r) win[r] = win[r + 1];
-              win[P] = ff(0.f, 0.f);
-              ++cur;
-            }
-            if constexpr (W == 4) {
-              const float4 nh = reinterpret_cast<const float4*>(bxh)[k];
-              const float4 nl = reinterpret_cast<const float4*>(bxl)[k];
-              AccFF::add_f(win[0], nh.x, nl.x, x);
-              AccFF::add_f(win[1], nh.y, nl.y, x);
-              AccFF::add_f(win[2], nh.z, nl.z, x);
-              AccFF::add_f(win[3], nh.w, nl.w, x);
-            } else {
-#pragma unroll
-              for (int r = 0; r < W; ++r) AccFF::add_f(win[r], bxh[k * W + r], bxl[k * W + r], x);
-            }
+      for (int k = 0; k < m0; ++k) {
+        const float x = q[k];
+        const int sk = spx[k];
+        while (cur < sk) {
+          if (cur >= 0 && cur < n0) {
+            const ff v = AccFF::finish(win[0]);
+            o[2 * cur] = v.hi;
+            o[2 * cur + 1] = v.lo;
           }
+#pragma unroll
+          for (int r = 0; r < P; ++r) win[r] = win[r + 1];
+          win[P] = ff(0.f, 0.f);
+          ++cur;
+        }
+        if constexpr (W == 4) {
+          const float4 nh = reinterpret_cast<const float4*>(bxh)[k];
+          const float4 nl = reinterpret_cast<const float4*>(bxl)[k];
+          AccFF::add_f(win[0], nh.x, nl.x, x);
+          AccFF::add_f(win[1], nh.y, nl.y, x);
+          AccFF::add_f(win[2], nh.z, nl.z, x);
+          AccFF::add_f(win[3], nh.w, nl.w, x);
+        } else {
+#pragma unroll
+          for (int r = 0; r < W; ++r) AccFF::add_f(win[r], bxh[k * W + r], bxl[k * W + r], x);
         }
       }
 #pragma unroll
       for (int r = 0; r < W; ++r)
-        if (cur + r >= 0 && cur + r < n0) o[cur + r] = AccFF::finish(win[r]);
+        if (cur + r >= 0 && cur + r < n0) {
+          const ff v = AccFF::finish(win[r]);
+          o[2 * (cur + r)] = v.hi;
+          o[2 * (cur + r) + 1] = v.lo;
+        }
     }
     __syncthreads();
     // ---- stage 2: columns along y, chunked over the y-control points
@@ -205,7 +233,7 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
         // rows whose span reaches control points [c0, c1): span in [c0-P, c1-1]
         const int gs0 = max(by.l0 + c0 - P, 0), gs1 = min(by.l0 + c1, L.ax[1].nspans);
         const int y0 = max(ss[gs0] - by.k0, 0), y1 = min(ss[gs1] - by.k0, m1);
-        const ff* col = T1 + zz * m1 * n0 + lx;
+        const float* colf = Qs + zz * m1 * ldq + 2 * lx;
         ff* o = T2 + zz * n1 * n0 + lx;
         ff win[W];
 #pragma unroll
@@ -220,7 +248,7 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
             win[P] = ff(0.f, 0.f);
             ++cur;
           }
-          const ff x = col[y * n0];
+          const ff x(colf[y * ldq], colf[y * ldq + 1]);
 #pragma unroll
           for (int r = 0; r < W; ++r) AccFF::add_v(win[r], byh[y * W + r], byl[y * W + r], x);
         }
@@ -230,6 +258,8 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
       }
     }
     __syncthreads();
+    // the staged rows are free again: fetch the next batch behind stage 3
+    if (z0 + zb < m2) stage_planes<TQ>(Qs, qwin, M0, M01, z0 + zb, min(zb, m2 - z0 - zb), m0, m1, ldq);
     // ---- stage 3: accumulate the planes into the z ring
     for (int zz = 0; zz < nz; ++zz) {
       const int kz = bz.k0 + z0 + zz;
@@ -238,7 +268,11 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
 #pragma unroll
         for (int i = 0; i < NPAIR; ++i) {
           const int q = threadIdx.x + i * NT;
-          if (q < npairs && curz >= 0 && curz < n2) out[(long long)curz * npairs + q] = AccFF::finish(ring[i][0]);
+          if (q < npairs && curz >= 0 && curz < n2) {
+            const ff v = AccFF::finish(ring[i][0]);
+            bad |= !isfinite(v.hi);
+            out[(long long)curz * npairs + q] = v;
+          }
 #pragma unroll
           for (int r = 0; r < P; ++r) ring[i][r] = ring[i][r + 1];
           ring[i][P] = ff(0.f, 0.f);
@@ -263,25 +297,28 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
         }
       }
     }
-    __syncthreads();
   }
 #pragma unroll
   for (int i = 0; i < NPAIR; ++i) {
     const int q = threadIdx.x + i * NT;
 #pragma unroll
     for (int r = 0; r < W; ++r)
-      if (q < npairs && curz + r >= 0 && curz + r < n2)
-        out[(long long)(curz + r) * npairs + q] = AccFF::finish(ring[i][r]);
+      if (q < npairs && curz + r >= 0 && curz + r < n2) {
+        const ff v = AccFF::finish(ring[i][r]);
+        bad |= !isfinite(v.hi);
+        out[(long long)(curz + r) * npairs + q] = v;
+      }
   }
   if (bad && status) atomicExch(status, MFA_ERR_NONFINITE);
 }
 
 template <int P>
-size_t proj3d_smem(int m0, int m1, int n0, int n1, int zb) {
+size_t proj3d_smem(int m0, int m1, int n0, int n1, int zb, int ldq) {
   constexpr int W = P + 1;
   size_t off = (size_t)(2 * W * (m0 + m1)) * 4 + (size_t)(m0 + m1) * 4;
   off = (off + 15) & ~size_t(15);
-  off += (size_t)zb * m1 * n0 * sizeof(ff);
+  off += (size_t)zb * m1 * ldq * 4;
+  off = (off + 15) & ~size_t(15);
   off += (size_t)zb * n1 * n0 * sizeof(ff);
   return off;
 }
@@ -289,16 +326,19 @@ size_t proj3d_smem(int m0, int m1, int n0, int n1, int zb) {
 constexpr int kProjThreads = 256;
 
 // Returns false when the fused kernel does not cover this layout (the caller
-// then runs the generic per-axis kernels).
+// then runs the generic per-axis kernels).  `inplace_ok` says every x-window
+// has at least two points per span, so the stage-1 output can overwrite the
+// consumed data in place.
 template <typename TQ>
 bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, int maxm1, int maxn0, int maxn1,
-                         const TQ* Q, ff* BL, int* status, cudaStream_t st) {
+                         bool inplace_ok, const TQ* Q, ff* BL, int* status, cudaStream_t st) {
   const int P = L.ax[0].p;
-  if (L.dim != 3 || L.ax[1].p != P || L.ax[2].p != P) return false;
+  if (L.dim != 3 || L.ax[1].p != P || L.ax[2].p != P || !inplace_ok) return false;
   const int npairs = maxn0 * maxn1;
   Proj3dArgs A;
   A.L = L;
   A.offL = offL;
+  A.ldq = std::max(maxm0, 2 * maxn0 + 1) | 1;
   // planes per batch: fill the stage-1 rows onto the threads
   A.zb = std::max(1, std::min(4, kProjThreads / std::max(maxm1, 1)));
   size_t smem = 0;
@@ -310,10 +350,10 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
   };
 #define MFA_PROJ_CASE(PP)                                                  \
   case PP: {                                                               \
-    smem = proj3d_smem<PP>(maxm0, maxm1, maxn0, maxn1, A.zb);              \
+    smem = proj3d_smem<PP>(maxm0, maxm1, maxn0, maxn1, A.zb, A.ldq);       \
     while (smem > 110 * 1024 && A.zb > 1) {                                \
       A.zb--;                                                              \
-      smem = proj3d_smem<PP>(maxm0, maxm1, maxn0, maxn1, A.zb);            \
+      smem = proj3d_smem<PP>(maxm0, maxm1, maxn0, maxn1, A.zb, A.ldq);     \
     }                                                                      \
     if (smem > 200 * 1024) return false;                                   \
     if (npairs <= 4 * kProjThreads)                                        \
@@ -335,10 +375,10 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
 #undef MFA_PROJ_CASE
 }
 
-template bool launch_project3d_ff<float>(const LayoutDev&, const long long*, int, int, int, int, const float*, ff*,
-                                         int*, cudaStream_t);
-template bool launch_project3d_ff<double>(const LayoutDev&, const long long*, int, int, int, int, const double*, ff*,
-                                          int*, cudaStream_t);
+template bool launch_project3d_ff<float>(const LayoutDev&, const long long*, int, int, int, int, bool, const float*,
+                                         ff*, int*, cudaStream_t);
+template bool launch_project3d_ff<double>(const LayoutDev&, const long long*, int, int, int, int, bool, const double*,
+                                          ff*, int*, cudaStream_t);
 
 }  // namespace mfa
 

@@ -64,7 +64,8 @@ struct mfa_model {
   // big buffers
   void *BL = nullptr, *X = nullptr, *P = nullptr, *Pprev = nullptr, *S1 = nullptr, *S2 = nullptr;
   float* part = nullptr;  // per-block metric partials of the float-float average
-  bool use_fused = true;  // fused 3-D kernels where they cover the layout
+  bool use_fused = true;     // fused 3-D kernels where they cover the layout
+  bool x_inplace_ok = true;  // every x-window has >= 2 points per span (in-place stage-1 output)
   int iters = 0;
   int grow_streak = 0;
   double last_dP = 0.0;
@@ -487,8 +488,8 @@ void run_encode(mfa_model* md, const TQ* q) {
   if constexpr (std::is_same<T, ff>::value) {
     if (md->dim == 3 && md->use_fused) {
       TRACED(h, TR_PROJECT_DATA,
-             fused = launch_project3d_ff<TQ>(L, md->offL, md->maxm[0], md->maxm[1], md->maxnL[0], md->maxnL[1], q, BL,
-                                              h->d_status, h->stream));
+             fused = launch_project3d_ff<TQ>(L, md->offL, md->maxm[0], md->maxm[1], md->maxnL[0], md->maxnL[1],
+                                              md->x_inplace_ok, q, BL, h->d_status, h->stream));
     }
   }
   for (int a = 0; a < md->dim && !fused; ++a) {
@@ -763,6 +764,20 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
     return MFA_ERR_ARG;
   }
   md->nsub = md->axh[0].S * md->axh[1].S * md->axh[2].S;
+  {
+    // stage-1 output of control point c (floats 2c, 2c+1) is written while
+    // reading the first point of span c+1; it must trail every unread point
+    const AxisHost& ax = md->axh[0];
+    for (const AxisSub& sb : ax.subs) {
+      for (int k = 0; k < sb.m && md->x_inplace_ok; ++k) {
+        const long long gk = sb.k0 + k;
+        long long sk = ax.M == 1 ? 0 : (gk * ax.nspans) / (ax.M - 1);
+        if (sk > ax.nspans - 1) sk = ax.nspans - 1;
+        const long long cmax = sk - sb.l0 - 1;  // highest CP emitted before reading point k
+        if (cmax >= 0 && 2 * cmax + 1 > k - 1) md->x_inplace_ok = false;
+      }
+    }
+  }
   std::vector<AxisOp> ops;
   std::vector<long long> offL, offS1, offS2;
   build_ops(md, ops, offL, offS1, offS2);
