@@ -484,62 +484,82 @@ __global__ void __launch_bounds__(kDecThreads) k_decode3d(LayoutDev L, const V* 
     nzl[k * W + r] = v.lo;
     if (r == 0) sz[k] = az.span[z0 + k] - cz0;
   }
-  // control-point block
+  // control-point block: lanes along x, warps over (z, y) rows of the block
   const long long n0 = L.ncp[0], n01 = L.ncp[0] * L.ncp[1];
-  const int nb = ncz * ncy * ncx;
-  for (int i = threadIdx.x; i < nb; i += kDecThreads) {
-    const int cx = i % ncx, r2 = i / ncx;
-    const int cy = r2 % ncy, cz = r2 / ncy;
-    Pb[i] = Pc[(long long)(cx0 + cx) + n0 * (cy0 + cy) + n01 * (cz0 + cz)];
+  const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;  // 8 groups of 32
+  for (int row = grp; row < ncz * ncy; row += kDecThreads / 32) {
+    const int cz = row / ncy, cy = row - cz * ncy;
+    const V* src = Pc + (long long)cx0 + n0 * (cy0 + cy) + n01 * (cz0 + cz);
+    for (int cx = lane; cx < ncx; cx += 32) Pb[row * ncx + cx] = src[cx];
   }
   __syncthreads();
-  // z expansion: Tz[z][cy][cx]
-  const int nzc = nz * ncy * ncx;
-  for (int i = threadIdx.x; i < nzc; i += kDecThreads) {
-    const int cx = i % ncx, r2 = i / ncx;
-    const int cy = r2 % ncy, z = r2 / ncy;
-    const V* src = Pb + (sz[z] * ncy + cy) * ncx + cx;
-    V acc = Val<V>::zero();
+  // z expansion: Tz[z][cy][cx]; lanes along cx, groups over cy, loop over z
+  for (int cy = grp; cy < ncy; cy += kDecThreads / 32) {
+    for (int cx = lane; cx < ncx; cx += 32) {
+#pragma unroll 2
+      for (int z = 0; z < nz; ++z) {
+        const V* src = Pb + (sz[z] * ncy + cy) * ncx + cx;
+        V acc = Val<V>::zero();
 #pragma unroll
-    for (int r = 0; r < W; ++r) Val<V>::add(acc, nzh[z * W + r], nzl[z * W + r], src[r * ncy * ncx]);
-    Tz[i] = Val<V>::finish(acc);
+        for (int r = 0; r < W; ++r) Val<V>::add(acc, nzh[z * W + r], nzl[z * W + r], src[r * ncy * ncx]);
+        Tz[(z * ncy + cy) * ncx + cx] = Val<V>::finish(acc);
+      }
+    }
   }
   __syncthreads();
-  // y expansion: Ty[z][y][cx]
-  const int nyc = nz * ny * ncx;
-  for (int i = threadIdx.x; i < nyc; i += kDecThreads) {
-    const int cx = i % ncx, r2 = i / ncx;
-    const int y = r2 % ny, z = r2 / ny;
-    const V* src = Tz + (z * ncy + sy[y]) * ncx + cx;
-    V acc = Val<V>::zero();
+  // y expansion: Ty[z][y][cx]; lanes along cx, groups over y, loop over z
+  for (int y = grp; y < ny; y += kDecThreads / 32) {
+    for (int cx = lane; cx < ncx; cx += 32) {
+#pragma unroll 2
+      for (int z = 0; z < nz; ++z) {
+        const V* src = Tz + (z * ncy + sy[y]) * ncx + cx;
+        V acc = Val<V>::zero();
 #pragma unroll
-    for (int r = 0; r < W; ++r) Val<V>::add(acc, nyh[y * W + r], nyl[y * W + r], src[r * ncx]);
-    Ty[i] = Val<V>::finish(acc);
+        for (int r = 0; r < W; ++r) Val<V>::add(acc, nyh[y * W + r], nyl[y * W + r], src[r * ncx]);
+        Ty[(z * ny + y) * ncx + cx] = Val<V>::finish(acc);
+      }
+    }
   }
   __syncthreads();
-  // x expansion of every point of the tile, then residual or output
+  // x expansion of every point of the tile, then residual or output:
+  // 64 threads along x, 4 along y
   float s2 = 0.f, emax = 0.f, qmin = INFINITY, qmax = -INFINITY;
   const long long M0 = L.M[0], M01 = L.M[0] * L.M[1];
-  const int npt = nz * ny * nx;
-  for (int i = threadIdx.x; i < npt; i += kDecThreads) {
-    const int x = i % nx, r2 = i / nx;
-    const int y = r2 % ny, z = r2 / ny;
-    const V* src = Ty + (z * ny + y) * ncx + sx[x];
-    V acc = Val<V>::zero();
+  const int xt = threadIdx.x & (kDecTX - 1), yt = threadIdx.x / kDecTX;
+  if (xt < nx) {
+    const float4 bh = W == 4 ? reinterpret_cast<const float4*>(nxh)[xt] : make_float4(0, 0, 0, 0);
+    const float4 bl = W == 4 ? reinterpret_cast<const float4*>(nxl)[xt] : make_float4(0, 0, 0, 0);
+    const int sxx = sx[xt];
+    for (int z = 0; z < nz; ++z) {
 #pragma unroll
-    for (int r = 0; r < W; ++r) Val<V>::add(acc, nxh[x * W + r], nxl[x * W + r], src[r]);
-    acc = Val<V>::finish(acc);
-    const long long g = (long long)(x0 + x) + M0 * (y0 + y) + M01 * (z0 + z);
-    if constexpr (RESID) {
-      const float q = (float)Q[g];
-      // E = q - (hi + lo): q - hi is exact when the fit is close (Sterbenz)
-      const float e = __fsub_rn(__fsub_rn(q, Val<V>::hi(acc)), Val<V>::lo(acc));
-      s2 = fmaf(e, e, s2);
-      emax = fmaxf(emax, fabsf(e));
-      qmin = fminf(qmin, q);
-      qmax = fmaxf(qmax, q);
-    } else {
-      out[g] = (TOut)((double)Val<V>::hi(acc) + (double)Val<V>::lo(acc));
+      for (int yy = 0; yy < kDecTY; yy += kDecThreads / kDecTX) {
+        const int y = yy + yt;
+        if (y >= ny) continue;
+        const V* src = Ty + (z * ny + y) * ncx + sxx;
+        V acc = Val<V>::zero();
+        if constexpr (W == 4) {
+          Val<V>::add(acc, bh.x, bl.x, src[0]);
+          Val<V>::add(acc, bh.y, bl.y, src[1]);
+          Val<V>::add(acc, bh.z, bl.z, src[2]);
+          Val<V>::add(acc, bh.w, bl.w, src[3]);
+        } else {
+#pragma unroll
+          for (int r = 0; r < W; ++r) Val<V>::add(acc, nxh[xt * W + r], nxl[xt * W + r], src[r]);
+        }
+        acc = Val<V>::finish(acc);
+        const long long g = (long long)(x0 + xt) + M0 * (y0 + y) + M01 * (z0 + z);
+        if constexpr (RESID) {
+          const float q = (float)Q[g];
+          // E = q - (hi + lo): q - hi is exact when the fit is close (Sterbenz)
+          const float e = __fsub_rn(__fsub_rn(q, Val<V>::hi(acc)), Val<V>::lo(acc));
+          s2 = fmaf(e, e, s2);
+          emax = fmaxf(emax, fabsf(e));
+          qmin = fminf(qmin, q);
+          qmax = fmaxf(qmax, q);
+        } else {
+          out[g] = (TOut)((double)Val<V>::hi(acc) + (double)Val<V>::lo(acc));
+        }
+      }
     }
   }
   if constexpr (RESID) {
@@ -728,7 +748,7 @@ __device__ __forceinline__ void solve_fibre_ff(ff* x, int n, int s, const float*
 template <int P, int NT, int NPAIR, int NPRE>
 __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* __restrict__ Pg,
                                                          const ff* __restrict__ BL, ff* __restrict__ X) {
-  constexpr int W = P + 1, B = 2 * P + 1;
+  constexpr int W = P + 1, B = 2 * P + 1, NG = NT / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   const LayoutDev& L = A.L;
   const int s = blockIdx.x;
@@ -738,6 +758,9 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
   const int nU0 = bx.nU, nU1 = by.nU, nU2 = bz.nU;
   const int oU0 = bx.oU, oU1 = by.oU, oU2 = bz.oU;
   const long long n0 = L.ncp[0], n01 = L.ncp[0] * L.ncp[1];
+  // thread map: lanes along the owned x points (nU0 <= 32), groups over y
+  const int ux = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const bool xin = ux < nU0;
 
   float* axh = reinterpret_cast<float*>(smem);  // [nU0][B]
   float* axl = axh + nU0 * B;
@@ -765,9 +788,8 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
   for (int i = threadIdx.x; i < nU1 * W; i += NT) fy[i] = L.ax[1].facU_f[(long long)by.bandU * W + i];
   for (int i = threadIdx.x; i < nU2 * W; i += NT) fz[i] = L.ax[2].facU_f[(long long)bz.bandU * W + i];
 
-  const int npairs = nU0 * nU1;
   const int nplane = nL1 * nL0;
-  ff ring[NPAIR][B];
+  ff ring[NPAIR][B];  // pair i of this thread: owned (ux, uy = grp + NG*i)
 #pragma unroll
   for (int i = 0; i < NPAIR; ++i)
 #pragma unroll
@@ -791,6 +813,12 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
       }
     }
   };
+  auto write_resid = [&](int i, int uz) {
+    const int uy = grp + NG * i;
+    const ff b = bl[(oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uz))];
+    const ff r = b - AccFF::finish(ring[i][0]);
+    R[(uz * nU1 + uy) * nU0 + ux] = r.hi + r.lo;
+  };
   fetch(lz_lo);
   for (int lz = lz_lo; lz <= lz_hi; ++lz) {
 #pragma unroll
@@ -801,50 +829,50 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
     __syncthreads();
     if (lz < lz_hi) fetch(lz + 1);
     // x band product, owned x rows
-    for (int i = threadIdx.x; i < nL1 * nU0; i += NT) {
-      const int ly = i / nU0, ux = i - ly * nU0;
+    if (xin) {
       const int c0 = oU0 + ux - P;
-      ff acc(0.f, 0.f);
+      for (int ly = grp; ly < nL1; ly += NG) {
+        ff acc(0.f, 0.f);
 #pragma unroll
-      for (int e = 0; e < B; ++e) {
-        const int c = c0 + e;
-        if (c >= 0 && c < nL0) AccFF::add_v(acc, axh[ux * B + e], axl[ux * B + e], Pp[ly * nL0 + c]);
+        for (int e = 0; e < B; ++e) {
+          const int c = c0 + e;
+          if (c >= 0 && c < nL0) AccFF::add_v(acc, axh[ux * B + e], axl[ux * B + e], Pp[ly * nL0 + c]);
+        }
+        Y1[ly * nU0 + ux] = AccFF::finish(acc);
       }
-      Y1[i] = AccFF::finish(acc);
     }
     __syncthreads();
     // y band product, owned y rows
-    for (int i = threadIdx.x; i < nU1 * nU0; i += NT) {
-      const int uy = i / nU0, ux = i - uy * nU0;
-      const int c0 = oU1 + uy - P;
-      ff acc(0.f, 0.f);
+    if (xin) {
 #pragma unroll
-      for (int e = 0; e < B; ++e) {
-        const int c = c0 + e;
-        if (c >= 0 && c < nL1) AccFF::add_v(acc, ayh[uy * B + e], ayl[uy * B + e], Y1[c * nU0 + ux]);
+      for (int i = 0; i < NPAIR; ++i) {
+        const int uy = grp + NG * i;
+        if (uy < nU1) {
+          const int c0 = oU1 + uy - P;
+          ff acc(0.f, 0.f);
+#pragma unroll
+          for (int e = 0; e < B; ++e) {
+            const int c = c0 + e;
+            if (c >= 0 && c < nL1) AccFF::add_v(acc, ayh[uy * B + e], ayl[uy * B + e], Y1[c * nU0 + ux]);
+          }
+          Y2[uy * nU0 + ux] = AccFF::finish(acc);
+        }
       }
-      Y2[i] = AccFF::finish(acc);
     }
     __syncthreads();
     // z band product into the ring: slot j holds owned z-point uz = lz - oU2 - P + j
     const int uzb = lz - oU2 - P;
 #pragma unroll
     for (int i = 0; i < NPAIR; ++i) {
-      const int q = threadIdx.x + i * NT;
-      if (q < npairs) {
-        const ff y2 = Y2[q];
+      const int uy = grp + NG * i;
+      if (xin && uy < nU1) {
+        const ff y2 = Y2[uy * nU0 + ux];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
           const int uz = uzb + j;
           if (uz >= 0 && uz < nU2) AccFF::add_v(ring[i][j], azh[uz * B + (2 * P - j)], azl[uz * B + (2 * P - j)], y2);
         }
-        // slot 0 is complete: residual r = B_U - (A x A x A) Z
-        if (uzb >= 0 && uzb < nU2) {
-          const int ux = q % nU0, uy = q / nU0;
-          const ff b = bl[(oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uzb))];
-          const ff r = b - AccFF::finish(ring[i][0]);
-          R[(uzb * nU1 + uy) * nU0 + ux] = r.hi + r.lo;
-        }
+        if (uzb >= 0 && uzb < nU2) write_resid(i, uzb);  // slot 0 is complete
       }
 #pragma unroll
       for (int j = 0; j < B - 1; ++j) ring[i][j] = ring[i][j + 1];
@@ -856,18 +884,18 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
   {
     const int uzb = lz_hi + 1 - oU2 - P;  // z-point now in slot 0
 #pragma unroll
-    for (int i = 0; i < NPAIR; ++i) {
-      const int q = threadIdx.x + i * NT;
-      if (q >= npairs) continue;
-      const int ux = q % nU0, uy = q / nU0;
+    for (int j = 0; j < B; ++j) {
+      const int uz = uzb + j;
 #pragma unroll
-      for (int j = 0; j < B; ++j) {
-        const int uz = uzb + j;
-        if (uz >= 0 && uz < nU2) {
-          const ff b = bl[(oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uz))];
-          const ff r = b - AccFF::finish(ring[i][j]);
-          R[(uz * nU1 + uy) * nU0 + ux] = r.hi + r.lo;
-        }
+      for (int i = 0; i < NPAIR; ++i) {
+        const int uy = grp + NG * i;
+        if (xin && uy < nU1 && uz >= 0 && uz < nU2) write_resid(i, uz);
+      }
+#pragma unroll
+      for (int i = 0; i < NPAIR; ++i) {
+#pragma unroll
+        for (int jj = 0; jj < B - 1; ++jj) ring[i][jj] = ring[i][jj + 1];
+        ring[i][B - 1] = ff(0.f, 0.f);
       }
     }
   }
@@ -876,19 +904,34 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
   for (int f = threadIdx.x; f < nU1 * nU2; f += NT) solve_fibre<P>(R + f * nU0, nU0, 1, fx);
   __syncthreads();
   for (int f = threadIdx.x; f < nU0 * nU2; f += NT) {
-    const int ux = f % nU0, uz = f / nU0;
-    solve_fibre<P>(R + uz * nU1 * nU0 + ux, nU1, nU0, fy);
+    const int fx0 = f % nU0, uz = f / nU0;
+    solve_fibre<P>(R + uz * nU1 * nU0 + fx0, nU1, nU0, fy);
   }
   __syncthreads();
   for (int f = threadIdx.x; f < nU0 * nU1; f += NT) solve_fibre<P>(R + f, nU2, nU0 * nU1, fz);
   __syncthreads();
-  // refined copy X_s^k = X_s^{k-1} + c_s
-  const int nUall = nU0 * nU1 * nU2;
-  for (int i = threadIdx.x; i < nUall; i += NT) {
-    const int ux = i % nU0, r2 = i / nU0;
-    const int uy = r2 % nU1, uz = r2 / nU1;
-    const long long li = (oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uz));
-    xs[li] = xs[li] + ff(R[i]);
+  // refined copy X_s^k = X_s^{k-1} + c_s (four z-planes of loads in flight)
+  if (xin) {
+#pragma unroll
+    for (int i = 0; i < NPAIR; ++i) {
+      const int uy = grp + NG * i;
+      if (uy >= nU1) continue;
+      for (int uz0 = 0; uz0 < nU2; uz0 += 4) {
+        ff v[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int uz = uz0 + t;
+          if (uz < nU2) v[t] = xs[(oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uz))];
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int uz = uz0 + t;
+          if (uz < nU2)
+            xs[(oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uz))] =
+                v[t] + ff(R[(uz * nU1 + uy) * nU0 + ux]);
+        }
+      }
+    }
   }
 }
 
@@ -911,9 +954,10 @@ bool launch_schwarz3d_ff(const LayoutDev& L, const long long* offL, const int* m
   Step3dArgs A;
   A.L = L;
   A.offL = offL;
-  const int npairs = maxnU[0] * maxnU[1];
+  constexpr int NG = kStepThreads / 32;
   const int nplane = maxnL[0] * maxnL[1];
-  if (npairs > 3 * kStepThreads || nplane > 4 * kStepThreads) return false;
+  // owned x points on the lanes, owned y points on NPAIR rounds of the groups
+  if (maxnU[0] > 32 || maxnU[1] > 4 * NG || nplane > 4 * kStepThreads) return false;
   auto go = [&](auto kernel, size_t sm) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -923,7 +967,10 @@ bool launch_schwarz3d_ff(const LayoutDev& L, const long long* offL, const int* m
   case PP: {                                                                                   \
     const size_t sm = step3d_smem<PP>(maxnL[0], maxnL[1], maxnU[0], maxnU[1], maxnU[2]);       \
     if (sm > 220 * 1024) return false;                                                         \
-    go(k_schwarz3d_ff<PP, kStepThreads, 3, 4>, sm);                                            \
+    if (maxnU[1] <= 2 * NG)                                                                    \
+      go(k_schwarz3d_ff<PP, kStepThreads, 2, 4>, sm);                                          \
+    else                                                                                       \
+      go(k_schwarz3d_ff<PP, kStepThreads, 4, 4>, sm);                                          \
     return true;                                                                               \
   }
   switch (p) {
