@@ -813,12 +813,20 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
       }
     }
   };
-  auto write_resid = [&](int i, int uz) {
+  auto b_at = [&](int i, int uz) -> ff {
     const int uy = grp + NG * i;
-    const ff b = bl[(oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uz))];
+    if (!xin || uy >= nU1 || uz < 0 || uz >= nU2) return ff(0.f, 0.f);
+    return bl[(oU0 + ux) + (long long)nL0 * ((oU1 + uy) + (long long)nL1 * (oU2 + uz))];
+  };
+  auto write_resid = [&](int i, int uz, ff b) {
+    const int uy = grp + NG * i;
     const ff r = b - AccFF::finish(ring[i][0]);
     R[(uz * nU1 + uy) * nU0 + ux] = r.hi + r.lo;
   };
+  // B_U of the owned z-point that completes at the current plane, fetched one plane ahead
+  ff bnext[NPAIR];
+#pragma unroll
+  for (int i = 0; i < NPAIR; ++i) bnext[i] = b_at(i, lz_lo - oU2 - P);
   fetch(lz_lo);
   for (int lz = lz_lo; lz <= lz_hi; ++lz) {
 #pragma unroll
@@ -862,6 +870,12 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
     __syncthreads();
     // z band product into the ring: slot j holds owned z-point uz = lz - oU2 - P + j
     const int uzb = lz - oU2 - P;
+    ff bcur[NPAIR];
+#pragma unroll
+    for (int i = 0; i < NPAIR; ++i) {
+      bcur[i] = bnext[i];
+      bnext[i] = b_at(i, uzb + 1);
+    }
 #pragma unroll
     for (int i = 0; i < NPAIR; ++i) {
       const int uy = grp + NG * i;
@@ -872,7 +886,7 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
           const int uz = uzb + j;
           if (uz >= 0 && uz < nU2) AccFF::add_v(ring[i][j], azh[uz * B + (2 * P - j)], azl[uz * B + (2 * P - j)], y2);
         }
-        if (uzb >= 0 && uzb < nU2) write_resid(i, uzb);  // slot 0 is complete
+        if (uzb >= 0 && uzb < nU2) write_resid(i, uzb, bcur[i]);  // slot 0 is complete
       }
 #pragma unroll
       for (int j = 0; j < B - 1; ++j) ring[i][j] = ring[i][j + 1];
@@ -889,7 +903,7 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
 #pragma unroll
       for (int i = 0; i < NPAIR; ++i) {
         const int uy = grp + NG * i;
-        if (xin && uy < nU1 && uz >= 0 && uz < nU2) write_resid(i, uz);
+        if (xin && uy < nU1 && uz >= 0 && uz < nU2) write_resid(i, uz, b_at(i, uz));
       }
 #pragma unroll
       for (int i = 0; i < NPAIR; ++i) {
