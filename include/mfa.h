@@ -51,7 +51,8 @@ enum {
   MFA_ERR_NOT_SPD = -5,    /* a local normal matrix had a non-positive Cholesky pivot */
   MFA_ERR_DIVERGED = -6,   /* the Schwarz update grew for 8 iterations in a row */
   MFA_ERR_NONFINITE = -7,  /* the input data held NaN or Inf */
-  MFA_ERR_UNSUPPORTED = -8 /* valid request outside what this build implements */
+  MFA_ERR_UNSUPPORTED = -8, /* valid request outside what this build implements */
+  MFA_ERR_TIMEOUT = -9      /* a kernel's bounded wait for an asynchronous copy gave up; results invalid */
 };
 
 enum { MFA_F32 = 0, MFA_F64 = 1 };

@@ -4,7 +4,12 @@
 // Accumulation: `AccFF` keeps float-float sums (products formed exactly with
 // FMA, sums compensated).  The kernels read the data once per subdomain window
 // and stream it through shared memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <algorithm>
+#include <cstdint>
+#include <cstring>
 
 #include "mfa_internal.cuh"
 
@@ -54,11 +59,18 @@ __device__ __forceinline__ float to_f(TQ x) {
 // Projection B_L = (N_z^T x N_y^T x N_x^T) Q over every window (the N^T Q
 // assembly of the local normal equations, Eq. minimization-problem).
 //
-// One CTA per subdomain streams its window in batches of ZB z-planes:
+// One CTA per subdomain streams its window in batches of ZB z-planes.  A batch
+// is one box of the data [ZB][BY][BX] copied by the tensor memory accelerator
+// (or, for unaligned or FP64 input, by per-element asynchronous copies into
+// the same layout): the box starts at the window's first x rounded down to a
+// multiple of four, so point k of a row sits at staged position cx + k, and
+// the positions outside the window carry zero basis values.  Rows are BX
+// floats apart with BX = 4 (mod 8), so a warp's 16-byte row reads are free of
+// bank conflicts.
 //   stage 1 (x): one thread per data row; a sliding window of P+1
-//                accumulators walks the row, each point adding its P+1 basis
-//                products; a control point is emitted when the span moves
-//                past it.
+//                accumulators walks the row four points at a time, each point
+//                adding its P+1 basis products; a control point is emitted
+//                (in place, over consumed data) when the span moves past it.
 //   stage 2 (y): one thread per (plane, x-control point, chunk of y-control
 //                points), same sliding window down the column.
 //   stage 3 (z): every thread owns NPAIR (x,y) control-point pairs and keeps
@@ -72,10 +84,37 @@ __device__ __forceinline__ float to_f(TQ x) {
 struct Proj3dArgs {
   LayoutDev L;
   const long long* offL;
-  int zb;     // planes per batch
-  int nch2;   // y-chunks per column in stage 2
-  int ldq;    // row pitch (floats) of the staged data, odd
+  int zb;        // planes per batch (box z)
+  int nch2;      // y-chunks per column in stage 2
+  int bx;        // staged row pitch in floats = box x; multiple of 4, = 4 (mod 8)
+  int by;        // staged rows per plane = box y = largest window along y
+  int mz;        // largest window along z
+  int n0, n1;    // largest L along x and y
 };
+
+// Shared-memory carve-up of the projection, used by the kernel and the launcher.
+struct ProjSmem {
+  size_t t2, txh, txl, tyh, tyl, tzh, tzl, spx, spy, spz, bar, total;
+};
+__host__ __device__ inline ProjSmem proj_smem_layout(int W, int zb, int bx, int by, int mz, int n0, int n1) {
+  ProjSmem s;
+  auto al = [](size_t o) { return (o + 15) & ~size_t(15); };
+  size_t o = (size_t)zb * by * bx * 4;  // staged data at offset 0 (128-byte aligned base)
+  s.t2 = al(o);
+  o = s.t2 + (size_t)zb * n1 * n0 * sizeof(ff);
+  s.txh = al(o);
+  s.txl = s.txh + (size_t)bx * W * 4;
+  s.tyh = s.txl + (size_t)bx * W * 4;
+  s.tyl = s.tyh + (size_t)by * W * 4;
+  s.tzh = s.tyl + (size_t)by * W * 4;
+  s.tzl = s.tzh + (size_t)mz * W * 4;
+  s.spx = s.tzl + (size_t)mz * W * 4;
+  s.spy = s.spx + (size_t)bx * 4;
+  s.spz = s.spy + (size_t)by * 4;
+  s.bar = al(s.spz + (size_t)mz * 4);
+  s.total = s.bar + 16;
+  return s;
+}
 
 __device__ __forceinline__ void cp_async_f32(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
@@ -84,68 +123,124 @@ __device__ __forceinline__ void cp_async_f32(float* dst, const float* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// Stage planes z0 .. z0+nz-1 of the window into Qs [nz][m1][ldq] with
-// coalesced copies: each warp copies whole rows, lanes along x.
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+// Arm the barrier for `bytes` and start the copy of one [z][y][x] box at
+// global coordinates (x, y, z) into `dst`.
+__device__ __forceinline__ void tma_load_box(const CUtensorMap* map, float* dst, unsigned long long* bar, int x,
+                                             int y, int z, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Wait for phase `parity` of the barrier; gives up after about two seconds of
+// clock cycles and returns false.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const long long t0 = clock64();
+  for (;;) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > 4000000000LL) return false;
+  }
+}
+
+// Per-element staging of planes z0 .. z0+nz-1 (rows y < m1) into the box
+// layout, for input the tensor copy cannot take: staged position i of a row
+// holds global x = xa + i, zero beyond the grid.
 template <typename TQ>
-__device__ __forceinline__ void stage_planes(float* Qs, const TQ* qwin, long long M0, long long M01, int z0, int nz,
-                                             int m0, int m1, int ldq) {
+__device__ __forceinline__ void stage_rows(float* Qs, const TQ* Q, long long M0, long long M01, int xa, int y0,
+                                           int z0, int nz, int m1, int bx, int by) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int row = warp; row < nz * m1; row += nwarp) {
     const int zz = row / m1, y = row - zz * m1;
-    const TQ* src = qwin + M01 * (z0 + zz) + M0 * y;
-    float* dst = Qs + row * ldq;
-    for (int x = lane; x < m0; x += 32) {
-      if constexpr (sizeof(TQ) == 4)
-        cp_async_f32(dst + x, reinterpret_cast<const float*>(src) + x);
+    const TQ* src = Q + M01 * (z0 + zz) + M0 * (y0 + y);
+    float* dst = Qs + (size_t)(zz * by + y) * bx;
+    for (int i = lane; i < bx; i += 32) {
+      const long long g = xa + i;
+      if (g >= M0)
+        dst[i] = 0.f;
+      else if constexpr (sizeof(TQ) == 4)
+        cp_async_f32(dst + i, reinterpret_cast<const float*>(src) + g);
       else
-        dst[x] = (float)src[x];
+        dst[i] = (float)src[g];
     }
   }
   cp_async_commit();
 }
 
-template <int P, int NT, int NPAIR, typename TQ>
-__global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* __restrict__ Q, ff* __restrict__ BL,
+template <int P, int NT, int NPAIR, bool TMA, typename TQ>
+__global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ CUtensorMap tmq, Proj3dArgs A,
+                                                         const TQ* __restrict__ Q, ff* __restrict__ BL,
                                                          int* status) {
   constexpr int W = P + 1;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const LayoutDev& L = A.L;
   const int s = blockIdx.x;
   const int s0 = s % L.S[0], s1 = (s / L.S[0]) % L.S[1], s2 = s / (L.S[0] * L.S[1]);
   const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];
   const int m0 = bx.m, m1 = by.m, m2 = bz.m;
   const int n0 = bx.nL, n1 = by.nL, n2 = bz.nL;
-  const int zb = A.zb, ldq = A.ldq;
+  const int zb = A.zb, BX = A.bx, BY = A.by;
+  const int cx = bx.k0 & 3;              // staged position of window point 0
+  const int xa = bx.k0 - cx;             // global x of staged position 0 (multiple of 4)
+  const int nq4 = (cx + m0 + 3) >> 2;    // 16-byte chunks of a row that hold window points
   const long long M0 = L.M[0], M01 = L.M[0] * L.M[1];
+  const ProjSmem lay = proj_smem_layout(W, zb, BX, BY, A.mz, A.n0, A.n1);
 
-  // shared: basis x and y as hi/lo rows of W values, local spans, staged data
-  // rows (overwritten in place by the stage-1 output: control point c of a row
-  // lands on floats 2c, 2c+1, behind every point still to be read when there
-  // are at least two points per span), stage-2 output
-  float* bxh = reinterpret_cast<float*>(smem);     // [m0][W]
-  float* bxl = bxh + m0 * W;                        // [m0][W]
-  float* byh = bxl + m0 * W;                        // [m1][W]
-  float* byl = byh + m1 * W;                        // [m1][W]
-  int* spx = reinterpret_cast<int*>(byl + m1 * W);  // [m0]
-  int* spy = spx + m0;                              // [m1]
-  size_t off = (size_t)(2 * W * (m0 + m1)) * 4 + (size_t)(m0 + m1) * 4;
-  off = (off + 15) & ~size_t(15);
-  float* Qs = reinterpret_cast<float*>(smem + off);  // [zb][m1][ldq]; row t's stage-1 output as ff at Qs + t*ldq
-  off += (size_t)zb * m1 * ldq * 4;
-  off = (off + 15) & ~size_t(15);
-  ff* T2 = reinterpret_cast<ff*>(smem + off);       // [zb][n1][n0]
+  float* Qs = reinterpret_cast<float*>(smem);  // [zb][BY][BX]; row t's stage-1 output as ff pairs at its start
+  ff* T2 = reinterpret_cast<ff*>(smem + lay.t2);  // [zb][n1][n0]
+  float* txh = reinterpret_cast<float*>(smem + lay.txh);  // [BX][W] by staged position
+  float* txl = reinterpret_cast<float*>(smem + lay.txl);
+  float* tyh = reinterpret_cast<float*>(smem + lay.tyh);  // [m1][W]
+  float* tyl = reinterpret_cast<float*>(smem + lay.tyl);
+  float* tzh = reinterpret_cast<float*>(smem + lay.tzh);  // [m2][W]
+  float* tzl = reinterpret_cast<float*>(smem + lay.tzl);
+  int* spx = reinterpret_cast<int*>(smem + lay.spx);      // [BX] local span by staged position
+  int* spy = reinterpret_cast<int*>(smem + lay.spy);
+  int* spz = reinterpret_cast<int*>(smem + lay.spz);
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + lay.bar);
+  const unsigned box_bytes = (unsigned)(zb * BY * BX * 4);
 
+  if constexpr (TMA) {
+    if (threadIdx.x == 0) {
+      mbar_init(bar, 1);
+      tma_load_box(&tmq, Qs, bar, xa, by.k0, bz.k0, box_bytes);
+    }
+  } else {
+    stage_rows<TQ>(Qs, Q, M0, M01, xa, by.k0, bz.k0, min(zb, m2), m1, BX, BY);
+  }
+
+  // basis tables: x by staged position (zero outside the window, span held
+  // at the nearest window point so no control point is emitted there)
   const ff* vx = L.ax[0].vals_ff;
   const ff* vy = L.ax[1].vals_ff;
   const ff* vz = L.ax[2].vals_ff;
-  for (int i = threadIdx.x; i < m0; i += NT) {
-    const int k = bx.k0 + i;
-    spx[i] = L.ax[0].span[k] - bx.l0;
+  for (int i = threadIdx.x; i < BX; i += NT) {
+    const int k = i - cx;
+    const bool in = k >= 0 && k < m0;
+    const int kk = min(max(k, 0), m0 - 1);
+    spx[i] = L.ax[0].span[bx.k0 + kk] - bx.l0;
 #pragma unroll
     for (int r = 0; r < W; ++r) {
-      const ff v = vx[(long long)k * W + r];
-      bxh[i * W + r] = v.hi;
-      bxl[i * W + r] = v.lo;
+      const ff v = in ? vx[(long long)(bx.k0 + k) * W + r] : ff(0.f, 0.f);
+      txh[i * W + r] = v.hi;
+      txl[i * W + r] = v.lo;
     }
   }
   for (int i = threadIdx.x; i < m1; i += NT) {
@@ -154,8 +249,18 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
 #pragma unroll
     for (int r = 0; r < W; ++r) {
       const ff v = vy[(long long)k * W + r];
-      byh[i * W + r] = v.hi;
-      byl[i * W + r] = v.lo;
+      tyh[i * W + r] = v.hi;
+      tyl[i * W + r] = v.lo;
+    }
+  }
+  for (int i = threadIdx.x; i < m2; i += NT) {
+    const int k = bz.k0 + i;
+    spz[i] = L.ax[2].span[k] - bz.l0;
+#pragma unroll
+    for (int r = 0; r < W; ++r) {
+      const ff v = vz[(long long)k * W + r];
+      tzh[i * W + r] = v.hi;
+      tzl[i * W + r] = v.lo;
     }
   }
 
@@ -166,56 +271,72 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
     for (int r = 0; r < W; ++r) ring[i][r] = ff(0.f, 0.f);
   const int npairs = n0 * n1;
   ff* out = BL + A.offL[s];
-  int curz = L.ax[2].span[bz.k0] - bz.l0;  // z-control point held in ring slot 0
   bool bad = false;
-  const TQ* qwin = Q + (long long)bx.k0 + M0 * by.k0 + M01 * bz.k0;
-  stage_planes<TQ>(Qs, qwin, M0, M01, 0, min(zb, m2), m0, m1, ldq);
+  unsigned phase = 0;
+  __syncthreads();     // tables written, barrier initialised
+  int curz = spz[0];   // z-control point held in ring slot 0
 
   for (int z0 = 0; z0 < m2; z0 += zb) {
     const int nz = min(zb, m2 - z0);
-    cp_async_wait_all();
-    __syncthreads();
-    // ---- stage 1: one staged row per thread, sliding window of P+1
-    // accumulators; the output overwrites the consumed part of the row
+    bool lost = false;
+    if constexpr (TMA) {
+      lost = !mbar_wait(bar, phase);
+      phase ^= 1u;
+    } else {
+      cp_async_wait_all();
+    }
+    if (__syncthreads_or(lost)) {
+      if (threadIdx.x == 0) {
+        if (status) atomicExch(status, MFA_ERR_TIMEOUT);
+        if constexpr (TMA) mbar_wait(bar, phase ^ 1u);  // one more bounded wait for the copy in flight
+      }
+      return;
+    }
+    // ---- stage 1: one staged row per thread, four points per 16-byte read,
+    // sliding window of P+1 accumulators; the output overwrites the consumed
+    // part of the row
     for (int t = threadIdx.x; t < nz * m1; t += NT) {
-      const float* q = Qs + t * ldq;
-      float* o = Qs + t * ldq;  // output of control point c at o[2c] (hi), o[2c+1] (lo); 4-byte aligned only
+      const int zz = t / m1, y = t - zz * m1;
+      float* row = Qs + (size_t)(zz * BY + y) * BX;
       ff win[W];
 #pragma unroll
       for (int r = 0; r < W; ++r) win[r] = ff(0.f, 0.f);
       int cur = spx[0];
-      for (int k = 0; k < m0; ++k) {
-        const float x = q[k];
-        const int sk = spx[k];
-        while (cur < sk) {
-          if (cur >= 0 && cur < n0) {
-            const ff v = AccFF::finish(win[0]);
-            o[2 * cur] = v.hi;
-            o[2 * cur + 1] = v.lo;
+      for (int j = 0; j < nq4; ++j) {
+        const float4 q4 = reinterpret_cast<const float4*>(row)[j];
+        const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int i = 4 * j + u;
+          const int sk = spx[i];
+          while (cur < sk) {
+            if (cur >= 0 && cur < n0) {
+              const ff v = AccFF::finish(win[0]);
+              *reinterpret_cast<float2*>(row + 2 * cur) = make_float2(v.hi, v.lo);
+            }
+#pragma unroll
+            for (int r = 0; r < P; ++r) win[r] = win[r + 1];
+            win[P] = ff(0.f, 0.f);
+            ++cur;
           }
+          if constexpr (W == 4) {
+            const float4 nh = reinterpret_cast<const float4*>(txh)[i];
+            const float4 nl = reinterpret_cast<const float4*>(txl)[i];
+            AccFF::add_f(win[0], nh.x, nl.x, qv[u]);
+            AccFF::add_f(win[1], nh.y, nl.y, qv[u]);
+            AccFF::add_f(win[2], nh.z, nl.z, qv[u]);
+            AccFF::add_f(win[3], nh.w, nl.w, qv[u]);
+          } else {
 #pragma unroll
-          for (int r = 0; r < P; ++r) win[r] = win[r + 1];
-          win[P] = ff(0.f, 0.f);
-          ++cur;
-        }
-        if constexpr (W == 4) {
-          const float4 nh = reinterpret_cast<const float4*>(bxh)[k];
-          const float4 nl = reinterpret_cast<const float4*>(bxl)[k];
-          AccFF::add_f(win[0], nh.x, nl.x, x);
-          AccFF::add_f(win[1], nh.y, nl.y, x);
-          AccFF::add_f(win[2], nh.z, nl.z, x);
-          AccFF::add_f(win[3], nh.w, nl.w, x);
-        } else {
-#pragma unroll
-          for (int r = 0; r < W; ++r) AccFF::add_f(win[r], bxh[k * W + r], bxl[k * W + r], x);
+            for (int r = 0; r < W; ++r) AccFF::add_f(win[r], txh[i * W + r], txl[i * W + r], qv[u]);
+          }
         }
       }
 #pragma unroll
       for (int r = 0; r < W; ++r)
         if (cur + r >= 0 && cur + r < n0) {
           const ff v = AccFF::finish(win[r]);
-          o[2 * (cur + r)] = v.hi;
-          o[2 * (cur + r) + 1] = v.lo;
+          *reinterpret_cast<float2*>(row + 2 * (cur + r)) = make_float2(v.hi, v.lo);
         }
     }
     __syncthreads();
@@ -233,7 +354,7 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
         // rows whose span reaches control points [c0, c1): span in [c0-P, c1-1]
         const int gs0 = max(by.l0 + c0 - P, 0), gs1 = min(by.l0 + c1, L.ax[1].nspans);
         const int y0 = max(ss[gs0] - by.k0, 0), y1 = min(ss[gs1] - by.k0, m1);
-        const float* colf = Qs + zz * m1 * ldq + 2 * lx;
+        const float* colf = Qs + (size_t)zz * BY * BX + 2 * lx;
         ff* o = T2 + zz * n1 * n0 + lx;
         ff win[W];
 #pragma unroll
@@ -248,22 +369,31 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
             win[P] = ff(0.f, 0.f);
             ++cur;
           }
-          const ff x(colf[y * ldq], colf[y * ldq + 1]);
+          const float2 xv = *reinterpret_cast<const float2*>(colf + (size_t)y * BX);
+          const ff x(xv.x, xv.y);
 #pragma unroll
-          for (int r = 0; r < W; ++r) AccFF::add_v(win[r], byh[y * W + r], byl[y * W + r], x);
+          for (int r = 0; r < W; ++r) AccFF::add_v(win[r], tyh[y * W + r], tyl[y * W + r], x);
         }
 #pragma unroll
         for (int r = 0; r < W; ++r)
           if (cur + r >= c0 && cur + r < c1) o[(cur + r) * n0] = AccFF::finish(win[r]);
       }
     }
+    // the staged rows are free again: order this CTA's shared-memory accesses
+    // before the copy engine's writes, then fetch the next batch behind stage 3
+    if constexpr (TMA) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
-    // the staged rows are free again: fetch the next batch behind stage 3
-    if (z0 + zb < m2) stage_planes<TQ>(Qs, qwin, M0, M01, z0 + zb, min(zb, m2 - z0 - zb), m0, m1, ldq);
+    if (z0 + zb < m2) {
+      if constexpr (TMA) {
+        if (threadIdx.x == 0) tma_load_box(&tmq, Qs, bar, xa, by.k0, bz.k0 + z0 + zb, box_bytes);
+      } else {
+        stage_rows<TQ>(Qs, Q, M0, M01, xa, by.k0, bz.k0 + z0 + zb, min(zb, m2 - z0 - zb), m1, BX, BY);
+      }
+    }
     // ---- stage 3: accumulate the planes into the z ring
     for (int zz = 0; zz < nz; ++zz) {
-      const int kz = bz.k0 + z0 + zz;
-      const int sz = L.ax[2].span[kz] - bz.l0;
+      const int kz = z0 + zz;
+      const int sz = spz[kz];
       while (curz < sz) {
 #pragma unroll
         for (int i = 0; i < NPAIR; ++i) {
@@ -282,9 +412,8 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
       float nzh[W], nzl[W];
 #pragma unroll
       for (int r = 0; r < W; ++r) {
-        const ff v = vz[(long long)kz * W + r];
-        nzh[r] = v.hi;
-        nzl[r] = v.lo;
+        nzh[r] = tzh[kz * W + r];
+        nzl[r] = tzl[kz * W + r];
       }
       const ff* t2 = T2 + zz * npairs;
 #pragma unroll
@@ -297,6 +426,7 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
         }
       }
     }
+    // T2 is rewritten by the next batch's stage 2 only after its stage-1 barrier
   }
 #pragma unroll
   for (int i = 0; i < NPAIR; ++i) {
@@ -312,58 +442,93 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(Proj3dArgs A, const TQ* 
   if (bad && status) atomicExch(status, MFA_ERR_NONFINITE);
 }
 
-template <int P>
-size_t proj3d_smem(int m0, int m1, int n0, int n1, int zb, int ldq) {
-  constexpr int W = P + 1;
-  size_t off = (size_t)(2 * W * (m0 + m1)) * 4 + (size_t)(m0 + m1) * 4;
-  off = (off + 15) & ~size_t(15);
-  off += (size_t)zb * m1 * ldq * 4;
-  off = (off + 15) & ~size_t(15);
-  off += (size_t)zb * n1 * n0 * sizeof(ff);
-  return off;
-}
-
 constexpr int kProjThreads = 256;
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
 
 // Returns false when the fused kernel does not cover this layout (the caller
 // then runs the generic per-axis kernels).  `inplace_ok` says every x-window
 // has at least two points per span, so the stage-1 output can overwrite the
 // consumed data in place.
 template <typename TQ>
-bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, int maxm1, int maxn0, int maxn1,
-                         bool inplace_ok, const TQ* Q, ff* BL, int* status, cudaStream_t st) {
+bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, int maxm1, int maxm2, int maxn0,
+                         int maxn1, bool inplace_ok, const TQ* Q, ff* BL, int* status, cudaStream_t st) {
   const int P = L.ax[0].p;
   if (L.dim != 3 || L.ax[1].p != P || L.ax[2].p != P || !inplace_ok) return false;
   const int npairs = maxn0 * maxn1;
   Proj3dArgs A;
   A.L = L;
   A.offL = offL;
-  A.ldq = std::max(maxm0, 2 * maxn0 + 1) | 1;
+  // row pitch: window plus alignment slack, room for the in-place output,
+  // a multiple of 4 floats with an odd number of 16-byte chunks
+  int bx = std::max(maxm0 + 3, 2 * maxn0 + 2);
+  bx = (bx + 3) & ~3;
+  if (bx % 8 == 0) bx += 4;
+  A.bx = bx;
+  A.by = maxm1;
+  A.mz = maxm2;
+  A.n0 = maxn0;
+  A.n1 = maxn1;
   // planes per batch: fill the stage-1 rows onto the threads
   A.zb = std::max(1, std::min(4, kProjThreads / std::max(maxm1, 1)));
-  size_t smem = 0;
-  auto pick = [&](auto kernel, size_t sm) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    A.nch2 = std::max(1, kProjThreads / std::max(1, A.zb * maxn0));
-    kernel<<<L.nsub, kProjThreads, sm, st>>>(A, Q, BL, status);
-  };
-#define MFA_PROJ_CASE(PP)                                                  \
-  case PP: {                                                               \
-    smem = proj3d_smem<PP>(maxm0, maxm1, maxn0, maxn1, A.zb, A.ldq);       \
-    while (smem > 110 * 1024 && A.zb > 1) {                                \
-      A.zb--;                                                              \
-      smem = proj3d_smem<PP>(maxm0, maxm1, maxn0, maxn1, A.zb, A.ldq);     \
-    }                                                                      \
-    if (smem > 200 * 1024) return false;                                   \
-    if (npairs <= 4 * kProjThreads)                                        \
-      pick(k_project3d_ff<PP, kProjThreads, 4, TQ>, smem);                 \
-    else if (npairs <= 8 * kProjThreads)                                   \
-      pick(k_project3d_ff<PP, kProjThreads, 8, TQ>, smem);                 \
-    else                                                                   \
-      return false;                                                        \
-    return true;                                                           \
+  const int W = P + 1;
+  size_t smem = proj_smem_layout(W, A.zb, A.bx, A.by, A.mz, A.n0, A.n1).total;
+  while (smem > 110 * 1024 && A.zb > 1) {
+    A.zb--;
+    smem = proj_smem_layout(W, A.zb, A.bx, A.by, A.mz, A.n0, A.n1).total;
   }
+  if (smem > 200 * 1024 || npairs > 8 * kProjThreads) return false;
+  A.nch2 = std::max(1, kProjThreads / std::max(1, A.zb * maxn0));
+
+  // the tensor copy takes FP32 data on a 16-byte aligned base with rows a
+  // multiple of 16 bytes long and boxes of at most 256 per dimension
+  CUtensorMap tmap;
+  std::memset(&tmap, 0, sizeof(tmap));
+  bool tma = sizeof(TQ) == 4 && (reinterpret_cast<uintptr_t>(Q) % 16) == 0 && L.M[0] % 4 == 0 && A.bx <= 256 &&
+             A.by <= 256 && tensor_map_encoder() != nullptr;
+  if (tma) {
+    const cuuint64_t dims[3] = {(cuuint64_t)L.M[0], (cuuint64_t)L.M[1], (cuuint64_t)L.M[2]};
+    const cuuint64_t strides[2] = {(cuuint64_t)L.M[0] * 4, (cuuint64_t)(L.M[0] * L.M[1]) * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)A.bx, (cuuint32_t)A.by, (cuuint32_t)A.zb};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    tma = tensor_map_encoder()(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<TQ*>(Q), dims, strides, box,
+                               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
+  auto go = [&](auto kernel) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    kernel<<<L.nsub, kProjThreads, smem, st>>>(tmap, A, Q, BL, status);
+  };
+#define MFA_PROJ_NP(PP, NP)                                             \
+  if constexpr (sizeof(TQ) == 4) {                                      \
+    if (tma)                                                            \
+      go(k_project3d_ff<PP, kProjThreads, NP, true, TQ>);               \
+    else                                                                \
+      go(k_project3d_ff<PP, kProjThreads, NP, false, TQ>);              \
+  } else {                                                              \
+    go(k_project3d_ff<PP, kProjThreads, NP, false, TQ>);                \
+  }
+#define MFA_PROJ_CASE(PP)                 \
+  case PP:                                \
+    if (npairs <= 4 * kProjThreads) {     \
+      MFA_PROJ_NP(PP, 4)                  \
+    } else {                              \
+      MFA_PROJ_NP(PP, 8)                  \
+    }                                     \
+    return true;
   switch (P) {
     MFA_PROJ_CASE(2)
     MFA_PROJ_CASE(3)
@@ -373,12 +538,13 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
       return false;
   }
 #undef MFA_PROJ_CASE
+#undef MFA_PROJ_NP
 }
 
-template bool launch_project3d_ff<float>(const LayoutDev&, const long long*, int, int, int, int, bool, const float*,
-                                         ff*, int*, cudaStream_t);
-template bool launch_project3d_ff<double>(const LayoutDev&, const long long*, int, int, int, int, bool, const double*,
-                                          ff*, int*, cudaStream_t);
+template bool launch_project3d_ff<float>(const LayoutDev&, const long long*, int, int, int, int, int, bool,
+                                         const float*, ff*, int*, cudaStream_t);
+template bool launch_project3d_ff<double>(const LayoutDev&, const long long*, int, int, int, int, int, bool,
+                                          const double*, ff*, int*, cudaStream_t);
 
 }  // namespace mfa
 
@@ -429,7 +595,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode3d(LayoutDev L, const V* 
                                                           double* __restrict__ partials) {
   constexpr int W = P + 1;
   constexpr int CX = (kDecTX * 1) + P + 1;  // generous bound on control points per tile row
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const int ntx = (int)((L.M[0] + kDecTX - 1) / kDecTX), nty = (int)((L.M[1] + kDecTY - 1) / kDecTY);
   const int tile = blockIdx.x;
   const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
@@ -749,7 +915,7 @@ template <int P, int NT, int NPAIR, int NPRE>
 __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* __restrict__ Pg,
                                                          const ff* __restrict__ BL, ff* __restrict__ X) {
   constexpr int W = P + 1, B = 2 * P + 1, NG = NT / 32;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const LayoutDev& L = A.L;
   const int s = blockIdx.x;
   const int s0 = s % L.S[0], s1 = (s / L.S[0]) % L.S[1], s2 = s / (L.S[0] * L.S[1]);
@@ -1163,7 +1329,7 @@ template <int P>
 __global__ void __launch_bounds__(128) k_iter0_xy_ff(LayoutDev L, const long long* __restrict__ offL,
                                                      const ff* __restrict__ BL, ff* __restrict__ X) {
   constexpr int W = P + 1;
-  extern __shared__ __align__(16) unsigned char smem[];
+  extern __shared__ __align__(128) unsigned char smem[];
   const int s = blockIdx.x, lz0 = blockIdx.y * kIt0Planes;
   const int s0 = s % L.S[0], s1 = (s / L.S[0]) % L.S[1], s2 = s / (L.S[0] * L.S[1]);
   const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];

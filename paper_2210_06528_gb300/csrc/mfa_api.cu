@@ -488,7 +488,7 @@ void run_encode(mfa_model* md, const TQ* q) {
   if constexpr (std::is_same<T, ff>::value) {
     if (md->dim == 3 && md->use_fused) {
       TRACED(h, TR_PROJECT_DATA,
-             fused = launch_project3d_ff<TQ>(L, md->offL, md->maxm[0], md->maxm[1], md->maxnL[0], md->maxnL[1],
+             fused = launch_project3d_ff<TQ>(L, md->offL, md->maxm[0], md->maxm[1], md->maxm[2], md->maxnL[0], md->maxnL[1],
                                               md->x_inplace_ok, q, BL, h->d_status, h->stream));
     }
   }
@@ -665,6 +665,7 @@ const char* mfa_status_string(int s) {
     case MFA_ERR_DIVERGED: return "Schwarz iteration diverged";
     case MFA_ERR_NONFINITE: return "non-finite input data";
     case MFA_ERR_UNSUPPORTED: return "unsupported request";
+    case MFA_ERR_TIMEOUT: return "device wait on an asynchronous copy timed out";
     default: return "unknown status";
   }
 }

@@ -123,8 +123,8 @@ template <typename TIn, typename TOut>
 void launch_cast(const TIn* in, TOut* out, long long n, cudaStream_t st);
 
 template <typename TQ>
-bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, int maxm1, int maxn0, int maxn1,
-                         bool inplace_ok, const TQ* Q, ff* BL, int* status, cudaStream_t st);
+bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, int maxm1, int maxm2, int maxn0,
+                         int maxn1, bool inplace_ok, const TQ* Q, ff* BL, int* status, cudaStream_t st);
 
 template <typename V, typename TQ, typename TOut, bool RESID>
 bool launch_decode3d(const LayoutDev& L, const V* P, const TQ* Q, TOut* out, double* partials, cudaStream_t st);

@@ -27,6 +27,7 @@ MFA_ERR_NOT_SPD = -5
 MFA_ERR_DIVERGED = -6
 MFA_ERR_NONFINITE = -7
 MFA_ERR_UNSUPPORTED = -8
+MFA_ERR_TIMEOUT = -9
 MFA_F32, MFA_F64 = 0, 1
 MFA_PREC_FP64, MFA_PREC_MIXED = 0, 1
 
