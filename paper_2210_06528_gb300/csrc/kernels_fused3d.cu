@@ -1168,58 +1168,115 @@ bool launch_schwarz3d_ff(const LayoutDev& L, const long long* offL, const int* m
 // Update (Sec. 2.3.2) in float-float: P^k(g) = (1/n_s) sum of the owned copies
 // of g in a fixed order; metrics max|P^k - P^{k-1}|, max|P^k| and the copy
 // spread are formed from float-float differences, so no FP64 arithmetic runs.
-// One thread per control point on a 3-D grid (no index divisions).
+// A persistent grid walks the rows of control points along x, every copy of
+// a control point loaded independently before they are combined; the small
+// owner and offset tables sit in shared memory.
 // ---------------------------------------------------------------------------
 
 __constant__ float c_inv_hi[9], c_inv_lo[9];  // 1/n as float-float, n = 1..8
+constexpr int kAvgThreads = 256;
 
-__global__ void __launch_bounds__(128) k_average_ff(LayoutDev L, const long long* __restrict__ offL,
-                                                    const ff* __restrict__ X, ff* __restrict__ P,
-                                                    const ff* __restrict__ Pprev, float* __restrict__ part) {
-  const int g0 = blockIdx.x * blockDim.x + threadIdx.x;
-  const int g1 = blockIdx.y, g2 = blockIdx.z;
-  float dmax = 0.f, pmax = 0.f, spread = 0.f;
-  if (g0 < (int)L.ncp[0]) {
-    const int4 o0 = L.ax[0].own_tab[g0], o1 = L.ax[1].own_tab[g1], o2 = L.ax[2].own_tab[g2];
-    ff sum(0.f, 0.f), first(0.f, 0.f);
-    float dlo = 0.f, dhi = 0.f;
-    int cnt = 0;
+// Tables of the update kept in shared memory when they fit (else read from
+// global memory): owner entries of every axis, L sizes, copy offsets.
+struct AvgTabs {
+  const int4 *ot0, *ot1, *ot2;
+  const int *nl0, *nl1;
+  const long long* off;
+};
+
+// All copies of control point (g0, g1, g2), loaded independently: slot
+// c = c0 + 2 c1 + 4 c2 picks owner c_a along axis a.
+struct AvgCopies {
+  ff v[8];
+  unsigned ok;
+  ff prev;
+};
+
+__device__ __forceinline__ void avg_load(const LayoutDev& L, const AvgTabs& T, const ff* __restrict__ X,
+                                         const ff* __restrict__ Pprev, long long g, int4 o0, int4 o1, int4 o2,
+                                         AvgCopies& cp) {
+  cp.prev = Pprev ? Pprev[g] : ff(0.f, 0.f);
+  cp.ok = 0u;
 #pragma unroll
-    for (int c2 = 0; c2 < 2; ++c2) {
-      const int sa2 = c2 ? o2.z : o2.x, li2 = c2 ? o2.w : o2.y;
-#pragma unroll
-      for (int c1 = 0; c1 < 2; ++c1) {
-        const int sa1 = c1 ? o1.z : o1.x, li1 = c1 ? o1.w : o1.y;
-#pragma unroll
-        for (int c0 = 0; c0 < 2; ++c0) {
-          const int sa0 = c0 ? o0.z : o0.x, li0 = c0 ? o0.w : o0.y;
-          if (sa0 < 0 || sa1 < 0 || sa2 < 0) continue;
-          const int nL0 = L.ax[0].nL_tab[sa0], nL1 = L.ax[1].nL_tab[sa1];
-          const int s = sa0 + L.S[0] * (sa1 + L.S[1] * sa2);
-          const int li = li0 + nL0 * (li1 + nL1 * li2);
-          const ff v = X[offL[s] + li];
-          if (cnt == 0) {
-            sum = v;
-            first = v;
-          } else {
-            sum = sum + v;
-            const ff d = v - first;
-            const float df = d.hi + d.lo;
-            dlo = fminf(dlo, df);
-            dhi = fmaxf(dhi, df);
-          }
-          ++cnt;
-        }
-      }
+  for (int c = 0; c < 8; ++c) {
+    const int c0 = c & 1, c1 = (c >> 1) & 1, c2 = c >> 2;
+    const int sa0 = c0 ? o0.z : o0.x, li0 = c0 ? o0.w : o0.y;
+    const int sa1 = c1 ? o1.z : o1.x, li1 = c1 ? o1.w : o1.y;
+    const int sa2 = c2 ? o2.z : o2.x, li2 = c2 ? o2.w : o2.y;
+    const bool ok = sa0 >= 0 && sa1 >= 0 && sa2 >= 0;
+    cp.v[c] = ff(0.f, 0.f);
+    if (ok) {
+      const int s = sa0 + L.S[0] * (sa1 + L.S[1] * sa2);
+      const long long li = li0 + (long long)T.nl0[sa0] * (li1 + (long long)T.nl1[sa1] * li2);
+      cp.v[c] = X[T.off[s] + li];
+      cp.ok |= 1u << c;
     }
-    const ff pn = cnt == 1 ? sum : sum * ff(c_inv_hi[cnt], c_inv_lo[cnt]);
-    const long long g = (long long)g0 + L.ncp[0] * ((long long)g1 + L.ncp[1] * g2);
-    P[g] = pn;
-    pmax = fabsf(pn.hi);
-    spread = dhi - dlo;
-    if (Pprev) {
-      const ff d = pn - Pprev[g];
-      dmax = fabsf(d.hi + d.lo);
+  }
+}
+
+__device__ __forceinline__ void avg_finish(const AvgCopies& cp, bool has_prev, long long g, ff* __restrict__ P,
+                                           float& dmax, float& pmax, float& spread) {
+  ff sum(0.f, 0.f), first(0.f, 0.f);
+  float dlo = 0.f, dhi = 0.f;
+  int cnt = 0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    if (!(cp.ok & (1u << c))) continue;
+    if (cnt == 0) {
+      sum = cp.v[c];
+      first = cp.v[c];
+    } else {
+      sum = sum + cp.v[c];
+      const ff d = cp.v[c] - first;
+      const float df = d.hi + d.lo;
+      dlo = fminf(dlo, df);
+      dhi = fmaxf(dhi, df);
+    }
+    ++cnt;
+  }
+  const ff pn = cnt == 1 ? sum : sum * ff(c_inv_hi[cnt], c_inv_lo[cnt]);
+  P[g] = pn;
+  pmax = fmaxf(pmax, fabsf(pn.hi));
+  spread = fmaxf(spread, dhi - dlo);
+  if (has_prev) {
+    const ff d = pn - cp.prev;
+    dmax = fmaxf(dmax, fabsf(d.hi + d.lo));
+  }
+}
+
+__global__ void __launch_bounds__(kAvgThreads, 4) k_average_ff(LayoutDev L, const long long* __restrict__ offL,
+                                                               const ff* __restrict__ X, ff* __restrict__ P,
+                                                               const ff* __restrict__ Pprev, float* __restrict__ part,
+                                                               int stage_tables) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int n0 = (int)L.ncp[0], n1 = (int)L.ncp[1], n2 = (int)L.ncp[2];
+  AvgTabs T{L.ax[0].own_tab, L.ax[1].own_tab, L.ax[2].own_tab, L.ax[0].nL_tab, L.ax[1].nL_tab, offL};
+  if (stage_tables) {
+    int4* t0 = reinterpret_cast<int4*>(smem);
+    int4* t1 = t0 + n0;
+    int4* t2 = t1 + n1;
+    long long* off = reinterpret_cast<long long*>(t2 + n2);
+    int* l0 = reinterpret_cast<int*>(off + L.nsub);
+    int* l1 = l0 + L.S[0];
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) t0[i] = T.ot0[i];
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) t1[i] = T.ot1[i];
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) t2[i] = T.ot2[i];
+    for (int i = threadIdx.x; i < L.nsub; i += blockDim.x) off[i] = offL[i];
+    for (int i = threadIdx.x; i < L.S[0]; i += blockDim.x) l0[i] = T.nl0[i];
+    for (int i = threadIdx.x; i < L.S[1]; i += blockDim.x) l1[i] = T.nl1[i];
+    __syncthreads();
+    T = AvgTabs{t0, t1, t2, l0, l1, off};
+  }
+  float dmax = 0.f, pmax = 0.f, spread = 0.f;
+  const long long nrows = (long long)n1 * n2;
+  for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const int g1 = (int)(r % n1), g2 = (int)(r / n1);
+    const int4 o1 = T.ot1[g1], o2 = T.ot2[g2];
+    for (int g0 = threadIdx.x; g0 < n0; g0 += blockDim.x) {
+      const long long g = (long long)g0 + (long long)n0 * r;
+      AvgCopies cp;
+      avg_load(L, T, X, Pprev, g, T.ot0[g0], o1, o2, cp);
+      avg_finish(cp, Pprev != nullptr, g, P, dmax, pmax, spread);
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -1227,7 +1284,7 @@ __global__ void __launch_bounds__(128) k_average_ff(LayoutDev L, const long long
     pmax = fmaxf(pmax, __shfl_down_sync(0xffffffffu, pmax, o));
     spread = fmaxf(spread, __shfl_down_sync(0xffffffffu, spread, o));
   }
-  __shared__ float red[3][4];
+  __shared__ float red[3][kAvgThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     red[0][wid] = dmax;
@@ -1237,15 +1294,14 @@ __global__ void __launch_bounds__(128) k_average_ff(LayoutDev L, const long long
   __syncthreads();
   if (threadIdx.x == 0) {
     float a = red[0][0], b = red[1][0], c = red[2][0];
-    for (int w = 1; w < 4; ++w) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
       a = fmaxf(a, red[0][w]);
       b = fmaxf(b, red[1][w]);
       c = fmaxf(c, red[2][w]);
     }
-    const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
-    part[3 * blk + 0] = a;
-    part[3 * blk + 1] = b;
-    part[3 * blk + 2] = c;
+    part[3 * blockIdx.x + 0] = a;
+    part[3 * blockIdx.x + 1] = b;
+    part[3 * blockIdx.x + 2] = c;
   }
 }
 
@@ -1287,7 +1343,7 @@ __global__ void k_metrics_reduce(const float* __restrict__ part, long long nblk,
   }
 }
 
-long long average_ff_blocks(const LayoutDev& L) { return ((L.ncp[0] + 127) / 128) * L.ncp[1] * L.ncp[2]; }
+long long average_ff_blocks(const LayoutDev&) { return kAvgBlocks; }
 
 // `part` holds 3 floats per block of the launch (average_ff_blocks).
 void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev, float* part,
@@ -1306,8 +1362,11 @@ void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, f
     cudaMemcpyToSymbol(c_inv_lo, l, sizeof(l));
     init[dev] = true;
   }
-  dim3 grid((unsigned)((L.ncp[0] + 127) / 128), (unsigned)L.ncp[1], (unsigned)L.ncp[2]);
-  k_average_ff<<<grid, 128, 0, st>>>(L, offL, X, P, Pprev, part);
+  const int threads = (int)std::min<long long>(kAvgThreads, ((L.ncp[0] + 31) / 32) * 32);
+  const size_t tab = (size_t)(L.ncp[0] + L.ncp[1] + L.ncp[2]) * sizeof(int4) + (size_t)L.nsub * sizeof(long long) +
+                     (size_t)(L.S[0] + L.S[1]) * sizeof(int);
+  const int stage = tab <= 40 * 1024;
+  k_average_ff<<<kAvgBlocks, threads, stage ? tab : 0, st>>>(L, offL, X, P, Pprev, part, stage);
   cudaMemsetAsync(metrics, 0, 3 * sizeof(unsigned long long), st);
   k_metrics_reduce<<<152, 256, 0, st>>>(part, average_ff_blocks(L), metrics);
 }

@@ -833,7 +833,7 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
   const long long ncp = (long long)md->axh[0].n * md->axh[1].n * md->axh[2].n;
   const size_t o_P = bg.take<char>(ncp * es), o_Pp = bg.take<char>(ncp * es);
   const size_t o_S1 = bg.take<char>(md->sizeS1 * es), o_S2 = bg.take<char>(md->sizeS2 * es);
-  const size_t o_part = bg.take<float>(3 * (size_t)(((md->axh[0].n + 127) / 128) * md->axh[1].n * md->axh[2].n));
+  const size_t o_part = bg.take<float>(3 * (size_t)kAvgBlocks);
   // host data staging: the data are copied into the pool before use
   const size_t qbytes = (size_t)npts_total * (q_dtype == MFA_F64 ? 8 : 4);
   const size_t o_Q = q_on_device ? 0 : bg.take<char>(qbytes);

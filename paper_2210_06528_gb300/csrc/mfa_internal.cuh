@@ -138,5 +138,6 @@ void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, f
                        unsigned long long* metrics, cudaStream_t st);
 
 constexpr int kResidualBlocks = 1216;  // 8 x 152 SMs
+constexpr int kAvgBlocks = 152 * 4;     // persistent float-float update: four CTAs per SM
 
 }  // namespace mfa
