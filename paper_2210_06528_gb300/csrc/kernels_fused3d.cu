@@ -71,8 +71,8 @@ __device__ __forceinline__ float to_f(TQ x) {
 //                accumulators walks the row four points at a time, each point
 //                adding its P+1 basis products; a control point is emitted
 //                (in place, over consumed data) when the span moves past it.
-//   stage 2 (y): one thread per (plane, x-control point, chunk of y-control
-//                points), same sliding window down the column.
+//   stage 2 (y): one thread per output (plane, y-control point, x-control
+//                point), summing the rows of the P+1 spans that support it.
 //   stage 3 (z): every thread owns NPAIR (x,y) control-point pairs and keeps
 //                a ring of P+1 accumulators per pair across the planes; a
 //                z-control point is written to B_L when the planes' span
@@ -85,7 +85,7 @@ struct Proj3dArgs {
   LayoutDev L;
   const long long* offL;
   int zb;        // planes per batch (box z)
-  int nch2;      // y-chunks per column in stage 2
+  int lx_shift;  // stage 2: log2 of the lanes per (plane, y-control point) group, 2^shift >= max L along x
   int bx;        // staged row pitch in floats = box x; multiple of 4, = 4 (mod 8)
   int by;        // staged rows per plane = box y = largest window along y
   int mz;        // largest window along z
@@ -340,43 +340,40 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
         }
     }
     __syncthreads();
-    // ---- stage 2: columns along y, chunked over the y-control points
+    // ---- stage 2 (gather form): one warp-aligned group of lanes per (plane,
+    // y-control point), lanes along x-control points; each output sums its
+    // P+1 supporting spans' rows, so the work per output is even and no row
+    // is read for a control point it does not touch
     {
-      const int nch = A.nch2;
-      const int csz = (n1 + nch - 1) / nch;
       const int* ss = L.ax[1].span_start;
-      for (int t = threadIdx.x; t < nz * n0 * nch; t += NT) {
-        const int zz = t / (n0 * nch);
-        const int rem = t - zz * n0 * nch;
-        const int ch = rem / n0, lx = rem - ch * n0;
-        const int c0 = ch * csz, c1 = min(n1, c0 + csz);
-        if (c0 >= c1) continue;
-        // rows whose span reaches control points [c0, c1): span in [c0-P, c1-1]
-        const int gs0 = max(by.l0 + c0 - P, 0), gs1 = min(by.l0 + c1, L.ax[1].nspans);
-        const int y0 = max(ss[gs0] - by.k0, 0), y1 = min(ss[gs1] - by.k0, m1);
-        const float* colf = Qs + (size_t)zz * BY * BX + 2 * lx;
-        ff* o = T2 + zz * n1 * n0 + lx;
-        ff win[W];
-#pragma unroll
-        for (int r = 0; r < W; ++r) win[r] = ff(0.f, 0.f);
-        int cur = y0 < m1 ? spy[y0] : c1;
-        for (int y = y0; y < y1; ++y) {
-          const int sy = spy[y];
-          while (cur < sy) {
-            if (cur >= c0 && cur < c1) o[cur * n0] = AccFF::finish(win[0]);
-#pragma unroll
-            for (int r = 0; r < P; ++r) win[r] = win[r + 1];
-            win[P] = ff(0.f, 0.f);
-            ++cur;
+      const int sh = A.lx_shift;                 // lanes per group = 1 << sh >= n0
+      const int lmask = (1 << sh) - 1;
+      const int lx = threadIdx.x & lmask;
+      const int gstep = NT >> sh;                // groups advanced per pass
+      int c1 = threadIdx.x >> sh, zz = 0;
+      while (c1 >= n1) {
+        c1 -= n1;
+        ++zz;
+      }
+      for (; zz < nz; ) {
+        if (lx < n0) {
+          const int g1 = by.l0 + c1;
+          const int ys = max(ss[max(g1 - P, 0)] - by.k0, 0);
+          const int ye = min(ss[min(g1, L.ax[1].nspans - 1) + 1] - by.k0, m1);
+          const float* colf = Qs + (size_t)zz * BY * BX + 2 * lx;
+          ff acc(0.f, 0.f);
+          for (int y = ys; y < ye; ++y) {
+            const int r = c1 - spy[y];
+            const float2 xv = *reinterpret_cast<const float2*>(colf + (size_t)y * BX);
+            AccFF::add_v(acc, tyh[y * W + r], tyl[y * W + r], ff(xv.x, xv.y));
           }
-          const float2 xv = *reinterpret_cast<const float2*>(colf + (size_t)y * BX);
-          const ff x(xv.x, xv.y);
-#pragma unroll
-          for (int r = 0; r < W; ++r) AccFF::add_v(win[r], tyh[y * W + r], tyl[y * W + r], x);
+          T2[(zz * n1 + c1) * n0 + lx] = AccFF::finish(acc);
         }
-#pragma unroll
-        for (int r = 0; r < W; ++r)
-          if (cur + r >= c0 && cur + r < c1) o[(cur + r) * n0] = AccFF::finish(win[r]);
+        c1 += gstep;
+        while (c1 >= n1) {
+          c1 -= n1;
+          ++zz;
+        }
       }
     }
     // the staged rows are free again: order this CTA's shared-memory accesses
@@ -490,7 +487,9 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
     smem = proj_smem_layout(W, A.zb, A.bx, A.by, A.mz, A.n0, A.n1).total;
   }
   if (smem > 200 * 1024 || npairs > 8 * kProjThreads) return false;
-  A.nch2 = std::max(1, kProjThreads / std::max(1, A.zb * maxn0));
+  A.lx_shift = 5;
+  while ((1 << A.lx_shift) < maxn0) ++A.lx_shift;
+  if ((1 << A.lx_shift) > kProjThreads) return false;
 
   // the tensor copy takes FP32 data on a 16-byte aligned base with rows a
   // multiple of 16 bytes long and boxes of at most 256 per dimension
