@@ -195,6 +195,45 @@ def run_reference(args, wl):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def window_sizes(M, nspans, S, delta, p):
+    """(points, L size) of every subdomain window along one axis: cores split
+    the spans evenly (the first nspans % S take one more), windows add delta
+    spans per interior side, points are those with u_k = k/(M-1) in the
+    closed window interval, L = window spans + p."""
+    out, a = [], 0
+    for i in range(S):
+        c = nspans // S + (1 if i < nspans % S else 0)
+        b = a + c
+        w0, w1 = max(a - delta, 0), min(b + delta, nspans)
+        k0 = -((-w0 * (M - 1)) // nspans)
+        k1 = (w1 * (M - 1)) // nspans
+        out.append((k1 - k0 + 1, (w1 - w0) + p))
+        a = b
+    return out
+
+
+# FP32 instructions of one float-float multiply-add: float x float-float
+# (exact product + TwoSum accumulate) and float-float x float-float
+FF_OPS_F, FF_OPS_V = 11, 12
+
+
+def projection_ops(wl):
+    """Algorithmic FP32 operations of one 3-D float-float projection launch:
+    per window point (P+1) float x float-float multiply-adds on the first
+    axis, then (P+1) float-float x float-float multiply-adds per element of
+    the x-reduced and xy-reduced arrays."""
+    W = wl["p"] + 1
+    ax = [window_sizes(wl["npts"][a], wl["nspans"][a], wl["nsub"][a], wl["delta"], wl["p"]) for a in range(3)]
+    sm = [sum(m for m, _ in ax[a]) for a in range(3)]
+    sn = [sum(n for _, n in ax[a]) for a in range(3)]
+    return W * (FF_OPS_F * sm[0] * sm[1] * sm[2] + FF_OPS_V * sn[0] * sm[1] * sm[2] + FF_OPS_V * sn[0] * sn[1] * sm[2])
+
+
+def alu_peak_tops(clock_mhz):
+    """FP32 lane instructions per second: 152 SMs x 128 FP32 lanes x SM clock."""
+    return 152 * 128 * clock_mhz * 1e6 / 1e12
+
+
 def algorithmic_bytes(cls_name, wl, qbytes, model_info):
     """Algorithmic bytes of one launch of a kernel class (what the method must
     move): the data-reading kernels read every data value once."""
@@ -289,14 +328,43 @@ def run_gb300(args, wl):
     m.free()
     del out
 
-    # ---- end to end through the C ABI with pinned host buffers
+    # ---- comparator: the plain per-subdomain FP64 form (one launch per
+    # subdomain and stage, window data re-read every iteration), same stop
+    lay64 = mfa.make_layout(d, wl["p"], npts, wl["nspans"], wl["nsub"], [wl["delta"]] * d, mfa.MFA_PREC_FP64)
+    plain = None
+    if not args.no_plain:
+        def step_plain():
+            m, rc, rep = h.encode_plain(q_dev, lay64, wl["max_iters"], wl["tol"])
+            r = m.residual(q_dev)
+            m.free()
+            return rep, r
+        step_plain()
+        torch.cuda.synchronize()
+        mfa.mfa_trace_enable(h.h, True)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        prep, pres = step_plain()
+        p1.record(stream)
+        torch.cuda.synchronize()
+        ptrace = mfa.trace_table(h.h)
+        mfa.mfa_trace_enable(h.h, False)
+        plain_ms = p0.elapsed_time(p1)
+        plain = {"value": world * M / (plain_ms * 1e-3), "unit": "pts/s", "ms_per_step": plain_ms,
+                 "precision": "fp64", "schwarz_iters": prep.iters, "rms_decoded": pres.rms_decoded,
+                 "gpu_launches": sum(n for (_, n) in ptrace.values()),
+                 "form": "one launch per subdomain and stage; window data re-read every iteration"}
+
+    # ---- end to end through the C ABI with pinned host buffers: the data
+    # cross to the device once (encode stages them; the residual reuses that
+    # copy) and the fitted control points come back into a pinned buffer
+    P_host = torch.empty(ncp, dtype=torch.float64).pin_memory()
+
     def step_e2e():
         m = h.encode(q_host, lay)  # host -> device copy inside
         m.iterate(wl["max_iters"], wl["tol"])
-        m.residual(q_host)  # second host -> device copy of the data
-        P = m.ctrl()  # device -> host read of the control points
+        m.residual(None)  # against the staged copy
+        m.ctrl(out=P_host)  # device -> host read of the control points
         m.free()
-        return P
 
     step_e2e()
     torch.cuda.synchronize()
@@ -310,7 +378,7 @@ def run_gb300(args, wl):
         tt = torch.tensor([e2e_s], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_s = float(tt.item())
-    e2e = {"value": world * M / e2e_s, "unit": "pts/s", "h2d_bytes_per_step": 2 * qbytes,
+    e2e = {"value": world * M / e2e_s, "unit": "pts/s", "h2d_bytes_per_step": qbytes,
            "d2h_bytes_per_step": ncp * 8}
 
     # ---- roofline of the dominant kernel class
@@ -325,20 +393,35 @@ def run_gb300(args, wl):
         ms_per = trace[name][0] / trace[name][1]
         ab = algorithmic_bytes(name, wl, qbytes, None)
         achieved = ab / (ms_per * 1e-3) / 1e9
+        hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
+               "algorithmic_bytes_per_launch": ab}
         roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": ab, "ms_per_launch": ms_per}
+        if name == "project_data" and d == 3 and prec == mfa.MFA_PREC_MIXED:
+            # the float-float projection is bound by the FP32 pipes, not by HBM
+            mhz = (clocks or {}).get("sm_mhz")
+            src = "median SM clock under load" if mhz else "maximum SM clock, no clock samples"
+            mhz = mhz or 2070.0
+            ops = projection_ops(wl)
+            ach = ops / (ms_per * 1e-3) / 1e12
+            pk = alu_peak_tops(mhz)
+            roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                    "traffic": None, "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src})",
+                    "op_convention": "one FP32 add, mul or fma instruction = 1 op",
+                    "algorithmic_ops_per_launch": ops, "ms_per_launch": ms_per, "hbm_view": hbm}
     if rank != 0:
         return
     cpu = cpu_baseline(wl, budget_s=args.cpu_budget) if world == 1 and not args.no_cpu else None
     line = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32" if prec == mfa.MFA_PREC_MIXED else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32x2" if prec == mfa.MFA_PREC_MIXED else "f64", "data": "synthetic",
             "config": {"workload": wl["name"], "points": M, "control_points": ncp, "precision": wl["precision"],
                        "stop": f"dP_rel <= {wl['tol']:g}", "schwarz_iters": sorted(set(iters_seen)),
                        "l2": "inputs larger than L2" if qbytes > 129e6 else "inputs smaller than L2",
                        "parallelism": f"replicas x{world}"},
             "decode_pts_per_s": world * M / (dec_ms * 1e-3), "decode_ms": dec_ms,
+            "plain_gpu": plain, "vs_plain_gpu": (value / plain["value"]) if plain else None,
             "roofline": roof, "dominant_kernel": dom[0] if dom else None, "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks,
@@ -355,6 +438,7 @@ def main():
     ap.add_argument("--workload", default="3d", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the per-subdomain comparator run")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

@@ -157,8 +157,27 @@ int mfa_schwarz_iterate(mfa_handle* h, mfa_model* m, int32_t max_iters, double t
 int mfa_decode(mfa_handle* h, const mfa_model* m, const double* pts, int64_t npts_q,
                const int32_t* deriv, void* out, int out_dtype, int out_on_device);
 
+/* The per-subdomain comparator form of encode + Schwarz iteration (the
+ * plain FP64 method as a straightforward GPU port would run it; no
+ * counterpart entry point in the paper, which runs one MPI task per
+ * subdomain): the same arithmetic as MFA_PREC_FP64, but every data-sized
+ * stage (projection of the window data, band products, banded solves) is one
+ * launch per subdomain and axis, and every Schwarz iteration re-reads the
+ * window data from q to rebuild the local right-hand sides.  Requires
+ * lay->precision == MFA_PREC_FP64.  Device data must stay valid until the
+ * call returns (it synchronises); host data are staged once.  Runs up to
+ * max_iters iterations (stop at dP_rel <= tol_dP) and returns the fitted
+ * model, usable with every other call, in *out; statuses as
+ * mfa_schwarz_iterate (on a negative status no model is returned). */
+int mfa_encode_plain(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype, int q_on_device,
+                     int32_t max_iters, double tol_dP, mfa_report* rep, mfa_model** out);
+
 /* Decoded error E = Q - R P over the full grid (Algorithm 1 "update local
- * error"): fills rep->rms_decoded, maxabs_decoded, data_range.  Synchronous. */
+ * error"): fills rep->rms_decoded, maxabs_decoded, data_range.  Synchronous.
+ * q == NULL uses the device copy that mfa_encode made of host data for this
+ * model (kept until mfa_free), so a host-data encode plus its residual moves
+ * the data across the link once; MFA_ERR_ARG if the model was encoded from
+ * device data (q_dtype and q_on_device are then ignored). */
 int mfa_residual(mfa_handle* h, const mfa_model* m, const void* q, int q_dtype,
                  int q_on_device, mfa_report* rep);
 

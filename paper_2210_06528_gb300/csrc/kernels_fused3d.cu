@@ -913,7 +913,7 @@ __device__ __forceinline__ void solve_fibre_ff(ff* x, int n, int s, const float*
 template <int P, int NT, int NPAIR, int NPRE>
 __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* __restrict__ Pg,
                                                          const ff* __restrict__ BL, ff* __restrict__ X) {
-  constexpr int W = P + 1, B = 2 * P + 1, NG = NT / 32;
+  constexpr int W = P + 1, B = 2 * P + 1, NG = NT / 32, XR = 4;
   extern __shared__ __align__(128) unsigned char smem[];
   const LayoutDev& L = A.L;
   const int s = blockIdx.x;
@@ -1001,17 +1001,30 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
     }
     __syncthreads();
     if (lz < lz_hi) fetch(lz + 1);
-    // x band product, owned x rows
+    // x band product, owned x rows; XR independent rows per thread in flight
     if (xin) {
       const int c0 = oU0 + ux - P;
-      for (int ly = grp; ly < nL1; ly += NG) {
-        ff acc(0.f, 0.f);
+      for (int ly0 = grp; ly0 < nL1; ly0 += XR * NG) {
+        ff acc[XR];
+#pragma unroll
+        for (int k = 0; k < XR; ++k) acc[k] = ff(0.f, 0.f);
 #pragma unroll
         for (int e = 0; e < B; ++e) {
           const int c = c0 + e;
-          if (c >= 0 && c < nL0) AccFF::add_v(acc, axh[ux * B + e], axl[ux * B + e], Pp[ly * nL0 + c]);
+          if (c >= 0 && c < nL0) {
+            const float h = axh[ux * B + e], l = axl[ux * B + e];
+#pragma unroll
+            for (int k = 0; k < XR; ++k) {
+              const int ly = ly0 + k * NG;
+              if (ly < nL1) AccFF::add_v(acc[k], h, l, Pp[ly * nL0 + c]);
+            }
+          }
         }
-        Y1[ly * nU0 + ux] = AccFF::finish(acc);
+#pragma unroll
+        for (int k = 0; k < XR; ++k) {
+          const int ly = ly0 + k * NG;
+          if (ly < nL1) Y1[ly * nU0 + ux] = AccFF::finish(acc[k]);
+        }
       }
     }
     __syncthreads();

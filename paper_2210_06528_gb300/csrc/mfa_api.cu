@@ -42,6 +42,11 @@ struct mfa_handle {
 
 struct mfa_model {
   mfa_handle* h = nullptr;
+  const void* q_staged = nullptr;  // device copy of host data given to mfa_encode (inside `big`)
+  int q_staged_dtype = MFA_F32;
+  bool plain = false;              // per-subdomain comparator form (mfa_encode_plain)
+  const void* q_src = nullptr;     // plain form: the device data it re-reads every iteration
+  int q_src_dtype = MFA_F32;
   int prec = MFA_PREC_FP64;
   int dim = 1;
   int degree = 1;
@@ -472,6 +477,30 @@ T* at_off(void* base, size_t off) {
 }
 
 // Launch the projection N^T Q (all subdomains) and iteration 0.
+// Projection B_L of every window, one subdomain per launch and axis (the
+// per-subdomain comparator form; the data are read again on every call).
+template <typename T, typename TQ>
+void plain_project(mfa_model* md, const TQ* q) {
+  mfa_handle* h = md->h;
+  const LayoutDev& L = md->L;
+  const int ns = md->nsub;
+  T* BL = (T*)md->BL;
+  T* S1 = (T*)md->S1;
+  T* S2 = (T*)md->S2;
+  auto opsk = [&](int kind) { return md->ops + (size_t)kind * ns; };
+  for (int sd = 0; sd < ns; ++sd)
+    for (int a = 0; a < md->dim; ++a) {
+      T* out = (a == md->dim - 1) ? BL : (a == 0 ? S1 : S2);
+      if (a == 0)
+        TRACED(h, TR_PROJECT_DATA,
+               (launch_contract<T, TQ>(L, 0, opsk(OP_PROJ0) + sd, 1, md->maxOut[0], q, out, h->d_status, h->stream)));
+      else
+        TRACED(h, TR_PROJECT_REDUCED,
+               (launch_contract<T, T>(L, a, opsk(OP_PROJ0 + a) + sd, 1, md->maxOut[a], a == 1 ? S1 : S2, out, nullptr,
+                                      h->stream)));
+    }
+}
+
 template <typename T, typename TQ>
 void run_encode(mfa_model* md, const TQ* q) {
   mfa_handle* h = md->h;
@@ -491,6 +520,10 @@ void run_encode(mfa_model* md, const TQ* q) {
              fused = launch_project3d_ff<TQ>(L, md->offL, md->maxm[0], md->maxm[1], md->maxm[2], md->maxnL[0], md->maxnL[1],
                                               md->x_inplace_ok, q, BL, h->d_status, h->stream));
     }
+  }
+  if (md->plain) {
+    plain_project<T, TQ>(md, q);
+    fused = true;
   }
   for (int a = 0; a < md->dim && !fused; ++a) {
     T* out = (a == md->dim - 1) ? BL : (a == 0 ? S1 : S2);
@@ -512,8 +545,15 @@ void run_encode(mfa_model* md, const TQ* q) {
     }
   }
   if (!it0) cudaMemcpyAsync(X, BL, md->sizeL * sizeof(T), cudaMemcpyDeviceToDevice, h->stream);
-  for (int a = 0; a < md->dim && !it0; ++a)
-    TRACED(h, TR_SOLVE_L, launch_band_solve<T>(L, a, false, opsk(OP_SOLVEL0 + a), ns, md->maxFibL[a], X, h->stream));
+  for (int a = 0; a < md->dim && !it0; ++a) {
+    if (md->plain) {
+      for (int sd = 0; sd < ns; ++sd)
+        TRACED(h, TR_SOLVE_L,
+               launch_band_solve<T>(L, a, false, opsk(OP_SOLVEL0 + a) + sd, 1, md->maxFibL[a], X, h->stream));
+    } else {
+      TRACED(h, TR_SOLVE_L, launch_band_solve<T>(L, a, false, opsk(OP_SOLVEL0 + a), ns, md->maxFibL[a], X, h->stream));
+    }
+  }
   cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
   if constexpr (std::is_same<T, ff>::value) {
     if (md->use_fused) {
@@ -549,19 +589,40 @@ void run_step(mfa_model* md) {
       }
     }
   }
+  if (md->plain) {
+    // the comparator form re-reads the data of every window each iteration
+    if (md->q_src_dtype == MFA_F64)
+      plain_project<T, double>(md, (const double*)md->q_src);
+    else
+      plain_project<T, float>(md, (const float*)md->q_src);
+  }
   TRACED(h, TR_FRAME_GATHER, launch_frame_gather<T>(L, md->offS2, md->maxL, (const T*)md->Pprev, S2, h->stream));
   for (int a = 0; a < md->dim; ++a) {
     const T* in = (a % 2 == 0) ? S2 : S1;
     T* out = (a % 2 == 0) ? S1 : S2;
-    TRACED(h, TR_BAND_APPLY, launch_band_apply<T>(L, a, opsk(OP_APPLY0 + a), ns, md->maxApply[a], in, out, h->stream));
+    if (md->plain) {
+      for (int sd = 0; sd < ns; ++sd)
+        TRACED(h, TR_BAND_APPLY,
+               launch_band_apply<T>(L, a, opsk(OP_APPLY0 + a) + sd, 1, md->maxApply[a], in, out, h->stream));
+    } else {
+      TRACED(h, TR_BAND_APPLY,
+             launch_band_apply<T>(L, a, opsk(OP_APPLY0 + a), ns, md->maxApply[a], in, out, h->stream));
+    }
   }
   const T* Y = (md->dim % 2 == 1) ? S1 : S2;
   const long long* offY = (md->dim % 2 == 1) ? md->offS1 : md->offS2;
   TRACED(h, TR_RHS_FINALIZE,
          launch_rhs_finalize<T>(L, md->offL, offY, md->maxU, (const T*)md->BL, Y, (T*)md->X, h->stream));
-  for (int a = 0; a < md->dim; ++a)
-    TRACED(h, TR_SOLVE_U,
-           launch_band_solve<T>(L, a, true, opsk(OP_SOLVEU0 + a), ns, md->maxFibU[a], (T*)md->X, h->stream));
+  for (int a = 0; a < md->dim; ++a) {
+    if (md->plain) {
+      for (int sd = 0; sd < ns; ++sd)
+        TRACED(h, TR_SOLVE_U,
+               launch_band_solve<T>(L, a, true, opsk(OP_SOLVEU0 + a) + sd, 1, md->maxFibU[a], (T*)md->X, h->stream));
+    } else {
+      TRACED(h, TR_SOLVE_U,
+             launch_band_solve<T>(L, a, true, opsk(OP_SOLVEU0 + a), ns, md->maxFibU[a], (T*)md->X, h->stream));
+    }
+  }
   cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
   TRACED(h, TR_AVERAGE,
          launch_average<T>(L, md->offL, (const T*)md->X, (T*)md->P, (const T*)md->Pprev, h->d_metrics, h->stream));
@@ -725,7 +786,32 @@ int mfa_destroy(mfa_handle* h) {
   return MFA_OK;
 }
 
+namespace {
+int encode_impl(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype, int q_on_device, bool plain,
+                mfa_model** out);
+}
+
 int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype, int q_on_device, mfa_model** out) {
+  return encode_impl(h, lay, q, q_dtype, q_on_device, false, out);
+}
+
+int mfa_encode_plain(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype, int q_on_device,
+                     int32_t max_iters, double tol_dP, mfa_report* rep, mfa_model** out) {
+  if (!h || !lay || !out || max_iters < 0) return MFA_ERR_ARG;
+  if (lay->precision != MFA_PREC_FP64) return MFA_ERR_ARG;
+  int rc = encode_impl(h, lay, q, q_dtype, q_on_device, true, out);
+  if (rc != MFA_OK) return rc;
+  rc = mfa_schwarz_iterate(h, *out, max_iters, tol_dP, rep);
+  if (rc < 0) {
+    mfa_free(*out);
+    *out = nullptr;
+  }
+  return rc;
+}
+
+namespace {
+int encode_impl(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype, int q_on_device, bool plain,
+                mfa_model** out) {
   if (!h || !lay || !q || !out) return MFA_ERR_ARG;
   *out = nullptr;
   if (lay->dim < 1 || lay->dim > MFA_MAX_DIM) return MFA_ERR_ARG;
@@ -736,6 +822,8 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
   mfa_model* md = new (std::nothrow) mfa_model();
   if (!md) return MFA_ERR_OOM;
   md->h = h;
+  md->plain = plain;
+  if (plain) md->use_fused = false;
   md->prec = lay->precision;
   md->dim = lay->dim;
   md->degree = lay->degree;
@@ -903,7 +991,11 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
     if (e == cudaSuccess) e = cudaMemcpyAsync(qbuf, q, qbytes, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     qd = qbuf;
+    md->q_staged = qbuf;
+    md->q_staged_dtype = q_dtype;
   }
+  md->q_src = qd;
+  md->q_src_dtype = q_dtype;
   if (md->prec == MFA_PREC_FP64) {
     if (q_dtype == MFA_F64)
       run_encode<double, double>(md, (const double*)qd);
@@ -927,6 +1019,7 @@ int mfa_encode(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype,
   *out = md;
   return MFA_OK;
 }
+}  // namespace
 
 int mfa_schwarz_iterate(mfa_handle* h, mfa_model* md, int32_t max_iters, double tol_dP, mfa_report* rep) {
   if (!h || !md || md->h != h || max_iters < 0) return MFA_ERR_ARG;
@@ -1044,7 +1137,13 @@ int mfa_decode(mfa_handle* h, const mfa_model* mdc, const double* pts, int64_t n
 
 int mfa_residual(mfa_handle* h, const mfa_model* mdc, const void* q, int q_dtype, int q_on_device, mfa_report* rep) {
   mfa_model* md = const_cast<mfa_model*>(mdc);
-  if (!h || !md || md->h != h || !q || !rep) return MFA_ERR_ARG;
+  if (!h || !md || md->h != h || !rep) return MFA_ERR_ARG;
+  if (!q) {  // the device copy this model staged from host data in mfa_encode
+    if (!md->q_staged) return MFA_ERR_ARG;
+    q = md->q_staged;
+    q_dtype = md->q_staged_dtype;
+    q_on_device = 1;
+  }
   if (q_dtype != MFA_F32 && q_dtype != MFA_F64) return MFA_ERR_ARG;
   DeviceGuard g(h->device);
   const long long n = (long long)md->axh[0].M * md->axh[1].M * md->axh[2].M;

@@ -79,6 +79,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_encode.argtypes = [P, ctypes.POINTER(mfa_layout), P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(P)]
     lib.mfa_schwarz_iterate.argtypes = [P, P, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(mfa_report)]
     lib.mfa_decode.argtypes = [P, P, P, ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int]
+    lib.mfa_encode_plain.argtypes = [P, ctypes.POINTER(mfa_layout), P, ctypes.c_int, ctypes.c_int, ctypes.c_int32,
+                                     ctypes.c_double, ctypes.POINTER(mfa_report), ctypes.POINTER(P)]
     lib.mfa_residual.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(mfa_report)]
     lib.mfa_get_ctrl.argtypes = [P, P, P, ctypes.c_int64]
     lib.mfa_num_ctrl.argtypes = [P]
@@ -167,6 +169,17 @@ def mfa_schwarz_iterate(h: int, m: int, max_iters: int, tol_dP: float):
     return rc, rep
 
 
+def mfa_encode_plain(h: int, layout: mfa_layout, q_ptr: int, q_dtype: int, q_on_device: bool, max_iters: int,
+                     tol_dP: float):
+    """Per-subdomain comparator form (FP64); returns (model, rc, report)."""
+    m = ctypes.c_void_p()
+    rep = mfa_report()
+    rc = load().mfa_encode_plain(ctypes.c_void_p(h), ctypes.byref(layout), ctypes.c_void_p(q_ptr), q_dtype,
+                                 int(q_on_device), int(max_iters), float(tol_dP), ctypes.byref(rep), ctypes.byref(m))
+    _check(rc, "mfa_encode_plain", ok=(MFA_OK, MFA_NOT_CONVERGED))
+    return m.value, rc, rep
+
+
 def mfa_decode(h: int, m: int, pts_ptr: int, npts_q: int, deriv, out_ptr: int, out_dtype: int,
                out_on_device: bool) -> None:
     d = None
@@ -188,10 +201,17 @@ def mfa_num_ctrl(m: int) -> int:
     return int(load().mfa_num_ctrl(ctypes.c_void_p(m)))
 
 
-def mfa_get_ctrl(h: int, m: int) -> np.ndarray:
+def mfa_get_ctrl(h: int, m: int, out=None):
+    """Control points as FP64 into ``out`` (a host numpy array or CPU torch
+    tensor of at least mfa_num_ctrl values, e.g. pinned), or a new array."""
     n = mfa_num_ctrl(m)
-    out = np.empty(n, dtype=np.float64)
-    _check(load().mfa_get_ctrl(ctypes.c_void_p(h), ctypes.c_void_p(m), out.ctypes.data, n), "mfa_get_ctrl")
+    if out is None:
+        out = np.empty(n, dtype=np.float64)
+    ptr, code, dev, keep = _ptr_dtype(out)
+    if dev or code != MFA_F64 or keep is not out:
+        raise TypeError("control points are read into a contiguous host float64 buffer")
+    cap = out.numel() if hasattr(out, "numel") else out.size
+    _check(load().mfa_get_ctrl(ctypes.c_void_p(h), ctypes.c_void_p(m), ptr, cap), "mfa_get_ctrl")
     return out
 
 
@@ -284,6 +304,12 @@ class Handle:
         m = mfa_encode(self.h, layout, ptr, code, dev)
         return Model(self, m, layout)
 
+    def encode_plain(self, q, layout: mfa_layout, max_iters: int, tol_dP: float):
+        """Encode and iterate in the per-subdomain comparator form; returns (Model, rc, report)."""
+        ptr, code, dev, keep = _ptr_dtype(q)
+        m, rc, rep = mfa_encode_plain(self.h, layout, ptr, code, dev, max_iters, tol_dP)
+        return Model(self, m, layout), rc, rep
+
     def sync(self) -> int:
         return mfa_sync(self.h)
 
@@ -313,10 +339,18 @@ class Model:
     def iterate(self, max_iters: int, tol_dP: float = 0.0):
         return mfa_schwarz_iterate(self.handle.h, self.m, max_iters, tol_dP)
 
-    def ctrl(self) -> np.ndarray:
+    def ctrl(self, out=None):
+        """Global control points (grid layout, reversed axes); with ``out`` a
+        preallocated host float64 buffer is filled and returned as is."""
+        if out is not None:
+            return mfa_get_ctrl(self.handle.h, self.m, out)
         return mfa_get_ctrl(self.handle.h, self.m).reshape(tuple(reversed(self.ncp)))
 
-    def residual(self, q) -> mfa_report:
+    def residual(self, q=None) -> mfa_report:
+        """Decoded error statistics against ``q``; None uses the device copy
+        encode() made of host data."""
+        if q is None:
+            return mfa_residual(self.handle.h, self.m, 0, MFA_F32, False)
         ptr, code, dev, keep = _ptr_dtype(q)
         return mfa_residual(self.handle.h, self.m, ptr, code, dev)
 

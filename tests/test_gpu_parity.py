@@ -245,3 +245,63 @@ def test_nonfinite_input_reported():
         m.free()
     finally:
         h.close()
+
+
+def test_residual_on_staged_host_copy_and_pinned_ctrl():
+    """A model encoded from host data keeps its device copy: residual(None)
+    equals residual(host data); a device-data model has no copy (MFA_ERR_ARG).
+    Control points read into a pinned buffer equal ctrl()."""
+    import torch
+    Q = inputs.gauss_3d((40, 36, 33), seed=3, dtype=np.float32)
+    h = mfa.Handle(0)
+    try:
+        lay = mfa.make_layout(3, 3, [40, 36, 33], [10, 9, 8], [2, 2, 1], [2, 2, 2], mfa.MFA_PREC_MIXED)
+        m = h.encode(Q, lay)
+        m.iterate(5, 0.0)
+        a, b = m.residual(None), m.residual(Q)
+        assert (a.rms_decoded, a.maxabs_decoded, a.data_range) == (b.rms_decoded, b.maxabs_decoded, b.data_range)
+        buf = torch.empty(mfa.mfa_num_ctrl(m.m), dtype=torch.float64).pin_memory()
+        m.ctrl(out=buf)
+        assert np.array_equal(buf.numpy(), m.ctrl().ravel())
+        m.free()
+        md = h.encode(torch.from_numpy(Q).cuda(), lay)
+        with pytest.raises(mfa.MFAError) as ei:
+            md.residual(None)
+        assert ei.value.code == mfa.MFA_ERR_ARG
+        md.free()
+    finally:
+        h.close()
+
+
+def test_plain_per_subdomain_form_equals_batched_fp64():
+    """The per-subdomain comparator form (one launch per subdomain and stage,
+    data re-read every iteration) runs the same FP64 arithmetic as the
+    batched path: identical control points and iteration count, and it
+    matches the oracle within the FP64 bar."""
+    Q = inputs.gauss_3d((30, 28, 26), seed=5, dtype=np.float32)
+    Qd = Q.astype(np.float64)
+    nspans, nsub, delta = [8, 7, 6], [2, 2, 2], 2
+    g = GpuRun(Q, 3, nspans, nsub, delta)
+    h = mfa.Handle(0)
+    try:
+        rc, rep = g.iterate(30, 1e-10)
+        import torch
+        m, rc2, rep2 = h.encode_plain(torch.from_numpy(Q).cuda(), g.layout, 30, 1e-10)
+        assert rep2.iters == rep.iters and rc2 == rc
+        P = m.ctrl()
+        assert np.array_equal(P, g.ctrl())
+        prob = oracle_problem(Qd, 3, nspans, nsub, delta)
+        ref = O.schwarz_solve(prob, Qd, max_iters=30, tol_dP=1e-10)
+        assert ref["iters"] == rep2.iters
+        assert rel_diff(P, ref["P"]) <= TOL_FP64
+        with pytest.raises(mfa.MFAError):
+            h.encode_plain(Q, layout_for_mixed(Q, nspans, nsub, delta), 3, 0.0)
+        m.free()
+    finally:
+        g.close()
+        h.close()
+
+
+def layout_for_mixed(Q, nspans, nsub, delta):
+    from mfa_cases import layout_for
+    return layout_for(Q, 3, nspans, nsub, delta, mfa.MFA_PREC_MIXED)
