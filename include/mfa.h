@@ -75,7 +75,7 @@ enum { MFA_PREC_FP64 = 0, MFA_PREC_MIXED = 1 };
  *   nsub[a]      subdomains along axis a (N = product)
  *   core_spans[a] NULL for an even split (the first nspans % nsub cores get
  *                one span more) or an array of nsub[a] span counts summing to
- *                nspans[a]; every core needs >= degree spans
+ *                nspans[a]; with nsub[a] > 1 every core needs >= degree spans
  *   overlap[a]   delta, extra knot spans shared per interior side (Sec. 2.2,
  *                "Augmenting Knot Spans with Overlap"), >= 0
  *   precision    MFA_PREC_FP64 or MFA_PREC_MIXED
@@ -238,6 +238,65 @@ const char* mfa_status_string(int status);
 #define MFA_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int mfa_decode_grid_noalloc(int32_t dim, int32_t degree, const int64_t* npts, const int32_t* nspans,
                             const double* ctrl, double* out, void* cuda_stream);
+
+/* ---- Batches of independent fits -----------------------------------------
+ * Many separate grids, each fitted on its own (one subdomain, N = 1: the
+ * global LSQ of Eq. minimization-problem), in a handful of launches for the
+ * whole batch instead of a set of launches per grid.  The paper fits one
+ * field at a time; the batch form serves workloads of thousands of small
+ * uneven fits.  Instances may differ in dimension, degree, grid and knot
+ * spans; they are grouped by (dimension, degree) and every group runs the
+ * projection, banded solves and decode as single launches over all of its
+ * instances.
+ *
+ * Data: one array of q_dtype values; instance i's grid (axis 0 fastest, the
+ * same convention as a single fit) starts at inst[i].q_offset.  Knots per
+ * axis are clamped uniform with nspans spans (nspans + degree control
+ * points) and u_k = k/(M-1), as for a single fit.  precision is
+ * MFA_PREC_FP64 or MFA_PREC_MIXED (float-float data passes, FP64
+ * factorisation).  Host data are staged once (kept for the residual with
+ * q == NULL); device data must stay valid until the call returns.
+ * Layout errors (Schoenberg-Whitney precheck per instance) return
+ * MFA_ERR_LAYOUT with no batch created. */
+typedef struct {
+  int32_t dim;        /* 1..MFA_MAX_DIM */
+  int32_t degree;     /* 1..MFA_MAX_DEGREE */
+  int64_t npts[3];    /* grid points per axis (entries beyond dim ignored) */
+  int32_t nspans[3];  /* knot spans per axis (entries beyond dim ignored) */
+  int64_t q_offset;   /* index of the instance's first value in the data array */
+} mfa_instance;
+
+typedef struct mfa_batch mfa_batch;
+
+int mfa_encode_batch(mfa_handle* h, int32_t count, const mfa_instance* inst, const void* q, int q_dtype,
+                     int q_on_device, int precision, mfa_batch** out);
+
+/* Refit the batch's instances to new data with the same layout (same
+ * instances and offsets): the projection and solves of every group run as
+ * one captured CUDA graph (captured on the first refit, replayed after).
+ * q must be device data, valid until the call returns; synchronous. */
+int mfa_batch_refit(mfa_handle* h, mfa_batch* b, const void* q, int q_dtype);
+
+/* Control points of every instance, concatenated in instance order (each
+ * instance in its own grid layout, axis 0 fastest, prod(nspans_a + degree)
+ * values).  mfa_batch_ctrl_offsets writes count + 1 offsets into it.
+ * mfa_batch_get_ctrl copies FP64 values to host memory (cap = capacity in
+ * values); synchronous. */
+int64_t mfa_batch_num_ctrl(const mfa_batch* b);
+int mfa_batch_ctrl_offsets(const mfa_batch* b, int64_t* host_off);
+int mfa_batch_get_ctrl(mfa_handle* h, const mfa_batch* b, double* host_out, int64_t cap);
+
+/* Decoded error of every instance against its data (q == NULL: the copy
+ * staged from host data): rms[i] and maxabs[i] (host arrays of count
+ * doubles).  Synchronous. */
+int mfa_batch_residual(mfa_handle* h, const mfa_batch* b, const void* q, int q_dtype, int q_on_device,
+                       double* rms, double* maxabs);
+
+/* Decode every instance on its own grid into out (out_dtype values laid out
+ * like the data: instance i at inst[i].q_offset). */
+int mfa_batch_decode(mfa_handle* h, const mfa_batch* b, void* out, int out_dtype, int out_on_device);
+
+int mfa_batch_free(mfa_batch* b);
 
 /* Tracing (per-phase timing of Algorithm 1's steps, as in the paper's
  * setup / solve / iterate / decode breakdown, Sec. 3.2.4).  When enabled,

@@ -186,17 +186,33 @@ __global__ void k_basis_all(SetupArgs A) {
   }
   if (a >= A.naxes) return;
   const AxisDev& ax = A.ax[a];
-  const int M = ax.M, nspans = ax.nspans, p = ax.p;
+  const int p = ax.p;
+  int M = ax.M, nspans = ax.nspans, kl = k, j0 = 0;
+  if (ax.pieces) {
+    // independent fits side by side: find the piece holding point k (pieces
+    // are sorted by k0), then use its own knot vector and parameters
+    int lo = 0, hi = ax.S - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ax.subs[mid].k0 <= k) lo = mid;
+      else hi = mid - 1;
+    }
+    const AxisSub sb = ax.subs[lo];
+    M = sb.m;
+    nspans = sb.w1 - sb.w0;
+    kl = k - sb.k0;
+    j0 = sb.l0;
+  }
   int j = 0;
   double u = 0.0;
   if (M > 1) {
-    j = (int)(((long long)k * nspans) / (M - 1));
+    j = (int)(((long long)kl * nspans) / (M - 1));
     if (j > nspans - 1) j = nspans - 1;
-    u = (double)k / (double)(M - 1);
+    u = (double)kl / (double)(M - 1);
   }
   double N[MFA_MAX_DEGREE + 1];
   cox_de_boor(j, u, p, nspans, N);
-  A.span[a][k] = j;
+  A.span[a][k] = j0 + j;
   for (int r = 0; r <= p; ++r) {
     A.vd[a][(long long)k * (p + 1) + r] = N[r];
     A.vf[a][(long long)k * (p + 1) + r] = (float)N[r];

@@ -45,6 +45,9 @@ struct mfa_model {
   const void* q_staged = nullptr;  // device copy of host data given to mfa_encode (inside `big`)
   int q_staged_dtype = MFA_F32;
   bool plain = false;              // per-subdomain comparator form (mfa_encode_plain)
+  bool batch = false;              // one (dimension, degree) group of a batch of independent fits
+  long long maxDec[3] = {0, 0, 0}; // batch: largest decode-stage output per axis
+  long long decS1 = 0, decS2 = 0;  // batch: decode stage scratch sizes (elements)
   const void* q_src = nullptr;     // plain form: the device data it re-reads every iteration
   int q_src_dtype = MFA_F32;
   int prec = MFA_PREC_FP64;
@@ -261,7 +264,8 @@ int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int
   ax.subs.clear();
   int a = 0, bandL = 0, bandU = 0;
   for (int s = 0; s < nsub; ++s) {
-    if (cs[s] < std::max(p, 1)) return MFA_ERR_LAYOUT;  // cores need >= p spans
+    // cores between interfaces need >= p spans; a single subdomain has none
+    if (nsub > 1 && cs[s] < std::max(p, 1)) return MFA_ERR_LAYOUT;
     AxisSub sb{};
     sb.a = a;
     sb.b = a + cs[s];
@@ -544,7 +548,7 @@ void run_encode(mfa_model* md, const TQ* q) {
       trace_end(h, TR_SOLVE_L, _ti, it0);
     }
   }
-  if (!it0) cudaMemcpyAsync(X, BL, md->sizeL * sizeof(T), cudaMemcpyDeviceToDevice, h->stream);
+  if (!it0 && X != BL) cudaMemcpyAsync(X, BL, md->sizeL * sizeof(T), cudaMemcpyDeviceToDevice, h->stream);
   for (int a = 0; a < md->dim && !it0; ++a) {
     if (md->plain) {
       for (int sd = 0; sd < ns; ++sd)
@@ -554,6 +558,7 @@ void run_encode(mfa_model* md, const TQ* q) {
       TRACED(h, TR_SOLVE_L, launch_band_solve<T>(L, a, false, opsk(OP_SOLVEL0 + a), ns, md->maxFibL[a], X, h->stream));
     }
   }
+  if (md->batch) return;  // one subdomain per instance: the solution is X itself
   cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
   if constexpr (std::is_same<T, ff>::value) {
     if (md->use_fused) {
@@ -787,6 +792,142 @@ int mfa_destroy(mfa_handle* h) {
 }
 
 namespace {
+// Upload the layout tables of a model whose host axes (md->axh) and operand
+// tables are built, allocate its buffers (plus `stage_bytes` for staged host
+// data, offset returned in *o_stage), fill the device layout and run the
+// setup kernels (basis, Gram bands, Cholesky factors).
+int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& ops,
+                      const std::vector<long long>& offL, const std::vector<long long>& offS1,
+                      const std::vector<long long>& offS2, size_t stage_bytes, size_t* o_stage) {
+  const int ns = md->nsub;
+  // ---- device tables in one arena
+  Arena ar;
+  size_t o_span[3], o_vd[3], o_vf[3], o_vff[3], o_ss[3], o_subs[3], o_of[3], o_oc[3], o_AL[3], o_fLd[3], o_fLf[3],
+      o_fLff[3], o_fUd[3], o_fUf[3], o_fUff[3], o_ot[3], o_nlt[3];
+  for (int a = 0; a < 3; ++a) {
+    const AxisHost& ax = md->axh[a];
+    const int w = ax.p + 1;
+    o_span[a] = ar.take<int>(ax.M);
+    o_vd[a] = ar.take<double>((size_t)ax.M * w);
+    o_vf[a] = ar.take<float>((size_t)ax.M * w);
+    o_vff[a] = ar.take<ff>((size_t)ax.M * w);
+    o_ss[a] = ar.take<int>(ax.nspans + 1);
+    o_subs[a] = ar.take<AxisSub>(ax.S);
+    o_of[a] = ar.take<int>(ax.n);
+    o_oc[a] = ar.take<int>(ax.n);
+    o_ot[a] = ar.take<int4>(ax.n);
+    o_nlt[a] = ar.take<int>(ax.S);
+    o_AL[a] = ar.take<double>((size_t)ax.bandL_rows * w);
+    o_fLd[a] = ar.take<double>((size_t)ax.bandL_rows * w);
+    o_fLf[a] = ar.take<float>((size_t)ax.bandL_rows * w);
+    o_fLff[a] = ar.take<ff>((size_t)ax.bandL_rows * w);
+    o_fUd[a] = ar.take<double>((size_t)ax.bandU_rows * w);
+    o_fUf[a] = ar.take<float>((size_t)ax.bandU_rows * w);
+    o_fUff[a] = ar.take<ff>((size_t)ax.bandU_rows * w);
+  }
+  const size_t o_offL = ar.take<long long>(ns), o_offS1 = ar.take<long long>(ns), o_offS2 = ar.take<long long>(ns);
+  const size_t o_ops = ar.take<AxisOp>(ops.size());
+  const size_t tables_bytes = ar.used;
+  // host staging image of the uploaded tables
+  std::vector<char> img(tables_bytes, 0);
+  for (int a = 0; a < 3; ++a) {
+    const AxisHost& ax = md->axh[a];
+    std::memcpy(img.data() + o_ss[a], ax.span_start.data(), sizeof(int) * ax.span_start.size());
+    std::memcpy(img.data() + o_subs[a], ax.subs.data(), sizeof(AxisSub) * ax.subs.size());
+    std::memcpy(img.data() + o_of[a], ax.own_first.data(), sizeof(int) * ax.n);
+    std::memcpy(img.data() + o_oc[a], ax.own_count.data(), sizeof(int) * ax.n);
+    std::memcpy(img.data() + o_ot[a], ax.own_tab.data(), sizeof(int4) * ax.n);
+    std::memcpy(img.data() + o_nlt[a], ax.nL_tab.data(), sizeof(int) * ax.S);
+  }
+  std::memcpy(img.data() + o_offL, offL.data(), sizeof(long long) * ns);
+  std::memcpy(img.data() + o_offS1, offS1.data(), sizeof(long long) * ns);
+  std::memcpy(img.data() + o_offS2, offS2.data(), sizeof(long long) * ns);
+  std::memcpy(img.data() + o_ops, ops.data(), sizeof(AxisOp) * ops.size());
+  // big buffers
+  const size_t es = elem_size(md->prec);
+  Arena bg;
+  // a batch group writes B_L and X into the batch's buffers and has no global P
+  const long long own_sizeL = md->batch ? 0 : md->sizeL;
+  const size_t o_BL = bg.take<char>(own_sizeL * es), o_X = bg.take<char>(own_sizeL * es);
+  const long long ncp = md->batch ? 0 : (long long)md->axh[0].n * md->axh[1].n * md->axh[2].n;
+  const size_t o_P = bg.take<char>(ncp * es), o_Pp = bg.take<char>(ncp * es);
+  const size_t o_S1 = bg.take<char>(md->sizeS1 * es), o_S2 = bg.take<char>(md->sizeS2 * es);
+  const size_t o_part = bg.take<float>(3 * (size_t)kAvgBlocks);
+  // host data staging: the data are copied into the pool before use
+  *o_stage = stage_bytes ? bg.take<char>(stage_bytes) : 0;
+  int rc = pool_alloc(h, &md->arena, tables_bytes);
+  if (rc == MFA_OK) rc = pool_alloc(h, &md->big, bg.used);
+  if (rc != MFA_OK) {
+    pool_free(h, md->arena);
+    pool_free(h, md->big);
+    md->arena = md->big = nullptr;
+    return rc;
+  }
+  // pageable source: the runtime has staged it when the call returns
+  cudaError_t e = cudaMemcpyAsync(md->arena, img.data(), tables_bytes, cudaMemcpyHostToDevice, h->stream);
+  // device layout struct
+  LayoutDev& L = md->L;
+  L.dim = md->dim;
+  L.nsub = ns;
+  for (int a = 0; a < 3; ++a) {
+    const AxisHost& ax = md->axh[a];
+    L.S[a] = ax.S;
+    L.ncp[a] = ax.n;
+    L.M[a] = ax.M;
+    AxisDev& d = L.ax[a];
+    d.M = ax.M;
+    d.nspans = ax.nspans;
+    d.p = ax.p;
+    d.n = ax.n;
+    d.S = ax.S;
+    d.pieces = ax.pieces;
+    d.span = at_off<int>(md->arena, o_span[a]);
+    d.vals_d = at_off<double>(md->arena, o_vd[a]);
+    d.vals_f = at_off<float>(md->arena, o_vf[a]);
+    d.vals_ff = at_off<ff>(md->arena, o_vff[a]);
+    d.span_start = at_off<int>(md->arena, o_ss[a]);
+    d.subs = at_off<AxisSub>(md->arena, o_subs[a]);
+    d.own_first = at_off<int>(md->arena, o_of[a]);
+    d.own_count = at_off<int>(md->arena, o_oc[a]);
+    d.own_tab = at_off<int4>(md->arena, o_ot[a]);
+    d.nL_tab = at_off<int>(md->arena, o_nlt[a]);
+    d.AL = at_off<double>(md->arena, o_AL[a]);
+    d.facL_d = at_off<double>(md->arena, o_fLd[a]);
+    d.facL_f = at_off<float>(md->arena, o_fLf[a]);
+    d.facL_ff = at_off<ff>(md->arena, o_fLff[a]);
+    d.facU_d = at_off<double>(md->arena, o_fUd[a]);
+    d.facU_f = at_off<float>(md->arena, o_fUf[a]);
+    d.facU_ff = at_off<ff>(md->arena, o_fUff[a]);
+  }
+  md->offL = at_off<long long>(md->arena, o_offL);
+  md->offS1 = at_off<long long>(md->arena, o_offS1);
+  md->offS2 = at_off<long long>(md->arena, o_offS2);
+  md->ops = at_off<AxisOp>(md->arena, o_ops);
+  md->BL = at_off<char>(md->big, o_BL);
+  md->X = at_off<char>(md->big, o_X);
+  md->P = at_off<char>(md->big, o_P);
+  md->Pprev = at_off<char>(md->big, o_Pp);
+  md->S1 = at_off<char>(md->big, o_S1);
+  md->S2 = at_off<char>(md->big, o_S2);
+  md->part = at_off<float>(md->big, o_part);
+  // setup kernels: basis tables, Gram bands, Cholesky factors (FP64), all axes per launch
+  {
+    int maxnL = 1;
+    for (int a = 0; a < 3; ++a) maxnL = std::max(maxnL, md->maxnL[a]);
+    TRACED_N(h, TR_SETUP, 2, launch_setup_all(L.ax, 3, maxnL, h->d_status, h->stream));
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    pool_free(h, md->arena);
+    pool_free(h, md->big);
+    md->arena = md->big = nullptr;
+    return cuda_status(e);
+  }
+  return MFA_OK;
+}
+}  // namespace
+
+namespace {
 int encode_impl(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype, int q_on_device, bool plain,
                 mfa_model** out);
 }
@@ -870,120 +1011,14 @@ int encode_impl(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype
   std::vector<AxisOp> ops;
   std::vector<long long> offL, offS1, offS2;
   build_ops(md, ops, offL, offS1, offS2);
-  const int ns = md->nsub;
-  // ---- device tables in one arena
-  Arena ar;
-  size_t o_span[3], o_vd[3], o_vf[3], o_vff[3], o_ss[3], o_subs[3], o_of[3], o_oc[3], o_AL[3], o_fLd[3], o_fLf[3],
-      o_fLff[3], o_fUd[3], o_fUf[3], o_fUff[3], o_ot[3], o_nlt[3];
-  for (int a = 0; a < 3; ++a) {
-    const AxisHost& ax = md->axh[a];
-    const int w = ax.p + 1;
-    o_span[a] = ar.take<int>(ax.M);
-    o_vd[a] = ar.take<double>((size_t)ax.M * w);
-    o_vf[a] = ar.take<float>((size_t)ax.M * w);
-    o_vff[a] = ar.take<ff>((size_t)ax.M * w);
-    o_ss[a] = ar.take<int>(ax.nspans + 1);
-    o_subs[a] = ar.take<AxisSub>(ax.S);
-    o_of[a] = ar.take<int>(ax.n);
-    o_oc[a] = ar.take<int>(ax.n);
-    o_ot[a] = ar.take<int4>(ax.n);
-    o_nlt[a] = ar.take<int>(ax.S);
-    o_AL[a] = ar.take<double>((size_t)ax.bandL_rows * w);
-    o_fLd[a] = ar.take<double>((size_t)ax.bandL_rows * w);
-    o_fLf[a] = ar.take<float>((size_t)ax.bandL_rows * w);
-    o_fLff[a] = ar.take<ff>((size_t)ax.bandL_rows * w);
-    o_fUd[a] = ar.take<double>((size_t)ax.bandU_rows * w);
-    o_fUf[a] = ar.take<float>((size_t)ax.bandU_rows * w);
-    o_fUff[a] = ar.take<ff>((size_t)ax.bandU_rows * w);
-  }
-  const size_t o_offL = ar.take<long long>(ns), o_offS1 = ar.take<long long>(ns), o_offS2 = ar.take<long long>(ns);
-  const size_t o_ops = ar.take<AxisOp>(ops.size());
-  const size_t tables_bytes = ar.used;
-  // host staging image of the uploaded tables
-  std::vector<char> img(tables_bytes, 0);
-  for (int a = 0; a < 3; ++a) {
-    const AxisHost& ax = md->axh[a];
-    std::memcpy(img.data() + o_ss[a], ax.span_start.data(), sizeof(int) * ax.span_start.size());
-    std::memcpy(img.data() + o_subs[a], ax.subs.data(), sizeof(AxisSub) * ax.subs.size());
-    std::memcpy(img.data() + o_of[a], ax.own_first.data(), sizeof(int) * ax.n);
-    std::memcpy(img.data() + o_oc[a], ax.own_count.data(), sizeof(int) * ax.n);
-    std::memcpy(img.data() + o_ot[a], ax.own_tab.data(), sizeof(int4) * ax.n);
-    std::memcpy(img.data() + o_nlt[a], ax.nL_tab.data(), sizeof(int) * ax.S);
-  }
-  std::memcpy(img.data() + o_offL, offL.data(), sizeof(long long) * ns);
-  std::memcpy(img.data() + o_offS1, offS1.data(), sizeof(long long) * ns);
-  std::memcpy(img.data() + o_offS2, offS2.data(), sizeof(long long) * ns);
-  std::memcpy(img.data() + o_ops, ops.data(), sizeof(AxisOp) * ops.size());
-  // big buffers
-  const size_t es = elem_size(md->prec);
-  Arena bg;
-  const size_t o_BL = bg.take<char>(md->sizeL * es), o_X = bg.take<char>(md->sizeL * es);
-  const long long ncp = (long long)md->axh[0].n * md->axh[1].n * md->axh[2].n;
-  const size_t o_P = bg.take<char>(ncp * es), o_Pp = bg.take<char>(ncp * es);
-  const size_t o_S1 = bg.take<char>(md->sizeS1 * es), o_S2 = bg.take<char>(md->sizeS2 * es);
-  const size_t o_part = bg.take<float>(3 * (size_t)kAvgBlocks);
-  // host data staging: the data are copied into the pool before use
   const size_t qbytes = (size_t)npts_total * (q_dtype == MFA_F64 ? 8 : 4);
-  const size_t o_Q = q_on_device ? 0 : bg.take<char>(qbytes);
-  int rc = pool_alloc(h, &md->arena, tables_bytes);
-  if (rc == MFA_OK) rc = pool_alloc(h, &md->big, bg.used);
+  size_t o_Q = 0;
+  int rc = materialize_model(h, md, ops, offL, offS1, offS2, q_on_device ? 0 : qbytes, &o_Q);
   if (rc != MFA_OK) {
-    pool_free(h, md->arena);
-    pool_free(h, md->big);
     delete md;
     return rc;
   }
-  cudaError_t e = cudaMemcpyAsync(md->arena, img.data(), tables_bytes, cudaMemcpyHostToDevice, h->stream);
-  // device layout struct
-  LayoutDev& L = md->L;
-  L.dim = md->dim;
-  L.nsub = ns;
-  for (int a = 0; a < 3; ++a) {
-    const AxisHost& ax = md->axh[a];
-    L.S[a] = ax.S;
-    L.ncp[a] = ax.n;
-    L.M[a] = ax.M;
-    AxisDev& d = L.ax[a];
-    d.M = ax.M;
-    d.nspans = ax.nspans;
-    d.p = ax.p;
-    d.n = ax.n;
-    d.S = ax.S;
-    d.span = at_off<int>(md->arena, o_span[a]);
-    d.vals_d = at_off<double>(md->arena, o_vd[a]);
-    d.vals_f = at_off<float>(md->arena, o_vf[a]);
-    d.vals_ff = at_off<ff>(md->arena, o_vff[a]);
-    d.span_start = at_off<int>(md->arena, o_ss[a]);
-    d.subs = at_off<AxisSub>(md->arena, o_subs[a]);
-    d.own_first = at_off<int>(md->arena, o_of[a]);
-    d.own_count = at_off<int>(md->arena, o_oc[a]);
-    d.own_tab = at_off<int4>(md->arena, o_ot[a]);
-    d.nL_tab = at_off<int>(md->arena, o_nlt[a]);
-    d.AL = at_off<double>(md->arena, o_AL[a]);
-    d.facL_d = at_off<double>(md->arena, o_fLd[a]);
-    d.facL_f = at_off<float>(md->arena, o_fLf[a]);
-    d.facL_ff = at_off<ff>(md->arena, o_fLff[a]);
-    d.facU_d = at_off<double>(md->arena, o_fUd[a]);
-    d.facU_f = at_off<float>(md->arena, o_fUf[a]);
-    d.facU_ff = at_off<ff>(md->arena, o_fUff[a]);
-  }
-  md->offL = at_off<long long>(md->arena, o_offL);
-  md->offS1 = at_off<long long>(md->arena, o_offS1);
-  md->offS2 = at_off<long long>(md->arena, o_offS2);
-  md->ops = at_off<AxisOp>(md->arena, o_ops);
-  md->BL = at_off<char>(md->big, o_BL);
-  md->X = at_off<char>(md->big, o_X);
-  md->P = at_off<char>(md->big, o_P);
-  md->Pprev = at_off<char>(md->big, o_Pp);
-  md->S1 = at_off<char>(md->big, o_S1);
-  md->S2 = at_off<char>(md->big, o_S2);
-  md->part = at_off<float>(md->big, o_part);
-  // setup kernels: basis tables, Gram bands, Cholesky factors (FP64), all axes per launch
-  {
-    int maxnL = 1;
-    for (int a = 0; a < 3; ++a) maxnL = std::max(maxnL, md->maxnL[a]);
-    TRACED_N(h, TR_SETUP, 2, launch_setup_all(L.ax, 3, maxnL, h->d_status, h->stream));
-  }
+  cudaError_t e = cudaSuccess;
   const void* qd = q;
   if (!q_on_device) {
     // host data: copy and wait, so the caller may reuse its buffer on return
@@ -1258,3 +1293,521 @@ int mfa_sync(mfa_handle* h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of independent fits
+// ---------------------------------------------------------------------------
+
+struct mfa_batch {
+  mfa_handle* h = nullptr;
+  int count = 0;
+  int prec = MFA_PREC_FP64;
+  std::vector<mfa_instance> inst;
+  std::vector<mfa_model*> groups;        // one per (dimension, degree)
+  std::vector<long long> cp_off;         // [count + 1] control-point offsets, instance order
+  std::vector<long long> q_len;          // values per instance
+  long long q_total = 0;                 // length of the data array the instances span
+  void* buf = nullptr;                   // control points of every instance (B_L, then solved in place)
+  void* tab = nullptr;                   // device: q offsets [count], lengths [count], residual out [2 count]
+  void* staged = nullptr;                // device copy of host data
+  int staged_dtype = MFA_F32;
+  cudaGraphExec_t graph = nullptr;       // captured refit
+  cudaStream_t cap = nullptr;            // private stream the refit is captured on
+  const void* graph_q = nullptr;
+  int graph_dtype = -1;
+};
+
+namespace {
+
+// One (dimension, degree) group as a model over virtual axes: axis a
+// concatenates the group's instances, each a piece with its own knot vector;
+// instance t of the group uses piece t on every axis of its dimension.
+int build_batch_group(mfa_batch* b, int d, int p, const std::vector<int>& mem, mfa_model** out) {
+  mfa_handle* h = b->h;
+  mfa_model* md = new (std::nothrow) mfa_model();
+  if (!md) return MFA_ERR_OOM;
+  md->h = h;
+  md->prec = b->prec;
+  md->dim = d;
+  md->degree = p;
+  md->batch = true;
+  md->use_fused = false;
+  const int ns = (int)mem.size();
+  for (int a = 0; a < 3; ++a) {
+    AxisHost& ax = md->axh[a];
+    if (a >= d) {
+      int rc = build_axis(ax, 1, 1, 0, 1, nullptr, 0);
+      if (rc != MFA_OK) {
+        delete md;
+        return rc;
+      }
+      continue;
+    }
+    ax = AxisHost{};
+    ax.p = p;
+    ax.S = ns;
+    ax.pieces = 1;
+    ax.M = 0;
+    ax.n = 0;
+    std::vector<int> ss;
+    for (int t = 0; t < ns; ++t) {
+      const mfa_instance& in = b->inst[mem[t]];
+      AxisHost one;
+      int rc = build_axis(one, in.npts[a], in.nspans[a], p, 1, nullptr, 0);
+      if (rc != MFA_OK) {
+        delete md;
+        return rc;
+      }
+      AxisSub sb = one.subs[0];
+      const int kbase = ax.M, cbase = ax.n;
+      sb.k0 += kbase;
+      sb.l0 += cbase;
+      sb.bandL += cbase;
+      sb.bandU += cbase;
+      ax.subs.push_back(sb);
+      // virtual spans share the control-point numbering: instance spans
+      // [cbase, cbase + nspans), then p empty span numbers
+      for (int j = 0; j < one.n; ++j) ss.push_back(kbase + (j < one.nspans ? one.span_start[j] : one.M));
+      ax.M += one.M;
+      ax.n += one.n;
+    }
+    ss.push_back(ax.M);
+    ax.nspans = ax.n;
+    ax.span_start = ss;
+    ax.own_first.assign(ax.n, 0);
+    ax.own_count.assign(ax.n, 1);
+    ax.own_tab.assign(ax.n, int4{0, 0, -1, 0});
+    ax.nL_tab.resize(ns);
+    for (int t = 0; t < ns; ++t) {
+      const AxisSub& sb = ax.subs[t];
+      ax.nL_tab[t] = sb.nL;
+      for (int l = 0; l < sb.nL; ++l) {
+        ax.own_first[sb.l0 + l] = t;
+        ax.own_tab[sb.l0 + l] = int4{t, l, -1, 0};
+      }
+    }
+    ax.bandL_rows = ax.n;
+    ax.bandU_rows = ax.n;
+  }
+  md->nsub = ns;
+  // operand tables
+  std::vector<AxisOp> ops((size_t)kOpKinds * ns, AxisOp{});
+  std::vector<long long> offL(ns), offS1(ns), offS2(ns);
+  long long a1 = 0, a2 = 0, d1 = 0, d2 = 0;
+  for (int t = 0; t < ns; ++t) {
+    const int i = mem[t];
+    const mfa_instance& in = b->inst[i];
+    AxisSub sb[3];
+    int m[3], nL[3], sa[3];
+    long long M[3];
+    for (int a = 0; a < 3; ++a) {
+      sa[a] = a < d ? t : 0;
+      sb[a] = md->axh[a].subs[sa[a]];
+      m[a] = sb[a].m;
+      nL[a] = sb[a].nL;
+      M[a] = a < d ? in.npts[a] : 1;
+    }
+    const long long szL = (long long)nL[0] * nL[1] * nL[2];
+    offL[t] = b->cp_off[i];
+    offS1[t] = a1;
+    offS2[t] = a2;
+    a1 += std::max((long long)nL[0] * m[1] * m[2], szL);
+    a2 += std::max((long long)nL[0] * nL[1] * m[2], szL);
+    md->sizeL += szL;
+    for (int a = 0; a < 3; ++a) {
+      md->maxm[a] = std::max(md->maxm[a], m[a]);
+      md->maxnL[a] = std::max(md->maxnL[a], nL[a]);
+      md->maxnU[a] = std::max(md->maxnU[a], nL[a]);
+    }
+    auto at = [&](int kind) -> AxisOp& { return ops[(size_t)kind * ns + t]; };
+    // projection: instance grid -> S1 -> S2 -> its control points
+    {
+      View vin = make_view(in.q_offset, m[0], m[1], m[2], 1, M[0], M[0] * M[1]);
+      int cur[3] = {m[0], m[1], m[2]};
+      for (int a = 0; a < d; ++a) {
+        cur[a] = nL[a];
+        const long long off = (a == d - 1) ? offL[t] : (a == 0 ? offS1[t] : offS2[t]);
+        View vout = contiguous(off, cur[0], cur[1], cur[2]);
+        AxisOp& op = at(OP_PROJ0 + a);
+        op.in = vin;
+        op.out = vout;
+        op.k0 = sb[a].k0;
+        op.kend = sb[a].k0 + sb[a].m;
+        op.c0 = sb[a].l0;
+        op.sa = sa[a];
+        md->maxOut[a] = std::max<long long>(md->maxOut[a], (long long)cur[0] * cur[1] * cur[2]);
+        vin = vout;
+      }
+    }
+    // solves in place over the control-point box
+    for (int a = 0; a < 3; ++a) {
+      AxisOp& opL = at(OP_SOLVEL0 + a);
+      opL.out = contiguous(offL[t], nL[0], nL[1], nL[2]);
+      opL.sa = sa[a];
+      at(OP_SOLVEU0 + a) = opL;
+      const int o1 = a == 0 ? 1 : 0, o2 = a == 2 ? 1 : 2;
+      md->maxFibL[a] = std::max(md->maxFibL[a], nL[o1] * nL[o2]);
+      md->maxFibU[a] = md->maxFibL[a];
+    }
+    // decode: control points -> D1 -> D2 -> the instance grid of the output
+    {
+      int cur[3] = {nL[0], nL[1], nL[2]};
+      View vin = contiguous(offL[t], cur[0], cur[1], cur[2]);
+      for (int a = 0; a < d; ++a) {
+        cur[a] = (int)M[a];
+        const long long sz = (long long)cur[0] * cur[1] * cur[2];
+        View vout;
+        if (a == d - 1) {
+          vout = make_view(in.q_offset, cur[0], cur[1], cur[2], 1, M[0], M[0] * M[1]);
+        } else {
+          long long& acc = (a == 0) ? d1 : d2;
+          vout = contiguous(acc, cur[0], cur[1], cur[2]);
+          acc += sz;
+        }
+        AxisOp& op = at(OP_DEC0 + a);
+        op.in = vin;
+        op.out = vout;
+        op.k0 = sb[a].k0;
+        op.kend = sb[a].k0 + sb[a].m;
+        op.c0 = sb[a].l0;
+        op.sa = sa[a];
+        md->maxDec[a] = std::max(md->maxDec[a], sz);
+        vin = vout;
+      }
+    }
+  }
+  md->sizeS1 = a1;
+  md->sizeS2 = a2;
+  md->decS1 = d1;
+  md->decS2 = d2;
+  size_t o_unused = 0;
+  int rc = materialize_model(h, md, ops, offL, offS1, offS2, 0, &o_unused);
+  if (rc != MFA_OK) {
+    delete md;
+    return rc;
+  }
+  md->BL = md->X = b->buf;
+  md->P = b->buf;
+  h->live_models++;
+  *out = md;
+  return MFA_OK;
+}
+
+template <typename T, typename TQ>
+void batch_fit_all(mfa_batch* b, const TQ* q) {
+  for (mfa_model* md : b->groups) run_encode<T, TQ>(md, q);
+}
+
+template <typename T>
+void batch_fit(mfa_batch* b, const void* q, int q_dtype) {
+  if (q_dtype == MFA_F64)
+    batch_fit_all<T, double>(b, (const double*)q);
+  else
+    batch_fit_all<T, float>(b, (const float*)q);
+}
+
+// Grid decode of every group into out (instance layout of the data).
+template <typename T, typename TOut>
+int batch_decode_into(mfa_batch* b, TOut* out) {
+  mfa_handle* h = b->h;
+  size_t need = 0;
+  for (mfa_model* md : b->groups) need = std::max<size_t>(need, (size_t)(md->decS1 + md->decS2) * sizeof(T));
+  int rc = ensure_ws(h, std::max<size_t>(need, 256));
+  if (rc != MFA_OK) return rc;
+  for (mfa_model* md : b->groups) {
+    T* s1 = (T*)h->ws;
+    T* s2 = s1 + md->decS1;
+    const int ns = md->nsub;
+    const T* in = (const T*)md->X;
+    for (int a = 0; a < md->dim; ++a) {
+      const AxisOp* op = md->ops + (size_t)(OP_DEC0 + a) * ns;
+      if (a == md->dim - 1) {
+        TRACED(h, TR_DECODE_OUT, (launch_expand<T, TOut>(md->L, a, op, ns, md->maxDec[a], in, out, h->stream)));
+      } else {
+        T* o = (a == 0) ? s1 : s2;
+        TRACED(h, TR_DECODE_STAGE, (launch_expand<T, T>(md->L, a, op, ns, md->maxDec[a], in, o, h->stream)));
+        in = o;
+      }
+    }
+  }
+  return MFA_OK;
+}
+
+template <typename TOut>
+int batch_decode_any(mfa_batch* b, TOut* out) {
+  return b->prec == MFA_PREC_FP64 ? batch_decode_into<double, TOut>(b, out) : batch_decode_into<ff, TOut>(b, out);
+}
+
+}  // namespace
+
+int mfa_encode_batch(mfa_handle* h, int32_t count, const mfa_instance* inst, const void* q, int q_dtype,
+                     int q_on_device, int precision, mfa_batch** out) {
+  if (!h || count < 1 || !inst || !q || !out) return MFA_ERR_ARG;
+  *out = nullptr;
+  if (q_dtype != MFA_F32 && q_dtype != MFA_F64) return MFA_ERR_ARG;
+  if (precision != MFA_PREC_FP64 && precision != MFA_PREC_MIXED) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  mfa_batch* b = new (std::nothrow) mfa_batch();
+  if (!b) return MFA_ERR_OOM;
+  b->h = h;
+  b->count = count;
+  b->prec = precision;
+  b->inst.assign(inst, inst + count);
+  b->cp_off.assign(count + 1, 0);
+  b->q_len.assign(count, 1);
+  // validate, count control points, group by (dimension, degree)
+  std::vector<std::vector<int>> grp((MFA_MAX_DIM + 1) * (MFA_MAX_DEGREE + 1));
+  for (int i = 0; i < count; ++i) {
+    const mfa_instance& in = b->inst[i];
+    if (in.dim < 1 || in.dim > MFA_MAX_DIM || in.degree < 1 || in.degree > MFA_MAX_DEGREE || in.q_offset < 0) {
+      delete b;
+      return MFA_ERR_ARG;
+    }
+    long long ncp = 1, len = 1;
+    for (int a = 0; a < in.dim; ++a) {
+      if (in.npts[a] < 1 || in.npts[a] > (1LL << 30) || in.nspans[a] < 1) {
+        delete b;
+        return MFA_ERR_ARG;
+      }
+      ncp *= in.nspans[a] + in.degree;
+      len *= in.npts[a];
+    }
+    b->cp_off[i + 1] = b->cp_off[i] + ncp;
+    b->q_len[i] = len;
+    b->q_total = std::max(b->q_total, in.q_offset + len);
+    grp[in.dim * (MFA_MAX_DEGREE + 1) + in.degree].push_back(i);
+  }
+  const size_t es = elem_size(precision);
+  const size_t qbytes = (size_t)b->q_total * (q_dtype == MFA_F64 ? 8 : 4);
+  int rc = pool_alloc(h, &b->buf, (size_t)b->cp_off[count] * es);
+  if (rc == MFA_OK) rc = pool_alloc(h, &b->tab, (size_t)count * 4 * sizeof(long long));
+  if (rc == MFA_OK && !q_on_device) rc = pool_alloc(h, &b->staged, qbytes);
+  if (rc != MFA_OK) {
+    mfa_batch_free(b);
+    return rc;
+  }
+  {
+    std::vector<long long> t(2 * (size_t)count);
+    for (int i = 0; i < count; ++i) {
+      t[i] = b->inst[i].q_offset;
+      t[count + i] = b->q_len[i];
+    }
+    cudaError_t e = cudaMemcpyAsync(b->tab, t.data(), t.size() * sizeof(long long), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) {
+      mfa_batch_free(b);
+      return cuda_status(e);
+    }
+  }
+  for (int d = 1; d <= MFA_MAX_DIM; ++d)
+    for (int p = 1; p <= MFA_MAX_DEGREE; ++p) {
+      const std::vector<int>& mem = grp[d * (MFA_MAX_DEGREE + 1) + p];
+      if (mem.empty()) continue;
+      mfa_model* md = nullptr;
+      rc = build_batch_group(b, d, p, mem, &md);
+      if (rc != MFA_OK) {
+        mfa_batch_free(b);
+        return rc;
+      }
+      b->groups.push_back(md);
+    }
+  const void* qd = q;
+  if (!q_on_device) {
+    cudaError_t e = cudaMemcpyAsync(b->staged, q, qbytes, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      mfa_batch_free(b);
+      return cuda_status(e);
+    }
+    qd = b->staged;
+    b->staged_dtype = q_dtype;
+  }
+  if (precision == MFA_PREC_FP64)
+    batch_fit<double>(b, qd, q_dtype);
+  else
+    batch_fit<ff>(b, qd, q_dtype);
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    mfa_batch_free(b);
+    return cuda_status(e);
+  }
+  int st = read_status(h);
+  if (st < 0) {
+    mfa_batch_free(b);
+    return st;
+  }
+  *out = b;
+  return MFA_OK;
+}
+
+int mfa_batch_refit(mfa_handle* h, mfa_batch* b, const void* q, int q_dtype) {
+  if (!h || !b || b->h != h || !q) return MFA_ERR_ARG;
+  if (q_dtype != MFA_F32 && q_dtype != MFA_F64) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  cudaError_t e = cudaSuccess;
+  if (!b->graph || b->graph_q != q || b->graph_dtype != q_dtype) {
+    if (b->graph) {
+      cudaGraphExecDestroy(b->graph);
+      b->graph = nullptr;
+    }
+    // capture the fit of every group once, on a private stream (the
+    // handle's stream may be the legacy default stream, which cannot be
+    // captured); tracing stays off inside the capture
+    if (!b->cap) {
+      e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        b->cap = nullptr;
+        return cuda_status(e);
+      }
+    }
+    const bool tr = h->trace_on;
+    trace_flush(h);
+    h->trace_on = false;
+    cudaStream_t user = h->stream;
+    h->stream = b->cap;
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      if (b->prec == MFA_PREC_FP64)
+        batch_fit<double>(b, q, q_dtype);
+      else
+        batch_fit<ff>(b, q, q_dtype);
+      const cudaError_t e2 = cudaStreamEndCapture(b->cap, &gr);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = e2;
+    }
+    h->stream = user;
+    h->trace_on = tr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+      b->graph = nullptr;
+      return cuda_status(e);
+    }
+    b->graph_q = q;
+    b->graph_dtype = q_dtype;
+  }
+  const int ti = trace_begin(h);
+  e = cudaGraphLaunch(b->graph, h->stream);
+  trace_end(h, TR_PROJECT_DATA, ti, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = read_status(h);
+  return st < 0 ? st : MFA_OK;
+}
+
+int64_t mfa_batch_num_ctrl(const mfa_batch* b) { return b ? (int64_t)b->cp_off[b->count] : MFA_ERR_ARG; }
+
+int mfa_batch_ctrl_offsets(const mfa_batch* b, int64_t* host_off) {
+  if (!b || !host_off) return MFA_ERR_ARG;
+  for (int i = 0; i <= b->count; ++i) host_off[i] = b->cp_off[i];
+  return MFA_OK;
+}
+
+int mfa_batch_get_ctrl(mfa_handle* h, const mfa_batch* b, double* host_out, int64_t cap) {
+  if (!h || !b || b->h != h || !host_out) return MFA_ERR_ARG;
+  const long long n = b->cp_off[b->count];
+  if (cap < n) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  int rc = ensure_ws(h, (size_t)n * sizeof(double));
+  if (rc != MFA_OK) return rc;
+  if (b->prec == MFA_PREC_FP64)
+    TRACED(h, TR_MISC, (launch_cast<double, double>((const double*)b->buf, (double*)h->ws, n, h->stream)));
+  else
+    TRACED(h, TR_MISC, (launch_cast<ff, double>((const ff*)b->buf, (double*)h->ws, n, h->stream)));
+  cudaError_t e = cudaMemcpyAsync(host_out, h->ws, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = read_status(h);
+  return st < 0 ? st : MFA_OK;
+}
+
+int mfa_batch_residual(mfa_handle* h, const mfa_batch* bc, const void* q, int q_dtype, int q_on_device, double* rms,
+                       double* maxabs) {
+  mfa_batch* b = const_cast<mfa_batch*>(bc);
+  if (!h || !b || b->h != h || !rms || !maxabs) return MFA_ERR_ARG;
+  if (!q) {
+    if (!b->staged) return MFA_ERR_ARG;
+    q = b->staged;
+    q_dtype = b->staged_dtype;
+    q_on_device = 1;
+  }
+  if (q_dtype != MFA_F32 && q_dtype != MFA_F64) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  const size_t qb = (size_t)b->q_total * (q_dtype == MFA_F64 ? 8 : 4);
+  void* qtmp = nullptr;
+  void* D = nullptr;
+  cudaError_t e = cudaSuccess;
+  int rc = pool_alloc(h, &D, (size_t)b->q_total * sizeof(double));
+  if (rc == MFA_OK && !q_on_device) {
+    rc = pool_alloc(h, &qtmp, qb);
+    if (rc == MFA_OK) e = cudaMemcpyAsync(qtmp, q, qb, cudaMemcpyHostToDevice, h->stream);
+    q = qtmp;
+  }
+  if (rc == MFA_OK && e == cudaSuccess) rc = batch_decode_any<double>(b, (double*)D);
+  const long long* off = (const long long*)b->tab;
+  double* res = (double*)h->d_partials;  // 2 doubles per instance, reused in chunks
+  std::vector<double> hr(2 * (size_t)std::min(b->count, 2 * kResidualBlocks));
+  for (int i0 = 0; rc == MFA_OK && e == cudaSuccess && i0 < b->count; i0 += 2 * kResidualBlocks) {
+    const int n = std::min(b->count - i0, 2 * kResidualBlocks);
+    if (q_dtype == MFA_F64)
+      TRACED(h, TR_RESIDUAL, launch_batch_residual<double>((const double*)D, (const double*)q, off + i0,
+                                                           off + b->count + i0, n, res, h->stream));
+    else
+      TRACED(h, TR_RESIDUAL, launch_batch_residual<float>((const double*)D, (const float*)q, off + i0,
+                                                          off + b->count + i0, n, res, h->stream));
+    e = cudaMemcpyAsync(hr.data(), res, 2 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    for (int k = 0; k < n && e == cudaSuccess; ++k) {
+      rms[i0 + k] = std::sqrt(hr[2 * k] / (double)b->q_len[i0 + k]);
+      maxabs[i0 + k] = hr[2 * k + 1];
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (qtmp) pool_free(h, qtmp);
+  if (D) pool_free(h, D);
+  if (rc != MFA_OK) return rc;
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = read_status(h);
+  return st < 0 ? st : MFA_OK;
+}
+
+int mfa_batch_decode(mfa_handle* h, const mfa_batch* bc, void* out, int out_dtype, int out_on_device) {
+  mfa_batch* b = const_cast<mfa_batch*>(bc);
+  if (!h || !b || b->h != h || !out) return MFA_ERR_ARG;
+  if (out_dtype != MFA_F32 && out_dtype != MFA_F64) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  const size_t osz = out_dtype == MFA_F64 ? 8 : 4;
+  void* dst = out;
+  int rc = MFA_OK;
+  if (!out_on_device) rc = pool_alloc(h, &dst, (size_t)b->q_total * osz);
+  if (rc != MFA_OK) return rc;
+  rc = out_dtype == MFA_F64 ? batch_decode_any<double>(b, (double*)dst) : batch_decode_any<float>(b, (float*)dst);
+  cudaError_t e = cudaSuccess;
+  if (rc == MFA_OK && !out_on_device)
+    e = cudaMemcpyAsync(out, dst, (size_t)b->q_total * osz, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (!out_on_device) pool_free(h, dst);
+  if (rc != MFA_OK) return rc;
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = read_status(h);
+  return st < 0 ? st : MFA_OK;
+}
+
+int mfa_batch_free(mfa_batch* b) {
+  if (!b) return MFA_ERR_ARG;
+  mfa_handle* h = b->h;
+  DeviceGuard g(h->device);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  for (mfa_model* md : b->groups) {
+    md->BL = md->X = md->P = nullptr;
+    mfa_free(md);
+  }
+  pool_free(h, b->buf);
+  pool_free(h, b->tab);
+  pool_free(h, b->staged);
+  delete b;
+  return MFA_OK;
+}
+

@@ -29,6 +29,8 @@ struct AxisSub {
 // Per-axis device tables.
 struct AxisDev {
   int M, nspans, p, n, S;
+  int pieces;               // 1: every piece (subs[i]) has its own knot vector with w1 - w0 spans over its
+                            // own points, spans numbered from its l0 (a batch of independent fits)
   const int* span;          // [M] knot span of every data point
   const double* vals_d;     // [M * (p+1)] N_{span+r,p}(u_k), r = 0..p
   const float* vals_f;      // same, rounded to FP32
@@ -77,6 +79,7 @@ struct AxisOp {
 // Host-side mirror of one axis.
 struct AxisHost {
   int M = 1, nspans = 1, p = 0, n = 1, S = 1;
+  int pieces = 0;
   std::vector<AxisSub> subs;
   std::vector<int> own_first, own_count, span_start, nL_tab;
   std::vector<int4> own_tab;
@@ -136,6 +139,10 @@ int launch_iter0_3d_ff(const LayoutDev& L, const long long* offL, const int* max
 long long average_ff_blocks(const LayoutDev& L);
 void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev, float* part,
                        unsigned long long* metrics, cudaStream_t st);
+
+template <typename TQ>
+void launch_batch_residual(const double* D, const TQ* Q, const long long* off, const long long* len, int count,
+                           double* out, cudaStream_t st);
 
 constexpr int kResidualBlocks = 1216;  // 8 x 152 SMs
 constexpr int kAvgBlocks = 152 * 4;     // persistent float-float update: four CTAs per SM

@@ -132,3 +132,56 @@ def uniform_points(npts: int, d: int, seed: int = 0) -> np.ndarray:
     """Uniform random points in [0,1]^d, shape (npts, d), for scattered decode."""
     rng = np.random.default_rng(seed)
     return rng.uniform(0.0, 1.0, size=(npts, d))
+
+
+def batch_instances(count: int = 4096, seed: int = 0, size2=(32, 512), size3=(16, 128), degrees=(2, 5),
+                    cp_ratio: int = 4, dims=(2, 3), dtype=np.float32):
+    """Seeded batch of independent grids shaped like the batched-fit workload.
+
+    Instances alternate over ``dims``; per-axis point counts are log-uniform
+    in ``size2`` (2-D) or ``size3`` (3-D; 1-D uses ``size2``); the degree is
+    uniform in ``degrees``; control points per axis are max(p + 1,
+    M // cp_ratio), i.e. nspans = that - p.  Fields alternate between a sum of
+    three shifted products of sin(x)/x on [-4 pi, 4 pi]^d and a sum of four
+    Gaussians (centres U[0,1]^d, sigma U[0.05, 0.2]) on [0,1]^d.
+
+    Returns (specs, data): specs are dicts with dim, degree, npts, nspans,
+    q_offset (grid axis 0 fastest, like a single fit); data is one array.
+    """
+    rng = np.random.default_rng(seed)
+    specs, parts, off = [], [], 0
+    for i in range(count):
+        d = dims[i % len(dims)]
+        lo, hi = size3 if d == 3 else size2
+        npts = [int(round(np.exp(rng.uniform(np.log(lo), np.log(hi))))) for _ in range(d)]
+        p = int(rng.integers(degrees[0], degrees[1] + 1))
+        nspans = [max(p + 1, M // cp_ratio) - p for M in npts]
+        kind = i % 4 < 2
+        if kind:
+            # sum of shifted separable sinc products on [-4 pi, 4 pi]^d
+            xs = [axis_coords(M, -4 * np.pi, 4 * np.pi) for M in npts]
+            field = 0.0
+            for _ in range(3):
+                a = rng.uniform(0.5, 1.0)
+                term = None
+                for ax in range(d):
+                    c = rng.uniform(-2 * np.pi, 2 * np.pi)
+                    f = sinc(xs[ax] - c)
+                    term = f if term is None else np.multiply.outer(f, term)
+                field = field + a * term
+        else:
+            xs = [axis_coords(M, 0.0, 1.0) for M in npts]
+            field = 0.0
+            for _ in range(4):
+                sig = rng.uniform(0.05, 0.2)
+                term = None
+                for ax in range(d):
+                    c = rng.uniform(0.0, 1.0)
+                    f = np.exp(-(xs[ax] - c) ** 2 / (2 * sig * sig))
+                    term = f if term is None else np.multiply.outer(f, term)
+                field = field + term
+        arr = np.asarray(field, dtype=np.float64).astype(dtype).ravel()
+        specs.append(dict(dim=d, degree=p, npts=npts, nspans=nspans, q_offset=off))
+        parts.append(arr)
+        off += arr.size
+    return specs, np.concatenate(parts)

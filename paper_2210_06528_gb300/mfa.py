@@ -50,6 +50,12 @@ class mfa_report(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class mfa_instance(ctypes.Structure):
+    """One independent fit of a batch (see mfa_encode_batch)."""
+    _fields_ = [("dim", ctypes.c_int32), ("degree", ctypes.c_int32), ("npts", ctypes.c_int64 * 3),
+                ("nspans", ctypes.c_int32 * 3), ("q_offset", ctypes.c_int64)]
+
+
 class MFAError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -98,8 +104,20 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_trace_read.restype = ctypes.c_int
     lib.mfa_trace_name.argtypes = [ctypes.c_int32]
     lib.mfa_trace_name.restype = ctypes.c_char_p
+    lib.mfa_encode_batch.argtypes = [P, ctypes.c_int32, ctypes.POINTER(mfa_instance), P, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int, ctypes.POINTER(P)]
+    lib.mfa_batch_refit.argtypes = [P, P, P, ctypes.c_int]
+    lib.mfa_batch_num_ctrl.argtypes = [P]
+    lib.mfa_batch_num_ctrl.restype = ctypes.c_int64
+    lib.mfa_batch_ctrl_offsets.argtypes = [P, P]
+    lib.mfa_batch_get_ctrl.argtypes = [P, P, P, ctypes.c_int64]
+    lib.mfa_batch_residual.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, P, P]
+    lib.mfa_batch_decode.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int]
+    lib.mfa_batch_free.argtypes = [P]
     for name in ["mfa_create", "mfa_destroy", "mfa_encode", "mfa_schwarz_iterate", "mfa_decode", "mfa_residual",
-                 "mfa_get_ctrl", "mfa_free", "mfa_sync"]:
+                 "mfa_get_ctrl", "mfa_free", "mfa_sync", "mfa_encode_plain", "mfa_encode_batch", "mfa_batch_refit",
+                 "mfa_batch_ctrl_offsets", "mfa_batch_get_ctrl", "mfa_batch_residual", "mfa_batch_decode",
+                 "mfa_batch_free"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -178,6 +196,70 @@ def mfa_encode_plain(h: int, layout: mfa_layout, q_ptr: int, q_dtype: int, q_on_
                                  int(q_on_device), int(max_iters), float(tol_dP), ctypes.byref(rep), ctypes.byref(m))
     _check(rc, "mfa_encode_plain", ok=(MFA_OK, MFA_NOT_CONVERGED))
     return m.value, rc, rep
+
+
+def make_instances(specs) -> "ctypes.Array":
+    """specs: iterable of dicts with dim, degree, npts, nspans, q_offset."""
+    specs = list(specs)
+    arr = (mfa_instance * len(specs))()
+    for k, sp in enumerate(specs):
+        d = int(sp["dim"])
+        arr[k].dim = d
+        arr[k].degree = int(sp["degree"])
+        npts = list(sp["npts"]) + [1] * (3 - d)
+        nsp = list(sp["nspans"]) + [1] * (3 - d)
+        for a in range(3):
+            arr[k].npts[a] = int(npts[a])
+            arr[k].nspans[a] = int(nsp[a])
+        arr[k].q_offset = int(sp["q_offset"])
+    return arr
+
+
+def mfa_encode_batch(h: int, inst, q_ptr: int, q_dtype: int, q_on_device: bool, precision: int) -> int:
+    b = ctypes.c_void_p()
+    _check(load().mfa_encode_batch(ctypes.c_void_p(h), len(inst), inst, ctypes.c_void_p(q_ptr), q_dtype,
+                                   int(q_on_device), int(precision), ctypes.byref(b)), "mfa_encode_batch")
+    return b.value
+
+
+def mfa_batch_refit(h: int, b: int, q_ptr: int, q_dtype: int) -> None:
+    _check(load().mfa_batch_refit(ctypes.c_void_p(h), ctypes.c_void_p(b), ctypes.c_void_p(q_ptr), q_dtype),
+           "mfa_batch_refit")
+
+
+def mfa_batch_num_ctrl(b: int) -> int:
+    return int(load().mfa_batch_num_ctrl(ctypes.c_void_p(b)))
+
+
+def mfa_batch_ctrl_offsets(b: int, count: int) -> np.ndarray:
+    off = np.empty(count + 1, dtype=np.int64)
+    _check(load().mfa_batch_ctrl_offsets(ctypes.c_void_p(b), off.ctypes.data), "mfa_batch_ctrl_offsets")
+    return off
+
+
+def mfa_batch_get_ctrl(h: int, b: int) -> np.ndarray:
+    n = mfa_batch_num_ctrl(b)
+    out = np.empty(n, dtype=np.float64)
+    _check(load().mfa_batch_get_ctrl(ctypes.c_void_p(h), ctypes.c_void_p(b), out.ctypes.data, n),
+           "mfa_batch_get_ctrl")
+    return out
+
+
+def mfa_batch_residual(h: int, b: int, count: int, q_ptr: int, q_dtype: int, q_on_device: bool):
+    rms = np.empty(count, dtype=np.float64)
+    mx = np.empty(count, dtype=np.float64)
+    _check(load().mfa_batch_residual(ctypes.c_void_p(h), ctypes.c_void_p(b), ctypes.c_void_p(q_ptr), q_dtype,
+                                     int(q_on_device), rms.ctypes.data, mx.ctypes.data), "mfa_batch_residual")
+    return rms, mx
+
+
+def mfa_batch_decode(h: int, b: int, out_ptr: int, out_dtype: int, out_on_device: bool) -> None:
+    _check(load().mfa_batch_decode(ctypes.c_void_p(h), ctypes.c_void_p(b), ctypes.c_void_p(out_ptr), out_dtype,
+                                   int(out_on_device)), "mfa_batch_decode")
+
+
+def mfa_batch_free(b: int) -> None:
+    _check(load().mfa_batch_free(ctypes.c_void_p(b)), "mfa_batch_free")
 
 
 def mfa_decode(h: int, m: int, pts_ptr: int, npts_q: int, deriv, out_ptr: int, out_dtype: int,
@@ -304,6 +386,13 @@ class Handle:
         m = mfa_encode(self.h, layout, ptr, code, dev)
         return Model(self, m, layout)
 
+    def encode_batch(self, specs, q, precision: int = MFA_PREC_MIXED) -> "Batch":
+        """Fit many independent grids at once (specs: dim, degree, npts, nspans, q_offset per instance)."""
+        inst = make_instances(specs)
+        ptr, code, dev, keep = _ptr_dtype(q)
+        b = mfa_encode_batch(self.h, inst, ptr, code, dev, precision)
+        return Batch(self, b, len(inst))
+
     def encode_plain(self, q, layout: mfa_layout, max_iters: int, tol_dP: float):
         """Encode and iterate in the per-subdomain comparator form; returns (Model, rc, report)."""
         ptr, code, dev, keep = _ptr_dtype(q)
@@ -374,3 +463,42 @@ class Model:
         if self.m:
             mfa_free(self.m)
             self.m = None
+
+
+class Batch:
+    """A batch of independent fits (mfa_encode_batch); control points are
+    concatenated in instance order."""
+
+    def __init__(self, handle: Handle, b: int, count: int):
+        self.handle = handle
+        self.b = b
+        self.count = count
+
+    def offsets(self) -> np.ndarray:
+        return mfa_batch_ctrl_offsets(self.b, self.count)
+
+    def ctrl(self) -> np.ndarray:
+        return mfa_batch_get_ctrl(self.handle.h, self.b)
+
+    def refit(self, q) -> None:
+        ptr, code, dev, keep = _ptr_dtype(q)
+        if not dev:
+            raise TypeError("refit takes device data")
+        mfa_batch_refit(self.handle.h, self.b, ptr, code)
+
+    def residual(self, q=None):
+        if q is None:
+            return mfa_batch_residual(self.handle.h, self.b, self.count, 0, MFA_F32, False)
+        ptr, code, dev, keep = _ptr_dtype(q)
+        return mfa_batch_residual(self.handle.h, self.b, self.count, ptr, code, dev)
+
+    def decode(self, out):
+        ptr, code, dev, keep = _ptr_dtype(out)
+        mfa_batch_decode(self.handle.h, self.b, ptr, code, dev)
+        return out
+
+    def free(self):
+        if self.b:
+            mfa_batch_free(self.b)
+            self.b = None
+

@@ -1,0 +1,107 @@
+"""Batches of independent fits (one subdomain each) against the oracle's
+global LSQ fit (Eq. minimization-problem, N = 1), instance by instance."""
+import numpy as np
+import pytest
+
+from mfa_cases import TOL_FP64, rel_diff
+from oracle import mfa_oracle as O
+from paper_2210_06528_gb300 import inputs, mfa
+
+pytestmark = pytest.mark.gpu
+
+
+def _oracle(spec, data):
+    d = spec["dim"]
+    npts = spec["npts"]
+    Q = data[spec["q_offset"]:spec["q_offset"] + int(np.prod(npts))].astype(np.float64).reshape(tuple(reversed(npts)))
+    prob = O.make_problem(spec["degree"], list(npts), list(spec["nspans"]), [1] * d, 0)
+    P = O.global_fit(prob, Q)
+    return prob, Q, P
+
+
+def _small_batch(seed, count=30):
+    return inputs.batch_instances(count, seed=seed, size2=(14, 70), size3=(10, 26), degrees=(1, 5), dims=(1, 2, 3))
+
+
+@pytest.mark.parametrize("precision", [mfa.MFA_PREC_FP64, mfa.MFA_PREC_MIXED])
+def test_batch_matches_oracle_per_instance(precision):
+    import torch
+    specs, data = _small_batch(7)
+    h = mfa.Handle(0)
+    try:
+        b = h.encode_batch(specs, torch.from_numpy(data).cuda(), precision)
+        P = b.ctrl()
+        off = b.offsets()
+        rms, mx = b.residual(torch.from_numpy(data).cuda())
+        D = b.decode(np.empty(data.size, dtype=np.float64))
+        for i, sp in enumerate(specs):
+            prob, Q, Pref = _oracle(sp, data)
+            Pi = P[off[i]:off[i + 1]]
+            assert rel_diff(Pi, Pref.ravel()) <= TOL_FP64, (i, sp)
+            st = O.residual_stats(prob, Q, Pref)
+            assert abs(rms[i] - st["rms"]) <= 0.01 * st["rms"] + 1e-15, (i, rms[i], st["rms"])
+            Dref = O.decode_grid(prob, Pref).ravel()
+            Di = D[sp["q_offset"]:sp["q_offset"] + Dref.size]
+            rng = float(Q.max() - Q.min())
+            assert np.abs(Di - Dref).max() <= 1e-9 * max(rng, 1.0)
+            assert abs(mx[i] - np.abs(Q.ravel() - Dref).max()) <= 1e-5 * max(rng, 1.0)
+        b.free()
+    finally:
+        h.close()
+
+
+def test_batch_refit_graph_equals_fresh_encode():
+    """The captured refit on new data gives the same control points as a
+    fresh batch encode of that data; replays on the same pointer reuse it."""
+    import torch
+    specs, data = _small_batch(11, count=20)
+    data2 = (2.0 * data).astype(np.float32)  # exact: a power-of-two scale commutes with every rounding
+    h = mfa.Handle(0)
+    try:
+        q1 = torch.from_numpy(data).cuda()
+        q2 = torch.from_numpy(data2).cuda()
+        b = h.encode_batch(specs, q1, mfa.MFA_PREC_MIXED)
+        b.refit(q2)
+        b.refit(q2)  # replay of the captured graph
+        P2 = b.ctrl()
+        c = h.encode_batch(specs, q2, mfa.MFA_PREC_MIXED)
+        assert np.array_equal(P2, c.ctrl())
+        b.refit(q1)  # new pointer: captured again
+        P1 = b.ctrl()
+        d = h.encode_batch(specs, q1, mfa.MFA_PREC_MIXED)
+        assert np.array_equal(P1, d.ctrl())
+        # linearity, exactly: fit(2 q) = 2 fit(q) bit for bit
+        assert np.array_equal(P2, 2.0 * P1)
+        for x in (b, c, d):
+            x.free()
+    finally:
+        h.close()
+
+
+def test_batch_host_data_and_staged_residual():
+    specs, data = _small_batch(3, count=12)
+    h = mfa.Handle(0)
+    try:
+        b = h.encode_batch(specs, data, mfa.MFA_PREC_FP64)
+        r1, m1 = b.residual(None)
+        r2, m2 = b.residual(data)
+        assert np.array_equal(r1, r2) and np.array_equal(m1, m2)
+        b.free()
+    finally:
+        h.close()
+
+
+def test_batch_layout_rejection():
+    """An instance with more control points than data points along an axis
+    fails the Schoenberg-Whitney precheck: no batch is created."""
+    specs, data = _small_batch(5, count=4)
+    bad = dict(specs[1])
+    bad["nspans"] = [bad["npts"][0] + 3] + list(bad["nspans"][1:])
+    specs[1] = bad
+    h = mfa.Handle(0)
+    try:
+        with pytest.raises(mfa.MFAError) as ei:
+            h.encode_batch(specs, data, mfa.MFA_PREC_MIXED)
+        assert ei.value.code == mfa.MFA_ERR_LAYOUT
+    finally:
+        h.close()
