@@ -32,6 +32,18 @@ __device__ __forceinline__ const float* fac_U<float>(const AxisDev& ax) { return
 template <>
 __device__ __forceinline__ const ff* fac_U<ff>(const AxisDev& ax) { return ax.facU_ff; }
 
+// Operand and element of this thread: from the tile map when there is one,
+// else operand blockIdx.y and element blockIdx.x * blockDim.x + threadIdx.x.
+__device__ __forceinline__ void tile_of(const TileMap& tm, int& opi, long long& idx) {
+  if (tm.op) {
+    opi = tm.op[blockIdx.x];
+    idx = tm.base[blockIdx.x] + threadIdx.x;
+  } else {
+    opi = blockIdx.y;
+    idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  }
+}
+
 __device__ __forceinline__ void unflatten(long long idx, const int* n, int* o) {
   o[0] = (int)(idx % n[0]);
   long long r = idx / n[0];
@@ -50,10 +62,12 @@ __device__ __forceinline__ bool finite_val(ff x) { return isfinite(x.hi); }
 // flags non-finite input.
 template <typename T, typename TIn>
 __global__ void k_contract(LayoutDev L, int axis, const AxisOp* ops, const TIn* __restrict__ in,
-                           T* __restrict__ out, int* status) {
-  const AxisOp op = ops[blockIdx.y];
+                           T* __restrict__ out, int* status, TileMap tm) {
+  int opi;
+  long long idx;
+  tile_of(tm, opi, idx);
+  const AxisOp op = ops[opi];
   const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
-  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nout) return;
   int o[3];
   unflatten(idx, op.out.n, o);
@@ -106,11 +120,16 @@ __device__ __forceinline__ T expand_one(const AxisDev& ax, const AxisOp& op, int
 }
 
 template <typename T, typename TOut>
-__global__ void k_expand(LayoutDev L, int axis, const AxisOp* ops, const T* __restrict__ in, TOut* __restrict__ out) {
-  const AxisOp op = ops[blockIdx.y];
+__global__ void k_expand(LayoutDev L, int axis, const AxisOp* ops, const T* __restrict__ in, TOut* __restrict__ out,
+                         TileMap tm) {
+  int opi;
+  long long idx0;
+  tile_of(tm, opi, idx0);
+  const AxisOp op = ops[opi];
   const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nout; idx += stride) {
+  // with a tile map every thread has one element; else a grid-stride loop
+  const long long stride = tm.op ? nout : (long long)gridDim.x * blockDim.x;
+  for (long long idx = idx0; idx < nout; idx += stride) {
     int o[3];
     unflatten(idx, op.out.n, o);
     const T val = expand_one<T>(L.ax[axis], op, axis, o, in);
@@ -233,12 +252,14 @@ __global__ void k_band_apply(LayoutDev L, int axis, const AxisOp* ops, const T* 
 // In-place banded Cholesky solve along one axis, one thread per fibre
 // (Sec. 2.3.1): forward L y = c, then backward L^T x = y.
 template <typename T>
-__global__ void k_band_solve(LayoutDev L, int axis, bool useU, const AxisOp* ops, T* x) {
-  const AxisOp op = ops[blockIdx.y];
+__global__ void k_band_solve(LayoutDev L, int axis, bool useU, const AxisOp* ops, T* x, TileMap tm) {
+  int opi;
+  long long f;
+  tile_of(tm, opi, f);
+  const AxisOp op = ops[opi];
   const View& v = op.out;
   const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
   const long long nf = (long long)v.n[a1] * v.n[a2];
-  const long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nf) return;
   const int i1 = (int)(f % v.n[a1]), i2 = (int)(f / v.n[a1]);
   const AxisDev& ax = L.ax[axis];
@@ -262,18 +283,26 @@ __global__ void k_band_solve(LayoutDev L, int axis, bool useU, const AxisOp* ops
 
 template <typename T, typename TIn>
 void launch_contract(const LayoutDev& L, int axis, const AxisOp* ops, int nops, int max_out, const TIn* in, T* out,
-                     int* status, cudaStream_t st) {
-  dim3 grid((max_out + 127) / 128, nops);
-  k_contract<T, TIn><<<grid, 128, 0, st>>>(L, axis, ops, in, out, status);
+                     int* status, cudaStream_t st, const TileMap* tm) {
+  if (tm && tm->op) {
+    if (tm->ntiles > 0) k_contract<T, TIn><<<tm->ntiles, kContractThreads, 0, st>>>(L, axis, ops, in, out, status, *tm);
+    return;
+  }
+  dim3 grid((max_out + kContractThreads - 1) / kContractThreads, nops);
+  k_contract<T, TIn><<<grid, kContractThreads, 0, st>>>(L, axis, ops, in, out, status, TileMap{});
 }
 
 template <typename T, typename TOut>
 void launch_expand(const LayoutDev& L, int axis, const AxisOp* ops, int nops, long long max_out, const T* in,
-                   TOut* out, cudaStream_t st) {
-  long long blocks = (max_out + 255) / 256;
+                   TOut* out, cudaStream_t st, const TileMap* tm) {
+  if (tm && tm->op) {
+    if (tm->ntiles > 0) k_expand<T, TOut><<<tm->ntiles, kExpandThreads, 0, st>>>(L, axis, ops, in, out, *tm);
+    return;
+  }
+  long long blocks = (max_out + kExpandThreads - 1) / kExpandThreads;
   if (blocks > 65535) blocks = 65535;
   dim3 grid((unsigned)blocks, nops);
-  k_expand<T, TOut><<<grid, 256, 0, st>>>(L, axis, ops, in, out);
+  k_expand<T, TOut><<<grid, kExpandThreads, 0, st>>>(L, axis, ops, in, out, TileMap{});
 }
 
 template <typename T, typename TQ>
@@ -295,33 +324,38 @@ void launch_band_apply(const LayoutDev& L, int axis, const AxisOp* ops, int nops
 
 template <typename T>
 void launch_band_solve(const LayoutDev& L, int axis, bool useU, const AxisOp* ops, int nops, int max_fibres, T* x,
-                       cudaStream_t st) {
-  dim3 grid((max_fibres + 63) / 64, nops);
-  k_band_solve<T><<<grid, 64, 0, st>>>(L, axis, useU, ops, x);
+                       cudaStream_t st, const TileMap* tm) {
+  if (tm && tm->op) {
+    if (tm->ntiles > 0) k_band_solve<T><<<tm->ntiles, kSolveThreads, 0, st>>>(L, axis, useU, ops, x, *tm);
+    return;
+  }
+  dim3 grid((max_fibres + kSolveThreads - 1) / kSolveThreads, nops);
+  k_band_solve<T><<<grid, kSolveThreads, 0, st>>>(L, axis, useU, ops, x, TileMap{});
 }
 
 #define MFA_INST_T(T)                                                                                        \
   template void launch_band_apply<T>(const LayoutDev&, int, const AxisOp*, int, int, const T*, T*, cudaStream_t);   \
-  template void launch_band_solve<T>(const LayoutDev&, int, bool, const AxisOp*, int, int, T*, cudaStream_t);      \
+  template void launch_band_solve<T>(const LayoutDev&, int, bool, const AxisOp*, int, int, T*, cudaStream_t,       \
+                                     const TileMap*);                                                            \
   template void launch_contract<T, float>(const LayoutDev&, int, const AxisOp*, int, int, const float*, T*, int*,  \
-                                          cudaStream_t);                                                           \
+                                          cudaStream_t, const TileMap*);                                           \
   template void launch_contract<T, double>(const LayoutDev&, int, const AxisOp*, int, int, const double*, T*, int*, \
-                                           cudaStream_t);                                                          \
+                                           cudaStream_t, const TileMap*);                                          \
   template void launch_expand_residual<T, float>(const LayoutDev&, int, const AxisOp*, long long, const T*,        \
                                                  const float*, double*, int, cudaStream_t);                        \
   template void launch_expand_residual<T, double>(const LayoutDev&, int, const AxisOp*, long long, const T*,       \
                                                   const double*, double*, int, cudaStream_t);                      \
   template void launch_expand<T, float>(const LayoutDev&, int, const AxisOp*, int, long long, const T*, float*,    \
-                                        cudaStream_t);                                                             \
+                                        cudaStream_t, const TileMap*);                                             \
   template void launch_expand<T, double>(const LayoutDev&, int, const AxisOp*, int, long long, const T*, double*,  \
-                                         cudaStream_t);
+                                         cudaStream_t, const TileMap*);
 
 MFA_INST_T(double)
 MFA_INST_T(float)
 MFA_INST_T(ff)
 template void launch_expand<ff, ff>(const LayoutDev&, int, const AxisOp*, int, long long, const ff*, ff*,
-                                    cudaStream_t);
+                                    cudaStream_t, const TileMap*);
 template void launch_contract<ff, ff>(const LayoutDev&, int, const AxisOp*, int, int, const ff*, ff*, int*,
-                                      cudaStream_t);
+                                      cudaStream_t, const TileMap*);
 
 }  // namespace mfa

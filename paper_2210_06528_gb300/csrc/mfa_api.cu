@@ -48,6 +48,8 @@ struct mfa_model {
   bool batch = false;              // one (dimension, degree) group of a batch of independent fits
   long long maxDec[3] = {0, 0, 0}; // batch: largest decode-stage output per axis
   long long decS1 = 0, decS2 = 0;  // batch: decode stage scratch sizes (elements)
+  TileMap tm_proj[3], tm_solve[3], tm_dec[3];  // batch: compact launches over the uneven instances
+  void* tiles = nullptr;                       // device storage of the tile maps
   const void* q_src = nullptr;     // plain form: the device data it re-reads every iteration
   int q_src_dtype = MFA_F32;
   int prec = MFA_PREC_FP64;
@@ -533,11 +535,12 @@ void run_encode(mfa_model* md, const TQ* q) {
     T* out = (a == md->dim - 1) ? BL : (a == 0 ? S1 : S2);
     if (a == 0)
       TRACED(h, TR_PROJECT_DATA,
-             (launch_contract<T, TQ>(L, 0, opsk(OP_PROJ0), ns, md->maxOut[0], q, out, h->d_status, h->stream)));
+             (launch_contract<T, TQ>(L, 0, opsk(OP_PROJ0), ns, md->maxOut[0], q, out, h->d_status, h->stream,
+                                     md->batch ? &md->tm_proj[0] : nullptr)));
     else
       TRACED(h, TR_PROJECT_REDUCED,
              (launch_contract<T, T>(L, a, opsk(OP_PROJ0 + a), ns, md->maxOut[a], a == 1 ? S1 : S2, out, nullptr,
-                                    h->stream)));
+                                    h->stream, md->batch ? &md->tm_proj[a] : nullptr)));
   }
   // iteration 0: unconstrained local solves on the L boxes
   int it0 = 0;
@@ -555,7 +558,8 @@ void run_encode(mfa_model* md, const TQ* q) {
         TRACED(h, TR_SOLVE_L,
                launch_band_solve<T>(L, a, false, opsk(OP_SOLVEL0 + a) + sd, 1, md->maxFibL[a], X, h->stream));
     } else {
-      TRACED(h, TR_SOLVE_L, launch_band_solve<T>(L, a, false, opsk(OP_SOLVEL0 + a), ns, md->maxFibL[a], X, h->stream));
+      TRACED(h, TR_SOLVE_L, launch_band_solve<T>(L, a, false, opsk(OP_SOLVEL0 + a), ns, md->maxFibL[a], X, h->stream,
+                                                 md->batch ? &md->tm_solve[a] : nullptr));
     }
   }
   if (md->batch) return;  // one subdomain per instance: the solution is X itself
@@ -1248,6 +1252,7 @@ int mfa_free(mfa_model* md) {
   DeviceGuard g(h->device);
   pool_free(h, md->arena);
   pool_free(h, md->big);
+  pool_free(h, md->tiles);
   h->live_models--;
   delete md;
   return MFA_OK;
@@ -1488,6 +1493,51 @@ int build_batch_group(mfa_batch* b, int d, int p, const std::vector<int>& mem, m
   }
   md->BL = md->X = b->buf;
   md->P = b->buf;
+  // tile maps: every operand of a launch split into blocks of the kernel's size
+  {
+    std::vector<int> top;
+    std::vector<long long> tbase;
+    struct Span { TileMap* tm; size_t first; };
+    std::vector<Span> spans;
+    auto add = [&](TileMap* tm, int kind, int threads, bool fibres, int a) {
+      spans.push_back({tm, top.size()});
+      for (int t = 0; t < ns; ++t) {
+        const View& v = ops[(size_t)kind * ns + t].out;
+        const int a1 = a == 0 ? 1 : 0, a2 = a == 2 ? 1 : 2;
+        const long long n = fibres ? (long long)v.n[a1] * v.n[a2] : (long long)v.n[0] * v.n[1] * v.n[2];
+        for (long long e = 0; e < n; e += threads) {
+          top.push_back(t);
+          tbase.push_back(e);
+        }
+      }
+      tm->ntiles = (int)(top.size() - spans.back().first);
+    };
+    for (int a = 0; a < d; ++a) {
+      add(&md->tm_proj[a], OP_PROJ0 + a, kContractThreads, false, a);
+      add(&md->tm_solve[a], OP_SOLVEL0 + a, kSolveThreads, true, a);
+      add(&md->tm_dec[a], OP_DEC0 + a, kExpandThreads, false, a);
+    }
+    const size_t nt = top.size();
+    rc = pool_alloc(h, &md->tiles, nt * (sizeof(int) + sizeof(long long)) + 16);
+    cudaError_t e = rc == MFA_OK ? cudaSuccess : cudaErrorMemoryAllocation;
+    long long* dbase = (long long*)md->tiles;
+    int* dop = (int*)(dbase + nt);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dbase, tbase.data(), nt * sizeof(long long), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dop, top.data(), nt * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    if (e != cudaSuccess) {
+      md->BL = md->X = md->P = nullptr;
+      pool_free(h, md->tiles);
+      md->tiles = nullptr;
+      pool_free(h, md->arena);
+      pool_free(h, md->big);
+      delete md;
+      return rc != MFA_OK ? rc : cuda_status(e);
+    }
+    for (const Span& sp : spans) {
+      sp.tm->op = dop + sp.first;
+      sp.tm->base = dbase + sp.first;
+    }
+  }
   h->live_models++;
   *out = md;
   return MFA_OK;
@@ -1522,10 +1572,12 @@ int batch_decode_into(mfa_batch* b, TOut* out) {
     for (int a = 0; a < md->dim; ++a) {
       const AxisOp* op = md->ops + (size_t)(OP_DEC0 + a) * ns;
       if (a == md->dim - 1) {
-        TRACED(h, TR_DECODE_OUT, (launch_expand<T, TOut>(md->L, a, op, ns, md->maxDec[a], in, out, h->stream)));
+        TRACED(h, TR_DECODE_OUT,
+               (launch_expand<T, TOut>(md->L, a, op, ns, md->maxDec[a], in, out, h->stream, &md->tm_dec[a])));
       } else {
         T* o = (a == 0) ? s1 : s2;
-        TRACED(h, TR_DECODE_STAGE, (launch_expand<T, T>(md->L, a, op, ns, md->maxDec[a], in, o, h->stream)));
+        TRACED(h, TR_DECODE_STAGE,
+               (launch_expand<T, T>(md->L, a, op, ns, md->maxDec[a], in, o, h->stream, &md->tm_dec[a])));
         in = o;
       }
     }

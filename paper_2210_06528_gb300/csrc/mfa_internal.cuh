@@ -86,6 +86,15 @@ struct AxisHost {
   int bandL_rows = 0, bandU_rows = 0;
 };
 
+// Compact launch over operands of very uneven sizes (batches of independent
+// fits): block b works on operand op[b], elements base[b] .. base[b] +
+// blockDim.x - 1 of it, so the grid holds exactly the tiles that exist.
+struct TileMap {
+  const int* op = nullptr;
+  const long long* base = nullptr;
+  int ntiles = 0;
+};
+
 // ---------------------------------------------------------------------------
 // kernel launchers (kernels_*.cu)
 // ---------------------------------------------------------------------------
@@ -97,10 +106,10 @@ void launch_chol(const AxisDev& ax, const double* AL, double* fLd, float* fLf, f
 
 template <typename T, typename TIn>
 void launch_contract(const LayoutDev& L, int axis, const AxisOp* ops, int nops, int max_out,
-                     const TIn* in, T* out, int* status, cudaStream_t st);
+                     const TIn* in, T* out, int* status, cudaStream_t st, const TileMap* tm = nullptr);
 template <typename T, typename TOut = T>
 void launch_expand(const LayoutDev& L, int axis, const AxisOp* ops, int nops, long long max_out,
-                   const T* in, TOut* out, cudaStream_t st);
+                   const T* in, TOut* out, cudaStream_t st, const TileMap* tm = nullptr);
 template <typename T, typename TQ>
 void launch_expand_residual(const LayoutDev& L, int axis, const AxisOp* op, long long nout, const T* in,
                             const TQ* q, double* partials, int nblocks, cudaStream_t st);
@@ -109,7 +118,7 @@ void launch_band_apply(const LayoutDev& L, int axis, const AxisOp* ops, int nops
                        const T* in, T* out, cudaStream_t st);
 template <typename T>
 void launch_band_solve(const LayoutDev& L, int axis, bool useU, const AxisOp* ops, int nops, int max_fibres,
-                       T* x, cudaStream_t st);
+                       T* x, cudaStream_t st, const TileMap* tm = nullptr);
 template <typename T>
 void launch_frame_gather(const LayoutDev& L, const long long* offL, int maxL, const T* P, T* Pt, cudaStream_t st);
 template <typename T>
@@ -145,6 +154,8 @@ void launch_batch_residual(const double* D, const TQ* Q, const long long* off, c
                            double* out, cudaStream_t st);
 
 constexpr int kResidualBlocks = 1216;  // 8 x 152 SMs
+// block sizes of the generic kernels (tile sizes of their TileMaps)
+constexpr int kContractThreads = 128, kExpandThreads = 256, kSolveThreads = 64;
 constexpr int kAvgBlocks = 152 * 4;     // persistent float-float update: four CTAs per SM
 
 }  // namespace mfa
