@@ -296,7 +296,62 @@ int mfa_batch_residual(mfa_handle* h, const mfa_batch* b, const void* q, int q_d
  * like the data: instance i at inst[i].q_offset). */
 int mfa_batch_decode(mfa_handle* h, const mfa_batch* b, void* out, int out_dtype, int out_on_device);
 
+/* Scattered decode of batch instances: query k evaluates instance qinst[k]
+ * at the points pts[pt_off[k] .. pt_off[k+1]), three doubles per point (the
+ * parameters u in [0,1] along axes 0, 1, 2, clamped; entries beyond the
+ * instance's dimension are ignored), writing one FP64 value per point into
+ * out.  All arrays on the host (on_device = 0) or all on the device; nq >= 1,
+ * offsets non-decreasing from pt_off[0] = 0.  Synchronous. */
+int mfa_batch_decode_points(mfa_handle* h, const mfa_batch* b, int32_t nq, const int32_t* qinst,
+                            const int64_t* pt_off, const double* pts, double* out, int on_device);
+
 int mfa_batch_free(mfa_batch* b);
+
+/* ---- Serving: continuous batching of encode requests and decode queries --
+ * No counterpart in the paper (which encodes one field per run); this is the
+ * serving form of the batch of independent fits.  Requests arrive from any
+ * host thread and get an id (> 0; a negative value is an error status).
+ * Admission is first come, first served against mem_budget bytes of device
+ * memory: an encode reserves its staged data, scratch and resident model, a
+ * decode its points and values; a request that alone exceeds the budget is
+ * refused with MFA_ERR_OOM.  `workers` threads each own a handle and a CUDA
+ * stream; a free worker takes every admitted request of one kind (encodes of
+ * one precision, at most max_batch of them, or decodes of resident models)
+ * as one job, so jobs overlap on the device and requests arriving meanwhile
+ * join the next job.
+ *   mfa_server_encode  fit one grid (FP32 data on the host, layout as one
+ *                      mfa_instance, q_offset ignored); the id names the
+ *                      model, which stays resident until mfa_server_release
+ *   mfa_server_decode  evaluate a model at npts points (3 doubles each: the
+ *                      parameters u in [0,1] per axis) into out (npts doubles);
+ *                      may be submitted while the model is still being fitted
+ *   mfa_server_wait    block until a request is done (timeout_s <= 0: no
+ *                      limit; MFA_ERR_TIMEOUT when it ran out), returning its
+ *                      status and timestamps (seconds since the server was
+ *                      created)
+ * The caller's buffers (data, points, values) must stay valid until the
+ * request is done.  mfa_server_destroy releases every model and joins the
+ * workers after the queued work. */
+typedef struct mfa_server mfa_server;
+typedef struct {
+  int32_t status;  /* MFA_OK or an error status */
+  int32_t kind;    /* 0 encode, 1 decode */
+  double t_submit, t_admit, t_start, t_done;
+} mfa_request_info;
+typedef struct {
+  int64_t budget, reserved, peak_reserved; /* bytes */
+  int64_t queued, resident_models, encode_jobs, decode_jobs;
+} mfa_server_stats_t;
+
+int mfa_server_create(int device, int32_t workers, int64_t mem_budget, int32_t max_batch, mfa_server** out);
+int64_t mfa_server_encode(mfa_server* s, const mfa_instance* inst, const void* host_q, int precision);
+int64_t mfa_server_decode(mfa_server* s, int64_t model, int64_t npts, const double* host_pts, double* host_out);
+int mfa_server_wait(mfa_server* s, int64_t id, double timeout_s, mfa_request_info* info);
+int mfa_server_release(mfa_server* s, int64_t model);
+int64_t mfa_server_num_ctrl(mfa_server* s, int64_t model);
+int mfa_server_get_ctrl(mfa_server* s, int64_t model, double* host_out, int64_t cap);
+int mfa_server_stats(mfa_server* s, mfa_server_stats_t* st);
+int mfa_server_destroy(mfa_server* s);
 
 /* Tracing (per-phase timing of Algorithm 1's steps, as in the paper's
  * setup / solve / iterate / decode breakdown, Sec. 3.2.4).  When enabled,

@@ -245,6 +245,68 @@ void launch_decode_points(const LayoutDev& L, const double* lo, const double* hi
                                                        deriv[0], deriv[1], deriv[2], P, out, out_dtype);
 }
 
+// Scattered decode of instances of a batch of independent fits: point k
+// belongs to query q with pt_off[q] <= k < pt_off[q+1], which evaluates
+// instance qinst[q]; coordinates are parameters u in [0,1] per axis (stride
+// 3, clamped), the value is sum over the (p+1)^dim control points of the
+// tensor-product basis (Sec. 2.1) in FP64.
+template <typename T>
+__global__ void k_decode_points_inst(const InstDesc* __restrict__ desc, const int* __restrict__ qinst,
+                                     const long long* __restrict__ pt_off, int nq, const double* __restrict__ pts,
+                                     const T* __restrict__ P, double* __restrict__ out) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= pt_off[nq]) return;
+  int lo = 0, hi = nq - 1;  // last query whose first point is <= k
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pt_off[mid] <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  const InstDesc D = desc[qinst[lo]];
+  double N[3][MFA_MAX_DEGREE + 1];
+  int span[3], pa[3];
+  for (int a = 0; a < 3; ++a) {
+    if (a < D.dim) {
+      const double u = fmin(fmax(pts[3 * k + a], 0.0), 1.0);
+      int j = (int)floor(u * D.nspans[a]);
+      if (j > D.nspans[a] - 1) j = D.nspans[a] - 1;
+      if (j < 0) j = 0;
+      span[a] = j;
+      pa[a] = D.p;
+      basis_derivs(j, u, D.p, D.nspans[a], 0, N[a]);
+    } else {
+      span[a] = 0;
+      pa[a] = 0;
+      N[a][0] = 1.0;
+    }
+  }
+  const long long n0 = D.n[0], n01 = (long long)D.n[0] * D.n[1];
+  double acc = 0.0;
+  for (int r2 = 0; r2 <= pa[2]; ++r2) {
+    double acc1 = 0.0;
+    for (int r1 = 0; r1 <= pa[1]; ++r1) {
+      double acc0 = 0.0;
+      const long long row = D.cp_off + (long long)(span[1] + r1) * n0 + (long long)(span[2] + r2) * n01;
+      for (int r0 = 0; r0 <= pa[0]; ++r0) acc0 += N[0][r0] * (double)P[row + span[0] + r0];
+      acc1 += N[1][r1] * acc0;
+    }
+    acc += N[2][r2] * acc1;
+  }
+  out[k] = acc;
+}
+
+template <typename T>
+void launch_decode_points_inst(const InstDesc* desc, const int* qinst, const long long* pt_off, int nq,
+                               long long npts, const double* pts, const T* P, double* out, cudaStream_t st) {
+  if (npts <= 0 || nq <= 0) return;
+  k_decode_points_inst<T><<<(unsigned)((npts + 127) / 128), 128, 0, st>>>(desc, qinst, pt_off, nq, pts, P, out);
+}
+
+template void launch_decode_points_inst<double>(const InstDesc*, const int*, const long long*, int, long long,
+                                                const double*, const double*, double*, cudaStream_t);
+template void launch_decode_points_inst<ff>(const InstDesc*, const int*, const long long*, int, long long,
+                                            const double*, const ff*, double*, cudaStream_t);
+
 template <typename TIn, typename TOut>
 __global__ void k_cast(const TIn* in, TOut* out, long long n) {
   const long long stride = (long long)gridDim.x * blockDim.x;

@@ -1313,7 +1313,8 @@ struct mfa_batch {
   std::vector<long long> q_len;          // values per instance
   long long q_total = 0;                 // length of the data array the instances span
   void* buf = nullptr;                   // control points of every instance (B_L, then solved in place)
-  void* tab = nullptr;                   // device: q offsets [count], lengths [count], residual out [2 count]
+  void* tab = nullptr;                   // device: q offsets [count], lengths [count]
+  void* desc = nullptr;                  // device: InstDesc [count] for scattered decode
   void* staged = nullptr;                // device copy of host data
   int staged_dtype = MFA_F32;
   cudaGraphExec_t graph = nullptr;       // captured refit
@@ -1633,6 +1634,7 @@ int mfa_encode_batch(mfa_handle* h, int32_t count, const mfa_instance* inst, con
   const size_t qbytes = (size_t)b->q_total * (q_dtype == MFA_F64 ? 8 : 4);
   int rc = pool_alloc(h, &b->buf, (size_t)b->cp_off[count] * es);
   if (rc == MFA_OK) rc = pool_alloc(h, &b->tab, (size_t)count * 4 * sizeof(long long));
+  if (rc == MFA_OK) rc = pool_alloc(h, &b->desc, (size_t)count * sizeof(InstDesc));
   if (rc == MFA_OK && !q_on_device) rc = pool_alloc(h, &b->staged, qbytes);
   if (rc != MFA_OK) {
     mfa_batch_free(b);
@@ -1644,7 +1646,21 @@ int mfa_encode_batch(mfa_handle* h, int32_t count, const mfa_instance* inst, con
       t[i] = b->inst[i].q_offset;
       t[count + i] = b->q_len[i];
     }
+    std::vector<InstDesc> dd(count);
+    for (int i = 0; i < count; ++i) {
+      const mfa_instance& in = b->inst[i];
+      InstDesc& D = dd[i];
+      D.dim = in.dim;
+      D.p = in.degree;
+      for (int a = 0; a < 3; ++a) {
+        D.nspans[a] = a < in.dim ? in.nspans[a] : 1;
+        D.n[a] = a < in.dim ? in.nspans[a] + in.degree : 1;
+      }
+      D.cp_off = b->cp_off[i];
+    }
     cudaError_t e = cudaMemcpyAsync(b->tab, t.data(), t.size() * sizeof(long long), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(b->desc, dd.data(), dd.size() * sizeof(InstDesc), cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) {
       mfa_batch_free(b);
       return cuda_status(e);
@@ -1858,8 +1874,95 @@ int mfa_batch_free(mfa_batch* b) {
   }
   pool_free(h, b->buf);
   pool_free(h, b->tab);
+  pool_free(h, b->desc);
   pool_free(h, b->staged);
   delete b;
   return MFA_OK;
+}
+
+namespace mfa {
+// Scattered decode of batch instances on any handle h (the batch's device
+// tables are only read); host or device arrays.
+int batch_decode_points_impl(mfa_handle* h, const mfa_batch* b, int32_t nq, const int32_t* qinst,
+                             const int64_t* pt_off, const double* pts, double* out, int on_device) {
+  if (!h || !b || nq < 1 || !qinst || !pt_off || !pts || !out) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  long long npts = 0;
+  const int32_t* dq = qinst;
+  const long long* doff = (const long long*)pt_off;
+  const double* dp = pts;
+  double* dout = out;
+  void* tmp = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!on_device) {
+    if (pt_off[0] != 0) return MFA_ERR_ARG;
+    for (int k = 0; k < nq; ++k) {
+      if (qinst[k] < 0 || qinst[k] >= b->count || pt_off[k + 1] < pt_off[k]) return MFA_ERR_ARG;
+    }
+    npts = pt_off[nq];
+    const size_t bytes = (size_t)nq * sizeof(int32_t) + (size_t)(nq + 1) * sizeof(long long) +
+                         (size_t)npts * 3 * sizeof(double) + (size_t)npts * sizeof(double) + 64;
+    int rc = pool_alloc(h, &tmp, bytes);
+    if (rc != MFA_OK) return rc;
+    char* c = (char*)tmp;
+    long long* o = (long long*)c;
+    double* pp = (double*)(o + nq + 1);
+    double* ov = pp + 3 * npts;
+    int32_t* qi = (int32_t*)(ov + npts);
+    e = cudaMemcpyAsync(o, pt_off, (size_t)(nq + 1) * sizeof(long long), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(qi, qinst, (size_t)nq * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess && npts)
+      e = cudaMemcpyAsync(pp, pts, (size_t)npts * 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+    dq = qi;
+    doff = o;
+    dp = pp;
+    dout = ov;
+  } else {
+    // the point count is needed for the grid: read the last offset
+    e = cudaMemcpyAsync(h->h_pinned, pt_off + nq, sizeof(long long), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) std::memcpy(&npts, h->h_pinned, sizeof(long long));
+  }
+  if (e == cudaSuccess && npts > 0) {
+    if (b->prec == MFA_PREC_FP64)
+      TRACED(h, TR_DECODE_POINTS, (launch_decode_points_inst<double>((const InstDesc*)b->desc, dq, doff, nq, npts, dp,
+                                                                     (const double*)b->buf, dout, h->stream)));
+    else
+      TRACED(h, TR_DECODE_POINTS, (launch_decode_points_inst<ff>((const InstDesc*)b->desc, dq, doff, nq, npts, dp,
+                                                                 (const ff*)b->buf, dout, h->stream)));
+  }
+  if (e == cudaSuccess && !on_device && npts > 0)
+    e = cudaMemcpyAsync(out, dout, (size_t)npts * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (tmp) pool_free(h, tmp);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = read_status(h);
+  return st < 0 ? st : MFA_OK;
+}
+
+// Control points of one instance as FP64 into host memory, on handle h.
+int batch_instance_ctrl(mfa_handle* h, const mfa_batch* b, int index, double* host_out, int64_t cap) {
+  if (!h || !b || index < 0 || index >= b->count || !host_out) return MFA_ERR_ARG;
+  const long long n = b->cp_off[index + 1] - b->cp_off[index];
+  if (cap < n) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  int rc = ensure_ws(h, (size_t)n * sizeof(double));
+  if (rc != MFA_OK) return rc;
+  if (b->prec == MFA_PREC_FP64)
+    launch_cast<double, double>((const double*)b->buf + b->cp_off[index], (double*)h->ws, n, h->stream);
+  else
+    launch_cast<ff, double>((const ff*)b->buf + b->cp_off[index], (double*)h->ws, n, h->stream);
+  cudaError_t e = cudaMemcpyAsync(host_out, h->ws, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e == cudaSuccess ? MFA_OK : cuda_status(e);
+}
+
+long long batch_instance_num_ctrl(const mfa_batch* b, int index) { return b->cp_off[index + 1] - b->cp_off[index]; }
+}  // namespace mfa
+
+int mfa_batch_decode_points(mfa_handle* h, const mfa_batch* b, int32_t nq, const int32_t* qinst,
+                            const int64_t* pt_off, const double* pts, double* out, int on_device) {
+  if (!h || !b || b->h != h) return MFA_ERR_ARG;
+  return mfa::batch_decode_points_impl(h, b, nq, qinst, pt_off, pts, out, on_device);
 }
 

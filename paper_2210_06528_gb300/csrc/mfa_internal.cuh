@@ -149,6 +149,22 @@ long long average_ff_blocks(const LayoutDev& L);
 void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev, float* part,
                        unsigned long long* metrics, cudaStream_t st);
 
+// Batch internals used by the serving runtime (any handle may read a batch).
+int batch_decode_points_impl(mfa_handle* h, const mfa_batch* b, int32_t nq, const int32_t* qinst,
+                             const int64_t* pt_off, const double* pts, double* out, int on_device);
+int batch_instance_ctrl(mfa_handle* h, const mfa_batch* b, int index, double* host_out, int64_t cap);
+long long batch_instance_num_ctrl(const mfa_batch* b, int index);
+
+// One instance of a batch of independent fits, for scattered decode.
+struct InstDesc {
+  int dim, p;
+  int nspans[3], n[3];
+  long long cp_off;
+};
+template <typename T>
+void launch_decode_points_inst(const InstDesc* desc, const int* qinst, const long long* pt_off, int nq,
+                               long long npts, const double* pts, const T* P, double* out, cudaStream_t st);
+
 template <typename TQ>
 void launch_batch_residual(const double* D, const TQ* Q, const long long* off, const long long* len, int count,
                            double* out, cudaStream_t st);

@@ -56,6 +56,23 @@ class mfa_instance(ctypes.Structure):
                 ("nspans", ctypes.c_int32 * 3), ("q_offset", ctypes.c_int64)]
 
 
+class mfa_request_info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("kind", ctypes.c_int32), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class mfa_server_stats_t(ctypes.Structure):
+    _fields_ = [("budget", ctypes.c_int64), ("reserved", ctypes.c_int64), ("peak_reserved", ctypes.c_int64),
+                ("queued", ctypes.c_int64), ("resident_models", ctypes.c_int64), ("encode_jobs", ctypes.c_int64),
+                ("decode_jobs", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class MFAError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -114,10 +131,24 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_batch_residual.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, P, P]
     lib.mfa_batch_decode.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int]
     lib.mfa_batch_free.argtypes = [P]
+    lib.mfa_batch_decode_points.argtypes = [P, P, ctypes.c_int32, P, P, P, P, ctypes.c_int]
+    lib.mfa_server_create.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(P)]
+    lib.mfa_server_encode.argtypes = [P, ctypes.POINTER(mfa_instance), P, ctypes.c_int]
+    lib.mfa_server_encode.restype = ctypes.c_int64
+    lib.mfa_server_decode.argtypes = [P, ctypes.c_int64, ctypes.c_int64, P, P]
+    lib.mfa_server_decode.restype = ctypes.c_int64
+    lib.mfa_server_wait.argtypes = [P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(mfa_request_info)]
+    lib.mfa_server_release.argtypes = [P, ctypes.c_int64]
+    lib.mfa_server_num_ctrl.argtypes = [P, ctypes.c_int64]
+    lib.mfa_server_num_ctrl.restype = ctypes.c_int64
+    lib.mfa_server_get_ctrl.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64]
+    lib.mfa_server_stats.argtypes = [P, ctypes.POINTER(mfa_server_stats_t)]
+    lib.mfa_server_destroy.argtypes = [P]
     for name in ["mfa_create", "mfa_destroy", "mfa_encode", "mfa_schwarz_iterate", "mfa_decode", "mfa_residual",
                  "mfa_get_ctrl", "mfa_free", "mfa_sync", "mfa_encode_plain", "mfa_encode_batch", "mfa_batch_refit",
                  "mfa_batch_ctrl_offsets", "mfa_batch_get_ctrl", "mfa_batch_residual", "mfa_batch_decode",
-                 "mfa_batch_free"]:
+                 "mfa_batch_free", "mfa_batch_decode_points", "mfa_server_create", "mfa_server_wait",
+                 "mfa_server_release", "mfa_server_get_ctrl", "mfa_server_stats", "mfa_server_destroy"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -256,6 +287,73 @@ def mfa_batch_residual(h: int, b: int, count: int, q_ptr: int, q_dtype: int, q_o
 def mfa_batch_decode(h: int, b: int, out_ptr: int, out_dtype: int, out_on_device: bool) -> None:
     _check(load().mfa_batch_decode(ctypes.c_void_p(h), ctypes.c_void_p(b), ctypes.c_void_p(out_ptr), out_dtype,
                                    int(out_on_device)), "mfa_batch_decode")
+
+
+def mfa_batch_decode_points(h: int, b: int, qinst, pt_off, pts, out) -> None:
+    """Host arrays: qinst int32 [nq], pt_off int64 [nq + 1], pts float64 [npts, 3], out float64 [npts]."""
+    qinst = np.ascontiguousarray(qinst, dtype=np.int32)
+    pt_off = np.ascontiguousarray(pt_off, dtype=np.int64)
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    if out.dtype != np.float64 or not out.flags.c_contiguous:
+        raise TypeError("out must be a contiguous float64 array")
+    _check(load().mfa_batch_decode_points(ctypes.c_void_p(h), ctypes.c_void_p(b), len(qinst), qinst.ctypes.data,
+                                          pt_off.ctypes.data, pts.ctypes.data, out.ctypes.data, 0),
+           "mfa_batch_decode_points")
+
+
+def mfa_server_create(device: int, workers: int, mem_budget: int, max_batch: int) -> int:
+    s = ctypes.c_void_p()
+    _check(load().mfa_server_create(int(device), int(workers), int(mem_budget), int(max_batch), ctypes.byref(s)),
+           "mfa_server_create")
+    return s.value
+
+
+def mfa_server_encode(s: int, inst, q_ptr: int, precision: int) -> int:
+    rid = load().mfa_server_encode(ctypes.c_void_p(s), ctypes.byref(inst), ctypes.c_void_p(q_ptr), int(precision))
+    if rid < 0:
+        raise MFAError(int(rid), "mfa_server_encode")
+    return int(rid)
+
+
+def mfa_server_decode(s: int, model: int, npts: int, pts_ptr: int, out_ptr: int) -> int:
+    rid = load().mfa_server_decode(ctypes.c_void_p(s), int(model), int(npts), ctypes.c_void_p(pts_ptr),
+                                   ctypes.c_void_p(out_ptr))
+    if rid < 0:
+        raise MFAError(int(rid), "mfa_server_decode")
+    return int(rid)
+
+
+def mfa_server_wait(s: int, rid: int, timeout_s: float = 0.0):
+    info = mfa_request_info()
+    rc = load().mfa_server_wait(ctypes.c_void_p(s), int(rid), float(timeout_s), ctypes.byref(info))
+    return rc, info
+
+
+def mfa_server_release(s: int, model: int) -> None:
+    _check(load().mfa_server_release(ctypes.c_void_p(s), int(model)), "mfa_server_release")
+
+
+def mfa_server_num_ctrl(s: int, model: int) -> int:
+    return int(load().mfa_server_num_ctrl(ctypes.c_void_p(s), int(model)))
+
+
+def mfa_server_get_ctrl(s: int, model: int) -> np.ndarray:
+    n = mfa_server_num_ctrl(s, model)
+    if n < 0:
+        raise MFAError(n, "mfa_server_num_ctrl")
+    out = np.empty(n, dtype=np.float64)
+    _check(load().mfa_server_get_ctrl(ctypes.c_void_p(s), int(model), out.ctypes.data, n), "mfa_server_get_ctrl")
+    return out
+
+
+def mfa_server_stats(s: int) -> dict:
+    st = mfa_server_stats_t()
+    _check(load().mfa_server_stats(ctypes.c_void_p(s), ctypes.byref(st)), "mfa_server_stats")
+    return st.as_dict()
+
+
+def mfa_server_destroy(s: int) -> None:
+    _check(load().mfa_server_destroy(ctypes.c_void_p(s)), "mfa_server_destroy")
 
 
 def mfa_batch_free(b: int) -> None:
@@ -497,8 +595,66 @@ class Batch:
         mfa_batch_decode(self.handle.h, self.b, ptr, code, dev)
         return out
 
+    def decode_points(self, qinst, pt_off, pts, out=None):
+        """Scattered decode: query k evaluates instance qinst[k] at pts[pt_off[k]:pt_off[k+1]]
+        (parameters in [0,1], three per point); returns float64 values."""
+        pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+        if out is None:
+            out = np.empty(len(pts), dtype=np.float64)
+        mfa_batch_decode_points(self.handle.h, self.b, qinst, pt_off, pts, out)
+        return out
+
     def free(self):
         if self.b:
             mfa_batch_free(self.b)
             self.b = None
+
+
+class Server:
+    """Continuous-batching server (mfa_server_*): encode requests and decode
+    queries from any thread; ids name requests and, for encodes, models.
+    Buffers passed in must stay alive until the request is done; the object
+    keeps references to them until wait() returns."""
+
+    def __init__(self, device: int = 0, workers: int = 3, mem_budget: int = 8 << 30, max_batch: int = 64):
+        self.s = mfa_server_create(device, workers, mem_budget, max_batch)
+        self._keep = {}
+
+    def encode(self, spec, q, precision: int = MFA_PREC_MIXED) -> int:
+        inst = make_instances([dict(spec, q_offset=0)])[0]
+        a = q if hasattr(q, "data_ptr") else np.ascontiguousarray(q, dtype=np.float32)
+        ptr = a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+        rid = mfa_server_encode(self.s, inst, ptr, precision)
+        self._keep[rid] = a
+        return rid
+
+    def decode(self, model: int, pts, out) -> int:
+        p = pts if hasattr(pts, "data_ptr") else np.ascontiguousarray(pts, dtype=np.float64)
+        pp = p.data_ptr() if hasattr(p, "data_ptr") else p.ctypes.data
+        op = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        n = (p.numel() if hasattr(p, "numel") else p.size) // 3
+        rid = mfa_server_decode(self.s, model, n, pp, op)
+        self._keep[rid] = (p, out)
+        return rid
+
+    def wait(self, rid: int, timeout_s: float = 0.0):
+        rc, info = mfa_server_wait(self.s, rid, timeout_s)
+        if rc != MFA_ERR_TIMEOUT:
+            self._keep.pop(rid, None)
+        return rc, info.as_dict()
+
+    def release(self, model: int) -> None:
+        mfa_server_release(self.s, model)
+
+    def ctrl(self, model: int) -> np.ndarray:
+        return mfa_server_get_ctrl(self.s, model)
+
+    def stats(self) -> dict:
+        return mfa_server_stats(self.s)
+
+    def close(self):
+        if self.s:
+            mfa_server_destroy(self.s)
+            self.s = None
+            self._keep.clear()
 

@@ -105,3 +105,40 @@ def test_batch_layout_rejection():
         assert ei.value.code == mfa.MFA_ERR_LAYOUT
     finally:
         h.close()
+
+
+def test_batch_decode_points_matches_grid_and_oracle():
+    """Scattered decode of batch instances: at the grid parameters it equals
+    the batch's grid decode; at random parameters it equals the oracle's
+    decode of the oracle fit."""
+    import torch
+    specs, data = _small_batch(13, count=10)
+    h = mfa.Handle(0)
+    rng = np.random.default_rng(0)
+    try:
+        b = h.encode_batch(specs, torch.from_numpy(data).cuda(), mfa.MFA_PREC_FP64)
+        D = b.decode(np.empty(data.size, dtype=np.float64))
+        qinst, off, pts, ref = [], [0], [], []
+        for i, sp in enumerate(specs):
+            d, npts = sp["dim"], sp["npts"]
+            grids = [np.arange(M) / max(M - 1, 1) for M in npts]
+            mesh = np.stack(np.meshgrid(*reversed(grids), indexing="ij"), -1).reshape(-1, d)[:, ::-1]
+            P3 = np.zeros((len(mesh), 3))
+            P3[:, :d] = mesh
+            qinst.append(i)
+            pts.append(P3)
+            off.append(off[-1] + len(P3))
+            ref.append(D[sp["q_offset"]:sp["q_offset"] + len(P3)])
+        vals = b.decode_points(qinst, off, np.concatenate(pts))
+        assert np.abs(vals - np.concatenate(ref)).max() <= 1e-11 * max(1.0, np.abs(data).max())
+        # random parameters against the oracle
+        for i in (0, 4, 7):
+            sp = specs[i]
+            prob, Q, Pref = _oracle(sp, data)
+            u = rng.uniform(0, 1, size=(257, 3))
+            got = b.decode_points([i], [0, len(u)], u)
+            want = O.scattered_decode(prob, Pref, u[:, :sp["dim"]])
+            assert np.abs(got - want).max() <= 1e-9 * max(1.0, np.abs(want).max())
+        b.free()
+    finally:
+        h.close()

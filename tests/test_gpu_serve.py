@@ -1,0 +1,117 @@
+"""Serving runtime: continuous batching of encode requests and decode queries.
+
+Every fit and every decoded value is the same whether a request runs alone or
+in a mix with others in flight (each instance is computed independently of
+the rest of its batch), admission keeps the reserved memory within the
+budget, and a query of a released model fails cleanly."""
+import numpy as np
+import pytest
+
+from mfa_cases import TOL_FP64, rel_diff
+from oracle import mfa_oracle as O
+from paper_2210_06528_gb300 import inputs, mfa
+
+pytestmark = pytest.mark.gpu
+
+
+def _workload(seed, count=8):
+    specs, data = inputs.batch_instances(count, seed=seed, size2=(24, 90), size3=(12, 28), degrees=(3, 3),
+                                         dims=(2, 3))
+    payloads = [data[sp["q_offset"]:sp["q_offset"] + int(np.prod(sp["npts"]))].copy() for sp in specs]
+    rng = np.random.default_rng(seed)
+    queries = []
+    for i in range(count):
+        for _ in range(2):
+            n = int(rng.integers(1, 3000))
+            queries.append((i, rng.uniform(0, 1, size=(n, 3))))
+    return specs, payloads, queries
+
+
+def _run(srv, specs, payloads, queries, alone):
+    models, ctrl, vals = [], [], []
+    if alone:
+        for sp, q in zip(specs, payloads):
+            rid = srv.encode(sp, q)
+            rc, _ = srv.wait(rid)
+            assert rc == mfa.MFA_OK
+            models.append(rid)
+        outs = []
+        for i, u in queries:
+            out = np.empty(len(u))
+            rc, _ = srv.wait(srv.decode(models[i], u, out))
+            assert rc == mfa.MFA_OK
+            outs.append(out)
+    else:
+        models = [srv.encode(sp, q) for sp, q in zip(specs, payloads)]
+        outs = [np.empty(len(u)) for _, u in queries]
+        rids = [srv.decode(models[i], u, o) for (i, u), o in zip(queries, outs)]  # before the fits finish
+        for rid in models + rids:
+            rc, _ = srv.wait(rid, 120.0)
+            assert rc == mfa.MFA_OK
+    for m in models:
+        ctrl.append(srv.ctrl(m))
+    return models, ctrl, outs
+
+
+def test_results_alone_equal_results_in_the_mix():
+    specs, payloads, queries = _workload(21)
+    srv = mfa.Server(0, workers=3, mem_budget=4 << 30)
+    try:
+        m1, c1, v1 = _run(srv, specs, payloads, queries, alone=True)
+        m2, c2, v2 = _run(srv, specs, payloads, queries, alone=False)
+        for a, b in zip(c1, c2):
+            assert np.array_equal(a, b)
+        for a, b in zip(v1, v2):
+            assert np.array_equal(a, b)
+        st = srv.stats()
+        assert st["resident_models"] == 2 * len(specs)
+        # parity of the served fit with the oracle's global fit
+        for i in (0, 3):
+            sp = specs[i]
+            Q = payloads[i].astype(np.float64).reshape(tuple(reversed(sp["npts"])))
+            prob = O.make_problem(sp["degree"], list(sp["npts"]), list(sp["nspans"]), [1] * sp["dim"], 0)
+            assert rel_diff(c1[i], O.global_fit(prob, Q).ravel()) <= TOL_FP64
+        for m in m1 + m2:
+            srv.release(m)
+        assert srv.stats()["reserved"] == 0
+    finally:
+        srv.close()
+
+
+def test_admission_under_a_tight_budget():
+    """A budget that fits a few requests at a time: everything still
+    completes in order of admission and the reservation never exceeds it."""
+    specs, payloads, queries = _workload(5, count=10)
+    budget = 24 << 20
+    srv = mfa.Server(0, workers=2, mem_budget=budget)
+    try:
+        ids = [srv.encode(sp, q) for sp, q in zip(specs, payloads)]
+        infos = []
+        for rid in ids:
+            rc, info = srv.wait(rid, 120.0)
+            assert rc == mfa.MFA_OK
+            infos.append(info)
+        st = srv.stats()
+        assert st["peak_reserved"] <= budget
+        assert all(infos[k]["t_admit"] <= infos[k + 1]["t_admit"] for k in range(len(infos) - 1))
+        for rid in ids:
+            srv.release(rid)
+        assert srv.stats()["reserved"] == 0
+        with pytest.raises(mfa.MFAError) as ei:
+            srv.encode(dict(specs[0], npts=[4000, 4000], nspans=[900, 900], dim=2), np.zeros(16_000_000, np.float32))
+        assert ei.value.code == mfa.MFA_ERR_OOM
+    finally:
+        srv.close()
+
+
+def test_query_of_a_released_model_fails():
+    specs, payloads, queries = _workload(9, count=2)
+    srv = mfa.Server(0, workers=1, mem_budget=1 << 30)
+    try:
+        m = srv.encode(specs[0], payloads[0])
+        assert srv.wait(m)[0] == mfa.MFA_OK
+        srv.release(m)
+        with pytest.raises(mfa.MFAError):
+            srv.decode(m, np.zeros((4, 3)), np.empty(4))
+    finally:
+        srv.close()
