@@ -242,6 +242,117 @@ def algorithmic_bytes(cls_name, wl, qbytes, model_info):
     return None
 
 
+def bench_batch(h, torch, mfa, stream, steps, count=4096, seed=0):
+    """Batch of independent fits: one full encode (host layout, setup, fit),
+    then timed refits of the captured CUDA graph on device data and one
+    per-instance residual."""
+    specs, data = inputs.batch_instances(count, seed=seed)
+    q = torch.from_numpy(data).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = h.encode_batch(specs, q, mfa.MFA_PREC_MIXED)
+    torch.cuda.synchronize()
+    enc_s = time.perf_counter() - t0
+    b.refit(q)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(max(steps, 1)):
+        b.refit(q)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    refit_ms = e0.elapsed_time(e1) / max(steps, 1)
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    rms, mx = b.residual(q)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    res_ms = r0.elapsed_time(r1)
+    b.free()
+    npts = int(data.size)
+    d2 = sum(1 for sp in specs if sp["dim"] == 2)
+    return {"workload": f"{count} independent fits ({d2} 2-D 32..512^2, {count - d2} 3-D 16..128^3 log-uniform, "
+                        "degree 2..5, control points max(p+1, M/4) per axis, sinc / Gaussian sums), mixed precision",
+            "points": npts,
+            "encode_s_incl_host_layout": enc_s, "refit_ms": refit_ms, "refit_pts_per_s": npts / (refit_ms * 1e-3),
+            "residual_ms": res_ms, "fit_plus_residual_pts_per_s": npts / ((refit_ms + res_ms) * 1e-3),
+            "rms_median": float(np.median(rms)), "rms_max": float(rms.max()),
+            "refit": "one CUDA graph per batch (projection + solves of every (dimension, degree) group)"}
+
+
+def bench_serve(torch, mfa, n_enc=160, mix=4, seed=1, workers=3, budget=48 << 30):
+    """Serving: a Poisson stream of encode requests (2-D 64..512^2, 3-D
+    32..256^3 log-uniform, p = 3, sinc / Gaussian sums, control points M/4 per
+    axis) mixed 1:4 with decode queries of 1e3..1e6 uniform random points
+    against a resident model chosen uniformly among those already requested.
+    Saturation is measured by submitting everything at once; then the same
+    stream is offered at 0.5x, 0.8x and 1.0x that rate."""
+    specs, data = inputs.batch_instances(n_enc, seed=seed, size2=(64, 512), size3=(32, 256), degrees=(3, 3))
+    payloads = [torch.from_numpy(data[sp["q_offset"]:sp["q_offset"] + int(np.prod(sp["npts"]))].copy()).pin_memory()
+                for sp in specs]
+    rng = np.random.default_rng(seed + 1)
+    stream = []  # (kind, index): encode k, or decode (model among encodes 0..k, points)
+    qpts = []
+    for k in range(n_enc):
+        stream.append(("enc", k))
+        for _ in range(mix):
+            m = int(rng.integers(0, k + 1))
+            n = int(round(np.exp(rng.uniform(np.log(1e3), np.log(1e6)))))
+            qpts.append(torch.from_numpy(rng.uniform(0, 1, size=(n, 3))).pin_memory())
+            stream.append(("dec", m, len(qpts) - 1))
+    outs = [torch.empty(len(q), dtype=torch.float64).pin_memory() for q in qpts]
+    enc_pts = sum(int(np.prod(sp["npts"])) for sp in specs)
+    dec_pts = sum(len(q) for q in qpts)
+
+    def run(rate):
+        srv = mfa.Server(0, workers=workers, mem_budget=budget)
+        ids, kinds, models = [], [], {}
+        t0 = time.perf_counter()
+        gaps = rng.exponential(1.0 / rate, size=len(stream)) if rate else np.zeros(len(stream))
+        t_next = t0
+        for ev, gap in zip(stream, gaps):
+            t_next += gap
+            while rate and time.perf_counter() < t_next:
+                time.sleep(min(1e-4, max(t_next - time.perf_counter(), 0)))
+            if ev[0] == "enc":
+                rid = srv.encode(specs[ev[1]], payloads[ev[1]])
+                models[ev[1]] = rid
+            else:
+                rid = srv.decode(models[ev[1]], qpts[ev[2]], outs[ev[2]])
+            ids.append(rid)
+            kinds.append(ev[0])
+        lat = {"enc": [], "dec": []}
+        t_end = 0.0
+        for rid, kd in zip(ids, kinds):
+            rc, info = srv.wait(rid, 600.0)
+            if rc != mfa.MFA_OK:
+                raise RuntimeError(f"serving request failed: {mfa.status_string(rc)}")
+            lat[kd].append(info["t_done"] - info["t_submit"])
+            t_end = max(t_end, info["t_done"])
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        allv = np.array(lat["enc"] + lat["dec"]) * 1e3
+        return {"requests_per_s": len(stream) / wall, "pts_per_s": (enc_pts + dec_pts) / wall, "wall_s": wall,
+                "p50_ms": float(np.percentile(allv, 50)), "p99_ms": float(np.percentile(allv, 99)),
+                "encode_p50_ms": float(np.percentile(np.array(lat["enc"]) * 1e3, 50)),
+                "encode_p99_ms": float(np.percentile(np.array(lat["enc"]) * 1e3, 99)),
+                "decode_p50_ms": float(np.percentile(np.array(lat["dec"]) * 1e3, 50)),
+                "decode_p99_ms": float(np.percentile(np.array(lat["dec"]) * 1e3, 99)),
+                "encode_jobs": st["encode_jobs"], "decode_jobs": st["decode_jobs"],
+                "peak_reserved_gb": st["peak_reserved"] / 1e9}
+
+    run(0)  # warm-up (allocations, module loading)
+    sat = run(0)
+    out = {"workload": f"{n_enc} encodes (2-D 64..512^2 / 3-D 32..256^3, p=3, control points M/4) + "
+                       f"{n_enc * mix} decode queries (1e3..1e6 points), Poisson arrivals",
+           "encode_points": enc_pts, "decode_points": dec_pts, "workers": workers, "budget_gb": budget / 1e9,
+           "saturation": sat, "offered": {}}
+    for f in (0.5, 0.8, 1.0):
+        out["offered"][f"{f:.1f}x"] = run(f * sat["requests_per_s"])
+    return out
+
+
 def run_gb300(args, wl):
     import torch
     import torch.distributed as dist
@@ -354,6 +465,11 @@ def run_gb300(args, wl):
                  "gpu_launches": sum(n for (_, n) in ptrace.values()),
                  "form": "one launch per subdomain and stage; window data re-read every iteration"}
 
+    # ---- batched independent fits: 4096 uneven 2-D / 3-D grids (sizes
+    # log-uniform 32..512 / 16..128, degree 2..5, control points M/4 per axis)
+    batched = None if args.no_batch else bench_batch(h, torch, mfa, stream, args.steps)
+    serving = None if args.no_serve else bench_serve(torch, mfa)
+
     # ---- end to end through the C ABI with pinned host buffers: the data
     # cross to the device once (encode stages them; the residual reuses that
     # copy) and the fitted control points come back into a pinned buffer
@@ -422,6 +538,7 @@ def run_gb300(args, wl):
                        "parallelism": f"replicas x{world}"},
             "decode_pts_per_s": world * M / (dec_ms * 1e-3), "decode_ms": dec_ms,
             "plain_gpu": plain, "vs_plain_gpu": (value / plain["value"]) if plain else None,
+            "batched_fits": batched, "serving": serving,
             "roofline": roof, "dominant_kernel": dom[0] if dom else None, "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks,
@@ -432,13 +549,15 @@ def run_gb300(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="3d", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the per-subdomain comparator run")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched independent fits")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
