@@ -157,6 +157,18 @@ int mfa_schwarz_iterate(mfa_handle* h, mfa_model* m, int32_t max_iters, double t
 int mfa_decode(mfa_handle* h, const mfa_model* m, const double* pts, int64_t npts_q,
                const int32_t* deriv, void* out, int out_dtype, int out_on_device);
 
+/* Update rule of the global control points from the subdomains' owned
+ * copies (Sec. 2.3).  MFA_UPDATE_AVERAGE (the default): the uniformly
+ * weighted average, w = 1/n_s.  MFA_UPDATE_OWNER: every control point takes
+ * the copy of the subdomain whose core holds its Greville abscissa
+ * (t_{g+1} + ... + t_{g+p})/p, per axis (restricted additive Schwarz); with
+ * overlap >= degree both rules have the global fit as their fixed point.
+ * Setting the rule recomputes the current global control points from the
+ * copies the model holds (after mfa_encode: the iteration-0 copies), so the
+ * rule applies to every update that follows.  Not for batch models. */
+enum { MFA_UPDATE_AVERAGE = 0, MFA_UPDATE_OWNER = 1 };
+int mfa_set_update_rule(mfa_handle* h, mfa_model* m, int rule);
+
 /* The per-subdomain comparator form of encode + Schwarz iteration (the
  * plain FP64 method as a straightforward GPU port would run it; no
  * counterpart entry point in the paper, which runs one MPI task per

@@ -377,10 +377,59 @@ def _local_mats(prob: Problem, s, Nglob, cols: str):
     return mats
 
 
-def average_copies(prob: Problem, subs, copies) -> tuple:
-    """Uniformly weighted average of every owned copy, w = 1/n_s (Sec. 2.3.2).
+def greville_owner(prob: Problem, a: int) -> np.ndarray:
+    """Owner-takes update (the restricted additive Schwarz variant of Sec. 2.3):
+    along axis a, the subdomain whose core span range [a_s, b_s) holds the
+    Greville abscissa xi_g = (t_{g+1} + ... + t_{g+p}) / p of control point g
+    (the last core also holds xi = 1).  Decided exactly: with knots
+    t_i = k_i / nspans, xi_g * nspans * p is the integer sum of the k_i."""
+    p, ns = prob.p, prob.nspans[a]
+    n = ns + p
+    k = [min(max(i - p, 0), ns) for i in range(n + p + 1)]  # t_i = k[i] / ns
+    pcs = prob.pieces(a)
+    own = np.empty(n, dtype=np.int64)
+    for g in range(n):
+        S = sum(k[g + 1:g + p + 1]) if p > 0 else k[g] + k[g + 1]
+        den = p if p > 0 else 2
+        own[g] = -1
+        for i, pc in enumerate(pcs):
+            last = i == len(pcs) - 1
+            if pc.a * den <= S and (S < pc.b * den or (last and S <= pc.b * den)):
+                own[g] = i
+                break
+        if own[g] < 0:
+            raise ValueError("Greville abscissa outside every core")
+    return own
+
+
+def average_copies(prob: Problem, subs, copies, update: str = "average") -> tuple:
+    """Update of the global control points from the owned copies.
+
+    update="average": uniformly weighted average of every owned copy,
+    w = 1/n_s (Sec. 2.3.2).  update="owner": every control point takes the
+    copy of the subdomain owning its Greville abscissa (greville_owner),
+    axis by axis in the tensor product.
 
     Returns (P, spread) where spread[g] = max copy - min copy of CP g."""
+    if update == "owner":
+        P, spread = average_copies(prob, subs, copies, "average")
+        own = [greville_owner(prob, a) for a in range(prob.d)]
+        pieces = [prob.pieces(a) for a in range(prob.d)]
+        P = np.full(P.shape, np.nan)
+        for s, c in zip(subs, copies):
+            masks = []
+            for a in range(prob.d):
+                ia = pieces[a].index(s[a])
+                masks.append(own[a][list(s[a].U)] == ia)
+            M = masks[0]
+            for a in range(1, prob.d):
+                M = np.multiply.outer(masks[a], M)  # numpy axis order: last grid axis first
+            sl = _box_slices([pc.U for pc in s], prob.d)
+            view = P[sl]
+            view[M] = c[M]
+        if np.isnan(P).any():
+            raise ValueError("a control point has no Greville owner among its owning subdomains")
+        return P, spread
     shape = tuple(reversed(prob.ncp()))
     acc = np.zeros(shape)
     cnt = np.zeros(shape)
@@ -406,7 +455,7 @@ def multiplicity(prob: Problem) -> np.ndarray:
     return cnt
 
 
-def schwarz_initial(prob: Problem, Q: np.ndarray) -> SchwarzState:
+def schwarz_initial(prob: Problem, Q: np.ndarray, update: str = "average") -> SchwarzState:
     """Iteration 0 of Algorithm 1: every subdomain solves the unconstrained
     local LSQ on its window data with all of L_s free (Eq. minimization-problem);
     the owned part U_s of each local solution is kept and averaged."""
@@ -420,13 +469,13 @@ def schwarz_initial(prob: Problem, Q: np.ndarray) -> SchwarzState:
         frames.append(PL)
         u_in_l = [range(pc.a - pc.w0, pc.a - pc.w0 + len(pc.U)) for pc in s]
         copies.append(box(PL, u_in_l).copy())
-    P, spread = average_copies(prob, subs, copies)
+    P, spread = average_copies(prob, subs, copies, update)
     st = SchwarzState(P=P, copies=copies, frames=frames, k=0)
     st.history.append({"k": 0, "spread": float(spread.max(initial=0.0))})
     return st
 
 
-def schwarz_step(prob: Problem, Q: np.ndarray, st: SchwarzState) -> SchwarzState:
+def schwarz_step(prob: Problem, Q: np.ndarray, st: SchwarzState, update: str = "average") -> SchwarzState:
     """One outer iteration k >= 1 of Algorithm 1.
 
     Exchange: each subdomain reads its frame F_s = L_s minus U_s from the
@@ -454,7 +503,7 @@ def schwarz_step(prob: Problem, Q: np.ndarray, st: SchwarzState) -> SchwarzState
         full[_box_slices(u_in_l, prob.d)] = PU
         frames.append(full)
         copies.append(PU)
-    P, spread = average_copies(prob, subs, copies)
+    P, spread = average_copies(prob, subs, copies, update)
     dP = float(np.max(np.abs(P - st.P)))
     pmax = float(np.max(np.abs(P)))
     new = SchwarzState(P=P, copies=copies, frames=frames, k=st.k + 1, history=list(st.history))
@@ -470,19 +519,19 @@ def residual_stats(prob: Problem, Q: np.ndarray, P: np.ndarray) -> dict:
 
 
 def schwarz_solve(prob: Problem, Q: np.ndarray, max_iters: int = 200, tol_dP: float = 0.0,
-                  tol_rms_stall: float = 0.0, keep_iterates: bool = False) -> dict:
+                  tol_rms_stall: float = 0.0, keep_iterates: bool = False, update: str = "average") -> dict:
     """Algorithm 1 to convergence.
 
     Stops after iteration k >= 1 when dP_rel = max|P^k - P^{k-1}| / max|P^k|
     <= tol_dP, or (if tol_rms_stall > 0) when the decoded RMS changes by at
     most tol_rms_stall * RMS_k, or at max_iters.
     """
-    st = schwarz_initial(prob, Q)
+    st = schwarz_initial(prob, Q, update)
     iterates = [st.P.copy()] if keep_iterates else None
     rms_prev = residual_stats(prob, Q, st.P)["rms"] if tol_rms_stall > 0 else None
     converged = False
     while st.k < max_iters:
-        st = schwarz_step(prob, Q, st)
+        st = schwarz_step(prob, Q, st, update)
         if keep_iterates:
             iterates.append(st.P.copy())
         h = st.history[-1]

@@ -1194,6 +1194,7 @@ struct AvgTabs {
   const int4 *ot0, *ot1, *ot2;
   const int *nl0, *nl1;
   const long long* off;
+  const int *pk0, *pk1, *pk2;  // owner-takes: slot (0 / 1) of the Greville owner per axis
 };
 
 // All copies of control point (g0, g1, g2), loaded independently: slot
@@ -1227,7 +1228,7 @@ __device__ __forceinline__ void avg_load(const LayoutDev& L, const AvgTabs& T, c
 }
 
 __device__ __forceinline__ void avg_finish(const AvgCopies& cp, bool has_prev, long long g, ff* __restrict__ P,
-                                           float& dmax, float& pmax, float& spread) {
+                                           float& dmax, float& pmax, float& spread, int owner_slot) {
   ff sum(0.f, 0.f), first(0.f, 0.f);
   float dlo = 0.f, dhi = 0.f;
   int cnt = 0;
@@ -1246,7 +1247,12 @@ __device__ __forceinline__ void avg_finish(const AvgCopies& cp, bool has_prev, l
     }
     ++cnt;
   }
-  const ff pn = cnt == 1 ? sum : sum * ff(c_inv_hi[cnt], c_inv_lo[cnt]);
+  ff pn = cnt == 1 ? sum : sum * ff(c_inv_hi[cnt], c_inv_lo[cnt]);
+  if (owner_slot >= 0) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (c == owner_slot) pn = cp.v[c];
+  }
   P[g] = pn;
   pmax = fmaxf(pmax, fabsf(pn.hi));
   spread = fmaxf(spread, dhi - dlo);
@@ -1259,10 +1265,11 @@ __device__ __forceinline__ void avg_finish(const AvgCopies& cp, bool has_prev, l
 __global__ void __launch_bounds__(kAvgThreads, 4) k_average_ff(LayoutDev L, const long long* __restrict__ offL,
                                                                const ff* __restrict__ X, ff* __restrict__ P,
                                                                const ff* __restrict__ Pprev, float* __restrict__ part,
-                                                               int stage_tables) {
+                                                               int stage_tables, int rule) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int n0 = (int)L.ncp[0], n1 = (int)L.ncp[1], n2 = (int)L.ncp[2];
-  AvgTabs T{L.ax[0].own_tab, L.ax[1].own_tab, L.ax[2].own_tab, L.ax[0].nL_tab, L.ax[1].nL_tab, offL};
+  AvgTabs T{L.ax[0].own_tab, L.ax[1].own_tab, L.ax[2].own_tab, L.ax[0].nL_tab, L.ax[1].nL_tab, offL,
+            L.ax[0].own_pick, L.ax[1].own_pick, L.ax[2].own_pick};
   if (stage_tables) {
     int4* t0 = reinterpret_cast<int4*>(smem);
     int4* t1 = t0 + n0;
@@ -1270,14 +1277,20 @@ __global__ void __launch_bounds__(kAvgThreads, 4) k_average_ff(LayoutDev L, cons
     long long* off = reinterpret_cast<long long*>(t2 + n2);
     int* l0 = reinterpret_cast<int*>(off + L.nsub);
     int* l1 = l0 + L.S[0];
+    int* k0 = l1 + L.S[1];
+    int* k1 = k0 + n0;
+    int* k2 = k1 + n1;
     for (int i = threadIdx.x; i < n0; i += blockDim.x) t0[i] = T.ot0[i];
     for (int i = threadIdx.x; i < n1; i += blockDim.x) t1[i] = T.ot1[i];
     for (int i = threadIdx.x; i < n2; i += blockDim.x) t2[i] = T.ot2[i];
     for (int i = threadIdx.x; i < L.nsub; i += blockDim.x) off[i] = offL[i];
     for (int i = threadIdx.x; i < L.S[0]; i += blockDim.x) l0[i] = T.nl0[i];
     for (int i = threadIdx.x; i < L.S[1]; i += blockDim.x) l1[i] = T.nl1[i];
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) k0[i] = T.pk0[i];
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) k1[i] = T.pk1[i];
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) k2[i] = T.pk2[i];
     __syncthreads();
-    T = AvgTabs{t0, t1, t2, l0, l1, off};
+    T = AvgTabs{t0, t1, t2, l0, l1, off, k0, k1, k2};
   }
   float dmax = 0.f, pmax = 0.f, spread = 0.f;
   const long long nrows = (long long)n1 * n2;
@@ -1288,7 +1301,8 @@ __global__ void __launch_bounds__(kAvgThreads, 4) k_average_ff(LayoutDev L, cons
       const long long g = (long long)g0 + (long long)n0 * r;
       AvgCopies cp;
       avg_load(L, T, X, Pprev, g, T.ot0[g0], o1, o2, cp);
-      avg_finish(cp, Pprev != nullptr, g, P, dmax, pmax, spread);
+      const int slot = rule == UPDATE_OWNER ? T.pk0[g0] + 2 * T.pk1[g1] + 4 * T.pk2[g2] : -1;
+      avg_finish(cp, Pprev != nullptr, g, P, dmax, pmax, spread, slot);
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -1359,7 +1373,7 @@ long long average_ff_blocks(const LayoutDev&) { return kAvgBlocks; }
 
 // `part` holds 3 floats per block of the launch (average_ff_blocks).
 void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev, float* part,
-                       unsigned long long* metrics, cudaStream_t st) {
+                       unsigned long long* metrics, cudaStream_t st, int rule) {
   static bool init[64] = {};  // reciprocal table in constant memory, set once per device
   int dev = 0;
   cudaGetDevice(&dev);
@@ -1375,10 +1389,10 @@ void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, f
     init[dev] = true;
   }
   const int threads = (int)std::min<long long>(kAvgThreads, ((L.ncp[0] + 31) / 32) * 32);
-  const size_t tab = (size_t)(L.ncp[0] + L.ncp[1] + L.ncp[2]) * sizeof(int4) + (size_t)L.nsub * sizeof(long long) +
-                     (size_t)(L.S[0] + L.S[1]) * sizeof(int);
+  const size_t tab = (size_t)(L.ncp[0] + L.ncp[1] + L.ncp[2]) * (sizeof(int4) + sizeof(int)) +
+                     (size_t)L.nsub * sizeof(long long) + (size_t)(L.S[0] + L.S[1]) * sizeof(int);
   const int stage = tab <= 40 * 1024;
-  k_average_ff<<<kAvgBlocks, threads, stage ? tab : 0, st>>>(L, offL, X, P, Pprev, part, stage);
+  k_average_ff<<<kAvgBlocks, threads, stage ? tab : 0, st>>>(L, offL, X, P, Pprev, part, stage, rule);
   cudaMemsetAsync(metrics, 0, 3 * sizeof(unsigned long long), st);
   k_metrics_reduce<<<152, 256, 0, st>>>(part, average_ff_blocks(L), metrics);
 }

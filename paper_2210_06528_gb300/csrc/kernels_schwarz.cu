@@ -74,7 +74,7 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* addr, doub
 // patterns of non-negative doubles.
 template <typename T>
 __global__ void k_average(LayoutDev L, const long long* offL, const T* __restrict__ X, T* __restrict__ P,
-                          const T* __restrict__ Pprev, unsigned long long* metrics) {
+                          const T* __restrict__ Pprev, unsigned long long* metrics, int rule) {
   const long long n = L.ncp[0] * L.ncp[1] * L.ncp[2];
   const long long stride = (long long)gridDim.x * blockDim.x;
   double dmax = 0.0, pmax = 0.0, spread = 0.0;
@@ -91,6 +91,7 @@ __global__ void k_average(LayoutDev L, const long long* offL, const T* __restric
     }
     double sum = 0.0, lo = INFINITY, hi = -INFINITY;
     int cnt = 0;
+    T owner_val = T(0);
     for (int c2 = 0; c2 < c[2]; ++c2)
       for (int c1 = 0; c1 < c[1]; ++c1)
         for (int c0 = 0; c0 < c[0]; ++c0) {
@@ -99,13 +100,16 @@ __global__ void k_average(LayoutDev L, const long long* offL, const T* __restric
           const AxisSub b0 = L.ax[0].subs[sa0], b1 = L.ax[1].subs[sa1], b2 = L.ax[2].subs[sa2];
           const long long li = (long long)(gi[0] - b0.l0) +
                                (long long)b0.nL * ((long long)(gi[1] - b1.l0) + (long long)b1.nL * (gi[2] - b2.l0));
-          const double v = (double)X[offL[s] + li];
+          const T xv = X[offL[s] + li];
+          const double v = (double)xv;
+          if (c0 == L.ax[0].own_pick[gi[0]] && c1 == L.ax[1].own_pick[gi[1]] && c2 == L.ax[2].own_pick[gi[2]])
+            owner_val = xv;
           sum += v;
           lo = fmin(lo, v);
           hi = fmax(hi, v);
           ++cnt;
         }
-    const T pn = (T)(sum / cnt);
+    const T pn = rule == UPDATE_OWNER ? owner_val : (T)(sum / cnt);
     P[g] = pn;
     pmax = fmax(pmax, fabs((double)pn));
     spread = fmax(spread, hi - lo);
@@ -138,11 +142,11 @@ void launch_rhs_finalize(const LayoutDev& L, const long long* offL, const long l
 
 template <typename T>
 void launch_average(const LayoutDev& L, const long long* offL, const T* X, T* P, const T* Pprev,
-                    unsigned long long* metrics, cudaStream_t st) {
+                    unsigned long long* metrics, cudaStream_t st, int rule) {
   const long long n = L.ncp[0] * L.ncp[1] * L.ncp[2];
   long long blocks = (n + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  k_average<T><<<(unsigned)blocks, 256, 0, st>>>(L, offL, X, P, Pprev, metrics);
+  k_average<T><<<(unsigned)blocks, 256, 0, st>>>(L, offL, X, P, Pprev, metrics, rule);
 }
 
 // ---------------------------------------------------------------------------
@@ -326,7 +330,7 @@ void launch_cast(const TIn* in, TOut* out, long long n, cudaStream_t st) {
   template void launch_rhs_finalize<T>(const LayoutDev&, const long long*, const long long*, int, const T*,      \
                                        const T*, T*, cudaStream_t);                                              \
   template void launch_average<T>(const LayoutDev&, const long long*, const T*, T*, const T*, unsigned long long*, \
-                                  cudaStream_t);                                                                  \
+                                  cudaStream_t, int);                                                             \
   template void launch_decode_points<T>(const LayoutDev&, const double*, const double*, const double*, long long, \
                                         const int*, const T*, void*, int, cudaStream_t);                          \
   template void launch_cast<T, double>(const T*, double*, long long, cudaStream_t);                              \

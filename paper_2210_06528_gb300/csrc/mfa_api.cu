@@ -46,6 +46,7 @@ struct mfa_model {
   int q_staged_dtype = MFA_F32;
   bool plain = false;              // per-subdomain comparator form (mfa_encode_plain)
   bool batch = false;              // one (dimension, degree) group of a batch of independent fits
+  int update = UPDATE_AVERAGE;     // rule of the global update from the owned copies
   long long maxDec[3] = {0, 0, 0}; // batch: largest decode-stage output per axis
   long long decS1 = 0, decS2 = 0;  // batch: decode stage scratch sizes (elements)
   TileMap tm_proj[3], tm_solve[3], tm_dec[3];  // batch: compact launches over the uneven instances
@@ -322,6 +323,31 @@ int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int
   }
   ax.nL_tab.resize(nsub);
   for (int s = 0; s < nsub; ++s) ax.nL_tab[s] = ax.subs[s].nL;
+  // owner-takes update: the owner of control point g is the subdomain whose
+  // core holds its Greville abscissa xi_g = (t_{g+1} + ... + t_{g+p}) / p;
+  // with t_i = c_i / nspans, xi_g * nspans * p = sum of the c_i, exact
+  ax.own_pick.assign(ax.n, 0);
+  for (int g = 0; g < ax.n; ++g) {
+    auto c = [&](int i) { return std::min(std::max(i - p, 0), nspans); };
+    long long S = 0, den = p;
+    if (p > 0) {
+      for (int i = g + 1; i <= g + p; ++i) S += c(i);
+    } else {
+      S = c(g) + c(g + 1);
+      den = 2;
+    }
+    int owner = -1;
+    for (int s = 0; s < nsub && owner < 0; ++s) {
+      const AxisSub& sb = ax.subs[s];
+      if (sb.a * den <= S && (S < sb.b * den || (s == nsub - 1 && S <= sb.b * den))) owner = s;
+    }
+    if (owner == ax.own_first[g])
+      ax.own_pick[g] = 0;
+    else if (ax.own_count[g] == 2 && owner == ax.own_first[g] + 1)
+      ax.own_pick[g] = 1;
+    else
+      return MFA_ERR_LAYOUT;  // the Greville owner always owns the point; guard against a broken layout
+  }
   // first data point of every span (span of point k = floor(k nspans / (M-1)), capped)
   ax.span_start.assign(nspans + 1, (int)M);
   int j = 0;
@@ -567,11 +593,12 @@ void run_encode(mfa_model* md, const TQ* q) {
   if constexpr (std::is_same<T, ff>::value) {
     if (md->use_fused) {
       TRACED_N(h, TR_AVERAGE, 2,
-               launch_average_ff(L, md->offL, X, (ff*)md->P, nullptr, md->part, h->d_metrics, h->stream));
+               launch_average_ff(L, md->offL, X, (ff*)md->P, nullptr, md->part, h->d_metrics, h->stream,
+                                 md->update));
       return;
     }
   }
-  TRACED(h, TR_AVERAGE, launch_average<T>(L, md->offL, X, (T*)md->P, nullptr, h->d_metrics, h->stream));
+  TRACED(h, TR_AVERAGE, launch_average<T>(L, md->offL, X, (T*)md->P, nullptr, h->d_metrics, h->stream, md->update));
 }
 
 // One Schwarz iteration k >= 1 in control-point space.
@@ -593,7 +620,7 @@ void run_step(mfa_model* md) {
       if (fused) {
         TRACED_N(h, TR_AVERAGE, 2,
                  launch_average_ff(L, md->offL, (const ff*)md->X, (ff*)md->P, (const ff*)md->Pprev, md->part,
-                                   h->d_metrics, h->stream));
+                                   h->d_metrics, h->stream, md->update));
         return;
       }
     }
@@ -634,7 +661,8 @@ void run_step(mfa_model* md) {
   }
   cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
   TRACED(h, TR_AVERAGE,
-         launch_average<T>(L, md->offL, (const T*)md->X, (T*)md->P, (const T*)md->Pprev, h->d_metrics, h->stream));
+         launch_average<T>(L, md->offL, (const T*)md->X, (T*)md->P, (const T*)md->Pprev, h->d_metrics, h->stream,
+                           md->update));
 }
 
 // Global grid decode; the last axis either writes `out` (type T) or is fused
@@ -807,7 +835,7 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
   // ---- device tables in one arena
   Arena ar;
   size_t o_span[3], o_vd[3], o_vf[3], o_vff[3], o_ss[3], o_subs[3], o_of[3], o_oc[3], o_AL[3], o_fLd[3], o_fLf[3],
-      o_fLff[3], o_fUd[3], o_fUf[3], o_fUff[3], o_ot[3], o_nlt[3];
+      o_fLff[3], o_fUd[3], o_fUf[3], o_fUff[3], o_ot[3], o_nlt[3], o_pk[3];
   for (int a = 0; a < 3; ++a) {
     const AxisHost& ax = md->axh[a];
     const int w = ax.p + 1;
@@ -821,6 +849,7 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
     o_oc[a] = ar.take<int>(ax.n);
     o_ot[a] = ar.take<int4>(ax.n);
     o_nlt[a] = ar.take<int>(ax.S);
+    o_pk[a] = ar.take<int>(ax.n);
     o_AL[a] = ar.take<double>((size_t)ax.bandL_rows * w);
     o_fLd[a] = ar.take<double>((size_t)ax.bandL_rows * w);
     o_fLf[a] = ar.take<float>((size_t)ax.bandL_rows * w);
@@ -842,6 +871,7 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
     std::memcpy(img.data() + o_oc[a], ax.own_count.data(), sizeof(int) * ax.n);
     std::memcpy(img.data() + o_ot[a], ax.own_tab.data(), sizeof(int4) * ax.n);
     std::memcpy(img.data() + o_nlt[a], ax.nL_tab.data(), sizeof(int) * ax.S);
+    std::memcpy(img.data() + o_pk[a], ax.own_pick.data(), sizeof(int) * ax.n);
   }
   std::memcpy(img.data() + o_offL, offL.data(), sizeof(long long) * ns);
   std::memcpy(img.data() + o_offS1, offS1.data(), sizeof(long long) * ns);
@@ -895,6 +925,7 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
     d.own_count = at_off<int>(md->arena, o_oc[a]);
     d.own_tab = at_off<int4>(md->arena, o_ot[a]);
     d.nL_tab = at_off<int>(md->arena, o_nlt[a]);
+    d.own_pick = at_off<int>(md->arena, o_pk[a]);
     d.AL = at_off<double>(md->arena, o_AL[a]);
     d.facL_d = at_off<double>(md->arena, o_fLd[a]);
     d.facL_f = at_off<float>(md->arena, o_fLf[a]);
@@ -1059,6 +1090,28 @@ int encode_impl(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype
   return MFA_OK;
 }
 }  // namespace
+
+int mfa_set_update_rule(mfa_handle* h, mfa_model* md, int rule) {
+  if (!h || !md || md->h != h || md->batch) return MFA_ERR_ARG;
+  if (rule != MFA_UPDATE_AVERAGE && rule != MFA_UPDATE_OWNER) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  md->update = rule == MFA_UPDATE_OWNER ? UPDATE_OWNER : UPDATE_AVERAGE;
+  // redo the current update from the copies the model holds
+  cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
+  if (md->prec == MFA_PREC_FP64)
+    TRACED(h, TR_AVERAGE, launch_average<double>(md->L, md->offL, (const double*)md->X, (double*)md->P, nullptr,
+                                                 h->d_metrics, h->stream, md->update));
+  else if (md->use_fused)
+    TRACED_N(h, TR_AVERAGE, 2, launch_average_ff(md->L, md->offL, (const ff*)md->X, (ff*)md->P, nullptr, md->part,
+                                                 h->d_metrics, h->stream, md->update));
+  else
+    TRACED(h, TR_AVERAGE, launch_average<ff>(md->L, md->offL, (const ff*)md->X, (ff*)md->P, nullptr, h->d_metrics,
+                                             h->stream, md->update));
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  int st = read_status(h);
+  return st < 0 ? st : MFA_OK;
+}
 
 int mfa_schwarz_iterate(mfa_handle* h, mfa_model* md, int32_t max_iters, double tol_dP, mfa_report* rep) {
   if (!h || !md || md->h != h || max_iters < 0) return MFA_ERR_ARG;
@@ -1382,6 +1435,7 @@ int build_batch_group(mfa_batch* b, int d, int p, const std::vector<int>& mem, m
     ax.span_start = ss;
     ax.own_first.assign(ax.n, 0);
     ax.own_count.assign(ax.n, 1);
+    ax.own_pick.assign(ax.n, 0);
     ax.own_tab.assign(ax.n, int4{0, 0, -1, 0});
     ax.nL_tab.resize(ns);
     for (int t = 0; t < ns; ++t) {

@@ -40,6 +40,7 @@ struct AxisDev {
   const int* own_first;     // [n] first subdomain-axis index owning CP g
   const int* own_count;     // [n] number of owners (1 or 2)
   const int4* own_tab;      // [n] {first owner, g - l0 in it, second owner or -1, g - l0 in it}
+  const int* own_pick;      // [n] 0 or 1: which owner holds the Greville abscissa (owner-takes update)
   const int* nL_tab;        // [S] L size of every piece
   const double* AL;         // Gram band rows of every piece, upper storage: A(i, i+e) at [i*(p+1)+e]
   const double* facL_d;     // Cholesky band of A_L: [i*(p+1)] = 1/L(i,i), [i*(p+1)+e] = L(i,i-e)
@@ -81,7 +82,7 @@ struct AxisHost {
   int M = 1, nspans = 1, p = 0, n = 1, S = 1;
   int pieces = 0;
   std::vector<AxisSub> subs;
-  std::vector<int> own_first, own_count, span_start, nL_tab;
+  std::vector<int> own_first, own_count, span_start, nL_tab, own_pick;
   std::vector<int4> own_tab;
   int bandL_rows = 0, bandU_rows = 0;
 };
@@ -124,9 +125,11 @@ void launch_frame_gather(const LayoutDev& L, const long long* offL, int maxL, co
 template <typename T>
 void launch_rhs_finalize(const LayoutDev& L, const long long* offL, const long long* offY, int maxU,
                          const T* BL, const T* Y, T* X, cudaStream_t st);
+// update rule of the global control points from the owned copies
+enum { UPDATE_AVERAGE = 0, UPDATE_OWNER = 1 };
 template <typename T>
 void launch_average(const LayoutDev& L, const long long* offL, const T* X, T* P, const T* Pprev,
-                    unsigned long long* metrics, cudaStream_t st);
+                    unsigned long long* metrics, cudaStream_t st, int rule = UPDATE_AVERAGE);
 template <typename T>
 void launch_decode_points(const LayoutDev& L, const double* lo, const double* hi, const double* pts, long long npts,
                           const int* deriv, const T* P, void* out, int out_dtype, cudaStream_t st);
@@ -147,7 +150,7 @@ int launch_iter0_3d_ff(const LayoutDev& L, const long long* offL, const int* max
                        cudaStream_t st);
 long long average_ff_blocks(const LayoutDev& L);
 void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev, float* part,
-                       unsigned long long* metrics, cudaStream_t st);
+                       unsigned long long* metrics, cudaStream_t st, int rule = UPDATE_AVERAGE);
 
 // Batch internals used by the serving runtime (any handle may read a batch).
 int batch_decode_points_impl(mfa_handle* h, const mfa_batch* b, int32_t nq, const int32_t* qinst,

@@ -30,6 +30,7 @@ MFA_ERR_UNSUPPORTED = -8
 MFA_ERR_TIMEOUT = -9
 MFA_F32, MFA_F64 = 0, 1
 MFA_PREC_FP64, MFA_PREC_MIXED = 0, 1
+MFA_UPDATE_AVERAGE, MFA_UPDATE_OWNER = 0, 1
 
 MFA_TRACE_CLASSES = 16
 
@@ -131,6 +132,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_batch_residual.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, P, P]
     lib.mfa_batch_decode.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int]
     lib.mfa_batch_free.argtypes = [P]
+    lib.mfa_set_update_rule.argtypes = [P, P, ctypes.c_int]
     lib.mfa_batch_decode_points.argtypes = [P, P, ctypes.c_int32, P, P, P, P, ctypes.c_int]
     lib.mfa_server_create.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(P)]
     lib.mfa_server_encode.argtypes = [P, ctypes.POINTER(mfa_instance), P, ctypes.c_int]
@@ -147,7 +149,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     for name in ["mfa_create", "mfa_destroy", "mfa_encode", "mfa_schwarz_iterate", "mfa_decode", "mfa_residual",
                  "mfa_get_ctrl", "mfa_free", "mfa_sync", "mfa_encode_plain", "mfa_encode_batch", "mfa_batch_refit",
                  "mfa_batch_ctrl_offsets", "mfa_batch_get_ctrl", "mfa_batch_residual", "mfa_batch_decode",
-                 "mfa_batch_free", "mfa_batch_decode_points", "mfa_server_create", "mfa_server_wait",
+                 "mfa_batch_free", "mfa_batch_decode_points", "mfa_set_update_rule", "mfa_server_create", "mfa_server_wait",
                  "mfa_server_release", "mfa_server_get_ctrl", "mfa_server_stats", "mfa_server_destroy"]:
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -287,6 +289,10 @@ def mfa_batch_residual(h: int, b: int, count: int, q_ptr: int, q_dtype: int, q_o
 def mfa_batch_decode(h: int, b: int, out_ptr: int, out_dtype: int, out_on_device: bool) -> None:
     _check(load().mfa_batch_decode(ctypes.c_void_p(h), ctypes.c_void_p(b), ctypes.c_void_p(out_ptr), out_dtype,
                                    int(out_on_device)), "mfa_batch_decode")
+
+
+def mfa_set_update_rule(h: int, m: int, rule: int) -> None:
+    _check(load().mfa_set_update_rule(ctypes.c_void_p(h), ctypes.c_void_p(m), int(rule)), "mfa_set_update_rule")
 
 
 def mfa_batch_decode_points(h: int, b: int, qinst, pt_off, pts, out) -> None:
@@ -522,6 +528,10 @@ class Model:
         self.degree = layout.degree
         self.npts = [int(layout.npts[a]) for a in range(self.dim)]
         self.ncp = [int(layout.nspans[a]) + layout.degree for a in range(self.dim)]
+
+    def set_update_rule(self, rule: int) -> None:
+        """MFA_UPDATE_AVERAGE or MFA_UPDATE_OWNER; recomputes the current global control points."""
+        mfa_set_update_rule(self.handle.h, self.m, rule)
 
     def iterate(self, max_iters: int, tol_dP: float = 0.0):
         return mfa_schwarz_iterate(self.handle.h, self.m, max_iters, tol_dP)

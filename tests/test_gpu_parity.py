@@ -15,14 +15,16 @@ from paper_2210_06528_gb300 import inputs, mfa
 pytestmark = pytest.mark.gpu
 
 
-def _iterate_parity(Q, p, nspans, nsub, delta, iters, cores=None, on_device=True):
+def _iterate_parity(Q, p, nspans, nsub, delta, iters, cores=None, on_device=True, update="average"):
     prob = oracle_problem(Q, p, nspans, nsub, delta, cores)
     g = GpuRun(Q, p, nspans, nsub, delta, cores=cores, on_device=on_device)
     try:
-        st = O.schwarz_initial(prob, Q)
+        if update == "owner":
+            g.model.set_update_rule(mfa.MFA_UPDATE_OWNER)
+        st = O.schwarz_initial(prob, Q, update)
         assert rel_diff(g.ctrl(), st.P) <= TOL_FP64, "iteration 0"
         for k in range(1, iters + 1):
-            st = O.schwarz_step(prob, Q, st)
+            st = O.schwarz_step(prob, Q, st, update)
             rc, rep = g.iterate(1)
             assert rep.iters == k
             assert rel_diff(g.ctrl(), st.P) <= TOL_FP64, f"iteration {k}"
@@ -305,3 +307,55 @@ def test_plain_per_subdomain_form_equals_batched_fp64():
 def layout_for_mixed(Q, nspans, nsub, delta):
     from mfa_cases import layout_for
     return layout_for(Q, 3, nspans, nsub, delta, mfa.MFA_PREC_MIXED)
+
+
+@pytest.mark.parametrize("dim,p,delta", [(1, 3, 1), (2, 2, 1), (2, 3, 3), (3, 3, 2)])
+def test_owner_update_iterates(dim, p, delta):
+    """Owner-takes update (Greville owner per axis): every iterate equals the
+    oracle's (FP64 path)."""
+    shapes = {1: (90,), 2: (40, 36), 3: (22, 20, 18)}
+    spans = {1: [24], 2: [10, 9], 3: [8, 7, 6]}
+    nsubs = {1: [3], 2: [2, 3], 3: [2, 2, 2]}
+    Q = inputs.random_field(shapes[dim], seed=dim + 10 * p)
+    _iterate_parity(Q, p, spans[dim], nsubs[dim], delta, iters=4, update="owner")
+
+
+def test_owner_update_mixed_3d_fused():
+    """Owner-takes update on the fused float-float 3-D path: converged control
+    points within 1e-9 of the oracle's owner-takes fixed point."""
+    Q = inputs.gauss_3d((48, 44, 40), seed=4, dtype=np.float32)
+    Qd = Q.astype(np.float64)
+    nspans, nsub, delta = [16, 14, 12], [2, 2, 2], 2
+    prob = oracle_problem(Qd, 3, nspans, nsub, delta)
+    # stop well above the float-float rounding floor of dP (about 1e-13)
+    ref = O.schwarz_solve(prob, Qd, max_iters=60, tol_dP=1e-10, update="owner")
+    g = GpuRun(Q, 3, nspans, nsub, delta, precision=mfa.MFA_PREC_MIXED)
+    try:
+        g.model.set_update_rule(mfa.MFA_UPDATE_OWNER)
+        rc, rep = g.iterate(60, 1e-10)
+        assert rep.iters == ref["iters"]
+        assert rel_diff(g.ctrl(), ref["P"]) <= TOL_FP64
+    finally:
+        g.close()
+
+
+
+def test_overlap_sweep_on_gpu():
+    """The delta = 0..2p sweep of Sec. 3.1.1 (asymmetric sinc, N = 5, p = 3)
+    through the library: each converged fit equals the oracle's, and from
+    delta = p on it is the single-subdomain fit."""
+    Q = inputs.asymmetric_sinc_1d(501)
+    ref = O.global_fit(O.make_problem(3, [501], [40], [1], 0), Q)
+    for delta in range(0, 7):
+        prob = oracle_problem(Q, 3, [40], [5], delta)
+        o = O.schwarz_solve(prob, Q, max_iters=400, tol_dP=1e-13)
+        g = GpuRun(Q, 3, [40], [5], delta)
+        try:
+            rc, rep = g.iterate(400, 1e-13)
+            assert rep.iters == o["iters"]
+            P = g.ctrl()
+            assert rel_diff(P, o["P"]) <= TOL_FP64
+            if delta >= 3:
+                assert rel_diff(P, ref) <= 1e-11
+        finally:
+            g.close()

@@ -192,11 +192,29 @@ def test_overlap_ge_p_converges_to_global_lstsq(npts, nspans, nsub, p):
     assert res["history"][-1]["spread"] <= 1e-10 * max(1, np.abs(ref).max())
 
 
-def _bruteforce_fixed_point(prob, Q):
+def _greville_owner_fraction(prob, a):
+    """Owner of every control point along axis a by its Greville abscissa,
+    computed with exact rationals from the knot vector (independent of the
+    oracle's integer sums)."""
+    from fractions import Fraction
+    p, ns = prob.p, prob.nspans[a]
+    t = [Fraction(min(max(i - p, 0), ns), ns) for i in range(ns + 2 * p + 1)]
+    pcs = prob.pieces(a)
+    own = []
+    for g in range(ns + p):
+        xi = sum(t[g + 1:g + p + 1]) / p
+        i = next(i for i, pc in enumerate(pcs)
+                 if Fraction(pc.a, ns) <= xi and (xi < Fraction(pc.b, ns) or (i == len(pcs) - 1 and xi <= 1)))
+        own.append(i)
+    return own
+
+
+def _bruteforce_fixed_point(prob, Q, update="average"):
     """Independent construction of the Schwarz fixed point: unknowns are all
     owned copies x_s; equations are the local normal equations of every
-    subdomain with its frame equal to the average of the copies, solved as one
-    dense linear system with explicit Kronecker matrices from scipy's basis."""
+    subdomain with its frame equal to the update of the copies (their average,
+    or the Greville owner's copy), solved as one dense linear system with
+    explicit Kronecker matrices from scipy's basis."""
     d = prob.d
     ncp = prob.ncp()
     gshape = tuple(reversed(ncp))
@@ -212,14 +230,25 @@ def _bruteforce_fixed_point(prob, Q):
         sizes.append(len(ug))
         ublocks.append(ug)
         n_unk += len(ug)
-    # averaging operator W: global P = W x
+    # update operator W: global P = W x
     W = np.zeros((G, n_unk))
-    cnt = np.zeros(G)
-    for o, ug in zip(offs, ublocks):
-        for j, g in enumerate(ug):
-            W[g, o + j] = 1.0
-            cnt[g] += 1
-    W /= cnt[:, None]
+    if update == "average":
+        cnt = np.zeros(G)
+        for o, ug in zip(offs, ublocks):
+            for j, g in enumerate(ug):
+                W[g, o + j] = 1.0
+                cnt[g] += 1
+        W /= cnt[:, None]
+    else:
+        own = [_greville_owner_fraction(prob, a) for a in range(d)]
+        pieces = [prob.pieces(a) for a in range(d)]
+        gmulti = np.array(np.unravel_index(np.arange(G), gshape)).T[:, ::-1]  # grid index per axis, axis 0 first
+        for o, ug, s in zip(offs, ublocks, subs):
+            idx = [pieces[a].index(s[a]) for a in range(d)]
+            for j, g in enumerate(ug):
+                if all(own[a][gmulti[g][a]] == idx[a] for a in range(d)):
+                    W[g, o + j] = 1.0
+        assert np.allclose(W.sum(axis=1), 1.0)
     A = np.zeros((n_unk, n_unk))
     b = np.zeros(n_unk)
     for o, ug, s in zip(offs, ublocks, subs):
@@ -355,3 +384,75 @@ def test_scattered_decode_matches_grid_decode():
     pts = np.array([[u0[i], u1[j]] for j in range(11) for i in range(13)])
     S = O.scattered_decode(prob, P, pts)
     assert np.abs(S - D.reshape(-1)).max() <= 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Owner-takes update (restricted additive Schwarz, Sec. 2.3): every control
+# point takes the copy of the subdomain owning its Greville abscissa
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("npts,nspans,nsub,p,delta", [((60,), (16,), (3,), 3, 1), ((40,), (12,), (3,), 2, 1),
+                                                       ((16, 15), (8, 6), (2, 2), 2, 1),
+                                                       ((17, 14), (8, 6), (3, 2), 3, 2)])
+def test_owner_update_fixed_point_bruteforce(npts, nspans, nsub, p, delta):
+    Q = inputs.random_field(npts, seed=11)
+    prob = O.make_problem(p, npts, nspans, nsub, delta)
+    res = O.schwarz_solve(prob, Q, max_iters=400, tol_dP=1e-14, update="owner")
+    ref = _bruteforce_fixed_point(prob, Q, update="owner")
+    assert res["converged"]
+    assert np.abs(res["P"] - ref).max() <= 1e-10 * max(1, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("npts,nspans,nsub,p,delta", [((70,), (20,), (4,), 3, 3), ((33, 30), (10, 9), (2, 3), 2, 2)])
+def test_owner_update_converges_to_global_fit_when_overlap_ge_p(npts, nspans, nsub, p, delta):
+    """delta >= p: both update rules share the global LSQ fixed point."""
+    Q = inputs.random_field(npts, seed=3)
+    prob = O.make_problem(p, npts, nspans, nsub, delta)
+    res = O.schwarz_solve(prob, Q, max_iters=400, tol_dP=1e-14, update="owner")
+    ref = O.global_fit(prob, Q)
+    assert np.abs(res["P"] - ref).max() <= 1e-10 * max(1, np.abs(ref).max())
+
+
+def test_greville_owner_is_an_owning_subdomain():
+    """The Greville abscissa of a control point lies in the core of one of the
+    subdomains that own it (its support meets that core), for uneven cores and
+    degrees 1..5; and the owner agrees with the exact-rational computation."""
+    for p in range(1, 6):
+        for cores in ([6, 7, 5], [5, 9], [4, 4, 4, 4]):
+            ns = sum(cores)
+            if min(cores) < p:
+                continue
+            prob = O.make_problem(p, [4 * ns + 3], [ns], [len(cores)], 1, cores=[cores])
+            own = O.greville_owner(prob, 0)
+            assert list(own) == _greville_owner_fraction(prob, 0)
+            pcs = prob.pieces(0)
+            for g, i in enumerate(own):
+                assert g in pcs[i].U
+
+
+def test_owner_update_single_subdomain_is_the_global_fit():
+    Q = inputs.random_field((30, 24), seed=2)
+    prob = O.make_problem(3, [30, 24], [9, 7], [1, 1], 0)
+    res = O.schwarz_solve(prob, Q, max_iters=3, tol_dP=0.0, update="owner")
+    assert np.abs(res["P"] - O.global_fit(prob, Q)).max() <= 1e-12
+
+
+
+def test_overlap_sweep_approaches_single_subdomain_fit():
+    """Sec. 3.1.1, asymmetric sinc with N = 5 and p = 3: the converged fit
+    deviates from the single-subdomain (N = 1) fit less and less as the
+    overlap grows from 0 to p - 1 (at least 3x per extra span here), and from
+    delta = p up to 2p it is the N = 1 fit itself (reading: with delta >= p
+    every owned control point's support lies inside its window)."""
+    Q = inputs.asymmetric_sinc_1d(501)
+    ref = O.global_fit(O.make_problem(3, [501], [40], [1], 0), Q)
+    devs = []
+    for delta in range(0, 7):
+        prob = O.make_problem(3, [501], [40], [5], delta)
+        res = O.schwarz_solve(prob, Q, max_iters=400, tol_dP=1e-14)
+        assert res["converged"]
+        devs.append(np.abs(res["P"] - ref).max() / np.abs(ref).max())
+    for d in range(0, 2):
+        assert devs[d + 1] * 3 <= devs[d]
+    assert devs[2] > 1e-9
+    assert max(devs[3:]) <= 1e-12
