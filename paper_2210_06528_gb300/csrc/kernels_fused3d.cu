@@ -942,8 +942,6 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
   off += (size_t)nL1 * nL0 * sizeof(ff);
   ff* Y1 = reinterpret_cast<ff*>(smem + off);    // [nL1][nU0]
   off += (size_t)nL1 * nU0 * sizeof(ff);
-  ff* Y2 = reinterpret_cast<ff*>(smem + off);    // [nU1][nU0]
-  off += (size_t)nU1 * nU0 * sizeof(ff);
   float* R = reinterpret_cast<float*>(smem + off);  // [nU2][nU1][nU0]
 
   load_band_rows<P>(L.ax[0], bx, axh, axl);
@@ -1028,24 +1026,24 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
       }
     }
     __syncthreads();
-    // y band product, owned y rows
-    if (xin) {
+    // y band product, owned y rows; each result feeds only this thread's own
+    // z ring, so it stays in registers
+    ff y2r[NPAIR];
 #pragma unroll
-      for (int i = 0; i < NPAIR; ++i) {
-        const int uy = grp + NG * i;
-        if (uy < nU1) {
-          const int c0 = oU1 + uy - P;
-          ff acc(0.f, 0.f);
+    for (int i = 0; i < NPAIR; ++i) {
+      const int uy = grp + NG * i;
+      y2r[i] = ff(0.f, 0.f);
+      if (xin && uy < nU1) {
+        const int c0 = oU1 + uy - P;
+        ff acc(0.f, 0.f);
 #pragma unroll
-          for (int e = 0; e < B; ++e) {
-            const int c = c0 + e;
-            if (c >= 0 && c < nL1) AccFF::add_v(acc, ayh[uy * B + e], ayl[uy * B + e], Y1[c * nU0 + ux]);
-          }
-          Y2[uy * nU0 + ux] = AccFF::finish(acc);
+        for (int e = 0; e < B; ++e) {
+          const int c = c0 + e;
+          if (c >= 0 && c < nL1) AccFF::add_v(acc, ayh[uy * B + e], ayl[uy * B + e], Y1[c * nU0 + ux]);
         }
+        y2r[i] = AccFF::finish(acc);
       }
     }
-    __syncthreads();
     // z band product into the ring: slot j holds owned z-point uz = lz - oU2 - P + j
     const int uzb = lz - oU2 - P;
     ff bcur[NPAIR];
@@ -1058,7 +1056,7 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
     for (int i = 0; i < NPAIR; ++i) {
       const int uy = grp + NG * i;
       if (xin && uy < nU1) {
-        const ff y2 = Y2[uy * nU0 + ux];
+        const ff y2 = y2r[i];
 #pragma unroll
         for (int j = 0; j < B; ++j) {
           const int uz = uzb + j;
@@ -1070,7 +1068,10 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
       for (int j = 0; j < B - 1; ++j) ring[i][j] = ring[i][j + 1];
       ring[i][B - 1] = ff(0.f, 0.f);
     }
-    __syncthreads();
+    // no barrier: the next plane's stores to Pp follow the x-band barrier of
+    // this plane (every thread has finished reading Pp), and Y1 is rewritten
+    // only after the next plane's first barrier (every thread has finished
+    // its y band here)
   }
   // owned z-points whose band ended with the last plane
   {
@@ -1132,7 +1133,7 @@ size_t step3d_smem(int nL0, int nL1, int nU0, int nU1, int nU2) {
   constexpr int W = P + 1, B = 2 * P + 1;
   size_t off = (size_t)(2 * B * (nU0 + nU1 + nU2) + W * (nU0 + nU1 + nU2)) * 4;
   off = (off + 15) & ~size_t(15);
-  off += (size_t)nL1 * nL0 * sizeof(ff) + (size_t)nL1 * nU0 * sizeof(ff) + (size_t)nU1 * nU0 * sizeof(ff);
+  off += (size_t)nL1 * nL0 * sizeof(ff) + (size_t)nL1 * nU0 * sizeof(ff);
   off += (size_t)nU0 * nU1 * nU2 * sizeof(float);
   return off;
 }
