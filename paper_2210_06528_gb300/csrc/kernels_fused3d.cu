@@ -938,10 +938,14 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
   float* fz = fy + nU1 * W;
   size_t off = (size_t)(2 * B * (nU0 + nU1 + nU2) + W * (nU0 + nU1 + nU2)) * 4;
   off = (off + 15) & ~size_t(15);
-  ff* Pp = reinterpret_cast<ff*>(smem + off);    // [nL1][nL0]
-  off += (size_t)nL1 * nL0 * sizeof(ff);
-  ff* Y1 = reinterpret_cast<ff*>(smem + off);    // [nL1][nU0]
-  off += (size_t)nL1 * nU0 * sizeof(ff);
+  // the plane and the x-band result carry P zero columns / rows on each side,
+  // so the band products read without bounds checks (band entries outside L
+  // are zero as well)
+  const int ldp = nL0 + 2 * P;
+  ff* Pp = reinterpret_cast<ff*>(smem + off);    // [nL1][P + nL0 + P]
+  off += (size_t)nL1 * ldp * sizeof(ff);
+  ff* Y1 = reinterpret_cast<ff*>(smem + off);    // [P + nL1 + P][nU0]
+  off += (size_t)(nL1 + 2 * P) * nU0 * sizeof(ff);
   float* R = reinterpret_cast<float*>(smem + off);  // [nU2][nU1][nU0]
 
   load_band_rows<P>(L.ax[0], bx, axh, axl);
@@ -952,6 +956,21 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
   for (int i = threadIdx.x; i < nU2 * W; i += NT) fz[i] = L.ax[2].facU_f[(long long)bz.bandU * W + i];
 
   const int nplane = nL1 * nL0;
+  for (int i = threadIdx.x; i < nL1 * 2 * P; i += NT) {
+    const int ly = i / (2 * P), e = i - ly * 2 * P;
+    Pp[ly * ldp + (e < P ? e : nL0 + e)] = ff(0.f, 0.f);
+  }
+  for (int i = threadIdx.x; i < 2 * P * nU0; i += NT) {
+    const int r = i / nU0, x = i - r * nU0;
+    Y1[(r < P ? r : nL1 + r) * nU0 + x] = ff(0.f, 0.f);
+  }
+  int pdst[NPRE];  // where this thread's prefetched values land in the padded plane
+#pragma unroll
+  for (int k = 0; k < NPRE; ++k) {
+    const int i = threadIdx.x + k * NT;
+    const int ly = i / nL0, lx = i - ly * nL0;
+    pdst[k] = i < nplane ? ly * ldp + P + lx : -1;
+  }
   ff ring[NPAIR][B];  // pair i of this thread: owned (ux, uy = grp + NG*i)
 #pragma unroll
   for (int i = 0; i < NPAIR; ++i)
@@ -993,10 +1012,8 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
   fetch(lz_lo);
   for (int lz = lz_lo; lz <= lz_hi; ++lz) {
 #pragma unroll
-    for (int k = 0; k < NPRE; ++k) {
-      const int i = threadIdx.x + k * NT;
-      if (i < nplane) Pp[i] = pre[k];
-    }
+    for (int k = 0; k < NPRE; ++k)
+      if (pdst[k] >= 0) Pp[pdst[k]] = pre[k];
     __syncthreads();
     if (lz < lz_hi) fetch(lz + 1);
     // x band product, owned x rows; XR independent rows per thread in flight
@@ -1006,22 +1023,20 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
         ff acc[XR];
 #pragma unroll
         for (int k = 0; k < XR; ++k) acc[k] = ff(0.f, 0.f);
+        const ff* prow = Pp + P + c0;
 #pragma unroll
         for (int e = 0; e < B; ++e) {
-          const int c = c0 + e;
-          if (c >= 0 && c < nL0) {
-            const float h = axh[ux * B + e], l = axl[ux * B + e];
+          const float h = axh[ux * B + e], l = axl[ux * B + e];
 #pragma unroll
-            for (int k = 0; k < XR; ++k) {
-              const int ly = ly0 + k * NG;
-              if (ly < nL1) AccFF::add_v(acc[k], h, l, Pp[ly * nL0 + c]);
-            }
+          for (int k = 0; k < XR; ++k) {
+            const int ly = ly0 + k * NG;
+            if (ly < nL1) AccFF::add_v(acc[k], h, l, prow[ly * ldp + e]);
           }
         }
 #pragma unroll
         for (int k = 0; k < XR; ++k) {
           const int ly = ly0 + k * NG;
-          if (ly < nL1) Y1[ly * nU0 + ux] = AccFF::finish(acc[k]);
+          if (ly < nL1) Y1[(P + ly) * nU0 + ux] = AccFF::finish(acc[k]);
         }
       }
     }
@@ -1036,11 +1051,9 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
       if (xin && uy < nU1) {
         const int c0 = oU1 + uy - P;
         ff acc(0.f, 0.f);
+        const ff* ycol = Y1 + (P + c0) * nU0 + ux;
 #pragma unroll
-        for (int e = 0; e < B; ++e) {
-          const int c = c0 + e;
-          if (c >= 0 && c < nL1) AccFF::add_v(acc, ayh[uy * B + e], ayl[uy * B + e], Y1[c * nU0 + ux]);
-        }
+        for (int e = 0; e < B; ++e) AccFF::add_v(acc, ayh[uy * B + e], ayl[uy * B + e], ycol[e * nU0]);
         y2r[i] = AccFF::finish(acc);
       }
     }
@@ -1133,7 +1146,7 @@ size_t step3d_smem(int nL0, int nL1, int nU0, int nU1, int nU2) {
   constexpr int W = P + 1, B = 2 * P + 1;
   size_t off = (size_t)(2 * B * (nU0 + nU1 + nU2) + W * (nU0 + nU1 + nU2)) * 4;
   off = (off + 15) & ~size_t(15);
-  off += (size_t)nL1 * nL0 * sizeof(ff) + (size_t)nL1 * nU0 * sizeof(ff);
+  off += (size_t)nL1 * (nL0 + 2 * P) * sizeof(ff) + (size_t)(nL1 + 2 * P) * nU0 * sizeof(ff);
   off += (size_t)nU0 * nU1 * nU2 * sizeof(float);
   return off;
 }
