@@ -628,6 +628,21 @@ __global__ void __launch_bounds__(kDecThreads) k_decode3d(LayoutDev L, const V* 
   const ff* vx = ax.vals_ff;
   const ff* vy = ay.vals_ff;
   const ff* vz = az.vals_ff;
+  if constexpr (RESID) {
+    // bring the tile's data rows into L2 now; they are read after the z and
+    // y expansions (one 128-byte line per thread: rows of up to 64 floats)
+    constexpr int kLines = kDecTX * (int)sizeof(TQ) / 128;
+    const int t = threadIdx.x;
+    if (t < kDecTY * kDecTZ * kLines) {
+      const int part = t % kLines, row = t / kLines;
+      const int y = row % kDecTY, z = row / kDecTY;
+      const int xs = part * (128 / (int)sizeof(TQ));
+      if (y < ny && z < nz && xs < nx) {
+        const TQ* a = Q + (long long)(x0 + xs) + L.M[0] * (y0 + y) + L.M[0] * L.M[1] * (z0 + z);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+      }
+    }
+  }
   for (int i = threadIdx.x; i < nx * W; i += kDecThreads) {
     const int k = i / W, r = i - k * W;
     const ff v = vx[(long long)(x0 + k) * W + r];
@@ -665,8 +680,17 @@ __global__ void __launch_bounds__(kDecThreads) k_decode3d(LayoutDev L, const V* 
       for (int z = 0; z < nz; ++z) {
         const V* src = Pb + (sz[z] * ncy + cy) * ncx + cx;
         V acc = Val<V>::zero();
+        if constexpr (W == 4) {
+          const float4 h = reinterpret_cast<const float4*>(nzh)[z], l = reinterpret_cast<const float4*>(nzl)[z];
+          const int st = ncy * ncx;
+          Val<V>::add(acc, h.x, l.x, src[0]);
+          Val<V>::add(acc, h.y, l.y, src[st]);
+          Val<V>::add(acc, h.z, l.z, src[2 * st]);
+          Val<V>::add(acc, h.w, l.w, src[3 * st]);
+        } else {
 #pragma unroll
-        for (int r = 0; r < W; ++r) Val<V>::add(acc, nzh[z * W + r], nzl[z * W + r], src[r * ncy * ncx]);
+          for (int r = 0; r < W; ++r) Val<V>::add(acc, nzh[z * W + r], nzl[z * W + r], src[r * ncy * ncx]);
+        }
         Tz[(z * ncy + cy) * ncx + cx] = Val<V>::finish(acc);
       }
     }
@@ -675,12 +699,24 @@ __global__ void __launch_bounds__(kDecThreads) k_decode3d(LayoutDev L, const V* 
   // y expansion: Ty[z][y][cx]; lanes along cx, groups over y, loop over z
   for (int y = grp; y < ny; y += kDecThreads / 32) {
     for (int cx = lane; cx < ncx; cx += 32) {
+      float4 yh4 = make_float4(0, 0, 0, 0), yl4 = make_float4(0, 0, 0, 0);
+      if constexpr (W == 4) {
+        yh4 = reinterpret_cast<const float4*>(nyh)[y];
+        yl4 = reinterpret_cast<const float4*>(nyl)[y];
+      }
 #pragma unroll 2
       for (int z = 0; z < nz; ++z) {
         const V* src = Tz + (z * ncy + sy[y]) * ncx + cx;
         V acc = Val<V>::zero();
+        if constexpr (W == 4) {
+          Val<V>::add(acc, yh4.x, yl4.x, src[0]);
+          Val<V>::add(acc, yh4.y, yl4.y, src[ncx]);
+          Val<V>::add(acc, yh4.z, yl4.z, src[2 * ncx]);
+          Val<V>::add(acc, yh4.w, yl4.w, src[3 * ncx]);
+        } else {
 #pragma unroll
-        for (int r = 0; r < W; ++r) Val<V>::add(acc, nyh[y * W + r], nyl[y * W + r], src[r * ncx]);
+          for (int r = 0; r < W; ++r) Val<V>::add(acc, nyh[y * W + r], nyl[y * W + r], src[r * ncx]);
+        }
         Ty[(z * ny + y) * ncx + cx] = Val<V>::finish(acc);
       }
     }
