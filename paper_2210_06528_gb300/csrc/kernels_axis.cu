@@ -2,6 +2,8 @@
 // Every launch covers all subdomains: blockIdx.y selects the subdomain, the x
 // dimension covers its output elements.  The per-subdomain operand views are
 // built once on the host (AxisOp tables) and kept on the device.
+#include <algorithm>
+
 #include "mfa_internal.cuh"
 
 namespace mfa {
@@ -189,11 +191,14 @@ __global__ void k_expand_residual(LayoutDev L, int axis, const AxisOp* opp, cons
   }
 }
 
-// Fixed-order final reduction of the per-block partials (deterministic).
-__global__ void k_reduce_partials(const double* partials, int nblocks, double* result) {
+// Fixed-order reduction of per-block partials (deterministic): CTA b reduces
+// rows [b * chunk, (b + 1) * chunk) of `partials` into row b of `result`.
+__global__ void k_reduce_partials(const double* partials, int nblocks, double* result, int chunk) {
   __shared__ double sh[4][256];
   double a = 0.0, b = 0.0, c = INFINITY, d = -INFINITY;
-  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+  const int r0 = blockIdx.x * chunk, r1 = min(nblocks, r0 + chunk);
+  result += 4 * blockIdx.x;
+  for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
     a += partials[4 * i];
     b = fmax(b, partials[4 * i + 1]);
     c = fmin(c, partials[4 * i + 2]);
@@ -311,8 +316,18 @@ void launch_expand_residual(const LayoutDev& L, int axis, const AxisOp* op, long
   k_expand_residual<T, TQ><<<nblocks, 256, 0, st>>>(L, axis, op, in, q, partials);
 }
 
-void launch_reduce_partials(const double* partials, int nblocks, double* result, cudaStream_t st) {
-  k_reduce_partials<<<1, 256, 0, st>>>(partials, nblocks, result);
+void launch_reduce_partials(const double* partials, int nblocks, double* result, cudaStream_t st, double* scratch,
+                            int scratch_rows) {
+  // two fixed-order passes when there are many partials: chunks on many SMs,
+  // then one CTA over the chunk results
+  const int R = std::min(128, scratch_rows);
+  if (scratch && nblocks > 8 * 256 && R > 1) {
+    const int chunk = (nblocks + R - 1) / R;
+    k_reduce_partials<<<R, 256, 0, st>>>(partials, nblocks, scratch, chunk);
+    k_reduce_partials<<<1, 256, 0, st>>>(scratch, R, result, R);
+  } else {
+    k_reduce_partials<<<1, 256, 0, st>>>(partials, nblocks, result, nblocks);
+  }
 }
 
 template <typename T>

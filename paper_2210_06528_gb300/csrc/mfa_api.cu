@@ -685,7 +685,8 @@ int run_decode_grid(mfa_model* md, TOut* out, const TQ* q) {
         TRACED(h, TR_RESIDUAL,
                fused = (launch_decode3d<ff, TQ, float, true>(L, (const ff*)md->P, q, nullptr, part, h->stream)));
         if (fused) {
-          TRACED(h, TR_REDUCE, launch_reduce_partials(part, (int)tiles, h->d_result, h->stream));
+          TRACED_N(h, TR_REDUCE, 2,
+                   launch_reduce_partials(part, (int)tiles, h->d_result, h->stream, h->d_partials, kResidualBlocks));
           return MFA_OK;
         }
       } else if constexpr (!std::is_same<TOut, ff>::value) {

@@ -133,7 +133,8 @@ void launch_average(const LayoutDev& L, const long long* offL, const T* X, T* P,
 template <typename T>
 void launch_decode_points(const LayoutDev& L, const double* lo, const double* hi, const double* pts, long long npts,
                           const int* deriv, const T* P, void* out, int out_dtype, cudaStream_t st);
-void launch_reduce_partials(const double* partials, int nblocks, double* result, cudaStream_t st);
+void launch_reduce_partials(const double* partials, int nblocks, double* result, cudaStream_t st,
+                            double* scratch = nullptr, int scratch_rows = 0);
 template <typename TIn, typename TOut>
 void launch_cast(const TIn* in, TOut* out, long long n, cudaStream_t st);
 
