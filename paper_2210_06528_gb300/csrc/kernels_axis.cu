@@ -46,7 +46,29 @@ __device__ __forceinline__ void tile_of(const TileMap& tm, int& opi, long long& 
   }
 }
 
+// The operand of this block, copied once into shared memory: every thread of
+// a block works on the same operand, so the descriptor is read once per
+// block instead of once per thread.  Called by all threads (it has a barrier).
+__device__ __forceinline__ const AxisOp& block_op(const AxisOp* ops, int opi) {
+  __shared__ AxisOp sop;
+  static_assert(sizeof(AxisOp) % sizeof(int) == 0, "AxisOp is copied as ints");
+  constexpr int nw = (int)(sizeof(AxisOp) / sizeof(int));
+  for (int i = threadIdx.x; i < nw; i += blockDim.x)
+    reinterpret_cast<int*>(&sop)[i] = reinterpret_cast<const int*>(ops + opi)[i];
+  __syncthreads();
+  return sop;
+}
+
 __device__ __forceinline__ void unflatten(long long idx, const int* n, int* o) {
+  if (idx < (1LL << 31)) {  // 32-bit unsigned division is several times cheaper
+    const unsigned i = (unsigned)idx, n0 = (unsigned)n[0], n1 = (unsigned)n[1];
+    const unsigned r = i / n0;
+    o[0] = (int)(i - r * n0);
+    const unsigned r2 = r / n1;
+    o[1] = (int)(r - r2 * n1);
+    o[2] = (int)r2;
+    return;
+  }
   o[0] = (int)(idx % n[0]);
   long long r = idx / n[0];
   o[1] = (int)(r % n[1]);
@@ -62,13 +84,14 @@ __device__ __forceinline__ bool finite_val(ff x) { return isfinite(x.hi); }
 // i.e. whose span is in [c0+l-p, c0+l] (the N^T Q assembly of the normal
 // equations, Eq. minimization-problem).  When reading raw data the kernel also
 // flags non-finite input.
-template <typename T, typename TIn>
-__global__ void k_contract(LayoutDev L, int axis, const AxisOp* ops, const TIn* __restrict__ in,
+template <typename T, typename TIn, int AXIS>
+__global__ void k_contract(LayoutDev L, const AxisOp* ops, const TIn* __restrict__ in,
                            T* __restrict__ out, int* status, TileMap tm) {
+  constexpr int axis = AXIS;
   int opi;
   long long idx;
   tile_of(tm, opi, idx);
-  const AxisOp op = ops[opi];
+  const AxisOp& op = block_op(ops, opi);
   const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
   if (idx >= nout) return;
   int o[3];
@@ -101,8 +124,8 @@ __global__ void k_contract(LayoutDev L, int axis, const AxisOp* ops, const TIn* 
 // Decode along one axis: out[k] = sum_r N_{span(k)+r}(u_k) in[span(k)+r-c0],
 // terms whose control point lies outside the input range are zero (R P,
 // Algorithm 1 error step).
-template <typename T>
-__device__ __forceinline__ T expand_one(const AxisDev& ax, const AxisOp& op, int axis, const int* o,
+template <typename T, int axis>
+__device__ __forceinline__ T expand_one(const AxisDev& ax, const AxisOp& op, const int* o,
                                         const T* __restrict__ in) {
   const int p = ax.p, w = p + 1;
   const int k = op.k0 + o[axis];
@@ -121,38 +144,132 @@ __device__ __forceinline__ T expand_one(const AxisDev& ax, const AxisOp& op, int
   return acc;
 }
 
-template <typename T, typename TOut>
-__global__ void k_expand(LayoutDev L, int axis, const AxisOp* ops, const T* __restrict__ in, TOut* __restrict__ out,
+template <typename T, typename TOut, int AXIS>
+__global__ void k_expand(LayoutDev L, const AxisOp* ops, const T* __restrict__ in, TOut* __restrict__ out,
                          TileMap tm) {
+  constexpr int axis = AXIS;
   int opi;
   long long idx0;
   tile_of(tm, opi, idx0);
-  const AxisOp op = ops[opi];
+  const AxisOp& op = block_op(ops, opi);
   const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
   // with a tile map every thread has one element; else a grid-stride loop
   const long long stride = tm.op ? nout : (long long)gridDim.x * blockDim.x;
   for (long long idx = idx0; idx < nout; idx += stride) {
     int o[3];
     unflatten(idx, op.out.n, o);
-    const T val = expand_one<T>(L.ax[axis], op, axis, o, in);
+    const T val = expand_one<T, AXIS>(L.ax[AXIS], op, o, in);
     const View& ov = op.out;
     out[ov.off + o[0] * ov.st[0] + o[1] * ov.st[1] + o[2] * ov.st[2]] = (TOut)val;
   }
 }
 
+// Batches of independent fits: the last decode axis of a group fused with
+// the residual against the data, over a tile map; every tile (one block)
+// writes its sum of E^2 and max |E| (FP64).  Q shares the output views.
+template <typename T, typename TQ, int AXIS>
+__global__ void k_expand_residual_tiles(LayoutDev L, const AxisOp* ops, const T* __restrict__ in,
+                                        const TQ* __restrict__ q, TileMap tm, double* __restrict__ tile_part) {
+  constexpr int axis = AXIS;
+  int opi;
+  long long idx;
+  tile_of(tm, opi, idx);
+  const AxisOp& op = block_op(ops, opi);
+  const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
+  double e2 = 0.0, emax = 0.0;
+  if (idx < nout) {
+    int o[3];
+    unflatten(idx, op.out.n, o);
+    const T val = expand_one<T, AXIS>(L.ax[AXIS], op, o, in);
+    const View& ov = op.out;
+    const double e = (double)q[ov.off + o[0] * ov.st[0] + o[1] * ov.st[1] + o[2] * ov.st[2]] - (double)val;
+    e2 = e * e;
+    emax = fabs(e);
+  }
+  for (int sft = 16; sft > 0; sft >>= 1) {
+    e2 += __shfl_down_sync(0xffffffffu, e2, sft);
+    emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, sft));
+  }
+  __shared__ double red[2][kExpandThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][w] = e2;
+    red[1][w] = emax;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[0][k];
+      b = fmax(b, red[1][k]);
+    }
+    tile_part[2 * blockIdx.x] = a;
+    tile_part[2 * blockIdx.x + 1] = b;
+  }
+}
+
+// Per-instance totals of the tile partials, tiles in order: instance i of
+// the group owns tiles [first[i], first[i+1]); out[2 * id[i]] = sum of E^2,
+// out[2 * id[i] + 1] = max |E|.  One warp per instance.
+__global__ void k_tiles_to_instances(const double* __restrict__ tile_part, const int* __restrict__ first,
+                                     const int* __restrict__ id, int count, double* __restrict__ out) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= count) return;
+  double a = 0.0, b = 0.0;
+  for (int t = first[i] + lane; t < first[i + 1]; t += 32) {
+    a += tile_part[2 * t];
+    b = fmax(b, tile_part[2 * t + 1]);
+  }
+  for (int sft = 16; sft > 0; sft >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, sft);
+    b = fmax(b, __shfl_down_sync(0xffffffffu, b, sft));
+  }
+  if (lane == 0) {
+    out[2 * id[i]] = a;
+    out[2 * id[i] + 1] = b;
+  }
+}
+
+// the axis is a template argument of the kernels, so every per-axis index of
+// an operand view is known at compile time and the view stays in registers
+#define MFA_AXIS_DISPATCH(axis, LAUNCH) \
+  do {                                  \
+    if ((axis) == 0) {                  \
+      constexpr int AX = 0;             \
+      LAUNCH;                           \
+    } else if ((axis) == 1) {           \
+      constexpr int AX = 1;             \
+      LAUNCH;                           \
+    } else {                            \
+      constexpr int AX = 2;             \
+      LAUNCH;                           \
+    }                                   \
+  } while (0)
+
+template <typename T, typename TQ>
+void launch_expand_residual_tiles(const LayoutDev& L, int axis, const AxisOp* ops, const T* in, const TQ* q,
+                                  const TileMap& tm, double* tile_part, const int* first, const int* id, int count,
+                                  double* out, cudaStream_t st) {
+  if (tm.ntiles > 0)
+    MFA_AXIS_DISPATCH(axis, (k_expand_residual_tiles<T, TQ, AX><<<tm.ntiles, kExpandThreads, 0, st>>>(L, ops, in, q, tm, tile_part)));
+  if (count > 0) k_tiles_to_instances<<<(count + 7) / 8, 256, 0, st>>>(tile_part, first, id, count, out);
+}
+
 // Final decode axis fused with the residual E = Q - R P: per-block partial
 // sums of E^2 (FP64), max |E|, min Q and max Q.  Q shares the output layout.
-template <typename T, typename TQ>
-__global__ void k_expand_residual(LayoutDev L, int axis, const AxisOp* opp, const T* __restrict__ in,
+template <typename T, typename TQ, int AXIS>
+__global__ void k_expand_residual(LayoutDev L, const AxisOp* opp, const T* __restrict__ in,
                                   const TQ* __restrict__ q, double* partials) {
-  const AxisOp op = *opp;
+  constexpr int axis = AXIS;
+  const AxisOp& op = block_op(opp, 0);
   const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
   const long long stride = (long long)gridDim.x * blockDim.x;
   double s2 = 0.0, emax = 0.0, qmin = INFINITY, qmax = -INFINITY;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nout; idx += stride) {
     int o[3];
     unflatten(idx, op.out.n, o);
-    const T val = expand_one<T>(L.ax[axis], op, axis, o, in);
+    const T val = expand_one<T, AXIS>(L.ax[AXIS], op, o, in);
     const double qv = (double)q[idx];
     const double e = qv - (double)val;
     s2 += e * e;
@@ -225,9 +342,10 @@ __global__ void k_reduce_partials(const double* partials, int nblocks, double* r
 // Banded matrix-vector product along one axis with the output restricted to
 // the owned rows: out[i] = sum_c A_L(oU+i, c) in[c], |oU+i-c| <= p.  This is
 // the coupling G = N_U^T N_L of the Schur-decoupled local problem.
-template <typename T>
-__global__ void k_band_apply(LayoutDev L, int axis, const AxisOp* ops, const T* __restrict__ in, T* __restrict__ out) {
-  const AxisOp op = ops[blockIdx.y];
+template <typename T, int AXIS>
+__global__ void k_band_apply(LayoutDev L, const AxisOp* ops, const T* __restrict__ in, T* __restrict__ out) {
+  constexpr int axis = AXIS;
+  const AxisOp& op = block_op(ops, blockIdx.y);
   const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
   const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= nout) return;
@@ -256,12 +374,13 @@ __global__ void k_band_apply(LayoutDev L, int axis, const AxisOp* ops, const T* 
 
 // In-place banded Cholesky solve along one axis, one thread per fibre
 // (Sec. 2.3.1): forward L y = c, then backward L^T x = y.
-template <typename T>
-__global__ void k_band_solve(LayoutDev L, int axis, bool useU, const AxisOp* ops, T* x, TileMap tm) {
+template <typename T, int AXIS>
+__global__ void k_band_solve(LayoutDev L, bool useU, const AxisOp* ops, T* x, TileMap tm) {
+  constexpr int axis = AXIS;
   int opi;
   long long f;
   tile_of(tm, opi, f);
-  const AxisOp op = ops[opi];
+  const AxisOp& op = block_op(ops, opi);
   const View& v = op.out;
   const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2;
   const long long nf = (long long)v.n[a1] * v.n[a2];
@@ -290,30 +409,30 @@ template <typename T, typename TIn>
 void launch_contract(const LayoutDev& L, int axis, const AxisOp* ops, int nops, int max_out, const TIn* in, T* out,
                      int* status, cudaStream_t st, const TileMap* tm) {
   if (tm && tm->op) {
-    if (tm->ntiles > 0) k_contract<T, TIn><<<tm->ntiles, kContractThreads, 0, st>>>(L, axis, ops, in, out, status, *tm);
+    if (tm->ntiles > 0) MFA_AXIS_DISPATCH(axis, (k_contract<T, TIn, AX><<<tm->ntiles, kContractThreads, 0, st>>>(L, ops, in, out, status, *tm)));
     return;
   }
   dim3 grid((max_out + kContractThreads - 1) / kContractThreads, nops);
-  k_contract<T, TIn><<<grid, kContractThreads, 0, st>>>(L, axis, ops, in, out, status, TileMap{});
+  MFA_AXIS_DISPATCH(axis, (k_contract<T, TIn, AX><<<grid, kContractThreads, 0, st>>>(L, ops, in, out, status, TileMap{})));
 }
 
 template <typename T, typename TOut>
 void launch_expand(const LayoutDev& L, int axis, const AxisOp* ops, int nops, long long max_out, const T* in,
                    TOut* out, cudaStream_t st, const TileMap* tm) {
   if (tm && tm->op) {
-    if (tm->ntiles > 0) k_expand<T, TOut><<<tm->ntiles, kExpandThreads, 0, st>>>(L, axis, ops, in, out, *tm);
+    if (tm->ntiles > 0) MFA_AXIS_DISPATCH(axis, (k_expand<T, TOut, AX><<<tm->ntiles, kExpandThreads, 0, st>>>(L, ops, in, out, *tm)));
     return;
   }
   long long blocks = (max_out + kExpandThreads - 1) / kExpandThreads;
   if (blocks > 65535) blocks = 65535;
   dim3 grid((unsigned)blocks, nops);
-  k_expand<T, TOut><<<grid, kExpandThreads, 0, st>>>(L, axis, ops, in, out, TileMap{});
+  MFA_AXIS_DISPATCH(axis, (k_expand<T, TOut, AX><<<grid, kExpandThreads, 0, st>>>(L, ops, in, out, TileMap{})));
 }
 
 template <typename T, typename TQ>
 void launch_expand_residual(const LayoutDev& L, int axis, const AxisOp* op, long long nout, const T* in, const TQ* q,
                             double* partials, int nblocks, cudaStream_t st) {
-  k_expand_residual<T, TQ><<<nblocks, 256, 0, st>>>(L, axis, op, in, q, partials);
+  MFA_AXIS_DISPATCH(axis, (k_expand_residual<T, TQ, AX><<<nblocks, 256, 0, st>>>(L, op, in, q, partials)));
 }
 
 void launch_reduce_partials(const double* partials, int nblocks, double* result, cudaStream_t st, double* scratch,
@@ -334,18 +453,18 @@ template <typename T>
 void launch_band_apply(const LayoutDev& L, int axis, const AxisOp* ops, int nops, int max_out, const T* in, T* out,
                        cudaStream_t st) {
   dim3 grid((max_out + 127) / 128, nops);
-  k_band_apply<T><<<grid, 128, 0, st>>>(L, axis, ops, in, out);
+  MFA_AXIS_DISPATCH(axis, (k_band_apply<T, AX><<<grid, 128, 0, st>>>(L, ops, in, out)));
 }
 
 template <typename T>
 void launch_band_solve(const LayoutDev& L, int axis, bool useU, const AxisOp* ops, int nops, int max_fibres, T* x,
                        cudaStream_t st, const TileMap* tm) {
   if (tm && tm->op) {
-    if (tm->ntiles > 0) k_band_solve<T><<<tm->ntiles, kSolveThreads, 0, st>>>(L, axis, useU, ops, x, *tm);
+    if (tm->ntiles > 0) MFA_AXIS_DISPATCH(axis, (k_band_solve<T, AX><<<tm->ntiles, kSolveThreads, 0, st>>>(L, useU, ops, x, *tm)));
     return;
   }
   dim3 grid((max_fibres + kSolveThreads - 1) / kSolveThreads, nops);
-  k_band_solve<T><<<grid, kSolveThreads, 0, st>>>(L, axis, useU, ops, x, TileMap{});
+  MFA_AXIS_DISPATCH(axis, (k_band_solve<T, AX><<<grid, kSolveThreads, 0, st>>>(L, useU, ops, x, TileMap{})));
 }
 
 #define MFA_INST_T(T)                                                                                        \
@@ -368,6 +487,18 @@ void launch_band_solve(const LayoutDev& L, int axis, bool useU, const AxisOp* op
 MFA_INST_T(double)
 MFA_INST_T(float)
 MFA_INST_T(ff)
+template void launch_expand_residual_tiles<double, float>(const LayoutDev&, int, const AxisOp*, const double*,
+                                                          const float*, const TileMap&, double*, const int*,
+                                                          const int*, int, double*, cudaStream_t);
+template void launch_expand_residual_tiles<double, double>(const LayoutDev&, int, const AxisOp*, const double*,
+                                                           const double*, const TileMap&, double*, const int*,
+                                                           const int*, int, double*, cudaStream_t);
+template void launch_expand_residual_tiles<ff, float>(const LayoutDev&, int, const AxisOp*, const ff*, const float*,
+                                                      const TileMap&, double*, const int*, const int*, int, double*,
+                                                      cudaStream_t);
+template void launch_expand_residual_tiles<ff, double>(const LayoutDev&, int, const AxisOp*, const ff*,
+                                                       const double*, const TileMap&, double*, const int*,
+                                                       const int*, int, double*, cudaStream_t);
 template void launch_expand<ff, ff>(const LayoutDev&, int, const AxisOp*, int, long long, const ff*, ff*,
                                     cudaStream_t, const TileMap*);
 template void launch_contract<ff, ff>(const LayoutDev&, int, const AxisOp*, int, int, const ff*, ff*, int*,

@@ -51,6 +51,8 @@ struct mfa_model {
   long long decS1 = 0, decS2 = 0;  // batch: decode stage scratch sizes (elements)
   TileMap tm_proj[3], tm_solve[3], tm_dec[3];  // batch: compact launches over the uneven instances
   void* tiles = nullptr;                       // device storage of the tile maps
+  const int* res_first = nullptr;              // batch: first last-axis decode tile of every instance [nsub + 1]
+  const int* res_id = nullptr;                 // batch: batch index of every instance of the group [nsub]
   const void* q_src = nullptr;     // plain form: the device data it re-reads every iteration
   int q_src_dtype = MFA_F32;
   int prec = MFA_PREC_FP64;
@@ -1573,13 +1575,31 @@ int build_batch_group(mfa_batch* b, int d, int p, const std::vector<int>& mem, m
       add(&md->tm_solve[a], OP_SOLVEL0 + a, kSolveThreads, true, a);
       add(&md->tm_dec[a], OP_DEC0 + a, kExpandThreads, false, a);
     }
+    // per instance: its first tile of the last decode axis (tiles of an
+    // operand are consecutive) and its index in the batch
+    std::vector<int> rfirst(ns + 1, 0), rid(ns);
+    {
+      const size_t f0 = spans.back().first;  // the last span added is the last decode axis
+      for (size_t k = f0; k < top.size(); ++k) rfirst[top[k] + 1]++;
+      for (int t = 0; t < ns; ++t) {
+        rfirst[t + 1] += rfirst[t];
+        rid[t] = mem[t];
+      }
+    }
     const size_t nt = top.size();
-    rc = pool_alloc(h, &md->tiles, nt * (sizeof(int) + sizeof(long long)) + 16);
+    rc = pool_alloc(h, &md->tiles, nt * (sizeof(int) + sizeof(long long)) + (2 * (size_t)ns + 1) * sizeof(int) + 16);
     cudaError_t e = rc == MFA_OK ? cudaSuccess : cudaErrorMemoryAllocation;
     long long* dbase = (long long*)md->tiles;
     int* dop = (int*)(dbase + nt);
+    int* dfirst = dop + nt;
+    int* did = dfirst + ns + 1;
     if (e == cudaSuccess) e = cudaMemcpyAsync(dbase, tbase.data(), nt * sizeof(long long), cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dop, top.data(), nt * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dfirst, rfirst.data(), (ns + 1) * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(did, rid.data(), ns * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    md->res_first = dfirst;
+    md->res_id = did;
     if (e != cudaSuccess) {
       md->BL = md->X = md->P = nullptr;
       pool_free(h, md->tiles);
@@ -1845,6 +1865,41 @@ int mfa_batch_get_ctrl(mfa_handle* h, const mfa_batch* b, double* host_out, int6
   return st < 0 ? st : MFA_OK;
 }
 
+namespace {
+// Decoded error of every instance of every group: stage expansions into the
+// workspace, then the last axis fused with E = Q - D over the tile map and a
+// fixed-order per-instance reduction into out[2 * i], out[2 * i + 1].
+template <typename T, typename TQ>
+int batch_residual_into(mfa_batch* b, const TQ* q, double* out) {
+  mfa_handle* h = b->h;
+  size_t need = 0;
+  for (mfa_model* md : b->groups)
+    need = std::max<size_t>(need, (size_t)(md->decS1 + md->decS2) * sizeof(T) +
+                                      2 * (size_t)md->tm_dec[md->dim - 1].ntiles * sizeof(double) + 64);
+  int rc = ensure_ws(h, need);
+  if (rc != MFA_OK) return rc;
+  for (mfa_model* md : b->groups) {
+    T* s1 = (T*)h->ws;
+    T* s2 = s1 + md->decS1;
+    double* tpart = (double*)(((uintptr_t)(s2 + md->decS2) + 15) & ~(uintptr_t)15);
+    const int ns = md->nsub, d = md->dim;
+    const T* in = (const T*)md->X;
+    for (int a = 0; a < d - 1; ++a) {
+      const AxisOp* op = md->ops + (size_t)(OP_DEC0 + a) * ns;
+      T* o = (a == 0) ? s1 : s2;
+      TRACED(h, TR_DECODE_STAGE,
+             (launch_expand<T, T>(md->L, a, op, ns, md->maxDec[a], in, o, h->stream, &md->tm_dec[a])));
+      in = o;
+    }
+    const AxisOp* op = md->ops + (size_t)(OP_DEC0 + d - 1) * ns;
+    TRACED_N(h, TR_RESIDUAL, 2,
+             (launch_expand_residual_tiles<T, TQ>(md->L, d - 1, op, in, q, md->tm_dec[d - 1], tpart, md->res_first,
+                                                  md->res_id, ns, out, h->stream)));
+  }
+  return MFA_OK;
+}
+}  // namespace
+
 int mfa_batch_residual(mfa_handle* h, const mfa_batch* bc, const void* q, int q_dtype, int q_on_device, double* rms,
                        double* maxabs) {
   mfa_batch* b = const_cast<mfa_batch*>(bc);
@@ -1859,38 +1914,34 @@ int mfa_batch_residual(mfa_handle* h, const mfa_batch* bc, const void* q, int q_
   DeviceGuard g(h->device);
   const size_t qb = (size_t)b->q_total * (q_dtype == MFA_F64 ? 8 : 4);
   void* qtmp = nullptr;
-  void* D = nullptr;
+  void* res = nullptr;
   cudaError_t e = cudaSuccess;
-  int rc = pool_alloc(h, &D, (size_t)b->q_total * sizeof(double));
+  int rc = pool_alloc(h, &res, 2 * (size_t)b->count * sizeof(double));
   if (rc == MFA_OK && !q_on_device) {
     rc = pool_alloc(h, &qtmp, qb);
     if (rc == MFA_OK) e = cudaMemcpyAsync(qtmp, q, qb, cudaMemcpyHostToDevice, h->stream);
     q = qtmp;
   }
-  if (rc == MFA_OK && e == cudaSuccess) rc = batch_decode_any<double>(b, (double*)D);
-  const long long* off = (const long long*)b->tab;
-  double* res = (double*)h->d_partials;  // 2 doubles per instance, reused in chunks
-  std::vector<double> hr(2 * (size_t)std::min(b->count, 2 * kResidualBlocks));
-  for (int i0 = 0; rc == MFA_OK && e == cudaSuccess && i0 < b->count; i0 += 2 * kResidualBlocks) {
-    const int n = std::min(b->count - i0, 2 * kResidualBlocks);
-    if (q_dtype == MFA_F64)
-      TRACED(h, TR_RESIDUAL, launch_batch_residual<double>((const double*)D, (const double*)q, off + i0,
-                                                           off + b->count + i0, n, res, h->stream));
+  if (rc == MFA_OK && e == cudaSuccess) {
+    if (b->prec == MFA_PREC_FP64)
+      rc = q_dtype == MFA_F64 ? batch_residual_into<double, double>(b, (const double*)q, (double*)res)
+                              : batch_residual_into<double, float>(b, (const float*)q, (double*)res);
     else
-      TRACED(h, TR_RESIDUAL, launch_batch_residual<float>((const double*)D, (const float*)q, off + i0,
-                                                          off + b->count + i0, n, res, h->stream));
-    e = cudaMemcpyAsync(hr.data(), res, 2 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    for (int k = 0; k < n && e == cudaSuccess; ++k) {
-      rms[i0 + k] = std::sqrt(hr[2 * k] / (double)b->q_len[i0 + k]);
-      maxabs[i0 + k] = hr[2 * k + 1];
-    }
+      rc = q_dtype == MFA_F64 ? batch_residual_into<ff, double>(b, (const double*)q, (double*)res)
+                              : batch_residual_into<ff, float>(b, (const float*)q, (double*)res);
   }
+  std::vector<double> hr(2 * (size_t)b->count);
+  if (rc == MFA_OK && e == cudaSuccess)
+    e = cudaMemcpyAsync(hr.data(), res, hr.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (qtmp) pool_free(h, qtmp);
-  if (D) pool_free(h, D);
+  if (res) pool_free(h, res);
   if (rc != MFA_OK) return rc;
   if (e != cudaSuccess) return cuda_status(e);
+  for (int i = 0; i < b->count; ++i) {
+    rms[i] = std::sqrt(hr[2 * i] / (double)b->q_len[i]);
+    maxabs[i] = hr[2 * i + 1];
+  }
   int st = read_status(h);
   return st < 0 ? st : MFA_OK;
 }

@@ -133,6 +133,10 @@ void launch_average(const LayoutDev& L, const long long* offL, const T* X, T* P,
 template <typename T>
 void launch_decode_points(const LayoutDev& L, const double* lo, const double* hi, const double* pts, long long npts,
                           const int* deriv, const T* P, void* out, int out_dtype, cudaStream_t st);
+template <typename T, typename TQ>
+void launch_expand_residual_tiles(const LayoutDev& L, int axis, const AxisOp* ops, const T* in, const TQ* q,
+                                  const TileMap& tm, double* tile_part, const int* first, const int* id, int count,
+                                  double* out, cudaStream_t st);
 void launch_reduce_partials(const double* partials, int nblocks, double* result, cudaStream_t st,
                             double* scratch = nullptr, int scratch_rows = 0);
 template <typename TIn, typename TOut>
@@ -169,9 +173,6 @@ template <typename T>
 void launch_decode_points_inst(const InstDesc* desc, const int* qinst, const long long* pt_off, int nq,
                                long long npts, const double* pts, const T* P, double* out, cudaStream_t st);
 
-template <typename TQ>
-void launch_batch_residual(const double* D, const TQ* Q, const long long* off, const long long* len, int count,
-                           double* out, cudaStream_t st);
 
 constexpr int kResidualBlocks = 1216;  // 8 x 152 SMs
 // block sizes of the generic kernels (tile sizes of their TileMaps)
