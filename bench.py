@@ -268,6 +268,7 @@ def bench_batch(h, torch, mfa, stream, steps, count=4096, seed=0):
     r1.record(stream)
     torch.cuda.synchronize()
     res_ms = r0.elapsed_time(r1)
+    rc, sizes, cand = b.tile_sizes()
     b.free()
     npts = int(data.size)
     d2 = sum(1 for sp in specs if sp["dim"] == 2)
@@ -277,7 +278,9 @@ def bench_batch(h, torch, mfa, stream, steps, count=4096, seed=0):
             "encode_s_incl_host_layout": enc_s, "refit_ms": refit_ms, "refit_pts_per_s": npts / (refit_ms * 1e-3),
             "residual_ms": res_ms, "fit_plus_residual_pts_per_s": npts / ((refit_ms + res_ms) * 1e-3),
             "rms_median": float(np.median(rms)), "rms_max": float(rms.max()),
-            "refit": "one CUDA graph per batch (projection + solves of every (dimension, degree) group)"}
+            "refit": "one CUDA graph per batch (projection + solves of every (dimension, degree) group)",
+            "tile_sizes": {"projection": sizes[0], "solve": sizes[1], "decode": sizes[2],
+                           "autotune_fit_ms": [[round(float(x), 3) for x in row] for row in cand]}}
 
 
 def bench_serve(torch, mfa, n_enc=160, mix=4, seed=1, workers=3, budget=48 << 30):

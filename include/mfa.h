@@ -289,6 +289,14 @@ int mfa_encode_batch(mfa_handle* h, int32_t count, const mfa_instance* inst, con
  * q must be device data, valid until the call returns; synchronous. */
 int mfa_batch_refit(mfa_handle* h, mfa_batch* b, const void* q, int q_dtype);
 
+/* Block sizes of the batch's launches (sizes[0] projection, [1] banded
+ * solves, [2] decode).  The first mfa_batch_refit picks the projection and
+ * solve sizes by timing the fit for 64/128/256 x 32/64/128 threads (a
+ * self-tuned choice per batch); candidate_ms (9 floats, may be NULL) gets
+ * each candidate's fit time, row-major by projection size.  Returns MFA_OK
+ * once tuned, MFA_NOT_CONVERGED before the first refit (defaults 128/64/256). */
+int mfa_batch_tile_sizes(const mfa_batch* b, int32_t* sizes, float* candidate_ms);
+
 /* Control points of every instance, concatenated in instance order (each
  * instance in its own grid layout, axis 0 fastest, prod(nspans_a + degree)
  * values).  mfa_batch_ctrl_offsets writes count + 1 offsets into it.

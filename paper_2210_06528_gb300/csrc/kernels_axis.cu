@@ -190,7 +190,7 @@ __global__ void k_expand_residual_tiles(LayoutDev L, const AxisOp* ops, const T*
     e2 += __shfl_down_sync(0xffffffffu, e2, sft);
     emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, sft));
   }
-  __shared__ double red[2][kExpandThreads / 32];
+  __shared__ double red[2][32];  // up to 1024 threads
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
     red[0][w] = e2;
@@ -252,7 +252,7 @@ void launch_expand_residual_tiles(const LayoutDev& L, int axis, const AxisOp* op
                                   const TileMap& tm, double* tile_part, const int* first, const int* id, int count,
                                   double* out, cudaStream_t st) {
   if (tm.ntiles > 0)
-    MFA_AXIS_DISPATCH(axis, (k_expand_residual_tiles<T, TQ, AX><<<tm.ntiles, kExpandThreads, 0, st>>>(L, ops, in, q, tm, tile_part)));
+    MFA_AXIS_DISPATCH(axis, (k_expand_residual_tiles<T, TQ, AX><<<tm.ntiles, tm.threads, 0, st>>>(L, ops, in, q, tm, tile_part)));
   if (count > 0) k_tiles_to_instances<<<(count + 7) / 8, 256, 0, st>>>(tile_part, first, id, count, out);
 }
 
@@ -409,7 +409,7 @@ template <typename T, typename TIn>
 void launch_contract(const LayoutDev& L, int axis, const AxisOp* ops, int nops, int max_out, const TIn* in, T* out,
                      int* status, cudaStream_t st, const TileMap* tm) {
   if (tm && tm->op) {
-    if (tm->ntiles > 0) MFA_AXIS_DISPATCH(axis, (k_contract<T, TIn, AX><<<tm->ntiles, kContractThreads, 0, st>>>(L, ops, in, out, status, *tm)));
+    if (tm->ntiles > 0) MFA_AXIS_DISPATCH(axis, (k_contract<T, TIn, AX><<<tm->ntiles, tm->threads, 0, st>>>(L, ops, in, out, status, *tm)));
     return;
   }
   dim3 grid((max_out + kContractThreads - 1) / kContractThreads, nops);
@@ -420,7 +420,7 @@ template <typename T, typename TOut>
 void launch_expand(const LayoutDev& L, int axis, const AxisOp* ops, int nops, long long max_out, const T* in,
                    TOut* out, cudaStream_t st, const TileMap* tm) {
   if (tm && tm->op) {
-    if (tm->ntiles > 0) MFA_AXIS_DISPATCH(axis, (k_expand<T, TOut, AX><<<tm->ntiles, kExpandThreads, 0, st>>>(L, ops, in, out, *tm)));
+    if (tm->ntiles > 0) MFA_AXIS_DISPATCH(axis, (k_expand<T, TOut, AX><<<tm->ntiles, tm->threads, 0, st>>>(L, ops, in, out, *tm)));
     return;
   }
   long long blocks = (max_out + kExpandThreads - 1) / kExpandThreads;
@@ -460,7 +460,7 @@ template <typename T>
 void launch_band_solve(const LayoutDev& L, int axis, bool useU, const AxisOp* ops, int nops, int max_fibres, T* x,
                        cudaStream_t st, const TileMap* tm) {
   if (tm && tm->op) {
-    if (tm->ntiles > 0) MFA_AXIS_DISPATCH(axis, (k_band_solve<T, AX><<<tm->ntiles, kSolveThreads, 0, st>>>(L, useU, ops, x, *tm)));
+    if (tm->ntiles > 0) MFA_AXIS_DISPATCH(axis, (k_band_solve<T, AX><<<tm->ntiles, tm->threads, 0, st>>>(L, useU, ops, x, *tm)));
     return;
   }
   dim3 grid((max_fibres + kSolveThreads - 1) / kSolveThreads, nops);

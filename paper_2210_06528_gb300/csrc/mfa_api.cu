@@ -53,6 +53,9 @@ struct mfa_model {
   void* tiles = nullptr;                       // device storage of the tile maps
   const int* res_first = nullptr;              // batch: first last-axis decode tile of every instance [nsub + 1]
   const int* res_id = nullptr;                 // batch: batch index of every instance of the group [nsub]
+  std::vector<AxisOp> hops;                    // batch: host copy of the operand tables (tile maps are rebuilt from it)
+  std::vector<int> hmem;                       // batch: batch index of every instance of the group
+  int tile_c = 0, tile_s = 0, tile_e = 0;      // batch: block sizes of the current tile maps
   const void* q_src = nullptr;     // plain form: the device data it re-reads every iteration
   int q_src_dtype = MFA_F32;
   int prec = MFA_PREC_FP64;
@@ -1374,12 +1377,85 @@ struct mfa_batch {
   void* staged = nullptr;                // device copy of host data
   int staged_dtype = MFA_F32;
   cudaGraphExec_t graph = nullptr;       // captured refit
+  bool tuned = false;                    // tile sizes picked by timing (first refit)
+  float tune_ms[9] = {};                 // fit time of every candidate (projection x solve block sizes)
   cudaStream_t cap = nullptr;            // private stream the refit is captured on
   const void* graph_q = nullptr;
   int graph_dtype = -1;
 };
 
 namespace {
+
+// Tile maps of a batch group for block sizes tc (projection), ts (solves) and
+// te (decode): every operand of a launch split into blocks of that size, plus
+// each instance's first tile of the last decode axis and its batch index.
+// Replaces the group's previous maps.
+int build_batch_tiles(mfa_handle* h, mfa_model* md, int tc, int ts, int te) {
+  const std::vector<AxisOp>& ops = md->hops;
+  const int ns = md->nsub, d = md->dim;
+  std::vector<int> top;
+  std::vector<long long> tbase;
+  struct Span {
+    TileMap* tm;
+    size_t first;
+  };
+  std::vector<Span> spans;
+  auto add = [&](TileMap* tm, int kind, int threads, bool fibres, int a) {
+    spans.push_back({tm, top.size()});
+    for (int t = 0; t < ns; ++t) {
+      const View& v = ops[(size_t)kind * ns + t].out;
+      const int a1 = a == 0 ? 1 : 0, a2 = a == 2 ? 1 : 2;
+      const long long n = fibres ? (long long)v.n[a1] * v.n[a2] : (long long)v.n[0] * v.n[1] * v.n[2];
+      for (long long e = 0; e < n; e += threads) {
+        top.push_back(t);
+        tbase.push_back(e);
+      }
+    }
+    tm->ntiles = (int)(top.size() - spans.back().first);
+    tm->threads = threads;
+  };
+  for (int a = 0; a < d; ++a) {
+    add(&md->tm_proj[a], OP_PROJ0 + a, tc, false, a);
+    add(&md->tm_solve[a], OP_SOLVEL0 + a, ts, true, a);
+    add(&md->tm_dec[a], OP_DEC0 + a, te, false, a);
+  }
+  std::vector<int> rfirst(ns + 1, 0), rid(ns);
+  const size_t f0 = spans.back().first;  // the last span added is the last decode axis
+  for (size_t k = f0; k < top.size(); ++k) rfirst[top[k] + 1]++;
+  for (int t = 0; t < ns; ++t) {
+    rfirst[t + 1] += rfirst[t];
+    rid[t] = md->hmem[t];
+  }
+  const size_t nt = top.size();
+  void* mem = nullptr;
+  int rc = pool_alloc(h, &mem, nt * (sizeof(int) + sizeof(long long)) + (2 * (size_t)ns + 1) * sizeof(int) + 16);
+  if (rc != MFA_OK) return rc;
+  long long* dbase = (long long*)mem;
+  int* dop = (int*)(dbase + nt);
+  int* dfirst = dop + nt;
+  int* did = dfirst + ns + 1;
+  cudaError_t e = cudaMemcpyAsync(dbase, tbase.data(), nt * sizeof(long long), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dop, top.data(), nt * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dfirst, rfirst.data(), (ns + 1) * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(did, rid.data(), ns * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+  if (e != cudaSuccess) {
+    pool_free(h, mem);
+    return cuda_status(e);
+  }
+  pool_free(h, md->tiles);  // stream-ordered: after the launches that used the old maps
+  md->tiles = mem;
+  md->res_first = dfirst;
+  md->res_id = did;
+  for (const Span& sp : spans) {
+    sp.tm->op = dop + sp.first;
+    sp.tm->base = dbase + sp.first;
+  }
+  md->tile_c = tc;
+  md->tile_s = ts;
+  md->tile_e = te;
+  return MFA_OK;
+}
 
 // One (dimension, degree) group as a model over virtual axes: axis a
 // concatenates the group's instances, each a piece with its own knot vector;
@@ -1551,68 +1627,15 @@ int build_batch_group(mfa_batch* b, int d, int p, const std::vector<int>& mem, m
   }
   md->BL = md->X = b->buf;
   md->P = b->buf;
-  // tile maps: every operand of a launch split into blocks of the kernel's size
-  {
-    std::vector<int> top;
-    std::vector<long long> tbase;
-    struct Span { TileMap* tm; size_t first; };
-    std::vector<Span> spans;
-    auto add = [&](TileMap* tm, int kind, int threads, bool fibres, int a) {
-      spans.push_back({tm, top.size()});
-      for (int t = 0; t < ns; ++t) {
-        const View& v = ops[(size_t)kind * ns + t].out;
-        const int a1 = a == 0 ? 1 : 0, a2 = a == 2 ? 1 : 2;
-        const long long n = fibres ? (long long)v.n[a1] * v.n[a2] : (long long)v.n[0] * v.n[1] * v.n[2];
-        for (long long e = 0; e < n; e += threads) {
-          top.push_back(t);
-          tbase.push_back(e);
-        }
-      }
-      tm->ntiles = (int)(top.size() - spans.back().first);
-    };
-    for (int a = 0; a < d; ++a) {
-      add(&md->tm_proj[a], OP_PROJ0 + a, kContractThreads, false, a);
-      add(&md->tm_solve[a], OP_SOLVEL0 + a, kSolveThreads, true, a);
-      add(&md->tm_dec[a], OP_DEC0 + a, kExpandThreads, false, a);
-    }
-    // per instance: its first tile of the last decode axis (tiles of an
-    // operand are consecutive) and its index in the batch
-    std::vector<int> rfirst(ns + 1, 0), rid(ns);
-    {
-      const size_t f0 = spans.back().first;  // the last span added is the last decode axis
-      for (size_t k = f0; k < top.size(); ++k) rfirst[top[k] + 1]++;
-      for (int t = 0; t < ns; ++t) {
-        rfirst[t + 1] += rfirst[t];
-        rid[t] = mem[t];
-      }
-    }
-    const size_t nt = top.size();
-    rc = pool_alloc(h, &md->tiles, nt * (sizeof(int) + sizeof(long long)) + (2 * (size_t)ns + 1) * sizeof(int) + 16);
-    cudaError_t e = rc == MFA_OK ? cudaSuccess : cudaErrorMemoryAllocation;
-    long long* dbase = (long long*)md->tiles;
-    int* dop = (int*)(dbase + nt);
-    int* dfirst = dop + nt;
-    int* did = dfirst + ns + 1;
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dbase, tbase.data(), nt * sizeof(long long), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dop, top.data(), nt * sizeof(int), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(dfirst, rfirst.data(), (ns + 1) * sizeof(int), cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(did, rid.data(), ns * sizeof(int), cudaMemcpyHostToDevice, h->stream);
-    md->res_first = dfirst;
-    md->res_id = did;
-    if (e != cudaSuccess) {
-      md->BL = md->X = md->P = nullptr;
-      pool_free(h, md->tiles);
-      md->tiles = nullptr;
-      pool_free(h, md->arena);
-      pool_free(h, md->big);
-      delete md;
-      return rc != MFA_OK ? rc : cuda_status(e);
-    }
-    for (const Span& sp : spans) {
-      sp.tm->op = dop + sp.first;
-      sp.tm->base = dbase + sp.first;
-    }
+  md->hops = ops;
+  md->hmem = mem;
+  rc = build_batch_tiles(h, md, kContractThreads, kSolveThreads, kExpandThreads);
+  if (rc != MFA_OK) {
+    md->BL = md->X = md->P = nullptr;
+    pool_free(h, md->arena);
+    pool_free(h, md->big);
+    delete md;
+    return rc;
   }
   h->live_models++;
   *out = md;
@@ -1667,6 +1690,67 @@ int batch_decode_any(mfa_batch* b, TOut* out) {
 }
 
 }  // namespace
+
+namespace {
+// Self-tuned tile sizes: the fit of every group (projection + solves) is timed
+// on the stream for every pair of block sizes (projection 64 / 128 / 256,
+// solves 32 / 64 / 128; one warm run, one timed run each) and the fastest
+// pair is kept for every group.  The decode keeps 256.
+int batch_autotune(mfa_batch* b, const void* q, int q_dtype) {
+  mfa_handle* h = b->h;
+  const int cand_c[3] = {64, 128, 256}, cand_s[3] = {32, 64, 128};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MFA_ERR_CUDA;
+  const bool tr = h->trace_on;
+  trace_flush(h);
+  h->trace_on = false;
+  float best = 1e30f;
+  int bc = kContractThreads, bs = kSolveThreads, rc = MFA_OK;
+  for (int ic = 0; ic < 3 && rc == MFA_OK; ++ic)
+    for (int is = 0; is < 3 && rc == MFA_OK; ++is) {
+      for (mfa_model* md : b->groups) {
+        rc = build_batch_tiles(h, md, cand_c[ic], cand_s[is], kExpandThreads);
+        if (rc != MFA_OK) break;
+      }
+      if (rc != MFA_OK) break;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {
+        cudaEventRecord(e0, h->stream);
+        if (b->prec == MFA_PREC_FP64)
+          batch_fit<double>(b, q, q_dtype);
+        else
+          batch_fit<ff>(b, q, q_dtype);
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = MFA_ERR_CUDA;
+        cudaEventElapsedTime(&ms, e0, e1);
+      }
+      b->tune_ms[ic * 3 + is] = ms;
+      if (ms < best) {
+        best = ms;
+        bc = cand_c[ic];
+        bs = cand_s[is];
+      }
+    }
+  for (mfa_model* md : b->groups)
+    if (rc == MFA_OK) rc = build_batch_tiles(h, md, bc, bs, kExpandThreads);
+  h->trace_on = tr;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc == MFA_OK) b->tuned = true;
+  return rc;
+}
+}  // namespace
+
+int mfa_batch_tile_sizes(const mfa_batch* b, int32_t* sizes, float* candidate_ms) {
+  if (!b || !sizes) return MFA_ERR_ARG;
+  const mfa_model* md = b->groups.empty() ? nullptr : b->groups[0];
+  sizes[0] = md ? md->tile_c : 0;
+  sizes[1] = md ? md->tile_s : 0;
+  sizes[2] = md ? md->tile_e : 0;
+  if (candidate_ms)
+    for (int i = 0; i < 9; ++i) candidate_ms[i] = b->tune_ms[i];
+  return b->tuned ? MFA_OK : MFA_NOT_CONVERGED;
+}
 
 int mfa_encode_batch(mfa_handle* h, int32_t count, const mfa_instance* inst, const void* q, int q_dtype,
                      int q_on_device, int precision, mfa_batch** out) {
@@ -1788,6 +1872,10 @@ int mfa_batch_refit(mfa_handle* h, mfa_batch* b, const void* q, int q_dtype) {
   if (q_dtype != MFA_F32 && q_dtype != MFA_F64) return MFA_ERR_ARG;
   DeviceGuard g(h->device);
   cudaError_t e = cudaSuccess;
+  if (!b->tuned) {
+    int rc = batch_autotune(b, q, q_dtype);
+    if (rc != MFA_OK) return rc;
+  }
   if (!b->graph || b->graph_q != q || b->graph_dtype != q_dtype) {
     if (b->graph) {
       cudaGraphExecDestroy(b->graph);

@@ -94,6 +94,7 @@ struct TileMap {
   const int* op = nullptr;
   const long long* base = nullptr;
   int ntiles = 0;
+  int threads = 0;  // block size = elements per tile
 };
 
 // ---------------------------------------------------------------------------

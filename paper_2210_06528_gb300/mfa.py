@@ -133,6 +133,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_batch_decode.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int]
     lib.mfa_batch_free.argtypes = [P]
     lib.mfa_set_update_rule.argtypes = [P, P, ctypes.c_int]
+    lib.mfa_batch_tile_sizes.argtypes = [P, P, P]
+    lib.mfa_batch_tile_sizes.restype = ctypes.c_int
     lib.mfa_batch_decode_points.argtypes = [P, P, ctypes.c_int32, P, P, P, P, ctypes.c_int]
     lib.mfa_server_create.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(P)]
     lib.mfa_server_encode.argtypes = [P, ctypes.POINTER(mfa_instance), P, ctypes.c_int]
@@ -293,6 +295,14 @@ def mfa_batch_decode(h: int, b: int, out_ptr: int, out_dtype: int, out_on_device
 
 def mfa_set_update_rule(h: int, m: int, rule: int) -> None:
     _check(load().mfa_set_update_rule(ctypes.c_void_p(h), ctypes.c_void_p(m), int(rule)), "mfa_set_update_rule")
+
+
+def mfa_batch_tile_sizes(b: int):
+    """(rc, [projection, solve, decode] block sizes, 3x3 candidate fit times in ms)."""
+    sizes = (ctypes.c_int32 * 3)()
+    ms = (ctypes.c_float * 9)()
+    rc = load().mfa_batch_tile_sizes(ctypes.c_void_p(b), sizes, ms)
+    return rc, list(sizes), np.array(list(ms)).reshape(3, 3)
 
 
 def mfa_batch_decode_points(h: int, b: int, qinst, pt_off, pts, out) -> None:
@@ -604,6 +614,9 @@ class Batch:
         ptr, code, dev, keep = _ptr_dtype(out)
         mfa_batch_decode(self.handle.h, self.b, ptr, code, dev)
         return out
+
+    def tile_sizes(self):
+        return mfa_batch_tile_sizes(self.b)
 
     def decode_points(self, qinst, pt_off, pts, out=None):
         """Scattered decode: query k evaluates instance qinst[k] at pts[pt_off[k]:pt_off[k+1]]

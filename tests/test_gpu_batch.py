@@ -61,7 +61,12 @@ def test_batch_refit_graph_equals_fresh_encode():
         q1 = torch.from_numpy(data).cuda()
         q2 = torch.from_numpy(data2).cuda()
         b = h.encode_batch(specs, q1, mfa.MFA_PREC_MIXED)
+        rc0, sizes0, _ = b.tile_sizes()
+        assert rc0 == mfa.MFA_NOT_CONVERGED and sizes0 == [128, 64, 256]
         b.refit(q2)
+        rc1, sizes1, cand = b.tile_sizes()  # tuned by timing on the first refit
+        assert rc1 == mfa.MFA_OK and sizes1[0] in (64, 128, 256) and sizes1[1] in (32, 64, 128)
+        assert (cand > 0).all() and cand.min() == cand[(64, 128, 256).index(sizes1[0]), (32, 64, 128).index(sizes1[1])]
         b.refit(q2)  # replay of the captured graph
         P2 = b.ctrl()
         c = h.encode_batch(specs, q2, mfa.MFA_PREC_MIXED)
