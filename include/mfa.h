@@ -52,7 +52,8 @@ enum {
   MFA_ERR_DIVERGED = -6,   /* the Schwarz update grew for 8 iterations in a row */
   MFA_ERR_NONFINITE = -7,  /* the input data held NaN or Inf */
   MFA_ERR_UNSUPPORTED = -8, /* valid request outside what this build implements */
-  MFA_ERR_TIMEOUT = -9      /* a kernel's bounded wait for an asynchronous copy gave up; results invalid */
+  MFA_ERR_TIMEOUT = -9,     /* a kernel's bounded wait for an asynchronous copy gave up; results invalid */
+  MFA_ERR_IO = -10          /* a file could not be read or written, or is not a saved model */
 };
 
 enum { MFA_F32 = 0, MFA_F64 = 1 };
@@ -156,6 +157,21 @@ int mfa_schwarz_iterate(mfa_handle* h, mfa_model* m, int32_t max_iters, double t
  *   out          dtype out_dtype, on the device if out_on_device            */
 int mfa_decode(mfa_handle* h, const mfa_model* m, const double* pts, int64_t npts_q,
                const int32_t* deriv, void* out, int out_dtype, int out_on_device);
+
+/* Persistence of a fitted model (the paper writes the encoded MFA to disk
+ * for later decoding, Algorithm 1 output).  mfa_save writes the layout, the
+ * update rule, the iteration count and the global control points exactly as
+ * held on the device (FP64, or float-float pairs for MFA_PREC_MIXED), plus,
+ * with flags & MFA_SAVE_STATE, the Schwarz state (B_L and the subdomain
+ * copies) so the iteration can continue after a load.  mfa_load rebuilds the
+ * model on the handle's device (layout, basis, factors) and restores those
+ * values bit for bit; a model loaded without state decodes and computes
+ * residuals but mfa_schwarz_iterate refuses it (MFA_ERR_ARG).  Files are
+ * little-endian and carry a magic and a version; anything else is refused
+ * with MFA_ERR_IO.  Not for batch models.  Synchronous. */
+#define MFA_SAVE_STATE 1
+int mfa_save(mfa_handle* h, const mfa_model* m, const char* path, int flags);
+int mfa_load(mfa_handle* h, const char* path, mfa_model** out);
 
 /* Update rule of the global control points from the subdomains' owned
  * copies (Sec. 2.3).  MFA_UPDATE_AVERAGE (the default): the uniformly

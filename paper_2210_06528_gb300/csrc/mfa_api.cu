@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <type_traits>
@@ -46,6 +47,8 @@ struct mfa_model {
   int q_staged_dtype = MFA_F32;
   bool plain = false;              // per-subdomain comparator form (mfa_encode_plain)
   bool batch = false;              // one (dimension, degree) group of a batch of independent fits
+  bool has_state = false;          // B_L and the subdomain copies are valid (the Schwarz iteration can run)
+  int overlap[3] = {0, 0, 0};      // delta per axis, as given
   int update = UPDATE_AVERAGE;     // rule of the global update from the owned copies
   long long maxDec[3] = {0, 0, 0}; // batch: largest decode-stage output per axis
   long long decS1 = 0, decS2 = 0;  // batch: decode stage scratch sizes (elements)
@@ -770,6 +773,7 @@ const char* mfa_status_string(int s) {
     case MFA_ERR_NONFINITE: return "non-finite input data";
     case MFA_ERR_UNSUPPORTED: return "unsupported request";
     case MFA_ERR_TIMEOUT: return "device wait on an asynchronous copy timed out";
+    case MFA_ERR_IO: return "file could not be read or written, or is not a saved model";
     default: return "unknown status";
   }
 }
@@ -992,13 +996,14 @@ int mfa_encode_plain(mfa_handle* h, const mfa_layout* lay, const void* q, int q_
 }
 
 namespace {
-int encode_impl(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype, int q_on_device, bool plain,
-                mfa_model** out) {
-  if (!h || !lay || !q || !out) return MFA_ERR_ARG;
+// A model for a layout: host layout, operand tables, device tables, buffers
+// (plus stage_bytes for staged host data, offset in *o_stage) and the setup
+// kernels (basis, Gram bands, Cholesky factors).  No data are read.
+int create_model(mfa_handle* h, const mfa_layout* lay, bool plain, size_t stage_bytes, mfa_model** out,
+                 size_t* o_stage) {
   *out = nullptr;
   if (lay->dim < 1 || lay->dim > MFA_MAX_DIM) return MFA_ERR_ARG;
   if (lay->degree < 1 || lay->degree > MFA_MAX_DEGREE) return MFA_ERR_ARG;
-  if (q_dtype != MFA_F32 && q_dtype != MFA_F64) return MFA_ERR_ARG;
   if (lay->precision != MFA_PREC_FP64 && lay->precision != MFA_PREC_MIXED) return MFA_ERR_ARG;
   DeviceGuard g(h->device);
   mfa_model* md = new (std::nothrow) mfa_model();
@@ -1021,6 +1026,7 @@ int encode_impl(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype
                       lay->overlap[a]);
       md->lo[a] = lay->lo[a];
       md->hi[a] = lay->hi[a];
+      md->overlap[a] = lay->overlap[a];
       npts_total *= lay->npts[a];
     } else {
       rc = build_axis(md->axh[a], 1, 1, 0, 1, nullptr, 0);
@@ -1052,13 +1058,28 @@ int encode_impl(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype
   std::vector<AxisOp> ops;
   std::vector<long long> offL, offS1, offS2;
   build_ops(md, ops, offL, offS1, offS2);
-  const size_t qbytes = (size_t)npts_total * (q_dtype == MFA_F64 ? 8 : 4);
-  size_t o_Q = 0;
-  int rc = materialize_model(h, md, ops, offL, offS1, offS2, q_on_device ? 0 : qbytes, &o_Q);
+  int rc = materialize_model(h, md, ops, offL, offS1, offS2, stage_bytes, o_stage);
   if (rc != MFA_OK) {
     delete md;
     return rc;
   }
+  *out = md;
+  return MFA_OK;
+}
+
+int encode_impl(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype, int q_on_device, bool plain,
+                mfa_model** out) {
+  if (!h || !lay || !q || !out) return MFA_ERR_ARG;
+  *out = nullptr;
+  if (q_dtype != MFA_F32 && q_dtype != MFA_F64) return MFA_ERR_ARG;
+  long long npts_total = 1;
+  for (int a = 0; a < lay->dim && a < 3; ++a) npts_total *= std::max<long long>(lay->npts[a], 1);
+  const size_t qbytes = (size_t)npts_total * (q_dtype == MFA_F64 ? 8 : 4);
+  size_t o_Q = 0;
+  mfa_model* md = nullptr;
+  int rc = create_model(h, lay, plain, q_on_device ? 0 : qbytes, &md, &o_Q);
+  if (rc != MFA_OK) return rc;
+  DeviceGuard g(h->device);
   cudaError_t e = cudaSuccess;
   const void* qd = q;
   if (!q_on_device) {
@@ -1091,6 +1112,7 @@ int encode_impl(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype
     return cuda_status(e);
   }
   md->iters = 0;
+  md->has_state = true;
   h->live_models++;
   *out = md;
   return MFA_OK;
@@ -1120,7 +1142,7 @@ int mfa_set_update_rule(mfa_handle* h, mfa_model* md, int rule) {
 }
 
 int mfa_schwarz_iterate(mfa_handle* h, mfa_model* md, int32_t max_iters, double tol_dP, mfa_report* rep) {
-  if (!h || !md || md->h != h || max_iters < 0) return MFA_ERR_ARG;
+  if (!h || !md || md->h != h || max_iters < 0 || (!md->has_state && max_iters > 0)) return MFA_ERR_ARG;
   DeviceGuard g(h->device);
   int status = read_status(h);  // surfaces encode-time device errors
   if (status < 0) return status;
@@ -1303,6 +1325,153 @@ int mfa_get_ctrl(mfa_handle* h, const mfa_model* mdc, double* host_out, int64_t 
   if (e != cudaSuccess) return cuda_status(e);
   int st = read_status(h);
   return st < 0 ? st : MFA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Persistence: a fitted model to a file and back (layout, update rule,
+// iteration count, global control points as stored on the device, and
+// optionally the Schwarz state: B_L and the subdomain copies)
+// ---------------------------------------------------------------------------
+
+namespace {
+constexpr char kMagic[8] = {'M', 'F', 'A', 'G', 'B', '3', 0, 1};
+constexpr int32_t kFileVersion = 1;
+
+struct FileHeader {
+  char magic[8];
+  int32_t version, dim, degree, precision, update, flags, iters, pad;
+  int64_t npts[3];
+  int32_t nspans[3], nsub[3], overlap[3], pad2;
+  double lo[3], hi[3];
+  double last_dP, last_jump;
+  int64_t ncp, sizeL;
+};
+}  // namespace
+
+int mfa_save(mfa_handle* h, const mfa_model* mdc, const char* path, int flags) {
+  mfa_model* md = const_cast<mfa_model*>(mdc);
+  if (!h || !md || md->h != h || !path || md->batch) return MFA_ERR_ARG;
+  if ((flags & MFA_SAVE_STATE) && !md->has_state) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  FileHeader H{};
+  std::memcpy(H.magic, kMagic, 8);
+  H.version = kFileVersion;
+  H.dim = md->dim;
+  H.degree = md->degree;
+  H.precision = md->prec;
+  H.update = md->update == UPDATE_OWNER ? MFA_UPDATE_OWNER : MFA_UPDATE_AVERAGE;
+  H.flags = flags & MFA_SAVE_STATE;
+  H.iters = md->iters;
+  for (int a = 0; a < 3; ++a) {
+    H.npts[a] = md->axh[a].M;
+    H.nspans[a] = md->axh[a].nspans;
+    H.nsub[a] = md->axh[a].S;
+    H.overlap[a] = md->overlap[a];
+    H.lo[a] = md->lo[a];
+    H.hi[a] = md->hi[a];
+  }
+  H.last_dP = md->last_dP;
+  H.last_jump = md->last_jump;
+  H.ncp = (long long)md->axh[0].n * md->axh[1].n * md->axh[2].n;
+  H.sizeL = md->sizeL;
+  const size_t es = elem_size(md->prec);
+  std::vector<char> buf((size_t)H.ncp * es + ((flags & MFA_SAVE_STATE) ? 2 * (size_t)md->sizeL * es : 0));
+  cudaError_t e = cudaMemcpyAsync(buf.data(), md->P, (size_t)H.ncp * es, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess && (flags & MFA_SAVE_STATE)) {
+    char* p2 = buf.data() + (size_t)H.ncp * es;
+    e = cudaMemcpyAsync(p2, md->BL, (size_t)md->sizeL * es, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p2 + (size_t)md->sizeL * es, md->X, (size_t)md->sizeL * es, cudaMemcpyDeviceToHost,
+                          h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return MFA_ERR_IO;
+  bool ok = std::fwrite(&H, sizeof(H), 1, f) == 1;
+  for (int a = 0; a < md->dim && ok; ++a)
+    for (const AxisSub& sb : md->axh[a].subs) {
+      const int32_t c = sb.b - sb.a;
+      ok = ok && std::fwrite(&c, sizeof(c), 1, f) == 1;
+    }
+  ok = ok && std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? MFA_OK : MFA_ERR_IO;
+}
+
+int mfa_load(mfa_handle* h, const char* path, mfa_model** out) {
+  if (!h || !path || !out) return MFA_ERR_ARG;
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return MFA_ERR_IO;
+  FileHeader H{};
+  bool ok = std::fread(&H, sizeof(H), 1, f) == 1 && std::memcmp(H.magic, kMagic, 8) == 0 &&
+            H.version == kFileVersion && H.dim >= 1 && H.dim <= MFA_MAX_DIM && H.degree >= 1 &&
+            H.degree <= MFA_MAX_DEGREE && (H.precision == MFA_PREC_FP64 || H.precision == MFA_PREC_MIXED);
+  std::vector<int32_t> cores[3];
+  for (int a = 0; a < H.dim && ok; ++a) {
+    ok = H.nsub[a] >= 1 && H.nsub[a] <= (1 << 20);
+    if (ok) {
+      cores[a].resize(H.nsub[a]);
+      ok = std::fread(cores[a].data(), sizeof(int32_t), H.nsub[a], f) == (size_t)H.nsub[a];
+    }
+  }
+  if (!ok) {
+    std::fclose(f);
+    return MFA_ERR_IO;
+  }
+  mfa_layout lay{};
+  lay.dim = H.dim;
+  lay.degree = H.degree;
+  lay.precision = H.precision;
+  for (int a = 0; a < 3; ++a) {
+    lay.npts[a] = H.npts[a];
+    lay.nspans[a] = H.nspans[a];
+    lay.nsub[a] = H.nsub[a];
+    lay.overlap[a] = H.overlap[a];
+    lay.lo[a] = H.lo[a];
+    lay.hi[a] = H.hi[a];
+    lay.core_spans[a] = a < H.dim ? cores[a].data() : nullptr;
+  }
+  mfa_model* md = nullptr;
+  size_t o_unused = 0;
+  int rc = create_model(h, &lay, false, 0, &md, &o_unused);
+  if (rc != MFA_OK) {
+    std::fclose(f);
+    return rc;
+  }
+  const size_t es = elem_size(md->prec);
+  const long long ncp = (long long)md->axh[0].n * md->axh[1].n * md->axh[2].n;
+  const bool state = (H.flags & MFA_SAVE_STATE) != 0;
+  ok = H.ncp == ncp && (!state || H.sizeL == md->sizeL);
+  std::vector<char> buf(ok ? (size_t)ncp * es + (state ? 2 * (size_t)md->sizeL * es : 0) : 0);
+  ok = ok && std::fread(buf.data(), 1, buf.size(), f) == buf.size();
+  std::fclose(f);
+  DeviceGuard g(h->device);
+  cudaError_t e = cudaSuccess;
+  if (ok) e = cudaMemcpyAsync(md->P, buf.data(), (size_t)ncp * es, cudaMemcpyHostToDevice, h->stream);
+  if (ok && state && e == cudaSuccess) {
+    const char* p2 = buf.data() + (size_t)ncp * es;
+    e = cudaMemcpyAsync(md->BL, p2, (size_t)md->sizeL * es, cudaMemcpyHostToDevice, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(md->X, p2 + (size_t)md->sizeL * es, (size_t)md->sizeL * es, cudaMemcpyHostToDevice,
+                          h->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (!ok || e != cudaSuccess) {
+    pool_free(h, md->arena);
+    pool_free(h, md->big);
+    delete md;
+    return ok ? cuda_status(e) : MFA_ERR_IO;
+  }
+  md->update = H.update == MFA_UPDATE_OWNER ? UPDATE_OWNER : UPDATE_AVERAGE;
+  md->iters = H.iters;
+  md->last_dP = H.last_dP;
+  md->last_jump = H.last_jump;
+  md->has_state = state;
+  h->live_models++;
+  *out = md;
+  return MFA_OK;
 }
 
 int mfa_free(mfa_model* md) {

@@ -28,6 +28,8 @@ MFA_ERR_DIVERGED = -6
 MFA_ERR_NONFINITE = -7
 MFA_ERR_UNSUPPORTED = -8
 MFA_ERR_TIMEOUT = -9
+MFA_ERR_IO = -10
+MFA_SAVE_STATE = 1
 MFA_F32, MFA_F64 = 0, 1
 MFA_PREC_FP64, MFA_PREC_MIXED = 0, 1
 MFA_UPDATE_AVERAGE, MFA_UPDATE_OWNER = 0, 1
@@ -133,6 +135,10 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_batch_decode.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int]
     lib.mfa_batch_free.argtypes = [P]
     lib.mfa_set_update_rule.argtypes = [P, P, ctypes.c_int]
+    lib.mfa_save.argtypes = [P, P, ctypes.c_char_p, ctypes.c_int]
+    lib.mfa_save.restype = ctypes.c_int
+    lib.mfa_load.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(P)]
+    lib.mfa_load.restype = ctypes.c_int
     lib.mfa_batch_tile_sizes.argtypes = [P, P, P]
     lib.mfa_batch_tile_sizes.restype = ctypes.c_int
     lib.mfa_batch_decode_points.argtypes = [P, P, ctypes.c_int32, P, P, P, P, ctypes.c_int]
@@ -295,6 +301,32 @@ def mfa_batch_decode(h: int, b: int, out_ptr: int, out_dtype: int, out_on_device
 
 def mfa_set_update_rule(h: int, m: int, rule: int) -> None:
     _check(load().mfa_set_update_rule(ctypes.c_void_p(h), ctypes.c_void_p(m), int(rule)), "mfa_set_update_rule")
+
+
+def mfa_save(h: int, m: int, path: str, flags: int = 0) -> None:
+    _check(load().mfa_save(ctypes.c_void_p(h), ctypes.c_void_p(m), os.fsencode(path), int(flags)), "mfa_save")
+
+
+def mfa_load(h: int, path: str) -> int:
+    m = ctypes.c_void_p()
+    _check(load().mfa_load(ctypes.c_void_p(h), os.fsencode(path), ctypes.byref(m)), "mfa_load")
+    return m.value
+
+
+def saved_layout(path: str) -> mfa_layout:
+    """The layout stored in a saved model's header (dimension, degree, grid,
+    spans, subdomains, overlap, precision, box)."""
+    import struct
+    with open(path, "rb") as f:
+        head = f.read(192)
+        fields = struct.unpack("<8s8i3q12i6d2d2q", head)
+        dim, degree, prec = fields[2], fields[3], fields[4]
+        npts = fields[9:12]
+        nspans, nsub, overlap = fields[12:15], fields[15:18], fields[18:21]
+        lo, hi = fields[22:25], fields[25:28]
+        cores = [list(struct.unpack(f"<{nsub[a]}i", f.read(4 * nsub[a]))) for a in range(dim)]
+    return make_layout(dim, degree, list(npts[:dim]), list(nspans[:dim]), list(nsub[:dim]), list(overlap[:dim]), prec,
+                       core_spans=cores, lo=list(lo[:dim]), hi=list(hi[:dim]))
 
 
 def mfa_batch_tile_sizes(b: int):
@@ -507,6 +539,11 @@ class Handle:
         b = mfa_encode_batch(self.h, inst, ptr, code, dev, precision)
         return Batch(self, b, len(inst))
 
+    def load(self, path: str) -> "Model":
+        """A model saved with Model.save, rebuilt on this handle's device."""
+        m = mfa_load(self.h, path)
+        return Model(self, m, saved_layout(path))
+
     def encode_plain(self, q, layout: mfa_layout, max_iters: int, tol_dP: float):
         """Encode and iterate in the per-subdomain comparator form; returns (Model, rc, report)."""
         ptr, code, dev, keep = _ptr_dtype(q)
@@ -538,6 +575,10 @@ class Model:
         self.degree = layout.degree
         self.npts = [int(layout.npts[a]) for a in range(self.dim)]
         self.ncp = [int(layout.nspans[a]) + layout.degree for a in range(self.dim)]
+
+    def save(self, path: str, state: bool = False) -> None:
+        """Write the model (and with state=True the Schwarz state, to iterate on after a load)."""
+        mfa_save(self.handle.h, self.m, path, MFA_SAVE_STATE if state else 0)
 
     def set_update_rule(self, rule: int) -> None:
         """MFA_UPDATE_AVERAGE or MFA_UPDATE_OWNER; recomputes the current global control points."""
