@@ -90,6 +90,8 @@ struct Proj3dArgs {
   int by;        // staged rows per plane = box y = largest window along y
   int mz;        // largest window along z
   int n0, n1;    // largest L along x and y
+  const AxisOp* inst;  // independent fits: the projection operand of every instance (data offset, strides)
+  const int* order;    // CTA -> subdomain / instance (largest first), or null
 };
 
 // Shared-memory carve-up of the projection, used by the kernel and the launcher.
@@ -191,16 +193,27 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
   constexpr int W = P + 1;
   extern __shared__ __align__(128) unsigned char smem[];
   const LayoutDev& L = A.L;
-  const int s = blockIdx.x;
-  const int s0 = s % L.S[0], s1 = (s / L.S[0]) % L.S[1], s2 = s / (L.S[0] * L.S[1]);
+  const int s = A.order ? A.order[blockIdx.x] : blockIdx.x;
+  int s0, s1, s2;
+  sub_pieces(L, s, s0, s1, s2);
   const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];
   const int m0 = bx.m, m1 = by.m, m2 = bz.m;
   const int n0 = bx.nL, n1 = by.nL, n2 = bz.nL;
   const int zb = A.zb, BX = A.bx, BY = A.by;
-  const int cx = bx.k0 & 3;              // staged position of window point 0
-  const int xa = bx.k0 - cx;             // global x of staged position 0 (multiple of 4)
+  // window origin in the data: the subdomain's corner of the one grid, or
+  // (independent fits) the instance's own grid at its offset and strides
+  long long M0 = L.M[0], M01 = L.M[0] * L.M[1];
+  int wx = bx.k0, wy = by.k0, wz = bz.k0;
+  if (A.inst) {
+    const View& v = A.inst[s].in;
+    Q += v.off;
+    M0 = v.st[1];
+    M01 = v.st[2];
+    wx = wy = wz = 0;
+  }
+  const int cx = TMA ? (wx & 3) : 0;     // staged position of window point 0
+  const int xa = wx - cx;                // data x of staged position 0 (multiple of 4 for the tensor copy)
   const int nq4 = (cx + m0 + 3) >> 2;    // 16-byte chunks of a row that hold window points
-  const long long M0 = L.M[0], M01 = L.M[0] * L.M[1];
   const ProjSmem lay = proj_smem_layout(W, zb, BX, BY, A.mz, A.n0, A.n1);
 
   float* Qs = reinterpret_cast<float*>(smem);  // [zb][BY][BX]; row t's stage-1 output as ff pairs at its start
@@ -220,10 +233,10 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
   if constexpr (TMA) {
     if (threadIdx.x == 0) {
       mbar_init(bar, 1);
-      tma_load_box(&tmq, Qs, bar, xa, by.k0, bz.k0, box_bytes);
+      tma_load_box(&tmq, Qs, bar, xa, wy, wz, box_bytes);
     }
   } else {
-    stage_rows<TQ>(Qs, Q, M0, M01, xa, by.k0, bz.k0, min(zb, m2), m1, BX, BY);
+    stage_rows<TQ>(Qs, Q, M0, M01, xa, wy, wz, min(zb, m2), m1, BX, BY);
   }
 
   // basis tables: x by staged position (zero outside the window, span held
@@ -382,9 +395,9 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
     __syncthreads();
     if (z0 + zb < m2) {
       if constexpr (TMA) {
-        if (threadIdx.x == 0) tma_load_box(&tmq, Qs, bar, xa, by.k0, bz.k0 + z0 + zb, box_bytes);
+        if (threadIdx.x == 0) tma_load_box(&tmq, Qs, bar, xa, wy, wz + z0 + zb, box_bytes);
       } else {
-        stage_rows<TQ>(Qs, Q, M0, M01, xa, by.k0, bz.k0 + z0 + zb, min(zb, m2 - z0 - zb), m1, BX, BY);
+        stage_rows<TQ>(Qs, Q, M0, M01, xa, wy, wz + z0 + zb, min(zb, m2 - z0 - zb), m1, BX, BY);
       }
     }
     // ---- stage 3: accumulate the planes into the z ring
@@ -461,13 +474,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // consumed data in place.
 template <typename TQ>
 bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, int maxm1, int maxm2, int maxn0,
-                         int maxn1, bool inplace_ok, const TQ* Q, ff* BL, int* status, cudaStream_t st) {
+                         int maxn1, bool inplace_ok, const TQ* Q, ff* BL, int* status, cudaStream_t st,
+                         const AxisOp* inst, const int* order) {
   const int P = L.ax[0].p;
   if (L.dim != 3 || L.ax[1].p != P || L.ax[2].p != P || !inplace_ok) return false;
   const int npairs = maxn0 * maxn1;
   Proj3dArgs A;
   A.L = L;
   A.offL = offL;
+  A.inst = inst;
+  A.order = order;
   // row pitch: window plus alignment slack, room for the in-place output,
   // a multiple of 4 floats with an odd number of 16-byte chunks
   int bx = std::max(maxm0 + 3, 2 * maxn0 + 2);
@@ -495,8 +511,8 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
   // multiple of 16 bytes long and boxes of at most 256 per dimension
   CUtensorMap tmap;
   std::memset(&tmap, 0, sizeof(tmap));
-  bool tma = sizeof(TQ) == 4 && (reinterpret_cast<uintptr_t>(Q) % 16) == 0 && L.M[0] % 4 == 0 && A.bx <= 256 &&
-             A.by <= 256 && tensor_map_encoder() != nullptr;
+  bool tma = !inst && sizeof(TQ) == 4 && (reinterpret_cast<uintptr_t>(Q) % 16) == 0 && L.M[0] % 4 == 0 &&
+             A.bx <= 256 && A.by <= 256 && tensor_map_encoder() != nullptr;
   if (tma) {
     const cuuint64_t dims[3] = {(cuuint64_t)L.M[0], (cuuint64_t)L.M[1], (cuuint64_t)L.M[2]};
     const cuuint64_t strides[2] = {(cuuint64_t)L.M[0] * 4, (cuuint64_t)(L.M[0] * L.M[1]) * 4};
@@ -541,9 +557,9 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
 }
 
 template bool launch_project3d_ff<float>(const LayoutDev&, const long long*, int, int, int, int, int, bool,
-                                         const float*, ff*, int*, cudaStream_t);
+                                         const float*, ff*, int*, cudaStream_t, const AxisOp*, const int*);
 template bool launch_project3d_ff<double>(const LayoutDev&, const long long*, int, int, int, int, int, bool,
-                                          const double*, ff*, int*, cudaStream_t);
+                                          const double*, ff*, int*, cudaStream_t, const AxisOp*, const int*);
 
 }  // namespace mfa
 
@@ -953,7 +969,8 @@ __global__ void __launch_bounds__(NT, 2) k_schwarz3d_ff(Step3dArgs A, const ff* 
   extern __shared__ __align__(128) unsigned char smem[];
   const LayoutDev& L = A.L;
   const int s = blockIdx.x;
-  const int s0 = s % L.S[0], s1 = (s / L.S[0]) % L.S[1], s2 = s / (L.S[0] * L.S[1]);
+  int s0, s1, s2;
+  sub_pieces(L, s, s0, s1, s2);
   const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];
   const int nL0 = bx.nL, nL1 = by.nL, nL2 = bz.nL;
   const int nU0 = bx.nU, nU1 = by.nU, nU2 = bz.nU;
@@ -1466,7 +1483,8 @@ __global__ void __launch_bounds__(128) k_iter0_xy_ff(LayoutDev L, const long lon
   constexpr int W = P + 1;
   extern __shared__ __align__(128) unsigned char smem[];
   const int s = blockIdx.x, lz0 = blockIdx.y * kIt0Planes;
-  const int s0 = s % L.S[0], s1 = (s / L.S[0]) % L.S[1], s2 = s / (L.S[0] * L.S[1]);
+  int s0, s1, s2;
+  sub_pieces(L, s, s0, s1, s2);
   const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];
   if (lz0 >= bz.nL) return;
   const int npl = min(kIt0Planes, bz.nL - lz0);
@@ -1507,7 +1525,8 @@ __global__ void __launch_bounds__(128) k_iter0_z_ff(LayoutDev L, const long long
                                                     ff* __restrict__ X) {
   constexpr int W = P + 1;
   const int s = blockIdx.y;
-  const int s0 = s % L.S[0], s1 = (s / L.S[0]) % L.S[1], s2 = s / (L.S[0] * L.S[1]);
+  int s0, s1, s2;
+  sub_pieces(L, s, s0, s1, s2);
   const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];
   const int nf = bx.nL * by.nL;
   const int f = blockIdx.x * blockDim.x + threadIdx.x;

@@ -56,6 +56,7 @@ struct mfa_model {
   void* tiles = nullptr;                       // device storage of the tile maps
   const int* res_first = nullptr;              // batch: first last-axis decode tile of every instance [nsub + 1]
   const int* res_id = nullptr;                 // batch: batch index of every instance of the group [nsub]
+  const int* order = nullptr;                  // batch: instances largest first (fused projection CTA order)
   std::vector<AxisOp> hops;                    // batch: host copy of the operand tables (tile maps are rebuilt from it)
   std::vector<int> hmem;                       // batch: batch index of every instance of the group
   int tile_c = 0, tile_s = 0, tile_e = 0;      // batch: block sizes of the current tile maps
@@ -558,7 +559,9 @@ void run_encode(mfa_model* md, const TQ* q) {
     if (md->dim == 3 && md->use_fused) {
       TRACED(h, TR_PROJECT_DATA,
              fused = launch_project3d_ff<TQ>(L, md->offL, md->maxm[0], md->maxm[1], md->maxm[2], md->maxnL[0], md->maxnL[1],
-                                              md->x_inplace_ok, q, BL, h->d_status, h->stream));
+                                              md->x_inplace_ok, q, BL, h->d_status, h->stream,
+                                              md->batch ? md->ops + (size_t)OP_PROJ0 * ns : nullptr,
+                                              md->batch ? md->order : nullptr));
     }
   }
   if (md->plain) {
@@ -1595,23 +1598,34 @@ int build_batch_tiles(mfa_handle* h, mfa_model* md, int tc, int ts, int te) {
     rfirst[t + 1] += rfirst[t];
     rid[t] = md->hmem[t];
   }
+  // instances by decreasing size: the fused projection's CTA order
+  std::vector<int> ord(ns);
+  for (int t = 0; t < ns; ++t) ord[t] = t;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+    const View& vx = ops[(size_t)OP_PROJ0 * ns + x].in;
+    const View& vy = ops[(size_t)OP_PROJ0 * ns + y].in;
+    return (long long)vx.n[0] * vx.n[1] * vx.n[2] > (long long)vy.n[0] * vy.n[1] * vy.n[2];
+  });
   const size_t nt = top.size();
   void* mem = nullptr;
-  int rc = pool_alloc(h, &mem, nt * (sizeof(int) + sizeof(long long)) + (2 * (size_t)ns + 1) * sizeof(int) + 16);
+  int rc = pool_alloc(h, &mem, nt * (sizeof(int) + sizeof(long long)) + (3 * (size_t)ns + 1) * sizeof(int) + 16);
   if (rc != MFA_OK) return rc;
   long long* dbase = (long long*)mem;
   int* dop = (int*)(dbase + nt);
   int* dfirst = dop + nt;
   int* did = dfirst + ns + 1;
+  int* dord = did + ns;
   cudaError_t e = cudaMemcpyAsync(dbase, tbase.data(), nt * sizeof(long long), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dop, top.data(), nt * sizeof(int), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(dfirst, rfirst.data(), (ns + 1) * sizeof(int), cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(did, rid.data(), ns * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dord, ord.data(), ns * sizeof(int), cudaMemcpyHostToDevice, h->stream);
   if (e != cudaSuccess) {
     pool_free(h, mem);
     return cuda_status(e);
   }
+  md->order = dord;
   pool_free(h, md->tiles);  // stream-ordered: after the launches that used the old maps
   md->tiles = mem;
   md->res_first = dfirst;
@@ -1798,6 +1812,31 @@ int build_batch_group(mfa_batch* b, int d, int p, const std::vector<int>& mem, m
   md->P = b->buf;
   md->hops = ops;
   md->hmem = mem;
+  md->L.diag = 1;
+  // fused float-float kernels for 3-D groups run one CTA per instance
+  // (largest first); they pay off only when no instance dominates: the
+  // largest one, alone on an SM, must not outlast the group's work spread
+  // over every CTA slot (2 per SM) by more than half.  Otherwise the tile
+  // maps of the generic kernels spread each instance over many CTAs.  The
+  // in-place stage-1 output needs >= 2 points per span on x.
+  long long pmax = 0, ptot = 0;
+  for (int t = 0; t < ns; ++t) {
+    const View& v = ops[(size_t)OP_PROJ0 * ns + t].in;
+    const long long np = (long long)v.n[0] * v.n[1] * v.n[2];
+    pmax = std::max(pmax, np);
+    ptot += np;
+  }
+  md->use_fused = (d == 3 && md->prec == MFA_PREC_MIXED && pmax * 2 * 152 <= 3 * ptot / 2);
+  md->x_inplace_ok = true;
+  for (const AxisSub& sb : md->axh[0].subs) {
+    const long long Mi = sb.m, nsi = sb.w1 - sb.w0;
+    for (long long k = 0; k < Mi && md->x_inplace_ok; ++k) {
+      long long sk = Mi == 1 ? 0 : (k * nsi) / (Mi - 1);
+      if (sk > nsi - 1) sk = nsi - 1;
+      const long long cmax = sk - 1;
+      if (cmax >= 0 && 2 * cmax + 1 > k - 1) md->x_inplace_ok = false;
+    }
+  }
   rc = build_batch_tiles(h, md, kContractThreads, kSolveThreads, kExpandThreads);
   if (rc != MFA_OK) {
     md->BL = md->X = md->P = nullptr;

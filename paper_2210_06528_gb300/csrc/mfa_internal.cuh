@@ -58,7 +58,22 @@ struct LayoutDev {
   long long ncp[3];    // n_a (1 for axes >= dim)
   long long M[3];
   AxisDev ax[3];
+  int diag;            // 1: subdomain s uses piece s on every axis with more than one piece (a batch of
+                       // independent fits); 0: the tensor product, s = s0 + S0 (s1 + S1 s2)
 };
+
+// The piece of subdomain s along each axis.
+__host__ __device__ inline void sub_pieces(const LayoutDev& L, int s, int& s0, int& s1, int& s2) {
+  if (L.diag) {
+    s0 = L.S[0] > 1 ? s : 0;
+    s1 = L.S[1] > 1 ? s : 0;
+    s2 = L.S[2] > 1 ? s : 0;
+  } else {
+    s0 = s % L.S[0];
+    s1 = (s / L.S[0]) % L.S[1];
+    s2 = s / (L.S[0] * L.S[1]);
+  }
+}
 
 // A strided 3-D view: element (i0,i1,i2) at off + i0*st[0] + i1*st[1] + i2*st[2].
 struct View {
@@ -145,7 +160,8 @@ void launch_cast(const TIn* in, TOut* out, long long n, cudaStream_t st);
 
 template <typename TQ>
 bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, int maxm1, int maxm2, int maxn0,
-                         int maxn1, bool inplace_ok, const TQ* Q, ff* BL, int* status, cudaStream_t st);
+                         int maxn1, bool inplace_ok, const TQ* Q, ff* BL, int* status, cudaStream_t st,
+                         const AxisOp* inst = nullptr, const int* order = nullptr);
 
 template <typename V, typename TQ, typename TOut, bool RESID>
 bool launch_decode3d(const LayoutDev& L, const V* P, const TQ* Q, TOut* out, double* partials, cudaStream_t st);
