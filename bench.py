@@ -356,15 +356,39 @@ def bench_serve(torch, mfa, n_enc=160, mix=4, seed=1, workers=3, budget=48 << 30
     return out
 
 
+# ---------------------------------------------------------------------------
+# replicas over ranks (one process per GPU, no collective on the data path)
+# ---------------------------------------------------------------------------
+
+def rank_env():
+    """(world, rank, local rank) from the launcher's environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x: float, device="cpu") -> float:
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def run_gb300(args, wl):
     import torch
     import torch.distributed as dist
 
     from paper_2210_06528_gb300 import mfa
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -418,11 +442,8 @@ def run_gb300(args, wl):
     t_ms = e0.elapsed_time(e1) / args.steps
     trace = mfa.trace_table(h.h)
     mfa.mfa_trace_enable(h.h, False)
-    if world > 1:
-        tt = torch.tensor([t_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-    value = world * M / (t_ms * 1e-3)
+    t_ms = max_over_ranks(t_ms, device="cuda")
+    value = job_rate(world, M, t_ms * 1e-3)
 
     # ---- decode throughput (grid decode into a device buffer)
     m = h.encode(q_dev, lay)
@@ -437,7 +458,7 @@ def run_gb300(args, wl):
         m.decode_grid(out)
     d1.record(stream)
     torch.cuda.synchronize()
-    dec_ms = d0.elapsed_time(d1) / args.steps
+    dec_ms = max_over_ranks(d0.elapsed_time(d1) / args.steps, device="cuda")
     ncp = mfa.mfa_num_ctrl(m.m)
     m.free()
     del out
@@ -462,8 +483,8 @@ def run_gb300(args, wl):
         torch.cuda.synchronize()
         ptrace = mfa.trace_table(h.h)
         mfa.mfa_trace_enable(h.h, False)
-        plain_ms = p0.elapsed_time(p1)
-        plain = {"value": world * M / (plain_ms * 1e-3), "unit": "pts/s", "ms_per_step": plain_ms,
+        plain_ms = max_over_ranks(p0.elapsed_time(p1), device="cuda")
+        plain = {"value": job_rate(world, M, plain_ms * 1e-3), "unit": "pts/s", "ms_per_step": plain_ms,
                  "precision": "fp64", "schwarz_iters": prep.iters, "rms_decoded": pres.rms_decoded,
                  "gpu_launches": sum(n for (_, n) in ptrace.values()),
                  "form": "one launch per subdomain and stage; window data re-read every iteration"}
@@ -493,11 +514,8 @@ def run_gb300(args, wl):
         step_e2e()
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        tt = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
-    e2e = {"value": world * M / e2e_s, "unit": "pts/s", "h2d_bytes_per_step": qbytes,
+    e2e_s = max_over_ranks(e2e_s, device="cuda")
+    e2e = {"value": job_rate(world, M, e2e_s), "unit": "pts/s", "h2d_bytes_per_step": qbytes,
            "d2h_bytes_per_step": ncp * 8}
 
     # ---- roofline of the dominant kernel class
@@ -539,7 +557,7 @@ def run_gb300(args, wl):
                        "stop": f"dP_rel <= {wl['tol']:g}", "schwarz_iters": sorted(set(iters_seen)),
                        "l2": "inputs larger than L2" if qbytes > 129e6 else "inputs smaller than L2",
                        "parallelism": f"replicas x{world}"},
-            "decode_pts_per_s": world * M / (dec_ms * 1e-3), "decode_ms": dec_ms,
+            "decode_pts_per_s": job_rate(world, M, dec_ms * 1e-3), "decode_ms": dec_ms,
             "plain_gpu": plain, "vs_plain_gpu": (value / plain["value"]) if plain else None,
             "batched_fits": batched, "serving": serving,
             "roofline": roof, "dominant_kernel": dom[0] if dom else None, "kernels": kernels,
