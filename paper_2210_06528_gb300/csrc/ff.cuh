@@ -64,6 +64,53 @@ __device__ __forceinline__ ff& operator-=(ff& a, ff b) { return a = a - b; }
 // acc += a * b with one rounding of the error terms (product accumulate)
 __device__ __forceinline__ void ff_fma_acc(ff& acc, ff a, ff b) { acc = acc + a * b; }
 
+// ---------------------------------------------------------------------------
+// Paired accumulation on the packed FP32 instructions of sm_100 and later
+// (one instruction issues the same operation on two lanes).  An ff2 holds two
+// independent float-float values, lane x and lane y.  Each lane runs the
+// operation sequence of the scalar compensated accumulation (product with its
+// FMA error, TwoSum of the high words, unnormalised low word) step for step,
+// so the paired sums equal the scalar ones bit for bit.  Subtractions are
+// written as fma(a, -1, b), which rounds exactly like b - a, and the product
+// enters negated (nn = -nh, a table value), so no negation is issued.
+// ---------------------------------------------------------------------------
+struct ff2 {
+  float2 hi, lo;
+};
+
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ ff2 ff2_zero() { return ff2{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+
+// a += p lane-wise, given pn = -p and e = the product's exact error terms
+__device__ __forceinline__ void ff2_acc(ff2& a, float2 pn, float2 e) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 s = __ffma2_rn(pn, m1, a.hi);   // hi + p
+  const float2 bb = __ffma2_rn(a.hi, m1, s);   // s - hi
+  const float2 t = __ffma2_rn(bb, m1, s);      // s - bb
+  const float2 u = __ffma2_rn(t, m1, a.hi);    // hi - (s - bb)
+  const float2 vn = __fadd2_rn(pn, bb);        // -(p - bb)
+  const float2 err = __ffma2_rn(vn, m1, u);    // (hi - (s - bb)) + (p - bb)
+  a.hi = s;
+  a.lo = __fadd2_rn(a.lo, __fadd2_rn(e, err));
+}
+
+// a += (nh + nl) * x lane-wise (x a float per lane), nn = -nh
+__device__ __forceinline__ void ff2_add_f(ff2& a, float2 nh, float2 nn, float2 nl, float2 x) {
+  const float2 pn = __fmul2_rn(nn, x);
+  float2 e = __ffma2_rn(nh, x, pn);
+  e = __ffma2_rn(nl, x, e);
+  ff2_acc(a, pn, e);
+}
+
+// a += (nh + nl) * (xh + xl) lane-wise, nn = -nh
+__device__ __forceinline__ void ff2_add_v(ff2& a, float2 nh, float2 nn, float2 nl, float2 xh, float2 xl) {
+  const float2 pn = __fmul2_rn(nn, xh);
+  float2 e = __ffma2_rn(nh, xh, pn);
+  e = __ffma2_rn(nh, xl, e);
+  e = __ffma2_rn(nl, xh, e);
+  ff2_acc(a, pn, e);
+}
+
 #endif
 
 }  // namespace mfa

@@ -164,9 +164,61 @@ __global__ void k_expand(LayoutDev L, const AxisOp* ops, const T* __restrict__ i
   }
 }
 
+// Accumulation of the residual E = q - value of the fused last decode axis.
+// FP32 data against float-float values stay on the FP32 pipes (the FP64 pipe
+// of this GPU is a small fraction of them): E = (q - hi) - lo, where q - hi is
+// exact once the fit is close (Sterbenz); E^2 is the exact FMA product summed
+// as a float-float, and the warp reduction moves float-floats.  Any FP64
+// operand keeps the FP64 form.
+template <typename T, typename TQ>
+struct ResidAcc {
+  double s2 = 0.0, emax = 0.0, qmin = INFINITY, qmax = -INFINITY;
+  __device__ __forceinline__ void add(TQ q, T v) {
+    const double qv = (double)q;
+    const double e = qv - (double)v;
+    s2 += e * e;
+    emax = fmax(emax, fabs(e));
+    qmin = fmin(qmin, qv);
+    qmax = fmax(qmax, qv);
+  }
+  __device__ __forceinline__ void warp_reduce() {
+    for (int o = 16; o > 0; o >>= 1) {
+      s2 += __shfl_down_sync(0xffffffffu, s2, o);
+      emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, o));
+      qmin = fmin(qmin, __shfl_down_sync(0xffffffffu, qmin, o));
+      qmax = fmax(qmax, __shfl_down_sync(0xffffffffu, qmax, o));
+    }
+  }
+  __device__ __forceinline__ double sum2() const { return s2; }
+};
+
+template <>
+struct ResidAcc<ff, float> {
+  ff s2 = ff(0.f, 0.f);
+  float emax = 0.f, qmin = INFINITY, qmax = -INFINITY;
+  __device__ __forceinline__ void add(float q, ff v) {
+    const float e = __fsub_rn(__fsub_rn(q, v.hi), v.lo);
+    const float p = __fmul_rn(e, e);
+    s2 += ff(p, __fmaf_rn(e, e, -p));
+    emax = fmaxf(emax, fabsf(e));
+    qmin = fminf(qmin, q);
+    qmax = fmaxf(qmax, q);
+  }
+  __device__ __forceinline__ void warp_reduce() {
+    for (int o = 16; o > 0; o >>= 1) {
+      s2 += ff(__shfl_down_sync(0xffffffffu, s2.hi, o), __shfl_down_sync(0xffffffffu, s2.lo, o));
+      emax = fmaxf(emax, __shfl_down_sync(0xffffffffu, emax, o));
+      qmin = fminf(qmin, __shfl_down_sync(0xffffffffu, qmin, o));
+      qmax = fmaxf(qmax, __shfl_down_sync(0xffffffffu, qmax, o));
+    }
+  }
+  __device__ __forceinline__ double sum2() const { return (double)s2.hi + (double)s2.lo; }
+};
+
 // Batches of independent fits: the last decode axis of a group fused with
 // the residual against the data, over a tile map; every tile (one block)
-// writes its sum of E^2 and max |E| (FP64).  Q shares the output views.
+// writes its sum of E^2 and max |E| (ResidAcc, stored as FP64).  Q shares the
+// output views.
 template <typename T, typename TQ, int AXIS>
 __global__ void k_expand_residual_tiles(LayoutDev L, const AxisOp* ops, const T* __restrict__ in,
                                         const TQ* __restrict__ q, TileMap tm, double* __restrict__ tile_part) {
@@ -176,25 +228,20 @@ __global__ void k_expand_residual_tiles(LayoutDev L, const AxisOp* ops, const T*
   tile_of(tm, opi, idx);
   const AxisOp& op = block_op(ops, opi);
   const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
-  double e2 = 0.0, emax = 0.0;
+  ResidAcc<T, TQ> acc;
   if (idx < nout) {
     int o[3];
     unflatten(idx, op.out.n, o);
     const T val = expand_one<T, AXIS>(L.ax[AXIS], op, o, in);
     const View& ov = op.out;
-    const double e = (double)q[ov.off + o[0] * ov.st[0] + o[1] * ov.st[1] + o[2] * ov.st[2]] - (double)val;
-    e2 = e * e;
-    emax = fabs(e);
+    acc.add(q[ov.off + o[0] * ov.st[0] + o[1] * ov.st[1] + o[2] * ov.st[2]], val);
   }
-  for (int sft = 16; sft > 0; sft >>= 1) {
-    e2 += __shfl_down_sync(0xffffffffu, e2, sft);
-    emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, sft));
-  }
+  acc.warp_reduce();
   __shared__ double red[2][32];  // up to 1024 threads
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   if (lane == 0) {
-    red[0][w] = e2;
-    red[1][w] = emax;
+    red[0][w] = acc.sum2();
+    red[1][w] = (double)acc.emax;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -257,7 +304,8 @@ void launch_expand_residual_tiles(const LayoutDev& L, int axis, const AxisOp* op
 }
 
 // Final decode axis fused with the residual E = Q - R P: per-block partial
-// sums of E^2 (FP64), max |E|, min Q and max Q.  Q shares the output layout.
+// sums of E^2, max |E|, min Q and max Q (ResidAcc), written as FP64.  Q shares
+// the output layout.
 template <typename T, typename TQ, int AXIS>
 __global__ void k_expand_residual(LayoutDev L, const AxisOp* opp, const T* __restrict__ in,
                                   const TQ* __restrict__ q, double* partials) {
@@ -265,31 +313,20 @@ __global__ void k_expand_residual(LayoutDev L, const AxisOp* opp, const T* __res
   const AxisOp& op = block_op(opp, 0);
   const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
   const long long stride = (long long)gridDim.x * blockDim.x;
-  double s2 = 0.0, emax = 0.0, qmin = INFINITY, qmax = -INFINITY;
+  ResidAcc<T, TQ> acc;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nout; idx += stride) {
     int o[3];
     unflatten(idx, op.out.n, o);
-    const T val = expand_one<T, AXIS>(L.ax[AXIS], op, o, in);
-    const double qv = (double)q[idx];
-    const double e = qv - (double)val;
-    s2 += e * e;
-    emax = fmax(emax, fabs(e));
-    qmin = fmin(qmin, qv);
-    qmax = fmax(qmax, qv);
+    acc.add(q[idx], expand_one<T, AXIS>(L.ax[AXIS], op, o, in));
   }
   __shared__ double sh[4][32];
-  for (int off = 16; off > 0; off >>= 1) {
-    s2 += __shfl_down_sync(0xffffffffu, s2, off);
-    emax = fmax(emax, __shfl_down_sync(0xffffffffu, emax, off));
-    qmin = fmin(qmin, __shfl_down_sync(0xffffffffu, qmin, off));
-    qmax = fmax(qmax, __shfl_down_sync(0xffffffffu, qmax, off));
-  }
+  acc.warp_reduce();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
-    sh[0][wid] = s2;
-    sh[1][wid] = emax;
-    sh[2][wid] = qmin;
-    sh[3][wid] = qmax;
+    sh[0][wid] = acc.sum2();
+    sh[1][wid] = (double)acc.emax;
+    sh[2][wid] = (double)acc.qmin;
+    sh[3][wid] = (double)acc.qmax;
   }
   __syncthreads();
   if (threadIdx.x == 0) {

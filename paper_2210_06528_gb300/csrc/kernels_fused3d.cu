@@ -95,27 +95,85 @@ struct Proj3dArgs {
 };
 
 // Shared-memory carve-up of the projection, used by the kernel and the launcher.
+// The basis lanes are padded to an even count WP so they pair up.
 struct ProjSmem {
-  size_t t2, txh, txl, tyh, tyl, tzh, tzl, spx, spy, spz, bar, total;
+  size_t t2h, t2l, txh, txn, txl, ty, tz, spx, spy, spz, bar, total;
+  int npp;  // stride of a plane of the stage-2 output (even)
 };
 __host__ __device__ inline ProjSmem proj_smem_layout(int W, int zb, int bx, int by, int mz, int n0, int n1) {
   ProjSmem s;
   auto al = [](size_t o) { return (o + 15) & ~size_t(15); };
+  const int WP = 2 * ((W + 1) / 2);
+  s.npp = (n0 * n1 + 1) & ~1;
   size_t o = (size_t)zb * by * bx * 4;  // staged data at offset 0 (128-byte aligned base)
-  s.t2 = al(o);
-  o = s.t2 + (size_t)zb * n1 * n0 * sizeof(ff);
-  s.txh = al(o);
-  s.txl = s.txh + (size_t)bx * W * 4;
-  s.tyh = s.txl + (size_t)bx * W * 4;
-  s.tyl = s.tyh + (size_t)by * W * 4;
-  s.tzh = s.tyl + (size_t)by * W * 4;
-  s.tzl = s.tzh + (size_t)mz * W * 4;
-  s.spx = s.tzl + (size_t)mz * W * 4;
+  s.t2h = al(o);
+  s.t2l = s.t2h + (size_t)zb * s.npp * 4;
+  s.txh = al(s.t2l + (size_t)zb * s.npp * 4);
+  s.txn = al(s.txh + (size_t)bx * WP * 4);
+  s.txl = al(s.txn + (size_t)bx * WP * 4);
+  s.ty = al(s.txl + (size_t)bx * WP * 4);
+  s.tz = s.ty + (size_t)by * W * 16;
+  s.spx = s.tz + (size_t)mz * W * 16;
   s.spy = s.spx + (size_t)bx * 4;
   s.spz = s.spy + (size_t)by * 4;
   s.bar = al(s.spz + (size_t)mz * 4);
   s.total = s.bar + 16;
   return s;
+}
+
+// NPR pairs of basis lanes of one table row (16-byte aligned when NPR = 2)
+template <int NPR>
+__device__ __forceinline__ void load_pairs(const float* t, float2* v) {
+  if constexpr (NPR == 2) {
+    const float4 a = *reinterpret_cast<const float4*>(t);
+    v[0] = make_float2(a.x, a.y);
+    v[1] = make_float2(a.z, a.w);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NPR; ++k) v[k] = reinterpret_cast<const float2*>(t)[k];
+  }
+}
+
+// Lane r of a window of W float-float accumulators held as pairs.
+template <int R>
+__device__ __forceinline__ ff ff2_lane(const ff2* w) {
+  if constexpr (R & 1)
+    return ff(w[R >> 1].hi.y, w[R >> 1].lo.y);
+  else
+    return ff(w[R >> 1].hi.x, w[R >> 1].lo.x);
+}
+
+// Slide a window of W paired accumulators by one: lane r takes lane r + 1,
+// lane W - 1 (and the padding lane of an odd W) restarts at zero.
+template <int W>
+__device__ __forceinline__ void ff2_shift(ff2* w) {
+  constexpr int NPR = (W + 1) / 2;
+#pragma unroll
+  for (int k = 0; k < NPR; ++k) {
+    w[k].hi.x = w[k].hi.y;
+    w[k].lo.x = w[k].lo.y;
+    if (k + 1 < NPR) {
+      w[k].hi.y = w[k + 1].hi.x;
+      w[k].lo.y = w[k + 1].lo.x;
+    } else {
+      w[k].hi.y = 0.f;
+      w[k].lo.y = 0.f;
+    }
+  }
+  if constexpr (W & 1) {
+    w[NPR - 1].hi.x = 0.f;
+    w[NPR - 1].lo.x = 0.f;
+  }
+}
+
+// Stage-1 output of x-control point c in a staged row: control points pair up
+// in 16-byte groups (hi of 2k, hi of 2k+1, lo of 2k, lo of 2k+1), so stage 2
+// reads two control points' values as ready-made lane pairs.
+__device__ __forceinline__ void emit_x_cp(float* row, int c, ff v) {
+  const ff f = fast_two_sum(v.hi, v.lo);
+  float* b = row + 4 * (c >> 1) + (c & 1);
+  b[0] = f.hi;
+  b[2] = f.lo;
 }
 
 __device__ __forceinline__ void cp_async_f32(float* dst, const float* src) {
@@ -191,6 +249,9 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
                                                          const TQ* __restrict__ Q, ff* __restrict__ BL,
                                                          int* status) {
   constexpr int W = P + 1;
+  constexpr int NPR = (W + 1) / 2, WP = 2 * NPR;  // basis lanes in pairs
+  constexpr int NS = NPAIR / 2;                    // stage-3 slots of two adjacent (x, y) pairs
+  static_assert(NPAIR % 2 == 0, "pairs come in twos");
   extern __shared__ __align__(128) unsigned char smem[];
   const LayoutDev& L = A.L;
   const int s = A.order ? A.order[blockIdx.x] : blockIdx.x;
@@ -215,15 +276,16 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
   const int xa = wx - cx;                // data x of staged position 0 (multiple of 4 for the tensor copy)
   const int nq4 = (cx + m0 + 3) >> 2;    // 16-byte chunks of a row that hold window points
   const ProjSmem lay = proj_smem_layout(W, zb, BX, BY, A.mz, A.n0, A.n1);
+  const int npp = lay.npp;
 
-  float* Qs = reinterpret_cast<float*>(smem);  // [zb][BY][BX]; row t's stage-1 output as ff pairs at its start
-  ff* T2 = reinterpret_cast<ff*>(smem + lay.t2);  // [zb][n1][n0]
-  float* txh = reinterpret_cast<float*>(smem + lay.txh);  // [BX][W] by staged position
-  float* txl = reinterpret_cast<float*>(smem + lay.txl);
-  float* tyh = reinterpret_cast<float*>(smem + lay.tyh);  // [m1][W]
-  float* tyl = reinterpret_cast<float*>(smem + lay.tyl);
-  float* tzh = reinterpret_cast<float*>(smem + lay.tzh);  // [m2][W]
-  float* tzl = reinterpret_cast<float*>(smem + lay.tzl);
+  float* Qs = reinterpret_cast<float*>(smem);  // [zb][BY][BX]; row t's stage-1 output in 16-byte groups at its start
+  float* T2h = reinterpret_cast<float*>(smem + lay.t2h);  // [zb][npp] hi words of the stage-2 output
+  float* T2l = reinterpret_cast<float*>(smem + lay.t2l);  // lo words
+  float* txh = reinterpret_cast<float*>(smem + lay.txh);  // [BX][WP] x basis by staged position: hi
+  float* txn = reinterpret_cast<float*>(smem + lay.txn);  //   -hi
+  float* txl = reinterpret_cast<float*>(smem + lay.txl);  //   lo
+  float4* ty = reinterpret_cast<float4*>(smem + lay.ty);  // [m1][W] {hi, -hi, lo, 0}
+  float4* tz = reinterpret_cast<float4*>(smem + lay.tz);  // [m2][W]
   int* spx = reinterpret_cast<int*>(smem + lay.spx);      // [BX] local span by staged position
   int* spy = reinterpret_cast<int*>(smem + lay.spy);
   int* spz = reinterpret_cast<int*>(smem + lay.spz);
@@ -239,8 +301,9 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
     stage_rows<TQ>(Qs, Q, M0, M01, xa, wy, wz, min(zb, m2), m1, BX, BY);
   }
 
-  // basis tables: x by staged position (zero outside the window, span held
-  // at the nearest window point so no control point is emitted there)
+  // basis tables: x by staged position (zero outside the window and in the
+  // padding lane, span held at the nearest window point so no control point
+  // is emitted there)
   const ff* vx = L.ax[0].vals_ff;
   const ff* vy = L.ax[1].vals_ff;
   const ff* vz = L.ax[2].vals_ff;
@@ -250,10 +313,11 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
     const int kk = min(max(k, 0), m0 - 1);
     spx[i] = L.ax[0].span[bx.k0 + kk] - bx.l0;
 #pragma unroll
-    for (int r = 0; r < W; ++r) {
-      const ff v = in ? vx[(long long)(bx.k0 + k) * W + r] : ff(0.f, 0.f);
-      txh[i * W + r] = v.hi;
-      txl[i * W + r] = v.lo;
+    for (int r = 0; r < WP; ++r) {
+      const ff v = in && r < W ? vx[(long long)(bx.k0 + k) * W + r] : ff(0.f, 0.f);
+      txh[i * WP + r] = v.hi;
+      txn[i * WP + r] = -v.hi;
+      txl[i * WP + r] = v.lo;
     }
   }
   for (int i = threadIdx.x; i < m1; i += NT) {
@@ -262,8 +326,7 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
 #pragma unroll
     for (int r = 0; r < W; ++r) {
       const ff v = vy[(long long)k * W + r];
-      tyh[i * W + r] = v.hi;
-      tyl[i * W + r] = v.lo;
+      ty[i * W + r] = make_float4(v.hi, -v.hi, v.lo, 0.f);
     }
   }
   for (int i = threadIdx.x; i < m2; i += NT) {
@@ -272,22 +335,23 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
 #pragma unroll
     for (int r = 0; r < W; ++r) {
       const ff v = vz[(long long)k * W + r];
-      tzh[i * W + r] = v.hi;
-      tzl[i * W + r] = v.lo;
+      tz[i * W + r] = make_float4(v.hi, -v.hi, v.lo, 0.f);
     }
   }
 
-  ff ring[NPAIR][W];
+  // stage-3 ring: slot j holds the (x, y) pairs q0 = 2 (threadIdx.x + j NT)
+  // (lane x) and q0 + 1 (lane y), entry r the z-control point curz + r
+  ff2 ring[NS][W];
 #pragma unroll
-  for (int i = 0; i < NPAIR; ++i)
+  for (int j = 0; j < NS; ++j)
 #pragma unroll
-    for (int r = 0; r < W; ++r) ring[i][r] = ff(0.f, 0.f);
+    for (int r = 0; r < W; ++r) ring[j][r] = ff2_zero();
   const int npairs = n0 * n1;
   ff* out = BL + A.offL[s];
   bool bad = false;
   unsigned phase = 0;
   __syncthreads();     // tables written, barrier initialised
-  int curz = spz[0];   // z-control point held in ring slot 0
+  int curz = spz[0];   // z-control point held in ring entry 0
 
   for (int z0 = 0; z0 < m2; z0 += zb) {
     const int nz = min(zb, m2 - z0);
@@ -306,14 +370,14 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
       return;
     }
     // ---- stage 1: one staged row per thread, four points per 16-byte read,
-    // sliding window of P+1 accumulators; the output overwrites the consumed
-    // part of the row
+    // sliding window of P+1 accumulators in lane pairs; the output overwrites
+    // the consumed part of the row
     for (int t = threadIdx.x; t < nz * m1; t += NT) {
       const int zz = t / m1, y = t - zz * m1;
       float* row = Qs + (size_t)(zz * BY + y) * BX;
-      ff win[W];
+      ff2 win[NPR];
 #pragma unroll
-      for (int r = 0; r < W; ++r) win[r] = ff(0.f, 0.f);
+      for (int k = 0; k < NPR; ++k) win[k] = ff2_zero();
       int cur = spx[0];
       for (int j = 0; j < nq4; ++j) {
         const float4 q4 = reinterpret_cast<const float4*>(row)[j];
@@ -323,43 +387,37 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
           const int i = 4 * j + u;
           const int sk = spx[i];
           while (cur < sk) {
-            if (cur >= 0 && cur < n0) {
-              const ff v = AccFF::finish(win[0]);
-              *reinterpret_cast<float2*>(row + 2 * cur) = make_float2(v.hi, v.lo);
-            }
-#pragma unroll
-            for (int r = 0; r < P; ++r) win[r] = win[r + 1];
-            win[P] = ff(0.f, 0.f);
+            if (cur >= 0 && cur < n0) emit_x_cp(row, cur, ff2_lane<0>(win));
+            ff2_shift<W>(win);
             ++cur;
           }
-          if constexpr (W == 4) {
-            const float4 nh = reinterpret_cast<const float4*>(txh)[i];
-            const float4 nl = reinterpret_cast<const float4*>(txl)[i];
-            AccFF::add_f(win[0], nh.x, nl.x, qv[u]);
-            AccFF::add_f(win[1], nh.y, nl.y, qv[u]);
-            AccFF::add_f(win[2], nh.z, nl.z, qv[u]);
-            AccFF::add_f(win[3], nh.w, nl.w, qv[u]);
-          } else {
+          float2 nh[NPR], nn[NPR], nl[NPR];
+          load_pairs<NPR>(txh + i * WP, nh);
+          load_pairs<NPR>(txn + i * WP, nn);
+          load_pairs<NPR>(txl + i * WP, nl);
+          const float2 x = dup2(qv[u]);
 #pragma unroll
-            for (int r = 0; r < W; ++r) AccFF::add_f(win[r], txh[i * W + r], txl[i * W + r], qv[u]);
-          }
+          for (int k = 0; k < NPR; ++k) ff2_add_f(win[k], nh[k], nn[k], nl[k], x);
         }
       }
-#pragma unroll
-      for (int r = 0; r < W; ++r)
-        if (cur + r >= 0 && cur + r < n0) {
-          const ff v = AccFF::finish(win[r]);
-          *reinterpret_cast<float2*>(row + 2 * (cur + r)) = make_float2(v.hi, v.lo);
-        }
+      if (cur >= 0 && cur < n0) emit_x_cp(row, cur, ff2_lane<0>(win));
+      if (cur + 1 >= 0 && cur + 1 < n0) emit_x_cp(row, cur + 1, ff2_lane<1>(win));
+      if (cur + 2 >= 0 && cur + 2 < n0) emit_x_cp(row, cur + 2, ff2_lane<2>(win));
+      if constexpr (W > 3)
+        if (cur + 3 >= 0 && cur + 3 < n0) emit_x_cp(row, cur + 3, ff2_lane<3 % W>(win));
+      if constexpr (W > 4)
+        if (cur + 4 >= 0 && cur + 4 < n0) emit_x_cp(row, cur + 4, ff2_lane<4 % W>(win));
+      if constexpr (W > 5)
+        if (cur + 5 >= 0 && cur + 5 < n0) emit_x_cp(row, cur + 5, ff2_lane<5 % W>(win));
     }
     __syncthreads();
     // ---- stage 2 (gather form): one warp-aligned group of lanes per (plane,
-    // y-control point), lanes along x-control points; each output sums its
-    // P+1 supporting spans' rows, so the work per output is even and no row
-    // is read for a control point it does not touch
+    // y-control point), each lane two adjacent x-control points; each output
+    // sums its P+1 supporting spans' rows, so the work per output is even and
+    // no row is read for a control point it does not touch
     {
       const int* ss = L.ax[1].span_start;
-      const int sh = A.lx_shift;                 // lanes per group = 1 << sh >= n0
+      const int sh = A.lx_shift;                 // lanes per group = 1 << sh >= n0 / 2
       const int lmask = (1 << sh) - 1;
       const int lx = threadIdx.x & lmask;
       const int gstep = NT >> sh;                // groups advanced per pass
@@ -369,18 +427,26 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
         ++zz;
       }
       for (; zz < nz; ) {
-        if (lx < n0) {
+        if (2 * lx < n0) {
           const int g1 = by.l0 + c1;
           const int ys = max(ss[max(g1 - P, 0)] - by.k0, 0);
           const int ye = min(ss[min(g1, L.ax[1].nspans - 1) + 1] - by.k0, m1);
-          const float* colf = Qs + (size_t)zz * BY * BX + 2 * lx;
-          ff acc(0.f, 0.f);
+          const float* colf = Qs + (size_t)zz * BY * BX + 4 * lx;
+          ff2 acc = ff2_zero();
           for (int y = ys; y < ye; ++y) {
-            const int r = c1 - spy[y];
-            const float2 xv = *reinterpret_cast<const float2*>(colf + (size_t)y * BX);
-            AccFF::add_v(acc, tyh[y * W + r], tyl[y * W + r], ff(xv.x, xv.y));
+            const float4 nb = ty[y * W + (c1 - spy[y])];
+            const float4 xv = *reinterpret_cast<const float4*>(colf + (size_t)y * BX);
+            ff2_add_v(acc, dup2(nb.x), dup2(nb.y), dup2(nb.z), make_float2(xv.x, xv.y), make_float2(xv.z, xv.w));
           }
-          T2[(zz * n1 + c1) * n0 + lx] = AccFF::finish(acc);
+          const ff v0 = AccFF::finish(ff(acc.hi.x, acc.lo.x));
+          const int o = zz * npp + c1 * n0 + 2 * lx;
+          T2h[o] = v0.hi;
+          T2l[o] = v0.lo;
+          if (2 * lx + 1 < n0) {
+            const ff v1 = AccFF::finish(ff(acc.hi.y, acc.lo.y));
+            T2h[o + 1] = v1.hi;
+            T2l[o + 1] = v1.lo;
+          }
         }
         c1 += gstep;
         while (c1 >= n1) {
@@ -406,47 +472,65 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
       const int sz = spz[kz];
       while (curz < sz) {
 #pragma unroll
-        for (int i = 0; i < NPAIR; ++i) {
-          const int q = threadIdx.x + i * NT;
-          if (q < npairs && curz >= 0 && curz < n2) {
-            const ff v = AccFF::finish(ring[i][0]);
-            bad |= !isfinite(v.hi);
-            out[(long long)curz * npairs + q] = v;
+        for (int j = 0; j < NS; ++j) {
+          const int q0 = 2 * (threadIdx.x + j * NT);
+          if (curz >= 0 && curz < n2) {
+            if (q0 < npairs) {
+              const ff v = AccFF::finish(ff(ring[j][0].hi.x, ring[j][0].lo.x));
+              bad |= !isfinite(v.hi);
+              out[(long long)curz * npairs + q0] = v;
+            }
+            if (q0 + 1 < npairs) {
+              const ff v = AccFF::finish(ff(ring[j][0].hi.y, ring[j][0].lo.y));
+              bad |= !isfinite(v.hi);
+              out[(long long)curz * npairs + q0 + 1] = v;
+            }
           }
 #pragma unroll
-          for (int r = 0; r < P; ++r) ring[i][r] = ring[i][r + 1];
-          ring[i][P] = ff(0.f, 0.f);
+          for (int r = 0; r < P; ++r) ring[j][r] = ring[j][r + 1];
+          ring[j][P] = ff2_zero();
         }
         ++curz;
       }
-      float nzh[W], nzl[W];
+      float2 zh[W], zn[W], zl[W];
 #pragma unroll
       for (int r = 0; r < W; ++r) {
-        nzh[r] = tzh[kz * W + r];
-        nzl[r] = tzl[kz * W + r];
+        const float4 b = tz[kz * W + r];
+        zh[r] = dup2(b.x);
+        zn[r] = dup2(b.y);
+        zl[r] = dup2(b.z);
       }
-      const ff* t2 = T2 + zz * npairs;
+      const float* th = T2h + zz * npp;
+      const float* tl = T2l + zz * npp;
 #pragma unroll
-      for (int i = 0; i < NPAIR; ++i) {
-        const int q = threadIdx.x + i * NT;
-        if (q < npairs) {
-          const ff x = t2[q];
+      for (int j = 0; j < NS; ++j) {
+        const int q0 = 2 * (threadIdx.x + j * NT);
+        if (q0 < npairs) {
+          const float2 xh = *reinterpret_cast<const float2*>(th + q0);
+          const float2 xl = *reinterpret_cast<const float2*>(tl + q0);
 #pragma unroll
-          for (int r = 0; r < W; ++r) AccFF::add_v(ring[i][r], nzh[r], nzl[r], x);
+          for (int r = 0; r < W; ++r) ff2_add_v(ring[j][r], zh[r], zn[r], zl[r], xh, xl);
         }
       }
     }
     // T2 is rewritten by the next batch's stage 2 only after its stage-1 barrier
   }
 #pragma unroll
-  for (int i = 0; i < NPAIR; ++i) {
-    const int q = threadIdx.x + i * NT;
+  for (int j = 0; j < NS; ++j) {
+    const int q0 = 2 * (threadIdx.x + j * NT);
 #pragma unroll
     for (int r = 0; r < W; ++r)
-      if (q < npairs && curz + r >= 0 && curz + r < n2) {
-        const ff v = AccFF::finish(ring[i][r]);
-        bad |= !isfinite(v.hi);
-        out[(long long)(curz + r) * npairs + q] = v;
+      if (curz + r >= 0 && curz + r < n2) {
+        if (q0 < npairs) {
+          const ff v = AccFF::finish(ff(ring[j][r].hi.x, ring[j][r].lo.x));
+          bad |= !isfinite(v.hi);
+          out[(long long)(curz + r) * npairs + q0] = v;
+        }
+        if (q0 + 1 < npairs) {
+          const ff v = AccFF::finish(ff(ring[j][r].hi.y, ring[j][r].lo.y));
+          bad |= !isfinite(v.hi);
+          out[(long long)(curz + r) * npairs + q0 + 1] = v;
+        }
       }
   }
   if (bad && status) atomicExch(status, MFA_ERR_NONFINITE);
@@ -497,14 +581,24 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
   // planes per batch: fill the stage-1 rows onto the threads
   A.zb = std::max(1, std::min(4, kProjThreads / std::max(maxm1, 1)));
   const int W = P + 1;
+  // two CTAs per SM when the batch fits: half the SM's shared memory less the
+  // per-block reservation
+  static size_t two_per_sm = [] {
+    int dev = 0, per_sm = 0, reserved = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    return per_sm > 0 ? (size_t)(per_sm / 2 - reserved) : (size_t)110 * 1024;
+  }();
   size_t smem = proj_smem_layout(W, A.zb, A.bx, A.by, A.mz, A.n0, A.n1).total;
-  while (smem > 110 * 1024 && A.zb > 1) {
+  while (smem > two_per_sm && A.zb > 1) {
     A.zb--;
     smem = proj_smem_layout(W, A.zb, A.bx, A.by, A.mz, A.n0, A.n1).total;
   }
   if (smem > 200 * 1024 || npairs > 8 * kProjThreads) return false;
-  A.lx_shift = 5;
-  while ((1 << A.lx_shift) < maxn0) ++A.lx_shift;
+  // stage 2: a group of 1 << lx_shift lanes covers the x-control points in pairs
+  A.lx_shift = 2;
+  while ((1 << A.lx_shift) < (maxn0 + 1) / 2) ++A.lx_shift;
   if ((1 << A.lx_shift) > kProjThreads) return false;
 
   // the tensor copy takes FP32 data on a 16-byte aligned base with rows a
@@ -780,22 +874,25 @@ __global__ void __launch_bounds__(kDecThreads) k_decode3d(LayoutDev L, const V* 
     }
   }
   if constexpr (RESID) {
-    // block reduction in FP64 (few operations per block) into this tile's slot
-    double ds2 = s2;
-    double demax = emax, dqmin = qmin, dqmax = qmax;
+    // block reduction into this tile's slot.  The extrema are exact in FP32;
+    // the sum of squares crosses the warp as a float-float, so every lane
+    // stays on the FP32 pipes (the FP64 pipe is a small fraction of them and
+    // all warps reach this point together); FP64 only for the 8 warp sums.
+    ff fs2(s2, 0.f);
     for (int o = 16; o > 0; o >>= 1) {
-      ds2 += __shfl_down_sync(0xffffffffu, ds2, o);
-      demax = fmax(demax, __shfl_down_sync(0xffffffffu, demax, o));
-      dqmin = fmin(dqmin, __shfl_down_sync(0xffffffffu, dqmin, o));
-      dqmax = fmax(dqmax, __shfl_down_sync(0xffffffffu, dqmax, o));
+      const ff other(__shfl_down_sync(0xffffffffu, fs2.hi, o), __shfl_down_sync(0xffffffffu, fs2.lo, o));
+      fs2 = fs2 + other;
+      emax = fmaxf(emax, __shfl_down_sync(0xffffffffu, emax, o));
+      qmin = fminf(qmin, __shfl_down_sync(0xffffffffu, qmin, o));
+      qmax = fmaxf(qmax, __shfl_down_sync(0xffffffffu, qmax, o));
     }
     __shared__ double red[4][kDecThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
-      red[0][wid] = ds2;
-      red[1][wid] = demax;
-      red[2][wid] = dqmin;
-      red[3][wid] = dqmax;
+      red[0][wid] = (double)fs2.hi + (double)fs2.lo;
+      red[1][wid] = emax;
+      red[2][wid] = qmin;
+      red[3][wid] = qmax;
     }
     __syncthreads();
     if (threadIdx.x == 0) {

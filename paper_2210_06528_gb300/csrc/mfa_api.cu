@@ -111,6 +111,10 @@ struct DeviceGuard {
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// Highest float of a staged row written by the fused projection's stage-1
+// output of control points 0..c (16-byte groups of two control points).
+inline long long stage1_reach(long long c) { return (c & 1) ? 2 * c + 1 : 2 * c + 2; }
+
 int cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return MFA_OK;
   if (e == cudaErrorMemoryAllocation) return MFA_ERR_OOM;
@@ -1045,8 +1049,10 @@ int create_model(mfa_handle* h, const mfa_layout* lay, bool plain, size_t stage_
   }
   md->nsub = md->axh[0].S * md->axh[1].S * md->axh[2].S;
   {
-    // stage-1 output of control point c (floats 2c, 2c+1) is written while
-    // reading the first point of span c+1; it must trail every unread point
+    // the fused projection's stage-1 output of control point c (floats
+    // 4(c/2) + c%2 and 4(c/2) + c%2 + 2 of the staged row) is written while
+    // the 16-byte chunk holding the first point of span c+1 is in registers;
+    // it must not reach past that chunk
     const AxisHost& ax = md->axh[0];
     for (const AxisSub& sb : ax.subs) {
       for (int k = 0; k < sb.m && md->x_inplace_ok; ++k) {
@@ -1054,7 +1060,7 @@ int create_model(mfa_handle* h, const mfa_layout* lay, bool plain, size_t stage_
         long long sk = ax.M == 1 ? 0 : (gk * ax.nspans) / (ax.M - 1);
         if (sk > ax.nspans - 1) sk = ax.nspans - 1;
         const long long cmax = sk - sb.l0 - 1;  // highest CP emitted before reading point k
-        if (cmax >= 0 && 2 * cmax + 1 > k - 1) md->x_inplace_ok = false;
+        if (cmax >= 0 && stage1_reach(cmax) > 4 * (k / 4) + 3) md->x_inplace_ok = false;
       }
     }
   }
@@ -1834,7 +1840,7 @@ int build_batch_group(mfa_batch* b, int d, int p, const std::vector<int>& mem, m
       long long sk = Mi == 1 ? 0 : (k * nsi) / (Mi - 1);
       if (sk > nsi - 1) sk = nsi - 1;
       const long long cmax = sk - 1;
-      if (cmax >= 0 && 2 * cmax + 1 > k - 1) md->x_inplace_ok = false;
+      if (cmax >= 0 && stage1_reach(cmax) > 4 * (k / 4) + 3) md->x_inplace_ok = false;
     }
   }
   rc = build_batch_tiles(h, md, kContractThreads, kSolveThreads, kExpandThreads);
