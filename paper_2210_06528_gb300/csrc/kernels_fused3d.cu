@@ -868,7 +868,12 @@ __global__ void __launch_bounds__(kDecThreads) k_decode3d(LayoutDev L, const V* 
           qmin = fminf(qmin, q);
           qmax = fmaxf(qmax, q);
         } else {
-          out[g] = (TOut)((double)Val<V>::hi(acc) + (double)Val<V>::lo(acc));
+          // hi + lo is exact in FP64, so a float output is its FP32 rounding
+          // (one FP32 add); a double output takes the exact sum
+          if constexpr (sizeof(TOut) == 4)
+            out[g] = __fadd_rn(Val<V>::hi(acc), Val<V>::lo(acc));
+          else
+            out[g] = (TOut)((double)Val<V>::hi(acc) + (double)Val<V>::lo(acc));
         }
       }
     }
@@ -1344,9 +1349,15 @@ bool launch_schwarz3d_ff(const LayoutDev& L, const long long* offL, const int* m
 // Update (Sec. 2.3.2) in float-float: P^k(g) = (1/n_s) sum of the owned copies
 // of g in a fixed order; metrics max|P^k - P^{k-1}|, max|P^k| and the copy
 // spread are formed from float-float differences, so no FP64 arithmetic runs.
-// A persistent grid walks the rows of control points along x, every copy of
-// a control point loaded independently before they are combined; the small
-// owner and offset tables sit in shared memory.
+// One launch, two kinds of block:
+//   - block s < nsub copies the box of control points that subdomain s owns
+//     alone on every axis (P = its copy): rows of the box stream from the copy
+//     to P, lanes along x, four rows in flight per warp;
+//   - the other blocks take the control points with two owners on some axis,
+//     rows handed out by an atomic counter: rows with two owners along y or z
+//     in full, the other rows at the x positions with two owners.  Every copy
+//     of such a point is loaded independently before they are combined; the
+//     owner and offset tables sit in shared memory.
 // ---------------------------------------------------------------------------
 
 __constant__ float c_inv_hi[9], c_inv_lo[9];  // 1/n as float-float, n = 1..8
@@ -1426,47 +1437,114 @@ __device__ __forceinline__ void avg_finish(const AvgCopies& cp, bool has_prev, l
   }
 }
 
-__global__ void __launch_bounds__(kAvgThreads, 4) k_average_ff(LayoutDev L, const long long* __restrict__ offL,
+// Metrics of one control point with a single copy v (P = v).
+__device__ __forceinline__ void avg_single(ff v, const ff* __restrict__ Pprev, long long g, ff* __restrict__ P,
+                                           float& dmax, float& pmax) {
+  P[g] = v;
+  pmax = fmaxf(pmax, fabsf(v.hi));
+  if (Pprev) {
+    const ff d = v - Pprev[g];
+    dmax = fmaxf(dmax, fabsf(d.hi + d.lo));
+  }
+}
+
+__global__ void __launch_bounds__(kAvgThreads, 3) k_average_ff(LayoutDev L, const long long* __restrict__ offL,
                                                                const ff* __restrict__ X, ff* __restrict__ P,
                                                                const ff* __restrict__ Pprev, float* __restrict__ part,
-                                                               int stage_tables, int rule) {
+                                                               unsigned* __restrict__ row_ctr, int stage_tables,
+                                                               int rule) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int n0 = (int)L.ncp[0], n1 = (int)L.ncp[1], n2 = (int)L.ncp[2];
-  AvgTabs T{L.ax[0].own_tab, L.ax[1].own_tab, L.ax[2].own_tab, L.ax[0].nL_tab, L.ax[1].nL_tab, offL,
-            L.ax[0].own_pick, L.ax[1].own_pick, L.ax[2].own_pick};
-  if (stage_tables) {
-    int4* t0 = reinterpret_cast<int4*>(smem);
-    int4* t1 = t0 + n0;
-    int4* t2 = t1 + n1;
-    long long* off = reinterpret_cast<long long*>(t2 + n2);
-    int* l0 = reinterpret_cast<int*>(off + L.nsub);
-    int* l1 = l0 + L.S[0];
-    int* k0 = l1 + L.S[1];
-    int* k1 = k0 + n0;
-    int* k2 = k1 + n1;
-    for (int i = threadIdx.x; i < n0; i += blockDim.x) t0[i] = T.ot0[i];
-    for (int i = threadIdx.x; i < n1; i += blockDim.x) t1[i] = T.ot1[i];
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) t2[i] = T.ot2[i];
-    for (int i = threadIdx.x; i < L.nsub; i += blockDim.x) off[i] = offL[i];
-    for (int i = threadIdx.x; i < L.S[0]; i += blockDim.x) l0[i] = T.nl0[i];
-    for (int i = threadIdx.x; i < L.S[1]; i += blockDim.x) l1[i] = T.nl1[i];
-    for (int i = threadIdx.x; i < n0; i += blockDim.x) k0[i] = T.pk0[i];
-    for (int i = threadIdx.x; i < n1; i += blockDim.x) k1[i] = T.pk1[i];
-    for (int i = threadIdx.x; i < n2; i += blockDim.x) k2[i] = T.pk2[i];
-    __syncthreads();
-    T = AvgTabs{t0, t1, t2, l0, l1, off, k0, k1, k2};
-  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   float dmax = 0.f, pmax = 0.f, spread = 0.f;
-  const long long nrows = (long long)n1 * n2;
-  for (long long r = blockIdx.x; r < nrows; r += gridDim.x) {
-    const int g1 = (int)(r % n1), g2 = (int)(r / n1);
-    const int4 o1 = T.ot1[g1], o2 = T.ot2[g2];
-    for (int g0 = threadIdx.x; g0 < n0; g0 += blockDim.x) {
-      const long long g = (long long)g0 + (long long)n0 * r;
-      AvgCopies cp;
-      avg_load(L, T, X, Pprev, g, T.ot0[g0], o1, o2, cp);
-      const int slot = rule == UPDATE_OWNER ? T.pk0[g0] + 2 * T.pk1[g1] + 4 * T.pk2[g2] : -1;
-      avg_finish(cp, Pprev != nullptr, g, P, dmax, pmax, spread, slot);
+  if ((int)blockIdx.x < L.nsub) {
+    // ---- the single-owner box of subdomain s
+    const int s = blockIdx.x;
+    int s0, s1, s2;
+    sub_pieces(L, s, s0, s1, s2);
+    const int2 r0 = L.ax[0].one_rng[s0], r1 = L.ax[1].one_rng[s1], r2 = L.ax[2].one_rng[s2];
+    const AxisSub b0 = L.ax[0].subs[s0], b1 = L.ax[1].subs[s1], b2 = L.ax[2].subs[s2];
+    const int nx = r0.y - r0.x, ny = r1.y - r1.x, nrows = ny * (r2.y - r2.x);
+    const ff* xs = X + offL[s] + (r0.x - b0.l0);
+    ff* ps = P + r0.x;
+    const ff* qs = Pprev ? Pprev + r0.x : nullptr;
+    const int nw = blockDim.x >> 5;
+    for (int rb = wid; rb < nrows; rb += 4 * nw) {
+      long long xo[4], po[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int r = min(rb + u * nw, nrows - 1);
+        const int y = r % ny, z = r / ny;
+        xo[u] = (long long)b0.nL * ((r1.x + y - b1.l0) + (long long)b1.nL * (r2.x + z - b2.l0));
+        po[u] = (long long)n0 * ((r1.x + y) + (long long)n1 * (r2.x + z));
+      }
+      for (int x = lane; x < nx; x += 32) {
+        ff v[4], q[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          v[u] = xs[xo[u] + x];
+          q[u] = qs ? qs[po[u] + x] : ff(0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (rb + u * nw >= nrows) continue;
+          ps[po[u] + x] = v[u];
+          pmax = fmaxf(pmax, fabsf(v[u].hi));
+          if (qs) {
+            const ff d = v[u] - q[u];
+            dmax = fmaxf(dmax, fabsf(d.hi + d.lo));
+          }
+        }
+      }
+    }
+  } else {
+    // ---- control points with two owners on some axis
+    AvgTabs T{L.ax[0].own_tab, L.ax[1].own_tab, L.ax[2].own_tab, L.ax[0].nL_tab, L.ax[1].nL_tab, offL,
+              L.ax[0].own_pick, L.ax[1].own_pick, L.ax[2].own_pick};
+    if (stage_tables) {
+      int4* t0 = reinterpret_cast<int4*>(smem);
+      int4* t1 = t0 + n0;
+      int4* t2 = t1 + n1;
+      long long* off = reinterpret_cast<long long*>(t2 + n2);
+      int* l0 = reinterpret_cast<int*>(off + L.nsub);
+      int* l1 = l0 + L.S[0];
+      int* k0 = l1 + L.S[1];
+      int* k1 = k0 + n0;
+      int* k2 = k1 + n1;
+      for (int i = threadIdx.x; i < n0; i += blockDim.x) t0[i] = T.ot0[i];
+      for (int i = threadIdx.x; i < n1; i += blockDim.x) t1[i] = T.ot1[i];
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) t2[i] = T.ot2[i];
+      for (int i = threadIdx.x; i < L.nsub; i += blockDim.x) off[i] = offL[i];
+      for (int i = threadIdx.x; i < L.S[0]; i += blockDim.x) l0[i] = T.nl0[i];
+      for (int i = threadIdx.x; i < L.S[1]; i += blockDim.x) l1[i] = T.nl1[i];
+      for (int i = threadIdx.x; i < n0; i += blockDim.x) k0[i] = T.pk0[i];
+      for (int i = threadIdx.x; i < n1; i += blockDim.x) k1[i] = T.pk1[i];
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) k2[i] = T.pk2[i];
+      __syncthreads();
+      T = AvgTabs{t0, t1, t2, l0, l1, off, k0, k1, k2};
+    }
+    const int nrows = L.n_full_rows + L.n_part_rows;
+    constexpr int kChunk = 2;  // rows per grab
+    for (;;) {
+      unsigned base = 0;
+      if (lane == 0) base = atomicAdd(row_ctr, kChunk);
+      base = __shfl_sync(0xffffffffu, base, 0);
+      if ((int)base >= nrows) break;
+      for (int k = (int)base; k < min((int)base + kChunk, nrows); ++k) {
+        const int r = L.shared_rows[k];
+        const int g1 = r % n1, g2 = r / n1;
+        const int4 o1 = T.ot1[g1], o2 = T.ot2[g2];
+        const bool full = k < L.n_full_rows;
+        const int cnt = full ? n0 : L.n_shared_x;
+        for (int j = lane; j < cnt; j += 32) {
+          const int g0 = full ? j : L.shared_x[j];
+          const long long g = (long long)g0 + (long long)n0 * r;
+          AvgCopies cp;
+          avg_load(L, T, X, Pprev, g, T.ot0[g0], o1, o2, cp);
+          const int slot = rule == UPDATE_OWNER ? T.pk0[g0] + 2 * T.pk1[g1] + 4 * T.pk2[g2] : -1;
+          avg_finish(cp, Pprev != nullptr, g, P, dmax, pmax, spread, slot);
+        }
+      }
     }
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -1475,7 +1553,6 @@ __global__ void __launch_bounds__(kAvgThreads, 4) k_average_ff(LayoutDev L, cons
     spread = fmaxf(spread, __shfl_down_sync(0xffffffffu, spread, o));
   }
   __shared__ float red[3][kAvgThreads / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     red[0][wid] = dmax;
     red[1][wid] = pmax;
@@ -1533,9 +1610,10 @@ __global__ void k_metrics_reduce(const float* __restrict__ part, long long nblk,
   }
 }
 
-long long average_ff_blocks(const LayoutDev&) { return kAvgBlocks; }
+long long average_ff_blocks(const LayoutDev& L) { return L.nsub + kAvgListBlocks; }
 
-// `part` holds 3 floats per block of the launch (average_ff_blocks).
+// `part` holds 3 floats per block of the launch (average_ff_blocks) and, after
+// them, the row counter of the shared control points.
 void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev, float* part,
                        unsigned long long* metrics, cudaStream_t st, int rule) {
   static bool init[64] = {};  // reciprocal table in constant memory, set once per device
@@ -1552,11 +1630,14 @@ void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, f
     cudaMemcpyToSymbol(c_inv_lo, l, sizeof(l));
     init[dev] = true;
   }
-  const int threads = (int)std::min<long long>(kAvgThreads, ((L.ncp[0] + 31) / 32) * 32);
   const size_t tab = (size_t)(L.ncp[0] + L.ncp[1] + L.ncp[2]) * (sizeof(int4) + sizeof(int)) +
                      (size_t)L.nsub * sizeof(long long) + (size_t)(L.S[0] + L.S[1]) * sizeof(int);
   const int stage = tab <= 40 * 1024;
-  k_average_ff<<<kAvgBlocks, threads, stage ? tab : 0, st>>>(L, offL, X, P, Pprev, part, stage, rule);
+  const long long nblk = average_ff_blocks(L);
+  unsigned* row_ctr = reinterpret_cast<unsigned*>(part + 3 * nblk);
+  cudaMemsetAsync(row_ctr, 0, sizeof(unsigned), st);
+  k_average_ff<<<(unsigned)nblk, kAvgThreads, stage ? tab : 0, st>>>(L, offL, X, P, Pprev, part, row_ctr, stage,
+                                                                      rule);
   cudaMemsetAsync(metrics, 0, 3 * sizeof(unsigned long long), st);
   k_metrics_reduce<<<152, 256, 0, st>>>(part, average_ff_blocks(L), metrics);
 }

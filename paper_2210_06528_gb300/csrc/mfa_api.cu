@@ -336,6 +336,21 @@ int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int
   }
   ax.nL_tab.resize(nsub);
   for (int s = 0; s < nsub; ++s) ax.nL_tab[s] = ax.subs[s].nL;
+  // control points owned by one piece alone: contiguous, since the U boxes of
+  // neighbouring pieces overlap only at their ends
+  ax.one_rng.assign(nsub, int2{0, 0});
+  for (int s = 0; s < nsub; ++s) {
+    int lo = -1, hi = -1;
+    for (int g = ax.subs[s].a; g < ax.subs[s].b + p; ++g)
+      if (ax.own_count[g] == 1) {
+        if (lo < 0) lo = g;
+        hi = g + 1;
+      }
+    if (lo < 0) continue;
+    for (int g = lo; g < hi; ++g)
+      if (ax.own_count[g] != 1 || ax.own_first[g] != s) return MFA_ERR_LAYOUT;
+    ax.one_rng[s] = int2{lo, hi};
+  }
   // owner-takes update: the owner of control point g is the subdomain whose
   // core holds its Greville abscissa xi_g = (t_{g+1} + ... + t_{g+p}) / p;
   // with t_i = c_i / nspans, xi_g * nspans * p = sum of the c_i, exact
@@ -852,7 +867,7 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
   // ---- device tables in one arena
   Arena ar;
   size_t o_span[3], o_vd[3], o_vf[3], o_vff[3], o_ss[3], o_subs[3], o_of[3], o_oc[3], o_AL[3], o_fLd[3], o_fLf[3],
-      o_fLff[3], o_fUd[3], o_fUf[3], o_fUff[3], o_ot[3], o_nlt[3], o_pk[3];
+      o_fLff[3], o_fUd[3], o_fUf[3], o_fUff[3], o_ot[3], o_nlt[3], o_pk[3], o_one[3];
   for (int a = 0; a < 3; ++a) {
     const AxisHost& ax = md->axh[a];
     const int w = ax.p + 1;
@@ -867,6 +882,7 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
     o_ot[a] = ar.take<int4>(ax.n);
     o_nlt[a] = ar.take<int>(ax.S);
     o_pk[a] = ar.take<int>(ax.n);
+    o_one[a] = ar.take<int2>(ax.S);
     o_AL[a] = ar.take<double>((size_t)ax.bandL_rows * w);
     o_fLd[a] = ar.take<double>((size_t)ax.bandL_rows * w);
     o_fLf[a] = ar.take<float>((size_t)ax.bandL_rows * w);
@@ -877,6 +893,24 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
   }
   const size_t o_offL = ar.take<long long>(ns), o_offS1 = ar.take<long long>(ns), o_offS2 = ar.take<long long>(ns);
   const size_t o_ops = ar.take<AxisOp>(ops.size());
+  // rows of control points with two owners on some axis (float-float update):
+  // rows with two owners along y or z first, then the rest with the x
+  // positions that have two owners
+  std::vector<int> rows_full, rows_part, xs;
+  if (!md->batch) {  // axes beyond the dimension have one control point with one owner
+    const AxisHost &a0 = md->axh[0], &a1 = md->axh[1], &a2 = md->axh[2];
+    for (int g0 = 0; g0 < a0.n; ++g0)
+      if (a0.own_count[g0] == 2) xs.push_back(g0);
+    for (int g2 = 0; g2 < a2.n; ++g2)
+      for (int g1 = 0; g1 < a1.n; ++g1) {
+        const int r = g1 + a1.n * g2;
+        if (a1.own_count[g1] == 2 || a2.own_count[g2] == 2)
+          rows_full.push_back(r);
+        else if (!xs.empty())
+          rows_part.push_back(r);
+      }
+  }
+  const size_t o_rows = ar.take<int>(rows_full.size() + rows_part.size()), o_xs = ar.take<int>(xs.size());
   const size_t tables_bytes = ar.used;
   // host staging image of the uploaded tables
   std::vector<char> img(tables_bytes, 0);
@@ -889,7 +923,11 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
     std::memcpy(img.data() + o_ot[a], ax.own_tab.data(), sizeof(int4) * ax.n);
     std::memcpy(img.data() + o_nlt[a], ax.nL_tab.data(), sizeof(int) * ax.S);
     std::memcpy(img.data() + o_pk[a], ax.own_pick.data(), sizeof(int) * ax.n);
+    std::memcpy(img.data() + o_one[a], ax.one_rng.data(), sizeof(int2) * ax.S);
   }
+  std::memcpy(img.data() + o_rows, rows_full.data(), sizeof(int) * rows_full.size());
+  std::memcpy(img.data() + o_rows + sizeof(int) * rows_full.size(), rows_part.data(), sizeof(int) * rows_part.size());
+  std::memcpy(img.data() + o_xs, xs.data(), sizeof(int) * xs.size());
   std::memcpy(img.data() + o_offL, offL.data(), sizeof(long long) * ns);
   std::memcpy(img.data() + o_offS1, offS1.data(), sizeof(long long) * ns);
   std::memcpy(img.data() + o_offS2, offS2.data(), sizeof(long long) * ns);
@@ -903,7 +941,9 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
   const long long ncp = md->batch ? 0 : (long long)md->axh[0].n * md->axh[1].n * md->axh[2].n;
   const size_t o_P = bg.take<char>(ncp * es), o_Pp = bg.take<char>(ncp * es);
   const size_t o_S1 = bg.take<char>(md->sizeS1 * es), o_S2 = bg.take<char>(md->sizeS2 * es);
-  const size_t o_part = bg.take<float>(3 * (size_t)kAvgBlocks);
+  // update partials (3 floats per block of the float-float update) and its
+  // row counter
+  const size_t o_part = bg.take<float>(3 * (size_t)(ns + kAvgListBlocks) + 1);
   // host data staging: the data are copied into the pool before use
   *o_stage = stage_bytes ? bg.take<char>(stage_bytes) : 0;
   int rc = pool_alloc(h, &md->arena, tables_bytes);
@@ -943,6 +983,7 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
     d.own_tab = at_off<int4>(md->arena, o_ot[a]);
     d.nL_tab = at_off<int>(md->arena, o_nlt[a]);
     d.own_pick = at_off<int>(md->arena, o_pk[a]);
+    d.one_rng = at_off<int2>(md->arena, o_one[a]);
     d.AL = at_off<double>(md->arena, o_AL[a]);
     d.facL_d = at_off<double>(md->arena, o_fLd[a]);
     d.facL_f = at_off<float>(md->arena, o_fLf[a]);
@@ -951,6 +992,11 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
     d.facU_f = at_off<float>(md->arena, o_fUf[a]);
     d.facU_ff = at_off<ff>(md->arena, o_fUff[a]);
   }
+  L.shared_rows = at_off<int>(md->arena, o_rows);
+  L.n_full_rows = (int)rows_full.size();
+  L.n_part_rows = (int)rows_part.size();
+  L.shared_x = at_off<int>(md->arena, o_xs);
+  L.n_shared_x = (int)xs.size();
   md->offL = at_off<long long>(md->arena, o_offL);
   md->offS1 = at_off<long long>(md->arena, o_offS1);
   md->offS2 = at_off<long long>(md->arena, o_offS2);
@@ -1706,9 +1752,11 @@ int build_batch_group(mfa_batch* b, int d, int p, const std::vector<int>& mem, m
     ax.own_pick.assign(ax.n, 0);
     ax.own_tab.assign(ax.n, int4{0, 0, -1, 0});
     ax.nL_tab.resize(ns);
+    ax.one_rng.assign(ns, int2{0, 0});
     for (int t = 0; t < ns; ++t) {
       const AxisSub& sb = ax.subs[t];
       ax.nL_tab[t] = sb.nL;
+      ax.one_rng[t] = int2{sb.l0, sb.l0 + sb.nL};
       for (int l = 0; l < sb.nL; ++l) {
         ax.own_first[sb.l0 + l] = t;
         ax.own_tab[sb.l0 + l] = int4{t, l, -1, 0};

@@ -42,6 +42,7 @@ struct AxisDev {
   const int4* own_tab;      // [n] {first owner, g - l0 in it, second owner or -1, g - l0 in it}
   const int* own_pick;      // [n] 0 or 1: which owner holds the Greville abscissa (owner-takes update)
   const int* nL_tab;        // [S] L size of every piece
+  const int2* one_rng;      // [S] control points owned by piece i alone: [x, y) (contiguous)
   const double* AL;         // Gram band rows of every piece, upper storage: A(i, i+e) at [i*(p+1)+e]
   const double* facL_d;     // Cholesky band of A_L: [i*(p+1)] = 1/L(i,i), [i*(p+1)+e] = L(i,i-e)
   const float* facL_f;
@@ -60,6 +61,13 @@ struct LayoutDev {
   AxisDev ax[3];
   int diag;            // 1: subdomain s uses piece s on every axis with more than one piece (a batch of
                        // independent fits); 0: the tensor product, s = s0 + S0 (s1 + S1 s2)
+  // control points with two owners on some axis, by rows along x (row
+  // r = g1 + n1 g2): `shared_rows` lists first the rows with two owners along
+  // y or z (every x), then the others (only the x positions `shared_x`)
+  const int* shared_rows;
+  int n_full_rows, n_part_rows;
+  const int* shared_x;
+  int n_shared_x;
 };
 
 // The piece of subdomain s along each axis.
@@ -98,6 +106,7 @@ struct AxisHost {
   int pieces = 0;
   std::vector<AxisSub> subs;
   std::vector<int> own_first, own_count, span_start, nL_tab, own_pick;
+  std::vector<int2> one_rng;  // per piece: control points owned by it alone, [x, y)
   std::vector<int4> own_tab;
   int bandL_rows = 0, bandU_rows = 0;
 };
@@ -194,6 +203,6 @@ void launch_decode_points_inst(const InstDesc* desc, const int* qinst, const lon
 constexpr int kResidualBlocks = 1216;  // 8 x 152 SMs
 // block sizes of the generic kernels (tile sizes of their TileMaps)
 constexpr int kContractThreads = 128, kExpandThreads = 256, kSolveThreads = 64;
-constexpr int kAvgBlocks = 152 * 4;     // persistent float-float update: four CTAs per SM
+constexpr int kAvgListBlocks = 152 * 3;  // float-float update: blocks on the shared control points (3 per SM)
 
 }  // namespace mfa
