@@ -660,50 +660,55 @@ template bool launch_project3d_ff<double>(const LayoutDev&, const long long*, in
 namespace mfa {
 
 // ---------------------------------------------------------------------------
-// value policies shared by the fused decode: V = ff (compensated) or float
-// ---------------------------------------------------------------------------
-
-template <typename V>
-struct Val;
-
-template <>
-struct Val<ff> {
-  __device__ __forceinline__ static ff zero() { return ff(0.f, 0.f); }
-  __device__ __forceinline__ static void add(ff& acc, float nh, float nl, ff x) { AccFF::add_v(acc, nh, nl, x); }
-  __device__ __forceinline__ static ff finish(ff a) { return AccFF::finish(a); }
-  __device__ __forceinline__ static float hi(ff a) { return a.hi; }
-  __device__ __forceinline__ static float lo(ff a) { return a.lo; }
-  __device__ __forceinline__ static const ff* vals(const AxisDev& ax) { return ax.vals_ff; }
-};
-
-template <>
-struct Val<float> {
-  __device__ __forceinline__ static float zero() { return 0.f; }
-  __device__ __forceinline__ static void add(float& acc, float nh, float, float x) { acc = fmaf(nh, x, acc); }
-  __device__ __forceinline__ static float finish(float a) { return a; }
-  __device__ __forceinline__ static float hi(float a) { return a; }
-  __device__ __forceinline__ static float lo(float) { return 0.f; }
-  __device__ __forceinline__ static const ff* vals(const AxisDev& ax) { return ax.vals_ff; }
-};
-
-// ---------------------------------------------------------------------------
 // Grid decode R P (Algorithm 1 error step) on tiles of TX x TY x TZ points,
 // fused with either the residual E = Q - R P (per-CTA partial sums of E^2,
 // max |E|, min Q, max Q) or a write of the decoded values.
 //
 // Per tile: load the (spans + P) control-point block, expand along z, then y,
-// then x; every output sums P+1 basis products with the basis held as hi/lo
-// floats (float-float sums for V = ff).
+// then x; every output sums P+1 float-float basis products.  The sums run on
+// the paired FP32 instructions (ff2), two outputs per thread, with shared
+// memory laid out so that each stage reads its lane pairs directly:
+//   z: outputs at x-control points (2k, 2k+1); block hi and lo words apart;
+//   y: outputs at rows y and y + TY/2 (gathered from the z stage);
+//   x: the two rows of the y stage, stored as {hi y, hi y', lo y, lo y'}.
 // ---------------------------------------------------------------------------
 
 constexpr int kDecTX = 64, kDecTY = 8, kDecTZ = 8, kDecThreads = 256;
+constexpr int kDecYH = kDecTY / 2;  // y rows pair as (y, y + kDecYH)
+static_assert(kDecThreads / 32 == kDecTZ, "one warp per plane in the z expansion");
+static_assert(kDecThreads == kDecTX * kDecYH, "x expansion: one thread per (x, row pair)");
+
+// Shared-memory carve-up of the decode (floats): block hi/lo [ncz][ncy][ncxp],
+// z stage hi/lo [TZ][ncy][ncxp], y stage float4 [TZ][TY/2][ncx], then the
+// basis tables (hi, lo) and local spans of the tile's points.
+struct DecSmem {
+  size_t pbh, pbl, tzh, tzl, ty, tab, total;
+};
+__host__ __device__ inline DecSmem dec_smem_layout(int W, int ncx, int ncy, int ncz) {
+  DecSmem d;
+  const int ncxp = (ncx + 1) & ~1;
+  const size_t blk = (size_t)ncz * ncy * ncxp * 4, tz = (size_t)kDecTZ * ncy * ncxp * 4;
+  d.pbh = 0;
+  d.pbl = d.pbh + blk;
+  d.tzh = d.pbl + blk;
+  d.tzl = d.tzh + tz;
+  d.ty = (d.tzl + tz + 15) & ~size_t(15);
+  d.tab = d.ty + (size_t)kDecTZ * kDecYH * ncx * 16;
+  d.total = d.tab + (size_t)(2 * W + 1) * (kDecTX + kDecTY + kDecTZ) * 4;
+  return d;
+}
+
+// a / d for 0 <= a < 2^22 and a divisor d > 0 given as rcp = 1/d: (a + 1/2) / d
+// lies at least 1/(2d) from an integer, far beyond the product's rounding
+__device__ __forceinline__ int div_small(int a, float rcp) { return (int)(((float)a + 0.5f) * rcp); }
 
 template <int P, typename V, typename TQ, typename TOut, bool RESID>
-__global__ void __launch_bounds__(kDecThreads) k_decode3d(LayoutDev L, const V* __restrict__ Pc,
-                                                          const TQ* __restrict__ Q, TOut* __restrict__ out,
-                                                          double* __restrict__ partials) {
+__global__ void __launch_bounds__(kDecThreads, (P >= 4 ? 3 : 4)) k_decode3d(LayoutDev L, const V* __restrict__ Pc,
+                                                                            const TQ* __restrict__ Q,
+                                                                            TOut* __restrict__ out,
+                                                                            double* __restrict__ partials) {
+  static_assert(sizeof(V) == sizeof(ff), "float-float control points");
   constexpr int W = P + 1;
-  constexpr int CX = (kDecTX * 1) + P + 1;  // generous bound on control points per tile row
   extern __shared__ __align__(128) unsigned char smem[];
   const int ntx = (int)((L.M[0] + kDecTX - 1) / kDecTX), nty = (int)((L.M[1] + kDecTY - 1) / kDecTY);
   const int tile = blockIdx.x;
@@ -714,30 +719,24 @@ __global__ void __launch_bounds__(kDecThreads) k_decode3d(LayoutDev L, const V* 
   const AxisDev &ax = L.ax[0], &ay = L.ax[1], &az = L.ax[2];
   const int cx0 = ax.span[x0], cy0 = ay.span[y0], cz0 = az.span[z0];
   const int ncx = ax.span[x1 - 1] + W - cx0, ncy = ay.span[y1 - 1] + W - cy0, ncz = az.span[z1 - 1] + W - cz0;
-  (void)CX;
-
-  // shared: basis of the tile's points (hi/lo), local spans, control block,
-  // z-expanded and y-expanded blocks
-  float* nxh = reinterpret_cast<float*>(smem);  // [TX][W]
+  const int ncxp = (ncx + 1) & ~1;
+  const DecSmem lay = dec_smem_layout(W, ncx, ncy, ncz);
+  float* Pbh = reinterpret_cast<float*>(smem + lay.pbh);
+  float* Pbl = reinterpret_cast<float*>(smem + lay.pbl);
+  float* Tzh = reinterpret_cast<float*>(smem + lay.tzh);
+  float* Tzl = reinterpret_cast<float*>(smem + lay.tzl);
+  float4* Ty = reinterpret_cast<float4*>(smem + lay.ty);
+  float* nxh = reinterpret_cast<float*>(smem + lay.tab);  // [TX][W]
   float* nxl = nxh + kDecTX * W;
-  float* nyh = nxl + kDecTX * W;                // [TY][W]
+  float* nyh = nxl + kDecTX * W;                          // [TY][W]
   float* nyl = nyh + kDecTY * W;
-  float* nzh = nyl + kDecTY * W;                // [TZ][W]
+  float* nzh = nyl + kDecTY * W;                          // [TZ][W]
   float* nzl = nzh + kDecTZ * W;
-  int* sx = reinterpret_cast<int*>(nzl + kDecTZ * W);
+  int* sx = reinterpret_cast<int*>(nzl + kDecTZ * W);     // local spans
   int* sy = sx + kDecTX;
   int* sz = sy + kDecTY;
-  size_t off = (size_t)(2 * W * (kDecTX + kDecTY + kDecTZ)) * 4 + (size_t)(kDecTX + kDecTY + kDecTZ) * 4;
-  off = (off + 15) & ~size_t(15);
-  V* Pb = reinterpret_cast<V*>(smem + off);  // [ncz][ncy][ncx]
-  off += (size_t)ncz * ncy * ncx * sizeof(V);
-  V* Tz = reinterpret_cast<V*>(smem + off);  // [nz][ncy][ncx]
-  off += (size_t)kDecTZ * ncy * ncx * sizeof(V);
-  V* Ty = reinterpret_cast<V*>(smem + off);  // [nz][ny][ncx]
+  const ff* Pf = reinterpret_cast<const ff*>(Pc);
 
-  const ff* vx = ax.vals_ff;
-  const ff* vy = ay.vals_ff;
-  const ff* vz = az.vals_ff;
   if constexpr (RESID) {
     // bring the tile's data rows into L2 now; they are read after the z and
     // y expansions (one 128-byte line per thread: rows of up to 64 floats)
@@ -753,129 +752,184 @@ __global__ void __launch_bounds__(kDecThreads) k_decode3d(LayoutDev L, const V* 
       }
     }
   }
-  for (int i = threadIdx.x; i < nx * W; i += kDecThreads) {
+  // basis tables of the tile's points, zero (span 0) past the grid's end
+  for (int i = threadIdx.x; i < kDecTX * W; i += kDecThreads) {
     const int k = i / W, r = i - k * W;
-    const ff v = vx[(long long)(x0 + k) * W + r];
-    nxh[k * W + r] = v.hi;
-    nxl[k * W + r] = v.lo;
-    if (r == 0) sx[k] = ax.span[x0 + k] - cx0;
+    const ff v = k < nx ? ax.vals_ff[(long long)(x0 + k) * W + r] : ff(0.f, 0.f);
+    nxh[i] = v.hi;
+    nxl[i] = v.lo;
+    if (r == 0) sx[k] = k < nx ? ax.span[x0 + k] - cx0 : 0;
   }
-  for (int i = threadIdx.x; i < ny * W; i += kDecThreads) {
+  for (int i = threadIdx.x; i < kDecTY * W; i += kDecThreads) {
     const int k = i / W, r = i - k * W;
-    const ff v = vy[(long long)(y0 + k) * W + r];
-    nyh[k * W + r] = v.hi;
-    nyl[k * W + r] = v.lo;
-    if (r == 0) sy[k] = ay.span[y0 + k] - cy0;
+    const ff v = k < ny ? ay.vals_ff[(long long)(y0 + k) * W + r] : ff(0.f, 0.f);
+    nyh[i] = v.hi;
+    nyl[i] = v.lo;
+    if (r == 0) sy[k] = k < ny ? ay.span[y0 + k] - cy0 : 0;
   }
-  for (int i = threadIdx.x; i < nz * W; i += kDecThreads) {
+  for (int i = threadIdx.x; i < kDecTZ * W; i += kDecThreads) {
     const int k = i / W, r = i - k * W;
-    const ff v = vz[(long long)(z0 + k) * W + r];
-    nzh[k * W + r] = v.hi;
-    nzl[k * W + r] = v.lo;
-    if (r == 0) sz[k] = az.span[z0 + k] - cz0;
+    const ff v = k < nz ? az.vals_ff[(long long)(z0 + k) * W + r] : ff(0.f, 0.f);
+    nzh[i] = v.hi;
+    nzl[i] = v.lo;
+    if (r == 0) sz[k] = k < nz ? az.span[z0 + k] - cz0 : 0;
   }
-  // control-point block: lanes along x, warps over (z, y) rows of the block
+  // control-point block, hi and lo words apart: lanes along x, warps over
+  // (z, y) rows of the block
   const long long n0 = L.ncp[0], n01 = L.ncp[0] * L.ncp[1];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;  // 8 groups of 32
   for (int row = grp; row < ncz * ncy; row += kDecThreads / 32) {
     const int cz = row / ncy, cy = row - cz * ncy;
-    const V* src = Pc + (long long)cx0 + n0 * (cy0 + cy) + n01 * (cz0 + cz);
-    for (int cx = lane; cx < ncx; cx += 32) Pb[row * ncx + cx] = src[cx];
+    const ff* src = Pf + (long long)cx0 + n0 * (cy0 + cy) + n01 * (cz0 + cz);
+    for (int cx = lane; cx < ncxp; cx += 32) {
+      const ff v = cx < ncx ? src[cx] : ff(0.f, 0.f);
+      Pbh[row * ncxp + cx] = v.hi;
+      Pbl[row * ncxp + cx] = v.lo;
+    }
   }
   __syncthreads();
-  // z expansion: Tz[z][cy][cx]; lanes along cx, groups over cy, loop over z
-  for (int cy = grp; cy < ncy; cy += kDecThreads / 32) {
-    for (int cx = lane; cx < ncx; cx += 32) {
-#pragma unroll 2
-      for (int z = 0; z < nz; ++z) {
-        const V* src = Pb + (sz[z] * ncy + cy) * ncx + cx;
-        V acc = Val<V>::zero();
-        if constexpr (W == 4) {
-          const float4 h = reinterpret_cast<const float4*>(nzh)[z], l = reinterpret_cast<const float4*>(nzl)[z];
-          const int st = ncy * ncx;
-          Val<V>::add(acc, h.x, l.x, src[0]);
-          Val<V>::add(acc, h.y, l.y, src[st]);
-          Val<V>::add(acc, h.z, l.z, src[2 * st]);
-          Val<V>::add(acc, h.w, l.w, src[3 * st]);
-        } else {
+  // z expansion: warp w takes plane z = w; lanes over (y-control point,
+  // x-control-point pair), two items in flight
+  {
+    const int z = grp;
+    if (z < nz) {
+      float2 bh[W], bn[W], bl[W];
 #pragma unroll
-          for (int r = 0; r < W; ++r) Val<V>::add(acc, nzh[z * W + r], nzl[z * W + r], src[r * ncy * ncx]);
+      for (int r = 0; r < W; ++r) {
+        bh[r] = dup2(nzh[z * W + r]);
+        bn[r] = dup2(-nzh[z * W + r]);
+        bl[r] = dup2(nzl[z * W + r]);
+      }
+      const int szz = sz[z];
+      const int npr = ncxp >> 1, nit = ncy * npr;
+      const float rcp = 1.f / (float)npr;
+      const int pst = ncy * ncxp;  // plane stride of the block
+      for (int it = lane; it < nit; it += 64) {
+        const int it2 = min(it + 32, nit - 1);
+        const int cya = div_small(it, rcp), ka = it - cya * npr;
+        const int cyb = div_small(it2, rcp), kb = it2 - cyb * npr;
+        const int oa = (szz * ncy + cya) * ncxp + 2 * ka, ob = (szz * ncy + cyb) * ncxp + 2 * kb;
+        ff2 A = ff2_zero(), B = ff2_zero();
+#pragma unroll
+        for (int r = 0; r < W; ++r) {
+          ff2_add_v(A, bh[r], bn[r], bl[r], *reinterpret_cast<const float2*>(Pbh + oa + r * pst),
+                    *reinterpret_cast<const float2*>(Pbl + oa + r * pst));
+          ff2_add_v(B, bh[r], bn[r], bl[r], *reinterpret_cast<const float2*>(Pbh + ob + r * pst),
+                    *reinterpret_cast<const float2*>(Pbl + ob + r * pst));
         }
-        Tz[(z * ncy + cy) * ncx + cx] = Val<V>::finish(acc);
+        {
+          const ff a = fast_two_sum(A.hi.x, A.lo.x), b = fast_two_sum(A.hi.y, A.lo.y);
+          const int to = (z * ncy + cya) * ncxp + 2 * ka;
+          *reinterpret_cast<float2*>(Tzh + to) = make_float2(a.hi, b.hi);
+          *reinterpret_cast<float2*>(Tzl + to) = make_float2(a.lo, b.lo);
+        }
+        if (it + 32 < nit) {
+          const ff a = fast_two_sum(B.hi.x, B.lo.x), b = fast_two_sum(B.hi.y, B.lo.y);
+          const int to = (z * ncy + cyb) * ncxp + 2 * kb;
+          *reinterpret_cast<float2*>(Tzh + to) = make_float2(a.hi, b.hi);
+          *reinterpret_cast<float2*>(Tzl + to) = make_float2(a.lo, b.lo);
+        }
       }
     }
   }
   __syncthreads();
-  // y expansion: Ty[z][y][cx]; lanes along cx, groups over y, loop over z
-  for (int y = grp; y < ny; y += kDecThreads / 32) {
-    for (int cx = lane; cx < ncx; cx += 32) {
-      float4 yh4 = make_float4(0, 0, 0, 0), yl4 = make_float4(0, 0, 0, 0);
-      if constexpr (W == 4) {
-        yh4 = reinterpret_cast<const float4*>(nyh)[y];
-        yl4 = reinterpret_cast<const float4*>(nyl)[y];
-      }
-#pragma unroll 2
-      for (int z = 0; z < nz; ++z) {
-        const V* src = Tz + (z * ncy + sy[y]) * ncx + cx;
-        V acc = Val<V>::zero();
-        if constexpr (W == 4) {
-          Val<V>::add(acc, yh4.x, yl4.x, src[0]);
-          Val<V>::add(acc, yh4.y, yl4.y, src[ncx]);
-          Val<V>::add(acc, yh4.z, yl4.z, src[2 * ncx]);
-          Val<V>::add(acc, yh4.w, yl4.w, src[3 * ncx]);
-        } else {
+  // y expansion: rows yl and yl + TY/2 together; a thread keeps its yl and
+  // has two (plane, x-control point) items in flight
+  {
+    constexpr int kPer = kDecThreads / kDecYH;  // threads per row pair
+    const int yl = threadIdx.x / kPer, tl = threadIdx.x - yl * kPer;
+    const int ya = yl, yb = yl + kDecYH;
+    if (ya < ny) {
+      float2 bh[W], bn[W], bl[W];
 #pragma unroll
-          for (int r = 0; r < W; ++r) Val<V>::add(acc, nyh[y * W + r], nyl[y * W + r], src[r * ncx]);
+      for (int r = 0; r < W; ++r) {
+        bh[r] = make_float2(nyh[ya * W + r], nyh[yb * W + r]);
+        bn[r] = make_float2(-nyh[ya * W + r], -nyh[yb * W + r]);
+        bl[r] = make_float2(nyl[ya * W + r], nyl[yb * W + r]);
+      }
+      const int ra = sy[ya], rb = sy[yb];
+      const int nit = nz * ncx;
+      const float rcp = 1.f / (float)ncx;
+      for (int it = tl; it < nit; it += 2 * kPer) {
+        const int it2 = min(it + kPer, nit - 1);
+        const int za = div_small(it, rcp), ca = it - za * ncx;
+        const int zb2 = div_small(it2, rcp), cb = it2 - zb2 * ncx;
+        const float* ha = Tzh + za * ncy * ncxp + ca;
+        const float* la = Tzl + za * ncy * ncxp + ca;
+        const float* hb = Tzh + zb2 * ncy * ncxp + cb;
+        const float* lb = Tzl + zb2 * ncy * ncxp + cb;
+        ff2 A = ff2_zero(), B = ff2_zero();
+#pragma unroll
+        for (int r = 0; r < W; ++r) {
+          ff2_add_v(A, bh[r], bn[r], bl[r], make_float2(ha[(ra + r) * ncxp], ha[(rb + r) * ncxp]),
+                    make_float2(la[(ra + r) * ncxp], la[(rb + r) * ncxp]));
+          ff2_add_v(B, bh[r], bn[r], bl[r], make_float2(hb[(ra + r) * ncxp], hb[(rb + r) * ncxp]),
+                    make_float2(lb[(ra + r) * ncxp], lb[(rb + r) * ncxp]));
         }
-        Ty[(z * ny + y) * ncx + cx] = Val<V>::finish(acc);
+        {
+          const ff a = fast_two_sum(A.hi.x, A.lo.x), b = fast_two_sum(A.hi.y, A.lo.y);
+          Ty[(za * kDecYH + yl) * ncx + ca] = make_float4(a.hi, b.hi, a.lo, b.lo);
+        }
+        if (it + kPer < nit) {
+          const ff a = fast_two_sum(B.hi.x, B.lo.x), b = fast_two_sum(B.hi.y, B.lo.y);
+          Ty[(zb2 * kDecYH + yl) * ncx + cb] = make_float4(a.hi, b.hi, a.lo, b.lo);
+        }
       }
     }
   }
   __syncthreads();
-  // x expansion of every point of the tile, then residual or output:
-  // 64 threads along x, 4 along y
+  // x expansion of every point of the tile, then residual or output: thread
+  // (xt, yl) evaluates rows yl and yl + TY/2, two planes at a time
   float s2 = 0.f, emax = 0.f, qmin = INFINITY, qmax = -INFINITY;
   const long long M0 = L.M[0], M01 = L.M[0] * L.M[1];
   const int xt = threadIdx.x & (kDecTX - 1), yt = threadIdx.x / kDecTX;
-  if (xt < nx) {
-    const float4 bh = W == 4 ? reinterpret_cast<const float4*>(nxh)[xt] : make_float4(0, 0, 0, 0);
-    const float4 bl = W == 4 ? reinterpret_cast<const float4*>(nxl)[xt] : make_float4(0, 0, 0, 0);
-    const int sxx = sx[xt];
-    for (int z = 0; z < nz; ++z) {
+  auto emit = [&](const ff2& acc, int z) {
 #pragma unroll
-      for (int yy = 0; yy < kDecTY; yy += kDecThreads / kDecTX) {
-        const int y = yy + yt;
-        if (y >= ny) continue;
-        const V* src = Ty + (z * ny + y) * ncx + sxx;
-        V acc = Val<V>::zero();
-        if constexpr (W == 4) {
-          Val<V>::add(acc, bh.x, bl.x, src[0]);
-          Val<V>::add(acc, bh.y, bl.y, src[1]);
-          Val<V>::add(acc, bh.z, bl.z, src[2]);
-          Val<V>::add(acc, bh.w, bl.w, src[3]);
-        } else {
-#pragma unroll
-          for (int r = 0; r < W; ++r) Val<V>::add(acc, nxh[xt * W + r], nxl[xt * W + r], src[r]);
-        }
-        acc = Val<V>::finish(acc);
-        const long long g = (long long)(x0 + xt) + M0 * (y0 + y) + M01 * (z0 + z);
-        if constexpr (RESID) {
-          const float q = (float)Q[g];
-          // E = q - (hi + lo): q - hi is exact when the fit is close (Sterbenz)
-          const float e = __fsub_rn(__fsub_rn(q, Val<V>::hi(acc)), Val<V>::lo(acc));
-          s2 = fmaf(e, e, s2);
-          emax = fmaxf(emax, fabsf(e));
-          qmin = fminf(qmin, q);
-          qmax = fmaxf(qmax, q);
-        } else {
-          // hi + lo is exact in FP64, so a float output is its FP32 rounding
-          // (one FP32 add); a double output takes the exact sum
-          if constexpr (sizeof(TOut) == 4)
-            out[g] = __fadd_rn(Val<V>::hi(acc), Val<V>::lo(acc));
-          else
-            out[g] = (TOut)((double)Val<V>::hi(acc) + (double)Val<V>::lo(acc));
-        }
+    for (int hh = 0; hh < 2; ++hh) {
+      const int y = yt + hh * kDecYH;
+      if (y >= ny) continue;
+      const ff v = hh ? fast_two_sum(acc.hi.y, acc.lo.y) : fast_two_sum(acc.hi.x, acc.lo.x);
+      const long long g = (long long)(x0 + xt) + M0 * (y0 + y) + M01 * (z0 + z);
+      if constexpr (RESID) {
+        const float q = (float)Q[g];
+        // E = q - (hi + lo): q - hi is exact when the fit is close (Sterbenz)
+        const float e = __fsub_rn(__fsub_rn(q, v.hi), v.lo);
+        s2 = fmaf(e, e, s2);
+        emax = fmaxf(emax, fabsf(e));
+        qmin = fminf(qmin, q);
+        qmax = fmaxf(qmax, q);
+      } else {
+        // hi + lo is exact in FP64, so a float output is its FP32 rounding
+        // (one FP32 add); a double output takes the exact sum
+        if constexpr (sizeof(TOut) == 4)
+          out[g] = __fadd_rn(v.hi, v.lo);
+        else
+          out[g] = (TOut)((double)v.hi + (double)v.lo);
       }
+    }
+  };
+  if (xt < nx && yt < ny) {
+    float2 bh[W], bn[W], bl[W];
+#pragma unroll
+    for (int r = 0; r < W; ++r) {
+      bh[r] = dup2(nxh[xt * W + r]);
+      bn[r] = dup2(-nxh[xt * W + r]);
+      bl[r] = dup2(nxl[xt * W + r]);
+    }
+    const int sxx = sx[xt];
+    for (int z = 0; z < nz; z += 2) {
+      const int z2 = min(z + 1, nz - 1);
+      const float4* sa = Ty + (z * kDecYH + yt) * ncx + sxx;
+      const float4* sb = Ty + (z2 * kDecYH + yt) * ncx + sxx;
+      ff2 A = ff2_zero(), B = ff2_zero();
+#pragma unroll
+      for (int r = 0; r < W; ++r) {
+        const float4 ta = sa[r], tb = sb[r];
+        ff2_add_v(A, bh[r], bn[r], bl[r], make_float2(ta.x, ta.y), make_float2(ta.z, ta.w));
+        ff2_add_v(B, bh[r], bn[r], bl[r], make_float2(tb.x, tb.y), make_float2(tb.z, tb.w));
+      }
+      emit(A, z);
+      if (z + 1 < nz) emit(B, z + 1);
     }
   }
   if constexpr (RESID) {
@@ -918,13 +972,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode3d(LayoutDev L, const V* 
 
 template <int P, typename V>
 size_t decode3d_smem(int ncx, int ncy, int ncz) {
-  constexpr int W = P + 1;
-  size_t off = (size_t)(2 * W * (kDecTX + kDecTY + kDecTZ)) * 4 + (size_t)(kDecTX + kDecTY + kDecTZ) * 4;
-  off = (off + 15) & ~size_t(15);
-  off += (size_t)ncz * ncy * ncx * sizeof(V);
-  off += (size_t)kDecTZ * ncy * ncx * sizeof(V);
-  off += (size_t)kDecTZ * kDecTY * ncx * sizeof(V);
-  return off;
+  return dec_smem_layout(P + 1, ncx, ncy, ncz).total;
 }
 
 long long decode3d_tiles(const LayoutDev& L) {

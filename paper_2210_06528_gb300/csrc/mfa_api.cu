@@ -29,6 +29,9 @@ struct mfa_handle {
   double* d_partials = nullptr;             // [4 * kResidualBlocks]
   double* d_result = nullptr;               // [4]
   double* h_pinned = nullptr;               // [16] readback
+  char* h_stage = nullptr;                  // pinned staging of layout tables (grown as needed)
+  size_t h_stage_cap = 0;
+  cudaEvent_t stage_done = nullptr;         // the last upload from h_stage has been read
   void* ws = nullptr;                       // growable scratch
   size_t ws_size = 0;
   int live_models = 0;
@@ -827,6 +830,7 @@ int mfa_create(int device, void* cuda_stream, mfa_handle** out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->d_partials, 4 * sizeof(double) * kResidualBlocks);
   if (e == cudaSuccess) e = cudaMalloc(&h->d_result, 256);
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_pinned, 256);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, 256, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
@@ -850,6 +854,8 @@ int mfa_destroy(mfa_handle* h) {
   cudaFree(h->d_partials);
   cudaFree(h->d_result);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  if (h->h_stage) cudaFreeHost(h->h_stage);
+  if (h->stage_done) cudaEventDestroy(h->stage_done);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
   return MFA_OK;
@@ -868,13 +874,10 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
   Arena ar;
   size_t o_span[3], o_vd[3], o_vf[3], o_vff[3], o_ss[3], o_subs[3], o_of[3], o_oc[3], o_AL[3], o_fLd[3], o_fLf[3],
       o_fLff[3], o_fUd[3], o_fUf[3], o_fUff[3], o_ot[3], o_nlt[3], o_pk[3], o_one[3];
+  // tables filled on the host come first (one upload), then the ones the
+  // setup kernels compute
   for (int a = 0; a < 3; ++a) {
     const AxisHost& ax = md->axh[a];
-    const int w = ax.p + 1;
-    o_span[a] = ar.take<int>(ax.M);
-    o_vd[a] = ar.take<double>((size_t)ax.M * w);
-    o_vf[a] = ar.take<float>((size_t)ax.M * w);
-    o_vff[a] = ar.take<ff>((size_t)ax.M * w);
     o_ss[a] = ar.take<int>(ax.nspans + 1);
     o_subs[a] = ar.take<AxisSub>(ax.S);
     o_of[a] = ar.take<int>(ax.n);
@@ -883,13 +886,6 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
     o_nlt[a] = ar.take<int>(ax.S);
     o_pk[a] = ar.take<int>(ax.n);
     o_one[a] = ar.take<int2>(ax.S);
-    o_AL[a] = ar.take<double>((size_t)ax.bandL_rows * w);
-    o_fLd[a] = ar.take<double>((size_t)ax.bandL_rows * w);
-    o_fLf[a] = ar.take<float>((size_t)ax.bandL_rows * w);
-    o_fLff[a] = ar.take<ff>((size_t)ax.bandL_rows * w);
-    o_fUd[a] = ar.take<double>((size_t)ax.bandU_rows * w);
-    o_fUf[a] = ar.take<float>((size_t)ax.bandU_rows * w);
-    o_fUff[a] = ar.take<ff>((size_t)ax.bandU_rows * w);
   }
   const size_t o_offL = ar.take<long long>(ns), o_offS1 = ar.take<long long>(ns), o_offS2 = ar.take<long long>(ns);
   const size_t o_ops = ar.take<AxisOp>(ops.size());
@@ -911,27 +907,59 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
       }
   }
   const size_t o_rows = ar.take<int>(rows_full.size() + rows_part.size()), o_xs = ar.take<int>(xs.size());
-  const size_t tables_bytes = ar.used;
-  // host staging image of the uploaded tables
-  std::vector<char> img(tables_bytes, 0);
+  const size_t host_bytes = ar.used;
   for (int a = 0; a < 3; ++a) {
     const AxisHost& ax = md->axh[a];
-    std::memcpy(img.data() + o_ss[a], ax.span_start.data(), sizeof(int) * ax.span_start.size());
-    std::memcpy(img.data() + o_subs[a], ax.subs.data(), sizeof(AxisSub) * ax.subs.size());
-    std::memcpy(img.data() + o_of[a], ax.own_first.data(), sizeof(int) * ax.n);
-    std::memcpy(img.data() + o_oc[a], ax.own_count.data(), sizeof(int) * ax.n);
-    std::memcpy(img.data() + o_ot[a], ax.own_tab.data(), sizeof(int4) * ax.n);
-    std::memcpy(img.data() + o_nlt[a], ax.nL_tab.data(), sizeof(int) * ax.S);
-    std::memcpy(img.data() + o_pk[a], ax.own_pick.data(), sizeof(int) * ax.n);
-    std::memcpy(img.data() + o_one[a], ax.one_rng.data(), sizeof(int2) * ax.S);
+    const int w = ax.p + 1;
+    o_span[a] = ar.take<int>(ax.M);
+    o_vd[a] = ar.take<double>((size_t)ax.M * w);
+    o_vf[a] = ar.take<float>((size_t)ax.M * w);
+    o_vff[a] = ar.take<ff>((size_t)ax.M * w);
+    o_AL[a] = ar.take<double>((size_t)ax.bandL_rows * w);
+    o_fLd[a] = ar.take<double>((size_t)ax.bandL_rows * w);
+    o_fLf[a] = ar.take<float>((size_t)ax.bandL_rows * w);
+    o_fLff[a] = ar.take<ff>((size_t)ax.bandL_rows * w);
+    o_fUd[a] = ar.take<double>((size_t)ax.bandU_rows * w);
+    o_fUf[a] = ar.take<float>((size_t)ax.bandU_rows * w);
+    o_fUff[a] = ar.take<ff>((size_t)ax.bandU_rows * w);
   }
-  std::memcpy(img.data() + o_rows, rows_full.data(), sizeof(int) * rows_full.size());
-  std::memcpy(img.data() + o_rows + sizeof(int) * rows_full.size(), rows_part.data(), sizeof(int) * rows_part.size());
-  std::memcpy(img.data() + o_xs, xs.data(), sizeof(int) * xs.size());
-  std::memcpy(img.data() + o_offL, offL.data(), sizeof(long long) * ns);
-  std::memcpy(img.data() + o_offS1, offS1.data(), sizeof(long long) * ns);
-  std::memcpy(img.data() + o_offS2, offS2.data(), sizeof(long long) * ns);
-  std::memcpy(img.data() + o_ops, ops.data(), sizeof(AxisOp) * ops.size());
+  const size_t tables_bytes = ar.used;
+  // host image of the uploaded tables, built in the handle's pinned staging
+  // buffer once its previous upload has been read (alignment gaps are never
+  // read, so the image is not cleared)
+  if (h->h_stage_cap < host_bytes) {
+    cudaEventSynchronize(h->stage_done);
+    if (h->h_stage) cudaFreeHost(h->h_stage);
+    h->h_stage = nullptr;
+    h->h_stage_cap = 0;
+    if (cudaMallocHost(&h->h_stage, host_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      h->h_stage = nullptr;
+      return MFA_ERR_OOM;
+    }
+    h->h_stage_cap = host_bytes;
+  } else {
+    cudaEventSynchronize(h->stage_done);
+  }
+  char* img = h->h_stage;
+  for (int a = 0; a < 3; ++a) {
+    const AxisHost& ax = md->axh[a];
+    std::memcpy(img + o_ss[a], ax.span_start.data(), sizeof(int) * ax.span_start.size());
+    std::memcpy(img + o_subs[a], ax.subs.data(), sizeof(AxisSub) * ax.subs.size());
+    std::memcpy(img + o_of[a], ax.own_first.data(), sizeof(int) * ax.n);
+    std::memcpy(img + o_oc[a], ax.own_count.data(), sizeof(int) * ax.n);
+    std::memcpy(img + o_ot[a], ax.own_tab.data(), sizeof(int4) * ax.n);
+    std::memcpy(img + o_nlt[a], ax.nL_tab.data(), sizeof(int) * ax.S);
+    std::memcpy(img + o_pk[a], ax.own_pick.data(), sizeof(int) * ax.n);
+    std::memcpy(img + o_one[a], ax.one_rng.data(), sizeof(int2) * ax.S);
+  }
+  std::memcpy(img + o_rows, rows_full.data(), sizeof(int) * rows_full.size());
+  std::memcpy(img + o_rows + sizeof(int) * rows_full.size(), rows_part.data(), sizeof(int) * rows_part.size());
+  std::memcpy(img + o_xs, xs.data(), sizeof(int) * xs.size());
+  std::memcpy(img + o_offL, offL.data(), sizeof(long long) * ns);
+  std::memcpy(img + o_offS1, offS1.data(), sizeof(long long) * ns);
+  std::memcpy(img + o_offS2, offS2.data(), sizeof(long long) * ns);
+  std::memcpy(img + o_ops, ops.data(), sizeof(AxisOp) * ops.size());
   // big buffers
   const size_t es = elem_size(md->prec);
   Arena bg;
@@ -954,8 +982,9 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
     md->arena = md->big = nullptr;
     return rc;
   }
-  // pageable source: the runtime has staged it when the call returns
-  cudaError_t e = cudaMemcpyAsync(md->arena, img.data(), tables_bytes, cudaMemcpyHostToDevice, h->stream);
+  // pinned source: the copy runs ahead of the setup kernels on the stream
+  cudaError_t e = cudaMemcpyAsync(md->arena, img, host_bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(h->stage_done, h->stream);
   // device layout struct
   LayoutDev& L = md->L;
   L.dim = md->dim;
