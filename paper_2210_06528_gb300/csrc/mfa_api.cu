@@ -20,6 +20,10 @@ using namespace mfa;
 // handle and model
 // ---------------------------------------------------------------------------
 
+namespace {
+struct PlanCache;
+}  // namespace
+
 struct mfa_handle {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -32,6 +36,9 @@ struct mfa_handle {
   char* h_stage = nullptr;                  // pinned staging of layout tables (grown as needed)
   size_t h_stage_cap = 0;
   cudaEvent_t stage_done = nullptr;         // the last upload from h_stage has been read
+  PlanCache* plan = nullptr;                // host products of the most recent single-model layout
+  void (*plan_free)(PlanCache*) = nullptr;  // its deleter (set with it)
+  bool plan_valid = false;                  // plan matches the image in h_stage
   void* ws = nullptr;                       // growable scratch
   size_t ws_size = 0;
   int live_models = 0;
@@ -856,39 +863,165 @@ int mfa_destroy(mfa_handle* h) {
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   if (h->h_stage) cudaFreeHost(h->h_stage);
   if (h->stage_done) cudaEventDestroy(h->stage_done);
+  if (h->plan && h->plan_free) h->plan_free(h->plan);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
   return MFA_OK;
 }
 
 namespace {
+// Offsets of a model's device tables (one arena: the host-filled tables
+// first, then those the setup kernels compute) and buffers (one pool block).
+struct TablePlan {
+  size_t o_span[3], o_vd[3], o_vf[3], o_vff[3], o_ss[3], o_subs[3], o_of[3], o_oc[3], o_AL[3], o_fLd[3], o_fLf[3],
+      o_fLff[3], o_fUd[3], o_fUf[3], o_fUff[3], o_ot[3], o_nlt[3], o_pk[3], o_one[3];
+  size_t o_offL = 0, o_offS1 = 0, o_offS2 = 0, o_ops = 0, o_rows = 0, o_xs = 0;
+  int n_full_rows = 0, n_part_rows = 0, n_xs = 0;
+  size_t host_bytes = 0, tables_bytes = 0;
+  size_t o_BL = 0, o_X = 0, o_P = 0, o_Pp = 0, o_S1 = 0, o_S2 = 0, o_part = 0, o_stage = 0, big_bytes = 0;
+};
+
+// Host products of one layout, kept per handle for the most recent layout of
+// a single model: the host axes and operand tables (a model copy without
+// device memory) and the table plan, whose image stays in h->h_stage while
+// h->plan_valid.  A model of the same layout then skips the host build; every
+// kernel (setup included) still runs.
+struct PlanCache {
+  mfa_layout lay{};
+  std::vector<int32_t> cores[3];
+  bool plain = false;
+  size_t stage_bytes = 0;
+  mfa_model* proto = nullptr;
+  TablePlan tp;
+};
+
+bool plan_matches(const PlanCache& pc, const mfa_layout* lay, bool plain, size_t stage_bytes) {
+  if (pc.plain != plain || pc.stage_bytes != stage_bytes) return false;
+  const mfa_layout& k = pc.lay;
+  if (k.dim != lay->dim || k.degree != lay->degree || k.precision != lay->precision) return false;
+  for (int a = 0; a < lay->dim && a < 3; ++a) {
+    if (k.npts[a] != lay->npts[a] || k.nspans[a] != lay->nspans[a] || k.nsub[a] != lay->nsub[a] ||
+        k.overlap[a] != lay->overlap[a] || k.lo[a] != lay->lo[a] || k.hi[a] != lay->hi[a])
+      return false;
+    if ((lay->core_spans[a] == nullptr) != pc.cores[a].empty()) return false;
+    if (lay->core_spans[a] &&
+        std::memcmp(lay->core_spans[a], pc.cores[a].data(), sizeof(int32_t) * pc.cores[a].size()) != 0)
+      return false;
+  }
+  return true;
+}
+
+// Allocate the model's tables and buffers, upload the host-filled tables from
+// the handle's pinned image (h->h_stage, host_bytes long), fill the device
+// layout and run the setup kernels (basis, Gram bands, Cholesky factors).
+int bind_model(mfa_handle* h, mfa_model* md, const TablePlan& tp) {
+  int rc = pool_alloc(h, &md->arena, tp.tables_bytes);
+  if (rc == MFA_OK) rc = pool_alloc(h, &md->big, tp.big_bytes);
+  if (rc != MFA_OK) {
+    pool_free(h, md->arena);
+    pool_free(h, md->big);
+    md->arena = md->big = nullptr;
+    return rc;
+  }
+  // pinned source: the copy runs ahead of the setup kernels on the stream
+  cudaError_t e = cudaMemcpyAsync(md->arena, h->h_stage, tp.host_bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(h->stage_done, h->stream);
+  LayoutDev& L = md->L;
+  L.dim = md->dim;
+  L.nsub = md->nsub;
+  for (int a = 0; a < 3; ++a) {
+    const AxisHost& ax = md->axh[a];
+    L.S[a] = ax.S;
+    L.ncp[a] = ax.n;
+    L.M[a] = ax.M;
+    AxisDev& d = L.ax[a];
+    d.M = ax.M;
+    d.nspans = ax.nspans;
+    d.p = ax.p;
+    d.n = ax.n;
+    d.S = ax.S;
+    d.pieces = ax.pieces;
+    d.span = at_off<int>(md->arena, tp.o_span[a]);
+    d.vals_d = at_off<double>(md->arena, tp.o_vd[a]);
+    d.vals_f = at_off<float>(md->arena, tp.o_vf[a]);
+    d.vals_ff = at_off<ff>(md->arena, tp.o_vff[a]);
+    d.span_start = at_off<int>(md->arena, tp.o_ss[a]);
+    d.subs = at_off<AxisSub>(md->arena, tp.o_subs[a]);
+    d.own_first = at_off<int>(md->arena, tp.o_of[a]);
+    d.own_count = at_off<int>(md->arena, tp.o_oc[a]);
+    d.own_tab = at_off<int4>(md->arena, tp.o_ot[a]);
+    d.nL_tab = at_off<int>(md->arena, tp.o_nlt[a]);
+    d.own_pick = at_off<int>(md->arena, tp.o_pk[a]);
+    d.one_rng = at_off<int2>(md->arena, tp.o_one[a]);
+    d.AL = at_off<double>(md->arena, tp.o_AL[a]);
+    d.facL_d = at_off<double>(md->arena, tp.o_fLd[a]);
+    d.facL_f = at_off<float>(md->arena, tp.o_fLf[a]);
+    d.facL_ff = at_off<ff>(md->arena, tp.o_fLff[a]);
+    d.facU_d = at_off<double>(md->arena, tp.o_fUd[a]);
+    d.facU_f = at_off<float>(md->arena, tp.o_fUf[a]);
+    d.facU_ff = at_off<ff>(md->arena, tp.o_fUff[a]);
+  }
+  L.shared_rows = at_off<int>(md->arena, tp.o_rows);
+  L.n_full_rows = tp.n_full_rows;
+  L.n_part_rows = tp.n_part_rows;
+  L.shared_x = at_off<int>(md->arena, tp.o_xs);
+  L.n_shared_x = tp.n_xs;
+  md->offL = at_off<long long>(md->arena, tp.o_offL);
+  md->offS1 = at_off<long long>(md->arena, tp.o_offS1);
+  md->offS2 = at_off<long long>(md->arena, tp.o_offS2);
+  md->ops = at_off<AxisOp>(md->arena, tp.o_ops);
+  md->BL = at_off<char>(md->big, tp.o_BL);
+  md->X = at_off<char>(md->big, tp.o_X);
+  md->P = at_off<char>(md->big, tp.o_P);
+  md->Pprev = at_off<char>(md->big, tp.o_Pp);
+  md->S1 = at_off<char>(md->big, tp.o_S1);
+  md->S2 = at_off<char>(md->big, tp.o_S2);
+  md->part = at_off<float>(md->big, tp.o_part);
+  // setup kernels: basis tables, Gram bands, Cholesky factors (FP64), all axes per launch
+  {
+    int maxnL = 1;
+    for (int a = 0; a < 3; ++a) maxnL = std::max(maxnL, md->maxnL[a]);
+    TRACED_N(h, TR_SETUP, 2, launch_setup_all(L.ax, 3, maxnL, h->d_status, h->stream));
+  }
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    pool_free(h, md->arena);
+    pool_free(h, md->big);
+    md->arena = md->big = nullptr;
+    return cuda_status(e);
+  }
+  return MFA_OK;
+}
+
 // Upload the layout tables of a model whose host axes (md->axh) and operand
 // tables are built, allocate its buffers (plus `stage_bytes` for staged host
 // data, offset returned in *o_stage), fill the device layout and run the
-// setup kernels (basis, Gram bands, Cholesky factors).
+// setup kernels.  The table image is built in the handle's pinned staging
+// buffer; the plan is returned in *keep when given.
 int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& ops,
                       const std::vector<long long>& offL, const std::vector<long long>& offS1,
-                      const std::vector<long long>& offS2, size_t stage_bytes, size_t* o_stage) {
+                      const std::vector<long long>& offS2, size_t stage_bytes, size_t* o_stage,
+                      TablePlan* keep = nullptr) {
   const int ns = md->nsub;
-  // ---- device tables in one arena
+  TablePlan tp;
   Arena ar;
-  size_t o_span[3], o_vd[3], o_vf[3], o_vff[3], o_ss[3], o_subs[3], o_of[3], o_oc[3], o_AL[3], o_fLd[3], o_fLf[3],
-      o_fLff[3], o_fUd[3], o_fUf[3], o_fUff[3], o_ot[3], o_nlt[3], o_pk[3], o_one[3];
   // tables filled on the host come first (one upload), then the ones the
   // setup kernels compute
   for (int a = 0; a < 3; ++a) {
     const AxisHost& ax = md->axh[a];
-    o_ss[a] = ar.take<int>(ax.nspans + 1);
-    o_subs[a] = ar.take<AxisSub>(ax.S);
-    o_of[a] = ar.take<int>(ax.n);
-    o_oc[a] = ar.take<int>(ax.n);
-    o_ot[a] = ar.take<int4>(ax.n);
-    o_nlt[a] = ar.take<int>(ax.S);
-    o_pk[a] = ar.take<int>(ax.n);
-    o_one[a] = ar.take<int2>(ax.S);
+    tp.o_ss[a] = ar.take<int>(ax.nspans + 1);
+    tp.o_subs[a] = ar.take<AxisSub>(ax.S);
+    tp.o_of[a] = ar.take<int>(ax.n);
+    tp.o_oc[a] = ar.take<int>(ax.n);
+    tp.o_ot[a] = ar.take<int4>(ax.n);
+    tp.o_nlt[a] = ar.take<int>(ax.S);
+    tp.o_pk[a] = ar.take<int>(ax.n);
+    tp.o_one[a] = ar.take<int2>(ax.S);
   }
-  const size_t o_offL = ar.take<long long>(ns), o_offS1 = ar.take<long long>(ns), o_offS2 = ar.take<long long>(ns);
-  const size_t o_ops = ar.take<AxisOp>(ops.size());
+  tp.o_offL = ar.take<long long>(ns);
+  tp.o_offS1 = ar.take<long long>(ns);
+  tp.o_offS2 = ar.take<long long>(ns);
+  tp.o_ops = ar.take<AxisOp>(ops.size());
   // rows of control points with two owners on some axis (float-float update):
   // rows with two owners along y or z first, then the rest with the x
   // positions that have two owners
@@ -906,151 +1039,84 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
           rows_part.push_back(r);
       }
   }
-  const size_t o_rows = ar.take<int>(rows_full.size() + rows_part.size()), o_xs = ar.take<int>(xs.size());
-  const size_t host_bytes = ar.used;
+  tp.o_rows = ar.take<int>(rows_full.size() + rows_part.size());
+  tp.o_xs = ar.take<int>(xs.size());
+  tp.n_full_rows = (int)rows_full.size();
+  tp.n_part_rows = (int)rows_part.size();
+  tp.n_xs = (int)xs.size();
+  tp.host_bytes = ar.used;
   for (int a = 0; a < 3; ++a) {
     const AxisHost& ax = md->axh[a];
     const int w = ax.p + 1;
-    o_span[a] = ar.take<int>(ax.M);
-    o_vd[a] = ar.take<double>((size_t)ax.M * w);
-    o_vf[a] = ar.take<float>((size_t)ax.M * w);
-    o_vff[a] = ar.take<ff>((size_t)ax.M * w);
-    o_AL[a] = ar.take<double>((size_t)ax.bandL_rows * w);
-    o_fLd[a] = ar.take<double>((size_t)ax.bandL_rows * w);
-    o_fLf[a] = ar.take<float>((size_t)ax.bandL_rows * w);
-    o_fLff[a] = ar.take<ff>((size_t)ax.bandL_rows * w);
-    o_fUd[a] = ar.take<double>((size_t)ax.bandU_rows * w);
-    o_fUf[a] = ar.take<float>((size_t)ax.bandU_rows * w);
-    o_fUff[a] = ar.take<ff>((size_t)ax.bandU_rows * w);
+    tp.o_span[a] = ar.take<int>(ax.M);
+    tp.o_vd[a] = ar.take<double>((size_t)ax.M * w);
+    tp.o_vf[a] = ar.take<float>((size_t)ax.M * w);
+    tp.o_vff[a] = ar.take<ff>((size_t)ax.M * w);
+    tp.o_AL[a] = ar.take<double>((size_t)ax.bandL_rows * w);
+    tp.o_fLd[a] = ar.take<double>((size_t)ax.bandL_rows * w);
+    tp.o_fLf[a] = ar.take<float>((size_t)ax.bandL_rows * w);
+    tp.o_fLff[a] = ar.take<ff>((size_t)ax.bandL_rows * w);
+    tp.o_fUd[a] = ar.take<double>((size_t)ax.bandU_rows * w);
+    tp.o_fUf[a] = ar.take<float>((size_t)ax.bandU_rows * w);
+    tp.o_fUff[a] = ar.take<ff>((size_t)ax.bandU_rows * w);
   }
-  const size_t tables_bytes = ar.used;
-  // host image of the uploaded tables, built in the handle's pinned staging
-  // buffer once its previous upload has been read (alignment gaps are never
-  // read, so the image is not cleared)
-  if (h->h_stage_cap < host_bytes) {
-    cudaEventSynchronize(h->stage_done);
-    if (h->h_stage) cudaFreeHost(h->h_stage);
-    h->h_stage = nullptr;
-    h->h_stage_cap = 0;
-    if (cudaMallocHost(&h->h_stage, host_bytes) != cudaSuccess) {
-      cudaGetLastError();
-      h->h_stage = nullptr;
-      return MFA_ERR_OOM;
-    }
-    h->h_stage_cap = host_bytes;
-  } else {
-    cudaEventSynchronize(h->stage_done);
-  }
-  char* img = h->h_stage;
-  for (int a = 0; a < 3; ++a) {
-    const AxisHost& ax = md->axh[a];
-    std::memcpy(img + o_ss[a], ax.span_start.data(), sizeof(int) * ax.span_start.size());
-    std::memcpy(img + o_subs[a], ax.subs.data(), sizeof(AxisSub) * ax.subs.size());
-    std::memcpy(img + o_of[a], ax.own_first.data(), sizeof(int) * ax.n);
-    std::memcpy(img + o_oc[a], ax.own_count.data(), sizeof(int) * ax.n);
-    std::memcpy(img + o_ot[a], ax.own_tab.data(), sizeof(int4) * ax.n);
-    std::memcpy(img + o_nlt[a], ax.nL_tab.data(), sizeof(int) * ax.S);
-    std::memcpy(img + o_pk[a], ax.own_pick.data(), sizeof(int) * ax.n);
-    std::memcpy(img + o_one[a], ax.one_rng.data(), sizeof(int2) * ax.S);
-  }
-  std::memcpy(img + o_rows, rows_full.data(), sizeof(int) * rows_full.size());
-  std::memcpy(img + o_rows + sizeof(int) * rows_full.size(), rows_part.data(), sizeof(int) * rows_part.size());
-  std::memcpy(img + o_xs, xs.data(), sizeof(int) * xs.size());
-  std::memcpy(img + o_offL, offL.data(), sizeof(long long) * ns);
-  std::memcpy(img + o_offS1, offS1.data(), sizeof(long long) * ns);
-  std::memcpy(img + o_offS2, offS2.data(), sizeof(long long) * ns);
-  std::memcpy(img + o_ops, ops.data(), sizeof(AxisOp) * ops.size());
+  tp.tables_bytes = ar.used;
   // big buffers
   const size_t es = elem_size(md->prec);
   Arena bg;
   // a batch group writes B_L and X into the batch's buffers and has no global P
   const long long own_sizeL = md->batch ? 0 : md->sizeL;
-  const size_t o_BL = bg.take<char>(own_sizeL * es), o_X = bg.take<char>(own_sizeL * es);
+  tp.o_BL = bg.take<char>(own_sizeL * es);
+  tp.o_X = bg.take<char>(own_sizeL * es);
   const long long ncp = md->batch ? 0 : (long long)md->axh[0].n * md->axh[1].n * md->axh[2].n;
-  const size_t o_P = bg.take<char>(ncp * es), o_Pp = bg.take<char>(ncp * es);
-  const size_t o_S1 = bg.take<char>(md->sizeS1 * es), o_S2 = bg.take<char>(md->sizeS2 * es);
+  tp.o_P = bg.take<char>(ncp * es);
+  tp.o_Pp = bg.take<char>(ncp * es);
+  tp.o_S1 = bg.take<char>(md->sizeS1 * es);
+  tp.o_S2 = bg.take<char>(md->sizeS2 * es);
   // update partials (3 floats per block of the float-float update) and its
   // row counter
-  const size_t o_part = bg.take<float>(3 * (size_t)(ns + kAvgListBlocks) + 1);
+  tp.o_part = bg.take<float>(3 * (size_t)(ns + kAvgListBlocks) + 1);
   // host data staging: the data are copied into the pool before use
-  *o_stage = stage_bytes ? bg.take<char>(stage_bytes) : 0;
-  int rc = pool_alloc(h, &md->arena, tables_bytes);
-  if (rc == MFA_OK) rc = pool_alloc(h, &md->big, bg.used);
-  if (rc != MFA_OK) {
-    pool_free(h, md->arena);
-    pool_free(h, md->big);
-    md->arena = md->big = nullptr;
-    return rc;
+  tp.o_stage = stage_bytes ? bg.take<char>(stage_bytes) : 0;
+  tp.big_bytes = bg.used;
+  // host image of the uploaded tables, built in the handle's pinned staging
+  // buffer once its previous upload has been read (alignment gaps are never
+  // read, so the image is not cleared); it no longer holds a cached plan
+  h->plan_valid = false;
+  cudaEventSynchronize(h->stage_done);
+  if (h->h_stage_cap < tp.host_bytes) {
+    if (h->h_stage) cudaFreeHost(h->h_stage);
+    h->h_stage = nullptr;
+    h->h_stage_cap = 0;
+    if (cudaMallocHost(&h->h_stage, tp.host_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      h->h_stage = nullptr;
+      return MFA_ERR_OOM;
+    }
+    h->h_stage_cap = tp.host_bytes;
   }
-  // pinned source: the copy runs ahead of the setup kernels on the stream
-  cudaError_t e = cudaMemcpyAsync(md->arena, img, host_bytes, cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = cudaEventRecord(h->stage_done, h->stream);
-  // device layout struct
-  LayoutDev& L = md->L;
-  L.dim = md->dim;
-  L.nsub = ns;
+  char* img = h->h_stage;
   for (int a = 0; a < 3; ++a) {
     const AxisHost& ax = md->axh[a];
-    L.S[a] = ax.S;
-    L.ncp[a] = ax.n;
-    L.M[a] = ax.M;
-    AxisDev& d = L.ax[a];
-    d.M = ax.M;
-    d.nspans = ax.nspans;
-    d.p = ax.p;
-    d.n = ax.n;
-    d.S = ax.S;
-    d.pieces = ax.pieces;
-    d.span = at_off<int>(md->arena, o_span[a]);
-    d.vals_d = at_off<double>(md->arena, o_vd[a]);
-    d.vals_f = at_off<float>(md->arena, o_vf[a]);
-    d.vals_ff = at_off<ff>(md->arena, o_vff[a]);
-    d.span_start = at_off<int>(md->arena, o_ss[a]);
-    d.subs = at_off<AxisSub>(md->arena, o_subs[a]);
-    d.own_first = at_off<int>(md->arena, o_of[a]);
-    d.own_count = at_off<int>(md->arena, o_oc[a]);
-    d.own_tab = at_off<int4>(md->arena, o_ot[a]);
-    d.nL_tab = at_off<int>(md->arena, o_nlt[a]);
-    d.own_pick = at_off<int>(md->arena, o_pk[a]);
-    d.one_rng = at_off<int2>(md->arena, o_one[a]);
-    d.AL = at_off<double>(md->arena, o_AL[a]);
-    d.facL_d = at_off<double>(md->arena, o_fLd[a]);
-    d.facL_f = at_off<float>(md->arena, o_fLf[a]);
-    d.facL_ff = at_off<ff>(md->arena, o_fLff[a]);
-    d.facU_d = at_off<double>(md->arena, o_fUd[a]);
-    d.facU_f = at_off<float>(md->arena, o_fUf[a]);
-    d.facU_ff = at_off<ff>(md->arena, o_fUff[a]);
+    std::memcpy(img + tp.o_ss[a], ax.span_start.data(), sizeof(int) * ax.span_start.size());
+    std::memcpy(img + tp.o_subs[a], ax.subs.data(), sizeof(AxisSub) * ax.subs.size());
+    std::memcpy(img + tp.o_of[a], ax.own_first.data(), sizeof(int) * ax.n);
+    std::memcpy(img + tp.o_oc[a], ax.own_count.data(), sizeof(int) * ax.n);
+    std::memcpy(img + tp.o_ot[a], ax.own_tab.data(), sizeof(int4) * ax.n);
+    std::memcpy(img + tp.o_nlt[a], ax.nL_tab.data(), sizeof(int) * ax.S);
+    std::memcpy(img + tp.o_pk[a], ax.own_pick.data(), sizeof(int) * ax.n);
+    std::memcpy(img + tp.o_one[a], ax.one_rng.data(), sizeof(int2) * ax.S);
   }
-  L.shared_rows = at_off<int>(md->arena, o_rows);
-  L.n_full_rows = (int)rows_full.size();
-  L.n_part_rows = (int)rows_part.size();
-  L.shared_x = at_off<int>(md->arena, o_xs);
-  L.n_shared_x = (int)xs.size();
-  md->offL = at_off<long long>(md->arena, o_offL);
-  md->offS1 = at_off<long long>(md->arena, o_offS1);
-  md->offS2 = at_off<long long>(md->arena, o_offS2);
-  md->ops = at_off<AxisOp>(md->arena, o_ops);
-  md->BL = at_off<char>(md->big, o_BL);
-  md->X = at_off<char>(md->big, o_X);
-  md->P = at_off<char>(md->big, o_P);
-  md->Pprev = at_off<char>(md->big, o_Pp);
-  md->S1 = at_off<char>(md->big, o_S1);
-  md->S2 = at_off<char>(md->big, o_S2);
-  md->part = at_off<float>(md->big, o_part);
-  // setup kernels: basis tables, Gram bands, Cholesky factors (FP64), all axes per launch
-  {
-    int maxnL = 1;
-    for (int a = 0; a < 3; ++a) maxnL = std::max(maxnL, md->maxnL[a]);
-    TRACED_N(h, TR_SETUP, 2, launch_setup_all(L.ax, 3, maxnL, h->d_status, h->stream));
-  }
-  if (e == cudaSuccess) e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    pool_free(h, md->arena);
-    pool_free(h, md->big);
-    md->arena = md->big = nullptr;
-    return cuda_status(e);
-  }
-  return MFA_OK;
+  std::memcpy(img + tp.o_rows, rows_full.data(), sizeof(int) * rows_full.size());
+  std::memcpy(img + tp.o_rows + sizeof(int) * rows_full.size(), rows_part.data(), sizeof(int) * rows_part.size());
+  std::memcpy(img + tp.o_xs, xs.data(), sizeof(int) * xs.size());
+  std::memcpy(img + tp.o_offL, offL.data(), sizeof(long long) * ns);
+  std::memcpy(img + tp.o_offS1, offS1.data(), sizeof(long long) * ns);
+  std::memcpy(img + tp.o_offS2, offS2.data(), sizeof(long long) * ns);
+  std::memcpy(img + tp.o_ops, ops.data(), sizeof(AxisOp) * ops.size());
+  *o_stage = tp.o_stage;
+  if (keep) *keep = tp;
+  return bind_model(h, md, tp);
 }
 }  // namespace
 
@@ -1088,6 +1154,18 @@ int create_model(mfa_handle* h, const mfa_layout* lay, bool plain, size_t stage_
   if (lay->degree < 1 || lay->degree > MFA_MAX_DEGREE) return MFA_ERR_ARG;
   if (lay->precision != MFA_PREC_FP64 && lay->precision != MFA_PREC_MIXED) return MFA_ERR_ARG;
   DeviceGuard g(h->device);
+  if (h->plan_valid && h->plan && h->plan->proto && plan_matches(*h->plan, lay, plain, stage_bytes)) {
+    mfa_model* md = new (std::nothrow) mfa_model(*h->plan->proto);
+    if (!md) return MFA_ERR_OOM;
+    const int rc = bind_model(h, md, h->plan->tp);
+    if (rc != MFA_OK) {
+      delete md;
+      return rc;
+    }
+    *o_stage = h->plan->tp.o_stage;
+    *out = md;
+    return MFA_OK;
+  }
   mfa_model* md = new (std::nothrow) mfa_model();
   if (!md) return MFA_ERR_OOM;
   md->h = h;
@@ -1142,10 +1220,37 @@ int create_model(mfa_handle* h, const mfa_layout* lay, bool plain, size_t stage_
   std::vector<AxisOp> ops;
   std::vector<long long> offL, offS1, offS2;
   build_ops(md, ops, offL, offS1, offS2);
-  int rc = materialize_model(h, md, ops, offL, offS1, offS2, stage_bytes, o_stage);
+  TablePlan tp;
+  int rc = materialize_model(h, md, ops, offL, offS1, offS2, stage_bytes, o_stage, &tp);
   if (rc != MFA_OK) {
     delete md;
     return rc;
+  }
+  // keep this layout's host products (no device memory) for its next model
+  if (!h->plan) {
+    h->plan = new (std::nothrow) PlanCache();
+    h->plan_free = [](PlanCache* pc) {
+      delete pc->proto;
+      delete pc;
+    };
+  }
+  if (h->plan) {
+    PlanCache& pc = *h->plan;
+    delete pc.proto;
+    pc.proto = new (std::nothrow) mfa_model(*md);
+    if (pc.proto) {
+      pc.proto->arena = pc.proto->big = nullptr;
+      pc.lay = *lay;
+      for (int a = 0; a < 3; ++a) {
+        pc.cores[a].clear();
+        if (a < lay->dim && lay->core_spans[a]) pc.cores[a].assign(lay->core_spans[a], lay->core_spans[a] + lay->nsub[a]);
+        pc.lay.core_spans[a] = nullptr;
+      }
+      pc.plain = plain;
+      pc.stage_bytes = stage_bytes;
+      pc.tp = tp;
+      h->plan_valid = true;
+    }
   }
   *out = md;
   return MFA_OK;

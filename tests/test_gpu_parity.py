@@ -359,3 +359,43 @@ def test_overlap_sweep_on_gpu():
                 assert rel_diff(P, ref) <= 1e-11
         finally:
             g.close()
+
+
+def test_repeat_encode_reuses_layout_plan():
+    """A handle keeps the host products of its latest layout; encoding the same
+    layout again (device or host data, with other layouts and data in between)
+    gives the same control points bit for bit as a fresh handle, and a
+    converged fit still matches the oracle."""
+    import torch
+    QA = inputs.gauss_3d((40, 36, 33), seed=7, dtype=np.float32)
+    QB = inputs.gauss_3d((40, 36, 33), seed=8, dtype=np.float32)
+    lay = mfa.make_layout(3, 3, [40, 36, 33], [10, 9, 8], [2, 2, 1], [2, 2, 2], mfa.MFA_PREC_MIXED)
+    other = mfa.make_layout(3, 3, [40, 36, 33], [9, 9, 8], [2, 1, 2], [1, 2, 2], mfa.MFA_PREC_MIXED)
+
+    def fit(h, Q, layout, on_device=True):
+        q = torch.from_numpy(Q).cuda() if on_device else Q
+        m = h.encode(q, layout)
+        m.iterate(40, 1e-12)
+        P = m.ctrl()
+        m.free()
+        return P
+
+    fresh, fresh2 = mfa.Handle(0), mfa.Handle(0)
+    try:
+        ref_A, ref_B = fit(fresh, QA, lay), fit(fresh2, QB, lay)
+    finally:
+        fresh.close()
+        fresh2.close()
+    h = mfa.Handle(0)
+    try:
+        assert np.array_equal(fit(h, QA, lay), ref_A)
+        assert np.array_equal(fit(h, QB, lay), ref_B)           # same layout, other data
+        fit(h, QA, other)                                        # another layout in between
+        assert np.array_equal(fit(h, QA, lay), ref_A)
+        assert np.array_equal(fit(h, QA, lay, on_device=False), ref_A)  # host data: staged copy in the pool
+        assert np.array_equal(fit(h, QA, lay, on_device=False), ref_A)
+        prob = oracle_problem(QA.astype(np.float64), 3, [10, 9, 8], [2, 2, 1], 2)
+        ref = O.schwarz_solve(prob, QA.astype(np.float64), max_iters=40, tol_dP=1e-12)
+        assert rel_diff(ref_A, ref["P"]) <= TOL_FP64
+    finally:
+        h.close()
