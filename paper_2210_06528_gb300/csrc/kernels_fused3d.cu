@@ -8,6 +8,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <cstring>
 
@@ -81,6 +82,16 @@ __device__ __forceinline__ float to_f(TQ x) {
 // compensated (TwoSum) accumulation.
 // ---------------------------------------------------------------------------
 
+constexpr int kProjMaxSplit = 8;  // units per window along z, at most
+
+// First plane of unit b of a window of m2 planes cut into K units of whole
+// batches of zb planes (unit K ends at m2).
+__host__ __device__ inline int proj_unit_start(int m2, int zb, int K, int b) {
+  const int nbat = (m2 + zb - 1) / zb;
+  const int z = zb * ((b * nbat) / K);
+  return b >= K || z > m2 ? m2 : z;
+}
+
 struct Proj3dArgs {
   LayoutDev L;
   const long long* offL;
@@ -92,6 +103,10 @@ struct Proj3dArgs {
   int n0, n1;    // largest L along x and y
   const AxisOp* inst;  // independent fits: the projection operand of every instance (data offset, strides)
   const int* order;    // CTA -> subdomain / instance (largest first), or null
+  int ksplit;          // units per window along z (CTA b: subdomain b % nsub, unit b / nsub)
+  ff* zpart;           // partial sums of the z-control points two units share (ksplit > 1)
+  unsigned* zctr;      // units finished per subdomain (zeroed before the launch)
+  int pstride;         // stride of a z-control point's (x, y) pairs in zpart
 };
 
 // Shared-memory carve-up of the projection, used by the kernel and the launcher.
@@ -254,13 +269,21 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
   static_assert(NPAIR % 2 == 0, "pairs come in twos");
   extern __shared__ __align__(128) unsigned char smem[];
   const LayoutDev& L = A.L;
-  const int s = A.order ? A.order[blockIdx.x] : blockIdx.x;
+  const int K = A.ksplit;
+  const int s = A.order ? A.order[blockIdx.x] : (int)(blockIdx.x % (unsigned)L.nsub);
+  const int kunit = A.order ? 0 : (int)(blockIdx.x / (unsigned)L.nsub);
   int s0, s1, s2;
   sub_pieces(L, s, s0, s1, s2);
   const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];
   const int m0 = bx.m, m1 = by.m, m2 = bz.m;
   const int n0 = bx.nL, n1 = by.nL, n2 = bz.nL;
   const int zb = A.zb, BX = A.bx, BY = A.by;
+  // the window's planes split into K units of whole batches (the host checks
+  // that every unit keeps more than P+1 knot spans); this CTA takes unit
+  // kunit, planes [zbnd[k], zbnd[k+1])
+  __shared__ int zbnd[kProjMaxSplit + 1];
+  __shared__ int last_unit;
+  if (threadIdx.x < K + 1) zbnd[threadIdx.x] = proj_unit_start(m2, zb, K, threadIdx.x);
   // window origin in the data: the subdomain's corner of the one grid, or
   // (independent fits) the instance's own grid at its offset and strides
   long long M0 = L.M[0], M01 = L.M[0] * L.M[1];
@@ -292,13 +315,15 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem + lay.bar);
   const unsigned box_bytes = (unsigned)(zb * BY * BX * 4);
 
+  __syncthreads();  // unit bounds
+  const int za = zbnd[kunit], zend = zbnd[kunit + 1];
   if constexpr (TMA) {
     if (threadIdx.x == 0) {
       mbar_init(bar, 1);
-      tma_load_box(&tmq, Qs, bar, xa, wy, wz, box_bytes);
+      tma_load_box(&tmq, Qs, bar, xa, wy, wz + za, box_bytes);
     }
   } else {
-    stage_rows<TQ>(Qs, Q, M0, M01, xa, wy, wz, min(zb, m2), m1, BX, BY);
+    stage_rows<TQ>(Qs, Q, M0, M01, xa, wy, wz + za, min(zb, zend - za), m1, BX, BY);
   }
 
   // basis tables: x by staged position (zero outside the window and in the
@@ -351,10 +376,21 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
   bool bad = false;
   unsigned phase = 0;
   __syncthreads();     // tables written, barrier initialised
-  int curz = spz[0];   // z-control point held in ring entry 0
+  int curz = spz[za];  // z-control point held in ring entry 0
+  // z-control points this unit shares with the previous unit ([hlo, hhi],
+  // at most P+1 of them) and with the next ([tlo, ...]): their sums go to
+  // partial slots
+  const int hlo = spz[za], hhi = kunit > 0 ? spz[za - 1] + P : hlo - 1;
+  const int tlo = kunit < K - 1 ? spz[zend] : INT_MAX;
+  const int pst = A.pstride;
+  auto zdst = [&](int c, int q) -> ff* {
+    if (c <= hhi) return A.zpart + ((size_t)(s * (K - 1) + kunit - 1) * 2 + 1) * W * pst + (size_t)(c - hlo) * pst + q;
+    if (c >= tlo) return A.zpart + ((size_t)(s * (K - 1) + kunit) * 2 + 0) * W * pst + (size_t)(c - tlo) * pst + q;
+    return out + (long long)c * npairs + q;
+  };
 
-  for (int z0 = 0; z0 < m2; z0 += zb) {
-    const int nz = min(zb, m2 - z0);
+  for (int z0 = za; z0 < zend; z0 += zb) {
+    const int nz = min(zb, zend - z0);
     bool lost = false;
     if constexpr (TMA) {
       lost = !mbar_wait(bar, phase);
@@ -459,11 +495,11 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
     // before the copy engine's writes, then fetch the next batch behind stage 3
     if constexpr (TMA) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();
-    if (z0 + zb < m2) {
+    if (z0 + zb < zend) {
       if constexpr (TMA) {
         if (threadIdx.x == 0) tma_load_box(&tmq, Qs, bar, xa, wy, wz + z0 + zb, box_bytes);
       } else {
-        stage_rows<TQ>(Qs, Q, M0, M01, xa, wy, wz + z0 + zb, min(zb, m2 - z0 - zb), m1, BX, BY);
+        stage_rows<TQ>(Qs, Q, M0, M01, xa, wy, wz + z0 + zb, min(zb, zend - z0 - zb), m1, BX, BY);
       }
     }
     // ---- stage 3: accumulate the planes into the z ring
@@ -478,12 +514,12 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
             if (q0 < npairs) {
               const ff v = AccFF::finish(ff(ring[j][0].hi.x, ring[j][0].lo.x));
               bad |= !isfinite(v.hi);
-              out[(long long)curz * npairs + q0] = v;
+              *zdst(curz, q0) = v;
             }
             if (q0 + 1 < npairs) {
               const ff v = AccFF::finish(ff(ring[j][0].hi.y, ring[j][0].lo.y));
               bad |= !isfinite(v.hi);
-              out[(long long)curz * npairs + q0 + 1] = v;
+              *zdst(curz, q0 + 1) = v;
             }
           }
 #pragma unroll
@@ -524,14 +560,39 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
         if (q0 < npairs) {
           const ff v = AccFF::finish(ff(ring[j][r].hi.x, ring[j][r].lo.x));
           bad |= !isfinite(v.hi);
-          out[(long long)(curz + r) * npairs + q0] = v;
+          *zdst(curz + r, q0) = v;
         }
         if (q0 + 1 < npairs) {
           const ff v = AccFF::finish(ff(ring[j][r].hi.y, ring[j][r].lo.y));
           bad |= !isfinite(v.hi);
-          out[(long long)(curz + r) * npairs + q0 + 1] = v;
+          *zdst(curz + r, q0 + 1) = v;
         }
       }
+  }
+  if (K > 1) {
+    // the last unit of the subdomain to finish adds the partial sums of every
+    // shared z-control point, the earlier planes' part first
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last_unit = atomicAdd(&A.zctr[s], 1u) == (unsigned)(K - 1);
+    __syncthreads();
+    if (last_unit) {
+      __threadfence();
+      for (int b = 1; b < K; ++b) {
+        const int zp = zbnd[b];
+        const int lo = spz[zp], hi = min(spz[zp - 1] + P, n2 - 1);
+        const ff* before = A.zpart + ((size_t)(s * (K - 1) + b - 1) * 2 + 0) * W * pst;
+        const ff* after = before + (size_t)W * pst;
+        for (int c = max(lo, 0); c <= hi; ++c)
+          for (int q = threadIdx.x; q < npairs; q += NT) {
+            const float2 u = __ldcg(reinterpret_cast<const float2*>(before + (size_t)(c - lo) * pst + q));
+            const float2 w = __ldcg(reinterpret_cast<const float2*>(after + (size_t)(c - lo) * pst + q));
+            const ff v = ff(u.x, u.y) + ff(w.x, w.y);
+            bad |= !isfinite(v.hi);
+            out[(long long)c * npairs + q] = v;
+          }
+      }
+    }
   }
   if (bad && status) atomicExch(status, MFA_ERR_NONFINITE);
 }
@@ -552,6 +613,45 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
+// Row pitch of the staged box: window plus alignment slack, room for the
+// in-place output, a multiple of 4 floats with an odd number of 16-byte chunks.
+static int proj_pitch(int maxm0, int maxn0) {
+  int bx = std::max(maxm0 + 3, 2 * maxn0 + 2);
+  bx = (bx + 3) & ~3;
+  if (bx % 8 == 0) bx += 4;
+  return bx;
+}
+
+int proj3d_planes_per_batch(int P, int maxm0, int maxm1, int maxm2, int maxn0, int maxn1) {
+  // fill the stage-1 rows onto the threads, then shrink until two CTAs fit an
+  // SM (half its shared memory less the per-block reservation)
+  static const size_t two_per_sm = [] {
+    int dev = 0, per_sm = 0, reserved = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    return per_sm > 0 ? (size_t)(per_sm / 2 - reserved) : (size_t)110 * 1024;
+  }();
+  const int bx = proj_pitch(maxm0, maxn0);
+  int zb = std::max(1, std::min(4, kProjThreads / std::max(maxm1, 1)));
+  while (zb > 1 && proj_smem_layout(P + 1, zb, bx, maxm1, maxm2, maxn0, maxn1).total > two_per_sm) zb--;
+  return zb;
+}
+
+bool proj3d_split_ok(int P, int zb, int K, long long M, int nspans, long long k0, int m) {
+  // every unit keeps more than P+1 knot spans, so no z-control point takes
+  // planes of three units (span of point k: floor(k nspans / (M-1)), capped)
+  auto span = [&](long long k) {
+    const long long sk = M == 1 ? 0 : (k * nspans) / (M - 1);
+    return sk > nspans - 1 ? (long long)nspans - 1 : sk;
+  };
+  for (int b = 0; b < K; ++b) {
+    const int z0 = proj_unit_start(m, zb, K, b), z1 = proj_unit_start(m, zb, K, b + 1);
+    if (z1 <= z0 || span(k0 + z1 - 1) - span(k0 + z0) + 1 < P + 2) return false;
+  }
+  return true;
+}
+
 // Returns false when the fused kernel does not cover this layout (the caller
 // then runs the generic per-axis kernels).  `inplace_ok` says every x-window
 // has at least two points per span, so the stage-1 output can overwrite the
@@ -559,7 +659,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 template <typename TQ>
 bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, int maxm1, int maxm2, int maxn0,
                          int maxn1, bool inplace_ok, const TQ* Q, ff* BL, int* status, cudaStream_t st,
-                         const AxisOp* inst, const int* order) {
+                         const AxisOp* inst, const int* order, int ksplit, ff* zpart, unsigned* zctr) {
   const int P = L.ax[0].p;
   if (L.dim != 3 || L.ax[1].p != P || L.ax[2].p != P || !inplace_ok) return false;
   const int npairs = maxn0 * maxn1;
@@ -568,33 +668,18 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
   A.offL = offL;
   A.inst = inst;
   A.order = order;
-  // row pitch: window plus alignment slack, room for the in-place output,
-  // a multiple of 4 floats with an odd number of 16-byte chunks
-  int bx = std::max(maxm0 + 3, 2 * maxn0 + 2);
-  bx = (bx + 3) & ~3;
-  if (bx % 8 == 0) bx += 4;
-  A.bx = bx;
+  A.ksplit = (inst || order || !zpart || !zctr) ? 1 : std::max(1, std::min(ksplit, kProjMaxSplit));
+  A.zpart = zpart;
+  A.zctr = zctr;
+  A.pstride = npairs;
+  A.bx = proj_pitch(maxm0, maxn0);
   A.by = maxm1;
   A.mz = maxm2;
   A.n0 = maxn0;
   A.n1 = maxn1;
-  // planes per batch: fill the stage-1 rows onto the threads
-  A.zb = std::max(1, std::min(4, kProjThreads / std::max(maxm1, 1)));
+  A.zb = proj3d_planes_per_batch(P, maxm0, maxm1, maxm2, maxn0, maxn1);
   const int W = P + 1;
-  // two CTAs per SM when the batch fits: half the SM's shared memory less the
-  // per-block reservation
-  static size_t two_per_sm = [] {
-    int dev = 0, per_sm = 0, reserved = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-    return per_sm > 0 ? (size_t)(per_sm / 2 - reserved) : (size_t)110 * 1024;
-  }();
-  size_t smem = proj_smem_layout(W, A.zb, A.bx, A.by, A.mz, A.n0, A.n1).total;
-  while (smem > two_per_sm && A.zb > 1) {
-    A.zb--;
-    smem = proj_smem_layout(W, A.zb, A.bx, A.by, A.mz, A.n0, A.n1).total;
-  }
+  const size_t smem = proj_smem_layout(W, A.zb, A.bx, A.by, A.mz, A.n0, A.n1).total;
   if (smem > 200 * 1024 || npairs > 8 * kProjThreads) return false;
   // stage 2: a group of 1 << lx_shift lanes covers the x-control points in pairs
   A.lx_shift = 2;
@@ -619,7 +704,8 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
   auto go = [&](auto kernel) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    kernel<<<L.nsub, kProjThreads, smem, st>>>(tmap, A, Q, BL, status);
+    if (A.ksplit > 1) cudaMemsetAsync(zctr, 0, sizeof(unsigned) * L.nsub, st);
+    kernel<<<L.nsub * A.ksplit, kProjThreads, smem, st>>>(tmap, A, Q, BL, status);
   };
 #define MFA_PROJ_NP(PP, NP)                                             \
   if constexpr (sizeof(TQ) == 4) {                                      \
@@ -651,9 +737,11 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
 }
 
 template bool launch_project3d_ff<float>(const LayoutDev&, const long long*, int, int, int, int, int, bool,
-                                         const float*, ff*, int*, cudaStream_t, const AxisOp*, const int*);
+                                         const float*, ff*, int*, cudaStream_t, const AxisOp*, const int*, int, ff*,
+                                         unsigned*);
 template bool launch_project3d_ff<double>(const LayoutDev&, const long long*, int, int, int, int, int, bool,
-                                          const double*, ff*, int*, cudaStream_t, const AxisOp*, const int*);
+                                          const double*, ff*, int*, cudaStream_t, const AxisOp*, const int*, int, ff*,
+                                          unsigned*);
 
 }  // namespace mfa
 

@@ -94,6 +94,9 @@ struct mfa_model {
   // big buffers
   void *BL = nullptr, *X = nullptr, *P = nullptr, *Pprev = nullptr, *S1 = nullptr, *S2 = nullptr;
   float* part = nullptr;  // per-block metric partials of the float-float average
+  int zsplit = 1;         // fused projection: units per window along z
+  ff* zpart = nullptr;    // its partial sums of shared z-control points
+  unsigned* zctr = nullptr;
   bool use_fused = true;     // fused 3-D kernels where they cover the layout
   bool x_inplace_ok = true;  // every x-window has >= 2 points per span (in-place stage-1 output)
   int iters = 0;
@@ -590,7 +593,7 @@ void run_encode(mfa_model* md, const TQ* q) {
              fused = launch_project3d_ff<TQ>(L, md->offL, md->maxm[0], md->maxm[1], md->maxm[2], md->maxnL[0], md->maxnL[1],
                                               md->x_inplace_ok, q, BL, h->d_status, h->stream,
                                               md->batch ? md->ops + (size_t)OP_PROJ0 * ns : nullptr,
-                                              md->batch ? md->order : nullptr));
+                                              md->batch ? md->order : nullptr, md->zsplit, md->zpart, md->zctr));
     }
   }
   if (md->plain) {
@@ -879,6 +882,7 @@ struct TablePlan {
   int n_full_rows = 0, n_part_rows = 0, n_xs = 0;
   size_t host_bytes = 0, tables_bytes = 0;
   size_t o_BL = 0, o_X = 0, o_P = 0, o_Pp = 0, o_S1 = 0, o_S2 = 0, o_part = 0, o_stage = 0, big_bytes = 0;
+  size_t o_zpart = 0, o_zctr = 0;
 };
 
 // Host products of one layout, kept per handle for the most recent layout of
@@ -977,6 +981,8 @@ int bind_model(mfa_handle* h, mfa_model* md, const TablePlan& tp) {
   md->S1 = at_off<char>(md->big, tp.o_S1);
   md->S2 = at_off<char>(md->big, tp.o_S2);
   md->part = at_off<float>(md->big, tp.o_part);
+  md->zpart = md->zsplit > 1 ? at_off<ff>(md->big, tp.o_zpart) : nullptr;
+  md->zctr = md->zsplit > 1 ? at_off<unsigned>(md->big, tp.o_zctr) : nullptr;
   // setup kernels: basis tables, Gram bands, Cholesky factors (FP64), all axes per launch
   {
     int maxnL = 1;
@@ -1076,6 +1082,26 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
   // update partials (3 floats per block of the float-float update) and its
   // row counter
   tp.o_part = bg.take<float>(3 * (size_t)(ns + kAvgListBlocks) + 1);
+  // fused projection: four units per window along z (whole batches of
+  // planes) when every unit keeps more than p+1 knot spans, so that a
+  // z-control point takes planes of two units at most; partial sums of the
+  // shared z-control points (p+1 per side of a cut)
+  md->zsplit = 1;
+  if (!md->batch && md->dim == 3 && md->prec == MFA_PREC_MIXED && md->use_fused) {
+    const AxisHost& az = md->axh[2];
+    constexpr int kUnits = 4;
+    const int zb = proj3d_planes_per_batch(md->degree, md->maxm[0], md->maxm[1], md->maxm[2], md->maxnL[0],
+                                           md->maxnL[1]);
+    bool ok = true;
+    for (const AxisSub& sb : az.subs)
+      ok = ok && proj3d_split_ok(az.p, zb, kUnits, az.M, az.nspans, sb.k0, sb.m);
+    if (ok) md->zsplit = kUnits;
+  }
+  if (md->zsplit > 1) {
+    tp.o_zpart =
+        bg.take<ff>((size_t)ns * (md->zsplit - 1) * 2 * (md->degree + 1) * md->maxnL[0] * md->maxnL[1]);
+    tp.o_zctr = bg.take<unsigned>(ns);
+  }
   // host data staging: the data are copied into the pool before use
   tp.o_stage = stage_bytes ? bg.take<char>(stage_bytes) : 0;
   tp.big_bytes = bg.used;

@@ -399,3 +399,21 @@ def test_repeat_encode_reuses_layout_plan():
         assert rel_diff(ref_A, ref["P"]) <= TOL_FP64
     finally:
         h.close()
+
+
+def test_fused_projection_split_along_z():
+    """Windows with enough knot spans along z are projected in four units per
+    window (two CTAs may share a z-control point, their partial sums added by
+    the last unit): converged control points within 1e-9 of the oracle's."""
+    Q = inputs.gauss_3d((28, 24, 192), seed=11, dtype=np.float32)  # x, y, z sizes; 26 z-spans per window
+    Qd = Q.astype(np.float64)
+    nspans, nsub, delta = [7, 6, 48], [1, 1, 2], 2
+    prob = oracle_problem(Qd, 3, nspans, nsub, delta)
+    ref = O.schwarz_solve(prob, Qd, max_iters=60, tol_dP=1e-10)
+    g = GpuRun(Q, 3, nspans, nsub, delta, precision=mfa.MFA_PREC_MIXED)
+    try:
+        rc, rep = g.iterate(60, 1e-10)
+        assert rc == mfa.MFA_OK and rep.iters == ref["iters"]
+        assert rel_diff(g.ctrl(), ref["P"]) <= TOL_FP64
+    finally:
+        g.close()
