@@ -552,7 +552,7 @@ def run_gb300(args, wl):
     cpu = cpu_baseline(wl, budget_s=args.cpu_budget) if world == 1 and not args.no_cpu else None
     line = {"metric": METRIC, "value": value, "unit": "pts/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32x2" if prec == mfa.MFA_PREC_MIXED else "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "float-float" if prec == mfa.MFA_PREC_MIXED else "f64", "data": "synthetic",
             "config": {"workload": wl["name"], "points": M, "control_points": ncp, "precision": wl["precision"],
                        "stop": f"dP_rel <= {wl['tol']:g}", "schwarz_iters": sorted(set(iters_seen)),
                        "l2": "inputs larger than L2" if qbytes > 129e6 else "inputs smaller than L2",

@@ -190,6 +190,27 @@ struct ResidAcc {
     }
   }
   __device__ __forceinline__ double sum2() const { return s2; }
+  // block reduction: warp totals through shared memory, merged by one thread
+  using Red = double;
+  static constexpr int kFields = 4;
+  __device__ __forceinline__ void store(Red* sm, int w, int stride) const {
+    sm[w] = s2;
+    sm[stride + w] = emax;
+    sm[2 * stride + w] = qmin;
+    sm[3 * stride + w] = qmax;
+  }
+  __device__ __forceinline__ void merge(const Red* sm, int w, int stride) {
+    s2 += sm[w];
+    emax = fmax(emax, sm[stride + w]);
+    qmin = fmin(qmin, sm[2 * stride + w]);
+    qmax = fmax(qmax, sm[3 * stride + w]);
+  }
+  __device__ __forceinline__ void out(double* o) const {
+    o[0] = s2;
+    o[1] = emax;
+    o[2] = qmin;
+    o[3] = qmax;
+  }
 };
 
 template <>
@@ -213,6 +234,27 @@ struct ResidAcc<ff, float> {
     }
   }
   __device__ __forceinline__ double sum2() const { return (double)s2.hi + (double)s2.lo; }
+  using Red = float;
+  static constexpr int kFields = 5;
+  __device__ __forceinline__ void store(Red* sm, int w, int stride) const {
+    sm[w] = s2.hi;
+    sm[stride + w] = s2.lo;
+    sm[2 * stride + w] = emax;
+    sm[3 * stride + w] = qmin;
+    sm[4 * stride + w] = qmax;
+  }
+  __device__ __forceinline__ void merge(const Red* sm, int w, int stride) {
+    s2 += ff(sm[w], sm[stride + w]);
+    emax = fmaxf(emax, sm[2 * stride + w]);
+    qmin = fminf(qmin, sm[3 * stride + w]);
+    qmax = fmaxf(qmax, sm[4 * stride + w]);
+  }
+  __device__ __forceinline__ void out(double* o) const {
+    o[0] = sum2();
+    o[1] = emax;
+    o[2] = qmin;
+    o[3] = qmax;
+  }
 };
 
 // Batches of independent fits: the last decode axis of a group fused with
@@ -237,21 +279,18 @@ __global__ void k_expand_residual_tiles(LayoutDev L, const AxisOp* ops, const T*
     acc.add(q[ov.off + o[0] * ov.st[0] + o[1] * ov.st[1] + o[2] * ov.st[2]], val);
   }
   acc.warp_reduce();
-  __shared__ double red[2][32];  // up to 1024 threads
+  using Acc = ResidAcc<T, TQ>;
+  __shared__ typename Acc::Red red[Acc::kFields * 32];  // up to 1024 threads
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[0][w] = acc.sum2();
-    red[1][w] = (double)acc.emax;
-  }
+  if (lane == 0) acc.store(red, w, 32);
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0.0, b = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-      a += red[0][k];
-      b = fmax(b, red[1][k]);
-    }
-    tile_part[2 * blockIdx.x] = a;
-    tile_part[2 * blockIdx.x + 1] = b;
+    Acc tot;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot.merge(red, k, 32);
+    double o[4];
+    tot.out(o);
+    tile_part[2 * blockIdx.x] = o[0];
+    tile_part[2 * blockIdx.x + 1] = o[1];
   }
 }
 
@@ -319,29 +358,18 @@ __global__ void k_expand_residual(LayoutDev L, const AxisOp* opp, const T* __res
     unflatten(idx, op.out.n, o);
     acc.add(q[idx], expand_one<T, AXIS>(L.ax[AXIS], op, o, in));
   }
-  __shared__ double sh[4][32];
   acc.warp_reduce();
+  using Acc = ResidAcc<T, TQ>;
+  __shared__ typename Acc::Red sh[Acc::kFields * 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    sh[0][wid] = acc.sum2();
-    sh[1][wid] = (double)acc.emax;
-    sh[2][wid] = (double)acc.qmin;
-    sh[3][wid] = (double)acc.qmax;
-  }
+  if (lane == 0) acc.store(sh, wid, 32);
   __syncthreads();
   if (threadIdx.x == 0) {
-    const int nw = blockDim.x >> 5;
-    double a = 0.0, b = 0.0, c = INFINITY, d = -INFINITY;
-    for (int i = 0; i < nw; ++i) {
-      a += sh[0][i];
-      b = fmax(b, sh[1][i]);
-      c = fmin(c, sh[2][i]);
-      d = fmax(d, sh[3][i]);
-    }
-    partials[4 * blockIdx.x + 0] = a;
-    partials[4 * blockIdx.x + 1] = b;
-    partials[4 * blockIdx.x + 2] = c;
-    partials[4 * blockIdx.x + 3] = d;
+    Acc tot;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) tot.merge(sh, i, 32);
+    double o[4];
+    tot.out(o);
+    for (int k = 0; k < 4; ++k) partials[4 * blockIdx.x + k] = o[k];
   }
 }
 

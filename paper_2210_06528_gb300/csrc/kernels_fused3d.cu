@@ -786,9 +786,12 @@ __host__ __device__ inline DecSmem dec_smem_layout(int W, int ncx, int ncy, int 
   return d;
 }
 
-// a / d for 0 <= a < 2^22 and a divisor d > 0 given as rcp = 1/d: (a + 1/2) / d
-// lies at least 1/(2d) from an integer, far beyond the product's rounding
-__device__ __forceinline__ int div_small(int a, float rcp) { return (int)(((float)a + 0.5f) * rcp); }
+// floor(a / d) for 0 <= a < 1024 and 0 < d <= 128 by a multiply and a shift:
+// with m = ceil(2^17 / d) the excess m d - 2^17 is below d <= 2^17 / 1024, so
+// a m / 2^17 stays within 1/d above a / d and never crosses the next integer
+// (integer only: no int/float conversions, which share the FP64 pipe)
+__device__ __forceinline__ unsigned div_magic(unsigned d) { return ((1u << 17) + d - 1) / d; }
+__device__ __forceinline__ int div_small(int a, unsigned m) { return (int)(((unsigned)a * m) >> 17); }
 
 template <int P, typename V, typename TQ, typename TOut, bool RESID>
 __global__ void __launch_bounds__(kDecThreads, (P >= 4 ? 3 : 4)) k_decode3d(LayoutDev L, const V* __restrict__ Pc,
@@ -890,7 +893,7 @@ __global__ void __launch_bounds__(kDecThreads, (P >= 4 ? 3 : 4)) k_decode3d(Layo
       }
       const int szz = sz[z];
       const int npr = ncxp >> 1, nit = ncy * npr;
-      const float rcp = 1.f / (float)npr;
+      const unsigned rcp = div_magic(npr);  // nit < 1024, npr <= 128 (tiles of at most 64 + P x-control points)
       const int pst = ncy * ncxp;  // plane stride of the block
       for (int it = lane; it < nit; it += 64) {
         const int it2 = min(it + 32, nit - 1);
@@ -937,7 +940,7 @@ __global__ void __launch_bounds__(kDecThreads, (P >= 4 ? 3 : 4)) k_decode3d(Layo
       }
       const int ra = sy[ya], rb = sy[yb];
       const int nit = nz * ncx;
-      const float rcp = 1.f / (float)ncx;
+      const unsigned rcp = div_magic(ncx);  // nit = nz * ncx < 1024, ncx <= 128
       for (int it = tl; it < nit; it += 2 * kPer) {
         const int it2 = min(it + kPer, nit - 1);
         const int za = div_small(it, rcp), ca = it - za * ncx;
@@ -1021,10 +1024,11 @@ __global__ void __launch_bounds__(kDecThreads, (P >= 4 ? 3 : 4)) k_decode3d(Layo
     }
   }
   if constexpr (RESID) {
-    // block reduction into this tile's slot.  The extrema are exact in FP32;
-    // the sum of squares crosses the warp as a float-float, so every lane
-    // stays on the FP32 pipes (the FP64 pipe is a small fraction of them and
-    // all warps reach this point together); FP64 only for the 8 warp sums.
+    // block reduction into this tile's slot.  The extrema are exact in FP32
+    // and the sum of squares moves as a float-float, so the whole reduction
+    // runs on the FP32 pipes; only the four results are widened to FP64 (the
+    // FP64 pipe of this GPU is a small fraction of the FP32 ones, and every
+    // tile ends here)
     ff fs2(s2, 0.f);
     for (int o = 16; o > 0; o >>= 1) {
       const ff other(__shfl_down_sync(0xffffffffu, fs2.hi, o), __shfl_down_sync(0xffffffffu, fs2.lo, o));
@@ -1033,24 +1037,26 @@ __global__ void __launch_bounds__(kDecThreads, (P >= 4 ? 3 : 4)) k_decode3d(Layo
       qmin = fminf(qmin, __shfl_down_sync(0xffffffffu, qmin, o));
       qmax = fmaxf(qmax, __shfl_down_sync(0xffffffffu, qmax, o));
     }
-    __shared__ double red[4][kDecThreads / 32];
+    __shared__ float red[5][kDecThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
-      red[0][wid] = (double)fs2.hi + (double)fs2.lo;
-      red[1][wid] = emax;
-      red[2][wid] = qmin;
-      red[3][wid] = qmax;
+      red[0][wid] = fs2.hi;
+      red[1][wid] = fs2.lo;
+      red[2][wid] = emax;
+      red[3][wid] = qmin;
+      red[4][wid] = qmax;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double a = 0.0, b = 0.0, c = INFINITY, d = -INFINITY;
+      ff a(0.f, 0.f);
+      float b = 0.f, c = INFINITY, d = -INFINITY;
       for (int w = 0; w < kDecThreads / 32; ++w) {
-        a += red[0][w];
-        b = fmax(b, red[1][w]);
-        c = fmin(c, red[2][w]);
-        d = fmax(d, red[3][w]);
+        a = a + ff(red[0][w], red[1][w]);
+        b = fmaxf(b, red[2][w]);
+        c = fminf(c, red[3][w]);
+        d = fmaxf(d, red[4][w]);
       }
-      partials[4 * (long long)tile + 0] = a;
+      partials[4 * (long long)tile + 0] = (double)a.hi + (double)a.lo;
       partials[4 * (long long)tile + 1] = b;
       partials[4 * (long long)tile + 2] = c;
       partials[4 * (long long)tile + 3] = d;
