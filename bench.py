@@ -217,6 +217,26 @@ def window_sizes(M, nspans, S, delta, p):
 FF_OPS_F, FF_OPS_V = 11, 12
 
 
+# DRAM bytes (read + write) of one fused 3-D projection launch, from one ncu
+# capture of the current kernel on the 384^3 case (6x6x6 windows of the 512^3
+# workload's shape): 290.9 MB read + 55.1 MB written.  The traffic grows with
+# the number of windows at a fixed window shape, so a workload of W such
+# windows moves W / 216 times that.  Kept for the kernel it was taken on.
+PROJECTION_TRAFFIC_384 = {"bytes": (290.871296 + 55.123968) * 1e6, "windows": 216}
+
+
+def projection_traffic(wl):
+    """DRAM bytes per launch scaled from the 384^3 capture, or None when the
+    workload's windows differ in shape from the captured ones."""
+    npts, nsub, nspans = wl["npts"], wl["nsub"], wl["nspans"]
+    same = (len(npts) == 3 and wl["p"] == 3 and wl["delta"] == 2 and wl["precision"] == "mixed"
+            and all(n == 64 * k and sp == 24 * k for n, sp, k in zip(npts, nspans, nsub)))
+    if not same:
+        return None
+    windows = nsub[0] * nsub[1] * nsub[2]
+    return PROJECTION_TRAFFIC_384["bytes"] * windows / PROJECTION_TRAFFIC_384["windows"]
+
+
 def projection_ops(wl):
     """Algorithmic FP32 operations of one 3-D float-float projection launch:
     per window point (P+1) float x float-float multiply-adds on the first
@@ -544,7 +564,10 @@ def run_gb300(args, wl):
             ach = ops / (ms_per * 1e-3) / 1e12
             pk = alu_peak_tops(mhz)
             roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                    "traffic": None, "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src})",
+                    "traffic": projection_traffic(wl),
+                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 384^3 capture, "
+                                      "scaled by the number of windows of the same shape",
+                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src})",
                     "op_convention": "one FP32 add, mul or fma instruction = 1 op",
                     "algorithmic_ops_per_launch": ops, "ms_per_launch": ms_per, "hbm_view": hbm}
     if rank != 0:
