@@ -401,18 +401,27 @@ def test_repeat_encode_reuses_layout_plan():
         h.close()
 
 
-def test_fused_projection_split_along_z():
-    """Windows with enough knot spans along z are projected in four units per
-    window (two CTAs may share a z-control point, their partial sums added by
-    the last unit): converged control points within 1e-9 of the oracle's."""
-    Q = inputs.gauss_3d((28, 24, 192), seed=11, dtype=np.float32)  # x, y, z sizes; 26 z-spans per window
+@pytest.mark.parametrize("p,npts,nspans,nsub", [
+    (3, (28, 24, 192), (7, 6, 48), (1, 1, 2)),
+    (2, (28, 24, 192), (7, 6, 48), (1, 1, 2)),
+    (4, (30, 32, 160), (8, 8, 40), (1, 2, 1)),
+    (5, (60, 36, 264), (12, 6, 44), (2, 1, 1)),
+])
+def test_fused_projection_split_along_z(p, npts, nspans, nsub):
+    """Windows with enough knot spans along z (26 to 44 here) are projected in
+    four units per window of whole plane batches (two CTAs may share a
+    z-control point; their partial sums are added by the last unit):
+    converged control points within 1e-9 of the oracle's, at even and odd
+    numbers of basis lanes.  The stop is dP_rel <= 1e-9, as in the other
+    mixed-path tests, above the float-float noise of dP."""
+    Q = inputs.gauss_3d(npts, seed=20 + p, dtype=np.float32)  # x, y, z sizes
     Qd = Q.astype(np.float64)
-    nspans, nsub, delta = [7, 6, 48], [1, 1, 2], 2
-    prob = oracle_problem(Qd, 3, nspans, nsub, delta)
-    ref = O.schwarz_solve(prob, Qd, max_iters=60, tol_dP=1e-10)
-    g = GpuRun(Q, 3, nspans, nsub, delta, precision=mfa.MFA_PREC_MIXED)
+    delta = 2
+    prob = oracle_problem(Qd, p, list(nspans), list(nsub), delta)
+    ref = O.schwarz_solve(prob, Qd, max_iters=60, tol_dP=1e-9)
+    g = GpuRun(Q, p, list(nspans), list(nsub), delta, precision=mfa.MFA_PREC_MIXED)
     try:
-        rc, rep = g.iterate(60, 1e-10)
+        rc, rep = g.iterate(60, 1e-9)
         assert rc == mfa.MFA_OK and rep.iters == ref["iters"]
         assert rel_diff(g.ctrl(), ref["P"]) <= TOL_FP64
     finally:
