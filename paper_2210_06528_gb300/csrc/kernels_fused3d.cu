@@ -417,20 +417,23 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
       int cur = spx[0];
       for (int j = 0; j < nq4; ++j) {
         const float4 q4 = reinterpret_cast<const float4*>(row)[j];
+        const int4 s4 = reinterpret_cast<const int4*>(spx)[j];  // spans of the chunk's four points
         const float qv[4] = {q4.x, q4.y, q4.z, q4.w};
+        const int sv[4] = {s4.x, s4.y, s4.z, s4.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int i = 4 * j + u;
-          const int sk = spx[i];
-          while (cur < sk) {
-            if (cur >= 0 && cur < n0) emit_x_cp(row, cur, ff2_lane<0>(win));
-            ff2_shift<W>(win);
-            ++cur;
-          }
+          // the point's basis rows are read before a control point is emitted,
+          // so their latency overlaps the emission
           float2 nh[NPR], nn[NPR], nl[NPR];
           load_pairs<NPR>(txh + i * WP, nh);
           load_pairs<NPR>(txn + i * WP, nn);
           load_pairs<NPR>(txl + i * WP, nl);
+          while (cur < sv[u]) {
+            if (cur >= 0 && cur < n0) emit_x_cp(row, cur, ff2_lane<0>(win));
+            ff2_shift<W>(win);
+            ++cur;
+          }
           const float2 x = dup2(qv[u]);
 #pragma unroll
           for (int k = 0; k < NPR; ++k) ff2_add_f(win[k], nh[k], nn[k], nl[k], x);
