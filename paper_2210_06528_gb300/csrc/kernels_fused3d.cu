@@ -83,6 +83,7 @@ __device__ __forceinline__ float to_f(TQ x) {
 // ---------------------------------------------------------------------------
 
 constexpr int kProjMaxSplit = 8;  // units per window along z, at most
+constexpr int kS2C = 8;           // projection stage 2: x-control points per lane (even)
 
 // First plane of unit b of a window of m2 planes cut into K units of whole
 // batches of zb planes (unit K ends at m2).
@@ -451,13 +452,13 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
     }
     __syncthreads();
     // ---- stage 2 (gather form): one warp-aligned group of lanes per (plane,
-    // y-control point), each lane four adjacent x-control points (two lane
-    // pairs, two independent sums); each output sums its P+1 supporting spans'
-    // rows, so the work per output is even and no row is read for a control
-    // point it does not touch
+    // y-control point), each lane S2C adjacent x-control points (S2C/2 lane
+    // pairs, independent sums sharing each basis read); each output sums its
+    // P+1 supporting spans' rows, so the work per output is even and no row is
+    // read for a control point it does not touch
     {
       const int* ss = L.ax[1].span_start;
-      const int sh = A.lx_shift;                 // lanes per group = 1 << sh >= n0 / 4
+      const int sh = A.lx_shift;                 // lanes per group = 1 << sh >= n0 / S2C
       const int lmask = (1 << sh) - 1;
       const int lx = threadIdx.x & lmask;
       const int gstep = NT >> sh;                // groups advanced per pass
@@ -467,29 +468,37 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
         ++zz;
       }
       for (; zz < nz; ) {
-        if (4 * lx < n0) {
+        if (kS2C * lx < n0) {
           const int g1 = by.l0 + c1;
           const int ys = max(ss[max(g1 - P, 0)] - by.k0, 0);
           const int ye = min(ss[min(g1, L.ax[1].nspans - 1) + 1] - by.k0, m1);
-          const float* colf = Qs + (size_t)zz * BY * BX + 8 * lx;
-          ff2 a0 = ff2_zero(), a1 = ff2_zero();
+          const float* colf = Qs + (size_t)zz * BY * BX + 2 * kS2C * lx;
+          ff2 a[kS2C / 2];
+#pragma unroll
+          for (int k = 0; k < kS2C / 2; ++k) a[k] = ff2_zero();
           for (int y = ys; y < ye; ++y) {
             const float4 nb = ty[y * W + (c1 - spy[y])];
-            const float4 u = *reinterpret_cast<const float4*>(colf + (size_t)y * BX);
-            const float4 v = *reinterpret_cast<const float4*>(colf + (size_t)y * BX + 4);
             const float2 bh = dup2(nb.x), bn = dup2(nb.y), bl = dup2(nb.z);
-            ff2_add_v(a0, bh, bn, bl, make_float2(u.x, u.y), make_float2(u.z, u.w));
-            ff2_add_v(a1, bh, bn, bl, make_float2(v.x, v.y), make_float2(v.z, v.w));
-          }
-          const int o = zz * npp + c1 * n0 + 4 * lx;
-          const ff r[4] = {AccFF::finish(ff(a0.hi.x, a0.lo.x)), AccFF::finish(ff(a0.hi.y, a0.lo.y)),
-                           AccFF::finish(ff(a1.hi.x, a1.lo.x)), AccFF::finish(ff(a1.hi.y, a1.lo.y))};
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
-            if (4 * lx + t < n0) {
-              T2h[o + t] = r[t].hi;
-              T2l[o + t] = r[t].lo;
+            for (int k = 0; k < kS2C / 2; ++k) {
+              const float4 u = *reinterpret_cast<const float4*>(colf + (size_t)y * BX + 4 * k);
+              ff2_add_v(a[k], bh, bn, bl, make_float2(u.x, u.y), make_float2(u.z, u.w));
             }
+          }
+          const int o = zz * npp + c1 * n0 + kS2C * lx;
+#pragma unroll
+          for (int k = 0; k < kS2C / 2; ++k) {
+            if (kS2C * lx + 2 * k < n0) {
+              const ff r = AccFF::finish(ff(a[k].hi.x, a[k].lo.x));
+              T2h[o + 2 * k] = r.hi;
+              T2l[o + 2 * k] = r.lo;
+            }
+            if (kS2C * lx + 2 * k + 1 < n0) {
+              const ff r = AccFF::finish(ff(a[k].hi.y, a[k].lo.y));
+              T2h[o + 2 * k + 1] = r.hi;
+              T2l[o + 2 * k + 1] = r.lo;
+            }
+          }
         }
         c1 += gstep;
         while (c1 >= n1) {
@@ -623,8 +632,8 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // Row pitch of the staged box: window plus alignment slack, room for the
 // in-place output, a multiple of 4 floats with an odd number of 16-byte chunks.
 static int proj_pitch(int maxm0, int maxn0) {
-  // stage 2 reads the control points of a row in 32-byte groups of four
-  int bx = std::max(maxm0 + 3, 8 * ((maxn0 + 3) / 4));
+  // stage 2 reads the control points of a row in groups of kS2C (2 floats each)
+  int bx = std::max(maxm0 + 3, 2 * kS2C * ((maxn0 + kS2C - 1) / kS2C));
   bx = (bx + 3) & ~3;
   if (bx % 8 == 0) bx += 4;
   return bx;
@@ -689,9 +698,9 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
   const int W = P + 1;
   const size_t smem = proj_smem_layout(W, A.zb, A.bx, A.by, A.mz, A.n0, A.n1).total;
   if (smem > 200 * 1024 || npairs > 8 * kProjThreads) return false;
-  // stage 2: a group of 1 << lx_shift lanes covers the x-control points in fours
-  A.lx_shift = 1;
-  while ((1 << A.lx_shift) < (maxn0 + 3) / 4) ++A.lx_shift;
+  // stage 2: a group of 1 << lx_shift lanes covers the x-control points, kS2C per lane
+  A.lx_shift = 0;
+  while ((1 << A.lx_shift) < (maxn0 + kS2C - 1) / kS2C) ++A.lx_shift;
   if ((1 << A.lx_shift) > kProjThreads) return false;
 
   // the tensor copy takes FP32 data on a 16-byte aligned base with rows a
