@@ -518,10 +518,28 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
         stage_rows<TQ>(Qs, Q, M0, M01, xa, wy, wz + z0 + zb, min(zb, zend - z0 - zb), m1, BX, BY);
       }
     }
-    // ---- stage 3: accumulate the planes into the z ring
+    // ---- stage 3: accumulate the planes into the z ring (the plane's basis
+    // row and stage-2 values are read before a z-control point is emitted)
     for (int zz = 0; zz < nz; ++zz) {
       const int kz = z0 + zz;
       const int sz = spz[kz];
+      float2 zh[W], zn[W], zl[W];
+#pragma unroll
+      for (int r = 0; r < W; ++r) {
+        const float4 b = tz[kz * W + r];
+        zh[r] = dup2(b.x);
+        zn[r] = dup2(b.y);
+        zl[r] = dup2(b.z);
+      }
+      const float* th = T2h + zz * npp;
+      const float* tl = T2l + zz * npp;
+      float2 xh[NS], xl[NS];
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        const int q0 = min(2 * (threadIdx.x + j * NT), npp - 2);
+        xh[j] = *reinterpret_cast<const float2*>(th + q0);
+        xl[j] = *reinterpret_cast<const float2*>(tl + q0);
+      }
       while (curz < sz) {
 #pragma unroll
         for (int j = 0; j < NS; ++j) {
@@ -544,24 +562,12 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
         }
         ++curz;
       }
-      float2 zh[W], zn[W], zl[W];
-#pragma unroll
-      for (int r = 0; r < W; ++r) {
-        const float4 b = tz[kz * W + r];
-        zh[r] = dup2(b.x);
-        zn[r] = dup2(b.y);
-        zl[r] = dup2(b.z);
-      }
-      const float* th = T2h + zz * npp;
-      const float* tl = T2l + zz * npp;
 #pragma unroll
       for (int j = 0; j < NS; ++j) {
         const int q0 = 2 * (threadIdx.x + j * NT);
         if (q0 < npairs) {
-          const float2 xh = *reinterpret_cast<const float2*>(th + q0);
-          const float2 xl = *reinterpret_cast<const float2*>(tl + q0);
 #pragma unroll
-          for (int r = 0; r < W; ++r) ff2_add_v(ring[j][r], zh[r], zn[r], zl[r], xh, xl);
+          for (int r = 0; r < W; ++r) ff2_add_v(ring[j][r], zh[r], zn[r], zl[r], xh[j], xl[j]);
         }
       }
     }
