@@ -430,7 +430,9 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
           load_pairs<NPR>(txh + i * WP, nh);
           load_pairs<NPR>(txn + i * WP, nn);
           load_pairs<NPR>(txl + i * WP, nl);
-          while (cur < sv[u]) {
+          // a point starts at most one new span (every span of a valid layout
+          // holds a data point; the host checks it for the fused path)
+          if (cur < sv[u]) {
             if (cur >= 0 && cur < n0) emit_x_cp(row, cur, ff2_lane<0>(win));
             ff2_shift<W>(win);
             ++cur;

@@ -1231,15 +1231,19 @@ int create_model(mfa_handle* h, const mfa_layout* lay, bool plain, size_t stage_
     // the fused projection's stage-1 output of control point c (floats
     // 4(c/2) + c%2 and 4(c/2) + c%2 + 2 of the staged row) is written while
     // the 16-byte chunk holding the first point of span c+1 is in registers;
-    // it must not reach past that chunk
+    // it must not reach past that chunk; and consecutive points advance at
+    // most one span (stage 1 emits at most one control point per point)
     const AxisHost& ax = md->axh[0];
     for (const AxisSub& sb : ax.subs) {
+      long long prev = -1;
       for (int k = 0; k < sb.m && md->x_inplace_ok; ++k) {
         const long long gk = sb.k0 + k;
         long long sk = ax.M == 1 ? 0 : (gk * ax.nspans) / (ax.M - 1);
         if (sk > ax.nspans - 1) sk = ax.nspans - 1;
         const long long cmax = sk - sb.l0 - 1;  // highest CP emitted before reading point k
         if (cmax >= 0 && stage1_reach(cmax) > 4 * (k / 4) + 3) md->x_inplace_ok = false;
+        if (k > 0 && sk - prev > 1) md->x_inplace_ok = false;
+        prev = sk;
       }
     }
   }
@@ -2044,11 +2048,14 @@ int build_batch_group(mfa_batch* b, int d, int p, const std::vector<int>& mem, m
   md->x_inplace_ok = true;
   for (const AxisSub& sb : md->axh[0].subs) {
     const long long Mi = sb.m, nsi = sb.w1 - sb.w0;
+    long long prev = -1;
     for (long long k = 0; k < Mi && md->x_inplace_ok; ++k) {
       long long sk = Mi == 1 ? 0 : (k * nsi) / (Mi - 1);
       if (sk > nsi - 1) sk = nsi - 1;
       const long long cmax = sk - 1;
       if (cmax >= 0 && stage1_reach(cmax) > 4 * (k / 4) + 3) md->x_inplace_ok = false;
+      if (k > 0 && sk - prev > 1) md->x_inplace_ok = false;  // one span per point at most
+      prev = sk;
     }
   }
   rc = build_batch_tiles(h, md, kContractThreads, kSolveThreads, kExpandThreads);
