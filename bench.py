@@ -219,10 +219,10 @@ FF_OPS_F, FF_OPS_V = 11, 12
 
 # DRAM bytes (read + write) of one fused 3-D projection launch, from one ncu
 # capture of the current kernel on the 384^3 case (6x6x6 windows of the 512^3
-# workload's shape): 290.9 MB read + 55.1 MB written.  The traffic grows with
+# workload's shape): 290.2 MB read + 55.9 MB written.  The traffic grows with
 # the number of windows at a fixed window shape, so a workload of W such
 # windows moves W / 216 times that.  Kept for the kernel it was taken on.
-PROJECTION_TRAFFIC_384 = {"bytes": (290.871296 + 55.123968) * 1e6, "windows": 216}
+PROJECTION_TRAFFIC_384 = {"bytes": (290.206720 + 55.914752) * 1e6, "windows": 216}
 
 
 def projection_traffic(wl):
