@@ -108,6 +108,7 @@ struct Proj3dArgs {
   ff* zpart;           // partial sums of the z-control points two units share (ksplit > 1)
   unsigned* zctr;      // units finished per subdomain (zeroed before the launch)
   int pstride;         // stride of a z-control point's (x, y) pairs in zpart
+  const int2* units;   // when set, CTA b takes unit units[b] = (subdomain, unit along z)
 };
 
 // Shared-memory carve-up of the projection, used by the kernel and the launcher.
@@ -271,8 +272,15 @@ __global__ void __launch_bounds__(NT, 2) k_project3d_ff(const __grid_constant__ 
   extern __shared__ __align__(128) unsigned char smem[];
   const LayoutDev& L = A.L;
   const int K = A.ksplit;
-  const int s = A.order ? A.order[blockIdx.x] : (int)(blockIdx.x % (unsigned)L.nsub);
-  const int kunit = A.order ? 0 : (int)(blockIdx.x / (unsigned)L.nsub);
+  int s, kunit;
+  if (A.units) {
+    const int2 u = A.units[blockIdx.x];
+    s = u.x;
+    kunit = u.y;
+  } else {
+    s = A.order ? A.order[blockIdx.x] : (int)(blockIdx.x % (unsigned)L.nsub);
+    kunit = A.order ? 0 : (int)(blockIdx.x / (unsigned)L.nsub);
+  }
   int s0, s1, s2;
   sub_pieces(L, s, s0, s1, s2);
   const AxisSub bx = L.ax[0].subs[s0], by = L.ax[1].subs[s1], bz = L.ax[2].subs[s2];
@@ -663,6 +671,8 @@ int proj3d_planes_per_batch(int P, int maxm0, int maxm1, int maxm2, int maxn0, i
   return zb;
 }
 
+int proj3d_unit_start(int m2, int zb, int K, int b) { return proj_unit_start(m2, zb, K, b); }
+
 bool proj3d_split_ok(int P, int zb, int K, long long M, int nspans, long long k0, int m) {
   // every unit keeps more than P+1 knot spans, so no z-control point takes
   // planes of three units (span of point k: floor(k nspans / (M-1)), capped)
@@ -684,7 +694,8 @@ bool proj3d_split_ok(int P, int zb, int K, long long M, int nspans, long long k0
 template <typename TQ>
 bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, int maxm1, int maxm2, int maxn0,
                          int maxn1, bool inplace_ok, const TQ* Q, ff* BL, int* status, cudaStream_t st,
-                         const AxisOp* inst, const int* order, int ksplit, ff* zpart, unsigned* zctr) {
+                         const AxisOp* inst, const int* order, int ksplit, ff* zpart, unsigned* zctr,
+                         const int2* units, int nunits, bool first) {
   const int P = L.ax[0].p;
   if (L.dim != 3 || L.ax[1].p != P || L.ax[2].p != P || !inplace_ok) return false;
   const int npairs = maxn0 * maxn1;
@@ -697,6 +708,8 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
   A.zpart = zpart;
   A.zctr = zctr;
   A.pstride = npairs;
+  A.units = A.ksplit > 1 ? units : nullptr;
+  if (A.units && nunits <= 0) return true;  // no unit in this part
   A.bx = proj_pitch(maxm0, maxn0);
   A.by = maxm1;
   A.mz = maxm2;
@@ -729,8 +742,8 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
   auto go = [&](auto kernel) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (A.ksplit > 1) cudaMemsetAsync(zctr, 0, sizeof(unsigned) * L.nsub, st);
-    kernel<<<L.nsub * A.ksplit, kProjThreads, smem, st>>>(tmap, A, Q, BL, status);
+    if (A.ksplit > 1 && first) cudaMemsetAsync(zctr, 0, sizeof(unsigned) * L.nsub, st);
+    kernel<<<A.units ? nunits : L.nsub * A.ksplit, kProjThreads, smem, st>>>(tmap, A, Q, BL, status);
   };
 #define MFA_PROJ_NP(PP, NP)                                             \
   if constexpr (sizeof(TQ) == 4) {                                      \
@@ -763,10 +776,10 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
 
 template bool launch_project3d_ff<float>(const LayoutDev&, const long long*, int, int, int, int, int, bool,
                                          const float*, ff*, int*, cudaStream_t, const AxisOp*, const int*, int, ff*,
-                                         unsigned*);
+                                         unsigned*, const int2*, int, bool);
 template bool launch_project3d_ff<double>(const LayoutDev&, const long long*, int, int, int, int, int, bool,
                                           const double*, ff*, int*, cudaStream_t, const AxisOp*, const int*, int, ff*,
-                                          unsigned*);
+                                          unsigned*, const int2*, int, bool);
 
 }  // namespace mfa
 

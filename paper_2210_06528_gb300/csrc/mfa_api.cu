@@ -22,6 +22,9 @@ using namespace mfa;
 
 namespace {
 struct PlanCache;
+// host data of a fused 3-D encode is copied in this many z-slabs, the
+// projection units of each slab launched as it lands
+constexpr int kSlabs = 8;
 }  // namespace
 
 struct mfa_handle {
@@ -36,6 +39,8 @@ struct mfa_handle {
   char* h_stage = nullptr;                  // pinned staging of layout tables (grown as needed)
   size_t h_stage_cap = 0;
   cudaEvent_t stage_done = nullptr;         // the last upload from h_stage has been read
+  cudaStream_t copy_stream = nullptr;       // host data copied slab by slab beside the projection
+  std::vector<cudaEvent_t> slab_ev;         // slab landed (copy stream) / buffers allocated (handle stream)
   PlanCache* plan = nullptr;                // host products of the most recent single-model layout
   void (*plan_free)(PlanCache*) = nullptr;  // its deleter (set with it)
   bool plan_valid = false;                  // plan matches the image in h_stage
@@ -95,6 +100,9 @@ struct mfa_model {
   void *BL = nullptr, *X = nullptr, *P = nullptr, *Pprev = nullptr, *S1 = nullptr, *S2 = nullptr;
   float* part = nullptr;  // per-block metric partials of the float-float average
   int zsplit = 1;         // fused projection: units per window along z
+  const int2* units = nullptr;   // its (subdomain, unit) pairs by the slab their last plane lands in
+  std::vector<int> slab_units;   // units of slabs < t: slab_units[t] (kSlabs + 1 entries)
+  long long slab_planes = 0;     // z-planes per slab of host data
   ff* zpart = nullptr;    // its partial sums of shared z-control points
   unsigned* zctr = nullptr;
   bool use_fused = true;     // fused 3-D kernels where they cover the layout
@@ -574,8 +582,34 @@ void plain_project(mfa_model* md, const TQ* q) {
     }
 }
 
+// Host data copied slab by slab on the handle's copy stream while the fused
+// projection runs (encode from host data): source, device staging buffer, the
+// bytes of one z-plane and the number of planes.
+struct StagedCopy {
+  const void* host;
+  void* dev;
+  size_t plane_bytes;
+  long long planes;
+};
+
+// Copy slabs [t0, t1) of the host data on the copy stream, each followed by
+// its event.
+cudaError_t copy_slabs(mfa_model* md, const StagedCopy& sc, int t0, int t1) {
+  mfa_handle* h = md->h;
+  cudaError_t e = cudaSuccess;
+  for (int t = t0; t < t1 && e == cudaSuccess; ++t) {
+    const long long z0 = std::min<long long>((long long)t * md->slab_planes, sc.planes);
+    const long long z1 = std::min<long long>(z0 + md->slab_planes, sc.planes);
+    if (z1 > z0)
+      e = cudaMemcpyAsync((char*)sc.dev + z0 * sc.plane_bytes, (const char*)sc.host + z0 * sc.plane_bytes,
+                          (size_t)(z1 - z0) * sc.plane_bytes, cudaMemcpyHostToDevice, h->copy_stream);
+    if (e == cudaSuccess) e = cudaEventRecord(h->slab_ev[t], h->copy_stream);
+  }
+  return e;
+}
+
 template <typename T, typename TQ>
-void run_encode(mfa_model* md, const TQ* q) {
+void run_encode(mfa_model* md, const TQ* q, const StagedCopy* sc = nullptr) {
   mfa_handle* h = md->h;
   const LayoutDev& L = md->L;
   const int ns = md->nsub;
@@ -587,8 +621,32 @@ void run_encode(mfa_model* md, const TQ* q) {
   // projection: the fused 3-D kernel when it covers the layout, else one
   // launch per axis where stage a reads the previous stage (the data for a = 0)
   bool fused = false;
+  int slabs_done = 0;  // host data: slabs already copied (all of them once the projection has its data)
   if constexpr (std::is_same<T, ff>::value) {
-    if (md->dim == 3 && md->use_fused) {
+    if (md->dim == 3 && md->use_fused && sc && md->units) {
+      // the units of slab t wait for slabs 0..t only, so the projection runs
+      // under the rest of the copy
+      fused = true;
+      for (int t = 0; t < kSlabs && fused; ++t) {
+        copy_slabs(md, *sc, t, t + 1);
+        slabs_done = t + 1;
+        cudaStreamWaitEvent(h->stream, h->slab_ev[t], 0);
+        TRACED(h, TR_PROJECT_DATA,
+               fused = launch_project3d_ff<TQ>(L, md->offL, md->maxm[0], md->maxm[1], md->maxm[2], md->maxnL[0],
+                                                md->maxnL[1], md->x_inplace_ok, q, BL, h->d_status, h->stream,
+                                                nullptr, nullptr, md->zsplit, md->zpart, md->zctr,
+                                                md->units + md->slab_units[t], md->slab_units[t + 1] - md->slab_units[t],
+                                                t == 0));
+      }
+    }
+  }
+  if (sc && slabs_done < kSlabs) {
+    // every other path reads the whole grid: copy the rest and wait for it
+    copy_slabs(md, *sc, slabs_done, kSlabs);
+    cudaStreamWaitEvent(h->stream, h->slab_ev[kSlabs - 1], 0);
+  }
+  if constexpr (std::is_same<T, ff>::value) {
+    if (md->dim == 3 && md->use_fused && !fused) {
       TRACED(h, TR_PROJECT_DATA,
              fused = launch_project3d_ff<TQ>(L, md->offL, md->maxm[0], md->maxm[1], md->maxm[2], md->maxnL[0], md->maxnL[1],
                                               md->x_inplace_ok, q, BL, h->d_status, h->stream,
@@ -841,6 +899,12 @@ int mfa_create(int device, void* cuda_stream, mfa_handle** out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->d_result, 256);
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_pinned, 256);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+  for (int i = 0; i <= kSlabs && e == cudaSuccess; ++i) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) h->slab_ev.push_back(ev);
+  }
   if (e == cudaSuccess) e = cudaMemsetAsync(h->d_status, 0, 256, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (e != cudaSuccess) {
@@ -866,6 +930,8 @@ int mfa_destroy(mfa_handle* h) {
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   if (h->h_stage) cudaFreeHost(h->h_stage);
   if (h->stage_done) cudaEventDestroy(h->stage_done);
+  for (cudaEvent_t ev : h->slab_ev) cudaEventDestroy(ev);
+  if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   if (h->plan && h->plan_free) h->plan_free(h->plan);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   delete h;
@@ -882,7 +948,7 @@ struct TablePlan {
   int n_full_rows = 0, n_part_rows = 0, n_xs = 0;
   size_t host_bytes = 0, tables_bytes = 0;
   size_t o_BL = 0, o_X = 0, o_P = 0, o_Pp = 0, o_S1 = 0, o_S2 = 0, o_part = 0, o_stage = 0, big_bytes = 0;
-  size_t o_zpart = 0, o_zctr = 0;
+  size_t o_zpart = 0, o_zctr = 0, o_units = 0;
 };
 
 // Host products of one layout, kept per handle for the most recent layout of
@@ -982,6 +1048,7 @@ int bind_model(mfa_handle* h, mfa_model* md, const TablePlan& tp) {
   md->S2 = at_off<char>(md->big, tp.o_S2);
   md->part = at_off<float>(md->big, tp.o_part);
   md->zpart = md->zsplit > 1 ? at_off<ff>(md->big, tp.o_zpart) : nullptr;
+  md->units = md->zsplit > 1 ? at_off<int2>(md->arena, tp.o_units) : nullptr;
   md->zctr = md->zsplit > 1 ? at_off<unsigned>(md->big, tp.o_zctr) : nullptr;
   // setup kernels: basis tables, Gram bands, Cholesky factors (FP64), all axes per launch
   {
@@ -1011,6 +1078,47 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
   const int ns = md->nsub;
   TablePlan tp;
   Arena ar;
+  // fused projection: four units per window along z (whole batches of
+  // planes) when every unit keeps more than p+1 knot spans, so that a
+  // z-control point takes planes of two units at most; partial sums of the
+  // shared z-control points (p+1 per side of a cut)
+  md->zsplit = 1;
+  if (!md->batch && md->dim == 3 && md->prec == MFA_PREC_MIXED && md->use_fused) {
+    const AxisHost& az = md->axh[2];
+    constexpr int kUnits = 4;
+    const int zb = proj3d_planes_per_batch(md->degree, md->maxm[0], md->maxm[1], md->maxm[2], md->maxnL[0],
+                                           md->maxnL[1]);
+    bool ok = true;
+    for (const AxisSub& sb : az.subs)
+      ok = ok && proj3d_split_ok(az.p, zb, kUnits, az.M, az.nspans, sb.k0, sb.m);
+    if (ok) md->zsplit = kUnits;
+  }
+  // the projection units ordered by the slab of host data their last plane
+  // lies in (slab t: planes [t sp, (t+1) sp) of the grid), so that the units
+  // of slab t can run as soon as slabs 0..t have landed
+  std::vector<int2> units;
+  md->slab_units.assign(kSlabs + 1, 0);
+  md->slab_planes = 0;
+  if (md->zsplit > 1) {
+    const AxisHost& az = md->axh[2];
+    const int zb = proj3d_planes_per_batch(md->degree, md->maxm[0], md->maxm[1], md->maxm[2], md->maxnL[0],
+                                           md->maxnL[1]);
+    const long long sp = (az.M + kSlabs - 1) / kSlabs;
+    md->slab_planes = sp;
+    std::vector<std::vector<int2>> by_slab(kSlabs);
+    for (int sd = 0; sd < ns; ++sd) {
+      const AxisSub& sb = az.subs[sd / (md->axh[0].S * md->axh[1].S)];
+      for (int k = 0; k < md->zsplit; ++k) {
+        const long long end = sb.k0 + proj3d_unit_start(sb.m, zb, md->zsplit, k + 1);  // one past the last plane
+        const int t = (int)std::min<long long>(kSlabs - 1, std::max<long long>(0, (end + sp - 1) / sp - 1));
+        by_slab[t].push_back(int2{sd, k});
+      }
+    }
+    for (int t = 0; t < kSlabs; ++t) {
+      units.insert(units.end(), by_slab[t].begin(), by_slab[t].end());
+      md->slab_units[t + 1] = (int)units.size();
+    }
+  }
   // tables filled on the host come first (one upload), then the ones the
   // setup kernels compute
   for (int a = 0; a < 3; ++a) {
@@ -1045,6 +1153,7 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
           rows_part.push_back(r);
       }
   }
+  tp.o_units = ar.take<int2>(units.size());
   tp.o_rows = ar.take<int>(rows_full.size() + rows_part.size());
   tp.o_xs = ar.take<int>(xs.size());
   tp.n_full_rows = (int)rows_full.size();
@@ -1082,21 +1191,6 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
   // update partials (3 floats per block of the float-float update) and its
   // row counter
   tp.o_part = bg.take<float>(3 * (size_t)(ns + kAvgListBlocks) + 1);
-  // fused projection: four units per window along z (whole batches of
-  // planes) when every unit keeps more than p+1 knot spans, so that a
-  // z-control point takes planes of two units at most; partial sums of the
-  // shared z-control points (p+1 per side of a cut)
-  md->zsplit = 1;
-  if (!md->batch && md->dim == 3 && md->prec == MFA_PREC_MIXED && md->use_fused) {
-    const AxisHost& az = md->axh[2];
-    constexpr int kUnits = 4;
-    const int zb = proj3d_planes_per_batch(md->degree, md->maxm[0], md->maxm[1], md->maxm[2], md->maxnL[0],
-                                           md->maxnL[1]);
-    bool ok = true;
-    for (const AxisSub& sb : az.subs)
-      ok = ok && proj3d_split_ok(az.p, zb, kUnits, az.M, az.nspans, sb.k0, sb.m);
-    if (ok) md->zsplit = kUnits;
-  }
   if (md->zsplit > 1) {
     tp.o_zpart =
         bg.take<ff>((size_t)ns * (md->zsplit - 1) * 2 * (md->degree + 1) * md->maxnL[0] * md->maxnL[1]);
@@ -1136,6 +1230,7 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
   std::memcpy(img + tp.o_rows, rows_full.data(), sizeof(int) * rows_full.size());
   std::memcpy(img + tp.o_rows + sizeof(int) * rows_full.size(), rows_part.data(), sizeof(int) * rows_part.size());
   std::memcpy(img + tp.o_xs, xs.data(), sizeof(int) * xs.size());
+  std::memcpy(img + tp.o_units, units.data(), sizeof(int2) * units.size());
   std::memcpy(img + tp.o_offL, offL.data(), sizeof(long long) * ns);
   std::memcpy(img + tp.o_offS1, offS1.data(), sizeof(long long) * ns);
   std::memcpy(img + tp.o_offS2, offS2.data(), sizeof(long long) * ns);
@@ -1301,27 +1396,47 @@ int encode_impl(mfa_handle* h, const mfa_layout* lay, const void* q, int q_dtype
   DeviceGuard g(h->device);
   cudaError_t e = cudaSuccess;
   const void* qd = q;
+  StagedCopy sc{};
+  bool staged = false;
   if (!q_on_device) {
-    // host data: copy and wait, so the caller may reuse its buffer on return
     void* qbuf = at_off<char>(md->big, o_Q);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(qbuf, q, qbytes, cudaMemcpyHostToDevice, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (md->units && (int)h->slab_ev.size() > kSlabs) {
+      // fused 3-D projection: the data cross in z-slabs on the copy stream
+      // (once the staging buffer's allocation is ordered before them) and
+      // the projection units of each slab start as it lands
+      e = cudaEventRecord(h->slab_ev[kSlabs], h->stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->slab_ev[kSlabs], 0);
+      sc = StagedCopy{q, qbuf, (size_t)lay->npts[0] * lay->npts[1] * (q_dtype == MFA_F64 ? 8 : 4), lay->npts[2]};
+      staged = true;
+    } else {
+      // host data: copy and wait, so the caller may reuse its buffer on return
+      if (e == cudaSuccess) e = cudaMemcpyAsync(qbuf, q, qbytes, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
     qd = qbuf;
     md->q_staged = qbuf;
     md->q_staged_dtype = q_dtype;
   }
   md->q_src = qd;
   md->q_src_dtype = q_dtype;
+  const StagedCopy* scp = staged ? &sc : nullptr;
   if (md->prec == MFA_PREC_FP64) {
     if (q_dtype == MFA_F64)
-      run_encode<double, double>(md, (const double*)qd);
+      run_encode<double, double>(md, (const double*)qd, scp);
     else
-      run_encode<double, float>(md, (const float*)qd);
+      run_encode<double, float>(md, (const float*)qd, scp);
   } else {
     if (q_dtype == MFA_F64)
-      run_encode<ff, double>(md, (const double*)qd);
+      run_encode<ff, double>(md, (const double*)qd, scp);
     else
-      run_encode<ff, float>(md, (const float*)qd);
+      run_encode<ff, float>(md, (const float*)qd, scp);
+  }
+  // the copies of the host data have finished when this returns, so the
+  // caller may reuse its buffer (the fit itself goes on on the stream); on
+  // an error too, before the staging buffer is released
+  if (staged) {
+    const cudaError_t ec = cudaStreamSynchronize(h->copy_stream);
+    if (e == cudaSuccess) e = ec;
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {

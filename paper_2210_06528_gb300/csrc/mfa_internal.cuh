@@ -171,13 +171,17 @@ void launch_cast(const TIn* in, TOut* out, long long n, cudaStream_t st);
 // whether cutting every window of the z axis (points k0 .. k0+m-1) into K
 // units of whole batches keeps more than P+1 knot spans in every unit.
 int proj3d_planes_per_batch(int P, int maxm0, int maxm1, int maxm2, int maxn0, int maxn1);
+// First plane of unit b of a window of m2 planes cut into K units of whole
+// batches of zb planes (b = K: m2).
+int proj3d_unit_start(int m2, int zb, int K, int b);
 bool proj3d_split_ok(int P, int zb, int K, long long M, int nspans, long long k0, int m);
 
 template <typename TQ>
 bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, int maxm1, int maxm2, int maxn0,
                          int maxn1, bool inplace_ok, const TQ* Q, ff* BL, int* status, cudaStream_t st,
                          const AxisOp* inst = nullptr, const int* order = nullptr, int ksplit = 1,
-                         ff* zpart = nullptr, unsigned* zctr = nullptr);
+                         ff* zpart = nullptr, unsigned* zctr = nullptr, const int2* units = nullptr,
+                         int nunits = 0, bool first = true);
 
 template <typename V, typename TQ, typename TOut, bool RESID>
 bool launch_decode3d(const LayoutDev& L, const V* P, const TQ* Q, TOut* out, double* partials, cudaStream_t st);

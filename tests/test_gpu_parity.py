@@ -420,9 +420,18 @@ def test_fused_projection_split_along_z(p, npts, nspans, nsub):
     prob = oracle_problem(Qd, p, list(nspans), list(nsub), delta)
     ref = O.schwarz_solve(prob, Qd, max_iters=60, tol_dP=1e-9)
     g = GpuRun(Q, p, list(nspans), list(nsub), delta, precision=mfa.MFA_PREC_MIXED)
+    gh = GpuRun(Q, p, list(nspans), list(nsub), delta, precision=mfa.MFA_PREC_MIXED, on_device=False)
     try:
         rc, rep = g.iterate(60, 1e-9)
         assert rc == mfa.MFA_OK and rep.iters == ref["iters"]
         assert rel_diff(g.ctrl(), ref["P"]) <= TOL_FP64
+        # host data cross in z-slabs beside the projection: the same units in
+        # the same order, so the fit is bit-identical to the device-data one
+        rch, reph = gh.iterate(60, 1e-9)
+        assert (rch, reph.iters) == (rc, rep.iters)
+        assert np.array_equal(gh.ctrl(), g.ctrl())
+        a, b = g.residual(), gh.model.residual(None)
+        assert (a.rms_decoded, a.maxabs_decoded, a.data_range) == (b.rms_decoded, b.maxabs_decoded, b.data_range)
     finally:
         g.close()
+        gh.close()
