@@ -522,8 +522,9 @@ def run_gb300(args, wl):
     def step_e2e():
         m = h.encode(q_host, lay)  # host -> device copy inside
         m.iterate(wl["max_iters"], wl["tol"])
+        m.ctrl_async(P_host)  # device -> host read of the control points, beside the residual
         m.residual(None)  # against the staged copy
-        m.ctrl(out=P_host)  # device -> host read of the control points
+        h.sync()  # the control points are in P_host
         m.free()
 
     step_e2e()

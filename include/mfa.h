@@ -213,13 +213,21 @@ int mfa_residual(mfa_handle* h, const mfa_model* m, const void* q, int q_dtype,
  * host memory; cap is the capacity of host_out in values.  Synchronous. */
 int mfa_get_ctrl(mfa_handle* h, const mfa_model* m, double* host_out, int64_t cap);
 
+/* The same copy, enqueued: the FP64 cast runs on the handle's stream and the
+ * copy to host_out on the handle's copy stream, so later calls (mfa_residual,
+ * another encode) proceed beside it.  host_out must stay valid, and holds the
+ * values only once mfa_sync(h) has returned; pinned memory keeps the copy
+ * asynchronous.  Errors as mfa_get_ctrl; copy errors surface at mfa_sync. */
+int mfa_get_ctrl_async(mfa_handle* h, const mfa_model* m, double* host_out, int64_t cap);
+
 /* Number of global control points of a model (prod n_a), or < 0 on error. */
 int64_t mfa_num_ctrl(const mfa_model* m);
 
 /* Free a model (stream-ordered on the stream of the handle that made it). */
 int mfa_free(mfa_model* m);
 
-/* Wait for the handle's stream; return and clear the device status word. */
+/* Wait for the handle's stream and its copy stream (asynchronous reads);
+ * return and clear the device status word. */
 int mfa_sync(mfa_handle* h);
 
 /* Static text for a status code. */

@@ -41,6 +41,10 @@ struct mfa_handle {
   cudaEvent_t stage_done = nullptr;         // the last upload from h_stage has been read
   cudaStream_t copy_stream = nullptr;       // host data copied slab by slab beside the projection
   std::vector<cudaEvent_t> slab_ev;         // slab landed (copy stream) / buffers allocated (handle stream)
+  void* rb = nullptr;                       // staging of asynchronous control-point reads
+  size_t rb_size = 0;
+  cudaEvent_t rb_ready = nullptr;           // rb written (handle stream)
+  cudaEvent_t rb_done = nullptr;            // rb copied out (copy stream)
   PlanCache* plan = nullptr;                // host products of the most recent single-model layout
   void (*plan_free)(PlanCache*) = nullptr;  // its deleter (set with it)
   bool plan_valid = false;                  // plan matches the image in h_stage
@@ -900,6 +904,8 @@ int mfa_create(int device, void* cuda_stream, mfa_handle** out) {
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_pinned, 256);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_ready, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_done, cudaEventDisableTiming);
   for (int i = 0; i <= kSlabs && e == cudaSuccess; ++i) {
     cudaEvent_t ev = nullptr;
     e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -920,7 +926,9 @@ int mfa_destroy(mfa_handle* h) {
   if (!h) return MFA_ERR_ARG;
   DeviceGuard g(h->device);
   cudaStreamSynchronize(h->stream);
+  if (h->copy_stream) cudaStreamSynchronize(h->copy_stream);
   if (h->ws) cudaFreeAsync(h->ws, h->stream);
+  if (h->rb) cudaFreeAsync(h->rb, h->stream);
   cudaStreamSynchronize(h->stream);
   if (h->pool) cudaMemPoolDestroy(h->pool);
   cudaFree(h->d_status);
@@ -931,6 +939,8 @@ int mfa_destroy(mfa_handle* h) {
   if (h->h_stage) cudaFreeHost(h->h_stage);
   if (h->stage_done) cudaEventDestroy(h->stage_done);
   for (cudaEvent_t ev : h->slab_ev) cudaEventDestroy(ev);
+  if (h->rb_ready) cudaEventDestroy(h->rb_ready);
+  if (h->rb_done) cudaEventDestroy(h->rb_done);
   if (h->copy_stream) cudaStreamDestroy(h->copy_stream);
   if (h->plan && h->plan_free) h->plan_free(h->plan);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -1661,6 +1671,40 @@ int mfa_get_ctrl(mfa_handle* h, const mfa_model* mdc, double* host_out, int64_t 
   return st < 0 ? st : MFA_OK;
 }
 
+int mfa_get_ctrl_async(mfa_handle* h, const mfa_model* mdc, double* host_out, int64_t cap) {
+  mfa_model* md = const_cast<mfa_model*>(mdc);
+  if (!h || !md || md->h != h || !host_out) return MFA_ERR_ARG;
+  const long long n = mfa_num_ctrl(md);
+  if (cap < n) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  const size_t bytes = (size_t)n * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (h->rb_size < bytes) {
+    // a larger staging buffer, once the last read out of the old one is done
+    e = cudaEventSynchronize(h->rb_done);
+    if (e != cudaSuccess) return cuda_status(e);
+    pool_free(h, h->rb);
+    h->rb = nullptr;
+    h->rb_size = 0;
+    const int rc = pool_alloc(h, &h->rb, bytes);
+    if (rc != MFA_OK) return rc;
+    h->rb_size = bytes;
+  }
+  // the cast waits for the previous read out of the buffer; the copy to the
+  // host runs on the copy stream, beside whatever the handle's stream does next
+  e = cudaStreamWaitEvent(h->stream, h->rb_done, 0);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (md->prec == MFA_PREC_FP64)
+    TRACED(h, TR_MISC, (launch_cast<double, double>((const double*)md->P, (double*)h->rb, n, h->stream)));
+  else
+    TRACED(h, TR_MISC, (launch_cast<ff, double>((const ff*)md->P, (double*)h->rb, n, h->stream)));
+  e = cudaEventRecord(h->rb_ready, h->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(h->copy_stream, h->rb_ready, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, h->rb, bytes, cudaMemcpyDeviceToHost, h->copy_stream);
+  if (e == cudaSuccess) e = cudaEventRecord(h->rb_done, h->copy_stream);
+  return cuda_status(e);
+}
+
 // ---------------------------------------------------------------------------
 // Persistence: a fitted model to a file and back (layout, update rule,
 // iteration count, global control points as stored on the device, and
@@ -1855,6 +1899,7 @@ int mfa_sync(mfa_handle* h) {
   if (!h) return MFA_ERR_ARG;
   DeviceGuard g(h->device);
   cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->copy_stream);
   if (e != cudaSuccess) return cuda_status(e);
   return read_status(h);
 }

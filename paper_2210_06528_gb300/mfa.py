@@ -109,6 +109,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
                                      ctypes.c_double, ctypes.POINTER(mfa_report), ctypes.POINTER(P)]
     lib.mfa_residual.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(mfa_report)]
     lib.mfa_get_ctrl.argtypes = [P, P, P, ctypes.c_int64]
+    lib.mfa_get_ctrl_async.argtypes = [P, P, P, ctypes.c_int64]
     lib.mfa_num_ctrl.argtypes = [P]
     lib.mfa_num_ctrl.restype = ctypes.c_int64
     lib.mfa_free.argtypes = [P]
@@ -155,7 +156,7 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_server_stats.argtypes = [P, ctypes.POINTER(mfa_server_stats_t)]
     lib.mfa_server_destroy.argtypes = [P]
     for name in ["mfa_create", "mfa_destroy", "mfa_encode", "mfa_schwarz_iterate", "mfa_decode", "mfa_residual",
-                 "mfa_get_ctrl", "mfa_free", "mfa_sync", "mfa_encode_plain", "mfa_encode_batch", "mfa_batch_refit",
+                 "mfa_get_ctrl", "mfa_get_ctrl_async", "mfa_free", "mfa_sync", "mfa_encode_plain", "mfa_encode_batch", "mfa_batch_refit",
                  "mfa_batch_ctrl_offsets", "mfa_batch_get_ctrl", "mfa_batch_residual", "mfa_batch_decode",
                  "mfa_batch_free", "mfa_batch_decode_points", "mfa_set_update_rule", "mfa_server_create", "mfa_server_wait",
                  "mfa_server_release", "mfa_server_get_ctrl", "mfa_server_stats", "mfa_server_destroy"]:
@@ -443,6 +444,18 @@ def mfa_get_ctrl(h: int, m: int, out=None):
     return out
 
 
+def mfa_get_ctrl_async(h: int, m: int, out):
+    """Enqueue the read of the control points into ``out`` (a host float64
+    buffer, pinned for an asynchronous copy); the values are there once
+    mfa_sync(h) has returned."""
+    ptr, code, dev, keep = _ptr_dtype(out)
+    if dev or code != MFA_F64 or keep is not out:
+        raise TypeError("control points are read into a contiguous host float64 buffer")
+    cap = out.numel() if hasattr(out, "numel") else out.size
+    _check(load().mfa_get_ctrl_async(ctypes.c_void_p(h), ctypes.c_void_p(m), ptr, cap), "mfa_get_ctrl_async")
+    return out
+
+
 def mfa_free(m: int) -> None:
     _check(load().mfa_free(ctypes.c_void_p(m)), "mfa_free")
 
@@ -593,6 +606,11 @@ class Model:
         if out is not None:
             return mfa_get_ctrl(self.handle.h, self.m, out)
         return mfa_get_ctrl(self.handle.h, self.m).reshape(tuple(reversed(self.ncp)))
+
+    def ctrl_async(self, out):
+        """Enqueue the read of the control points into the host float64
+        buffer ``out``; it holds them once Handle.sync() has returned."""
+        return mfa_get_ctrl_async(self.handle.h, self.m, out)
 
     def residual(self, q=None) -> mfa_report:
         """Decoded error statistics against ``q``; None uses the device copy

@@ -275,6 +275,36 @@ def test_residual_on_staged_host_copy_and_pinned_ctrl():
         h.close()
 
 
+def test_async_control_point_read_beside_residual():
+    """mfa_get_ctrl_async fills a pinned buffer beside later stream work: after
+    a residual call and mfa_sync it holds exactly what mfa_get_ctrl returns,
+    and a second read into another buffer reuses the staging in order."""
+    import torch
+    Q = inputs.gauss_3d((40, 36, 33), seed=9, dtype=np.float32)
+    h = mfa.Handle(0)
+    try:
+        lay = mfa.make_layout(3, 3, [40, 36, 33], [10, 9, 8], [2, 2, 1], [2, 2, 2], mfa.MFA_PREC_MIXED)
+        m = h.encode(Q, lay)
+        m.iterate(5, 0.0)
+        n = mfa.mfa_num_ctrl(m.m)
+        a = torch.empty(n, dtype=torch.float64).pin_memory()
+        b = torch.empty(n, dtype=torch.float64).pin_memory()
+        m.ctrl_async(a)
+        res = m.residual(None)
+        m.iterate(1, 0.0)
+        m.ctrl_async(b)
+        assert h.sync() == mfa.MFA_OK
+        assert res.rms_decoded > 0
+        ref = m.ctrl().ravel()
+        assert np.array_equal(b.numpy(), ref)
+        assert not np.array_equal(a.numpy(), ref)  # the read before the extra step
+        with pytest.raises(mfa.MFAError):
+            m.ctrl_async(torch.empty(n - 1, dtype=torch.float64))
+        m.free()
+    finally:
+        h.close()
+
+
 def test_plain_per_subdomain_form_equals_batched_fp64():
     """The per-subdomain comparator form (one launch per subdomain and stage,
     data re-read every iteration) runs the same FP64 arithmetic as the
