@@ -24,7 +24,7 @@ namespace {
 struct PlanCache;
 // host data of a fused 3-D encode is copied in this many z-slabs, the
 // projection units of each slab launched as it lands
-constexpr int kSlabs = 8;
+constexpr int kSlabs = 16;
 }  // namespace
 
 struct mfa_handle {
