@@ -1631,8 +1631,9 @@ __device__ __forceinline__ void avg_single(ff v, const ff* __restrict__ Pprev, l
 __global__ void __launch_bounds__(kAvgThreads, 3) k_average_ff(LayoutDev L, const long long* __restrict__ offL,
                                                                const ff* __restrict__ X, ff* __restrict__ P,
                                                                const ff* __restrict__ Pprev, float* __restrict__ part,
-                                                               unsigned* __restrict__ row_ctr, int stage_tables,
-                                                               int rule) {
+                                                               unsigned* __restrict__ row_ctr,
+                                                               unsigned long long* __restrict__ metrics,
+                                                               int stage_tables, int rule) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int n0 = (int)L.ncp[0], n1 = (int)L.ncp[1], n2 = (int)L.ncp[2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -1750,50 +1751,50 @@ __global__ void __launch_bounds__(kAvgThreads, 3) k_average_ff(LayoutDev L, cons
     part[3 * blockIdx.x + 1] = b;
     part[3 * blockIdx.x + 2] = c;
   }
-}
-
-// Maxima of the per-block metric partials into metrics[0..2] (bit patterns of
-// non-negative doubles, the same format the host reads; metrics must start at
-// zero).  A few hundred blocks, one atomic per block and metric.
-__global__ void k_metrics_reduce(const float* __restrict__ part, long long nblk, unsigned long long* metrics) {
-  float a = 0.f, b = 0.f, c = 0.f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nblk; i += (long long)gridDim.x * blockDim.x) {
-    a = fmaxf(a, part[3 * i]);
-    b = fmaxf(b, part[3 * i + 1]);
-    c = fmaxf(c, part[3 * i + 2]);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    a = fmaxf(a, __shfl_down_sync(0xffffffffu, a, o));
-    b = fmaxf(b, __shfl_down_sync(0xffffffffu, b, o));
-    c = fmaxf(c, __shfl_down_sync(0xffffffffu, c, o));
-  }
-  __shared__ float red[3][8];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[0][wid] = a;
-    red[1][wid] = b;
-    red[2][wid] = c;
-  }
+  // the last block to finish reduces every block's partials, in a fixed
+  // order, into metrics[0..2] (bit patterns of non-negative doubles)
+  __shared__ int last_block;
+  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
-      a = fmaxf(a, red[0][w]);
-      b = fmaxf(b, red[1][w]);
-      c = fmaxf(c, red[2][w]);
+  if (threadIdx.x == 0) last_block = atomicAdd(row_ctr + 1, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (last_block) {
+    __threadfence();
+    float a = 0.f, b = 0.f, c = 0.f;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+      a = fmaxf(a, __ldcg(part + 3 * i));
+      b = fmaxf(b, __ldcg(part + 3 * i + 1));
+      c = fmaxf(c, __ldcg(part + 3 * i + 2));
     }
-    a = fmaxf(a, red[0][0]);
-    b = fmaxf(b, red[1][0]);
-    c = fmaxf(c, red[2][0]);
-    atomicMax(&metrics[0], (unsigned long long)__double_as_longlong((double)a));
-    atomicMax(&metrics[1], (unsigned long long)__double_as_longlong((double)b));
-    atomicMax(&metrics[2], (unsigned long long)__double_as_longlong((double)c));
+    for (int o = 16; o > 0; o >>= 1) {
+      a = fmaxf(a, __shfl_down_sync(0xffffffffu, a, o));
+      b = fmaxf(b, __shfl_down_sync(0xffffffffu, b, o));
+      c = fmaxf(c, __shfl_down_sync(0xffffffffu, c, o));
+    }
+    if (lane == 0) {
+      red[0][wid] = a;
+      red[1][wid] = b;
+      red[2][wid] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+        a = fmaxf(a, red[0][w]);
+        b = fmaxf(b, red[1][w]);
+        c = fmaxf(c, red[2][w]);
+      }
+      metrics[0] = (unsigned long long)__double_as_longlong((double)a);
+      metrics[1] = (unsigned long long)__double_as_longlong((double)b);
+      metrics[2] = (unsigned long long)__double_as_longlong((double)c);
+    }
   }
 }
 
 long long average_ff_blocks(const LayoutDev& L) { return L.nsub + kAvgListBlocks; }
 
 // `part` holds 3 floats per block of the launch (average_ff_blocks) and, after
-// them, the row counter of the shared control points.
+// them, the row counter of the shared control points and the finished-block
+// counter.
 void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev, float* part,
                        unsigned long long* metrics, cudaStream_t st, int rule) {
   static bool init[64] = {};  // reciprocal table in constant memory, set once per device
@@ -1815,11 +1816,9 @@ void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, f
   const int stage = tab <= 40 * 1024;
   const long long nblk = average_ff_blocks(L);
   unsigned* row_ctr = reinterpret_cast<unsigned*>(part + 3 * nblk);
-  cudaMemsetAsync(row_ctr, 0, sizeof(unsigned), st);
-  k_average_ff<<<(unsigned)nblk, kAvgThreads, stage ? tab : 0, st>>>(L, offL, X, P, Pprev, part, row_ctr, stage,
-                                                                      rule);
-  cudaMemsetAsync(metrics, 0, 3 * sizeof(unsigned long long), st);
-  k_metrics_reduce<<<152, 256, 0, st>>>(part, average_ff_blocks(L), metrics);
+  cudaMemsetAsync(row_ctr, 0, 2 * sizeof(unsigned), st);
+  k_average_ff<<<(unsigned)nblk, kAvgThreads, stage ? tab : 0, st>>>(L, offL, X, P, Pprev, part, row_ctr, metrics,
+                                                                      stage, rule);
 }
 
 }  // namespace mfa

@@ -697,7 +697,7 @@ void run_encode(mfa_model* md, const TQ* q, const StagedCopy* sc = nullptr) {
   cudaMemsetAsync(h->d_metrics, 0, 4 * sizeof(unsigned long long), h->stream);
   if constexpr (std::is_same<T, ff>::value) {
     if (md->use_fused) {
-      TRACED_N(h, TR_AVERAGE, 2,
+      TRACED_N(h, TR_AVERAGE, 1,
                launch_average_ff(L, md->offL, X, (ff*)md->P, nullptr, md->part, h->d_metrics, h->stream,
                                  md->update));
       return;
@@ -723,7 +723,7 @@ void run_step(mfa_model* md) {
              fused = launch_schwarz3d_ff(L, md->offL, md->maxnL, md->maxnU, (const ff*)md->Pprev, (const ff*)md->BL,
                                          (ff*)md->X, h->stream));
       if (fused) {
-        TRACED_N(h, TR_AVERAGE, 2,
+        TRACED_N(h, TR_AVERAGE, 1,
                  launch_average_ff(L, md->offL, (const ff*)md->X, (ff*)md->P, (const ff*)md->Pprev, md->part,
                                    h->d_metrics, h->stream, md->update));
         return;
@@ -1198,9 +1198,9 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
   tp.o_Pp = bg.take<char>(ncp * es);
   tp.o_S1 = bg.take<char>(md->sizeS1 * es);
   tp.o_S2 = bg.take<char>(md->sizeS2 * es);
-  // update partials (3 floats per block of the float-float update) and its
-  // row counter
-  tp.o_part = bg.take<float>(3 * (size_t)(ns + kAvgListBlocks) + 1);
+  // update partials (3 floats per block of the float-float update), its row
+  // counter and its finished-block counter
+  tp.o_part = bg.take<float>(3 * (size_t)(ns + kAvgListBlocks) + 2);
   if (md->zsplit > 1) {
     tp.o_zpart =
         bg.take<ff>((size_t)ns * (md->zsplit - 1) * 2 * (md->degree + 1) * md->maxnL[0] * md->maxnL[1]);
@@ -1474,7 +1474,7 @@ int mfa_set_update_rule(mfa_handle* h, mfa_model* md, int rule) {
     TRACED(h, TR_AVERAGE, launch_average<double>(md->L, md->offL, (const double*)md->X, (double*)md->P, nullptr,
                                                  h->d_metrics, h->stream, md->update));
   else if (md->use_fused)
-    TRACED_N(h, TR_AVERAGE, 2, launch_average_ff(md->L, md->offL, (const ff*)md->X, (ff*)md->P, nullptr, md->part,
+    TRACED_N(h, TR_AVERAGE, 1, launch_average_ff(md->L, md->offL, (const ff*)md->X, (ff*)md->P, nullptr, md->part,
                                                  h->d_metrics, h->stream, md->update));
   else
     TRACED(h, TR_AVERAGE, launch_average<ff>(md->L, md->offL, (const ff*)md->X, (ff*)md->P, nullptr, h->d_metrics,
