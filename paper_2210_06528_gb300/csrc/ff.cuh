@@ -61,8 +61,6 @@ __device__ __forceinline__ ff operator*(ff a, ff b) {
 __device__ __forceinline__ ff& operator+=(ff& a, ff b) { return a = a + b; }
 __device__ __forceinline__ ff& operator-=(ff& a, ff b) { return a = a - b; }
 
-// acc += a * b with one rounding of the error terms (product accumulate)
-__device__ __forceinline__ void ff_fma_acc(ff& acc, ff a, ff b) { acc = acc + a * b; }
 
 // ---------------------------------------------------------------------------
 // Paired accumulation on the packed FP32 instructions of sm_100 and later

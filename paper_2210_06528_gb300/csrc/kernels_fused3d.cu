@@ -23,20 +23,9 @@ namespace mfa {
 struct AccFF {
   using V = ff;
   __device__ static V zero() { return ff(0.f, 0.f); }
-  // acc += (nh + nl) * x, x a float: the product hi part is exact with its FMA
-  // error term; the sum uses TwoSum and keeps the low word unnormalised
-  // (renormalised by finish()).
-  __device__ __forceinline__ static void add_f(V& acc, float nh, float nl, float x) {
-    const float p = __fmul_rn(nh, x);
-    float e = __fmaf_rn(nh, x, -p);
-    e = __fmaf_rn(nl, x, e);
-    const float s = __fadd_rn(acc.hi, p);
-    const float bb = __fsub_rn(s, acc.hi);
-    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    acc.hi = s;
-    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, err));
-  }
-  // acc += (nh + nl) * (x.hi + x.lo)
+  // acc += (nh + nl) * (x.hi + x.lo): the product's high part with its exact
+  // FMA error and the cross terms, TwoSum of the high words, the low word
+  // kept unnormalised (renormalised by finish())
   __device__ __forceinline__ static void add_v(V& acc, float nh, float nl, V x) {
     const float p = __fmul_rn(nh, x.hi);
     float e = __fmaf_rn(nh, x.hi, -p);
@@ -51,10 +40,6 @@ struct AccFF {
   __device__ __forceinline__ static V finish(V a) { return fast_two_sum(a.hi, a.lo); }
 };
 
-template <typename TQ>
-__device__ __forceinline__ float to_f(TQ x) {
-  return (float)x;
-}
 
 // ---------------------------------------------------------------------------
 // Projection B_L = (N_z^T x N_y^T x N_x^T) Q over every window (the N^T Q
