@@ -465,3 +465,43 @@ def test_fused_projection_split_along_z(p, npts, nspans, nsub):
     finally:
         g.close()
         gh.close()
+
+
+def test_plan_cache_keys_on_core_split_contents():
+    """Two layouts equal but for their core split (given as arrays) are
+    different plans: encoding them alternately through one handle gives each
+    the fit a fresh handle gives it, also when the same array object is
+    rewritten in place between the calls."""
+    import torch
+    Q = inputs.gauss_3d((48, 36, 30), seed=12, dtype=np.float32)
+    q = torch.from_numpy(Q).cuda()
+
+    def lay(cores_x):
+        return mfa.make_layout(3, 3, [48, 36, 30], [12, 9, 8], [2, 1, 1], [2, 2, 2], mfa.MFA_PREC_MIXED,
+                               core_spans=[list(cores_x), None, None])
+
+    def fit(h, layout):
+        m = h.encode(q, layout)
+        m.iterate(30, 1e-10)
+        P = m.ctrl()
+        m.free()
+        return P
+
+    refs = {}
+    for c in ((6, 6), (5, 7)):
+        hf = mfa.Handle(0)
+        try:
+            refs[c] = fit(hf, lay(c))
+        finally:
+            hf.close()
+    assert not np.array_equal(refs[(6, 6)], refs[(5, 7)])
+    h = mfa.Handle(0)
+    try:
+        for c in ((6, 6), (5, 7), (6, 6), (5, 7)):
+            assert np.array_equal(fit(h, lay(c)), refs[c])
+        one = lay((6, 6))
+        assert np.array_equal(fit(h, one), refs[(6, 6)])
+        one._keep[0][0], one._keep[0][1] = 5, 7  # the same array, rewritten
+        assert np.array_equal(fit(h, one), refs[(5, 7)])
+    finally:
+        h.close()
