@@ -725,8 +725,7 @@ bool launch_project3d_ff(const LayoutDev& L, const long long* offL, int maxm0, i
                                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
   }
   auto go = [&](auto kernel) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    ensure_smem(kernel, smem, true);
     if (A.ksplit > 1 && first) cudaMemsetAsync(zctr, 0, sizeof(unsigned) * L.nsub, st);
     kernel<<<A.units ? nunits : L.nsub * A.ksplit, kProjThreads, smem, st>>>(tmap, A, Q, BL, status);
   };
@@ -1113,7 +1112,7 @@ bool launch_decode3d(const LayoutDev& L, const V* P, const TQ* Q, TOut* out, dou
   const long long tiles = decode3d_tiles(L);
   if (tiles > (1LL << 31) - 1) return false;
   auto go = [&](auto kernel, size_t smem) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ensure_smem(kernel, smem);
     kernel<<<(unsigned)tiles, kDecThreads, smem, st>>>(L, P, Q, out, partials);
   };
 #define MFA_DEC_CASE(PP)                                                    \
@@ -1485,8 +1484,7 @@ bool launch_schwarz3d_ff(const LayoutDev& L, const long long* offL, const int* m
   // owned x points on the lanes, owned y points on NPAIR rounds of the groups
   if (maxnU[0] > 32 || maxnU[1] > 4 * NG || nplane > 4 * kStepThreads) return false;
   auto go = [&](auto kernel, size_t sm) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    ensure_smem(kernel, sm, true);
     kernel<<<L.nsub, kStepThreads, sm, st>>>(A, P, BL, X);
   };
 #define MFA_STEP_CASE(PP)                                                                      \
@@ -1923,7 +1921,7 @@ int launch_iter0_3d_ff(const LayoutDev& L, const long long* offL, const int* max
   dim3 g1(L.nsub, (maxnL[2] + kIt0Planes - 1) / kIt0Planes);
   dim3 g2((maxnL[0] * maxnL[1] + 127) / 128, L.nsub);
   auto go = [&](auto kxy, auto kz) {
-    cudaFuncSetAttribute(kxy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    ensure_smem(kxy, smem);
     kxy<<<g1, 128, smem, st>>>(L, offL, BL, X);
     kz<<<g2, 128, 0, st>>>(L, offL, X);
   };
@@ -1937,3 +1935,26 @@ int launch_iter0_3d_ff(const LayoutDev& L, const long long* offL, const int* max
 }
 
 }  // namespace mfa
+
+#include <map>
+#include <mutex>
+
+namespace mfa {
+
+void ensure_smem_attr(const void* kernel, size_t bytes, bool carveout) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> set;  // (kernel, device) -> largest size set
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = set[{kernel, dev}];
+  if (cur != 0 && bytes <= cur) return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
+    cur = bytes;
+  else
+    cudaGetLastError();  // the launch reports the problem
+  if (carveout) cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
+}  // namespace mfa
+

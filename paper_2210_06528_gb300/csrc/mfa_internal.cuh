@@ -121,6 +121,16 @@ struct TileMap {
   int threads = 0;  // block size = elements per tile
 };
 
+// Dynamic shared-memory limit (and, with `carveout`, the preferred shared
+// memory share) of a kernel, set once per kernel, device and size: the
+// attribute persists, and setting it again on every launch costs host time on
+// the launch path.
+void ensure_smem_attr(const void* kernel, size_t bytes, bool carveout = false);
+template <typename K>
+inline void ensure_smem(K kernel, size_t bytes, bool carveout = false) {
+  ensure_smem_attr(reinterpret_cast<const void*>(kernel), bytes, carveout);
+}
+
 // ---------------------------------------------------------------------------
 // kernel launchers (kernels_*.cu)
 // ---------------------------------------------------------------------------
