@@ -505,3 +505,61 @@ def test_plan_cache_keys_on_core_split_contents():
         assert np.array_equal(fit(h, one), refs[(5, 7)])
     finally:
         h.close()
+
+
+def test_two_handles_on_two_threads_match_one():
+    """Two host threads, each with a handle on its own stream, encoding host
+    data (copy stream, slab pipeline), iterating, reading the control points
+    asynchronously and taking the residual at the same time: every fit is
+    bit-identical to the same fit on one handle."""
+    import threading
+    import torch
+    Q = inputs.gauss_3d((28, 24, 192), seed=31, dtype=np.float32)
+    lay = mfa.make_layout(3, 3, [28, 24, 192], [7, 6, 48], [1, 1, 2], [2, 2, 2], mfa.MFA_PREC_MIXED)
+    n = None
+
+    def fit(h, out):
+        m = h.encode(Q, lay)
+        m.iterate(30, 1e-9)
+        m.ctrl_async(out)
+        r = m.residual(None)
+        assert h.sync() == mfa.MFA_OK
+        m.free()
+        return r.rms_decoded
+
+    h0 = mfa.Handle(0)
+    try:
+        n = 1
+        for a in range(3):
+            n *= [7, 6, 48][a] + 3
+        ref = torch.empty(n, dtype=torch.float64).pin_memory()
+        ref_rms = fit(h0, ref)
+    finally:
+        h0.close()
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    hs = [mfa.Handle(0, stream=s.cuda_stream) for s in streams]
+    outs = [[torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(3)] for _ in hs]
+    rms = [[None] * 3 for _ in hs]
+    errs = []
+
+    def run(i):
+        try:
+            for k in range(3):
+                rms[i][k] = fit(hs[i], outs[i][k])
+        except Exception as e:  # reported below
+            errs.append(e)
+
+    try:
+        ts = [threading.Thread(target=run, args=(i,)) for i in range(2)]
+        for t in ts:
+            t.start()
+        for t in ts:
+            t.join()
+        assert not errs, errs
+        for i in range(2):
+            for k in range(3):
+                assert np.array_equal(outs[i][k].numpy(), ref.numpy())
+                assert rms[i][k] == ref_rms
+    finally:
+        for h in hs:
+            h.close()
