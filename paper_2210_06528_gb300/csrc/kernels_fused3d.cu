@@ -11,6 +11,8 @@
 #include <climits>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 #include "mfa_internal.cuh"
 
@@ -1780,19 +1782,25 @@ long long average_ff_blocks(const LayoutDev& L) { return L.nsub + kAvgListBlocks
 // counter.
 void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev, float* part,
                        unsigned long long* metrics, cudaStream_t st, int rule) {
-  static bool init[64] = {};  // reciprocal table in constant memory, set once per device
+  // reciprocal table in constant memory, set once per device (handles on
+  // several host threads may reach this together)
+  static std::mutex init_mu;
+  static bool init[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64 && !init[dev]) {
-    float h[9] = {0}, l[9] = {0};
-    for (int n = 1; n <= 8; ++n) {
-      const ff v(1.0 / n);
-      h[n] = v.hi;
-      l[n] = v.lo;
+  if (dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> lock(init_mu);
+    if (!init[dev]) {
+      float h[9] = {0}, l[9] = {0};
+      for (int n = 1; n <= 8; ++n) {
+        const ff v(1.0 / n);
+        h[n] = v.hi;
+        l[n] = v.lo;
+      }
+      cudaMemcpyToSymbol(c_inv_hi, h, sizeof(h));
+      cudaMemcpyToSymbol(c_inv_lo, l, sizeof(l));
+      init[dev] = true;
     }
-    cudaMemcpyToSymbol(c_inv_hi, h, sizeof(h));
-    cudaMemcpyToSymbol(c_inv_lo, l, sizeof(l));
-    init[dev] = true;
   }
   const size_t tab = (size_t)(L.ncp[0] + L.ncp[1] + L.ncp[2]) * (sizeof(int4) + sizeof(int)) +
                      (size_t)L.nsub * sizeof(long long) + (size_t)(L.S[0] + L.S[1]) * sizeof(int);
@@ -1935,9 +1943,6 @@ int launch_iter0_3d_ff(const LayoutDev& L, const long long* offL, const int* max
 }
 
 }  // namespace mfa
-
-#include <map>
-#include <mutex>
 
 namespace mfa {
 
