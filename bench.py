@@ -288,8 +288,27 @@ def bench_batch(h, torch, mfa, stream, steps, count=4096, seed=0):
     r1.record(stream)
     torch.cuda.synchronize()
     res_ms = r0.elapsed_time(r1)
+    # scattered decode: 4096 uniform random parameter points per instance,
+    # device resident, one query per instance
+    per = 4096
+    qi = torch.arange(count, dtype=torch.int32, device="cuda")
+    poff = torch.arange(count + 1, dtype=torch.int64, device="cuda") * per
+    gen = torch.Generator(device="cuda").manual_seed(seed + 7)
+    upts = torch.rand((count * per, 3), dtype=torch.float64, device="cuda", generator=gen)
+    uout = torch.empty(count * per, dtype=torch.float64, device="cuda")
+    b.decode_points(qi, poff, upts, uout)
+    torch.cuda.synchronize()
+    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nrep = 5
+    d0.record(stream)
+    for _ in range(nrep):
+        b.decode_points(qi, poff, upts, uout)
+    d1.record(stream)
+    torch.cuda.synchronize()
+    dec_ms = d0.elapsed_time(d1) / nrep
     rc, sizes, cand = b.tile_sizes()
     b.free()
+    del upts, uout
     npts = int(data.size)
     d2 = sum(1 for sp in specs if sp["dim"] == 2)
     return {"workload": f"{count} independent fits ({d2} 2-D 32..512^2, {count - d2} 3-D 16..128^3 log-uniform, "
@@ -297,6 +316,8 @@ def bench_batch(h, torch, mfa, stream, steps, count=4096, seed=0):
             "points": npts,
             "encode_s_incl_host_layout": enc_s, "refit_ms": refit_ms, "refit_pts_per_s": npts / (refit_ms * 1e-3),
             "residual_ms": res_ms, "fit_plus_residual_pts_per_s": npts / ((refit_ms + res_ms) * 1e-3),
+            "scattered_decode": {"points": count * per, "ms": dec_ms, "pts_per_s": count * per / (dec_ms * 1e-3),
+                                 "inputs": "4096 uniform random parameter points per instance, on the device"},
             "rms_median": float(np.median(rms)), "rms_max": float(rms.max()),
             "refit": "one CUDA graph per batch (projection + solves of every (dimension, degree) group)",
             "tile_sizes": {"projection": sizes[0], "solve": sizes[1], "decode": sizes[2],

@@ -61,6 +61,23 @@ __device__ __forceinline__ ff operator*(ff a, ff b) {
 __device__ __forceinline__ ff& operator+=(ff& a, ff b) { return a = a + b; }
 __device__ __forceinline__ ff& operator-=(ff& a, ff b) { return a = a - b; }
 
+// a += (nh + nl) * (x.hi + x.lo): the product's high part with its exact FMA
+// error and the cross terms, TwoSum of the high words, the low word kept
+// unnormalised (ff_norm renormalises once at the end of a sum)
+__device__ __forceinline__ void ff_acc_prod(ff& a, float nh, float nl, ff x) {
+  const float p = __fmul_rn(nh, x.hi);
+  float e = __fmaf_rn(nh, x.hi, -p);
+  e = __fmaf_rn(nh, x.lo, e);
+  e = __fmaf_rn(nl, x.hi, e);
+  const float s = __fadd_rn(a.hi, p);
+  const float bb = __fsub_rn(s, a.hi);
+  const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  a.hi = s;
+  a.lo = __fadd_rn(a.lo, __fadd_rn(e, err));
+}
+
+__device__ __forceinline__ ff ff_norm(ff a) { return fast_two_sum(a.hi, a.lo); }
+
 
 // ---------------------------------------------------------------------------
 // Paired accumulation on the packed FP32 instructions of sm_100 and later

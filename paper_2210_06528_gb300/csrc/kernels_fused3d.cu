@@ -25,21 +25,9 @@ namespace mfa {
 struct AccFF {
   using V = ff;
   __device__ static V zero() { return ff(0.f, 0.f); }
-  // acc += (nh + nl) * (x.hi + x.lo): the product's high part with its exact
-  // FMA error and the cross terms, TwoSum of the high words, the low word
-  // kept unnormalised (renormalised by finish())
-  __device__ __forceinline__ static void add_v(V& acc, float nh, float nl, V x) {
-    const float p = __fmul_rn(nh, x.hi);
-    float e = __fmaf_rn(nh, x.hi, -p);
-    e = __fmaf_rn(nh, x.lo, e);
-    e = __fmaf_rn(nl, x.hi, e);
-    const float s = __fadd_rn(acc.hi, p);
-    const float bb = __fsub_rn(s, acc.hi);
-    const float err = __fadd_rn(__fsub_rn(acc.hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
-    acc.hi = s;
-    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, err));
-  }
-  __device__ __forceinline__ static V finish(V a) { return fast_two_sum(a.hi, a.lo); }
+  // acc += (nh + nl) * x, low word unnormalised until finish()
+  __device__ __forceinline__ static void add_v(V& acc, float nh, float nl, V x) { ff_acc_prod(acc, nh, nl, x); }
+  __device__ __forceinline__ static V finish(V a) { return ff_norm(a); }
 };
 
 

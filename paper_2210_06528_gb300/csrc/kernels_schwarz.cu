@@ -2,6 +2,8 @@
 // scattered decode.
 #include "mfa_internal.cuh"
 
+#include <type_traits>
+
 namespace mfa {
 
 struct SubBox {
@@ -241,12 +243,19 @@ __global__ void k_decode_points(LayoutDev L, double lo0, double lo1, double lo2,
     ((float*)out)[k] = (float)acc;
 }
 
+void launch_decode_points_ff(const LayoutDev& L, const double* lo, const double* hi, const double* pts,
+                             long long npts, const int* deriv, const ff* P, void* out, int out_dtype, cudaStream_t st);
+
 template <typename T>
 void launch_decode_points(const LayoutDev& L, const double* lo, const double* hi, const double* pts, long long npts,
                           const int* deriv, const T* P, void* out, int out_dtype, cudaStream_t st) {
-  long long blocks = (npts + 127) / 128;
-  k_decode_points<T><<<(unsigned)blocks, 128, 0, st>>>(L, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], pts, npts,
-                                                       deriv[0], deriv[1], deriv[2], P, out, out_dtype);
+  if constexpr (std::is_same<T, ff>::value) {
+    launch_decode_points_ff(L, lo, hi, pts, npts, deriv, P, out, out_dtype, st);
+  } else {
+    long long blocks = (npts + 127) / 128;
+    k_decode_points<T><<<(unsigned)blocks, 128, 0, st>>>(L, lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], pts, npts,
+                                                         deriv[0], deriv[1], deriv[2], P, out, out_dtype);
+  }
 }
 
 // Scattered decode of instances of a batch of independent fits: point k
@@ -299,17 +308,271 @@ __global__ void k_decode_points_inst(const InstDesc* __restrict__ desc, const in
   out[k] = acc;
 }
 
+void launch_decode_points_inst_ff(const InstDesc* desc, const int* qinst, const long long* pt_off, int nq,
+                                  long long npts, const double* pts, const ff* P, double* out, int p_uniform,
+                                  cudaStream_t st);
+
 template <typename T>
 void launch_decode_points_inst(const InstDesc* desc, const int* qinst, const long long* pt_off, int nq,
-                               long long npts, const double* pts, const T* P, double* out, cudaStream_t st) {
+                               long long npts, const double* pts, const T* P, double* out, int p_uniform,
+                               cudaStream_t st) {
   if (npts <= 0 || nq <= 0) return;
-  k_decode_points_inst<T><<<(unsigned)((npts + 127) / 128), 128, 0, st>>>(desc, qinst, pt_off, nq, pts, P, out);
+  if constexpr (std::is_same<T, ff>::value)
+    launch_decode_points_inst_ff(desc, qinst, pt_off, nq, npts, pts, P, out, p_uniform, st);
+  else
+    k_decode_points_inst<T><<<(unsigned)((npts + 127) / 128), 128, 0, st>>>(desc, qinst, pt_off, nq, pts, P, out);
 }
 
 template void launch_decode_points_inst<double>(const InstDesc*, const int*, const long long*, int, long long,
-                                                const double*, const double*, double*, cudaStream_t);
+                                                const double*, const double*, double*, int, cudaStream_t);
 template void launch_decode_points_inst<ff>(const InstDesc*, const int*, const long long*, int, long long,
-                                            const double*, const ff*, double*, cudaStream_t);
+                                            const double*, const ff*, double*, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Scattered decode of float-float control points on the FP32 pipes.
+//
+// The recurrences are those of basis_derivs, taken in knot units: with x =
+// u * nspans, the clamped uniform knots are the integers K(i) = clamp(i - p,
+// 0, nspans) and a point of span j sits at x = j + t, 0 <= t <= 1.  Every
+// denominator of the recurrence is then a difference of two knots bounding
+// span j, an integer 1..q, so each division is a product with a float-float
+// reciprocal, and the FP64 pipe (1/64 of the FP32 rate here) is used only to
+// split the FP64 coordinate and to widen the result.  Derivatives come out
+// with respect to x; the caller scales by nspans^r per axis.
+// ---------------------------------------------------------------------------
+
+// 1/d for a small positive integer d as a float-float: the rounded float
+// reciprocal r and (1 - r d) / d, whose numerator the FMA forms exactly
+__device__ __forceinline__ ff ff_rcp_int(int d) {
+  const float df = (float)d;
+  const float r = __frcp_rn(df);
+  const float e = __fmaf_rn(-r, df, 1.f);
+  return ff(r, __fmul_rn(e, r));
+}
+
+// k - t and t - k for a small integer k
+__device__ __forceinline__ ff ff_int_minus(int k, ff t) {
+  const ff s = two_sum((float)k, -t.hi);
+  return fast_two_sum(s.hi, __fsub_rn(s.lo, t.lo));
+}
+__device__ __forceinline__ ff ff_minus_int(ff t, int k) {
+  const ff s = two_sum(t.hi, -(float)k);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, t.lo));
+}
+
+// Knot span j of the knot coordinate xk (clamped to [0, nspans], NaN to 0)
+// and its offset t = xk - j as a float-float.  The split into float words
+// rounds xk to about 48 bits.
+__device__ __forceinline__ int knot_span_ff(double xk, int nspans, ff& t) {
+  float h = __double2float_rn(xk);
+  float l = __double2float_rn(xk - (double)h);
+  const float ns = (float)nspans;
+  if (!(h > 0.f) && !(h == 0.f && l >= 0.f)) h = l = 0.f;  // negative or NaN
+  if (h > ns || (h == ns && l > 0.f)) {
+    h = ns;
+    l = 0.f;
+  }
+  const float jf = floorf(h);
+  int j = (int)jf;
+  if (h == jf && l < 0.f) --j;
+  j = min(max(j, 0), nspans - 1);
+  // h - j is exact: j <= h <= j + 1 and either j = 0 or h <= 2j; |l| is
+  // below half an ulp of h and h - j is 0 or a multiple of that ulp
+  t = fast_two_sum(__fsub_rn(h, (float)j), l);
+  return j;
+}
+
+// Degree of a decode instantiation: P > 0 fixes it at compile time (every
+// loop unrolled, the basis in registers); P = 0 takes the runtime degree p
+// (loops kept, arrays sized for MFA_MAX_DEGREE).
+template <int P>
+struct DegreeOf {
+  static constexpr int kLen = P > 0 ? P + 1 : MFA_MAX_DEGREE + 1;
+  static constexpr int kUnroll = P > 0 ? P + 1 : 1;
+};
+
+// Values (rder = 0) or order-rder derivatives in x of the p+1 degree-p
+// functions nonzero on span j at x = j + t (Sec. 2.1, Cox-de Boor).
+template <int P>
+__device__ __forceinline__ void basis_derivs_ff(int j, ff t, int p_rt, int nspans, int rder,
+                                                ff (&N)[DegreeOf<P>::kLen]) {
+  constexpr int U = DegreeOf<P>::kUnroll;
+  const int p = P > 0 ? P : p_rt;
+  const int q0 = p - rder;
+#pragma unroll U
+  for (int r = 0; r <= p; ++r) N[r] = ff(0.f, 0.f);
+  if (q0 < 0) return;
+  N[0] = ff(1.f, 0.f);
+#pragma unroll U
+  for (int q = 1; q <= p; ++q) {
+    ff carry(0.f, 0.f);
+#pragma unroll U
+    for (int r = 0; r < q; ++r) {
+      const int kl = max(r + 1 - q, -j);     // knot K(j + p + r + 1 - q) - j
+      const int kr = min(r + 1, nspans - j);  // knot K(j + p + r + 1) - j
+      const ff w = N[r] * ff_rcp_int(kr - kl);
+      if (q <= q0) {
+        N[r] = carry + ff_int_minus(kr, t) * w;
+        carry = ff_minus_int(t, kl) * w;
+      } else {
+        const ff wq = w * ff((float)q, 0.f);
+        N[r] = carry - wq;
+        carry = wq;
+      }
+    }
+    N[q] = carry;
+  }
+}
+
+// Sum of the (p+1)^DIM basis products with the control points of the
+// support, x fastest; `row0` points at control point (span0, span1, span2).
+template <int P, int DIM>
+__device__ __forceinline__ ff tensor_sum_ff(const ff* __restrict__ row0, long long n0, long long n01, int p_rt,
+                                            const ff (&N)[3][DegreeOf<P>::kLen]) {
+  constexpr int U = DegreeOf<P>::kUnroll;
+  const int p = P > 0 ? P : p_rt;
+  const int R1 = DIM > 1 ? p : 0, R2 = DIM > 2 ? p : 0;
+  ff acc(0.f, 0.f);
+#pragma unroll U
+  for (int r2 = 0; r2 <= R2; ++r2) {
+    ff acc1(0.f, 0.f);
+#pragma unroll U
+    for (int r1 = 0; r1 <= R1; ++r1) {
+      const ff* row = row0 + r1 * n0 + r2 * n01;
+      ff acc0(0.f, 0.f);
+#pragma unroll U
+      for (int r0 = 0; r0 <= p; ++r0) ff_acc_prod(acc0, N[0][r0].hi, N[0][r0].lo, row[r0]);
+      acc0 = ff_norm(acc0);
+      if (DIM > 1)
+        ff_acc_prod(acc1, N[1][r1].hi, N[1][r1].lo, acc0);
+      else
+        acc1 = acc0;
+    }
+    acc1 = ff_norm(acc1);
+    if (DIM > 2)
+      ff_acc_prod(acc, N[2][r2].hi, N[2][r2].lo, acc1);
+    else
+      acc = acc1;
+  }
+  return ff_norm(acc);
+}
+
+// One point: knot coordinates xk[a] (a < dim), derivative orders der[a].
+template <int P>
+__device__ __forceinline__ ff decode_point_ff(int dim, int p_rt, const double (&xk)[3], const int (&ns)[3],
+                                              const int (&der)[3], const ff* __restrict__ Pc, long long n0,
+                                              long long n01) {
+  ff N[3][DegreeOf<P>::kLen];
+  int span[3] = {0, 0, 0};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (a < dim) {
+      ff t;
+      span[a] = knot_span_ff(xk[a], ns[a], t);
+      basis_derivs_ff<P>(span[a], t, p_rt, ns[a], der[a], N[a]);
+    }
+  }
+  const ff* row0 = Pc + span[0] + span[1] * n0 + span[2] * n01;
+  if (dim == 3) return tensor_sum_ff<P, 3>(row0, n0, n01, p_rt, N);
+  if (dim == 2) return tensor_sum_ff<P, 2>(row0, n0, n01, p_rt, N);
+  return tensor_sum_ff<P, 1>(row0, n0, n01, p_rt, N);
+}
+
+// Batch instances (same indexing as k_decode_points_inst), one point per
+// thread; P > 0 when every instance of the batch has degree P.
+template <int P>
+__global__ void k_decode_points_inst_ff(const InstDesc* __restrict__ desc, const int* __restrict__ qinst,
+                                        const long long* __restrict__ pt_off, int nq, const double* __restrict__ pts,
+                                        const ff* __restrict__ Pc, double* __restrict__ out) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= pt_off[nq]) return;
+  int lo = 0, hi = nq - 1;  // last query whose first point is <= k
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pt_off[mid] <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  const InstDesc D = desc[qinst[lo]];
+  const double* u = pts + 3 * k;
+  const double xk[3] = {u[0] * D.nspans[0], u[1] * D.nspans[1], u[2] * D.nspans[2]};
+  const int der[3] = {0, 0, 0};
+  const ff v = decode_point_ff<P>(D.dim, D.p, xk, D.nspans, der, Pc + D.cp_off, D.n[0], (long long)D.n[0] * D.n[1]);
+  out[k] = (double)v.hi + (double)v.lo;
+}
+
+void launch_decode_points_inst_ff(const InstDesc* desc, const int* qinst, const long long* pt_off, int nq,
+                                  long long npts, const double* pts, const ff* P, double* out, int p_uniform,
+                                  cudaStream_t st) {
+  const unsigned blocks = (unsigned)((npts + 127) / 128);
+  switch (p_uniform) {
+    case 1: k_decode_points_inst_ff<1><<<blocks, 128, 0, st>>>(desc, qinst, pt_off, nq, pts, P, out); break;
+    case 2: k_decode_points_inst_ff<2><<<blocks, 128, 0, st>>>(desc, qinst, pt_off, nq, pts, P, out); break;
+    case 3: k_decode_points_inst_ff<3><<<blocks, 128, 0, st>>>(desc, qinst, pt_off, nq, pts, P, out); break;
+    case 4: k_decode_points_inst_ff<4><<<blocks, 128, 0, st>>>(desc, qinst, pt_off, nq, pts, P, out); break;
+    default: k_decode_points_inst_ff<0><<<blocks, 128, 0, st>>>(desc, qinst, pt_off, nq, pts, P, out); break;
+  }
+}
+
+// Model points in the model's coordinates: x_k = (pts - lo) * s with s =
+// nspans / (hi - lo) per axis; the derivative scale is formed on the host.
+struct PointMap {
+  double lo[3], s[3];
+  int ns[3], der[3];
+  long long n0, n01;
+  int dim, p;
+  double scale;
+};
+
+template <int P>
+__global__ void k_decode_points_ff(PointMap m, const double* __restrict__ pts, long long npts,
+                                   const ff* __restrict__ Pc, void* __restrict__ out, int out_dtype) {
+  const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= npts) return;
+  double xk[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (a < m.dim) xk[a] = (pts[k * m.dim + a] - m.lo[a]) * m.s[a];
+  const ff v = decode_point_ff<P>(m.dim, m.p, xk, m.ns, m.der, Pc, m.n0, m.n01);
+  if (m.scale != 1.0) {
+    const double d = ((double)v.hi + (double)v.lo) * m.scale;
+    if (out_dtype == MFA_F64)
+      ((double*)out)[k] = d;
+    else
+      ((float*)out)[k] = (float)d;
+  } else if (out_dtype == MFA_F64) {
+    ((double*)out)[k] = (double)v.hi + (double)v.lo;
+  } else {
+    ((float*)out)[k] = __fadd_rn(v.hi, v.lo);
+  }
+}
+
+void launch_decode_points_ff(const LayoutDev& L, const double* lo, const double* hi, const double* pts,
+                             long long npts, const int* deriv, const ff* P, void* out, int out_dtype, cudaStream_t st) {
+  if (npts <= 0) return;
+  PointMap m;
+  m.dim = L.dim;
+  m.p = L.ax[0].p;
+  m.scale = 1.0;
+  for (int a = 0; a < 3; ++a) {
+    const bool on = a < L.dim;
+    const double len = on ? hi[a] - lo[a] : 0.0;
+    m.lo[a] = on ? lo[a] : 0.0;
+    m.ns[a] = L.ax[a].nspans;
+    m.s[a] = len != 0.0 ? (double)m.ns[a] / len : 0.0;
+    m.der[a] = on ? deriv[a] : 0;
+    for (int r = 0; r < m.der[a]; ++r) m.scale *= (double)m.ns[a] / len;  // d/du = nspans d/dx, u = (x - lo) / len
+  }
+  m.n0 = L.ncp[0];
+  m.n01 = (long long)L.ncp[0] * L.ncp[1];
+  const unsigned blocks = (unsigned)((npts + 127) / 128);
+  switch (m.p) {
+    case 1: k_decode_points_ff<1><<<blocks, 128, 0, st>>>(m, pts, npts, P, out, out_dtype); break;
+    case 2: k_decode_points_ff<2><<<blocks, 128, 0, st>>>(m, pts, npts, P, out, out_dtype); break;
+    case 3: k_decode_points_ff<3><<<blocks, 128, 0, st>>>(m, pts, npts, P, out, out_dtype); break;
+    case 4: k_decode_points_ff<4><<<blocks, 128, 0, st>>>(m, pts, npts, P, out, out_dtype); break;
+    default: k_decode_points_ff<0><<<blocks, 128, 0, st>>>(m, pts, npts, P, out, out_dtype); break;
+  }
+}
 
 template <typename TIn, typename TOut>
 __global__ void k_cast(const TIn* in, TOut* out, long long n) {

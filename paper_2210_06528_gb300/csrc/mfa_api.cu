@@ -2707,12 +2707,16 @@ int batch_decode_points_impl(mfa_handle* h, const mfa_batch* b, int32_t nq, cons
     if (e == cudaSuccess) std::memcpy(&npts, h->h_pinned, sizeof(long long));
   }
   if (e == cudaSuccess && npts > 0) {
+    int p_uniform = b->inst.empty() ? 0 : b->inst[0].degree;
+    for (const mfa_instance& in : b->inst)
+      if (in.degree != p_uniform) p_uniform = 0;
     if (b->prec == MFA_PREC_FP64)
       TRACED(h, TR_DECODE_POINTS, (launch_decode_points_inst<double>((const InstDesc*)b->desc, dq, doff, nq, npts, dp,
-                                                                     (const double*)b->buf, dout, h->stream)));
+                                                                     (const double*)b->buf, dout, p_uniform,
+                                                                     h->stream)));
     else
       TRACED(h, TR_DECODE_POINTS, (launch_decode_points_inst<ff>((const InstDesc*)b->desc, dq, doff, nq, npts, dp,
-                                                                 (const ff*)b->buf, dout, h->stream)));
+                                                                 (const ff*)b->buf, dout, p_uniform, h->stream)));
   }
   if (e == cudaSuccess && !on_device && npts > 0)
     e = cudaMemcpyAsync(out, dout, (size_t)npts * sizeof(double), cudaMemcpyDeviceToHost, h->stream);

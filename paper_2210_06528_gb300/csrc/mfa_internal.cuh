@@ -218,7 +218,8 @@ struct InstDesc {
 };
 template <typename T>
 void launch_decode_points_inst(const InstDesc* desc, const int* qinst, const long long* pt_off, int nq,
-                               long long npts, const double* pts, const T* P, double* out, cudaStream_t st);
+                               long long npts, const double* pts, const T* P, double* out, int p_uniform,
+                               cudaStream_t st);  // p_uniform: the degree of every instance, else 0
 
 
 constexpr int kResidualBlocks = 1216;  // 8 x 152 SMs

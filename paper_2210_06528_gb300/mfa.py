@@ -339,7 +339,17 @@ def mfa_batch_tile_sizes(b: int):
 
 
 def mfa_batch_decode_points(h: int, b: int, qinst, pt_off, pts, out) -> None:
-    """Host arrays: qinst int32 [nq], pt_off int64 [nq + 1], pts float64 [npts, 3], out float64 [npts]."""
+    """Host arrays: qinst int32 [nq], pt_off int64 [nq + 1], pts float64 [npts, 3], out float64 [npts];
+    or all four as contiguous CUDA tensors of those types."""
+    if hasattr(pts, "is_cuda") and pts.is_cuda:
+        for t, dt in ((qinst, "torch.int32"), (pt_off, "torch.int64"), (pts, "torch.float64"), (out, "torch.float64")):
+            if not (hasattr(t, "is_cuda") and t.is_cuda and t.is_contiguous() and str(t.dtype) == dt):
+                raise TypeError("device decode: qinst int32, pt_off int64, pts and out float64, contiguous CUDA")
+        _check(load().mfa_batch_decode_points(ctypes.c_void_p(h), ctypes.c_void_p(b), int(qinst.numel()),
+                                              ctypes.c_void_p(qinst.data_ptr()), ctypes.c_void_p(pt_off.data_ptr()),
+                                              ctypes.c_void_p(pts.data_ptr()), ctypes.c_void_p(out.data_ptr()), 1),
+               "mfa_batch_decode_points")
+        return
     qinst = np.ascontiguousarray(qinst, dtype=np.int32)
     pt_off = np.ascontiguousarray(pt_off, dtype=np.int64)
     pts = np.ascontiguousarray(pts, dtype=np.float64)
@@ -679,7 +689,11 @@ class Batch:
 
     def decode_points(self, qinst, pt_off, pts, out=None):
         """Scattered decode: query k evaluates instance qinst[k] at pts[pt_off[k]:pt_off[k+1]]
-        (parameters in [0,1], three per point); returns float64 values."""
+        (parameters in [0,1], three per point); returns float64 values.  CUDA
+        tensors (int32, int64, float64 [npts, 3], float64 out) stay on the device."""
+        if hasattr(pts, "is_cuda") and pts.is_cuda:
+            mfa_batch_decode_points(self.handle.h, self.b, qinst, pt_off, pts, out)
+            return out
         pts = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
         if out is None:
             out = np.empty(len(pts), dtype=np.float64)

@@ -149,6 +149,47 @@ def test_batch_decode_points_matches_grid_and_oracle():
         h.close()
 
 
+@pytest.mark.parametrize("degrees", [(1, 5), (1, 1), (2, 2), (3, 3), (4, 4), (6, 7)])
+def test_batch_decode_points_float_float(degrees):
+    """Scattered decode of a mixed-precision batch (float-float control
+    points, float-float arithmetic): equal to the oracle's decode of the
+    batch's own control points at random parameters, at the knots, at 0 and
+    1, and at parameters outside [0, 1] (clamped).  One degree per batch runs
+    the kernel compiled for that degree; several degrees, the general one."""
+    import torch
+    specs, data = inputs.batch_instances(12, seed=21, size2=(14, 70), size3=(10, 26), degrees=degrees,
+                                         dims=(1, 2, 3))
+    h = mfa.Handle(0)
+    rng = np.random.default_rng(3)
+    try:
+        b = h.encode_batch(specs, torch.from_numpy(data).cuda(), mfa.MFA_PREC_MIXED)
+        P = b.ctrl()
+        off = b.offsets()
+        qinst, poff, pts, want = [], [0], [], []
+        for i, sp in enumerate(specs):
+            d, p = sp["dim"], sp["degree"]
+            ncp = [n + p for n in sp["nspans"]]
+            prob = O.make_problem(p, list(sp["npts"]), list(sp["nspans"]), [1] * d, 0)
+            Pi = P[off[i]:off[i + 1]].reshape(tuple(reversed(ncp)))
+            u = rng.uniform(0, 1, size=(200, 3))
+            ns = max(sp["nspans"])
+            knots = np.arange(ns + 1) / ns
+            u[:len(knots), 0] = knots
+            u[len(knots):len(knots) + 4] = [[0, 0, 0], [1, 1, 1], [-0.25, 1.5, 0.5], [1.75, -1e-3, 1.0]]
+            qinst.append(i)
+            pts.append(u)
+            poff.append(poff[-1] + len(u))
+            want.append(O.scattered_decode(prob, Pi, np.clip(u[:, :d], 0.0, 1.0)))
+        got = b.decode_points(qinst, poff, np.concatenate(pts))
+        for i in range(len(specs)):
+            g = got[poff[i]:poff[i + 1]]
+            scale = max(1.0, np.abs(P[off[i]:off[i + 1]]).max())
+            assert np.abs(g - want[i]).max() <= 1e-12 * scale, (i, specs[i])
+        b.free()
+    finally:
+        h.close()
+
+
 def test_batch_of_many_small_3d_fits_fused_path():
     """Many similar small 3-D fits (no instance dominates the batch): the
     fused float-float kernels run one CTA per instance; every instance checked

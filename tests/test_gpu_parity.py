@@ -171,6 +171,35 @@ def test_scattered_decode_and_derivatives():
         g.close()
 
 
+@pytest.mark.parametrize("p", [2, 3, 5])
+def test_scattered_decode_float_float(p):
+    """Scattered decode of a mixed-precision model (float-float control
+    points and arithmetic) with derivatives, FP64 and FP32 output: equal to
+    the oracle's decode of the model's own control points."""
+    Q = inputs.paper_2d(50)
+    lo, hi = [-4.0, -4.0], [4.0, 4.0]
+    prob = oracle_problem(Q, p, [16, 15], [2, 2], 3)
+    g = GpuRun(Q.astype(np.float32), p, [16, 15], [2, 2], 3, lo=lo, hi=hi, precision=mfa.MFA_PREC_MIXED)
+    try:
+        g.iterate(4)
+        P = g.ctrl()
+        u = inputs.uniform_points(500, 2, seed=9)
+        u[:4] = [[0, 0], [1, 1], [0.5, 1.0], [0.25, 0.0]]
+        x = np.asarray(lo) + u * (np.asarray(hi) - np.asarray(lo))
+        for der in [(0, 0), (1, 0), (0, 2), (1, 1), (p, 1)]:
+            out = np.empty(len(u))
+            g.model.decode_points(np.ascontiguousarray(x), out, der)
+            oref = O.scattered_decode(prob, P, u, der) / (8.0 ** sum(der))
+            scale = max(np.abs(oref).max(), 1e-12)
+            assert np.abs(out - oref).max() <= 1e-11 * scale, der
+        out32 = np.empty(len(u), dtype=np.float32)
+        g.model.decode_points(np.ascontiguousarray(x), out32, (0, 0))
+        oref = O.scattered_decode(prob, P, u)
+        assert np.abs(out32 - oref).max() <= 2e-7 * max(np.abs(oref).max(), 1e-12)
+    finally:
+        g.close()
+
+
 def test_mixed_precision_2d_noise():
     """FP32 data passes and control-point iteration; FP64 Gram/Cholesky."""
     Q = inputs.sinc_2d(256, noise=1e-3, seed=0, dtype=np.float32)
