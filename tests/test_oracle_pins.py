@@ -456,3 +456,33 @@ def test_overlap_sweep_approaches_single_subdomain_fit():
         assert devs[d + 1] * 3 <= devs[d]
     assert devs[2] > 1e-9
     assert max(devs[3:]) <= 1e-12
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_scattered_derivatives_reproduce_polynomial_derivatives(p):
+    """Sec. 2.1: a tensor polynomial of per-axis degree <= p lies in the spline
+    space, so the global fit reproduces it and every mixed partial derivative
+    of the decoded spline equals the polynomial's, computed here in closed
+    form from its coefficients. Orders differ per axis and the coefficients
+    differ per axis, so a derivative taken along the wrong axis fails."""
+    npts, nspans = (23, 19, 17), (5, 4, 3)
+    rng = np.random.default_rng(40 + p)
+    coef = [rng.standard_normal(p + 1) for _ in range(3)]
+    X = np.meshgrid(*[uniform_u(M) for M in reversed(npts)], indexing="ij")  # numpy axis 0 = grid axis 2
+    Q = np.ones(X[0].shape)
+    for a in range(3):
+        Q = Q * np.polynomial.polynomial.polyval(X[2 - a], coef[a])
+    prob = O.make_problem(p, npts, nspans, [1, 1, 1], 0)
+    P = O.global_fit(prob, Q)
+    u = rng.uniform(0.0, 1.0, size=(25, 3))
+    u[0] = 0.0
+    u[1] = 1.0
+    u[2] = [1 / nspans[0], 2 / nspans[1], 1 / nspans[2]]  # on interior breakpoints
+    for order in [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 0, 2), (2, 0, 1), (1, 1, 1), (p, 0, 0), (0, 2, p)]:
+        ours = O.scattered_decode(prob, P, u, deriv=order)
+        ref = np.ones(len(u))
+        for a in range(3):
+            c = np.polynomial.polynomial.polyder(coef[a], order[a]) if order[a] else coef[a]
+            ref = ref * np.polynomial.polynomial.polyval(u[:, a], c)
+        scale = max(1.0, np.abs(ref).max()) * (p * max(nspans)) ** sum(order)
+        assert np.abs(ours - ref).max() <= 1e-12 * scale, order
