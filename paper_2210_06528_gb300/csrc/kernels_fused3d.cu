@@ -172,6 +172,10 @@ __device__ __forceinline__ void cp_async_f32(float* dst, const float* src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async_8(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
@@ -1832,6 +1836,12 @@ __global__ void __launch_bounds__(128) k_iter0_xy_ff(LayoutDev L, const long lon
   size_t off = (size_t)2 * W * (nL0 + nL1) * 4;
   off = (off + 15) & ~size_t(15);
   ff* T = reinterpret_cast<ff*>(smem + off);  // [npl][nL1][nL0]
+  const int npp = nL0 * nL1;
+  const long long base = offL[s] + (long long)lz0 * npp;
+  // the planes' right-hand sides as asynchronous 8-byte copies, all in
+  // flight together, under the factor tables' loads
+  for (int i = threadIdx.x; i < npl * npp; i += blockDim.x) cp_async_8(T + i, BL + base + i);
+  cp_async_commit();
   const ff* Fx = L.ax[0].facL_ff + (long long)bx.bandL * W;
   const ff* Fy = L.ax[1].facL_ff + (long long)by.bandL * W;
   for (int i = threadIdx.x; i < nL0 * W; i += blockDim.x) {
@@ -1842,9 +1852,7 @@ __global__ void __launch_bounds__(128) k_iter0_xy_ff(LayoutDev L, const long lon
     fyh[i] = Fy[i].hi;
     fyl[i] = Fy[i].lo;
   }
-  const int npp = nL0 * nL1;
-  const long long base = offL[s] + (long long)lz0 * npp;
-  for (int i = threadIdx.x; i < npl * npp; i += blockDim.x) T[i] = BL[base + i];
+  cp_async_wait_all();
   __syncthreads();
   for (int f = threadIdx.x; f < npl * nL1; f += blockDim.x) solve_fibre_ff<P>(T + f * nL0, nL0, 1, fxh, fxl);
   __syncthreads();
@@ -1856,10 +1864,15 @@ __global__ void __launch_bounds__(128) k_iter0_xy_ff(LayoutDev L, const long lon
   for (int i = threadIdx.x; i < npl * npp; i += blockDim.x) X[base + i] = T[i];
 }
 
+// staged = 1: the thread's fibre is first copied into its own column of
+// shared memory (n x blockDim.x float-float values; every copy in flight
+// together), solved there and written back; no other thread reads the
+// column, so no block barrier is needed.  staged = 0: solved in place.
 template <int P>
 __global__ void __launch_bounds__(128) k_iter0_z_ff(LayoutDev L, const long long* __restrict__ offL,
-                                                    ff* __restrict__ X) {
+                                                    ff* __restrict__ X, int staged) {
   constexpr int W = P + 1;
+  extern __shared__ __align__(16) unsigned char zsm[];
   const int s = blockIdx.y;
   int s0, s1, s2;
   sub_pieces(L, s, s0, s1, s2);
@@ -1868,8 +1881,17 @@ __global__ void __launch_bounds__(128) k_iter0_z_ff(LayoutDev L, const long long
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nf) return;
   const int n = bz.nL;
-  const long long st = nf;
-  ff* x = X + offL[s] + f;
+  ff* const xg = X + offL[s] + f;
+  ff* x = xg;
+  long long st = nf;
+  if (staged) {
+    ff* col = reinterpret_cast<ff*>(zsm) + threadIdx.x;
+    for (int i = 0; i < n; ++i) cp_async_8(col + i * blockDim.x, xg + (long long)i * nf);
+    cp_async_commit();
+    cp_async_wait_all();
+    x = col;
+    st = blockDim.x;
+  }
   const ff* F = L.ax[2].facL_ff + (long long)bz.bandL * W;
   ff win[P];  // the last P solved values, win[0] the most recent
 #pragma unroll
@@ -1904,6 +1926,8 @@ __global__ void __launch_bounds__(128) k_iter0_z_ff(LayoutDev L, const long long
     for (int e = P - 1; e > 0; --e) win[e] = win[e - 1];
     win[0] = v;
   }
+  if (staged)
+    for (int i = 0; i < n; ++i) xg[(long long)i * nf] = x[i * st];
 }
 
 // Returns the number of kernels launched (0 when not covered).
@@ -1916,10 +1940,13 @@ int launch_iter0_3d_ff(const LayoutDev& L, const long long* offL, const int* max
   if (smem > 200 * 1024) return 0;
   dim3 g1(L.nsub, (maxnL[2] + kIt0Planes - 1) / kIt0Planes);
   dim3 g2((maxnL[0] * maxnL[1] + 127) / 128, L.nsub);
+  // z fibres staged in shared memory when a block's columns fit in 48 KB
+  const size_t zsmem = (size_t)maxnL[2] * 128 * sizeof(ff);
+  const int zstaged = zsmem <= 48 * 1024;
   auto go = [&](auto kxy, auto kz) {
     ensure_smem(kxy, smem);
     kxy<<<g1, 128, smem, st>>>(L, offL, BL, X);
-    kz<<<g2, 128, 0, st>>>(L, offL, X);
+    kz<<<g2, 128, zstaged ? zsmem : 0, st>>>(L, offL, X, zstaged);
   };
   switch (p) {
     case 2: go(k_iter0_xy_ff<2>, k_iter0_z_ff<2>); return 2;
