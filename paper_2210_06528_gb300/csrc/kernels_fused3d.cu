@@ -1864,15 +1864,10 @@ __global__ void __launch_bounds__(128) k_iter0_xy_ff(LayoutDev L, const long lon
   for (int i = threadIdx.x; i < npl * npp; i += blockDim.x) X[base + i] = T[i];
 }
 
-// staged = 1: the thread's fibre is first copied into its own column of
-// shared memory (n x blockDim.x float-float values; every copy in flight
-// together), solved there and written back; no other thread reads the
-// column, so no block barrier is needed.  staged = 0: solved in place.
 template <int P>
 __global__ void __launch_bounds__(128) k_iter0_z_ff(LayoutDev L, const long long* __restrict__ offL,
-                                                    ff* __restrict__ X, int staged) {
+                                                    ff* __restrict__ X) {
   constexpr int W = P + 1;
-  extern __shared__ __align__(16) unsigned char zsm[];
   const int s = blockIdx.y;
   int s0, s1, s2;
   sub_pieces(L, s, s0, s1, s2);
@@ -1881,17 +1876,8 @@ __global__ void __launch_bounds__(128) k_iter0_z_ff(LayoutDev L, const long long
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= nf) return;
   const int n = bz.nL;
-  ff* const xg = X + offL[s] + f;
-  ff* x = xg;
-  long long st = nf;
-  if (staged) {
-    ff* col = reinterpret_cast<ff*>(zsm) + threadIdx.x;
-    for (int i = 0; i < n; ++i) cp_async_8(col + i * blockDim.x, xg + (long long)i * nf);
-    cp_async_commit();
-    cp_async_wait_all();
-    x = col;
-    st = blockDim.x;
-  }
+  const long long st = nf;
+  ff* x = X + offL[s] + f;
   const ff* F = L.ax[2].facL_ff + (long long)bz.bandL * W;
   ff win[P];  // the last P solved values, win[0] the most recent
 #pragma unroll
@@ -1926,8 +1912,6 @@ __global__ void __launch_bounds__(128) k_iter0_z_ff(LayoutDev L, const long long
     for (int e = P - 1; e > 0; --e) win[e] = win[e - 1];
     win[0] = v;
   }
-  if (staged)
-    for (int i = 0; i < n; ++i) xg[(long long)i * nf] = x[i * st];
 }
 
 // Returns the number of kernels launched (0 when not covered).
@@ -1940,13 +1924,10 @@ int launch_iter0_3d_ff(const LayoutDev& L, const long long* offL, const int* max
   if (smem > 200 * 1024) return 0;
   dim3 g1(L.nsub, (maxnL[2] + kIt0Planes - 1) / kIt0Planes);
   dim3 g2((maxnL[0] * maxnL[1] + 127) / 128, L.nsub);
-  // z fibres staged in shared memory when a block's columns fit in 48 KB
-  const size_t zsmem = (size_t)maxnL[2] * 128 * sizeof(ff);
-  const int zstaged = zsmem <= 48 * 1024;
   auto go = [&](auto kxy, auto kz) {
     ensure_smem(kxy, smem);
     kxy<<<g1, 128, smem, st>>>(L, offL, BL, X);
-    kz<<<g2, 128, zstaged ? zsmem : 0, st>>>(L, offL, X, zstaged);
+    kz<<<g2, 128, 0, st>>>(L, offL, X);
   };
   switch (p) {
     case 2: go(k_iter0_xy_ff<2>, k_iter0_z_ff<2>); return 2;
