@@ -36,7 +36,7 @@ from paper_2210_06528_gb300 import inputs  # noqa: E402
 METRIC = "encode pts/s (Schwarz-converged) + decode pts/s vs plain GPU; serve p50/p99"
 
 WORKLOADS = {
-    # BASELINE 3-D workload: 512^3 FP32 grid of 16 seeded Gaussians + sin(6 pi x) cos(4 pi y) z,
+    # 3-D workload: 512^3 FP32 grid of 16 seeded Gaussians + sin(6 pi x) cos(4 pi y) z,
     # p = 3, 8x8x8 subdomains of 24 core spans (192 spans, 195 control points per axis), overlap 2.
     "3d": dict(name="3d_512^3_gauss16_p3_8x8x8sub_24spans_overlap2_mixed", npts=(512, 512, 512), p=3,
                nspans=(192, 192, 192), nsub=(8, 8, 8), delta=2, precision="mixed", tol=1e-7, max_iters=50,
@@ -46,11 +46,11 @@ WORKLOADS = {
     "3d384": dict(name="3d_384^3_gauss16_p3_6x6x6sub_24spans_overlap2_mixed", npts=(384, 384, 384), p=3,
                   nspans=(144, 144, 144), nsub=(6, 6, 6), delta=2, precision="mixed", tol=1e-7, max_iters=50,
                   sample=dict(npts=(128, 128, 128), nspans=(48, 48, 48), nsub=(2, 2, 2))),
-    # BASELINE 2-D workload: 1024^2 sinc(x) sinc(y) + N(0, 1e-3), p = 3, 4x4 subdomains of 64 core spans.
+    # 2-D workload: 1024^2 sinc(x) sinc(y) + N(0, 1e-3), p = 3, 4x4 subdomains of 64 core spans.
     "2d": dict(name="2d_1024^2_sinc_noise1e-3_p3_4x4sub_64spans_overlap2_mixed", npts=(1024, 1024), p=3,
                nspans=(256, 256), nsub=(4, 4), delta=2, precision="mixed", tol=1e-6, max_iters=50,
                sample=dict(npts=(512, 512), nspans=(128, 128), nsub=(2, 2))),
-    # BASELINE 1-D workload: 1024 points of sin(x)/x, p = 3, 4 subdomains of 32 core spans, FP64.
+    # 1-D workload: 1024 points of sin(x)/x, p = 3, 4 subdomains of 32 core spans, FP64.
     "1d": dict(name="1d_1024_sinc_p3_4sub_32spans_overlap2_fp64", npts=(1024,), p=3, nspans=(128,), nsub=(4,),
                delta=2, precision="fp64", tol=1e-10, max_iters=200,
                sample=dict(npts=(1024,), nspans=(128,), nsub=(4,))),

@@ -25,7 +25,7 @@ What it computes, in the paper's order (Algorithm 1):
     iterate averages every owned copy with weight 1/n_s.
   * Algorithm 1, "update local error": decode R P and the residual Q - R P.
 
-Readings where the paper is silent (all are listed in the design doc):
+Readings where the paper is silent:
   * data parameters u_k = k / (M - 1) on every axis; M = 1 gives u = 0;
   * global knots clamped and uniform: nspans spans, n = nspans + p control
     points; subdomain interfaces sit on breakpoints, so interior knots float;

@@ -28,7 +28,7 @@ def rel_diff(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-class GpuRun:
+class GpuFit:
     """One model on the GPU; keeps the handle alive."""
 
     def __init__(self, Q, p, nspans, nsub, delta, precision=mfa.MFA_PREC_FP64, cores=None, on_device=True,

@@ -8,7 +8,7 @@ the FP64 bar (relative difference <= 1e-9).
 import numpy as np
 import pytest
 
-from mfa_cases import TOL_FP64, GpuRun, oracle_problem, rel_diff
+from mfa_cases import TOL_FP64, GpuFit, oracle_problem, rel_diff
 from oracle import mfa_oracle as O
 from paper_2210_06528_gb300 import inputs, mfa
 
@@ -19,7 +19,7 @@ def _mixed_case(Q, p, nspans, nsub, delta, tol, max_iters=50, check_decode=True)
     Qd = Q.astype(np.float64)
     prob = oracle_problem(Qd, p, nspans, nsub, delta)
     ref = O.schwarz_solve(prob, Qd, max_iters=max_iters, tol_dP=tol)
-    g = GpuRun(Q, p, nspans, nsub, delta, precision=mfa.MFA_PREC_MIXED)
+    g = GpuFit(Q, p, nspans, nsub, delta, precision=mfa.MFA_PREC_MIXED)
     try:
         rc, rep = g.iterate(max_iters, tol)
         assert rep.iters == ref["iters"]
@@ -96,7 +96,7 @@ def test_mixed_3d_unaligned_base_matches_aligned():
     element by element; the fit is bit-identical to the tensor-copy staging."""
     import torch
     Q = inputs.gauss_3d((64, 56, 48), seed=11, dtype=np.float32)
-    a = GpuRun(Q, 3, [20, 18, 16], [2, 2, 2], 2, precision=mfa.MFA_PREC_MIXED)
+    a = GpuFit(Q, 3, [20, 18, 16], [2, 2, 2], 2, precision=mfa.MFA_PREC_MIXED)
     h = mfa.Handle(0)
     try:
         a.iterate(4, 0.0)

@@ -8,7 +8,7 @@ Mixed path: decoded RMS within 1% of the oracle's and max |decoded difference|
 import numpy as np
 import pytest
 
-from mfa_cases import TOL_FP64, GpuRun, oracle_problem, rel_diff
+from mfa_cases import TOL_FP64, GpuFit, oracle_problem, rel_diff
 from oracle import mfa_oracle as O
 from paper_2210_06528_gb300 import inputs, mfa
 
@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 def _iterate_parity(Q, p, nspans, nsub, delta, iters, cores=None, on_device=True, update="average"):
     prob = oracle_problem(Q, p, nspans, nsub, delta, cores)
-    g = GpuRun(Q, p, nspans, nsub, delta, cores=cores, on_device=on_device)
+    g = GpuFit(Q, p, nspans, nsub, delta, cores=cores, on_device=on_device)
     try:
         if update == "owner":
             g.model.set_update_rule(mfa.MFA_UPDATE_OWNER)
@@ -49,7 +49,7 @@ def test_config1_sinc_1d_fp64_full():
     Q = inputs.sinc_1d(1024)
     prob = oracle_problem(Q, 3, [128], [4], 2)
     ref = O.schwarz_solve(prob, Q, max_iters=200, tol_dP=1e-10, keep_iterates=True)
-    g = GpuRun(Q, 3, [128], [4], 2)
+    g = GpuFit(Q, 3, [128], [4], 2)
     try:
         assert rel_diff(g.ctrl(), ref["iterates"][0]) <= TOL_FP64
         rc, rep = g.iterate(200, 1e-10)
@@ -98,7 +98,7 @@ def test_3d_anisotropic_fp32_input():
     Q = inputs.gauss_3d((37, 29, 23), seed=3, dtype=np.float32)
     Qd = Q.astype(np.float64)
     prob = oracle_problem(Qd, 3, [12, 9, 7], [2, 2, 1], 2)
-    g = GpuRun(Q, 3, [12, 9, 7], [2, 2, 1], 2)
+    g = GpuFit(Q, 3, [12, 9, 7], [2, 2, 1], 2)
     try:
         st = O.schwarz_initial(prob, Qd)
         assert rel_diff(g.ctrl(), st.P) <= TOL_FP64
@@ -112,7 +112,7 @@ def test_3d_anisotropic_fp32_input():
 
 def test_single_subdomain_equals_global_fit():
     Q = inputs.paper_2d(64)
-    g = GpuRun(Q, 3, [20, 17], [1, 1], 2)
+    g = GpuFit(Q, 3, [20, 17], [1, 1], 2)
     try:
         prob = oracle_problem(Q, 3, [20, 17], [1, 1], 2)
         Pg = O.global_fit(prob, Q)
@@ -128,7 +128,7 @@ def test_overlap_ge_p_converges_to_global_fit():
     Q = inputs.asymmetric_sinc_1d(400)
     prob = oracle_problem(Q, 3, [80], [5], 3)
     Pg = O.global_fit(prob, Q)
-    g = GpuRun(Q, 3, [80], [5], 3)
+    g = GpuFit(Q, 3, [80], [5], 3)
     try:
         rc, rep = g.iterate(300, 1e-14)
         assert rc == mfa.MFA_OK
@@ -140,7 +140,7 @@ def test_overlap_ge_p_converges_to_global_fit():
 
 def test_polynomial_reproduction_on_gpu():
     Q = inputs.tensor_polynomial((45, 38), 3, seed=2)
-    g = GpuRun(Q, 3, [14, 12], [3, 3], 1)
+    g = GpuFit(Q, 3, [14, 12], [3, 3], 1)
     try:
         res = g.residual()
         assert res.maxabs_decoded <= 1e-10 * res.data_range
@@ -155,7 +155,7 @@ def test_scattered_decode_and_derivatives():
     lo, hi = [-4.0, -4.0], [4.0, 4.0]
     prob = oracle_problem(Q, 3, [16, 15], [2, 2], 3)
     ref = O.schwarz_solve(prob, Q, max_iters=50, tol_dP=1e-13)
-    g = GpuRun(Q, 3, [16, 15], [2, 2], 3, lo=lo, hi=hi)
+    g = GpuFit(Q, 3, [16, 15], [2, 2], 3, lo=lo, hi=hi)
     try:
         g.iterate(50, 1e-13)
         u = inputs.uniform_points(500, 2, seed=9)
@@ -179,7 +179,7 @@ def test_scattered_decode_float_float(p):
     Q = inputs.paper_2d(50)
     lo, hi = [-4.0, -4.0], [4.0, 4.0]
     prob = oracle_problem(Q, p, [16, 15], [2, 2], 3)
-    g = GpuRun(Q.astype(np.float32), p, [16, 15], [2, 2], 3, lo=lo, hi=hi, precision=mfa.MFA_PREC_MIXED)
+    g = GpuFit(Q.astype(np.float32), p, [16, 15], [2, 2], 3, lo=lo, hi=hi, precision=mfa.MFA_PREC_MIXED)
     try:
         g.iterate(4)
         P = g.ctrl()
@@ -206,7 +206,7 @@ def test_mixed_precision_2d_noise():
     Qd = Q.astype(np.float64)
     prob = oracle_problem(Qd, 3, [64, 64], [4, 4], 2)
     ref = O.schwarz_solve(prob, Qd, max_iters=30, tol_dP=1e-7)
-    g = GpuRun(Q, 3, [64, 64], [4, 4], 2, precision=mfa.MFA_PREC_MIXED)
+    g = GpuFit(Q, 3, [64, 64], [4, 4], 2, precision=mfa.MFA_PREC_MIXED)
     try:
         g.iterate(30, 1e-6)
         res = g.residual()
@@ -342,7 +342,7 @@ def test_plain_per_subdomain_form_equals_batched_fp64():
     Q = inputs.gauss_3d((30, 28, 26), seed=5, dtype=np.float32)
     Qd = Q.astype(np.float64)
     nspans, nsub, delta = [8, 7, 6], [2, 2, 2], 2
-    g = GpuRun(Q, 3, nspans, nsub, delta)
+    g = GpuFit(Q, 3, nspans, nsub, delta)
     h = mfa.Handle(0)
     try:
         rc, rep = g.iterate(30, 1e-10)
@@ -388,7 +388,7 @@ def test_owner_update_mixed_3d_fused():
     prob = oracle_problem(Qd, 3, nspans, nsub, delta)
     # stop well above the float-float rounding floor of dP (about 1e-13)
     ref = O.schwarz_solve(prob, Qd, max_iters=60, tol_dP=1e-10, update="owner")
-    g = GpuRun(Q, 3, nspans, nsub, delta, precision=mfa.MFA_PREC_MIXED)
+    g = GpuFit(Q, 3, nspans, nsub, delta, precision=mfa.MFA_PREC_MIXED)
     try:
         g.model.set_update_rule(mfa.MFA_UPDATE_OWNER)
         rc, rep = g.iterate(60, 1e-10)
@@ -408,7 +408,7 @@ def test_overlap_sweep_on_gpu():
     for delta in range(0, 7):
         prob = oracle_problem(Q, 3, [40], [5], delta)
         o = O.schwarz_solve(prob, Q, max_iters=400, tol_dP=1e-13)
-        g = GpuRun(Q, 3, [40], [5], delta)
+        g = GpuFit(Q, 3, [40], [5], delta)
         try:
             rc, rep = g.iterate(400, 1e-13)
             assert rep.iters == o["iters"]
@@ -478,8 +478,8 @@ def test_fused_projection_split_along_z(p, npts, nspans, nsub):
     delta = 2
     prob = oracle_problem(Qd, p, list(nspans), list(nsub), delta)
     ref = O.schwarz_solve(prob, Qd, max_iters=60, tol_dP=1e-9)
-    g = GpuRun(Q, p, list(nspans), list(nsub), delta, precision=mfa.MFA_PREC_MIXED)
-    gh = GpuRun(Q, p, list(nspans), list(nsub), delta, precision=mfa.MFA_PREC_MIXED, on_device=False)
+    g = GpuFit(Q, p, list(nspans), list(nsub), delta, precision=mfa.MFA_PREC_MIXED)
+    gh = GpuFit(Q, p, list(nspans), list(nsub), delta, precision=mfa.MFA_PREC_MIXED, on_device=False)
     try:
         rc, rep = g.iterate(60, 1e-9)
         assert rc == mfa.MFA_OK and rep.iters == ref["iters"]

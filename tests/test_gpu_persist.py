@@ -6,7 +6,7 @@ import os
 import numpy as np
 import pytest
 
-from mfa_cases import GpuRun
+from mfa_cases import GpuFit
 from paper_2210_06528_gb300 import inputs, mfa
 
 pytestmark = pytest.mark.gpu
@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 @pytest.mark.parametrize("precision", [mfa.MFA_PREC_FP64, mfa.MFA_PREC_MIXED])
 def test_save_load_roundtrip_and_continue(tmp_path, precision):
     Q = inputs.gauss_3d((40, 36, 34), seed=8, dtype=np.float32)
-    g = GpuRun(Q, 3, [12, 11, 10], [2, 2, 2], 2, precision=precision)
+    g = GpuFit(Q, 3, [12, 11, 10], [2, 2, 2], 2, precision=precision)
     try:
         g.model.set_update_rule(mfa.MFA_UPDATE_OWNER)
         g.iterate(2, 0.0)
@@ -40,7 +40,7 @@ def test_save_load_roundtrip_and_continue(tmp_path, precision):
 
 def test_stateless_load_decodes_but_does_not_iterate(tmp_path):
     Q = inputs.gauss_3d((30, 28, 26), seed=2, dtype=np.float32)
-    g = GpuRun(Q, 3, [9, 8, 7], [2, 1, 2], 1)
+    g = GpuFit(Q, 3, [9, 8, 7], [2, 1, 2], 1)
     try:
         g.iterate(3, 0.0)
         path = str(tmp_path / "m.mfa")

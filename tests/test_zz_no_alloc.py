@@ -15,7 +15,7 @@ already run every other test.
 import numpy as np
 import pytest
 
-from mfa_cases import GpuRun
+from mfa_cases import GpuFit
 from paper_2210_06528_gb300 import inputs, mfa
 
 pytestmark = pytest.mark.gpu
@@ -26,7 +26,7 @@ TOL = 1e-10
 
 def _reference(Q, p, nspans, nsub, delta):
     import torch
-    g = GpuRun(Q, p, nspans, nsub, delta)
+    g = GpuFit(Q, p, nspans, nsub, delta)
     g.iterate(2)
     ref = torch.empty(Q.shape, dtype=torch.float64, device="cuda")
     g.model.decode_grid(ref)  # the allocating entry point
