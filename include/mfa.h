@@ -233,6 +233,31 @@ int mfa_sync(mfa_handle* h);
 /* Static text for a status code. */
 const char* mfa_status_string(int status);
 
+/* The layout of one axis, built on the host exactly as mfa_encode builds it
+ * (Sec. 2.2: subdomain cores, the overlap delta in knot spans, the data each
+ * subdomain fits, its local control points, and the owner of every control
+ * point for the owner-takes update of Sec. 2.3).  No device is touched, so
+ * this runs on a machine without a GPU.
+ *   npts, nspans, degree   grid points, global knot spans and p of the axis
+ *   nsub, core_spans       subdomains and their core spans (NULL: even
+ *                          split, the extra spans to the first subdomains)
+ *   overlap                delta, in knot spans
+ *   out                    caller-owned, cap >= nsub rows of 8 int32 values,
+ *                          row s = { a, b, w0, w1, k0, k1, l0, nL }:
+ *                          core spans [a, b); window spans [w0, w1) (the core
+ *                          widened by delta, clipped); data points k0..k1
+ *                          (parameters k/(npts-1) in the closed window
+ *                          interval); local control points l0 .. l0+nL-1
+ *   owner                  caller-owned, nspans + degree int32 values or
+ *                          NULL: the subdomain whose core holds control point
+ *                          g's Greville abscissa
+ * Returns MFA_OK; MFA_ERR_ARG for sizes out of range or cap < nsub;
+ * MFA_ERR_LAYOUT for this axis's rejections in mfa_encode (a core of fewer
+ * than degree spans between interfaces, or a window whose collocation matrix
+ * fails the Schoenberg-Whitney condition).  Nothing is written on an error. */
+int mfa_axis_layout(int64_t npts, int32_t nspans, int32_t degree, int32_t nsub, const int32_t* core_spans,
+                    int32_t overlap, int32_t* out, int32_t cap, int32_t* owner);
+
 /* Grid decode that allocates nothing.
  *
  * The paper has no counterpart to this call; it exists for callers that

@@ -875,6 +875,29 @@ const char* mfa_status_string(int s) {
   }
 }
 
+int mfa_axis_layout(int64_t npts, int32_t nspans, int32_t degree, int32_t nsub, const int32_t* core_spans,
+                    int32_t overlap, int32_t* out, int32_t cap, int32_t* owner) {
+  if (!out || npts < 1 || degree < 1 || degree > MFA_MAX_DEGREE || nsub < 1 || cap < nsub) return MFA_ERR_ARG;
+  AxisHost ax;
+  const int rc = build_axis(ax, npts, nspans, degree, nsub, core_spans, overlap);
+  if (rc != MFA_OK) return rc;
+  for (int s = 0; s < nsub; ++s) {
+    const AxisSub& sb = ax.subs[s];
+    int32_t* o = out + 8 * (size_t)s;
+    o[0] = sb.a;
+    o[1] = sb.b;
+    o[2] = sb.w0;
+    o[3] = sb.w1;
+    o[4] = sb.k0;
+    o[5] = sb.k0 + sb.m - 1;
+    o[6] = sb.l0;
+    o[7] = sb.nL;
+  }
+  if (owner)
+    for (int g = 0; g < ax.n; ++g) owner[g] = ax.own_first[g] + ax.own_pick[g];
+  return MFA_OK;
+}
+
 int mfa_create(int device, void* cuda_stream, mfa_handle** out) {
   if (!out) return MFA_ERR_ARG;
   *out = nullptr;

@@ -116,6 +116,10 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_sync.argtypes = [P]
     lib.mfa_status_string.argtypes = [ctypes.c_int]
     lib.mfa_status_string.restype = ctypes.c_char_p
+    lib.mfa_axis_layout.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                    ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    lib.mfa_axis_layout.restype = ctypes.c_int
     lib.mfa_decode_grid_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_int32), P, P, P]
     lib.mfa_decode_grid_noalloc.restype = ctypes.c_int
@@ -202,6 +206,20 @@ def make_layout(dim, degree, npts, nspans, nsub, overlap, precision=MFA_PREC_FP6
     lay.precision = precision
     lay._keep = keep
     return lay
+
+
+def mfa_axis_layout(npts: int, nspans: int, degree: int, nsub: int, overlap: int, core_spans=None):
+    """Host-built layout of one axis (no device needed): returns (rows, owner)
+    with rows[s] = (a, b, w0, w1, k0, k1, l0, nL) per subdomain and owner[g]
+    the Greville owner of control point g; raises MFAError on a rejection."""
+    rows = (ctypes.c_int32 * (8 * max(nsub, 1)))()
+    owner = (ctypes.c_int32 * max(nspans + degree, 1))()
+    cores = None
+    if core_spans is not None:
+        cores = (ctypes.c_int32 * len(core_spans))(*[int(c) for c in core_spans])
+    _check(load().mfa_axis_layout(int(npts), int(nspans), int(degree), int(nsub), cores, int(overlap), rows,
+                                  int(nsub), owner), "mfa_axis_layout")
+    return np.array(rows, dtype=np.int64).reshape(nsub, 8), np.array(owner, dtype=np.int64)
 
 
 def mfa_create(device: int = 0, stream: int = 0) -> int:
