@@ -331,6 +331,9 @@ class Problem:
 
 
 def make_problem(p, npts, nspans, nsub, delta, cores=None) -> Problem:
+    """A decomposed fit (Sec. 2.2): degree p, grid points and global knot spans
+    per axis, subdomains per axis (cores split evenly unless given), and the
+    overlap delta in knot spans (one value or one per axis)."""
     d = len(npts)
     if cores is None:
         cores = [even_cores(nspans[a], nsub[a]) for a in range(d)]
@@ -369,6 +372,9 @@ class SchwarzState:
 
 
 def _local_mats(prob: Problem, s, Nglob, cols: str):
+    """Per-axis collocation matrices of subdomain s (Sec. 2.2): its window's
+    data rows against its local control points L (cols = "L") or its owned
+    ones U (cols = "U"), cut from the global basis matrices."""
     mats = []
     for a, pc in enumerate(s):
         rows = pc.pts
