@@ -24,11 +24,27 @@ What it computes, in the paper's order (Algorithm 1):
     Eq. (global-system) with the constraint imposed exactly; the new global
     iterate averages every owned copy with weight 1/n_s.
   * Algorithm 1, "update local error": decode R P and the residual Q - R P.
+  * Algorithm 1, "check convergence metrics" and Sec. 2.2 (C^0 .. C^{p-1}):
+    one-sided derivative jumps between neighbouring local splines at every
+    subdomain interface.
+  * Sec. 2.2 and Sec. 3.1.1 (clamped versus floating interface knots): the
+    clamped-interface variant repeats every interface breakpoint p times, so
+    neighbours share exactly one control point there (C^0 only).
+  * Sec. 2.1, Eq. (nurbs-basis) with W != 1 and Sec. 4: rational basis with
+    per-axis control-point weights.
 
 Readings where the paper is silent:
   * data parameters u_k = k / (M - 1) on every axis; M = 1 gives u = 0;
   * global knots clamped and uniform: nspans spans, n = nspans + p control
     points; subdomain interfaces sit on breakpoints, so interior knots float;
+  * clamped-interface variant: the same breakpoints, each interface breakpoint
+    repeated p times (n = nspans + p + (p - 1)(N_a - 1) per axis); inside a
+    core this is the core's own clamped uniform knot vector, and the single
+    control point at the interface is shared by both neighbours;
+  * NURBS weights are separable, W_g = W_0[g_0] W_1[g_1] W_2[g_2], so the
+    rational basis is the tensor product of per-axis rational bases and the
+    fit stays separable; the weights are fixed inputs, so averaging the
+    weighted control points P W equals averaging P;
   * subdomain cores are contiguous span ranges [a, b); a core owns the control
     points whose support meets it, U = [a, b + p);
   * the overlap delta extends the core by delta spans per interior side: the
@@ -63,6 +79,24 @@ def clamped_uniform_knots(nspans: int, p: int) -> np.ndarray:
     Sec. 2.2; interior knots single, i.e. floating at interfaces)."""
     interior = [i / nspans for i in range(1, nspans)]
     return np.array([0.0] * (p + 1) + interior + [1.0] * (p + 1), dtype=np.float64)
+
+
+def knot_ints(nspans: int, p: int, cores: Optional[Sequence[int]] = None) -> List[int]:
+    """Knot positions in units of one span (t_i = k_i / nspans).  Without
+    ``cores`` the clamped uniform vector; with ``cores`` the clamped-interface
+    variant (Sec. 2.2): every interface breakpoint between two cores is
+    repeated p times (at least once), which makes the spline C^0 there and
+    makes its one straddling control point interpolate the interface value."""
+    bounds = set()
+    if cores is not None:
+        acc = 0
+        for c in list(cores)[:-1]:
+            acc += c
+            bounds.add(acc)
+    k = [0] * (p + 1)
+    for i in range(1, nspans):
+        k += [i] * (max(p, 1) if i in bounds else 1)
+    return k + [nspans] * (p + 1)
 
 
 def grid_params(M: int) -> np.ndarray:
@@ -138,6 +172,23 @@ def basis_matrix(t: np.ndarray, p: int, u, deriv: int = 0, side: str = "right") 
     return D
 
 
+def rational_basis(t: np.ndarray, p: int, W: np.ndarray, u, deriv: int = 0, side: str = "right") -> np.ndarray:
+    """Rational basis R_i = N_i W_i / sum_j N_j W_j (Sec. 2.1, Eq. nurbs-basis)
+    and its derivatives.  With A = sum_i N_i W_i P_i and w = sum_j N_j W_j the
+    curve is A / w; differentiating w R = N W r times (Leibniz) gives
+        R^(r) = (N^(r) W - sum_{j=1..r} binom(r, j) w^(j) R^(r-j)) / w."""
+    W = np.asarray(W, np.float64)
+    Nd = [basis_matrix(t, p, u, r, side) for r in range(deriv + 1)]
+    w = [N @ W for N in Nd]
+    R = []
+    for r in range(deriv + 1):
+        v = Nd[r] * W[None, :]
+        for j in range(1, r + 1):
+            v = v - math.comb(r, j) * w[j][:, None] * R[r - j]
+        R.append(v / w[0][:, None])
+    return R[deriv]
+
+
 # ---------------------------------------------------------------------------
 # Sec. 2.2: subdomain layout along one axis
 # ---------------------------------------------------------------------------
@@ -152,6 +203,9 @@ class AxisPiece:
     pts   [k0, k1]        : data points in the closed window interval
     U     [a, b + p)      : owned control points, P(Omega) and P(Delta)
     L     [w0, w1 + p)    : every control point touching the window
+    The control-point ranges are shifted by ``cshift`` (the first control
+    point of span j is j + cshift(j)) in the clamped-interface variant, where
+    each interface before span j adds p - 1 control points.
     """
 
     a: int
@@ -161,14 +215,27 @@ class AxisPiece:
     k0: int
     k1: int
     p: int
+    u0: int = -1  # first owned control point (-1: floating knots, a)
+    u1: int = -1  # one past the last owned control point
+    l0: int = -1
+    l1: int = -1
 
     @property
     def U(self) -> range:
-        return range(self.a, self.b + self.p)
+        if self.u0 < 0:
+            return range(self.a, self.b + self.p)
+        return range(self.u0, self.u1)
 
     @property
     def L(self) -> range:
-        return range(self.w0, self.w1 + self.p)
+        if self.l0 < 0:
+            return range(self.w0, self.w1 + self.p)
+        return range(self.l0, self.l1)
+
+    @property
+    def oU(self) -> int:
+        """Offset of U inside L."""
+        return self.U.start - self.L.start
 
     @property
     def pts(self) -> range:
@@ -182,14 +249,23 @@ def even_cores(nspans: int, nsub: int) -> List[int]:
     return [base + (1 if s < extra else 0) for s in range(nsub)]
 
 
-def axis_pieces(M: int, nspans: int, p: int, core_spans: Sequence[int], delta: int) -> List[AxisPiece]:
+def axis_pieces(M: int, nspans: int, p: int, core_spans: Sequence[int], delta: int,
+                clamped: bool = False) -> List[AxisPiece]:
     """Index sets of every subdomain along one axis.
 
     Window membership of data point k (parameter k/(M-1)) in the closed
     interval [w0/nspans, w1/nspans] is decided exactly:
         w0 * (M-1) <= k * nspans <= w1 * (M-1).
+    With ``clamped`` (interface knots repeated p times) the first control
+    point of span j is j + (p - 1) * (number of interfaces at or before j).
     """
     assert sum(core_spans) == nspans
+    starts = list(np.cumsum([0] + list(core_spans)))
+    ifaces = starts[1:-1]
+
+    def first_cp(j):
+        return j + (max(p, 1) - 1) * sum(1 for b in ifaces if b <= j) if clamped else j
+
     pieces = []
     a = 0
     for c in core_spans:
@@ -201,7 +277,11 @@ def axis_pieces(M: int, nspans: int, p: int, core_spans: Sequence[int], delta: i
         else:
             ks = [k for k in range(M) if w0 * (M - 1) <= k * nspans <= w1 * (M - 1)]
             k0, k1 = ks[0], ks[-1]
-        pieces.append(AxisPiece(a, b, w0, w1, k0, k1, p))
+        if clamped:
+            pieces.append(AxisPiece(a, b, w0, w1, k0, k1, p, first_cp(a), first_cp(b - 1) + p + 1,
+                                    first_cp(w0), first_cp(w1 - 1) + p + 1))
+        else:
+            pieces.append(AxisPiece(a, b, w0, w1, k0, k1, p))
         a = b
     return pieces
 
@@ -292,7 +372,10 @@ class Problem:
     """A gridded MFA problem in the adopted reading.
 
     npts[a], nspans[a], cores[a] (list of core span counts), delta[a] per grid
-    axis a = 0..d-1, one degree p for all axes.
+    axis a = 0..d-1, one degree p for all axes.  ``clamped``: interface knots
+    repeated p times (Sec. 2.2 / 3.1.1 clamped variant) instead of floating.
+    ``weights``: None (B-splines, W = 1) or one array of control-point weights
+    per axis (separable NURBS weights, Eq. nurbs-basis).
     """
 
     p: int
@@ -300,25 +383,36 @@ class Problem:
     nspans: List[int]
     cores: List[List[int]]
     delta: List[int]
+    clamped: bool = False
+    weights: Optional[List[np.ndarray]] = None
 
     @property
     def d(self) -> int:
         return len(self.npts)
 
+    def knot_ints(self, a: int) -> List[int]:
+        return knot_ints(self.nspans[a], self.p, self.cores[a] if self.clamped else None)
+
     def ncp(self) -> List[int]:
-        return [s + self.p for s in self.nspans]
+        return [len(self.knot_ints(a)) - self.p - 1 for a in range(self.d)]
 
     def knots(self, a: int) -> np.ndarray:
-        return clamped_uniform_knots(self.nspans[a], self.p)
+        return np.array(self.knot_ints(a), dtype=np.float64) / self.nspans[a]
 
     def params(self, a: int) -> np.ndarray:
         return grid_params(self.npts[a])
 
+    def basis_at(self, a: int, u, deriv: int = 0, side: str = "right") -> np.ndarray:
+        """Basis rows of axis a (rational when weights are given) at parameters u."""
+        if self.weights is None:
+            return basis_matrix(self.knots(a), self.p, u, deriv, side)
+        return rational_basis(self.knots(a), self.p, self.weights[a], u, deriv, side)
+
     def basis(self, a: int) -> np.ndarray:
-        return basis_matrix(self.knots(a), self.p, self.params(a))
+        return self.basis_at(a, self.params(a))
 
     def pieces(self, a: int) -> List[AxisPiece]:
-        return axis_pieces(self.npts[a], self.nspans[a], self.p, self.cores[a], self.delta[a])
+        return axis_pieces(self.npts[a], self.nspans[a], self.p, self.cores[a], self.delta[a], self.clamped)
 
     def subdomains(self):
         """All subdomains as tuples of AxisPiece, axis 0 varying fastest."""
@@ -330,16 +424,22 @@ class Problem:
         return out
 
 
-def make_problem(p, npts, nspans, nsub, delta, cores=None) -> Problem:
+def make_problem(p, npts, nspans, nsub, delta, cores=None, clamped=False, weights=None) -> Problem:
     """A decomposed fit (Sec. 2.2): degree p, grid points and global knot spans
     per axis, subdomains per axis (cores split evenly unless given), and the
-    overlap delta in knot spans (one value or one per axis)."""
+    overlap delta in knot spans (one value or one per axis).  ``clamped``
+    selects clamped interface knots; ``weights`` per-axis NURBS weights."""
     d = len(npts)
     if cores is None:
         cores = [even_cores(nspans[a], nsub[a]) for a in range(d)]
     if isinstance(delta, int):
         delta = [delta] * d
-    return Problem(p, list(npts), list(nspans), [list(c) for c in cores], list(delta))
+    prob = Problem(p, list(npts), list(nspans), [list(c) for c in cores], list(delta), bool(clamped))
+    if weights is not None:
+        prob.weights = [np.asarray(w, np.float64) for w in weights]
+        for a in range(d):
+            assert prob.weights[a].shape == (prob.ncp()[a],) and (prob.weights[a] > 0).all()
+    return prob
 
 
 # ---------------------------------------------------------------------------
@@ -389,9 +489,9 @@ def greville_owner(prob: Problem, a: int) -> np.ndarray:
     Greville abscissa xi_g = (t_{g+1} + ... + t_{g+p}) / p of control point g
     (the last core also holds xi = 1).  Decided exactly: with knots
     t_i = k_i / nspans, xi_g * nspans * p is the integer sum of the k_i."""
-    p, ns = prob.p, prob.nspans[a]
-    n = ns + p
-    k = [min(max(i - p, 0), ns) for i in range(n + p + 1)]  # t_i = k[i] / ns
+    p = prob.p
+    k = prob.knot_ints(a)  # t_i = k[i] / nspans
+    n = len(k) - p - 1
     pcs = prob.pieces(a)
     own = np.empty(n, dtype=np.int64)
     for g in range(n):
@@ -452,15 +552,6 @@ def average_copies(prob: Problem, subs, copies, update: str = "average") -> tupl
     return acc / cnt, hi - lo
 
 
-def multiplicity(prob: Problem) -> np.ndarray:
-    """n_s(g): number of subdomains owning control point g."""
-    shape = tuple(reversed(prob.ncp()))
-    cnt = np.zeros(shape, dtype=np.int64)
-    for s in prob.subdomains():
-        cnt[_box_slices([pc.U for pc in s], prob.d)] += 1
-    return cnt
-
-
 def schwarz_initial(prob: Problem, Q: np.ndarray, update: str = "average") -> SchwarzState:
     """Iteration 0 of Algorithm 1: every subdomain solves the unconstrained
     local LSQ on its window data with all of L_s free (Eq. minimization-problem);
@@ -473,7 +564,7 @@ def schwarz_initial(prob: Problem, Q: np.ndarray, update: str = "average") -> Sc
         mats = _local_mats(prob, s, Nglob, "L")
         PL = separable_lsq(box(Q, [pc.pts for pc in s]), mats)
         frames.append(PL)
-        u_in_l = [range(pc.a - pc.w0, pc.a - pc.w0 + len(pc.U)) for pc in s]
+        u_in_l = [range(pc.oU, pc.oU + len(pc.U)) for pc in s]
         copies.append(box(PL, u_in_l).copy())
     P, spread = average_copies(prob, subs, copies, update)
     st = SchwarzState(P=P, copies=copies, frames=frames, k=0)
@@ -500,7 +591,7 @@ def schwarz_step(prob: Problem, Q: np.ndarray, st: SchwarzState, update: str = "
     for s in subs:
         Lr = [pc.L for pc in s]
         PF = box(st.P, Lr).copy()
-        u_in_l = [range(pc.a - pc.w0, pc.a - pc.w0 + len(pc.U)) for pc in s]
+        u_in_l = [range(pc.oU, pc.oU + len(pc.U)) for pc in s]
         PF[_box_slices(u_in_l, prob.d)] = 0.0
         matsL = _local_mats(prob, s, Nglob, "L")
         R = box(Q, [pc.pts for pc in s]) - decode_box(PF, matsL)
@@ -560,31 +651,88 @@ def schwarz_solve(prob: Problem, Q: np.ndarray, max_iters: int = 200, tol_dP: fl
 # ---------------------------------------------------------------------------
 
 
-def interface_jumps_1d(prob: Problem, st: SchwarzState, max_order: Optional[int] = None) -> np.ndarray:
-    """1-D: jumps of derivative orders 0..max_order between neighbouring local
-    splines at each interface breakpoint.  The local spline of subdomain s is
-    the one it solved last (owned copy plus the frame it held); the left one is
-    evaluated as a left limit, the right one as a right limit.
-    Returns an array [n_interfaces, max_order + 1]."""
-    assert prob.d == 1
-    p = prob.p
+def interface_jumps(prob: Problem, st: SchwarzState, max_order: Optional[int] = None) -> np.ndarray:
+    """Jumps of derivative orders 0..max_order between the local splines of
+    neighbouring subdomains at every interface (Sec. 2.2: C^0 .. C^{p-1};
+    Algorithm 1 "check convergence metrics").
+
+    The local spline of subdomain s is the one it solved last: its L box of
+    control points, the owned copy plus the frame it held (``st.frames``).  At
+    an interface between pieces i and i+1 along axis a (breakpoint
+    tau = b_i / nspans_a) the left subdomain is evaluated as a left limit and
+    the right one as a right limit, for every pair of subdomains that differ
+    only in their piece along a.  Along the other axes the samples are the
+    data points of the pair's common core (closed core interval).  Order r is
+    the r-th derivative along a with respect to the knot coordinate
+    x = u * nspans_a (span units, so every order has the scale of the data).
+
+    Returns an array [n_interface_pairs, max_order + 1] of maxima over each
+    pair's samples, pairs ordered by axis, then by subdomain index."""
+    p, d = prob.p, prob.d
     if max_order is None:
         max_order = p
-    t = prob.knots(0)
-    pieces = prob.pieces(0)
+    subs = prob.subdomains()
+    pieces = [prob.pieces(a) for a in range(d)]
+    Nfull = [prob.basis(a) for a in range(d)]
+    index = {tuple(pieces[a].index(s[a]) for a in range(d)): i for i, s in enumerate(subs)}
     out = []
-    for i in range(len(pieces) - 1):
-        left, right = pieces[i], pieces[i + 1]
-        tau = left.b / prob.nspans[0]
-        row = []
-        for r in range(max_order + 1):
-            DL = basis_matrix(t, p, [tau], r, side="left")[0]
-            DR = basis_matrix(t, p, [tau], r, side="right")[0]
-            vL = DL[left.L.start:left.L.stop] @ st.frames[i]
-            vR = DR[right.L.start:right.L.stop] @ st.frames[i + 1]
-            row.append(abs(vL - vR))
-        out.append(row)
-    return np.array(out)
+    for a in range(d):
+        ns = prob.nspans[a]
+        for key, i in sorted(index.items(), key=lambda kv: (kv[1])):
+            if key[a] + 1 >= len(pieces[a]):
+                continue
+            nkey = list(key)
+            nkey[a] += 1
+            j = index[tuple(nkey)]
+            sL, sR = subs[i], subs[j]
+            tau = sL[a].b / ns
+            row = []
+            for r in range(max_order + 1):
+                vals = []
+                for s, X, side in ((sL, st.frames[i], "left"), (sR, st.frames[j], "right")):
+                    mats = []
+                    for b in range(d):
+                        Lr = s[b].L
+                        if b == a:
+                            D = prob.basis_at(a, [tau], r, side) / ns ** r
+                            mats.append(D[:, Lr.start:Lr.stop])
+                        else:
+                            M = prob.npts[b]
+                            lo, hi = s[b].a, s[b].b
+                            ks = [k for k in range(M)
+                                  if M == 1 or lo * (M - 1) <= k * prob.nspans[b] <= hi * (M - 1)]
+                            mats.append(Nfull[b][ks][:, Lr.start:Lr.stop])
+                    vals.append(decode_box(X, mats))
+                row.append(float(np.max(np.abs(vals[0] - vals[1]))))
+            out.append(row)
+    return np.array(out).reshape(-1, max_order + 1)
+
+
+def global_jumps(prob: Problem, P: np.ndarray, max_order: Optional[int] = None) -> np.ndarray:
+    """Jumps of derivative orders 0..max_order of the global spline (control
+    points P) across every interface breakpoint, as one-sided limits (Sec. 2.2:
+    floating interface knots keep the global spline C^{p-1}, clamped interface
+    knots only C^0).  Samples along the other axes are all data points; order
+    r is in span units as in interface_jumps.  Returns [n_interfaces_total,
+    max_order + 1]."""
+    p, d = prob.p, prob.d
+    if max_order is None:
+        max_order = p
+    Nfull = [prob.basis(a) for a in range(d)]
+    out = []
+    for a in range(d):
+        ns = prob.nspans[a]
+        for pc in prob.pieces(a)[:-1]:
+            tau = pc.b / ns
+            row = []
+            for r in range(max_order + 1):
+                v = []
+                for side in ("left", "right"):
+                    mats = [Nfull[b] if b != a else prob.basis_at(a, [tau], r, side) / ns ** r for b in range(d)]
+                    v.append(decode_box(P, mats))
+                row.append(float(np.max(np.abs(v[0] - v[1]))))
+            out.append(row)
+    return np.array(out).reshape(-1, max_order + 1)
 
 
 def scattered_decode(prob: Problem, P: np.ndarray, u: np.ndarray, deriv=None) -> np.ndarray:
@@ -598,7 +746,7 @@ def scattered_decode(prob: Problem, P: np.ndarray, u: np.ndarray, deriv=None) ->
     for k in range(len(u)):
         T = P
         for a in range(d):
-            row = basis_matrix(prob.knots(a), prob.p, [u[k, a]], deriv[a])  # (1, n_a)
+            row = prob.basis_at(a, [u[k, a]], deriv[a])  # (1, n_a)
             T = apply_along_axis(T, row, a)
         out[k] = float(np.asarray(T).reshape(-1)[0])
     return out
