@@ -11,9 +11,11 @@
  * Conventions shared by every call:
  *  - Grids are stored with grid axis 0 fastest in memory: value (i0,i1,i2) of
  *    a grid with npts = (M0,M1,M2) sits at offset i0 + M0*(i1 + M1*i2).
- *    Control points use the same convention with n_a = nspans_a + degree.
- *  - Knots on axis a are clamped and uniform with nspans_a spans; the data
- *    parameters are u_k = k/(M_a - 1).  Physical coordinates map affinely from
+ *    Control points use the same convention with n_a = nspans_a + degree
+ *    (more with MFA_KNOTS_CLAMPED, see there).
+ *  - Knots on axis a are clamped at the ends and uniform with nspans_a spans
+ *    (single interior knots unless MFA_KNOTS_CLAMPED); the data parameters
+ *    are u_k = k/(M_a - 1).  Physical coordinates map affinely from
  *    [lo_a, hi_a] to [0, 1].
  *  - Ownership: the caller owns every pointer it passes (q, pts, out, host_out);
  *    the library reads or writes them only inside the call's stream work and
@@ -60,13 +62,39 @@ enum { MFA_F32 = 0, MFA_F64 = 1 };
 
 /* Arithmetic of the fit.
  * MFA_PREC_FP64 : every step in FP64 (the plain method).
- * MFA_PREC_MIXED: data passes (projection, decode, residual) and the
- *                 control-point iteration in FP32; Gram matrices and their
- *                 Cholesky factors in FP64; residual reductions in FP64. */
+ * MFA_PREC_MIXED: FP64 Gram matrices and Cholesky factors (rounded to FP32
+ *                 and float-float copies for the kernels).  Everything else
+ *                 runs on the FP32 pipes in float-float arithmetic (a value is
+ *                 an unevaluated sum hi + lo of two floats, about 48 bits):
+ *                 basis values, the projection N^T Q, the iteration-0 solves,
+ *                 the Schwarz residual B_U - A_{U,L} Z, the averaging and its
+ *                 metrics, decode and residual.  The correction solve of each
+ *                 Schwarz step is plain FP32 (iterative refinement: its
+ *                 right-hand side is the float-float residual, so it adds no
+ *                 rounding floor at the fixed point).  Residual reductions
+ *                 sum E^2 in float-float and widen only per-tile totals to
+ *                 FP64.  FP64 input data are carried exactly (as float-float)
+ *                 through the projection and the residual.
+ *                 Accuracy: decoded RMS within 1 % of the FP64 fit's and
+ *                 control points within about 1e-9 relative of it. */
 enum { MFA_PREC_FP64 = 0, MFA_PREC_MIXED = 1 };
 
 #define MFA_MAX_DIM 3
 #define MFA_MAX_DEGREE 7
+
+/* Knots at the subdomain interfaces (Sec. 2.2; Sec. 3.1.1 "Comparison of
+ * Clamped vs Floating Boundary Knots").
+ * MFA_KNOTS_FLOATING: single interior knots; neighbours share the p control
+ *                     points straddling an interface and the converged fit
+ *                     is C^{p-1} there (the paper's method).
+ * MFA_KNOTS_CLAMPED : every interface breakpoint is repeated p times, so each
+ *                     core carries its own clamped uniform knot vector and
+ *                     neighbours share exactly one control point, the value at
+ *                     the interface; the fit is C^0 there and depends on the
+ *                     subdomain count.  Axis a then has
+ *                     n_a = nspans[a] + degree + (degree - 1)(nsub[a] - 1)
+ *                     control points. */
+enum { MFA_KNOTS_FLOATING = 0, MFA_KNOTS_CLAMPED = 1 };
 
 /* Problem layout (Sec. 2.2, Eq. vecp-layout; Algorithm 1 parameters N, p).
  *   dim          1..3
@@ -80,7 +108,15 @@ enum { MFA_PREC_FP64 = 0, MFA_PREC_MIXED = 1 };
  *   overlap[a]   delta, extra knot spans shared per interior side (Sec. 2.2,
  *                "Augmenting Knot Spans with Overlap"), >= 0
  *   precision    MFA_PREC_FP64 or MFA_PREC_MIXED
- *   lo[a], hi[a] physical extent of axis a (used by scattered decode)     */
+ *   lo[a], hi[a] physical extent of axis a (used by scattered decode)
+ *   knots        MFA_KNOTS_FLOATING (the default, 0) or MFA_KNOTS_CLAMPED
+ *   weights[a]   NULL (B-splines, W = 1) or n_a positive control-point
+ *                weights of axis a (host memory, read during mfa_encode): the
+ *                NURBS basis of Sec. 2.1, Eq. nurbs-basis, with the separable
+ *                weights W_g = W_0[g_0] W_1[g_1] W_2[g_2], so the rational
+ *                basis is a tensor product and the fit stays separable.  The
+ *                weights are fixed, so the Schwarz update of the weighted
+ *                control points P W (Sec. 4) equals the update of P. */
 typedef struct {
   int32_t dim;
   int32_t degree;
@@ -92,6 +128,8 @@ typedef struct {
   int32_t precision;
   double lo[3];
   double hi[3];
+  int32_t knots;
+  const double* weights[3];
 } mfa_layout;
 
 /* Convergence and error metrics (Algorithm 1: "update local error",
@@ -102,7 +140,12 @@ typedef struct {
  *                shared control point: the jump residual F_ij of
  *                Eq. (nonlinear-residuals) measured in control-point space
  *   rms_decoded, maxabs_decoded   RMS and max |Q - R P| over all data
- *   data_range   max(Q) - min(Q)                                           */
+ *   data_range   max(Q) - min(Q)
+ *   jump_orders  number of entries of jump_deriv filled by
+ *                mfa_interface_jumps (0 otherwise)
+ *   jump_deriv[r] largest jump of the r-th derivative across any subdomain
+ *                interface between the local splines of the two neighbours
+ *                (Sec. 2.2: C^0 .. C^{p-1}; see mfa_interface_jumps)       */
 typedef struct {
   int32_t iters;
   int32_t status;
@@ -111,6 +154,9 @@ typedef struct {
   double rms_decoded;
   double maxabs_decoded;
   double data_range;
+  int32_t jump_orders;
+  int32_t pad_;
+  double jump_deriv[MFA_MAX_DEGREE + 1];
 } mfa_report;
 
 /* Create a handle bound to CUDA device `device` and stream `cuda_stream`
@@ -139,13 +185,38 @@ int mfa_encode(mfa_handle* h, const mfa_layout* layout, const void* q, int q_dty
  * control points of every subdomain from the lagged global iterate (a device
  * gather), re-solve every subdomain with its frame held fixed (the Schur
  * decoupling of Eq. global-system, done in control-point space without
- * re-reading the data), and average the owned copies into P^k.  Stops after
- * an iteration with dP_rel <= tol_dP or after max_iters iterations.
- * Returns MFA_OK when the tolerance was met, MFA_NOT_CONVERGED when
- * max_iters ran out (tol_dP <= 0 always runs max_iters), or an error.
- * `rep` (may be NULL) receives iters, dP_rel, jump_max. */
+ * re-reading the data), and average the owned copies into P^k.
+ * Stops ("check convergence metrics") after the first iteration k with
+ *   dP_rel <= tol_dP                                (tol_dP > 0), or
+ *   |RMS_k - RMS_{k-1}| <= tol_rms_stall * RMS_k     (tol_rms_stall > 0),
+ * where RMS_k is the decoded RMS error of P^k over all data (RMS_0 that of
+ * the encode's P^0), or after max_iters iterations.  The stall test decodes
+ * the full grid once per iteration against the data given to mfa_encode:
+ * host data were staged there; device data must still be valid and
+ * unchanged.  Returns MFA_OK when a tolerance was met, MFA_NOT_CONVERGED
+ * when max_iters ran out (both tolerances <= 0 always run max_iters), or an
+ * error.  `rep` (may be NULL) receives iters, dP_rel, jump_max and, with the
+ * stall test, rms_decoded, maxabs_decoded and data_range of the last
+ * iterate. */
 int mfa_schwarz_iterate(mfa_handle* h, mfa_model* m, int32_t max_iters, double tol_dP,
-                        mfa_report* rep);
+                        double tol_rms_stall, mfa_report* rep);
+
+/* Continuity across subdomain interfaces (Sec. 2.2: C^0 .. C^{p-1};
+ * Algorithm 1 "check convergence metrics").  For every pair of subdomains
+ * that are neighbours along an axis a, their local splines -- the control
+ * points each used in its last solve: its owned copy plus the frame values
+ * it held (after mfa_encode: its whole unconstrained local solution) -- are
+ * evaluated at the interface breakpoint, the left one as a left limit and the
+ * right one as a right limit, at every data point of the pair's common core
+ * along the other axes.  jump r is the largest |difference| of the r-th
+ * derivative along a, taken with respect to the knot coordinate
+ * x = u * nspans[a] (so every order has the scale of the data), over all
+ * pairs and samples.  Fills rep->jump_deriv[0..max_order] and
+ * rep->jump_orders = max_order + 1 (0 <= max_order <= degree); with overlap
+ * >= degree a converged floating-knot fit has jumps at rounding level for
+ * r < p.  A model with one subdomain has no interfaces and reports zeros.
+ * Synchronous; computed in FP64 from the model's values. */
+int mfa_interface_jumps(mfa_handle* h, const mfa_model* m, int32_t max_order, mfa_report* rep);
 
 /* Decode the global MFA (Algorithm 1 error step, R P; Sec. 2.1 derivatives).
  *   pts == NULL  full data grid: writes prod(npts) values in grid layout
@@ -242,13 +313,16 @@ const char* mfa_status_string(int status);
  *   nsub, core_spans       subdomains and their core spans (NULL: even
  *                          split, the extra spans to the first subdomains)
  *   overlap                delta, in knot spans
- *   out                    caller-owned, cap >= nsub rows of 8 int32 values,
- *                          row s = { a, b, w0, w1, k0, k1, l0, nL }:
+ *   knots                  MFA_KNOTS_FLOATING or MFA_KNOTS_CLAMPED
+ *   out                    caller-owned, cap >= nsub rows of 10 int32 values,
+ *                          row s = { a, b, w0, w1, k0, k1, l0, nL, oU, nU }:
  *                          core spans [a, b); window spans [w0, w1) (the core
  *                          widened by delta, clipped); data points k0..k1
  *                          (parameters k/(npts-1) in the closed window
- *                          interval); local control points l0 .. l0+nL-1
- *   owner                  caller-owned, nspans + degree int32 values or
+ *                          interval); local control points l0 .. l0+nL-1, of
+ *                          which l0+oU .. l0+oU+nU-1 are owned
+ *   owner                  caller-owned, n int32 values (n = nspans + degree,
+ *                          plus (degree - 1)(nsub - 1) for clamped knots) or
  *                          NULL: the subdomain whose core holds control point
  *                          g's Greville abscissa
  * Returns MFA_OK; MFA_ERR_ARG for sizes out of range or cap < nsub;
@@ -256,7 +330,7 @@ const char* mfa_status_string(int status);
  * than degree spans between interfaces, or a window whose collocation matrix
  * fails the Schoenberg-Whitney condition).  Nothing is written on an error. */
 int mfa_axis_layout(int64_t npts, int32_t nspans, int32_t degree, int32_t nsub, const int32_t* core_spans,
-                    int32_t overlap, int32_t* out, int32_t cap, int32_t* owner);
+                    int32_t overlap, int32_t knots, int32_t* out, int32_t cap, int32_t* owner);
 
 /* Grid decode that allocates nothing.
  *
@@ -288,14 +362,19 @@ int mfa_axis_layout(int64_t npts, int32_t nspans, int32_t degree, int32_t nsub, 
  * returns MFA_ERR_UNSUPPORTED before any work is queued (roughly: 2-D grids
  * up to npts[0] * (nspans[1] + degree) of 4M values, 3-D grids whose
  * npts[0]*npts[1]*(nspans[2]+degree) stays near 3M values).
- * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls on a device share the array and it
- * keeps the last call's contents (every element a call reads was written by
- * that call first, so nothing needs clearing); calls whose GPU work overlaps
- * in time, on different streams or from different host threads, race on the
- * array and must be serialised by the caller.
- * Returns MFA_OK, MFA_ERR_ARG, MFA_ERR_UNSUPPORTED or MFA_ERR_CUDA. */
+ * Every call looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, which queues no stream work), so the address stays
+ * right after the context is torn down and created again.  The first call
+ * on a device also loads the library's device code there: make that first
+ * call before any stream capture.  All calls on a device share the array and
+ * it keeps the last call's contents (every element a call reads was written
+ * by that call first, so nothing needs clearing); calls whose GPU work
+ * overlaps in time, on different streams or from different host threads,
+ * race on the array and must be serialised by the caller.
+ * Returns MFA_OK, MFA_ERR_ARG, MFA_ERR_UNSUPPORTED or MFA_ERR_CUDA.
+ * MFA_ERR_CUDA is returned without queueing anything when a launch error
+ * from earlier work is still pending on the calling thread (that error is
+ * left in place for its owner), and after a launch of this call fails. */
 #define MFA_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int mfa_decode_grid_noalloc(int32_t dim, int32_t degree, const int64_t* npts, const int32_t* nspans,
                             const double* ctrl, double* out, void* cuda_stream);

@@ -4,8 +4,6 @@
 // address obtained with cudaGetSymbolAddress, never the symbol itself.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "mfa_internal.cuh"
 
 namespace {
@@ -14,25 +12,18 @@ namespace {
 // GPU that loads the library until the process exits.
 static __device__ __align__(256) unsigned char g_decode_scratch[MFA_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on `dev` (the current device), looked
-// up once per device.
-int scratch_address(int dev, unsigned char** out) {
-  if (dev < 0 || dev >= kMaxDevices) return MFA_ERR_ARG;
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_decode_scratch);
-    if (e != cudaSuccess || !p) {
-      cudaGetLastError();
-      return MFA_ERR_CUDA;
-    }
-    g_scratch_addr[dev] = p;
+// Device address of the scratch array in the calling thread's current
+// context.  Looked up on every call (a table lookup in the runtime that
+// queues no stream work), so a context that was torn down and created again,
+// where the module may load at another address, never sees a stale pointer.
+int scratch_address(unsigned char** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_decode_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();  // the error came from this lookup
+    return MFA_ERR_CUDA;
   }
-  *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  *out = static_cast<unsigned char*>(p);
   return MFA_OK;
 }
 
@@ -129,14 +120,13 @@ extern "C" int mfa_decode_grid_noalloc(int32_t dim, int32_t degree, const int64_
   }
   if (used > (size_t)MFA_NOALLOC_SCRATCH_BYTES) return MFA_ERR_UNSUPPORTED;
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    cudaGetLastError();
-    return MFA_ERR_CUDA;
-  }
+  // a launch error left pending by earlier, unrelated work is not this
+  // call's: refuse, and leave it for the code that caused it
+  if (cudaPeekAtLastError() != cudaSuccess) return MFA_ERR_CUDA;
   unsigned char* base = nullptr;
-  int rc = scratch_address(dev, &base);
+  int rc = scratch_address(&base);
   if (rc != MFA_OK) return rc;
+  const int grid_cap = 32 * mfa::device_sm_count();
   cudaStream_t st = (cudaStream_t)cuda_stream;
 
   // basis tables of every axis into the scratch
@@ -152,6 +142,7 @@ extern "C" int mfa_decode_grid_noalloc(int32_t dim, int32_t degree, const int64_
     double* vd = reinterpret_cast<double*>(base + off_vd[a]);
     float* vf = reinterpret_cast<float*>(base + off_vf[a]);
     mfa::launch_basis(ax, sp, vd, vf, nullptr, st);
+    if (cudaGetLastError() != cudaSuccess) return MFA_ERR_CUDA;  // this launch failed
     span[a] = sp;
     vals[a] = vd;
   }
@@ -171,10 +162,10 @@ extern "C" int mfa_decode_grid_noalloc(int32_t dim, int32_t degree, const int64_
     s.vals = vals[a];
     const long long total = cur[0] * cur[1] * cur[2];
     long long blocks = (total + 255) / 256;
-    if (blocks > 152 * 32) blocks = 152 * 32;
+    if (blocks > grid_cap) blocks = grid_cap;
     k_expand_static<<<(unsigned)blocks, 256, 0, st>>>(s);
+    if (cudaGetLastError() != cudaSuccess) return MFA_ERR_CUDA;  // this launch failed
     in = s.out;
   }
-  cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? MFA_OK : MFA_ERR_CUDA;
+  return MFA_OK;
 }

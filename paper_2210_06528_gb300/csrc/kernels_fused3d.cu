@@ -1517,7 +1517,16 @@ bool launch_schwarz3d_ff(const LayoutDev& L, const long long* offL, const int* m
 //     owner and offset tables sit in shared memory.
 // ---------------------------------------------------------------------------
 
-__constant__ float c_inv_hi[9], c_inv_lo[9];  // 1/n as float-float, n = 1..8
+// 1/n as float-float, n = 1..8 (hi = 1/n rounded to FP32, lo = the rest
+// rounded), fixed when the module loads so a reloaded module has them too
+#define MFA_INV_HI(n) ((float)(1.0 / (n)))
+#define MFA_INV_LO(n) ((float)(1.0 / (n) - (double)MFA_INV_HI(n)))
+__constant__ float c_inv_hi[9] = {0.f,           MFA_INV_HI(1), MFA_INV_HI(2), MFA_INV_HI(3), MFA_INV_HI(4),
+                                  MFA_INV_HI(5), MFA_INV_HI(6), MFA_INV_HI(7), MFA_INV_HI(8)};
+__constant__ float c_inv_lo[9] = {0.f,           MFA_INV_LO(1), MFA_INV_LO(2), MFA_INV_LO(3), MFA_INV_LO(4),
+                                  MFA_INV_LO(5), MFA_INV_LO(6), MFA_INV_LO(7), MFA_INV_LO(8)};
+#undef MFA_INV_HI
+#undef MFA_INV_LO
 constexpr int kAvgThreads = 256;
 
 // Tables of the update kept in shared memory when they fit (else read from
@@ -1767,33 +1776,16 @@ __global__ void __launch_bounds__(kAvgThreads, 3) k_average_ff(LayoutDev L, cons
   }
 }
 
-long long average_ff_blocks(const LayoutDev& L) { return L.nsub + kAvgListBlocks; }
+long long average_ff_blocks(const LayoutDev& L) {
+  const int list = 3 * device_sm_count();  // blocks on the shared control points: 3 per SM
+  return L.nsub + (list < kAvgListBlocks ? list : kAvgListBlocks);
+}
 
 // `part` holds 3 floats per block of the launch (average_ff_blocks) and, after
 // them, the row counter of the shared control points and the finished-block
 // counter.
 void launch_average_ff(const LayoutDev& L, const long long* offL, const ff* X, ff* P, const ff* Pprev, float* part,
                        unsigned long long* metrics, cudaStream_t st, int rule) {
-  // reciprocal table in constant memory, set once per device (handles on
-  // several host threads may reach this together)
-  static std::mutex init_mu;
-  static bool init[64] = {};
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 0 && dev < 64) {
-    std::lock_guard<std::mutex> lock(init_mu);
-    if (!init[dev]) {
-      float h[9] = {0}, l[9] = {0};
-      for (int n = 1; n <= 8; ++n) {
-        const ff v(1.0 / n);
-        h[n] = v.hi;
-        l[n] = v.lo;
-      }
-      cudaMemcpyToSymbol(c_inv_hi, h, sizeof(h));
-      cudaMemcpyToSymbol(c_inv_lo, l, sizeof(l));
-      init[dev] = true;
-    }
-  }
   const size_t tab = (size_t)(L.ncp[0] + L.ncp[1] + L.ncp[2]) * (sizeof(int4) + sizeof(int)) +
                      (size_t)L.nsub * sizeof(long long) + (size_t)(L.S[0] + L.S[1]) * sizeof(int);
   const int stage = tab <= 40 * 1024;
@@ -1943,18 +1935,17 @@ int launch_iter0_3d_ff(const LayoutDev& L, const long long* offL, const int* max
 namespace mfa {
 
 void ensure_smem_attr(const void* kernel, size_t bytes, bool carveout) {
-  static std::mutex mu;
-  static std::map<std::pair<const void*, int>, size_t> set;  // (kernel, device) -> largest size set
-  int dev = 0;
-  cudaGetDevice(&dev);
-  std::lock_guard<std::mutex> lock(mu);
-  size_t& cur = set[{kernel, dev}];
-  if (cur != 0 && bytes <= cur) return;
-  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess)
-    cur = bytes;
-  else
+  // the limit the kernel has in the current context right now (a context
+  // created again after a reset starts from the default), raised only when
+  // too small
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes >= bytes &&
+      (!carveout || fa.preferredShmemCarveout == 100))
+    return;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
     cudaGetLastError();  // the launch reports the problem
-  if (carveout) cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (carveout && cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+    cudaGetLastError();
 }
 
 }  // namespace mfa

@@ -147,7 +147,8 @@ void launch_average(const LayoutDev& L, const long long* offL, const T* X, T* P,
                     unsigned long long* metrics, cudaStream_t st, int rule) {
   const long long n = L.ncp[0] * L.ncp[1] * L.ncp[2];
   long long blocks = (n + 255) / 256;
-  if (blocks > 152 * 16) blocks = 152 * 16;
+  const long long cap = 16LL * device_sm_count();
+  if (blocks > cap) blocks = cap;
   k_average<T><<<(unsigned)blocks, 256, 0, st>>>(L, offL, X, P, Pprev, metrics, rule);
 }
 
@@ -199,6 +200,73 @@ __device__ void basis_derivs(int j, double u, int p, int nspans, int rder, doubl
   }
 }
 
+// Derivatives of order rder (with respect to u) of the p+1 basis functions of
+// axis `ax` nonzero at u, into N; returns the first one's control point.
+// Floating knots: the global clamped uniform knots.  Clamped interfaces: the
+// core holding u and its own clamped uniform knots of b - a spans at the local
+// parameter (x - a)/(b - a), x = u * gspans, so each derivative order takes a
+// factor gspans / (b - a).  With weights, the rational basis R = N W / w
+// (Eq. nurbs-basis) and its derivatives from differentiating w R = N W r times
+// (Leibniz): R^(r) = (N^(r) W - sum_{j=1..r} binom(r, j) w^(j) R^(r-j)) / w,
+// w^(j) = sum N^(j) W.
+__device__ int axis_basis(const AxisDev& ax, double u, int rder, double* N) {
+  const int p = ax.p;
+  int first, ns, j;
+  double ul, dscale = 1.0;
+  if (ax.kmode == KMODE_CLAMPED) {
+    const int gs = ax.gspans;
+    const double x = u * gs;
+    int jg = (int)floor(x);
+    jg = jg > gs - 1 ? gs - 1 : (jg < 0 ? 0 : jg);
+    int lo = 0, hi = ax.S - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ax.subs[mid].a <= jg) lo = mid;
+      else hi = mid - 1;
+    }
+    const AxisSub sb = ax.subs[lo];
+    ns = sb.b - sb.a;
+    j = jg - sb.a;
+    ul = (x - (double)sb.a) / (double)ns;
+    first = sb.l0 + sb.oU + j;
+    dscale = (double)gs / (double)ns;
+  } else {
+    ns = ax.nspans;
+    j = (int)floor(u * ns);
+    j = j > ns - 1 ? ns - 1 : (j < 0 ? 0 : j);
+    ul = u;
+    first = j;
+  }
+  if (!ax.wts) {
+    basis_derivs(j, ul, p, ns, rder, N);
+    double f = 1.0;
+    for (int r = 0; r < rder; ++r) f *= dscale;
+    for (int r = 0; r <= p; ++r) N[r] *= f;
+    return first;
+  }
+  double R[MFA_MAX_DEGREE + 1][MFA_MAX_DEGREE + 1], w[MFA_MAX_DEGREE + 1];
+  double f = 1.0;
+  for (int i = 0; i <= rder; ++i) {
+    basis_derivs(j, ul, p, ns, i, R[i]);
+    w[i] = 0.0;
+    for (int r = 0; r <= p; ++r) {
+      R[i][r] *= f * ax.wts[first + r];  // N^(i) W
+      w[i] += R[i][r];
+    }
+    f *= dscale;
+  }
+  for (int i = 0; i <= rder; ++i) {
+    double binom = 1.0;  // binom(i, jj)
+    for (int jj = 1; jj <= i; ++jj) {
+      binom = binom * (i - jj + 1) / jj;
+      for (int r = 0; r <= p; ++r) R[i][r] -= binom * w[jj] * R[i - jj][r];
+    }
+    for (int r = 0; r <= p; ++r) R[i][r] /= w[0];
+  }
+  for (int r = 0; r <= p; ++r) N[r] = R[rder][r];
+  return first;
+}
+
 template <typename T>
 __global__ void k_decode_points(LayoutDev L, double lo0, double lo1, double lo2, double hi0, double hi1, double hi2,
                                 const double* __restrict__ pts, long long npts, int d0, int d1, int d2,
@@ -219,11 +287,7 @@ __global__ void k_decode_points(LayoutDev L, double lo0, double lo1, double lo2,
       u = fmin(fmax(u, 0.0), 1.0);
       for (int r = 0; r < der[a]; ++r) scale /= len;
     }
-    int j = (int)floor(u * ax.nspans);
-    if (j > ax.nspans - 1) j = ax.nspans - 1;
-    if (j < 0) j = 0;
-    span[a] = j;
-    basis_derivs(j, u, ax.p, ax.nspans, a < L.dim ? der[a] : 0, N[a]);
+    span[a] = axis_basis(ax, u, a < L.dim ? der[a] : 0, N[a]);
   }
   double acc = 0.0;
   for (int r2 = 0; r2 <= L.ax[2].p; ++r2) {

@@ -188,30 +188,66 @@ __global__ void k_basis_all(SetupArgs A) {
   const AxisDev& ax = A.ax[a];
   const int p = ax.p;
   int M = ax.M, nspans = ax.nspans, kl = k, j0 = 0;
-  if (ax.pieces) {
-    // independent fits side by side: find the piece holding point k (pieces
-    // are sorted by k0), then use its own knot vector and parameters
+  int j = 0;
+  double u = 0.0;
+  if (ax.kmode == KMODE_CLAMPED) {
+    // clamped interfaces: the point's span on the grid (largest j with
+    // j/gspans <= k/(M-1), exact in integers), the core [a, b) holding it, and
+    // that core's own clamped uniform knots of b - a spans at the local
+    // parameter (x - a)/(b - a), x = u * gspans; spans numbered from the
+    // core's first owned control point
+    const int gs = ax.gspans;
+    int jg = 0;
+    double x = 0.0;
+    if (M > 1) {
+      jg = (int)(((long long)k * gs) / (M - 1));
+      if (jg > gs - 1) jg = gs - 1;
+      x = (double)k * (double)gs / (double)(M - 1);
+    }
     int lo = 0, hi = ax.S - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (ax.subs[mid].k0 <= k) lo = mid;
+      if (ax.subs[mid].a <= jg) lo = mid;
       else hi = mid - 1;
     }
     const AxisSub sb = ax.subs[lo];
-    M = sb.m;
-    nspans = sb.w1 - sb.w0;
-    kl = k - sb.k0;
-    j0 = sb.l0;
-  }
-  int j = 0;
-  double u = 0.0;
-  if (M > 1) {
-    j = (int)(((long long)kl * nspans) / (M - 1));
-    if (j > nspans - 1) j = nspans - 1;
-    u = (double)kl / (double)(M - 1);
+    nspans = sb.b - sb.a;
+    j = jg - sb.a;
+    u = (x - (double)sb.a) / (double)nspans;
+    j0 = sb.l0 + sb.oU;
+  } else {
+    if (ax.pieces) {
+      // independent fits side by side: find the piece holding point k (pieces
+      // are sorted by k0), then use its own knot vector and parameters
+      int lo = 0, hi = ax.S - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ax.subs[mid].k0 <= k) lo = mid;
+        else hi = mid - 1;
+      }
+      const AxisSub sb = ax.subs[lo];
+      M = sb.m;
+      nspans = sb.w1 - sb.w0;
+      kl = k - sb.k0;
+      j0 = sb.l0;
+    }
+    if (M > 1) {
+      j = (int)(((long long)kl * nspans) / (M - 1));
+      if (j > nspans - 1) j = nspans - 1;
+      u = (double)kl / (double)(M - 1);
+    }
   }
   double N[MFA_MAX_DEGREE + 1];
   cox_de_boor(j, u, p, nspans, N);
+  if (ax.wts) {
+    // rational basis R_g = N_g W_g / sum_h N_h W_h (Eq. nurbs-basis)
+    double wsum = 0.0;
+    for (int r = 0; r <= p; ++r) {
+      N[r] *= ax.wts[j0 + j + r];
+      wsum += N[r];
+    }
+    for (int r = 0; r <= p; ++r) N[r] /= wsum;
+  }
   A.span[a][k] = j0 + j;
   for (int r = 0; r <= p; ++r) {
     A.vd[a][(long long)k * (p + 1) + r] = N[r];

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -82,8 +83,10 @@ struct mfa_model {
   const void* q_src = nullptr;     // plain form: the device data it re-reads every iteration
   int q_src_dtype = MFA_F32;
   int prec = MFA_PREC_FP64;
+  int knots = MFA_KNOTS_FLOATING;  // knots at the interfaces, as given in the layout
   int dim = 1;
   int degree = 1;
+  double last_rms = -1.0;          // decoded RMS of the current iterate, when the stall test has computed it
   double lo[3] = {0, 0, 0}, hi[3] = {1, 1, 1};
   AxisHost axh[3];
   LayoutDev L{};
@@ -116,6 +119,22 @@ struct mfa_model {
   double last_dP = 0.0;
   double last_jump = 0.0;
 };
+
+namespace mfa {
+int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (dev >= 0 && dev < 64) {
+    const int c = cache[dev].load(std::memory_order_relaxed);
+    if (c > 0) return c;
+  }
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) return 1;
+  if (dev >= 0 && dev < 64) cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+}  // namespace mfa
 
 namespace {
 
@@ -251,16 +270,16 @@ void trace_end(mfa_handle* h, int cls, int i, int nlaunch = 1) {
 // ---------------------------------------------------------------------------
 
 // Does control point g have a nonzero basis value at data point k?  Exact in
-// integers: the open support (t_{g-p}, t_{g+1}) in parameter space, plus the
-// clamped end values N_0(0) = N_{n-1}(1) = 1.
-bool in_open_support(long long k, int g, int p, int nspans, long long M) {
-  const int n = nspans + p;
-  if (M == 1) return true;
-  if (g == 0 && k == 0) return true;
-  if (g == n - 1 && k == M - 1) return true;
-  const long long lo = std::max(g - p, 0), hi = std::min(g + 1, nspans);
-  const long long x = k * nspans;
-  return lo * (M - 1) < x && x < hi * (M - 1);
+// integers with the knot positions t_i = kn[i] / gspans: N_g is positive on
+// the open interval (t_g, t_{g+p+1}), at its left end when the knot there has
+// multiplicity p+1 (a clamped start), and the last function at u = 1.
+bool in_support(const AxisHost& ax, long long k, int g) {
+  if (ax.M == 1) return true;
+  const long long x = k * ax.gspans, M1 = ax.M - 1;
+  const long long lo = ax.knots[g], hi = ax.knots[g + ax.p + 1];
+  if (lo * M1 < x && x < hi * M1) return true;
+  if (x == lo * M1 && ax.knots[g + ax.p] == lo && lo < hi) return true;
+  return g == ax.n - 1 && k == ax.M - 1;
 }
 
 // Schoenberg-Whitney condition for the window's collocation matrix: a
@@ -272,7 +291,7 @@ bool schoenberg_whitney(const AxisHost& ax, const AxisSub& sb) {
     const int g = sb.l0 + l;
     bool found = false;
     for (long long k = next; k < sb.k0 + sb.m; ++k) {
-      if (in_open_support(k, g, ax.p, ax.nspans, ax.M)) {
+      if (in_support(ax, k, g)) {
         next = k + 1;
         found = true;
         break;
@@ -283,14 +302,26 @@ bool schoenberg_whitney(const AxisHost& ax, const AxisSub& sb) {
   return true;
 }
 
-int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int32_t* core, int delta) {
+// Layout of one axis (Sec. 2.2).  Floating knots: single interior knots,
+// span j carries control points j .. j+p.  Clamped interfaces (Sec. 2.2 /
+// Sec. 3.1.1 variant): every interface breakpoint is repeated p times, so the
+// first control point of span j is j + (p-1) * (number of interfaces at or
+// before j), each core carries its own clamped uniform knot vector, and
+// neighbours share the single control point at their interface.  Spans are
+// numbered by their first control point throughout (`nspans` then counts the
+// span numbers, `gspans` the grid's knot spans).
+int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int32_t* core, int delta,
+               int knots = MFA_KNOTS_FLOATING) {
   if (M < 1 || M > (1LL << 30)) return MFA_ERR_ARG;
+  if (knots != MFA_KNOTS_FLOATING && knots != MFA_KNOTS_CLAMPED) return MFA_ERR_ARG;
   if (nspans < 1 || nsub < 1 || nsub > nspans || delta < 0) return MFA_ERR_LAYOUT;
+  // clamping changes nothing for p <= 1 or a single core
+  const bool clamped = knots == MFA_KNOTS_CLAMPED && p > 1 && nsub > 1;
   ax.M = (int)M;
-  ax.nspans = nspans;
+  ax.gspans = nspans;
   ax.p = p;
-  ax.n = nspans + p;
   ax.S = nsub;
+  ax.kmode = clamped ? KMODE_CLAMPED : KMODE_FLOATING;
   std::vector<int> cs(nsub);
   if (core) {
     long long tot = 0;
@@ -302,14 +333,30 @@ int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int
   } else {
     for (int s = 0; s < nsub; ++s) cs[s] = nspans / nsub + (s < nspans % nsub ? 1 : 0);
   }
-  ax.subs.clear();
-  int a = 0, bandL = 0, bandU = 0;
+  // cores between interfaces need >= p spans; a single subdomain has none
+  std::vector<int> piece_of_span(nspans, 0), core_start(nsub + 1, 0);
   for (int s = 0; s < nsub; ++s) {
-    // cores between interfaces need >= p spans; a single subdomain has none
     if (nsub > 1 && cs[s] < std::max(p, 1)) return MFA_ERR_LAYOUT;
+    core_start[s + 1] = core_start[s] + cs[s];
+    for (int j = core_start[s]; j < core_start[s + 1]; ++j) piece_of_span[j] = s;
+  }
+  // first control point of span j; knot positions (multiplicity p at clamped interfaces)
+  auto first_cp = [&](int j) { return clamped ? j + (p - 1) * piece_of_span[j] : j; };
+  ax.nspans = first_cp(nspans - 1) + 1;
+  ax.n = ax.nspans + p;
+  ax.knots.assign(p + 1, 0);
+  for (int i = 1; i < nspans; ++i) {
+    const bool iface = clamped && piece_of_span[i] != piece_of_span[i - 1];
+    for (int r = 0; r < (iface ? p : 1); ++r) ax.knots.push_back(i);
+  }
+  for (int r = 0; r <= p; ++r) ax.knots.push_back(nspans);
+  if ((int)ax.knots.size() != ax.n + p + 1) return MFA_ERR_LAYOUT;
+  ax.subs.clear();
+  int bandL = 0, bandU = 0;
+  for (int s = 0; s < nsub; ++s) {
     AxisSub sb{};
-    sb.a = a;
-    sb.b = a + cs[s];
+    sb.a = core_start[s];
+    sb.b = core_start[s + 1];
     sb.w0 = std::max(sb.a - delta, 0);
     sb.w1 = std::min(sb.b + delta, nspans);
     // closed window [w0/nspans, w1/nspans]: w0 (M-1) <= k nspans <= w1 (M-1)
@@ -323,17 +370,16 @@ int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int
       sb.k0 = (int)k0;
       sb.m = (int)(k1 - k0 + 1);
     }
-    sb.l0 = sb.w0;
-    sb.nL = sb.w1 + p - sb.w0;
-    sb.oU = sb.a - sb.w0;
-    sb.nU = sb.b + p - sb.a;
+    sb.l0 = first_cp(sb.w0);
+    sb.nL = first_cp(sb.w1 - 1) + p + 1 - sb.l0;
+    sb.oU = first_cp(sb.a) - sb.l0;
+    sb.nU = first_cp(sb.b - 1) + p + 1 - first_cp(sb.a);
     sb.bandL = bandL;
     sb.bandU = bandU;
     bandL += sb.nL;
     bandU += sb.nU;
     if (!schoenberg_whitney(ax, sb)) return MFA_ERR_LAYOUT;
     ax.subs.push_back(sb);
-    a = sb.b;
   }
   ax.bandL_rows = bandL;
   ax.bandU_rows = bandU;
@@ -342,7 +388,7 @@ int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int
   ax.own_count.assign(ax.n, 0);
   for (int s = 0; s < nsub; ++s) {
     const AxisSub& sb = ax.subs[s];
-    for (int g = sb.a; g < sb.b + p; ++g) {
+    for (int g = sb.l0 + sb.oU; g < sb.l0 + sb.oU + sb.nU; ++g) {
       if (ax.own_first[g] < 0) ax.own_first[g] = s;
       ax.own_count[g]++;
     }
@@ -366,7 +412,8 @@ int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int
   ax.one_rng.assign(nsub, int2{0, 0});
   for (int s = 0; s < nsub; ++s) {
     int lo = -1, hi = -1;
-    for (int g = ax.subs[s].a; g < ax.subs[s].b + p; ++g)
+    const AxisSub& sb = ax.subs[s];
+    for (int g = sb.l0 + sb.oU; g < sb.l0 + sb.oU + sb.nU; ++g)
       if (ax.own_count[g] == 1) {
         if (lo < 0) lo = g;
         hi = g + 1;
@@ -378,15 +425,14 @@ int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int
   }
   // owner-takes update: the owner of control point g is the subdomain whose
   // core holds its Greville abscissa xi_g = (t_{g+1} + ... + t_{g+p}) / p;
-  // with t_i = c_i / nspans, xi_g * nspans * p = sum of the c_i, exact
+  // with t_i = kn_i / nspans, xi_g * nspans * p = sum of the kn_i, exact
   ax.own_pick.assign(ax.n, 0);
   for (int g = 0; g < ax.n; ++g) {
-    auto c = [&](int i) { return std::min(std::max(i - p, 0), nspans); };
     long long S = 0, den = p;
     if (p > 0) {
-      for (int i = g + 1; i <= g + p; ++i) S += c(i);
+      for (int i = g + 1; i <= g + p; ++i) S += ax.knots[i];
     } else {
-      S = c(g) + c(g + 1);
+      S = ax.knots[g] + ax.knots[g + 1];
       den = 2;
     }
     int owner = -1;
@@ -401,13 +447,15 @@ int build_axis(AxisHost& ax, long long M, int nspans, int p, int nsub, const int
     else
       return MFA_ERR_LAYOUT;  // the Greville owner always owns the point; guard against a broken layout
   }
-  // first data point of every span (span of point k = floor(k nspans / (M-1)), capped)
-  ax.span_start.assign(nspans + 1, (int)M);
+  // first data point of every span number (span of point k = floor(k nspans / (M-1)), capped, then numbered
+  // by its first control point; unused numbers start where the next span does)
+  ax.span_start.assign(ax.nspans + 1, (int)M);
   int j = 0;
   for (long long k = 0; k < M; ++k) {
     long long sk = (M == 1) ? 0 : (k * nspans) / (M - 1);
     if (sk > nspans - 1) sk = nspans - 1;
-    while (j <= sk) ax.span_start[j++] = (int)k;
+    const int v = first_cp((int)sk);
+    while (j <= v) ax.span_start[j++] = (int)k;
   }
   return MFA_OK;
 }
@@ -626,7 +674,10 @@ void run_encode(mfa_model* md, const TQ* q, const StagedCopy* sc = nullptr) {
   // launch per axis where stage a reads the previous stage (the data for a = 0)
   bool fused = false;
   int slabs_done = 0;  // host data: slabs already copied (all of them once the projection has its data)
-  if constexpr (std::is_same<T, ff>::value) {
+  // the fused projection stages FP32 data; FP64 data take the per-axis
+  // kernels, which carry them exactly as float-float
+  constexpr bool kFusedData = std::is_same<T, ff>::value && std::is_same<TQ, float>::value;
+  if constexpr (kFusedData) {
     if (md->dim == 3 && md->use_fused && sc && md->units) {
       // the units of slab t wait for slabs 0..t only, so the projection runs
       // under the rest of the copy
@@ -649,7 +700,7 @@ void run_encode(mfa_model* md, const TQ* q, const StagedCopy* sc = nullptr) {
     copy_slabs(md, *sc, slabs_done, kSlabs);
     cudaStreamWaitEvent(h->stream, h->slab_ev[kSlabs - 1], 0);
   }
-  if constexpr (std::is_same<T, ff>::value) {
+  if constexpr (kFusedData) {
     if (md->dim == 3 && md->use_fused && !fused) {
       TRACED(h, TR_PROJECT_DATA,
              fused = launch_project3d_ff<TQ>(L, md->offL, md->maxm[0], md->maxm[1], md->maxm[2], md->maxnL[0], md->maxnL[1],
@@ -778,21 +829,24 @@ int run_decode_grid(mfa_model* md, TOut* out, const TQ* q) {
   const LayoutDev& L = md->L;
   const int ns = md->nsub;
   const int d = md->dim;
-  // fused 3-D tiles: one kernel, residual partials per tile
+  // fused 3-D tiles: one kernel, residual partials per tile (FP32 data; FP64
+  // data take the per-axis residual, which keeps them exact)
   if constexpr (std::is_same<T, ff>::value) {
     if (d == 3 && md->use_fused) {
       bool fused = false;
       if (q) {
-        const long long tiles = decode3d_tiles(L);
-        int rc = ensure_ws(h, (size_t)tiles * 4 * sizeof(double));
-        if (rc != MFA_OK) return rc;
-        double* part = (double*)h->ws;
-        TRACED(h, TR_RESIDUAL,
-               fused = (launch_decode3d<ff, TQ, float, true>(L, (const ff*)md->P, q, nullptr, part, h->stream)));
-        if (fused) {
-          TRACED_N(h, TR_REDUCE, 2,
-                   launch_reduce_partials(part, (int)tiles, h->d_result, h->stream, h->d_partials, kResidualBlocks));
-          return MFA_OK;
+        if constexpr (std::is_same<TQ, float>::value) {
+          const long long tiles = decode3d_tiles(L);
+          int rc = ensure_ws(h, (size_t)tiles * 4 * sizeof(double));
+          if (rc != MFA_OK) return rc;
+          double* part = (double*)h->ws;
+          TRACED(h, TR_RESIDUAL,
+                 fused = (launch_decode3d<ff, TQ, float, true>(L, (const ff*)md->P, q, nullptr, part, h->stream)));
+          if (fused) {
+            TRACED_N(h, TR_REDUCE, 2,
+                     launch_reduce_partials(part, (int)tiles, h->d_result, h->stream, h->d_partials, kResidualBlocks));
+            return MFA_OK;
+          }
         }
       } else if constexpr (!std::is_same<TOut, ff>::value) {
         TRACED(h, TR_DECODE_OUT,
@@ -839,6 +893,94 @@ int run_decode_grid(mfa_model* md, TOut* out, const TQ* q) {
   return MFA_OK;
 }
 
+// One-sided derivatives of orders 0..R, with respect to the knot coordinate
+// x = u * gspans, of the p+1 basis functions of axis `ax` nonzero next to the
+// breakpoint xb (an integer knot position): on the span ending at xb (side 0,
+// the left limit) or starting there (side 1, the right limit).  The degree is
+// raised by the Cox-de Boor recurrence on the axis's own knot vector and the
+// derivative orders come from
+//   d/dx N_{m,q} = q/(t_{m+q}-t_m) N_{m,q-1} - q/(t_{m+q+1}-t_{m+1}) N_{m+1,q-1}
+// (terms with a zero denominator dropped); with weights, the rational basis
+// and its derivatives by the Leibniz rule.  out[r*(p+1) + c] is order r of
+// control point first + c; returns first, or -1 if xb is not inside the axis.
+int host_onesided_basis(const AxisHost& ax, int xb, int side, int R, double* out) {
+  const int p = ax.p;
+  const std::vector<int>& t = ax.knots;
+  int i = -1;  // knot interval [t_i, t_{i+1}) with t_i < t_{i+1}
+  for (int k = p; k + 1 < (int)t.size() - p; ++k) {
+    if (t[k] >= t[k + 1]) continue;
+    if ((side == 1 && t[k] == xb) || (side == 0 && t[k + 1] == xb)) {
+      i = k;
+      break;
+    }
+  }
+  if (i < 0) return -1;
+  const double x = xb;
+  std::vector<double> D((size_t)(R + 1) * (p + 1), 0.0);
+  for (int r = 0; r <= R; ++r) {
+    double N[MFA_MAX_DEGREE + 1] = {0};
+    if (r > p) continue;
+    N[0] = 1.0;
+    const int q0 = p - r;
+    for (int q = 1; q <= p; ++q) {
+      double nw[MFA_MAX_DEGREE + 1] = {0};
+      for (int c = 0; c <= q; ++c) {
+        const int m = i - q + c;  // function N_{m,q}; N_{m,q-1} = N[c-1], N_{m+1,q-1} = N[c]
+        const double dl = t[m + q] - t[m], dr = t[m + q + 1] - t[m + 1];
+        double v = 0.0;
+        if (q <= q0) {
+          if (c >= 1 && dl > 0) v += (x - t[m]) / dl * N[c - 1];
+          if (c < q && dr > 0) v += (t[m + q + 1] - x) / dr * N[c];
+        } else {
+          if (c >= 1 && dl > 0) v += q / dl * N[c - 1];
+          if (c < q && dr > 0) v -= q / dr * N[c];
+        }
+        nw[c] = v;
+      }
+      for (int c = 0; c <= q; ++c) N[c] = nw[c];
+    }
+    for (int c = 0; c <= p; ++c) D[(size_t)r * (p + 1) + c] = N[c];
+  }
+  const int first = i - p;
+  if (!ax.wts.empty()) {
+    std::vector<double> w(R + 1, 0.0);
+    for (int r = 0; r <= R; ++r)
+      for (int c = 0; c <= p; ++c) {
+        D[(size_t)r * (p + 1) + c] *= ax.wts[first + c];
+        w[r] += D[(size_t)r * (p + 1) + c];
+      }
+    for (int r = 0; r <= R; ++r) {
+      double binom = 1.0;
+      for (int j = 1; j <= r; ++j) {
+        binom = binom * (r - j + 1) / j;
+        for (int c = 0; c <= p; ++c) D[(size_t)r * (p + 1) + c] -= binom * w[j] * D[(size_t)(r - j) * (p + 1) + c];
+      }
+      for (int c = 0; c <= p; ++c) D[(size_t)r * (p + 1) + c] /= w[0];
+    }
+  }
+  std::copy(D.begin(), D.end(), out);
+  return first;
+}
+
+// Decoded error of the model's current P against device data qd: fills
+// r = {sum E^2, max |E|, min Q, max Q}; synchronous.
+int model_residual(mfa_model* md, const void* qd, int q_dtype, double r[4]) {
+  mfa_handle* h = md->h;
+  int rc;
+  if (md->prec == MFA_PREC_FP64)
+    rc = q_dtype == MFA_F64 ? run_decode_grid<double, double, double>(md, nullptr, (const double*)qd)
+                            : run_decode_grid<double, float, double>(md, nullptr, (const float*)qd);
+  else
+    rc = q_dtype == MFA_F64 ? run_decode_grid<ff, double, ff>(md, nullptr, (const double*)qd)
+                            : run_decode_grid<ff, float, ff>(md, nullptr, (const float*)qd);
+  if (rc != MFA_OK) return rc;
+  cudaError_t e = cudaMemcpyAsync(h->h_pinned, h->d_result, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::memcpy(r, h->h_pinned, 4 * sizeof(double));
+  return MFA_OK;
+}
+
 int read_status(mfa_handle* h) {
   int st = 0;
   cudaError_t e = cudaMemcpyAsync(h->h_pinned, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
@@ -876,14 +1018,16 @@ const char* mfa_status_string(int s) {
 }
 
 int mfa_axis_layout(int64_t npts, int32_t nspans, int32_t degree, int32_t nsub, const int32_t* core_spans,
-                    int32_t overlap, int32_t* out, int32_t cap, int32_t* owner) {
+                    int32_t overlap, int32_t knots, int32_t* out, int32_t cap, int32_t* owner) {
   if (!out || npts < 1 || degree < 1 || degree > MFA_MAX_DEGREE || nsub < 1 || cap < nsub) return MFA_ERR_ARG;
   AxisHost ax;
-  const int rc = build_axis(ax, npts, nspans, degree, nsub, core_spans, overlap);
+  const int rc = build_axis(ax, npts, nspans, degree, nsub, core_spans, overlap, knots);
   if (rc != MFA_OK) return rc;
   for (int s = 0; s < nsub; ++s) {
     const AxisSub& sb = ax.subs[s];
-    int32_t* o = out + 8 * (size_t)s;
+    int32_t* o = out + 10 * (size_t)s;
+    o[8] = sb.oU;
+    o[9] = sb.nU;
     o[0] = sb.a;
     o[1] = sb.b;
     o[2] = sb.w0;
@@ -975,6 +1119,7 @@ namespace {
 // Offsets of a model's device tables (one arena: the host-filled tables
 // first, then those the setup kernels compute) and buffers (one pool block).
 struct TablePlan {
+  size_t o_w[3];
   size_t o_span[3], o_vd[3], o_vf[3], o_vff[3], o_ss[3], o_subs[3], o_of[3], o_oc[3], o_AL[3], o_fLd[3], o_fLf[3],
       o_fLff[3], o_fUd[3], o_fUf[3], o_fUff[3], o_ot[3], o_nlt[3], o_pk[3], o_one[3];
   size_t o_offL = 0, o_offS1 = 0, o_offS2 = 0, o_ops = 0, o_rows = 0, o_xs = 0;
@@ -992,6 +1137,7 @@ struct TablePlan {
 struct PlanCache {
   mfa_layout lay{};
   std::vector<int32_t> cores[3];
+  std::vector<double> wts[3];
   bool plain = false;
   size_t stage_bytes = 0;
   mfa_model* proto = nullptr;
@@ -1001,7 +1147,8 @@ struct PlanCache {
 bool plan_matches(const PlanCache& pc, const mfa_layout* lay, bool plain, size_t stage_bytes) {
   if (pc.plain != plain || pc.stage_bytes != stage_bytes) return false;
   const mfa_layout& k = pc.lay;
-  if (k.dim != lay->dim || k.degree != lay->degree || k.precision != lay->precision) return false;
+  if (k.dim != lay->dim || k.degree != lay->degree || k.precision != lay->precision || k.knots != lay->knots)
+    return false;
   for (int a = 0; a < lay->dim && a < 3; ++a) {
     if (k.npts[a] != lay->npts[a] || k.nspans[a] != lay->nspans[a] || k.nsub[a] != lay->nsub[a] ||
         k.overlap[a] != lay->overlap[a] || k.lo[a] != lay->lo[a] || k.hi[a] != lay->hi[a])
@@ -1009,6 +1156,9 @@ bool plan_matches(const PlanCache& pc, const mfa_layout* lay, bool plain, size_t
     if ((lay->core_spans[a] == nullptr) != pc.cores[a].empty()) return false;
     if (lay->core_spans[a] &&
         std::memcmp(lay->core_spans[a], pc.cores[a].data(), sizeof(int32_t) * pc.cores[a].size()) != 0)
+      return false;
+    if ((lay->weights[a] == nullptr) != pc.wts[a].empty()) return false;
+    if (lay->weights[a] && std::memcmp(lay->weights[a], pc.wts[a].data(), sizeof(double) * pc.wts[a].size()) != 0)
       return false;
   }
   return true;
@@ -1044,6 +1194,9 @@ int bind_model(mfa_handle* h, mfa_model* md, const TablePlan& tp) {
     d.n = ax.n;
     d.S = ax.S;
     d.pieces = ax.pieces;
+    d.kmode = ax.kmode;
+    d.gspans = ax.gspans;
+    d.wts = ax.wts.empty() ? nullptr : at_off<double>(md->arena, tp.o_w[a]);
     d.span = at_off<int>(md->arena, tp.o_span[a]);
     d.vals_d = at_off<double>(md->arena, tp.o_vd[a]);
     d.vals_f = at_off<float>(md->arena, tp.o_vf[a]);
@@ -1164,6 +1317,7 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
     tp.o_nlt[a] = ar.take<int>(ax.S);
     tp.o_pk[a] = ar.take<int>(ax.n);
     tp.o_one[a] = ar.take<int2>(ax.S);
+    tp.o_w[a] = ar.take<double>(ax.wts.size());
   }
   tp.o_offL = ar.take<long long>(ns);
   tp.o_offS1 = ar.take<long long>(ns);
@@ -1259,6 +1413,7 @@ int materialize_model(mfa_handle* h, mfa_model* md, const std::vector<AxisOp>& o
     std::memcpy(img + tp.o_nlt[a], ax.nL_tab.data(), sizeof(int) * ax.S);
     std::memcpy(img + tp.o_pk[a], ax.own_pick.data(), sizeof(int) * ax.n);
     std::memcpy(img + tp.o_one[a], ax.one_rng.data(), sizeof(int2) * ax.S);
+    std::memcpy(img + tp.o_w[a], ax.wts.data(), sizeof(double) * ax.wts.size());
   }
   std::memcpy(img + tp.o_rows, rows_full.data(), sizeof(int) * rows_full.size());
   std::memcpy(img + tp.o_rows + sizeof(int) * rows_full.size(), rows_part.data(), sizeof(int) * rows_part.size());
@@ -1289,7 +1444,7 @@ int mfa_encode_plain(mfa_handle* h, const mfa_layout* lay, const void* q, int q_
   if (lay->precision != MFA_PREC_FP64) return MFA_ERR_ARG;
   int rc = encode_impl(h, lay, q, q_dtype, q_on_device, true, out);
   if (rc != MFA_OK) return rc;
-  rc = mfa_schwarz_iterate(h, *out, max_iters, tol_dP, rep);
+  rc = mfa_schwarz_iterate(h, *out, max_iters, tol_dP, 0.0, rep);
   if (rc < 0) {
     mfa_free(*out);
     *out = nullptr;
@@ -1307,6 +1462,7 @@ int create_model(mfa_handle* h, const mfa_layout* lay, bool plain, size_t stage_
   if (lay->dim < 1 || lay->dim > MFA_MAX_DIM) return MFA_ERR_ARG;
   if (lay->degree < 1 || lay->degree > MFA_MAX_DEGREE) return MFA_ERR_ARG;
   if (lay->precision != MFA_PREC_FP64 && lay->precision != MFA_PREC_MIXED) return MFA_ERR_ARG;
+  if (lay->knots != MFA_KNOTS_FLOATING && lay->knots != MFA_KNOTS_CLAMPED) return MFA_ERR_ARG;
   DeviceGuard g(h->device);
   if (h->plan_valid && h->plan && h->plan->proto && plan_matches(*h->plan, lay, plain, stage_bytes)) {
     mfa_model* md = new (std::nothrow) mfa_model(*h->plan->proto);
@@ -1337,7 +1493,14 @@ int create_model(mfa_handle* h, const mfa_layout* lay, bool plain, size_t stage_
         return MFA_ERR_ARG;
       }
       rc = build_axis(md->axh[a], lay->npts[a], lay->nspans[a], lay->degree, lay->nsub[a], lay->core_spans[a],
-                      lay->overlap[a]);
+                      lay->overlap[a], lay->knots);
+      if (rc == MFA_OK && lay->weights[a]) {
+        // separable NURBS weights (Sec. 2.1, Eq. nurbs-basis): positive and finite
+        AxisHost& ax = md->axh[a];
+        ax.wts.assign(lay->weights[a], lay->weights[a] + ax.n);
+        for (double w : ax.wts)
+          if (!(w > 0.0) || !std::isfinite(w)) rc = MFA_ERR_ARG;
+      }
       md->lo[a] = lay->lo[a];
       md->hi[a] = lay->hi[a];
       md->overlap[a] = lay->overlap[a];
@@ -1355,6 +1518,9 @@ int create_model(mfa_handle* h, const mfa_layout* lay, bool plain, size_t stage_
     return MFA_ERR_ARG;
   }
   md->nsub = md->axh[0].S * md->axh[1].S * md->axh[2].S;
+  md->knots = lay->knots;
+  for (int a = 0; a < 3; ++a)
+    if (md->axh[a].kmode != KMODE_FLOATING) md->use_fused = false;  // the fused kernels take uniform spans
   {
     // the fused projection's stage-1 output of control point c (floats
     // 4(c/2) + c%2 and 4(c/2) + c%2 + 2 of the staged row) is written while
@@ -1403,6 +1569,8 @@ int create_model(mfa_handle* h, const mfa_layout* lay, bool plain, size_t stage_
         pc.cores[a].clear();
         if (a < lay->dim && lay->core_spans[a]) pc.cores[a].assign(lay->core_spans[a], lay->core_spans[a] + lay->nsub[a]);
         pc.lay.core_spans[a] = nullptr;
+        pc.wts[a] = a < lay->dim ? md->axh[a].wts : std::vector<double>();
+        pc.lay.weights[a] = nullptr;
       }
       pc.plain = plain;
       pc.stage_bytes = stage_bytes;
@@ -1508,11 +1676,24 @@ int mfa_set_update_rule(mfa_handle* h, mfa_model* md, int rule) {
   return st < 0 ? st : MFA_OK;
 }
 
-int mfa_schwarz_iterate(mfa_handle* h, mfa_model* md, int32_t max_iters, double tol_dP, mfa_report* rep) {
+int mfa_schwarz_iterate(mfa_handle* h, mfa_model* md, int32_t max_iters, double tol_dP, double tol_rms_stall,
+                        mfa_report* rep) {
   if (!h || !md || md->h != h || max_iters < 0 || (!md->has_state && max_iters > 0)) return MFA_ERR_ARG;
+  if (!(tol_rms_stall == tol_rms_stall) || !(tol_dP == tol_dP)) return MFA_ERR_ARG;
+  const bool stall = tol_rms_stall > 0 && max_iters > 0;
+  if (stall && (!md->q_src || md->batch)) return MFA_ERR_ARG;  // the stall test decodes against the encoded data
   DeviceGuard g(h->device);
   int status = read_status(h);  // surfaces encode-time device errors
   if (status < 0) return status;
+  const long long npts = (long long)md->axh[0].M * md->axh[1].M * md->axh[2].M;
+  double res[4] = {0, 0, 0, 0};
+  double rms_prev = 0.0;
+  if (stall) {
+    // RMS of the current iterate (P^0 right after the encode)
+    const int rr = model_residual(md, md->q_src, md->q_src_dtype, res);
+    if (rr != MFA_OK) return rr;
+    rms_prev = std::sqrt(res[0] / (double)npts);
+  }
   int rc = MFA_NOT_CONVERGED;
   for (int it = 0; it < max_iters; ++it) {
     if (md->prec == MFA_PREC_FP64)
@@ -1535,6 +1716,7 @@ int mfa_schwarz_iterate(mfa_handle* h, mfa_model* md, int32_t max_iters, double 
       md->grow_streak = 0;
     md->last_dP = dP;
     md->last_jump = v[2];
+    md->last_rms = -1.0;
     if (!std::isfinite(dP) || md->grow_streak >= 8) {
       rc = MFA_ERR_DIVERGED;
       break;
@@ -1542,6 +1724,18 @@ int mfa_schwarz_iterate(mfa_handle* h, mfa_model* md, int32_t max_iters, double 
     if (tol_dP > 0 && dP <= tol_dP) {
       rc = MFA_OK;
       break;
+    }
+    if (stall) {
+      // decoded-residual stall: |RMS_k - RMS_{k-1}| <= tol * RMS_k
+      const int rr = model_residual(md, md->q_src, md->q_src_dtype, res);
+      if (rr != MFA_OK) return rr;
+      const double rms = std::sqrt(res[0] / (double)npts);
+      md->last_rms = rms;
+      if (std::fabs(rms - rms_prev) <= tol_rms_stall * rms) {
+        rc = MFA_OK;
+        break;
+      }
+      rms_prev = rms;
     }
   }
   if (max_iters == 0) rc = MFA_OK;
@@ -1552,6 +1746,11 @@ int mfa_schwarz_iterate(mfa_handle* h, mfa_model* md, int32_t max_iters, double 
     rep->status = rc;
     rep->dP_rel = md->last_dP;
     rep->jump_max = md->last_jump;
+    if (stall && md->last_rms >= 0) {
+      rep->rms_decoded = md->last_rms;
+      rep->maxabs_decoded = res[1];
+      rep->data_range = res[3] - res[2];
+    }
   }
   return rc;
 }
@@ -1575,12 +1774,24 @@ int mfa_decode(mfa_handle* h, const mfa_model* mdc, const double* pts, int64_t n
     // scattered points: copy coordinates (host) to the workspace
     const size_t pbytes = (size_t)npts_q * md->dim * sizeof(double);
     const size_t obytes = out_on_device ? 0 : (size_t)npts_q * osz;
-    int rc = ensure_ws(h, align256(pbytes) + align256(obytes) + 256);
+    // float-float models with clamped interfaces or NURBS weights decode from
+    // an FP64 copy of their control points with the general basis kernel
+    bool general = false;
+    for (int a = 0; a < md->dim; ++a) general = general || md->axh[a].kmode != KMODE_FLOATING || !md->axh[a].wts.empty();
+    const bool via64 = general && md->prec != MFA_PREC_FP64;
+    const long long ncp = (long long)md->axh[0].n * md->axh[1].n * md->axh[2].n;
+    const size_t cbytes = via64 ? (size_t)ncp * sizeof(double) : 0;
+    int rc = ensure_ws(h, align256(pbytes) + align256(obytes) + align256(cbytes) + 256);
     if (rc != MFA_OK) return rc;
     double* dpts = (double*)h->ws;
     void* dout = out_on_device ? out : (void*)((char*)h->ws + align256(pbytes));
+    double* P64 = (double*)((char*)h->ws + align256(pbytes) + align256(obytes));
     cudaError_t e = cudaMemcpyAsync(dpts, pts, pbytes, cudaMemcpyDefault, h->stream);
-    if (md->prec == MFA_PREC_FP64)
+    if (via64) {
+      TRACED(h, TR_MISC, (launch_cast<ff, double>((const ff*)md->P, P64, ncp, h->stream)));
+      TRACED(h, TR_DECODE_POINTS,
+             launch_decode_points<double>(md->L, md->lo, md->hi, dpts, npts_q, der, P64, dout, out_dtype, h->stream));
+    } else if (md->prec == MFA_PREC_FP64)
       TRACED(h, TR_DECODE_POINTS,
              launch_decode_points<double>(md->L, md->lo, md->hi, dpts, npts_q, der, (const double*)md->P, dout,
                                           out_dtype, h->stream));
@@ -1644,21 +1855,10 @@ int mfa_residual(mfa_handle* h, const mfa_model* mdc, const void* q, int q_dtype
     e = cudaMemcpyAsync(qtmp, q, qb, cudaMemcpyHostToDevice, h->stream);
     qd = qtmp;
   }
-  int rc;
-  if (md->prec == MFA_PREC_FP64)
-    rc = q_dtype == MFA_F64 ? run_decode_grid<double, double, double>(md, nullptr, (const double*)qd)
-                            : run_decode_grid<double, float, double>(md, nullptr, (const float*)qd);
-  else
-    rc = q_dtype == MFA_F64 ? run_decode_grid<ff, double, ff>(md, nullptr, (const double*)qd)
-                            : run_decode_grid<ff, float, ff>(md, nullptr, (const float*)qd);
-  if (rc == MFA_OK && e == cudaSuccess)
-    e = cudaMemcpyAsync(h->h_pinned, h->d_result, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  double r[4] = {0, 0, 0, 0};
+  int rc = e == cudaSuccess ? model_residual(md, qd, q_dtype, r) : cuda_status(e);
   if (qtmp) pool_free(h, qtmp);
   if (rc != MFA_OK) return rc;
-  if (e != cudaSuccess) return cuda_status(e);
-  double r[4];
-  std::memcpy(r, h->h_pinned, sizeof(r));
   rep->rms_decoded = std::sqrt(r[0] / (double)n);
   rep->maxabs_decoded = r[1];
   rep->data_range = r[3] - r[2];
@@ -1667,6 +1867,99 @@ int mfa_residual(mfa_handle* h, const mfa_model* mdc, const void* q, int q_dtype
   rep->jump_max = md->last_jump;
   int st = read_status(h);
   rep->status = st;
+  return st < 0 ? st : MFA_OK;
+}
+
+int mfa_interface_jumps(mfa_handle* h, const mfa_model* mdc, int32_t max_order, mfa_report* rep) {
+  mfa_model* md = const_cast<mfa_model*>(mdc);
+  if (!h || !md || md->h != h || !rep || md->batch || !md->has_state) return MFA_ERR_ARG;
+  if (max_order < 0 || max_order > md->degree) return MFA_ERR_ARG;
+  DeviceGuard g(h->device);
+  const int R = max_order, p = md->degree, w = (R + 1) * (p + 1);
+  // one-sided rows at every interface of every axis, then the neighbour pairs
+  std::vector<double> rows;
+  std::vector<int> rowcp;
+  int row0[3] = {0, 0, 0};
+  for (int a = 0; a < md->dim; ++a) {
+    const AxisHost& ax = md->axh[a];
+    row0[a] = (int)rowcp.size();
+    for (int i = 0; i + 1 < ax.S; ++i)
+      for (int side = 0; side < 2; ++side) {
+        rows.resize(rows.size() + w);
+        const int f = host_onesided_basis(ax, ax.subs[i].b, side, R, rows.data() + rows.size() - w);
+        if (f < 0) return MFA_ERR_LAYOUT;
+        rowcp.push_back(f);
+      }
+  }
+  // samples along the other axes: the data points of the pair's common core
+  auto core_pts = [&](int b, int piece, int& k0, int& k1) {
+    const AxisHost& ax = md->axh[b];
+    const AxisSub& sb = ax.subs[piece];
+    if (ax.M == 1) {
+      k0 = 0;
+      k1 = 1;
+      return;
+    }
+    const long long M1 = ax.M - 1;
+    k0 = (int)((sb.a * M1 + ax.gspans - 1) / ax.gspans);
+    k1 = (int)((sb.b * M1) / ax.gspans) + 1;
+  };
+  std::vector<JumpPair> pairs;
+  const int S0 = md->axh[0].S, S1 = md->axh[1].S;
+  for (int a = 0; a < md->dim; ++a)
+    for (int sd = 0; sd < md->nsub; ++sd) {
+      const int sa[3] = {sd % S0, (sd / S0) % S1, sd / (S0 * S1)};
+      if (sa[a] + 1 >= md->axh[a].S) continue;
+      JumpPair jp{};
+      jp.s = sd;
+      jp.t = sd + (a == 0 ? 1 : (a == 1 ? S0 : S0 * S1));
+      jp.axis = a;
+      jp.iface = row0[a] + 2 * sa[a];  // row of the left limit; the right limit follows it
+      for (int b = 0; b < 3; ++b) {
+        if (b == a) {
+          jp.k0[b] = 0;
+          jp.k1[b] = 1;
+        } else {
+          core_pts(b, sa[b], jp.k0[b], jp.k1[b]);
+        }
+      }
+      pairs.push_back(jp);
+    }
+  for (int r = 0; r <= MFA_MAX_DEGREE; ++r) rep->jump_deriv[r] = 0.0;
+  rep->jump_orders = R + 1;
+  if (pairs.empty()) return MFA_OK;
+  const size_t b_pairs = align256(pairs.size() * sizeof(JumpPair)), b_rows = align256(rows.size() * sizeof(double));
+  const size_t b_cp = align256(rowcp.size() * sizeof(int));
+  int rc = ensure_ws(h, b_pairs + b_rows + b_cp + 256);
+  if (rc != MFA_OK) return rc;
+  char* ws = (char*)h->ws;
+  JumpPair* dpairs = (JumpPair*)ws;
+  double* drows = (double*)(ws + b_pairs);
+  int* dcp = (int*)(ws + b_pairs + b_rows);
+  unsigned long long* dout = (unsigned long long*)(ws + b_pairs + b_rows + b_cp);
+  cudaError_t e = cudaMemcpyAsync(dpairs, pairs.data(), pairs.size() * sizeof(JumpPair), cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(drows, rows.data(), rows.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dcp, rowcp.data(), rowcp.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dout, 0, (R + 1) * sizeof(unsigned long long), h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int use_frames = md->iters > 0 ? 1 : 0;
+  if (md->prec == MFA_PREC_FP64)
+    TRACED(h, TR_MISC, launch_interface_jumps<double>(md->L, md->offL, (const double*)md->X,
+                                                      (const double*)md->Pprev, use_frames, dpairs,
+                                                      (int)pairs.size(), drows, dcp, R, dout, h->stream));
+  else
+    TRACED(h, TR_MISC, launch_interface_jumps<ff>(md->L, md->offL, (const ff*)md->X, (const ff*)md->Pprev, use_frames,
+                                                  dpairs, (int)pairs.size(), drows, dcp, R, dout, h->stream));
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->h_pinned, dout, (R + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  std::memcpy(rep->jump_deriv, h->h_pinned, (R + 1) * sizeof(double));
+  int st = read_status(h);
   return st < 0 ? st : MFA_OK;
 }
 
@@ -1736,13 +2029,15 @@ int mfa_get_ctrl_async(mfa_handle* h, const mfa_model* mdc, double* host_out, in
 
 namespace {
 constexpr char kMagic[8] = {'M', 'F', 'A', 'G', 'B', '3', 0, 1};
-constexpr int32_t kFileVersion = 1;
+// version 2 adds the knot mode, NURBS weights and (with state) the lagged
+// iterate; version 1 files (floating knots, no weights) are still read
+constexpr int32_t kFileVersion = 2;
 
 struct FileHeader {
   char magic[8];
-  int32_t version, dim, degree, precision, update, flags, iters, pad;
+  int32_t version, dim, degree, precision, update, flags, iters, knots;
   int64_t npts[3];
-  int32_t nspans[3], nsub[3], overlap[3], pad2;
+  int32_t nspans[3], nsub[3], overlap[3], wmask;  // wmask: bit a set when axis a has weights
   double lo[3], hi[3];
   double last_dP, last_jump;
   int64_t ncp, sizeL;
@@ -1763,9 +2058,11 @@ int mfa_save(mfa_handle* h, const mfa_model* mdc, const char* path, int flags) {
   H.update = md->update == UPDATE_OWNER ? MFA_UPDATE_OWNER : MFA_UPDATE_AVERAGE;
   H.flags = flags & MFA_SAVE_STATE;
   H.iters = md->iters;
+  H.knots = md->knots;
   for (int a = 0; a < 3; ++a) {
+    if (!md->axh[a].wts.empty()) H.wmask |= 1 << a;
     H.npts[a] = md->axh[a].M;
-    H.nspans[a] = md->axh[a].nspans;
+    H.nspans[a] = md->axh[a].gspans;
     H.nsub[a] = md->axh[a].S;
     H.overlap[a] = md->overlap[a];
     H.lo[a] = md->lo[a];
@@ -1776,13 +2073,17 @@ int mfa_save(mfa_handle* h, const mfa_model* mdc, const char* path, int flags) {
   H.ncp = (long long)md->axh[0].n * md->axh[1].n * md->axh[2].n;
   H.sizeL = md->sizeL;
   const size_t es = elem_size(md->prec);
-  std::vector<char> buf((size_t)H.ncp * es + ((flags & MFA_SAVE_STATE) ? 2 * (size_t)md->sizeL * es : 0));
+  const bool state = (flags & MFA_SAVE_STATE) != 0;
+  std::vector<char> buf((size_t)H.ncp * es * (state ? 2 : 1) + (state ? 2 * (size_t)md->sizeL * es : 0));
   cudaError_t e = cudaMemcpyAsync(buf.data(), md->P, (size_t)H.ncp * es, cudaMemcpyDeviceToHost, h->stream);
-  if (e == cudaSuccess && (flags & MFA_SAVE_STATE)) {
+  if (e == cudaSuccess && state) {
     char* p2 = buf.data() + (size_t)H.ncp * es;
     e = cudaMemcpyAsync(p2, md->BL, (size_t)md->sizeL * es, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(p2 + (size_t)md->sizeL * es, md->X, (size_t)md->sizeL * es, cudaMemcpyDeviceToHost,
+                          h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p2 + 2 * (size_t)md->sizeL * es, md->Pprev, (size_t)H.ncp * es, cudaMemcpyDeviceToHost,
                           h->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1795,6 +2096,9 @@ int mfa_save(mfa_handle* h, const mfa_model* mdc, const char* path, int flags) {
       const int32_t c = sb.b - sb.a;
       ok = ok && std::fwrite(&c, sizeof(c), 1, f) == 1;
     }
+  for (int a = 0; a < md->dim && ok; ++a)
+    if (H.wmask & (1 << a))
+      ok = std::fwrite(md->axh[a].wts.data(), sizeof(double), md->axh[a].wts.size(), f) == md->axh[a].wts.size();
   ok = ok && std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
   ok = (std::fclose(f) == 0) && ok;
   return ok ? MFA_OK : MFA_ERR_IO;
@@ -1807,16 +2111,30 @@ int mfa_load(mfa_handle* h, const char* path, mfa_model** out) {
   if (!f) return MFA_ERR_IO;
   FileHeader H{};
   bool ok = std::fread(&H, sizeof(H), 1, f) == 1 && std::memcmp(H.magic, kMagic, 8) == 0 &&
-            H.version == kFileVersion && H.dim >= 1 && H.dim <= MFA_MAX_DIM && H.degree >= 1 &&
-            H.degree <= MFA_MAX_DEGREE && (H.precision == MFA_PREC_FP64 || H.precision == MFA_PREC_MIXED);
+            (H.version == 1 || H.version == kFileVersion) && H.dim >= 1 && H.dim <= MFA_MAX_DIM &&
+            H.degree >= 1 && H.degree <= MFA_MAX_DEGREE &&
+            (H.precision == MFA_PREC_FP64 || H.precision == MFA_PREC_MIXED);
+  if (ok && H.version == 1) {
+    H.knots = MFA_KNOTS_FLOATING;
+    H.wmask = 0;
+  }
+  ok = ok && (H.knots == MFA_KNOTS_FLOATING || H.knots == MFA_KNOTS_CLAMPED) && (H.wmask & ~7) == 0;
   std::vector<int32_t> cores[3];
+  std::vector<double> wts[3];
   for (int a = 0; a < H.dim && ok; ++a) {
-    ok = H.nsub[a] >= 1 && H.nsub[a] <= (1 << 20);
+    ok = H.nsub[a] >= 1 && H.nsub[a] <= (1 << 20) && H.nspans[a] >= 1 && H.nspans[a] <= (1 << 30);
     if (ok) {
       cores[a].resize(H.nsub[a]);
       ok = std::fread(cores[a].data(), sizeof(int32_t), H.nsub[a], f) == (size_t)H.nsub[a];
     }
   }
+  for (int a = 0; a < H.dim && ok; ++a)
+    if (H.wmask & (1 << a)) {
+      long long n = (long long)H.nspans[a] + H.degree;
+      if (H.knots == MFA_KNOTS_CLAMPED && H.degree > 1) n += (long long)(H.degree - 1) * (H.nsub[a] - 1);
+      wts[a].resize((size_t)n);
+      ok = std::fread(wts[a].data(), sizeof(double), (size_t)n, f) == (size_t)n;
+    }
   if (!ok) {
     std::fclose(f);
     return MFA_ERR_IO;
@@ -1825,7 +2143,9 @@ int mfa_load(mfa_handle* h, const char* path, mfa_model** out) {
   lay.dim = H.dim;
   lay.degree = H.degree;
   lay.precision = H.precision;
+  lay.knots = H.knots;
   for (int a = 0; a < 3; ++a) {
+    lay.weights[a] = wts[a].empty() ? nullptr : wts[a].data();
     lay.npts[a] = H.npts[a];
     lay.nspans[a] = H.nspans[a];
     lay.nsub[a] = H.nsub[a];
@@ -1844,8 +2164,9 @@ int mfa_load(mfa_handle* h, const char* path, mfa_model** out) {
   const size_t es = elem_size(md->prec);
   const long long ncp = (long long)md->axh[0].n * md->axh[1].n * md->axh[2].n;
   const bool state = (H.flags & MFA_SAVE_STATE) != 0;
+  const bool has_prev = state && H.version >= 2;
   ok = H.ncp == ncp && (!state || H.sizeL == md->sizeL);
-  std::vector<char> buf(ok ? (size_t)ncp * es + (state ? 2 * (size_t)md->sizeL * es : 0) : 0);
+  std::vector<char> buf(ok ? (size_t)ncp * es * (has_prev ? 2 : 1) + (state ? 2 * (size_t)md->sizeL * es : 0) : 0);
   ok = ok && std::fread(buf.data(), 1, buf.size(), f) == buf.size();
   std::fclose(f);
   DeviceGuard g(h->device);
@@ -1857,6 +2178,11 @@ int mfa_load(mfa_handle* h, const char* path, mfa_model** out) {
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(md->X, p2 + (size_t)md->sizeL * es, (size_t)md->sizeL * es, cudaMemcpyHostToDevice,
                           h->stream);
+    // the lagged iterate (the frames of the last step); a version-1 file has
+    // none, and its P stands in for it
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(md->Pprev, has_prev ? p2 + 2 * (size_t)md->sizeL * es : buf.data(), (size_t)ncp * es,
+                          cudaMemcpyHostToDevice, h->stream);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   if (!ok || e != cudaSuccess) {
@@ -2227,7 +2553,7 @@ int build_batch_group(mfa_batch* b, int d, int p, const std::vector<int>& mem, m
     pmax = std::max(pmax, np);
     ptot += np;
   }
-  md->use_fused = (d == 3 && md->prec == MFA_PREC_MIXED && pmax * 2 * 152 <= 3 * ptot / 2);
+  md->use_fused = (d == 3 && md->prec == MFA_PREC_MIXED && pmax * 2 * device_sm_count() <= 3 * ptot / 2);
   md->x_inplace_ok = true;
   for (const AxisSub& sb : md->axh[0].subs) {
     const long long Mi = sb.m, nsi = sb.w1 - sb.w0;

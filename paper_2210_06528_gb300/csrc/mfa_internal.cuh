@@ -26,11 +26,23 @@ struct AxisSub {
   int bandU;  // first row of this piece in the per-axis U band arrays
 };
 
-// Per-axis device tables.
+// Knot layout of an axis.
+enum { KMODE_FLOATING = 0, KMODE_CLAMPED = 2 };
+
+// Per-axis device tables.  Spans are numbered by the first control point
+// nonzero on them (span j has control points j .. j+p), so `nspans` counts
+// span numbers, including numbers no span uses (between the pieces of a batch
+// or across the repeated knots of a clamped interface); `gspans` is the
+// number of knot spans of the axis's own grid.
 struct AxisDev {
   int M, nspans, p, n, S;
   int pieces;               // 1: every piece (subs[i]) has its own knot vector with w1 - w0 spans over its
                             // own points, spans numbered from its l0 (a batch of independent fits)
+  int kmode;                // KMODE_FLOATING, or KMODE_CLAMPED: interface knots repeated p times, so the
+                            // points of core [a, b) use that core's own clamped uniform knots (b - a spans),
+                            // spans numbered from the core's first owned control point
+  int gspans;               // knot spans of the grid (uniform breakpoints i / gspans)
+  const double* wts;        // [n] NURBS control-point weights, or nullptr (W = 1)
   const int* span;          // [M] knot span of every data point
   const double* vals_d;     // [M * (p+1)] N_{span+r,p}(u_k), r = 0..p
   const float* vals_f;      // same, rounded to FP32
@@ -104,6 +116,10 @@ struct AxisOp {
 struct AxisHost {
   int M = 1, nspans = 1, p = 0, n = 1, S = 1;
   int pieces = 0;
+  int kmode = KMODE_FLOATING;
+  int gspans = 1;
+  std::vector<int> knots;    // knot positions in span units (t_i = knots[i] / gspans), n + p + 1 of them
+  std::vector<double> wts;   // NURBS weights (empty: W = 1)
   std::vector<AxisSub> subs;
   std::vector<int> own_first, own_count, span_start, nL_tab, own_pick;
   std::vector<int2> one_rng;  // per piece: control points owned by it alone, [x, y)
@@ -120,6 +136,10 @@ struct TileMap {
   int ntiles = 0;
   int threads = 0;  // block size = elements per tile
 };
+
+// Streaming multiprocessors of the calling thread's current device (read once
+// per device ordinal from cudaDevAttrMultiProcessorCount; 1 if unavailable).
+int device_sm_count();
 
 // Dynamic shared-memory limit (and, with `carveout`, the preferred shared
 // memory share) of a kernel, set once per kernel, device and size: the
@@ -174,6 +194,18 @@ void launch_expand_residual_tiles(const LayoutDev& L, int axis, const AxisOp* op
                                   double* out, cudaStream_t st);
 void launch_reduce_partials(const double* partials, int nblocks, double* result, cudaStream_t st,
                             double* scratch = nullptr, int scratch_rows = 0);
+
+// Interface jumps (mfa_interface_jumps): one pair of neighbouring subdomains
+// along `axis`, left piece index `iface` on that axis.
+struct JumpPair {
+  int s, t;          // left and right subdomain
+  int axis, iface;
+  int k0[3], k1[3];  // sample data points [k0, k1) along every axis (one along `axis`)
+};
+template <typename T>
+void launch_interface_jumps(const LayoutDev& L, const long long* offL, const T* X, const T* Pprev, int use_frames,
+                            const JumpPair* pairs, int npairs, const double* rows, const int* rowcp, int R,
+                            unsigned long long* out, cudaStream_t st);
 template <typename TIn, typename TOut>
 void launch_cast(const TIn* in, TOut* out, long long n, cudaStream_t st);
 
@@ -222,9 +254,11 @@ void launch_decode_points_inst(const InstDesc* desc, const int* qinst, const lon
                                cudaStream_t st);  // p_uniform: the degree of every instance, else 0
 
 
-constexpr int kResidualBlocks = 1216;  // 8 x 152 SMs
+constexpr int kResidualBlocks = 1216;  // fixed partition of the residual reduction (FP64 partials, any device)
 // block sizes of the generic kernels (tile sizes of their TileMaps)
 constexpr int kContractThreads = 128, kExpandThreads = 256, kSolveThreads = 64;
-constexpr int kAvgListBlocks = 152 * 3;  // float-float update: blocks on the shared control points (3 per SM)
+// float-float update: at most this many blocks on the shared control points
+// (3 per SM of the device, capped; the partials buffer is sized for the cap)
+constexpr int kAvgListBlocks = 768;
 
 }  // namespace mfa

@@ -32,6 +32,8 @@ MFA_ERR_IO = -10
 MFA_SAVE_STATE = 1
 MFA_F32, MFA_F64 = 0, 1
 MFA_PREC_FP64, MFA_PREC_MIXED = 0, 1
+MFA_KNOTS_FLOATING, MFA_KNOTS_CLAMPED = 0, 1
+MFA_MAX_DEGREE = 7
 MFA_UPDATE_AVERAGE, MFA_UPDATE_OWNER = 0, 1
 
 MFA_TRACE_CLASSES = 16
@@ -41,16 +43,21 @@ class mfa_layout(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("degree", ctypes.c_int32), ("npts", ctypes.c_int64 * 3),
                 ("nspans", ctypes.c_int32 * 3), ("nsub", ctypes.c_int32 * 3),
                 ("core_spans", ctypes.POINTER(ctypes.c_int32) * 3), ("overlap", ctypes.c_int32 * 3),
-                ("precision", ctypes.c_int32), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3)]
+                ("precision", ctypes.c_int32), ("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("knots", ctypes.c_int32), ("weights", ctypes.POINTER(ctypes.c_double) * 3)]
 
 
 class mfa_report(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("dP_rel", ctypes.c_double),
                 ("jump_max", ctypes.c_double), ("rms_decoded", ctypes.c_double),
-                ("maxabs_decoded", ctypes.c_double), ("data_range", ctypes.c_double)]
+                ("maxabs_decoded", ctypes.c_double), ("data_range", ctypes.c_double),
+                ("jump_orders", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("jump_deriv", ctypes.c_double * (MFA_MAX_DEGREE + 1))]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("pad_", "jump_deriv")}
+        d["jump_deriv"] = [self.jump_deriv[r] for r in range(self.jump_orders)]
+        return d
 
 
 class mfa_instance(ctypes.Structure):
@@ -103,7 +110,10 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_create.argtypes = [ctypes.c_int, P, ctypes.POINTER(P)]
     lib.mfa_destroy.argtypes = [P]
     lib.mfa_encode.argtypes = [P, ctypes.POINTER(mfa_layout), P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(P)]
-    lib.mfa_schwarz_iterate.argtypes = [P, P, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(mfa_report)]
+    lib.mfa_schwarz_iterate.argtypes = [P, P, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                        ctypes.POINTER(mfa_report)]
+    lib.mfa_interface_jumps.argtypes = [P, P, ctypes.c_int32, ctypes.POINTER(mfa_report)]
+    lib.mfa_interface_jumps.restype = ctypes.c_int
     lib.mfa_decode.argtypes = [P, P, P, ctypes.c_int64, P, P, ctypes.c_int, ctypes.c_int]
     lib.mfa_encode_plain.argtypes = [P, ctypes.POINTER(mfa_layout), P, ctypes.c_int, ctypes.c_int, ctypes.c_int32,
                                      ctypes.c_double, ctypes.POINTER(mfa_report), ctypes.POINTER(P)]
@@ -117,8 +127,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_status_string.argtypes = [ctypes.c_int]
     lib.mfa_status_string.restype = ctypes.c_char_p
     lib.mfa_axis_layout.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
-                                    ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
-                                    ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.POINTER(ctypes.c_int32), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
     lib.mfa_axis_layout.restype = ctypes.c_int
     lib.mfa_decode_grid_noalloc.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                             ctypes.POINTER(ctypes.c_int32), P, P, P]
@@ -183,12 +193,24 @@ def _check(rc: int, where: str, ok=(MFA_OK,)) -> int:
 # C-named wrappers (argument marshalling only)
 # ---------------------------------------------------------------------------
 
+def ncp_of(degree, nspans, nsub, knots=MFA_KNOTS_FLOATING):
+    """Control points of one axis: nspans + degree, plus (degree - 1) per
+    interface with clamped interface knots."""
+    n = int(nspans) + int(degree)
+    if knots == MFA_KNOTS_CLAMPED and degree > 1:
+        n += (int(degree) - 1) * (int(nsub) - 1)
+    return n
+
+
 def make_layout(dim, degree, npts, nspans, nsub, overlap, precision=MFA_PREC_FP64, core_spans=None, lo=None,
-                hi=None):
-    """Build an mfa_layout; the returned object keeps the core arrays alive."""
+                hi=None, knots=MFA_KNOTS_FLOATING, weights=None):
+    """Build an mfa_layout; the returned object keeps the core and weight
+    arrays alive.  weights: None or one array of n_a positive weights per axis
+    (separable NURBS weights)."""
     lay = mfa_layout()
     lay.dim = dim
     lay.degree = degree
+    lay.knots = int(knots)
     keep = []
     for a in range(3):
         lay.npts[a] = int(npts[a]) if a < dim else 1
@@ -203,23 +225,32 @@ def make_layout(dim, degree, npts, nspans, nsub, overlap, precision=MFA_PREC_FP6
             lay.core_spans[a] = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int32))
         else:
             lay.core_spans[a] = ctypes.POINTER(ctypes.c_int32)()
+        if weights is not None and a < dim and weights[a] is not None:
+            warr = np.ascontiguousarray(weights[a], dtype=np.float64)
+            keep.append(warr)
+            lay.weights[a] = warr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        else:
+            lay.weights[a] = ctypes.POINTER(ctypes.c_double)()
     lay.precision = precision
     lay._keep = keep
     return lay
 
 
-def mfa_axis_layout(npts: int, nspans: int, degree: int, nsub: int, overlap: int, core_spans=None):
+def mfa_axis_layout(npts: int, nspans: int, degree: int, nsub: int, overlap: int, core_spans=None,
+                    knots: int = MFA_KNOTS_FLOATING):
     """Host-built layout of one axis (no device needed): returns (rows, owner)
-    with rows[s] = (a, b, w0, w1, k0, k1, l0, nL) per subdomain and owner[g]
-    the Greville owner of control point g; raises MFAError on a rejection."""
-    rows = (ctypes.c_int32 * (8 * max(nsub, 1)))()
-    owner = (ctypes.c_int32 * max(nspans + degree, 1))()
+    with rows[s] = (a, b, w0, w1, k0, k1, l0, nL, oU, nU) per subdomain and
+    owner[g] the Greville owner of control point g; raises MFAError on a
+    rejection."""
+    rows = (ctypes.c_int32 * (10 * max(nsub, 1)))()
+    n = ncp_of(degree, nspans, nsub, knots)
+    owner = (ctypes.c_int32 * max(n, 1))()
     cores = None
     if core_spans is not None:
         cores = (ctypes.c_int32 * len(core_spans))(*[int(c) for c in core_spans])
-    _check(load().mfa_axis_layout(int(npts), int(nspans), int(degree), int(nsub), cores, int(overlap), rows,
-                                  int(nsub), owner), "mfa_axis_layout")
-    return np.array(rows, dtype=np.int64).reshape(nsub, 8), np.array(owner, dtype=np.int64)
+    _check(load().mfa_axis_layout(int(npts), int(nspans), int(degree), int(nsub), cores, int(overlap), int(knots),
+                                  rows, int(nsub), owner), "mfa_axis_layout")
+    return np.array(rows, dtype=np.int64).reshape(nsub, 10), np.array(owner, dtype=np.int64)
 
 
 def mfa_create(device: int = 0, stream: int = 0) -> int:
@@ -239,12 +270,19 @@ def mfa_encode(h: int, layout: mfa_layout, q_ptr: int, q_dtype: int, q_on_device
     return m.value
 
 
-def mfa_schwarz_iterate(h: int, m: int, max_iters: int, tol_dP: float):
+def mfa_schwarz_iterate(h: int, m: int, max_iters: int, tol_dP: float, tol_rms_stall: float = 0.0):
     rep = mfa_report()
     rc = load().mfa_schwarz_iterate(ctypes.c_void_p(h), ctypes.c_void_p(m), int(max_iters), float(tol_dP),
-                                    ctypes.byref(rep))
+                                    float(tol_rms_stall), ctypes.byref(rep))
     _check(rc, "mfa_schwarz_iterate", ok=(MFA_OK, MFA_NOT_CONVERGED))
     return rc, rep
+
+
+def mfa_interface_jumps(h: int, m: int, max_order: int) -> mfa_report:
+    rep = mfa_report()
+    _check(load().mfa_interface_jumps(ctypes.c_void_p(h), ctypes.c_void_p(m), int(max_order), ctypes.byref(rep)),
+           "mfa_interface_jumps")
+    return rep
 
 
 def mfa_encode_plain(h: int, layout: mfa_layout, q_ptr: int, q_dtype: int, q_on_device: bool, max_iters: int,
@@ -334,18 +372,30 @@ def mfa_load(h: int, path: str) -> int:
 
 def saved_layout(path: str) -> mfa_layout:
     """The layout stored in a saved model's header (dimension, degree, grid,
-    spans, subdomains, overlap, precision, box)."""
+    spans, subdomains, overlap, precision, box, knots at the interfaces and
+    NURBS weights)."""
     import struct
     with open(path, "rb") as f:
         head = f.read(192)
         fields = struct.unpack("<8s8i3q12i6d2d2q", head)
-        dim, degree, prec = fields[2], fields[3], fields[4]
+        version, dim, degree, prec = fields[1], fields[2], fields[3], fields[4]
+        knots = fields[8] if version >= 2 else MFA_KNOTS_FLOATING
         npts = fields[9:12]
         nspans, nsub, overlap = fields[12:15], fields[15:18], fields[18:21]
+        wmask = fields[21] if version >= 2 else 0
         lo, hi = fields[22:25], fields[25:28]
         cores = [list(struct.unpack(f"<{nsub[a]}i", f.read(4 * nsub[a]))) for a in range(dim)]
+        weights = None
+        if wmask:
+            weights = []
+            for a in range(dim):
+                if wmask & (1 << a):
+                    n = ncp_of(degree, nspans[a], nsub[a], knots)
+                    weights.append(np.frombuffer(f.read(8 * n), dtype="<f8").copy())
+                else:
+                    weights.append(None)
     return make_layout(dim, degree, list(npts[:dim]), list(nspans[:dim]), list(nsub[:dim]), list(overlap[:dim]), prec,
-                       core_spans=cores, lo=list(lo[:dim]), hi=list(hi[:dim]))
+                       core_spans=cores, lo=list(lo[:dim]), hi=list(hi[:dim]), knots=knots, weights=weights)
 
 
 def mfa_batch_tile_sizes(b: int):
@@ -615,7 +665,7 @@ class Model:
         self.dim = layout.dim
         self.degree = layout.degree
         self.npts = [int(layout.npts[a]) for a in range(self.dim)]
-        self.ncp = [int(layout.nspans[a]) + layout.degree for a in range(self.dim)]
+        self.ncp = [ncp_of(layout.degree, layout.nspans[a], layout.nsub[a], layout.knots) for a in range(self.dim)]
 
     def save(self, path: str, state: bool = False) -> None:
         """Write the model (and with state=True the Schwarz state, to iterate on after a load)."""
@@ -625,8 +675,15 @@ class Model:
         """MFA_UPDATE_AVERAGE or MFA_UPDATE_OWNER; recomputes the current global control points."""
         mfa_set_update_rule(self.handle.h, self.m, rule)
 
-    def iterate(self, max_iters: int, tol_dP: float = 0.0):
-        return mfa_schwarz_iterate(self.handle.h, self.m, max_iters, tol_dP)
+    def iterate(self, max_iters: int, tol_dP: float = 0.0, tol_rms_stall: float = 0.0):
+        """Schwarz iterations until dP_rel <= tol_dP or the decoded RMS stalls
+        (|RMS_k - RMS_{k-1}| <= tol_rms_stall RMS_k); returns (rc, report)."""
+        return mfa_schwarz_iterate(self.handle.h, self.m, max_iters, tol_dP, tol_rms_stall)
+
+    def jumps(self, max_order: int) -> np.ndarray:
+        """Largest interface jump of every derivative order 0..max_order (span units)."""
+        rep = mfa_interface_jumps(self.handle.h, self.m, max_order)
+        return np.array([rep.jump_deriv[r] for r in range(rep.jump_orders)])
 
     def ctrl(self, out=None):
         """Global control points (grid layout, reversed axes); with ``out`` a

@@ -11,17 +11,19 @@ from paper_2210_06528_gb300 import mfa
 TOL_FP64 = 1e-9
 
 
-def layout_for(Q, p, nspans, nsub, delta, precision, cores=None, lo=None, hi=None):
+def layout_for(Q, p, nspans, nsub, delta, precision, cores=None, lo=None, hi=None, knots=mfa.MFA_KNOTS_FLOATING,
+               weights=None):
     npts = list(reversed(Q.shape))
     d = len(npts)
     if np.isscalar(delta):
         delta = [delta] * d
-    return mfa.make_layout(d, p, npts, nspans, nsub, delta, precision, core_spans=cores, lo=lo, hi=hi)
+    return mfa.make_layout(d, p, npts, nspans, nsub, delta, precision, core_spans=cores, lo=lo, hi=hi, knots=knots,
+                           weights=weights)
 
 
-def oracle_problem(Q, p, nspans, nsub, delta, cores=None):
+def oracle_problem(Q, p, nspans, nsub, delta, cores=None, clamped=False, weights=None):
     npts = list(reversed(Q.shape))
-    return O.make_problem(p, npts, list(nspans), list(nsub), delta, cores=cores)
+    return O.make_problem(p, npts, list(nspans), list(nsub), delta, cores=cores, clamped=clamped, weights=weights)
 
 
 def rel_diff(a, b):
@@ -32,18 +34,18 @@ class GpuFit:
     """One model on the GPU; keeps the handle alive."""
 
     def __init__(self, Q, p, nspans, nsub, delta, precision=mfa.MFA_PREC_FP64, cores=None, on_device=True,
-                 lo=None, hi=None):
+                 lo=None, hi=None, knots=mfa.MFA_KNOTS_FLOATING, weights=None):
         import torch
         self.handle = mfa.Handle(0)
-        self.layout = layout_for(Q, p, nspans, nsub, delta, precision, cores, lo, hi)
+        self.layout = layout_for(Q, p, nspans, nsub, delta, precision, cores, lo, hi, knots, weights)
         self.q = torch.from_numpy(np.ascontiguousarray(Q)).cuda() if on_device else np.ascontiguousarray(Q)
         self.model = self.handle.encode(self.q, self.layout)
 
     def ctrl(self):
         return self.model.ctrl()
 
-    def iterate(self, n, tol=0.0):
-        return self.model.iterate(n, tol)
+    def iterate(self, n, tol=0.0, tol_rms_stall=0.0):
+        return self.model.iterate(n, tol, tol_rms_stall)
 
     def residual(self):
         return self.model.residual(self.q)

@@ -25,7 +25,7 @@ def lib_path():
 def test_header_declares_the_boundary():
     names = declared_functions()
     for required in ["mfa_encode", "mfa_schwarz_iterate", "mfa_decode", "mfa_residual", "mfa_create",
-                     "mfa_destroy", "mfa_get_ctrl", "mfa_free", "mfa_sync"]:
+                     "mfa_destroy", "mfa_get_ctrl", "mfa_free", "mfa_sync", "mfa_interface_jumps"]:
         assert required in names
 
 
@@ -58,9 +58,11 @@ def test_layout_struct_matches_header_size(lib_path):
     """ctypes mirrors of mfa_layout / mfa_report have the C sizes."""
     import ctypes
     from paper_2210_06528_gb300 import mfa
-    # dim, degree (8) + npts (24) + nspans, nsub (24) + 3 pointers (24) + overlap (12) + precision (4) + lo, hi (48)
-    assert ctypes.sizeof(mfa.mfa_layout) == 8 + 24 + 24 + 24 + 12 + 4 + 48
-    assert ctypes.sizeof(mfa.mfa_report) == 8 + 5 * 8
+    # dim, degree (8) + npts (24) + nspans, nsub (24) + 3 pointers (24) + overlap (12) + precision (4) + lo, hi
+    # (48) + knots (4, then 4 of padding) + 3 weight pointers (24)
+    assert ctypes.sizeof(mfa.mfa_layout) == 8 + 24 + 24 + 24 + 12 + 4 + 48 + 8 + 24
+    # iters, status (8) + 5 doubles + jump_orders and padding (8) + jump_deriv (8 doubles)
+    assert ctypes.sizeof(mfa.mfa_report) == 8 + 5 * 8 + 8 + 8 * 8
 
 
 def test_no_oracle_import_in_product():

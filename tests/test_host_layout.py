@@ -24,9 +24,10 @@ def mfa():
     return M
 
 
-def oracle_rows(M, nspans, p, cores, delta):
-    pcs = O.axis_pieces(M, nspans, p, cores, delta)
-    return np.array([[pc.a, pc.b, pc.w0, pc.w1, pc.k0, pc.k1, pc.w0, pc.w1 + p - pc.w0] for pc in pcs]), pcs
+def oracle_rows(M, nspans, p, cores, delta, clamped=False):
+    pcs = O.axis_pieces(M, nspans, p, cores, delta, clamped)
+    return np.array([[pc.a, pc.b, pc.w0, pc.w1, pc.k0, pc.k1, pc.L.start, len(pc.L), pc.oU, len(pc.U)]
+                     for pc in pcs]), pcs
 
 
 def column_matching_size(nz):
@@ -47,7 +48,7 @@ def column_matching_size(nz):
     return sum(1 for c in range(cols) if augment(c, [False] * rows))
 
 
-def windows_full_rank(M, nspans, p, pcs):
+def windows_full_rank(M, nspans, p, pcs, t=None):
     """Every window's collocation matrix (its data points x its local control
     points) has full column rank, so its least-squares fit is unique. By the
     Schoenberg-Whitney theorem that holds exactly when every local control
@@ -55,10 +56,11 @@ def windows_full_rank(M, nspans, p, pcs):
     as a maximum bipartite matching over the nonzero entries of the oracle's
     basis matrix (a numerical rank would misjudge the badly conditioned
     windows of about one point per span)."""
-    t = O.clamped_uniform_knots(nspans, p)
+    if t is None:
+        t = O.clamped_uniform_knots(nspans, p)
     u = O.grid_params(M)
     for pc in pcs:
-        N = O.basis_matrix(t, p, u[pc.k0:pc.k1 + 1])[:, pc.w0:pc.w1 + p]
+        N = O.basis_matrix(t, p, u[pc.k0:pc.k1 + 1])[:, pc.L.start:pc.L.stop]
         if column_matching_size(N != 0.0) < N.shape[1]:
             return False
     return True
@@ -115,6 +117,40 @@ def test_random_layouts_match_oracle(mfa):
         accepted += 1
     # the draw covers both outcomes
     assert accepted > 100 and rejected > 20, (accepted, rejected)
+
+
+def test_random_clamped_layouts_match_oracle(mfa):
+    """Clamped interface knots (Sec. 2.2 / Sec. 3.1.1): every interface
+    breakpoint repeated p times; the control-point ranges, owners and
+    rejections agree with the oracle's layout on that knot vector."""
+    rng = np.random.default_rng(17)
+    accepted = rejected = 0
+    for _ in range(300):
+        p = int(rng.integers(1, 6))
+        M = int(rng.integers(2, 300))
+        top = M + 8 if rng.integers(0, 3) == 0 else max(2, M // 2 + 8)
+        nspans = int(rng.integers(1, top))
+        nsub = int(rng.integers(1, max(2, min(6, nspans // p) + 1)))
+        if nsub > 1 and nspans < p * nsub:
+            nsub = 1
+        delta = int(rng.integers(0, 2 * p + 1))
+        cores = random_cores(rng, nspans, nsub, p)
+        want, pcs = oracle_rows(M, nspans, p, cores, delta, clamped=True)
+        prob = O.make_problem(p, [M], [nspans], [nsub], delta, cores=[cores], clamped=True)
+        ok = windows_full_rank(M, nspans, p, pcs, prob.knots(0))
+        try:
+            rows, owner = mfa.mfa_axis_layout(M, nspans, p, nsub, delta, core_spans=cores,
+                                              knots=mfa.MFA_KNOTS_CLAMPED)
+        except mfa.MFAError as e:
+            assert e.code == mfa.MFA_ERR_LAYOUT, (M, nspans, p, cores, delta)
+            assert not ok, (M, nspans, p, cores, delta)
+            rejected += 1
+            continue
+        assert ok, (M, nspans, p, cores, delta)
+        assert np.array_equal(rows, want), (M, nspans, p, cores, delta)
+        assert np.array_equal(owner, O.greville_owner(prob, 0)), (M, nspans, p, cores, delta)
+        accepted += 1
+    assert accepted > 80 and rejected > 10, (accepted, rejected)
 
 
 def test_rejections(mfa):

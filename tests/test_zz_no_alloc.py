@@ -15,7 +15,8 @@ already run every other test.
 import numpy as np
 import pytest
 
-from mfa_cases import GpuFit
+from mfa_cases import GpuFit, oracle_problem
+from oracle import mfa_oracle as O
 from paper_2210_06528_gb300 import inputs, mfa
 
 pytestmark = pytest.mark.gpu
@@ -30,10 +31,13 @@ def _reference(Q, p, nspans, nsub, delta):
     g.iterate(2)
     ref = torch.empty(Q.shape, dtype=torch.float64, device="cuda")
     g.model.decode_grid(ref)  # the allocating entry point
-    P = torch.from_numpy(np.ascontiguousarray(g.ctrl())).cuda()
+    Ph = np.ascontiguousarray(g.ctrl())
+    P = torch.from_numpy(Ph).cuda()
     torch.cuda.synchronize()
     g.close()
-    return ref, P
+    # and the oracle's decode of the same control points
+    oref = O.decode_grid(oracle_problem(Q, p, nspans, nsub, delta), Ph)
+    return ref, P, oref
 
 
 def test_noalloc_decode_matches_decode_on_consecutive_calls():
@@ -45,7 +49,7 @@ def test_noalloc_decode_matches_decode_on_consecutive_calls():
     ]
     stream = torch.cuda.current_stream().cuda_stream
     for Q, p, nspans, nsub, delta in cases:
-        ref, P = _reference(Q, p, nspans, nsub, delta)
+        ref, P, oref = _reference(Q, p, nspans, nsub, delta)
         npts = list(reversed(Q.shape))
         for call in range(2):
             out = torch.full(Q.shape, float("nan"), dtype=torch.float64, device="cuda")
@@ -53,6 +57,8 @@ def test_noalloc_decode_matches_decode_on_consecutive_calls():
             torch.cuda.synchronize()
             err = (out - ref).abs().max().item()
             assert err <= TOL * max(ref.abs().max().item(), 1.0), (Q.shape, call, err)
+            err_o = np.abs(out.cpu().numpy() - oref).max()
+            assert err_o <= TOL * max(np.abs(oref).max(), 1.0), (Q.shape, call, err_o)
 
 
 def test_noalloc_decode_rejects_requests_beyond_its_scratch():
