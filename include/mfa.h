@@ -76,8 +76,26 @@ enum { MFA_F32 = 0, MFA_F64 = 1 };
  *                 FP64.  FP64 input data are carried exactly (as float-float)
  *                 through the projection and the residual.
  *                 Accuracy: decoded RMS within 1 % of the FP64 fit's and
- *                 control points within about 1e-9 relative of it. */
-enum { MFA_PREC_FP64 = 0, MFA_PREC_MIXED = 1 };
+ *                 control points within about 1e-9 relative of it.
+ * MFA_PREC_FP32 : (batches of independent fits and the server) FP32 basis
+ *                 values, FP32 projection N^T Q and FP32 decode / residual,
+ *                 read straight from FP32 data; FP64 Gram matrices and
+ *                 Cholesky factors; banded solves in float-float (about 48
+ *                 bits) with the factors' float-float copies; control points
+ *                 kept as float-float and read back as FP64.  An instance
+ *                 whose a-priori FP32 error bound 2^-24 prod_a
+ *                 sqrt(cond(N_a^T N_a)) exceeds 2e-6 of the data range gets
+ *                 one step of iterative refinement (r = q - N P decoded and
+ *                 projected in FP32 from the FP32 copy of P, solved, added).
+ *                 For fits whose error is far above FP32 rounding of the data
+ *                 (a decoded RMS of at least 100 x 2^-24 x the data range
+ *                 keeps the FP32 error below 1 % of the RMS); FP32 data only,
+ *                 and MFA_ERR_UNSUPPORTED for an instance outside the
+ *                 kernels' staging limits (points along axis 0 <= 1023,
+ *                 control points along axis 0 <= 256, W x points along axis 0
+ *                 <= 8192 with W = 4 for degree <= 3 and 8 above, and for 3-D
+ *                 control points of axes 0 and 1 <= 4096 in product). */
+enum { MFA_PREC_FP64 = 0, MFA_PREC_MIXED = 1, MFA_PREC_FP32 = 2 };
 
 #define MFA_MAX_DIM 3
 #define MFA_MAX_DEGREE 7
@@ -393,8 +411,8 @@ int mfa_decode_grid_noalloc(int32_t dim, int32_t degree, const int64_t* npts, co
  * same convention as a single fit) starts at inst[i].q_offset.  Knots per
  * axis are clamped uniform with nspans spans (nspans + degree control
  * points) and u_k = k/(M-1), as for a single fit.  precision is
- * MFA_PREC_FP64 or MFA_PREC_MIXED (float-float data passes, FP64
- * factorisation).  Host data are staged once (kept for the residual with
+ * MFA_PREC_FP64, MFA_PREC_MIXED (float-float data passes, FP64
+ * factorisation) or MFA_PREC_FP32 (FP32 data passes, FP64 solves).  Host data are staged once (kept for the residual with
  * q == NULL); device data must stay valid until the call returns.
  * Layout errors (Schoenberg-Whitney precheck per instance) return
  * MFA_ERR_LAYOUT with no batch created. */

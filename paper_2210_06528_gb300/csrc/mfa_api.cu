@@ -6,6 +6,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <map>
+#include <tuple>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -466,6 +468,10 @@ namespace {
 
 // Byte sizes of the element type the model computes in.
 inline size_t elem_size(int prec) { return prec == MFA_PREC_FP64 ? sizeof(double) : sizeof(ff); }
+// control points held in FP64 (MFA_PREC_FP64); float-float for
+// MFA_PREC_MIXED and for MFA_PREC_FP32 batches (their banded solves run in
+// float-float on the FP32 pipes: this GPU's FP64 rate is a small fraction)
+inline bool f64_store(int prec) { return prec == MFA_PREC_FP64; }
 
 View make_view(long long off, int n0, int n1, int n2, long long s0, long long s1, long long s2) {
   View v;
@@ -2279,6 +2285,31 @@ struct mfa_batch {
   cudaStream_t cap = nullptr;            // private stream the refit is captured on
   const void* graph_q = nullptr;
   int graph_dtype = -1;
+  // MFA_PREC_FP32: instance descriptors, projection and residual items, the
+  // z-contraction tiles, the xy-reduced planes of 3-D instances, an FP32 copy
+  // of the control points for the residual and the residual item totals
+  void* b32 = nullptr;
+  B32Inst* b32_inst = nullptr;
+  B32Item* b32_pitems = nullptr;  // projection and residual items (instance by instance)
+  int* b32_rfirst = nullptr;      // [2 count]: items of instance i are [rfirst[2 i], rfirst[2 i + 1])
+  int* b32_ztile_inst = nullptr;
+  long long* b32_ztile_base = nullptr;
+  float* b32_R = nullptr;
+  float* b32_Z = nullptr;         // y partial sums at warp boundaries of split 2-D instances
+  float* b32_P32 = nullptr;
+  double* b32_part = nullptr;
+  int n_pitems = 0, n_ztiles = 0;
+  // launches per class (0: 1-D and 2-D instances, 1: 3-D) and degree
+  B32Caps caps[2][MFA_MAX_DEGREE + 1] = {};
+  // iterative refinement of the instances whose FP32 error bound is large:
+  // their projection items and z tiles, and the correction buffer (FP64)
+  B32Item* b32_fitems = nullptr;
+  int* b32_ftile_inst = nullptr;
+  long long* b32_ftile_base = nullptr;
+  ff* b32_dX = nullptr;
+  int n_fitems = 0, n_ftiles = 0, n_refined = 0;
+  int pfirst[2][MFA_MAX_DEGREE + 1] = {}, ffirst[2][MFA_MAX_DEGREE + 1] = {};
+  int item_pts = 131072;  // data points per projection / residual item of a 3-D instance
 };
 
 namespace {
@@ -2593,6 +2624,386 @@ void batch_fit(mfa_batch* b, const void* q, int q_dtype) {
     batch_fit_all<T, float>(b, (const float*)q);
 }
 
+// FP32 data passes: the fused projection of every instance (one launch per
+// class and degree), the z contraction of the 3-D instances, the banded
+// solves of every group, and the FP32 copy of the control points the
+// residual decodes from; then one refinement step for the instances whose
+// FP32 error bound is large.
+void batch_fit32(mfa_batch* b, const float* q) {
+  mfa_handle* h = b->h;
+  ff* X = (ff*)b->buf;
+  TRACED(h, TR_PROJECT_DATA, for (int c = 0; c < 2; ++c) launch_b32(B32_PROJECT, b->b32_inst, b->b32_pitems,
+                                                                     b->pfirst[c], b->caps[c], q, nullptr, X,
+                                                                     b->b32_R, b->b32_Z, nullptr, h->stream));
+  if (b->n_ztiles)
+    TRACED(h, TR_PROJECT_REDUCED,
+           launch_b32_zcontract(b->b32_inst, b->b32_ztile_inst, b->b32_ztile_base, b->n_ztiles, b->b32_R, X,
+                                h->stream));
+  auto solve_all = [&](ff* x) {
+    for (mfa_model* md : b->groups)
+      for (int a = 0; a < md->dim; ++a)
+        TRACED(h, TR_SOLVE_L,
+               launch_band_solve<ff>(md->L, a, false, md->ops + (size_t)(OP_SOLVEL0 + a) * md->nsub, md->nsub,
+                                     md->maxFibL[a], x, h->stream, &md->tm_solve[a]));
+  };
+  solve_all(X);
+  const long long ncp = b->cp_off[b->count];
+  TRACED(h, TR_MISC, (launch_cast<ff, float>(X, b->b32_P32, ncp, h->stream)));
+  if (b->n_fitems) {
+    // one step of iterative refinement for the badly conditioned instances:
+    // project r = q - N P32, solve, add the correction
+    cudaMemsetAsync(b->b32_dX, 0, (size_t)ncp * sizeof(ff), h->stream);
+    TRACED(h, TR_PROJECT_DATA, for (int c = 0; c < 2; ++c) launch_b32(B32_REFINE, b->b32_inst, b->b32_fitems,
+                                                                       b->ffirst[c], b->caps[c], q, b->b32_P32,
+                                                                       b->b32_dX, b->b32_R, b->b32_Z, nullptr,
+                                                                       h->stream));
+    if (b->n_ftiles)
+      TRACED(h, TR_PROJECT_REDUCED,
+             launch_b32_zcontract(b->b32_inst, b->b32_ftile_inst, b->b32_ftile_base, b->n_ftiles, b->b32_R,
+                                  b->b32_dX, h->stream));
+    solve_all(b->b32_dX);
+    TRACED(h, TR_MISC, launch_b32_add(X, b->b32_dX, ncp, h->stream));
+    TRACED(h, TR_MISC, (launch_cast<ff, float>(X, b->b32_P32, ncp, h->stream)));
+  }
+}
+
+void batch_fit_any(mfa_batch* b, const void* q, int q_dtype) {
+  if (b->prec == MFA_PREC_FP32)
+    batch_fit32(b, (const float*)q);
+  else if (b->prec == MFA_PREC_FP64)
+    batch_fit<double>(b, q, q_dtype);
+  else
+    batch_fit<ff>(b, q, q_dtype);
+}
+
+// Limits of the FP32 data-pass kernels for one instance: a row (padded to
+// an odd pitch) fits one warp's staging buffer, the x basis values fit the
+// CTA's table, the open y control points of a streamed plane fit eight
+// column groups, and a 3-D instance's z-expanded control-point plane fits a
+// warp's buffer.
+bool b32_supported(const mfa_instance& in) {
+  const int p = in.degree;
+  const long long M0 = in.npts[0], n0 = (long long)in.nspans[0] + p;
+  const int W = p < 4 ? 4 : 8;  // basis values per point in shared memory
+  if ((M0 | 1) > kB32Stage || n0 > kB32Threads || W * M0 > 8192) return false;
+  if (in.dim == 3) {
+    const long long n1 = (long long)in.nspans[1] + p, n2 = (long long)in.nspans[2] + p;
+    if (n0 * n1 > 4096 || n0 * n1 * n2 * std::max(n0, n1) >= (1LL << 32)) return false;
+  }
+  return true;
+}
+
+// Condition number of the normal matrix N^T N of one axis (M points
+// u_k = k/(M-1), clamped uniform knots of nspans spans, degree p): the basis
+// by the Cox-de Boor recurrence, the banded Gram matrix, its largest
+// eigenvalue by power iteration and its smallest by inverse iteration
+// (banded Cholesky solves).  An estimate, for choosing where the FP32 data
+// passes need a refinement step.
+double host_gram_cond(long long M, int ns, int p) {
+  const int n = ns + p, w = p + 1;
+  std::vector<double> A((size_t)n * w, 0.0);
+  auto knot = [&](int i) { return (double)std::min(std::max(i - p, 0), ns) / ns; };
+  double N[MFA_MAX_DEGREE + 1];
+  for (long long k = 0; k < M; ++k) {
+    const double u = M > 1 ? (double)k / (double)(M - 1) : 0.0;
+    int j = M > 1 ? (int)((k * ns) / (M - 1)) : 0;
+    j = std::min(j, ns - 1);
+    const int i = j + p;
+    N[0] = 1.0;
+    for (int q = 1; q <= p; ++q) {
+      double carry = 0.0;
+      for (int r = 0; r < q; ++r) {
+        const double tl = knot(i - q + r + 1), tr = knot(i + r + 1);
+        const double wgt = N[r] / (tr - tl);
+        const double right = (tr - u) * wgt, left = (u - tl) * wgt;
+        N[r] = carry + right;
+        carry = left;
+      }
+      N[q] = carry;
+    }
+    for (int r = 0; r <= p; ++r)
+      for (int e = 0; r + e <= p; ++e) A[(size_t)(j + r) * w + e] += N[r] * N[r + e];
+  }
+  auto matvec = [&](const std::vector<double>& x, std::vector<double>& y) {
+    std::fill(y.begin(), y.end(), 0.0);
+    for (int r = 0; r < n; ++r)
+      for (int e = 0; e <= p && r + e < n; ++e) {
+        const double a = A[(size_t)r * w + e];
+        y[r] += a * x[r + e];
+        if (e) y[r + e] += a * x[r];
+      }
+  };
+  // banded Cholesky A = L L^T, L(i, i-e) at F[i*w+e]
+  std::vector<double> F((size_t)n * w, 0.0);
+  for (int i = 0; i < n; ++i) {
+    for (int e = p; e >= 1; --e) {
+      const int j = i - e;
+      if (j < 0) continue;
+      double sacc = A[(size_t)j * w + e];
+      for (int f = e + 1; f <= p; ++f)
+        if (i - f >= 0) sacc -= F[(size_t)i * w + f] * F[(size_t)j * w + (f - e)];
+      F[(size_t)i * w + e] = sacc / F[(size_t)j * w];
+    }
+    double d = A[(size_t)i * w];
+    for (int e = 1; e <= p; ++e)
+      if (i - e >= 0) d -= F[(size_t)i * w + e] * F[(size_t)i * w + e];
+    if (!(d > 0.0)) return 1e300;
+    F[(size_t)i * w] = std::sqrt(d);
+  }
+  auto solve = [&](std::vector<double>& x) {
+    for (int i = 0; i < n; ++i) {
+      double v = x[i];
+      for (int e = 1; e <= p && i - e >= 0; ++e) v -= F[(size_t)i * w + e] * x[i - e];
+      x[i] = v / F[(size_t)i * w];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double v = x[i];
+      for (int e = 1; e <= p && i + e < n; ++e) v -= F[(size_t)(i + e) * w + e] * x[i + e];
+      x[i] = v / F[(size_t)i * w];
+    }
+  };
+  std::vector<double> x(n), y(n);
+  auto normalise = [&](std::vector<double>& v) {
+    double s2 = 0.0;
+    for (double t : v) s2 += t * t;
+    const double s = std::sqrt(s2);
+    for (double& t : v) t /= s;
+    return s;
+  };
+  for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.37 * ((i * 7919) % 13);
+  normalise(x);
+  double lmax = 0.0;
+  for (int it = 0; it < 60; ++it) {
+    matvec(x, y);
+    lmax = normalise(y);
+    x.swap(y);
+  }
+  for (int i = 0; i < n; ++i) x[i] = ((i * 7919) % 13) - 6.0 + 0.5;
+  normalise(x);
+  double inv = 0.0;
+  for (int it = 0; it < 60; ++it) {
+    solve(x);
+    inv = normalise(x);
+  }
+  return lmax * inv;
+}
+
+// Device tables of the FP32 data passes: descriptors with each instance's
+// chunk geometry, CTA items (3-D: ranges of planes of about item_pts points,
+// split between eight warps; 2-D: the whole instance, split between warps by
+// y knot spans; 1-D: the whole instance), each instance's item range, the
+// launch capacities per class and degree, z-contraction tiles, and the
+// subset of items and tiles that the refinement step reprojects.
+int build_b32(mfa_batch* b) {
+  mfa_handle* h = b->h;
+  const int count = b->count;
+  std::vector<B32Inst> D(count);
+  long long rsize = 0;
+  for (mfa_model* md : b->groups)
+    for (int t = 0; t < md->nsub; ++t) {
+      const int i = md->hmem[t];
+      const mfa_instance& in = b->inst[i];
+      B32Inst& d = D[i];
+      d.dim = in.dim;
+      d.p = in.degree;
+      for (int a = 0; a < 3; ++a) {
+        const bool act = a < in.dim;
+        d.M[a] = act ? (int)in.npts[a] : 1;
+        d.n[a] = act ? in.nspans[a] + in.degree : 1;
+        d.kbase[a] = act ? md->axh[a].subs[t].k0 : 0;
+        d.cbase[a] = act ? md->axh[a].subs[t].l0 : 0;
+        d.span[a] = act ? md->L.ax[a].span : nullptr;
+        d.vals[a] = act ? md->L.ax[a].vals_f : nullptr;
+        d.sstart[a] = act ? md->L.ax[a].span_start : nullptr;
+      }
+      d.q_off = in.q_offset;
+      d.x_off = b->cp_off[i];
+      d.r_off = 0;
+    }
+  for (int i = 0; i < count; ++i)
+    if (D[i].dim == 3) {
+      D[i].r_off = rsize;
+      rsize += (long long)D[i].M[2] * D[i].n[1] * D[i].n[0];
+    }
+  // chunk geometry of every instance and the launch capacities
+  auto cls_of = [&](int i) { return D[i].dim == 3 ? 1 : 0; };
+  B32Caps caps[2][MFA_MAX_DEGREE + 1];
+  std::memset(caps, 0, sizeof(caps));
+  for (int i = 0; i < count; ++i) {
+    B32Inst& d = D[i];
+    const int p = d.p, M0 = d.M[0], M1 = d.M[1], M2 = d.M[2], n0 = d.n[0], n1 = d.n[1];
+    const int pitch = M0 | 1, n0s = n0 | 1, W = p < 4 ? 4 : 8;
+    const int ns0 = n0 - p, ns1 = n1 - (d.dim >= 2 ? p : 0);
+    int rows;
+    if (d.dim == 1) {
+      d.mode = 0;
+      d.np = 1;
+      rows = 1;
+    } else if (M1 * pitch <= kB32Stage) {
+      d.mode = 0;
+      d.np = d.dim == 3 ? std::max(1, std::min(kB32Stage / (M1 * pitch), M2)) : 1;
+      rows = d.np * M1;
+    } else {
+      d.mode = 1;
+      d.np = 1;
+      rows = std::min(kB32Stage / pitch, M1);
+    }
+    d.R = rows;
+    // x segments: one lane per (pair of rows, segment) while row pairs alone
+    // leave lanes idle
+    const int pairs = (rows + 1) / 2;
+    d.S = pairs >= 32 ? 1 : std::min(std::max(1, ns0 / p), std::max(1, 32 / pairs));
+    B32Caps& c = caps[cls_of(i)][p];
+    c.vb = std::max(c.vb, M0 * W);
+    c.sx = std::max(c.sx, ns0 + 1);
+    c.sy = std::max(c.sy, ns1 + 1);
+    c.vy = std::max(c.vy, M1 * W);
+    c.ysp = std::max(c.ysp, M1);
+    c.stage = std::max(c.stage, rows * pitch);
+    c.xr = std::max(c.xr, rows * n0s);
+    if (d.mode == 1 && n0 > 32) c.ring = std::max(c.ring, (p + 1) * ((n0 + 31) / 32) * 32);
+    if (d.dim == 3) c.dz = std::max(c.dz, d.np * n1 * n0);
+  }
+  for (int k = 0; k < 2; ++k)
+    for (int p = 1; p <= MFA_MAX_DEGREE; ++p)
+      for (int mode : {B32_PROJECT, B32_REFINE, B32_RESIDUAL})
+        if (b32_smem_bytes(caps[k][p], mode) > 220 * 1024) return MFA_ERR_UNSUPPORTED;
+  // items by class and degree (one launch each), largest instances first,
+  // the items of an instance contiguous
+  std::vector<int> ord(count);
+  for (int i = 0; i < count; ++i) ord[i] = i;
+  std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) {
+    if (cls_of(x) != cls_of(y)) return cls_of(x) < cls_of(y);
+    if (D[x].p != D[y].p) return D[x].p < D[y].p;
+    return b->q_len[x] > b->q_len[y];
+  });
+  const long long ipts = std::max(b->item_pts, 4096);
+  std::vector<B32Item> pit;
+  std::vector<int> rrange(2 * (size_t)count, 0);
+  long long zsize = 0;
+  for (int i : ord) {
+    const B32Inst& d = D[i];
+    rrange[2 * i] = (int)pit.size();
+    if (d.dim == 3) {
+      const long long plane = (long long)d.M[0] * d.M[1];
+      const int unit = 8 * d.np;  // whole chunks for every warp
+      int ppi = (int)std::min<long long>(d.M[2], ((ipts / plane + unit - 1) / unit) * unit);
+      ppi = std::max(ppi, std::min(unit, d.M[2]));
+      for (int k2 = 0; k2 < d.M[2]; k2 += ppi) {
+        const int k2e = std::min(k2 + ppi, d.M[2]);
+        pit.push_back(B32Item{i, k2 * d.M[1], k2e * d.M[1], std::min(8, k2e - k2), 0});
+      }
+    } else if (d.dim == 2) {
+      const int ns1 = d.n[1] - d.p;
+      const int nw = d.mode == 1 ? std::max(1, std::min(8, ns1 / d.p)) : 1;
+      pit.push_back(B32Item{i, 0, d.M[1], nw, nw > 1 ? zsize : 0});
+      if (nw > 1) zsize += 2LL * nw * d.p * d.n[0];
+    } else {
+      pit.push_back(B32Item{i, 0, 1, 1, 0});
+    }
+    rrange[2 * i + 1] = (int)pit.size();
+  }
+  // first[k][q]: items of class k and degree <= q end there (absolute)
+  auto firsts = [&](const std::vector<B32Item>& v, int first[2][MFA_MAX_DEGREE + 1]) {
+    int cnt[2][MFA_MAX_DEGREE + 1] = {};
+    for (const B32Item& x : v) cnt[cls_of(x.inst)][D[x.inst].p]++;
+    int acc = 0;
+    for (int k = 0; k < 2; ++k)
+      for (int q = 0; q <= MFA_MAX_DEGREE; ++q) {
+        acc += cnt[k][q];
+        first[k][q] = acc;
+      }
+  };
+  firsts(pit, b->pfirst);
+  std::vector<int> zti;
+  std::vector<long long> ztb;
+  for (int i = 0; i < count; ++i)
+    if (D[i].dim == 3) {
+      const long long n = (long long)D[i].n[0] * D[i].n[1] * D[i].n[2];
+      for (long long e = 0; e < n; e += 256) {
+        zti.push_back(i);
+        ztb.push_back(e);
+      }
+    }
+  // a refinement step where the FP32 error bound 2^-24 prod_a sqrt(cond(N_a^T N_a))
+  // of the decoded values, relative to the data, exceeds 2e-6 (observed errors
+  // stay below ~1.1x this bound; after one step they fall below 1e-6)
+  std::map<std::tuple<long long, int, int>, double> conds;
+  std::vector<char> refine(count, 0);
+  for (int i = 0; i < count; ++i) {
+    const mfa_instance& in = b->inst[i];
+    double g = std::ldexp(1.0, -24);
+    for (int a = 0; a < in.dim; ++a) {
+      const auto key = std::make_tuple((long long)in.npts[a], in.nspans[a], in.degree);
+      auto itc = conds.find(key);
+      if (itc == conds.end()) itc = conds.emplace(key, host_gram_cond(in.npts[a], in.nspans[a], in.degree)).first;
+      g *= std::sqrt(itc->second);
+    }
+    refine[i] = g > 2e-6;
+  }
+  std::vector<B32Item> fit;
+  for (const B32Item& x : pit)
+    if (refine[x.inst]) fit.push_back(x);
+  firsts(fit, b->ffirst);
+  std::vector<int> fti;
+  std::vector<long long> ftb;
+  for (size_t k = 0; k < zti.size(); ++k)
+    if (refine[zti[k]]) {
+      fti.push_back(zti[k]);
+      ftb.push_back(ztb[k]);
+    }
+  int nref = 0;
+  for (int i = 0; i < count; ++i) nref += refine[i];
+  std::memcpy(b->caps, caps, sizeof(caps));
+  Arena ar;
+  const size_t o_inst = ar.take<B32Inst>(count), o_pit = ar.take<B32Item>(pit.size()),
+               o_rf = ar.take<int>(2 * (size_t)count), o_zi = ar.take<int>(zti.size()),
+               o_zb = ar.take<long long>(ztb.size()), o_fit = ar.take<B32Item>(fit.size()),
+               o_fti = ar.take<int>(fti.size()), o_ftb = ar.take<long long>(ftb.size());
+  const size_t host_bytes = ar.used;
+  const size_t o_R = ar.take<float>(rsize), o_Z = ar.take<float>(zsize), o_P = ar.take<float>(b->cp_off[count]),
+               o_part = ar.take<double>(2 * pit.size()), o_dX = ar.take<ff>(nref ? b->cp_off[count] : 0);
+  void* mem = nullptr;
+  int rc = pool_alloc(h, &mem, ar.used);
+  if (rc != MFA_OK) return rc;
+  std::vector<char> img(host_bytes);
+  std::memcpy(img.data() + o_inst, D.data(), sizeof(B32Inst) * D.size());
+  std::memcpy(img.data() + o_pit, pit.data(), sizeof(B32Item) * pit.size());
+  std::memcpy(img.data() + o_rf, rrange.data(), sizeof(int) * rrange.size());
+  std::memcpy(img.data() + o_zi, zti.data(), sizeof(int) * zti.size());
+  std::memcpy(img.data() + o_zb, ztb.data(), sizeof(long long) * ztb.size());
+  std::memcpy(img.data() + o_fit, fit.data(), sizeof(B32Item) * fit.size());
+  std::memcpy(img.data() + o_fti, fti.data(), sizeof(int) * fti.size());
+  std::memcpy(img.data() + o_ftb, ftb.data(), sizeof(long long) * ftb.size());
+  cudaError_t e = cudaMemcpyAsync(mem, img.data(), host_bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // the image is a local vector
+  if (e != cudaSuccess) {
+    pool_free(h, mem);
+    return cuda_status(e);
+  }
+  pool_free(h, b->b32);  // stream-ordered: after the launches that used the old tables
+  b->b32 = mem;
+  b->b32_inst = at_off<B32Inst>(mem, o_inst);
+  b->b32_pitems = at_off<B32Item>(mem, o_pit);
+  b->b32_rfirst = at_off<int>(mem, o_rf);
+  b->b32_ztile_inst = at_off<int>(mem, o_zi);
+  b->b32_ztile_base = at_off<long long>(mem, o_zb);
+  b->b32_R = at_off<float>(mem, o_R);
+  b->b32_Z = at_off<float>(mem, o_Z);
+  b->b32_P32 = at_off<float>(mem, o_P);
+  b->b32_part = at_off<double>(mem, o_part);
+  b->b32_fitems = at_off<B32Item>(mem, o_fit);
+  b->b32_ftile_inst = at_off<int>(mem, o_fti);
+  b->b32_ftile_base = at_off<long long>(mem, o_ftb);
+  b->b32_dX = nref ? at_off<ff>(mem, o_dX) : nullptr;
+  b->n_pitems = (int)pit.size();
+  b->n_ztiles = (int)zti.size();
+  b->n_fitems = (int)fit.size();
+  b->n_ftiles = (int)fti.size();
+  b->n_refined = nref;
+  return MFA_OK;
+}
+
 // Grid decode of every group into out (instance layout of the data).
 template <typename T, typename TOut>
 int batch_decode_into(mfa_batch* b, TOut* out) {
@@ -2624,7 +3035,7 @@ int batch_decode_into(mfa_batch* b, TOut* out) {
 
 template <typename TOut>
 int batch_decode_any(mfa_batch* b, TOut* out) {
-  return b->prec == MFA_PREC_FP64 ? batch_decode_into<double, TOut>(b, out) : batch_decode_into<ff, TOut>(b, out);
+  return f64_store(b->prec) ? batch_decode_into<double, TOut>(b, out) : batch_decode_into<ff, TOut>(b, out);
 }
 
 }  // namespace
@@ -2654,10 +3065,7 @@ int batch_autotune(mfa_batch* b, const void* q, int q_dtype) {
       float ms = 0.f;
       for (int rep = 0; rep < 2; ++rep) {
         cudaEventRecord(e0, h->stream);
-        if (b->prec == MFA_PREC_FP64)
-          batch_fit<double>(b, q, q_dtype);
-        else
-          batch_fit<ff>(b, q, q_dtype);
+        batch_fit_any(b, q, q_dtype);
         cudaEventRecord(e1, h->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) rc = MFA_ERR_CUDA;
         cudaEventElapsedTime(&ms, e0, e1);
@@ -2695,7 +3103,14 @@ int mfa_encode_batch(mfa_handle* h, int32_t count, const mfa_instance* inst, con
   if (!h || count < 1 || !inst || !q || !out) return MFA_ERR_ARG;
   *out = nullptr;
   if (q_dtype != MFA_F32 && q_dtype != MFA_F64) return MFA_ERR_ARG;
-  if (precision != MFA_PREC_FP64 && precision != MFA_PREC_MIXED) return MFA_ERR_ARG;
+  if (precision != MFA_PREC_FP64 && precision != MFA_PREC_MIXED && precision != MFA_PREC_FP32) return MFA_ERR_ARG;
+  if (precision == MFA_PREC_FP32) {
+    // FP32 data passes read FP32 data, within the kernels' staging limits
+    if (q_dtype != MFA_F32) return MFA_ERR_UNSUPPORTED;
+    for (int i = 0; i < count; ++i)
+      if (inst[i].dim >= 1 && inst[i].dim <= MFA_MAX_DIM && inst[i].degree >= 1 && !b32_supported(inst[i]))
+        return MFA_ERR_UNSUPPORTED;
+  }
   DeviceGuard g(h->device);
   mfa_batch* b = new (std::nothrow) mfa_batch();
   if (!b) return MFA_ERR_OOM;
@@ -2786,10 +3201,14 @@ int mfa_encode_batch(mfa_handle* h, int32_t count, const mfa_instance* inst, con
     qd = b->staged;
     b->staged_dtype = q_dtype;
   }
-  if (precision == MFA_PREC_FP64)
-    batch_fit<double>(b, qd, q_dtype);
-  else
-    batch_fit<ff>(b, qd, q_dtype);
+  if (precision == MFA_PREC_FP32) {
+    rc = build_b32(b);
+    if (rc != MFA_OK) {
+      mfa_batch_free(b);
+      return rc;
+    }
+  }
+  batch_fit_any(b, qd, q_dtype);
   cudaError_t e = cudaStreamSynchronize(h->stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -2837,10 +3256,7 @@ int mfa_batch_refit(mfa_handle* h, mfa_batch* b, const void* q, int q_dtype) {
     cudaGraph_t gr = nullptr;
     e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      if (b->prec == MFA_PREC_FP64)
-        batch_fit<double>(b, q, q_dtype);
-      else
-        batch_fit<ff>(b, q, q_dtype);
+      batch_fit_any(b, q, q_dtype);
       const cudaError_t e2 = cudaStreamEndCapture(b->cap, &gr);
       e = cudaGetLastError();
       if (e == cudaSuccess) e = e2;
@@ -2880,7 +3296,7 @@ int mfa_batch_get_ctrl(mfa_handle* h, const mfa_batch* b, double* host_out, int6
   DeviceGuard g(h->device);
   int rc = ensure_ws(h, (size_t)n * sizeof(double));
   if (rc != MFA_OK) return rc;
-  if (b->prec == MFA_PREC_FP64)
+  if (f64_store(b->prec))
     TRACED(h, TR_MISC, (launch_cast<double, double>((const double*)b->buf, (double*)h->ws, n, h->stream)));
   else
     TRACED(h, TR_MISC, (launch_cast<ff, double>((const ff*)b->buf, (double*)h->ws, n, h->stream)));
@@ -2948,8 +3364,15 @@ int mfa_batch_residual(mfa_handle* h, const mfa_batch* bc, const void* q, int q_
     if (rc == MFA_OK) e = cudaMemcpyAsync(qtmp, q, qb, cudaMemcpyHostToDevice, h->stream);
     q = qtmp;
   }
+  if (rc == MFA_OK && e == cudaSuccess && b->prec == MFA_PREC_FP32 && q_dtype != MFA_F32) rc = MFA_ERR_UNSUPPORTED;
   if (rc == MFA_OK && e == cudaSuccess) {
-    if (b->prec == MFA_PREC_FP64)
+    if (b->prec == MFA_PREC_FP32) {
+      TRACED(h, TR_RESIDUAL, for (int c = 0; c < 2; ++c) launch_b32(B32_RESIDUAL, b->b32_inst, b->b32_pitems,
+                                                                     b->pfirst[c], b->caps[c], (const float*)q,
+                                                                     b->b32_P32, nullptr, nullptr, nullptr,
+                                                                     b->b32_part, h->stream));
+      TRACED(h, TR_REDUCE, launch_b32_reduce(b->b32_rfirst, b->count, b->b32_part, (double*)res, h->stream));
+    } else if (b->prec == MFA_PREC_FP64)
       rc = q_dtype == MFA_F64 ? batch_residual_into<double, double>(b, (const double*)q, (double*)res)
                               : batch_residual_into<double, float>(b, (const float*)q, (double*)res);
     else
@@ -3008,6 +3431,7 @@ int mfa_batch_free(mfa_batch* b) {
   pool_free(h, b->tab);
   pool_free(h, b->desc);
   pool_free(h, b->staged);
+  pool_free(h, b->b32);
   delete b;
   return MFA_OK;
 }
@@ -3059,7 +3483,7 @@ int batch_decode_points_impl(mfa_handle* h, const mfa_batch* b, int32_t nq, cons
     int p_uniform = b->inst.empty() ? 0 : b->inst[0].degree;
     for (const mfa_instance& in : b->inst)
       if (in.degree != p_uniform) p_uniform = 0;
-    if (b->prec == MFA_PREC_FP64)
+    if (f64_store(b->prec))
       TRACED(h, TR_DECODE_POINTS, (launch_decode_points_inst<double>((const InstDesc*)b->desc, dq, doff, nq, npts, dp,
                                                                      (const double*)b->buf, dout, p_uniform,
                                                                      h->stream)));
@@ -3084,7 +3508,7 @@ int batch_instance_ctrl(mfa_handle* h, const mfa_batch* b, int index, double* ho
   DeviceGuard g(h->device);
   int rc = ensure_ws(h, (size_t)n * sizeof(double));
   if (rc != MFA_OK) return rc;
-  if (b->prec == MFA_PREC_FP64)
+  if (f64_store(b->prec))
     launch_cast<double, double>((const double*)b->buf + b->cp_off[index], (double*)h->ws, n, h->stream);
   else
     launch_cast<ff, double>((const ff*)b->buf + b->cp_off[index], (double*)h->ws, n, h->stream);

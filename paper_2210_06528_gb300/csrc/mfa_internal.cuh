@@ -242,6 +242,56 @@ int batch_decode_points_impl(mfa_handle* h, const mfa_batch* b, int32_t nq, cons
 int batch_instance_ctrl(mfa_handle* h, const mfa_batch* b, int index, double* host_out, int64_t cap);
 long long batch_instance_num_ctrl(const mfa_batch* b, int index);
 
+// FP32 data passes of a batch of independent fits (MFA_PREC_FP32): one
+// descriptor per instance, pointing into its group's virtual-axis tables.
+struct B32Inst {
+  int dim, p;
+  int M[3], n[3];          // points and control points per axis (1 beyond dim)
+  int kbase[3], cbase[3];  // the instance's first point / control point on the group's axes
+  long long q_off;         // first data value
+  long long x_off;         // first control point in the batch buffer (float-float)
+  long long r_off;         // 3-D: first value of its xy-reduced planes (M2 x n1 x n0 floats)
+  const int* span[3];      // group tables: first control point of every point
+  const float* vals[3];    // FP32 basis values, (p_a + 1) per point
+  const int* sstart[3];    // first point of every span number
+  int mode;                // 0: a warp stages whole planes (np at a time); 1: up to R rows of one plane
+  int np, R;
+  int S;                   // x segments per row (at least p knot spans each when S > 1)
+};
+// One CTA's work: rows [r0, r1) (row = k1 + M1 k2) of one instance, shared by
+// nw warps (3-D: by planes; 2-D: by y knot spans, partial sums of the y
+// control points at the warps' boundaries in Z from z_off on).
+struct B32Item {
+  int inst;
+  int r0, r1;
+  int nw;
+  long long z_off;
+};
+// Shared-memory capacities (elements) of one launch, the maxima over its
+// instances: per CTA the x basis values (W per point), the x and y span
+// starts, the y basis values (W per row) and the y span of every row; per
+// warp the staged rows, the x-reduced rows, the y accumulators of a streamed
+// plane and the z-expanded control points.
+struct B32Caps {
+  int vb, sx, sy, vy, ysp;
+  int stage, xr, ring, dz;
+};
+constexpr int kB32Threads = 256;
+constexpr int kB32Stage = 1024;  // data values a warp stages per chunk (rows padded to odd pitch)
+enum { B32_PROJECT = 0, B32_REFINE = 1, B32_RESIDUAL = 2 };
+size_t b32_smem_bytes(const B32Caps& cap, int mode);
+// One launch per degree present: items[first[p - 1] .. first[p]) have degree
+// p (first has MFA_MAX_DEGREE + 1 entries), with capacities caps[p].
+//  B32_PROJECT: N^T q into X (2-D, 1-D) or R (3-D, xy-reduced planes);
+//  B32_REFINE: the same for r = q - N P32 (dX in X);
+//  B32_RESIDUAL: per item sum of E^2 and max |E|, E = q - N P32, in part.
+void launch_b32(int mode, const B32Inst* insts, const B32Item* items, const int* first, const B32Caps* caps,
+                const float* Q, const float* P32, ff* X, float* R, float* Z, double* part, cudaStream_t st);
+void launch_b32_add(ff* X, const ff* dX, long long n, cudaStream_t st);
+void launch_b32_zcontract(const B32Inst* insts, const int* tile_inst, const long long* tile_base, int ntiles,
+                          const float* R, ff* X, cudaStream_t st);
+void launch_b32_reduce(const int* range, int count, const double* part, double* out, cudaStream_t st);
+
 // One instance of a batch of independent fits, for scattered decode.
 struct InstDesc {
   int dim, p;

@@ -387,7 +387,7 @@ int mfa_server_create(int device, int32_t workers, int64_t mem_budget, int32_t m
 
 int64_t mfa_server_encode(mfa_server* s, const mfa_instance* inst, const void* host_q, int precision) {
   if (!s || !inst || !host_q) return MFA_ERR_ARG;
-  if (precision != MFA_PREC_FP64 && precision != MFA_PREC_MIXED) return MFA_ERR_ARG;
+  if (precision != MFA_PREC_FP64 && precision != MFA_PREC_MIXED && precision != MFA_PREC_FP32) return MFA_ERR_ARG;
   if (inst->dim < 1 || inst->dim > MFA_MAX_DIM || inst->degree < 1 || inst->degree > MFA_MAX_DEGREE) return MFA_ERR_ARG;
   auto r = std::make_unique<Req>();
   r->kind = 0;

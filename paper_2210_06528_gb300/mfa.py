@@ -31,7 +31,7 @@ MFA_ERR_TIMEOUT = -9
 MFA_ERR_IO = -10
 MFA_SAVE_STATE = 1
 MFA_F32, MFA_F64 = 0, 1
-MFA_PREC_FP64, MFA_PREC_MIXED = 0, 1
+MFA_PREC_FP64, MFA_PREC_MIXED, MFA_PREC_FP32 = 0, 1, 2
 MFA_KNOTS_FLOATING, MFA_KNOTS_CLAMPED = 0, 1
 MFA_MAX_DEGREE = 7
 MFA_UPDATE_AVERAGE, MFA_UPDATE_OWNER = 0, 1
