@@ -46,9 +46,10 @@ WORKLOADS = {
     "3d384": dict(name="3d_384^3_gauss16_p3_6x6x6sub_24spans_overlap2_mixed", npts=(384, 384, 384), p=3,
                   nspans=(144, 144, 144), nsub=(6, 6, 6), delta=2, precision="mixed", tol=1e-7, max_iters=50,
                   sample=dict(npts=(128, 128, 128), nspans=(48, 48, 48), nsub=(2, 2, 2))),
-    # 2-D workload: 1024^2 sinc(x) sinc(y) + N(0, 1e-3), p = 3, 4x4 subdomains of 64 core spans.
+    # 2-D workload: 1024^2 sinc(x) sinc(y) + N(0, 1e-3), p = 3, 4x4 subdomains of 64 core spans,
+    # Schwarz to decoded-residual stall |RMS_k - RMS_{k-1}| <= 1e-6 RMS_k.
     "2d": dict(name="2d_1024^2_sinc_noise1e-3_p3_4x4sub_64spans_overlap2_mixed", npts=(1024, 1024), p=3,
-               nspans=(256, 256), nsub=(4, 4), delta=2, precision="mixed", tol=1e-6, max_iters=50,
+               nspans=(256, 256), nsub=(4, 4), delta=2, precision="mixed", tol=0.0, stall=1e-6, max_iters=50,
                sample=dict(npts=(512, 512), nspans=(128, 128), nsub=(2, 2))),
     # 1-D workload: 1024 points of sin(x)/x, p = 3, 4 subdomains of 32 core spans, FP64.
     "1d": dict(name="1d_1024_sinc_p3_4sub_32spans_overlap2_fp64", npts=(1024,), p=3, nspans=(128,), nsub=(4,),
@@ -95,7 +96,7 @@ class ClockSampler:
             os.close(fd)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                          "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -137,17 +138,23 @@ def oracle_sample_step(wl):
     Q = make_data(wl, smp["npts"]).astype(np.float64)
     prob = O.make_problem(wl["p"], list(smp["npts"]), list(smp["nspans"]), list(smp["nsub"]), wl["delta"])
     t0 = time.perf_counter()
-    res = O.schwarz_solve(prob, Q, max_iters=wl["max_iters"], tol_dP=wl["tol"])
+    res = O.schwarz_solve(prob, Q, max_iters=wl["max_iters"], tol_dP=wl["tol"], tol_rms_stall=wl.get("stall", 0.0))
     O.residual_stats(prob, Q, res["P"])
     dt = time.perf_counter() - t0
     return int(np.prod(smp["npts"])), dt
+
+
+def stop_desc(wl):
+    if wl.get("stall"):
+        return f"|RMS_k - RMS_(k-1)| <= {wl['stall']:g} RMS_k"
+    return f"dP_rel <= {wl['tol']:g}"
 
 
 def sample_desc(wl):
     smp = wl["sample"]
     return (f"{'x'.join(map(str, smp['npts']))} grid, {'x'.join(map(str, smp['nsub']))} subdomains with the "
             f"workload's per-subdomain shape (p={wl['p']}, overlap {wl['delta']}, same points per span), "
-            f"oracle Schwarz to dP_rel <= {wl['tol']:g} + residual, FP64 numpy")
+            f"oracle Schwarz to {stop_desc(wl)} + residual, FP64 numpy")
 
 
 def host_cores():
@@ -249,9 +256,14 @@ def projection_ops(wl):
     return W * (FF_OPS_F * sm[0] * sm[1] * sm[2] + FF_OPS_V * sn[0] * sm[1] * sm[2] + FF_OPS_V * sn[0] * sn[1] * sm[2])
 
 
-def alu_peak_tops(clock_mhz):
-    """FP32 lane instructions per second: 152 SMs x 128 FP32 lanes x SM clock."""
-    return 152 * 128 * clock_mhz * 1e6 / 1e12
+def sm_count(device=0):
+    import torch
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
+
+
+def alu_peak_tops(clock_mhz, sms):
+    """FP32 lane instructions per second: SMs x 128 FP32 lanes x SM clock."""
+    return sms * 128 * clock_mhz * 1e6 / 1e12
 
 
 def algorithmic_bytes(cls_name, wl, qbytes, model_info):
@@ -262,15 +274,16 @@ def algorithmic_bytes(cls_name, wl, qbytes, model_info):
     return None
 
 
-def bench_batch(h, torch, mfa, stream, steps, count=4096, seed=0):
+def bench_batch(h, torch, mfa, stream, steps, precision, count=4096, seed=0, decode=True):
     """Batch of independent fits: one full encode (host layout, setup, fit),
     then timed refits of the captured CUDA graph on device data and one
-    per-instance residual."""
+    per-instance residual; with the data-pass kernels timed on their own
+    (one traced encode) against the HBM peak."""
     specs, data = inputs.batch_instances(count, seed=seed)
     q = torch.from_numpy(data).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    b = h.encode_batch(specs, q, mfa.MFA_PREC_MIXED)
+    b = h.encode_batch(specs, q, precision)
     torch.cuda.synchronize()
     enc_s = time.perf_counter() - t0
     b.refit(q)
@@ -282,55 +295,103 @@ def bench_batch(h, torch, mfa, stream, steps, count=4096, seed=0):
     e1.record(stream)
     torch.cuda.synchronize()
     refit_ms = e0.elapsed_time(e1) / max(steps, 1)
+    b.residual(q)
+    torch.cuda.synchronize()
     r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     r0.record(stream)
-    rms, mx = b.residual(q)
+    for _ in range(5):
+        rms, mx = b.residual(q)
     r1.record(stream)
     torch.cuda.synchronize()
-    res_ms = r0.elapsed_time(r1)
-    # scattered decode: 4096 uniform random parameter points per instance,
-    # device resident, one query per instance
-    per = 4096
-    qi = torch.arange(count, dtype=torch.int32, device="cuda")
-    poff = torch.arange(count + 1, dtype=torch.int64, device="cuda") * per
-    gen = torch.Generator(device="cuda").manual_seed(seed + 7)
-    upts = torch.rand((count * per, 3), dtype=torch.float64, device="cuda", generator=gen)
-    uout = torch.empty(count * per, dtype=torch.float64, device="cuda")
-    b.decode_points(qi, poff, upts, uout)
-    torch.cuda.synchronize()
-    d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    nrep = 5
-    d0.record(stream)
-    for _ in range(nrep):
+    res_ms = r0.elapsed_time(r1) / 5
+    info = b.info()
+    npts = int(info["points"])
+    qbytes = 4 * npts
+    # data-pass kernels of one fit and one residual, traced (not captured)
+    mfa.mfa_trace_enable(h.h, True)
+    b2 = h.encode_batch(specs, q, precision)
+    b2.residual(q)
+    tr = mfa.trace_table(h.h)
+    mfa.mfa_trace_enable(h.h, False)
+    b2.free()
+    peak, peak_kind = load_peaks()
+    passes = {}
+    for name in ("project_data", "refine_data", "residual"):
+        if name in tr and tr[name][0] > 0:
+            ms = tr[name][0]
+            byts = qbytes
+            if name == "refine_data":
+                byts = None  # reads only the refined instances' data (reported as time)
+            ent = {"ms": ms, "launches": tr[name][1]}
+            if byts:
+                ach = byts / (ms * 1e-3) / 1e9
+                ent.update({"algorithmic_bytes": byts, "achieved_gbs": ach, "hbm_frac": ach / peak})
+            passes[name] = ent
+    out = {"precision": {mfa.MFA_PREC_FP32: "fp32", mfa.MFA_PREC_MIXED: "mixed", mfa.MFA_PREC_FP64: "fp64"}[precision],
+           "points": npts, "instances": count, "refined_instances": info["refined"], "items": info["items"],
+           "encode_s_incl_host_layout": enc_s, "refit_ms": refit_ms, "refit_pts_per_s": npts / (refit_ms * 1e-3),
+           "residual_ms": res_ms, "residual_pts_per_s": npts / (res_ms * 1e-3),
+           "fit_plus_residual_pts_per_s": npts / ((refit_ms + res_ms) * 1e-3),
+           "data_passes": passes, "peak_gbs": peak, "peak_source": peak_kind,
+           "kernels_ms": {k: round(v[0], 4) for k, v in tr.items()},
+           "rms": rms, "rms_median": float(np.median(rms)), "rms_max": float(rms.max())}
+    if decode:
+        # scattered decode: 4096 uniform random parameter points per instance,
+        # device resident, one query per instance
+        per = 4096
+        qi = torch.arange(count, dtype=torch.int32, device="cuda")
+        poff = torch.arange(count + 1, dtype=torch.int64, device="cuda") * per
+        gen = torch.Generator(device="cuda").manual_seed(seed + 7)
+        upts = torch.rand((count * per, 3), dtype=torch.float64, device="cuda", generator=gen)
+        uout = torch.empty(count * per, dtype=torch.float64, device="cuda")
         b.decode_points(qi, poff, upts, uout)
-    d1.record(stream)
-    torch.cuda.synchronize()
-    dec_ms = d0.elapsed_time(d1) / nrep
+        torch.cuda.synchronize()
+        d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nrep = 5
+        d0.record(stream)
+        for _ in range(nrep):
+            b.decode_points(qi, poff, upts, uout)
+        d1.record(stream)
+        torch.cuda.synchronize()
+        dec_ms = d0.elapsed_time(d1) / nrep
+        out["scattered_decode"] = {"points": count * per, "ms": dec_ms, "pts_per_s": count * per / (dec_ms * 1e-3),
+                                   "inputs": "4096 uniform random parameter points per instance, on the device"}
+        del upts, uout
     rc, sizes, cand = b.tile_sizes()
+    out["tile_sizes"] = {"projection": sizes[0], "solve": sizes[1], "decode": sizes[2],
+                         "autotune_fit_ms": [[round(float(x), 3) for x in row] for row in cand]}
     b.free()
-    del upts, uout
-    npts = int(data.size)
+    return out
+
+
+def bench_batched(h, torch, mfa, stream, steps, count=4096, seed=0):
+    """The batched workload in FP32 data-pass precision (the line's batched
+    result) and in mixed precision beside it, with the per-instance decoded
+    RMS of the two compared."""
+    f32 = bench_batch(h, torch, mfa, stream, steps, mfa.MFA_PREC_FP32, count, seed)
+    mix = bench_batch(h, torch, mfa, stream, steps, mfa.MFA_PREC_MIXED, count, seed, decode=False)
+    r32, rmx = f32.pop("rms"), mix.pop("rms")
+    rel = np.abs(r32 - rmx) / np.maximum(rmx, 1e-300)
+    specs, _ = inputs.batch_instances(count, seed=seed)
     d2 = sum(1 for sp in specs if sp["dim"] == 2)
     return {"workload": f"{count} independent fits ({d2} 2-D 32..512^2, {count - d2} 3-D 16..128^3 log-uniform, "
-                        "degree 2..5, control points max(p+1, M/4) per axis, sinc / Gaussian sums), mixed precision",
-            "points": npts,
-            "encode_s_incl_host_layout": enc_s, "refit_ms": refit_ms, "refit_pts_per_s": npts / (refit_ms * 1e-3),
-            "residual_ms": res_ms, "fit_plus_residual_pts_per_s": npts / ((refit_ms + res_ms) * 1e-3),
-            "scattered_decode": {"points": count * per, "ms": dec_ms, "pts_per_s": count * per / (dec_ms * 1e-3),
-                                 "inputs": "4096 uniform random parameter points per instance, on the device"},
-            "rms_median": float(np.median(rms)), "rms_max": float(rms.max()),
-            "refit": "one CUDA graph per batch (projection + solves of every (dimension, degree) group)",
-            "tile_sizes": {"projection": sizes[0], "solve": sizes[1], "decode": sizes[2],
-                           "autotune_fit_ms": [[round(float(x), 3) for x in row] for row in cand]}}
+                        "degree 2..5, control points max(p+1, M/4) per axis, sinc / Gaussian sums)",
+            "fp32": f32, "mixed": mix,
+            "fp32_vs_mixed_rms": {"max_rel": float(rel.max()), "median_rel": float(np.median(rel)),
+                                  "within_1pct": int((rel <= 0.01).sum()), "instances": count},
+            "refit": "one CUDA graph per batch (projection, z contraction and solves of every group)"}
 
 
-def bench_serve(torch, mfa, n_enc=160, mix=4, seed=1, workers=3, budget=48 << 30):
+def bench_serve(torch, mfa, n_enc=160, mix=4, seed=1, workers=3, budget=48 << 30, precision=None):
     """Serving: a Poisson stream of encode requests (2-D 64..512^2, 3-D
     32..256^3 log-uniform, p = 3, sinc / Gaussian sums, control points M/4 per
     axis) mixed 1:4 with decode queries of 1e3..1e6 uniform random points
     against a resident model chosen uniformly among those already requested.
     Saturation is measured by submitting everything at once; then the same
-    stream is offered at 0.5x, 0.8x and 1.0x that rate."""
+    stream is offered at 0.5x, 0.8x and 1.0x that rate.  Encodes run in FP32
+    data-pass precision."""
+    if precision is None:
+        precision = mfa.MFA_PREC_FP32
     specs, data = inputs.batch_instances(n_enc, seed=seed, size2=(64, 512), size3=(32, 256), degrees=(3, 3))
     payloads = [torch.from_numpy(data[sp["q_offset"]:sp["q_offset"] + int(np.prod(sp["npts"]))].copy()).pin_memory()
                 for sp in specs]
@@ -359,7 +420,7 @@ def bench_serve(torch, mfa, n_enc=160, mix=4, seed=1, workers=3, budget=48 << 30
             while rate and time.perf_counter() < t_next:
                 time.sleep(min(1e-4, max(t_next - time.perf_counter(), 0)))
             if ev[0] == "enc":
-                rid = srv.encode(specs[ev[1]], payloads[ev[1]])
+                rid = srv.encode(specs[ev[1]], payloads[ev[1]], precision)
                 models[ev[1]] = rid
             else:
                 rid = srv.decode(models[ev[1]], qpts[ev[2]], outs[ev[2]])
@@ -391,9 +452,79 @@ def bench_serve(torch, mfa, n_enc=160, mix=4, seed=1, workers=3, budget=48 << 30
     out = {"workload": f"{n_enc} encodes (2-D 64..512^2 / 3-D 32..256^3, p=3, control points M/4) + "
                        f"{n_enc * mix} decode queries (1e3..1e6 points), Poisson arrivals",
            "encode_points": enc_pts, "decode_points": dec_pts, "workers": workers, "budget_gb": budget / 1e9,
+           "encode_precision": "fp32" if precision == mfa.MFA_PREC_FP32 else "mixed",
            "saturation": sat, "offered": {}}
     for f in (0.5, 0.8, 1.0):
         out["offered"][f"{f:.1f}x"] = run(f * sat["requests_per_s"])
+    return out
+
+
+def load_golden():
+    """The oracle's Schwarz-converged fits of the 1-D and 2-D workloads
+    (written by tests/golden/make_workload_rms.py from the oracle alone)."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "workload_rms.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def bench_workload(h, torch, mfa, stream, key, steps):
+    """One of the smaller workloads (1-D, 2-D) run like the line's own:
+    encode + Schwarz to the workload's stop + residual per step, device data,
+    CUDA events; the decoded RMS beside the oracle's, and the HBM fraction of
+    its dominant data-reading kernel (these grids fit in L2 and a step is a
+    chain of small launches, so the fraction is latency-bound)."""
+    wl = WORKLOADS[key]
+    npts = wl["npts"]
+    q = torch.from_numpy(make_data(wl, npts)).cuda()
+    prec = mfa.MFA_PREC_MIXED if wl["precision"] == "mixed" else mfa.MFA_PREC_FP64
+    d = len(npts)
+    lay = mfa.make_layout(d, wl["p"], npts, wl["nspans"], wl["nsub"], [wl["delta"]] * d, prec)
+
+    def step():
+        m = h.encode(q, lay)
+        rc, rep = m.iterate(wl["max_iters"], wl["tol"], wl.get("stall", 0.0))
+        res = m.residual(q)
+        m.free()
+        return rep, res
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    mfa.mfa_trace_enable(h.h, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = max(steps, 1)
+    e0.record(stream)
+    for _ in range(n):
+        rep, res = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    trace = mfa.trace_table(h.h)
+    mfa.mfa_trace_enable(h.h, False)
+    ms = e0.elapsed_time(e1) / n
+    M = q.numel()
+    qbytes = M * q.element_size()
+    peak, peak_kind = load_peaks()
+    data_cls = {k: v for k, v in trace.items() if k in ("project_data", "residual") and v[1] > 0}
+    hbm = None
+    if data_cls:
+        name = max(data_cls.items(), key=lambda kv: kv[1][0])[0]
+        ms_per = trace[name][0] / trace[name][1]
+        ach = qbytes / (ms_per * 1e-3) / 1e9
+        hbm = {"kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+               "peak_source": peak_kind, "algorithmic_bytes_per_launch": qbytes, "ms_per_launch": ms_per,
+               "note": f"latency-bound: {qbytes / 1e6:.3g} MB of data per launch, smaller than L2"}
+    gold = load_golden().get(key)
+    out = {"workload": wl["name"], "points": M, "pts_per_s": M / (ms * 1e-3), "ms_per_step": ms,
+           "precision": wl["precision"], "stop": stop_desc(wl), "schwarz_iters": rep.iters,
+           "rms_decoded": res.rms_decoded, "maxabs_decoded": res.maxabs_decoded, "hbm": hbm,
+           "gpu_launches_per_step": sum(v[1] for v in trace.values()) / n}
+    if gold:
+        out["oracle"] = {"iters": gold["iters"], "rms": gold["rms"], "max": gold["max"],
+                         "source": "tests/golden/workload_rms.json (FP64 oracle)"}
+        out["rms_rel_diff_vs_oracle"] = abs(res.rms_decoded - gold["rms"]) / gold["rms"]
+        out["iters_equal_oracle"] = rep.iters == gold["iters"]
     return out
 
 
@@ -455,7 +586,7 @@ def run_gb300(args, wl):
 
     def step(q):
         m = h.encode(q, lay)
-        rc, rep = m.iterate(wl["max_iters"], wl["tol"])
+        rc, rep = m.iterate(wl["max_iters"], wl["tol"], wl.get("stall", 0.0))
         res = m.residual(q)
         iters_seen.append(rep.iters)
         m.free()
@@ -488,7 +619,7 @@ def run_gb300(args, wl):
 
     # ---- decode throughput (grid decode into a device buffer)
     m = h.encode(q_dev, lay)
-    m.iterate(wl["max_iters"], wl["tol"])
+    m.iterate(wl["max_iters"], wl["tol"], wl.get("stall", 0.0))
     out = torch.empty_like(q_dev)
     for _ in range(2):
         m.decode_grid(out)
@@ -510,7 +641,7 @@ def run_gb300(args, wl):
     plain = None
     if not args.no_plain:
         def step_plain():
-            m, rc, rep = h.encode_plain(q_dev, lay64, wl["max_iters"], wl["tol"])
+            m, rc, rep = h.encode_plain(q_dev, lay64, wl["max_iters"], wl["tol"] or 1e-6)
             r = m.residual(q_dev)
             m.free()
             return rep, r
@@ -532,8 +663,14 @@ def run_gb300(args, wl):
 
     # ---- batched independent fits: 4096 uneven 2-D / 3-D grids (sizes
     # log-uniform 32..512 / 16..128, degree 2..5, control points M/4 per axis)
-    batched = None if args.no_batch else bench_batch(h, torch, mfa, stream, args.steps)
+    batched = None if args.no_batch else bench_batched(h, torch, mfa, stream, args.steps)
     serving = None if args.no_serve else bench_serve(torch, mfa)
+    # ---- the other workloads of the paper's shapes (1-D FP64, 2-D mixed)
+    others = {}
+    if not args.no_others:
+        for key in ("1d", "2d"):
+            if WORKLOADS[key]["name"] != wl["name"]:
+                others[key] = bench_workload(h, torch, mfa, stream, key, min(args.steps, 20))
 
     # ---- end to end through the C ABI with pinned host buffers: the data
     # cross to the device once (encode stages them; the residual reuses that
@@ -546,7 +683,7 @@ def run_gb300(args, wl):
 
     def step_e2e(hh, P_host):
         m = hh.encode(q_host, lay)  # host -> device copy inside
-        m.iterate(wl["max_iters"], wl["tol"])
+        m.iterate(wl["max_iters"], wl["tol"], wl.get("stall", 0.0))
         m.ctrl_async(P_host)  # device -> host read of the control points, beside the residual
         m.residual(None)  # against the staged copy
         hh.sync()  # the control points are in P_host
@@ -586,7 +723,9 @@ def run_gb300(args, wl):
     for hh in handles:
         hh.close()
 
-    # ---- roofline of the dominant kernel class
+    # ---- roofline of the dominant data-reading kernel: HBM bytes of the
+    # method (every data value read once) over its measured time; for the
+    # float-float projection the FP32-issue view beside it
     peak, peak_kind = load_peaks()
     launches = sum(n for (_, n) in trace.values())
     dom = max(trace.items(), key=lambda kv: kv[1][0]) if trace else None
@@ -598,26 +737,24 @@ def run_gb300(args, wl):
         ms_per = trace[name][0] / trace[name][1]
         ab = algorithmic_bytes(name, wl, qbytes, None)
         achieved = ab / (ms_per * 1e-3) / 1e9
-        hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_kind,
-               "algorithmic_bytes_per_launch": ab}
         roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                "algorithmic_bytes_per_launch": ab, "ms_per_launch": ms_per}
+                "frac": achieved / peak, "traffic": projection_traffic(wl) if name == "project_data" else None,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 384^3 capture of the "
+                                  "fused projection, scaled by the number of windows of the same shape",
+                "peak_source": peak_kind, "algorithmic_bytes_per_launch": ab, "ms_per_launch": ms_per}
         if name == "project_data" and d == 3 and prec == mfa.MFA_PREC_MIXED:
-            # the float-float projection is bound by the FP32 pipes, not by HBM
             mhz = (clocks or {}).get("sm_mhz")
             src = "median SM clock under load" if mhz else "maximum SM clock, no clock samples"
             mhz = mhz or 2070.0
+            sms = sm_count(local)
             ops = projection_ops(wl)
             ach = ops / (ms_per * 1e-3) / 1e12
-            pk = alu_peak_tops(mhz)
-            roof = {"kernel": name, "bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                    "traffic": projection_traffic(wl),
-                    "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one 384^3 capture, "
-                                      "scaled by the number of windows of the same shape",
-                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src})",
-                    "op_convention": "one FP32 add, mul or fma instruction = 1 op",
-                    "algorithmic_ops_per_launch": ops, "ms_per_launch": ms_per, "hbm_view": hbm}
+            pk = alu_peak_tops(mhz, sms)
+            roof["alu_view"] = {"achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                                "peak_source": f"derived: {sms} SMs x 128 FP32 lanes x {mhz:.0f} MHz ({src})",
+                                "op_convention": "one FP32 add, mul or fma instruction = 1 op (float-float "
+                                                 "multiply-add = 11-12 FP32 instructions)",
+                                "algorithmic_ops_per_launch": ops}
     if rank != 0:
         return
     cpu = cpu_baseline(wl, budget_s=args.cpu_budget) if world == 1 and not args.no_cpu else None
@@ -625,12 +762,12 @@ def run_gb300(args, wl):
             "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "float-float" if prec == mfa.MFA_PREC_MIXED else "f64", "data": "synthetic",
             "config": {"workload": wl["name"], "points": M, "control_points": ncp, "precision": wl["precision"],
-                       "stop": f"dP_rel <= {wl['tol']:g}", "schwarz_iters": sorted(set(iters_seen)),
+                       "stop": stop_desc(wl), "schwarz_iters": sorted(set(iters_seen)),
                        "l2": "inputs larger than L2" if qbytes > 129e6 else "inputs smaller than L2",
                        "parallelism": f"replicas x{world}"},
             "decode_pts_per_s": job_rate(world, M, dec_ms * 1e-3), "decode_ms": dec_ms,
             "plain_gpu": plain, "vs_plain_gpu": (value / plain["value"]) if plain else None,
-            "batched_fits": batched, "serving": serving,
+            "batched_fits": batched, "serving": serving, "workloads": others or None,
             "roofline": roof, "dominant_kernel": dom[0] if dom else None, "kernels": kernels,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clocks,
@@ -650,6 +787,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the per-subdomain comparator run")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched independent fits")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
+    ap.add_argument("--no-others", action="store_true", help="skip the 1-D and 2-D workload records")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

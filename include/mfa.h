@@ -443,6 +443,22 @@ int mfa_batch_refit(mfa_handle* h, mfa_batch* b, const void* q, int q_dtype);
  * once tuned, MFA_NOT_CONVERGED before the first refit (defaults 128/64/256). */
 int mfa_batch_tile_sizes(const mfa_batch* b, int32_t* sizes, float* candidate_ms);
 
+/* Shape of a batch: instances, (dimension, degree) groups, precision, and
+ * for MFA_PREC_FP32 the instances that get a refinement step and the CTA
+ * items of the data passes; data points and control points in total.  The
+ * paper has no counterpart (a report of this library's batching). */
+typedef struct mfa_batch_info_t {
+  int32_t count;
+  int32_t groups;
+  int32_t precision;
+  int32_t refined;
+  int32_t items;
+  int32_t reserved;
+  int64_t points;
+  int64_t ctrl;
+} mfa_batch_info_t;
+int mfa_batch_info(const mfa_batch* b, mfa_batch_info_t* out);
+
 /* Control points of every instance, concatenated in instance order (each
  * instance in its own grid layout, axis 0 fastest, prod(nspans_a + degree)
  * values).  mfa_batch_ctrl_offsets writes count + 1 offsets into it.

@@ -212,13 +212,13 @@ enum TraceClass {
   TR_DECODE_POINTS,    // scattered decode
   TR_MISC,             // casts
   TR_REDUCE,           // final fixed-order reduction of residual partials
-  TR_UNUSED15
+  TR_REFINE_DATA       // refinement projection of r = q - N P (MFA_PREC_FP32 batches)
 };
 
 const char* kTraceNames[MFA_TRACE_CLASSES] = {
     "setup_basis_gram_chol", "project_data", "project_reduced", "solve_iter0", "average", "frame_gather",
     "band_apply", "rhs_finalize", "solve_owned", "decode_stage", "residual", "decode_out", "decode_points",
-    "cast", "reduce", "unused15"};
+    "cast", "reduce", "refine_data"};
 
 void trace_flush(mfa_handle* h) {
   if (h->pending.empty()) {
@@ -2653,7 +2653,7 @@ void batch_fit32(mfa_batch* b, const float* q) {
     // one step of iterative refinement for the badly conditioned instances:
     // project r = q - N P32, solve, add the correction
     cudaMemsetAsync(b->b32_dX, 0, (size_t)ncp * sizeof(ff), h->stream);
-    TRACED(h, TR_PROJECT_DATA, for (int c = 0; c < 2; ++c) launch_b32(B32_REFINE, b->b32_inst, b->b32_fitems,
+    TRACED(h, TR_REFINE_DATA, for (int c = 0; c < 2; ++c) launch_b32(B32_REFINE, b->b32_inst, b->b32_fitems,
                                                                        b->ffirst[c], b->caps[c], q, b->b32_P32,
                                                                        b->b32_dX, b->b32_R, b->b32_Z, nullptr,
                                                                        h->stream));
@@ -3086,6 +3086,19 @@ int batch_autotune(mfa_batch* b, const void* q, int q_dtype) {
   return rc;
 }
 }  // namespace
+
+int mfa_batch_info(const mfa_batch* b, mfa_batch_info_t* out) {
+  if (!b || !out) return MFA_ERR_ARG;
+  std::memset(out, 0, sizeof(*out));
+  out->count = b->count;
+  out->groups = (int32_t)b->groups.size();
+  out->precision = b->prec;
+  out->refined = b->n_refined;
+  out->items = b->n_pitems;
+  for (int i = 0; i < b->count; ++i) out->points += b->q_len[i];
+  out->ctrl = b->cp_off[b->count];
+  return MFA_OK;
+}
 
 int mfa_batch_tile_sizes(const mfa_batch* b, int32_t* sizes, float* candidate_ms) {
   if (!b || !sizes) return MFA_ERR_ARG;

@@ -156,6 +156,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_load.restype = ctypes.c_int
     lib.mfa_batch_tile_sizes.argtypes = [P, P, P]
     lib.mfa_batch_tile_sizes.restype = ctypes.c_int
+    lib.mfa_batch_info.argtypes = [P, P]
+    lib.mfa_batch_info.restype = ctypes.c_int
     lib.mfa_batch_decode_points.argtypes = [P, P, ctypes.c_int32, P, P, P, P, ctypes.c_int]
     lib.mfa_server_create.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(P)]
     lib.mfa_server_encode.argtypes = [P, ctypes.POINTER(mfa_instance), P, ctypes.c_int]
@@ -396,6 +398,18 @@ def saved_layout(path: str) -> mfa_layout:
                     weights.append(None)
     return make_layout(dim, degree, list(npts[:dim]), list(nspans[:dim]), list(nsub[:dim]), list(overlap[:dim]), prec,
                        core_spans=cores, lo=list(lo[:dim]), hi=list(hi[:dim]), knots=knots, weights=weights)
+
+
+class MfaBatchInfo(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("groups", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("refined", ctypes.c_int32), ("items", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("points", ctypes.c_int64), ("ctrl", ctypes.c_int64)]
+
+
+def mfa_batch_info(b: int) -> dict:
+    info = MfaBatchInfo()
+    _check(load().mfa_batch_info(ctypes.c_void_p(b), ctypes.byref(info)), "mfa_batch_info")
+    return {f: getattr(info, f) for f, _ in MfaBatchInfo._fields_ if f != "reserved"}
 
 
 def mfa_batch_tile_sizes(b: int):
@@ -761,6 +775,9 @@ class Batch:
 
     def tile_sizes(self):
         return mfa_batch_tile_sizes(self.b)
+
+    def info(self) -> dict:
+        return mfa_batch_info(self.b)
 
     def decode_points(self, qinst, pt_off, pts, out=None):
         """Scattered decode: query k evaluates instance qinst[k] at pts[pt_off[k]:pt_off[k+1]]

@@ -115,3 +115,53 @@ def test_query_of_a_released_model_fails():
             srv.decode(m, np.zeros((4, 3)), np.empty(4))
     finally:
         srv.close()
+
+
+def _run_prec(srv, specs, payloads, queries, alone, precision):
+    models, outs = [], []
+    if alone:
+        for sp, q in zip(specs, payloads):
+            rid = srv.encode(sp, q, precision)
+            rc, _ = srv.wait(rid)
+            assert rc == mfa.MFA_OK
+            models.append(rid)
+        for i, u in queries:
+            out = np.empty(len(u))
+            rc, _ = srv.wait(srv.decode(models[i], u, out))
+            assert rc == mfa.MFA_OK
+            outs.append(out)
+    else:
+        models = [srv.encode(sp, q, precision) for sp, q in zip(specs, payloads)]
+        outs = [np.empty(len(u)) for _, u in queries]
+        rids = [srv.decode(models[i], u, o) for (i, u), o in zip(queries, outs)]
+        for rid in models + rids:
+            rc, _ = srv.wait(rid, 120.0)
+            assert rc == mfa.MFA_OK
+    return models, [srv.ctrl(m) for m in models], outs
+
+
+def test_fp32_encodes_alone_equal_the_mix_and_meet_the_bar():
+    """Served encodes in FP32 data-pass precision: the same control points
+    and decoded values alone and in the mix, and the decoded values within
+    1e-5 of the data range of the oracle's global fit decoded at the same
+    points."""
+    specs, payloads, queries = _workload(33)
+    srv = mfa.Server(0, workers=3, mem_budget=4 << 30)
+    try:
+        m1, c1, v1 = _run_prec(srv, specs, payloads, queries, True, mfa.MFA_PREC_FP32)
+        m2, c2, v2 = _run_prec(srv, specs, payloads, queries, False, mfa.MFA_PREC_FP32)
+        for a, b in zip(c1, c2):
+            assert np.array_equal(a, b)
+        for a, b in zip(v1, v2):
+            assert np.array_equal(a, b)
+        for qi, (i, u) in enumerate(queries):
+            sp = specs[i]
+            Q = payloads[i].astype(np.float64).reshape(tuple(reversed(sp["npts"])))
+            prob = O.make_problem(sp["degree"], list(sp["npts"]), list(sp["nspans"]), [1] * sp["dim"], 0)
+            want = O.scattered_decode(prob, O.global_fit(prob, Q), u[:, :sp["dim"]])
+            rng = float(Q.max() - Q.min())
+            assert np.abs(v1[qi] - want).max() <= 1e-5 * rng, (qi, sp)
+        for m in m1 + m2:
+            srv.release(m)
+    finally:
+        srv.close()
