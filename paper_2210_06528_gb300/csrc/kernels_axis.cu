@@ -438,10 +438,15 @@ __global__ void k_band_apply(LayoutDev L, const AxisOp* ops, const T* __restrict
 }
 
 // In-place banded Cholesky solve along one axis, one thread per fibre
-// (Sec. 2.3.1): forward L y = c, then backward L^T x = y.
+// (Sec. 2.3.1): forward L y = c, then backward L^T x = y.  The p values last
+// solved stay in registers (a window shifted by one per step), and the next
+// right-hand side and factor row are loaded one step ahead, so the recurrence
+// waits on arithmetic only; the operations and their order are those of the
+// plain substitution.
 template <typename T, int AXIS>
 __global__ void k_band_solve(LayoutDev L, bool useU, const AxisOp* ops, T* x, TileMap tm) {
   constexpr int axis = AXIS;
+  constexpr int PM = MFA_MAX_DEGREE;
   int opi;
   long long f;
   tile_of(tm, opi, f);
@@ -458,15 +463,50 @@ __global__ void k_band_solve(LayoutDev L, bool useU, const AxisOp* ops, T* x, Ti
   const int n = v.n[axis];
   T* base = x + v.off + (long long)i1 * v.st[a1] + (long long)i2 * v.st[a2];
   const long long s = v.st[axis];
+  T win[PM];  // win[e - 1] = the value solved e steps ago
+#pragma unroll
+  for (int e = 0; e < PM; ++e) win[e] = T(0.f);
+  T Fr[PM + 1];  // factor row of the current step
+  T rhs = n > 0 ? base[0] : T(0.f);
+#pragma unroll
+  for (int e = 0; e <= PM; ++e) Fr[e] = e <= p && n > 0 ? F[e] : T(0.f);
   for (int i = 0; i < n; ++i) {
-    T acc = base[i * s];
-    for (int e = 1; e <= p && e <= i; ++e) acc -= F[i * w + e] * base[(i - e) * s];
-    base[i * s] = acc * F[i * w];
+    // next step's operands, independent of this step's result
+    T rhs_n = i + 1 < n ? base[(i + 1) * s] : T(0.f);
+    T Fn[PM + 1];
+#pragma unroll
+    for (int e = 0; e <= PM; ++e) Fn[e] = e <= p && i + 1 < n ? F[(i + 1) * w + e] : T(0.f);
+    T acc = rhs;
+#pragma unroll
+    for (int e = 1; e <= PM; ++e)
+      if (e <= p && e <= i) acc -= Fr[e] * win[e - 1];
+    const T xi = acc * Fr[0];
+    base[i * s] = xi;
+#pragma unroll
+    for (int e = PM - 1; e > 0; --e) win[e] = win[e - 1];
+    win[0] = xi;
+    rhs = rhs_n;
+#pragma unroll
+    for (int e = 0; e <= PM; ++e) Fr[e] = Fn[e];
   }
+  // backward: x_i = (y_i - sum_e L(i+e, i) x_{i+e}) / L(i, i); the window
+  // holds x_{i+1} .. x_{i+p}, starting from the last forward values
+  // (win[0] = y_{n-1}, which is the first value solved backwards)
+#pragma unroll
+  for (int e = 0; e < PM; ++e) win[e] = T(0.f);
+  rhs = n > 0 ? base[(n - 1) * s] : T(0.f);
   for (int i = n - 1; i >= 0; --i) {
-    T acc = base[i * s];
-    for (int e = 1; e <= p && i + e < n; ++e) acc -= F[(i + e) * w + e] * base[(i + e) * s];
-    base[i * s] = acc * F[i * w];
+    T rhs_n = i > 0 ? base[(i - 1) * s] : T(0.f);
+    T acc = rhs;
+#pragma unroll
+    for (int e = 1; e <= PM; ++e)
+      if (e <= p && i + e < n) acc -= F[(i + e) * w + e] * win[e - 1];
+    const T xi = acc * F[i * w];
+    base[i * s] = xi;
+#pragma unroll
+    for (int e = PM - 1; e > 0; --e) win[e] = win[e - 1];
+    win[0] = xi;
+    rhs = rhs_n;
   }
 }
 
