@@ -357,9 +357,22 @@ def bench_batch(h, torch, mfa, stream, steps, precision, count=4096, seed=0, dec
         out["scattered_decode"] = {"points": count * per, "ms": dec_ms, "pts_per_s": count * per / (dec_ms * 1e-3),
                                    "inputs": "4096 uniform random parameter points per instance, on the device"}
         del upts, uout
-    rc, sizes, cand = b.tile_sizes()
-    out["tile_sizes"] = {"projection": sizes[0], "solve": sizes[1], "decode": sizes[2],
-                         "autotune_fit_ms": [[round(float(x), 3) for x in row] for row in cand]}
+    tun = []
+    for g in b.group_tuning():
+        c = [x for x in g["candidate_ms"] if x > 0]
+        ent = {"dim": g["dim"], "degree": g["degree"], "instances": g["instances"], "solve_threads": g["tile_s"],
+               "chosen_ms": round(g["chosen_ms"], 4), "candidates_ms": [round(x, 4) for x in g["candidate_ms"]],
+               "spread": round(max(c) / min(c), 3) if c else None}
+        if precision == mfa.MFA_PREC_FP32:
+            ent["item_pts"] = g["item_pts"]
+        else:
+            ent.update({"projection_threads": g["tile_c"], "fused": bool(g["fused"])})
+        tun.append(ent)
+    out["autotune"] = {"groups": tun,
+                       "candidates": ("solve threads 32/64/128 per group; projection items of 32K/128K/512K points "
+                                      "per batch" if precision == mfa.MFA_PREC_FP32 else
+                                      "projection threads 64/128/256 x solve threads 32/64/128, and the fused "
+                                      "one-CTA-per-instance path for 3-D groups, per group")}
     b.free()
     return out
 

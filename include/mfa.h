@@ -436,12 +436,41 @@ int mfa_encode_batch(mfa_handle* h, int32_t count, const mfa_instance* inst, con
 int mfa_batch_refit(mfa_handle* h, mfa_batch* b, const void* q, int q_dtype);
 
 /* Block sizes of the batch's launches (sizes[0] projection, [1] banded
- * solves, [2] decode).  The first mfa_batch_refit picks the projection and
- * solve sizes by timing the fit for 64/128/256 x 32/64/128 threads (a
- * self-tuned choice per batch); candidate_ms (9 floats, may be NULL) gets
- * each candidate's fit time, row-major by projection size.  Returns MFA_OK
- * once tuned, MFA_NOT_CONVERGED before the first refit (defaults 128/64/256). */
+ * solves, [2] decode) of its first group.  The first mfa_batch_refit tunes
+ * every (dimension, degree) group on its own (mfa_batch_group_tuning);
+ * candidate_ms (9 floats, may be NULL) gets, for FP64 and mixed batches, the
+ * sum over the groups of each tiled candidate's fit time, row-major by
+ * projection size (64/128/256 threads) x solve size (32/64/128).  Returns
+ * MFA_OK once tuned, MFA_NOT_CONVERGED before the first refit (defaults
+ * 128/64/256). */
 int mfa_batch_tile_sizes(const mfa_batch* b, int32_t* sizes, float* candidate_ms);
+
+/* Tuning of one (dimension, degree) group of a batch (group 0 ..
+ * mfa_batch_info().groups - 1), chosen by timing on the first refit.  The
+ * paper has no counterpart (a report of this library's autotuner).
+ *   FP64 / mixed batches: candidate_ms[3 i + j] = the group's fit with
+ *     projection blocks of 64/128/256 (i) and solve blocks of 32/64/128 (j)
+ *     threads; candidate_ms[9] = its fused one-CTA-per-instance 3-D path
+ *     (mixed 3-D groups; -1 otherwise); the fastest is kept (`fused`,
+ *     tile_c, tile_s).  The fused path sums in another order than the tiled
+ *     one, so the choice can change the fit's last bits (both within the
+ *     FP64 bar); block sizes never do.
+ *   FP32 batches: candidate_ms[0..2] = the group's solves with 32/64/128
+ *     threads; candidate_ms[3..5] = the batch's FP32 projection with CTA
+ *     items of about 32 K / 128 K / 512 K points (`item_pts` is the
+ *     batch-wide choice; neither changes the fit).
+ * chosen_ms is the kept candidate's time.  Returns MFA_NOT_CONVERGED before
+ * the first refit. */
+#define MFA_TUNE_CANDIDATES 10
+typedef struct mfa_group_tuning_t {
+  int32_t dim, degree, instances;
+  int32_t tile_c, tile_s, tile_e;
+  int32_t fused;
+  int32_t item_pts;
+  float chosen_ms;
+  float candidate_ms[MFA_TUNE_CANDIDATES];
+} mfa_group_tuning_t;
+int mfa_batch_group_tuning(const mfa_batch* b, int32_t group, mfa_group_tuning_t* out);
 
 /* Shape of a batch: instances, (dimension, degree) groups, precision, and
  * for MFA_PREC_FP32 the instances that get a refinement step and the CTA

@@ -7,6 +7,7 @@
 #include <atomic>
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <tuple>
 #include <cstdint>
 #include <cstdio>
@@ -42,6 +43,9 @@ struct mfa_handle {
   char* h_stage = nullptr;                  // pinned staging of layout tables (grown as needed)
   size_t h_stage_cap = 0;
   cudaEvent_t stage_done = nullptr;         // the last upload from h_stage has been read
+  char* h_stage32 = nullptr;                // pinned staging of FP32 batch tables (grown as needed)
+  size_t h_stage32_cap = 0;
+  cudaEvent_t stage32_done = nullptr;       // the last upload from h_stage32 has been read
   cudaStream_t copy_stream = nullptr;       // host data copied slab by slab beside the projection
   std::vector<cudaEvent_t> slab_ev;         // slab landed (copy stream) / buffers allocated (handle stream)
   void* rb = nullptr;                       // staging of asynchronous control-point reads
@@ -82,6 +86,8 @@ struct mfa_model {
   std::vector<AxisOp> hops;                    // batch: host copy of the operand tables (tile maps are rebuilt from it)
   std::vector<int> hmem;                       // batch: batch index of every instance of the group
   int tile_c = 0, tile_s = 0, tile_e = 0;      // batch: block sizes of the current tile maps
+  float tune_ms[MFA_TUNE_CANDIDATES] = {};     // batch: this group's timed candidates (-1: not run)
+  float tune_best = 0.f;                       // batch: time of the chosen candidate
   const void* q_src = nullptr;     // plain form: the device data it re-reads every iteration
   int q_src_dtype = MFA_F32;
   int prec = MFA_PREC_FP64;
@@ -1076,6 +1082,7 @@ int mfa_create(int device, void* cuda_stream, mfa_handle** out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->d_result, 256);
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_pinned, 256);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->stage_done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->stage32_done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->copy_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_ready, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->rb_done, cudaEventDisableTiming);
@@ -1111,6 +1118,8 @@ int mfa_destroy(mfa_handle* h) {
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   if (h->h_stage) cudaFreeHost(h->h_stage);
   if (h->stage_done) cudaEventDestroy(h->stage_done);
+  if (h->h_stage32) cudaFreeHost(h->h_stage32);
+  if (h->stage32_done) cudaEventDestroy(h->stage32_done);
   for (cudaEvent_t ev : h->slab_ev) cudaEventDestroy(ev);
   if (h->rb_ready) cudaEventDestroy(h->rb_ready);
   if (h->rb_done) cudaEventDestroy(h->rb_done);
@@ -2773,7 +2782,7 @@ double host_gram_cond(long long M, int ns, int p) {
   for (int i = 0; i < n; ++i) x[i] = 1.0 + 0.37 * ((i * 7919) % 13);
   normalise(x);
   double lmax = 0.0;
-  for (int it = 0; it < 60; ++it) {
+  for (int it = 0; it < 30; ++it) {
     matvec(x, y);
     lmax = normalise(y);
     x.swap(y);
@@ -2781,7 +2790,7 @@ double host_gram_cond(long long M, int ns, int p) {
   for (int i = 0; i < n; ++i) x[i] = ((i * 7919) % 13) - 6.0 + 0.5;
   normalise(x);
   double inv = 0.0;
-  for (int it = 0; it < 60; ++it) {
+  for (int it = 0; it < 30; ++it) {
     solve(x);
     inv = normalise(x);
   }
@@ -2928,16 +2937,27 @@ int build_b32(mfa_batch* b) {
   // a refinement step where the FP32 error bound 2^-24 prod_a sqrt(cond(N_a^T N_a))
   // of the decoded values, relative to the data, exceeds 2e-6 (observed errors
   // stay below ~1.1x this bound; after one step they fall below 1e-6)
-  std::map<std::tuple<long long, int, int>, double> conds;
+  // (condition numbers cached for the process: one estimate per axis shape)
+  static std::mutex cond_mu;
+  static std::map<std::tuple<long long, int, int>, double> conds;
   std::vector<char> refine(count, 0);
   for (int i = 0; i < count; ++i) {
     const mfa_instance& in = b->inst[i];
     double g = std::ldexp(1.0, -24);
     for (int a = 0; a < in.dim; ++a) {
       const auto key = std::make_tuple((long long)in.npts[a], in.nspans[a], in.degree);
-      auto itc = conds.find(key);
-      if (itc == conds.end()) itc = conds.emplace(key, host_gram_cond(in.npts[a], in.nspans[a], in.degree)).first;
-      g *= std::sqrt(itc->second);
+      double c;
+      {
+        std::lock_guard<std::mutex> lk(cond_mu);
+        auto itc = conds.find(key);
+        c = itc == conds.end() ? -1.0 : itc->second;
+      }
+      if (c < 0.0) {
+        c = host_gram_cond(in.npts[a], in.nspans[a], in.degree);
+        std::lock_guard<std::mutex> lk(cond_mu);
+        conds.emplace(key, c);
+      }
+      g *= std::sqrt(c);
     }
     refine[i] = g > 2e-6;
   }
@@ -2966,17 +2986,32 @@ int build_b32(mfa_batch* b) {
   void* mem = nullptr;
   int rc = pool_alloc(h, &mem, ar.used);
   if (rc != MFA_OK) return rc;
-  std::vector<char> img(host_bytes);
-  std::memcpy(img.data() + o_inst, D.data(), sizeof(B32Inst) * D.size());
-  std::memcpy(img.data() + o_pit, pit.data(), sizeof(B32Item) * pit.size());
-  std::memcpy(img.data() + o_rf, rrange.data(), sizeof(int) * rrange.size());
-  std::memcpy(img.data() + o_zi, zti.data(), sizeof(int) * zti.size());
-  std::memcpy(img.data() + o_zb, ztb.data(), sizeof(long long) * ztb.size());
-  std::memcpy(img.data() + o_fit, fit.data(), sizeof(B32Item) * fit.size());
-  std::memcpy(img.data() + o_fti, fti.data(), sizeof(int) * fti.size());
-  std::memcpy(img.data() + o_ftb, ftb.data(), sizeof(long long) * ftb.size());
-  cudaError_t e = cudaMemcpyAsync(mem, img.data(), host_bytes, cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // the image is a local vector
+  // the table image in the handle's pinned FP32 staging buffer, once its
+  // previous upload has been read: the copy then needs no stream sync
+  cudaEventSynchronize(h->stage32_done);
+  if (h->h_stage32_cap < host_bytes) {
+    if (h->h_stage32) cudaFreeHost(h->h_stage32);
+    h->h_stage32 = nullptr;
+    h->h_stage32_cap = 0;
+    if (cudaMallocHost(&h->h_stage32, host_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      h->h_stage32 = nullptr;
+      pool_free(h, mem);
+      return MFA_ERR_OOM;
+    }
+    h->h_stage32_cap = host_bytes;
+  }
+  char* const img = h->h_stage32;
+  std::memcpy(img + o_inst, D.data(), sizeof(B32Inst) * D.size());
+  std::memcpy(img + o_pit, pit.data(), sizeof(B32Item) * pit.size());
+  std::memcpy(img + o_rf, rrange.data(), sizeof(int) * rrange.size());
+  std::memcpy(img + o_zi, zti.data(), sizeof(int) * zti.size());
+  std::memcpy(img + o_zb, ztb.data(), sizeof(long long) * ztb.size());
+  std::memcpy(img + o_fit, fit.data(), sizeof(B32Item) * fit.size());
+  std::memcpy(img + o_fti, fti.data(), sizeof(int) * fti.size());
+  std::memcpy(img + o_ftb, ftb.data(), sizeof(long long) * ftb.size());
+  cudaError_t e = cudaMemcpyAsync(mem, img, host_bytes, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(h->stage32_done, h->stream);
   if (e != cudaSuccess) {
     pool_free(h, mem);
     return cuda_status(e);
@@ -3045,6 +3080,37 @@ namespace {
 // on the stream for every pair of block sizes (projection 64 / 128 / 256,
 // solves 32 / 64 / 128; one warm run, one timed run each) and the fastest
 // pair is kept for every group.  The decode keeps 256.
+// One group's fit (projection, iteration-0 solves) on the handle's stream.
+void group_fit_any(mfa_batch* b, mfa_model* md, const void* q, int q_dtype) {
+  if (b->prec == MFA_PREC_FP64) {
+    if (q_dtype == MFA_F64)
+      run_encode<double, double>(md, (const double*)q);
+    else
+      run_encode<double, float>(md, (const float*)q);
+  } else {
+    if (q_dtype == MFA_F64)
+      run_encode<ff, double>(md, (const double*)q);
+    else
+      run_encode<ff, float>(md, (const float*)q);
+  }
+}
+
+// The FP32 batch's float-float solves of one group.
+void group_solve32(mfa_batch* b, mfa_model* md) {
+  for (int a = 0; a < md->dim; ++a)
+    launch_band_solve<ff>(md->L, a, false, md->ops + (size_t)(OP_SOLVEL0 + a) * md->nsub, md->nsub, md->maxFibL[a],
+                          (ff*)b->buf, b->h->stream, &md->tm_solve[a]);
+}
+
+// Autotuning on the first refit, per (dimension, degree) group.
+//  - FP64 / mixed: every group times its own fit for projection blocks of
+//    64/128/256 threads x solve blocks of 32/64/128 (the elements a CTA
+//    takes) and, for 3-D mixed groups, the fused one-CTA-per-instance path;
+//    each group keeps its fastest candidate.
+//  - FP32: the data passes' work per CTA item (3-D ranges of planes of about
+//    32 K, 128 K or 512 K points), timed over the batch's projection, and
+//    every group's solve block size, timed over that group's solves.
+// The second of two runs of each candidate is kept.
 int batch_autotune(mfa_batch* b, const void* q, int q_dtype) {
   mfa_handle* h = b->h;
   const int cand_c[3] = {64, 128, 256}, cand_s[3] = {32, 64, 128};
@@ -3053,32 +3119,94 @@ int batch_autotune(mfa_batch* b, const void* q, int q_dtype) {
   const bool tr = h->trace_on;
   trace_flush(h);
   h->trace_on = false;
-  float best = 1e30f;
-  int bc = kContractThreads, bs = kSolveThreads, rc = MFA_OK;
-  for (int ic = 0; ic < 3 && rc == MFA_OK; ++ic)
-    for (int is = 0; is < 3 && rc == MFA_OK; ++is) {
-      for (mfa_model* md : b->groups) {
-        rc = build_batch_tiles(h, md, cand_c[ic], cand_s[is], kExpandThreads);
-        if (rc != MFA_OK) break;
-      }
+  int rc = MFA_OK;
+  auto timed = [&](auto&& work) {
+    float ms = 0.f;
+    for (int rep = 0; rep < 2 && rc == MFA_OK; ++rep) {
+      cudaEventRecord(e0, h->stream);
+      work();
+      cudaEventRecord(e1, h->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = MFA_ERR_CUDA;
+      cudaEventElapsedTime(&ms, e0, e1);
+    }
+    return ms;
+  };
+  for (mfa_model* md : b->groups)
+    for (float& t : md->tune_ms) t = -1.f;
+  for (float& t : b->tune_ms) t = 0.f;
+  if (b->prec == MFA_PREC_FP32) {
+    const int cand_items[3] = {32768, 131072, 524288};
+    const float* qf = (const float*)q;
+    float best = 1e30f;
+    int bi = b->item_pts;
+    for (int k = 0; k < 3 && rc == MFA_OK; ++k) {
+      b->item_pts = cand_items[k];
+      rc = build_b32(b);
       if (rc != MFA_OK) break;
-      float ms = 0.f;
-      for (int rep = 0; rep < 2; ++rep) {
-        cudaEventRecord(e0, h->stream);
-        batch_fit_any(b, q, q_dtype);
-        cudaEventRecord(e1, h->stream);
-        if (cudaEventSynchronize(e1) != cudaSuccess) rc = MFA_ERR_CUDA;
-        cudaEventElapsedTime(&ms, e0, e1);
-      }
-      b->tune_ms[ic * 3 + is] = ms;
+      const float ms = timed([&] {
+        for (int c = 0; c < 2; ++c)
+          launch_b32(B32_PROJECT, b->b32_inst, b->b32_pitems, b->pfirst[c], b->caps[c], qf, nullptr, (ff*)b->buf,
+                     b->b32_R, b->b32_Z, nullptr, h->stream);
+      });
+      for (mfa_model* md : b->groups) md->tune_ms[3 + k] = ms;
       if (ms < best) {
         best = ms;
-        bc = cand_c[ic];
-        bs = cand_s[is];
+        bi = cand_items[k];
       }
     }
-  for (mfa_model* md : b->groups)
-    if (rc == MFA_OK) rc = build_batch_tiles(h, md, bc, bs, kExpandThreads);
+    if (rc == MFA_OK && b->item_pts != bi) {
+      b->item_pts = bi;
+      rc = build_b32(b);
+    }
+    for (int is = 0; is < 3 && rc == MFA_OK; ++is)
+      for (mfa_model* md : b->groups) {
+        rc = build_batch_tiles(h, md, md->tile_c, cand_s[is], kExpandThreads);
+        if (rc != MFA_OK) break;
+        md->tune_ms[is] = timed([&] { group_solve32(b, md); });
+      }
+    for (mfa_model* md : b->groups) {
+      if (rc != MFA_OK) break;
+      int bs = 0;
+      for (int is = 1; is < 3; ++is)
+        if (md->tune_ms[is] < md->tune_ms[bs]) bs = is;
+      md->tune_best = md->tune_ms[bs];
+      rc = build_batch_tiles(h, md, md->tile_c, cand_s[bs], kExpandThreads);
+    }
+  } else {
+    // fused candidate first (3-D mixed groups), then the tiled grid
+    std::vector<char> fused_ok(b->groups.size(), 0);
+    for (size_t g = 0; g < b->groups.size() && rc == MFA_OK; ++g) {
+      mfa_model* md = b->groups[g];
+      if (md->dim != 3 || md->prec != MFA_PREC_MIXED) continue;
+      const bool was = md->use_fused;
+      md->use_fused = true;
+      md->tune_ms[9] = timed([&] { group_fit_any(b, md, q, q_dtype); });
+      fused_ok[g] = 1;
+      md->use_fused = was;
+    }
+    for (int ic = 0; ic < 3 && rc == MFA_OK; ++ic)
+      for (int is = 0; is < 3 && rc == MFA_OK; ++is)
+        for (mfa_model* md : b->groups) {
+          rc = build_batch_tiles(h, md, cand_c[ic], cand_s[is], kExpandThreads);
+          if (rc != MFA_OK) break;
+          const bool was = md->use_fused;
+          md->use_fused = false;
+          const float ms = timed([&] { group_fit_any(b, md, q, q_dtype); });
+          md->use_fused = was;
+          md->tune_ms[ic * 3 + is] = ms;
+          b->tune_ms[ic * 3 + is] += ms;
+        }
+    for (size_t g = 0; g < b->groups.size() && rc == MFA_OK; ++g) {
+      mfa_model* md = b->groups[g];
+      int bk = 0;
+      for (int k = 1; k < 9; ++k)
+        if (md->tune_ms[k] < md->tune_ms[bk]) bk = k;
+      const bool fz = fused_ok[g] && md->tune_ms[9] >= 0.f && md->tune_ms[9] < md->tune_ms[bk];
+      md->use_fused = fz;
+      md->tune_best = fz ? md->tune_ms[9] : md->tune_ms[bk];
+      rc = build_batch_tiles(h, md, cand_c[bk / 3], cand_s[bk % 3], kExpandThreads);
+    }
+  }
   h->trace_on = tr;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -3098,6 +3226,23 @@ int mfa_batch_info(const mfa_batch* b, mfa_batch_info_t* out) {
   for (int i = 0; i < b->count; ++i) out->points += b->q_len[i];
   out->ctrl = b->cp_off[b->count];
   return MFA_OK;
+}
+
+int mfa_batch_group_tuning(const mfa_batch* b, int32_t group, mfa_group_tuning_t* out) {
+  if (!b || !out || group < 0 || group >= (int)b->groups.size()) return MFA_ERR_ARG;
+  const mfa_model* md = b->groups[group];
+  std::memset(out, 0, sizeof(*out));
+  out->dim = md->dim;
+  out->degree = md->degree;
+  out->instances = md->nsub;
+  out->tile_c = md->tile_c;
+  out->tile_s = md->tile_s;
+  out->tile_e = md->tile_e;
+  out->fused = md->dim == 3 && md->prec == MFA_PREC_MIXED && md->use_fused ? 1 : 0;
+  out->item_pts = b->prec == MFA_PREC_FP32 ? b->item_pts : 0;
+  out->chosen_ms = md->tune_best;
+  for (int k = 0; k < MFA_TUNE_CANDIDATES; ++k) out->candidate_ms[k] = md->tune_ms[k];
+  return b->tuned ? MFA_OK : MFA_NOT_CONVERGED;
 }
 
 int mfa_batch_tile_sizes(const mfa_batch* b, int32_t* sizes, float* candidate_ms) {

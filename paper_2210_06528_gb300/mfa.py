@@ -158,6 +158,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_batch_tile_sizes.restype = ctypes.c_int
     lib.mfa_batch_info.argtypes = [P, P]
     lib.mfa_batch_info.restype = ctypes.c_int
+    lib.mfa_batch_group_tuning.argtypes = [P, ctypes.c_int32, P]
+    lib.mfa_batch_group_tuning.restype = ctypes.c_int
     lib.mfa_batch_decode_points.argtypes = [P, P, ctypes.c_int32, P, P, P, P, ctypes.c_int]
     lib.mfa_server_create.argtypes = [ctypes.c_int, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, ctypes.POINTER(P)]
     lib.mfa_server_encode.argtypes = [P, ctypes.POINTER(mfa_instance), P, ctypes.c_int]
@@ -410,6 +412,26 @@ def mfa_batch_info(b: int) -> dict:
     info = MfaBatchInfo()
     _check(load().mfa_batch_info(ctypes.c_void_p(b), ctypes.byref(info)), "mfa_batch_info")
     return {f: getattr(info, f) for f, _ in MfaBatchInfo._fields_ if f != "reserved"}
+
+
+MFA_TUNE_CANDIDATES = 10
+
+
+class MfaGroupTuning(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("degree", ctypes.c_int32), ("instances", ctypes.c_int32),
+                ("tile_c", ctypes.c_int32), ("tile_s", ctypes.c_int32), ("tile_e", ctypes.c_int32),
+                ("fused", ctypes.c_int32), ("item_pts", ctypes.c_int32), ("chosen_ms", ctypes.c_float),
+                ("candidate_ms", ctypes.c_float * MFA_TUNE_CANDIDATES)]
+
+
+def mfa_batch_group_tuning(b: int, group: int):
+    """(rc, dict) of one group's autotuned choice and its timed candidates."""
+    t = MfaGroupTuning()
+    rc = load().mfa_batch_group_tuning(ctypes.c_void_p(b), int(group), ctypes.byref(t))
+    _check(rc, "mfa_batch_group_tuning", ok=(MFA_OK, MFA_NOT_CONVERGED))
+    out = {f: getattr(t, f) for f, _ in MfaGroupTuning._fields_ if f != "candidate_ms"}
+    out["candidate_ms"] = [float(x) for x in t.candidate_ms]
+    return rc, out
 
 
 def mfa_batch_tile_sizes(b: int):
@@ -778,6 +800,10 @@ class Batch:
 
     def info(self) -> dict:
         return mfa_batch_info(self.b)
+
+    def group_tuning(self):
+        """Autotuned choice of every (dimension, degree) group (after the first refit)."""
+        return [mfa_batch_group_tuning(self.b, g)[1] for g in range(self.info()["groups"])]
 
     def decode_points(self, qinst, pt_off, pts, out=None):
         """Scattered decode: query k evaluates instance qinst[k] at pts[pt_off[k]:pt_off[k+1]]
