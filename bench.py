@@ -359,17 +359,23 @@ def bench_batch(h, torch, mfa, stream, steps, precision, count=4096, seed=0, dec
         del upts, uout
     tun = []
     for g in b.group_tuning():
-        c = [x for x in g["candidate_ms"] if x > 0]
+        cm = g["candidate_ms"]
+
+        def spread(xs):
+            xs = [x for x in xs if x > 0]
+            return round(max(xs) / min(xs), 3) if xs else None
+
         ent = {"dim": g["dim"], "degree": g["degree"], "instances": g["instances"], "solve_threads": g["tile_s"],
-               "chosen_ms": round(g["chosen_ms"], 4), "candidates_ms": [round(x, 4) for x in g["candidate_ms"]],
-               "spread": round(max(c) / min(c), 3) if c else None}
+               "chosen_ms": round(g["chosen_ms"], 4), "candidates_ms": [round(x, 4) for x in cm]}
         if precision == mfa.MFA_PREC_FP32:
-            ent["item_pts"] = g["item_pts"]
+            ent.update({"item_pts": g["item_pts"], "solve_spread": spread(cm[0:3]), "item_spread": spread(cm[3:6])})
         else:
-            ent.update({"projection_threads": g["tile_c"], "fused": bool(g["fused"])})
+            ent.update({"projection_threads": g["tile_c"], "fused": bool(g["fused"]),
+                        "tiled_spread": spread(cm[0:9]),
+                        "fused_vs_best_tiled": round(cm[9] / min(cm[0:9]), 3) if cm[9] > 0 else None})
         tun.append(ent)
     out["autotune"] = {"groups": tun,
-                       "candidates": ("solve threads 32/64/128 per group; projection items of 32K/128K/512K points "
+                       "candidates": ("solve threads 32/64/128 per group; projection items of 16K/32K/128K points "
                                       "per batch" if precision == mfa.MFA_PREC_FP32 else
                                       "projection threads 64/128/256 x solve threads 32/64/128, and the fused "
                                       "one-CTA-per-instance path for 3-D groups, per group")}

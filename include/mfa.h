@@ -457,7 +457,7 @@ int mfa_batch_tile_sizes(const mfa_batch* b, int32_t* sizes, float* candidate_ms
  *     FP64 bar); block sizes never do.
  *   FP32 batches: candidate_ms[0..2] = the group's solves with 32/64/128
  *     threads; candidate_ms[3..5] = the batch's FP32 projection with CTA
- *     items of about 32 K / 128 K / 512 K points (`item_pts` is the
+ *     items of about 16 K / 32 K / 128 K points (`item_pts` is the
  *     batch-wide choice; neither changes the fit).
  * chosen_ms is the kept candidate's time.  Returns MFA_NOT_CONVERGED before
  * the first refit. */

@@ -2318,7 +2318,7 @@ struct mfa_batch {
   ff* b32_dX = nullptr;
   int n_fitems = 0, n_ftiles = 0, n_refined = 0;
   int pfirst[2][MFA_MAX_DEGREE + 1] = {}, ffirst[2][MFA_MAX_DEGREE + 1] = {};
-  int item_pts = 131072;  // data points per projection / residual item of a 3-D instance
+  int item_pts = 32768;  // data points per projection / residual item of a 3-D instance (autotuned)
 };
 
 namespace {
@@ -3108,7 +3108,7 @@ void group_solve32(mfa_batch* b, mfa_model* md) {
 //    takes) and, for 3-D mixed groups, the fused one-CTA-per-instance path;
 //    each group keeps its fastest candidate.
 //  - FP32: the data passes' work per CTA item (3-D ranges of planes of about
-//    32 K, 128 K or 512 K points), timed over the batch's projection, and
+//    16 K, 32 K or 128 K points), timed over the batch's projection, and
 //    every group's solve block size, timed over that group's solves.
 // The second of two runs of each candidate is kept.
 int batch_autotune(mfa_batch* b, const void* q, int q_dtype) {
@@ -3135,7 +3135,7 @@ int batch_autotune(mfa_batch* b, const void* q, int q_dtype) {
     for (float& t : md->tune_ms) t = -1.f;
   for (float& t : b->tune_ms) t = 0.f;
   if (b->prec == MFA_PREC_FP32) {
-    const int cand_items[3] = {32768, 131072, 524288};
+    const int cand_items[3] = {16384, 32768, 131072};
     const float* qf = (const float*)q;
     float best = 1e30f;
     int bi = b->item_pts;

@@ -111,11 +111,11 @@ def test_fp32_refit_graph_equals_fresh_encode_and_is_linear():
         P2 = b.ctrl()
         # autotuned: CTA item size for the batch, solve block size per group
         for g in b.group_tuning():
-            assert g["item_pts"] in (32768, 131072, 524288)
+            assert g["item_pts"] in (16384, 32768, 131072)
             assert min(g["candidate_ms"][:6]) > 0
             assert g["chosen_ms"] == min(g["candidate_ms"][:3])
             assert g["candidate_ms"][(32, 64, 128).index(g["tile_s"])] == g["chosen_ms"]
-            k = (32768, 131072, 524288).index(g["item_pts"])
+            k = (16384, 32768, 131072).index(g["item_pts"])
             assert g["candidate_ms"][3 + k] == min(g["candidate_ms"][3:6])
         c = h.encode_batch(specs, q2, FP32)
         assert np.array_equal(P2, c.ctrl())
