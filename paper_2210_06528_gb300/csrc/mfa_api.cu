@@ -232,6 +232,7 @@ void trace_flush(mfa_handle* h) {
     return;
   }
   cudaEventSynchronize(h->ev[h->pending.back().second + 1]);
+  cudaStreamSynchronize(h->stream);  // events recorded on a batch's side streams are joined into it
   for (auto& pr : h->pending) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, h->ev[pr.second], h->ev[pr.second + 1]) == cudaSuccess)
@@ -2317,6 +2318,12 @@ struct mfa_batch {
   long long* b32_ftile_base = nullptr;
   ff* b32_dX = nullptr;
   int n_fitems = 0, n_ftiles = 0, n_refined = 0;
+  // side streams on which the groups' independent work runs side by side
+  // (forked from and joined back into the handle's stream; a captured refit
+  // records them as parallel branches)
+  cudaStream_t side[8] = {};
+  int nside = 0;
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   int pfirst[2][MFA_MAX_DEGREE + 1] = {}, ffirst[2][MFA_MAX_DEGREE + 1] = {};
   int item_pts = 32768;  // data points per projection / residual item of a 3-D instance (autotuned)
 };
@@ -2620,9 +2627,60 @@ int build_batch_group(mfa_batch* b, int d, int p, const std::vector<int>& mem, m
   return MFA_OK;
 }
 
+// Side streams of a batch (created on first use, one per group up to 8);
+// 0 or 1 means the groups run on the handle's stream.
+int batch_sides(mfa_batch* b) {
+  const int want = std::min<int>(8, (int)b->groups.size());
+  if (want <= 1) return 0;
+  if (b->nside == 0) {
+    if (cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    for (int i = 0; i < want; ++i) {
+      if (cudaStreamCreateWithFlags(&b->side[i], cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        break;
+      }
+      b->nside = i + 1;
+    }
+  }
+  return b->nside;
+}
+
+// Every side stream waits for the work queued so far on the handle's stream.
+void batch_fork(mfa_batch* b) {
+  cudaEventRecord(b->fork_ev, b->h->stream);
+  for (int i = 0; i < b->nside; ++i) cudaStreamWaitEvent(b->side[i], b->fork_ev, 0);
+}
+
+// The handle's stream waits for everything queued on the side streams.
+void batch_join(mfa_batch* b) {
+  for (int i = 0; i < b->nside; ++i) {
+    cudaEventRecord(b->join_ev, b->side[i]);
+    cudaStreamWaitEvent(b->h->stream, b->join_ev, 0);
+  }
+}
+
+// The groups' fits (independent: own tables, own scratch, disjoint control
+// points) run side by side, group g on side stream g mod nside.
 template <typename T, typename TQ>
 void batch_fit_all(mfa_batch* b, const TQ* q) {
-  for (mfa_model* md : b->groups) run_encode<T, TQ>(md, q);
+  mfa_handle* h = b->h;
+  const int ns = batch_sides(b);
+  if (ns <= 1) {
+    for (mfa_model* md : b->groups) run_encode<T, TQ>(md, q);
+    return;
+  }
+  cudaStream_t main = h->stream;
+  batch_fork(b);
+  for (size_t g = 0; g < b->groups.size(); ++g) {
+    h->stream = b->side[g % ns];  // run_encode launches on the handle's stream
+    run_encode<T, TQ>(b->groups[g], q);
+  }
+  h->stream = main;
+  batch_join(b);
 }
 
 template <typename T>
@@ -2648,12 +2706,20 @@ void batch_fit32(mfa_batch* b, const float* q) {
     TRACED(h, TR_PROJECT_REDUCED,
            launch_b32_zcontract(b->b32_inst, b->b32_ztile_inst, b->b32_ztile_base, b->n_ztiles, b->b32_R, X,
                                 h->stream));
+  // the groups' solves side by side (independent fibres of disjoint control points)
   auto solve_all = [&](ff* x) {
-    for (mfa_model* md : b->groups)
+    const int ns = batch_sides(b);
+    const int _ti = trace_begin(h);
+    if (ns > 1) batch_fork(b);
+    for (size_t g = 0; g < b->groups.size(); ++g) {
+      mfa_model* md = b->groups[g];
+      cudaStream_t st = ns > 1 ? b->side[g % ns] : h->stream;
       for (int a = 0; a < md->dim; ++a)
-        TRACED(h, TR_SOLVE_L,
-               launch_band_solve<ff>(md->L, a, false, md->ops + (size_t)(OP_SOLVEL0 + a) * md->nsub, md->nsub,
-                                     md->maxFibL[a], x, h->stream, &md->tm_solve[a]));
+        launch_band_solve<ff>(md->L, a, false, md->ops + (size_t)(OP_SOLVEL0 + a) * md->nsub, md->nsub,
+                              md->maxFibL[a], x, st, &md->tm_solve[a]);
+    }
+    if (ns > 1) batch_join(b);
+    trace_end(h, TR_SOLVE_L, _ti);
   };
   solve_all(X);
   const long long ncp = b->cp_off[b->count];
@@ -3581,6 +3647,10 @@ int mfa_batch_free(mfa_batch* b) {
   DeviceGuard g(h->device);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->nside) cudaStreamSynchronize(h->stream);
+  for (int i = 0; i < b->nside; ++i) cudaStreamDestroy(b->side[i]);
+  if (b->fork_ev) cudaEventDestroy(b->fork_ev);
+  if (b->join_ev) cudaEventDestroy(b->join_ev);
   for (mfa_model* md : b->groups) {
     md->BL = md->X = md->P = nullptr;
     mfa_free(md);
