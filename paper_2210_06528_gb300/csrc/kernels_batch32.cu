@@ -575,12 +575,14 @@ __global__ void __launch_bounds__(kB32Threads, MODE == B32_REFINE ? 1 : 2) k_b32
 
 template <int MODE>
 void launch_mode(const B32Inst* insts, const B32Item* items, const int* first, const B32Caps* caps, const float* Q,
-                 const float* P32, ff* X, float* R, float* Z, double* part, cudaStream_t st) {
+                 const float* P32, ff* X, float* R, float* Z, double* part, cudaStream_t st, const cudaStream_t* sides,
+                 int nsides, int& k) {
 #define MFA_B32_LAUNCH(PP)                                                                                   \
   if (first[PP] > first[PP - 1]) {                                                                          \
     const size_t smem = b32_smem_bytes(caps[PP], MODE);                                                     \
     ensure_smem(k_b32<PP, MODE>, smem);                                                                     \
-    k_b32<PP, MODE><<<first[PP] - first[PP - 1], kB32Threads, smem, st>>>(insts, items + first[PP - 1],      \
+    cudaStream_t s_ = nsides > 0 ? sides[k++ % nsides] : st;                                                \
+    k_b32<PP, MODE><<<first[PP] - first[PP - 1], kB32Threads, smem, s_>>>(insts, items + first[PP - 1],      \
                                                                           first[PP - 1], caps[PP], Q, P32, X, \
                                                                           R, Z, part);                      \
   }
@@ -596,13 +598,17 @@ size_t b32_smem_bytes(const B32Caps& cap, int mode) {
 }
 
 void launch_b32(int mode, const B32Inst* insts, const B32Item* items, const int* first, const B32Caps* caps,
-                const float* Q, const float* P32, ff* X, float* R, float* Z, double* part, cudaStream_t st) {
+                const float* Q, const float* P32, ff* X, float* R, float* Z, double* part, cudaStream_t st,
+                const cudaStream_t* sides, int nsides, int* next_side) {
+  int k0 = next_side ? *next_side : 0;
+  int& k = next_side ? *next_side : k0;
   if (mode == B32_PROJECT)
-    launch_mode<B32_PROJECT>(insts, items, first, caps, Q, nullptr, X, R, Z, nullptr, st);
+    launch_mode<B32_PROJECT>(insts, items, first, caps, Q, nullptr, X, R, Z, nullptr, st, sides, nsides, k);
   else if (mode == B32_REFINE)
-    launch_mode<B32_REFINE>(insts, items, first, caps, Q, P32, X, R, Z, nullptr, st);
+    launch_mode<B32_REFINE>(insts, items, first, caps, Q, P32, X, R, Z, nullptr, st, sides, nsides, k);
   else
-    launch_mode<B32_RESIDUAL>(insts, items, first, caps, Q, P32, nullptr, nullptr, nullptr, part, st);
+    launch_mode<B32_RESIDUAL>(insts, items, first, caps, Q, P32, nullptr, nullptr, nullptr, part, st, sides, nsides,
+                              k);
 }
 
 // X += dX over n float-float values (the refinement's correction of the

@@ -2696,12 +2696,25 @@ void batch_fit(mfa_batch* b, const void* q, int q_dtype) {
 // solves of every group, and the FP32 copy of the control points the
 // residual decodes from; then one refinement step for the instances whose
 // FP32 error bound is large.
+// One FP32 data pass over both classes: the launches of every (class,
+// degree) side by side on the batch's side streams (disjoint outputs), so
+// that no launch's tail idles the GPU.
+void b32_pass(mfa_batch* b, int mode, const B32Item* items, int first[2][MFA_MAX_DEGREE + 1], const float* q,
+              ff* X, double* part) {
+  mfa_handle* h = b->h;
+  const int ns = batch_sides(b);
+  int k = 0;
+  if (ns > 1) batch_fork(b);
+  for (int c = 0; c < 2; ++c)
+    launch_b32(mode, b->b32_inst, items, first[c], b->caps[c], q, b->b32_P32, X, b->b32_R, b->b32_Z, part,
+               h->stream, ns > 1 ? b->side : nullptr, ns > 1 ? ns : 0, &k);
+  if (ns > 1) batch_join(b);
+}
+
 void batch_fit32(mfa_batch* b, const float* q) {
   mfa_handle* h = b->h;
   ff* X = (ff*)b->buf;
-  TRACED(h, TR_PROJECT_DATA, for (int c = 0; c < 2; ++c) launch_b32(B32_PROJECT, b->b32_inst, b->b32_pitems,
-                                                                     b->pfirst[c], b->caps[c], q, nullptr, X,
-                                                                     b->b32_R, b->b32_Z, nullptr, h->stream));
+  TRACED(h, TR_PROJECT_DATA, b32_pass(b, B32_PROJECT, b->b32_pitems, b->pfirst, q, X, nullptr));
   if (b->n_ztiles)
     TRACED(h, TR_PROJECT_REDUCED,
            launch_b32_zcontract(b->b32_inst, b->b32_ztile_inst, b->b32_ztile_base, b->n_ztiles, b->b32_R, X,
@@ -2728,10 +2741,7 @@ void batch_fit32(mfa_batch* b, const float* q) {
     // one step of iterative refinement for the badly conditioned instances:
     // project r = q - N P32, solve, add the correction
     cudaMemsetAsync(b->b32_dX, 0, (size_t)ncp * sizeof(ff), h->stream);
-    TRACED(h, TR_REFINE_DATA, for (int c = 0; c < 2; ++c) launch_b32(B32_REFINE, b->b32_inst, b->b32_fitems,
-                                                                       b->ffirst[c], b->caps[c], q, b->b32_P32,
-                                                                       b->b32_dX, b->b32_R, b->b32_Z, nullptr,
-                                                                       h->stream));
+    TRACED(h, TR_REFINE_DATA, b32_pass(b, B32_REFINE, b->b32_fitems, b->ffirst, q, b->b32_dX, nullptr));
     if (b->n_ftiles)
       TRACED(h, TR_PROJECT_REDUCED,
              launch_b32_zcontract(b->b32_inst, b->b32_ftile_inst, b->b32_ftile_base, b->n_ftiles, b->b32_R,
@@ -3591,10 +3601,8 @@ int mfa_batch_residual(mfa_handle* h, const mfa_batch* bc, const void* q, int q_
   if (rc == MFA_OK && e == cudaSuccess && b->prec == MFA_PREC_FP32 && q_dtype != MFA_F32) rc = MFA_ERR_UNSUPPORTED;
   if (rc == MFA_OK && e == cudaSuccess) {
     if (b->prec == MFA_PREC_FP32) {
-      TRACED(h, TR_RESIDUAL, for (int c = 0; c < 2; ++c) launch_b32(B32_RESIDUAL, b->b32_inst, b->b32_pitems,
-                                                                     b->pfirst[c], b->caps[c], (const float*)q,
-                                                                     b->b32_P32, nullptr, nullptr, nullptr,
-                                                                     b->b32_part, h->stream));
+      TRACED(h, TR_RESIDUAL, b32_pass(b, B32_RESIDUAL, b->b32_pitems, b->pfirst, (const float*)q, nullptr,
+                                      b->b32_part));
       TRACED(h, TR_REDUCE, launch_b32_reduce(b->b32_rfirst, b->count, b->b32_part, (double*)res, h->stream));
     } else if (b->prec == MFA_PREC_FP64)
       rc = q_dtype == MFA_F64 ? batch_residual_into<double, double>(b, (const double*)q, (double*)res)

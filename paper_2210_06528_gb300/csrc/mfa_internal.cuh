@@ -285,8 +285,11 @@ size_t b32_smem_bytes(const B32Caps& cap, int mode);
 //  B32_PROJECT: N^T q into X (2-D, 1-D) or R (3-D, xy-reduced planes);
 //  B32_REFINE: the same for r = q - N P32 (dX in X);
 //  B32_RESIDUAL: per item sum of E^2 and max |E|, E = q - N P32, in part.
+// With sides (nsides > 0), the launches of successive degrees go to
+// sides[(*next_side)++ % nsides] instead of st (the caller forks and joins).
 void launch_b32(int mode, const B32Inst* insts, const B32Item* items, const int* first, const B32Caps* caps,
-                const float* Q, const float* P32, ff* X, float* R, float* Z, double* part, cudaStream_t st);
+                const float* Q, const float* P32, ff* X, float* R, float* Z, double* part, cudaStream_t st,
+                const cudaStream_t* sides = nullptr, int nsides = 0, int* next_side = nullptr);
 void launch_b32_add(ff* X, const ff* dX, long long n, cudaStream_t st);
 void launch_b32_zcontract(const B32Inst* insts, const int* tile_inst, const long long* tile_base, int ntiles,
                           const float* R, ff* X, cudaStream_t st);
