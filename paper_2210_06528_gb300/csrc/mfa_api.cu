@@ -3548,14 +3548,24 @@ namespace {
 template <typename T, typename TQ>
 int batch_residual_into(mfa_batch* b, const TQ* q, double* out) {
   mfa_handle* h = b->h;
-  size_t need = 0;
-  for (mfa_model* md : b->groups)
-    need = std::max<size_t>(need, (size_t)(md->decS1 + md->decS2) * sizeof(T) +
-                                      2 * (size_t)md->tm_dec[md->dim - 1].ntiles * sizeof(double) + 64);
-  int rc = ensure_ws(h, need);
+  // every group its own workspace region, so that the groups run side by side
+  const size_t ng = b->groups.size();
+  std::vector<size_t> woff(ng + 1, 0);
+  for (size_t g = 0; g < ng; ++g) {
+    const mfa_model* md = b->groups[g];
+    const size_t sz = (size_t)(md->decS1 + md->decS2) * sizeof(T) +
+                      2 * (size_t)md->tm_dec[md->dim - 1].ntiles * sizeof(double) + 64;
+    woff[g + 1] = woff[g] + ((sz + 255) & ~(size_t)255);
+  }
+  int rc = ensure_ws(h, woff[ng]);
   if (rc != MFA_OK) return rc;
-  for (mfa_model* md : b->groups) {
-    T* s1 = (T*)h->ws;
+  const int nsd = batch_sides(b);
+  cudaStream_t main = h->stream;
+  if (nsd > 1) batch_fork(b);
+  for (size_t g = 0; g < ng; ++g) {
+    mfa_model* md = b->groups[g];
+    if (nsd > 1) h->stream = b->side[g % nsd];
+    T* s1 = (T*)((char*)h->ws + woff[g]);
     T* s2 = s1 + md->decS1;
     double* tpart = (double*)(((uintptr_t)(s2 + md->decS2) + 15) & ~(uintptr_t)15);
     const int ns = md->nsub, d = md->dim;
@@ -3572,6 +3582,8 @@ int batch_residual_into(mfa_batch* b, const TQ* q, double* out) {
              (launch_expand_residual_tiles<T, TQ>(md->L, d - 1, op, in, q, md->tm_dec[d - 1], tpart, md->res_first,
                                                   md->res_id, ns, out, h->stream)));
   }
+  h->stream = main;
+  if (nsd > 1) batch_join(b);
   return MFA_OK;
 }
 }  // namespace
