@@ -1699,8 +1699,13 @@ int mfa_schwarz_iterate(mfa_handle* h, mfa_model* md, int32_t max_iters, double 
   const bool stall = tol_rms_stall > 0 && max_iters > 0;
   if (stall && (!md->q_src || md->batch)) return MFA_ERR_ARG;  // the stall test decodes against the encoded data
   DeviceGuard g(h->device);
-  int status = read_status(h);  // surfaces encode-time device errors
-  if (status < 0) return status;
+  // encode-time device errors surface here, or with the first iteration's
+  // metrics (one read-back per iteration carries both)
+  int status = 0;
+  if (max_iters == 0 || stall) {
+    status = read_status(h);
+    if (status < 0) return status;
+  }
   const long long npts = (long long)md->axh[0].M * md->axh[1].M * md->axh[2].M;
   double res[4] = {0, 0, 0, 0};
   double rms_prev = 0.0;
@@ -1716,14 +1721,27 @@ int mfa_schwarz_iterate(mfa_handle* h, mfa_model* md, int32_t max_iters, double 
       run_step<double>(md);
     else
       run_step<ff>(md);
+    // the metrics and the status word in one read-back
     cudaError_t e = cudaMemcpyAsync(h->h_pinned, h->d_metrics, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                     h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->h_pinned + 4, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_status(e);
     unsigned long long bits[3];
     std::memcpy(bits, h->h_pinned, sizeof(bits));
     double v[3];
     std::memcpy(v, bits, sizeof(v));
+    int st = 0;
+    std::memcpy(&st, h->h_pinned + 4, sizeof(int));
+    if (st != 0) {
+      cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream);
+      if (st < 0) {
+        status = st;
+        rc = st;
+        break;
+      }
+    }
     const double dP = v[1] > 0 ? v[0] / v[1] : 0.0;
     md->iters++;
     if (md->iters > 1 && dP > md->last_dP && dP > 0)
@@ -1755,8 +1773,10 @@ int mfa_schwarz_iterate(mfa_handle* h, mfa_model* md, int32_t max_iters, double 
     }
   }
   if (max_iters == 0) rc = MFA_OK;
-  status = read_status(h);
-  if (status < 0) rc = status;
+  if (stall && status >= 0) {  // the residual decodes after the last read-back
+    status = read_status(h);
+    if (status < 0) rc = status;
+  }
   if (rep) {
     rep->iters = md->iters;
     rep->status = rc;
