@@ -261,9 +261,11 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
         const float* dra = MODE != B32_PROJECT ? L.dzy + ia * n0s : nullptr;
         const float* drb = MODE != B32_PROJECT ? L.dzy + ib * n0s : nullptr;
         const float m2 = two ? 1.f : 0.f;  // residual: row b counted once
-        float aa[P + 1], ab[P + 1];
+        // accumulators of rows a and b side by side: paired FP32 instructions
+        // (per lane the same rounding as fmaf)
+        float2 acc[P + 1];
 #pragma unroll
-        for (int c = 0; c <= P; ++c) aa[c] = ab[c] = 0.f;
+        for (int c = 0; c <= P; ++c) acc[c] = make_float2(0.f, 0.f);
         int k = T.sx[ga];
         // 32-bit shared addresses of point k of rows a and b and of its basis values
         unsigned qa_at = smem_u32(pa) + 4u * k;
@@ -271,13 +273,10 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
         unsigned b_at = smem_u32(T.vb) + 4u * W * k;
         for (int s = ga; s < gb; ++s) {
           const int ke = T.sx[s + 1];
-          float da[P + 1], db[P + 1];
+          float2 d2[P + 1];
           if (MODE != B32_PROJECT) {
 #pragma unroll
-            for (int c = 0; c <= P; ++c) {
-              da[c] = dra[s + c];
-              db[c] = drb[s + c];
-            }
+            for (int c = 0; c <= P; ++c) d2[c] = make_float2(dra[s + c], drb[s + c]);
           }
           for (; k < ke; ++k, qa_at += 4u, b_at += 4u * W) {
             float qa = lds(qa_at), qb = lds(qa_at + qb_off);
@@ -295,14 +294,11 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
               b[7 % W] = b1.w;
             }
             if (MODE != B32_PROJECT) {
-              float va = 0.f, vb2 = 0.f;
+              float2 v2 = make_float2(0.f, 0.f);
 #pragma unroll
-              for (int c = 0; c <= P; ++c) {
-                va = fmaf(b[c], da[c], va);
-                vb2 = fmaf(b[c], db[c], vb2);
-              }
-              qa -= va;
-              qb -= vb2;
+              for (int c = 0; c <= P; ++c) v2 = __ffma2_rn(make_float2(b[c], b[c]), d2[c], v2);
+              qa -= v2.x;
+              qb -= v2.y;
               if (MODE == B32_RESIDUAL) {
                 const float eb = qb * m2;
                 s2 = fmaf(qa, qa, s2);
@@ -311,39 +307,34 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
               }
             }
             if (MODE != B32_RESIDUAL) {
+              const float2 q2 = make_float2(qa, qb);
 #pragma unroll
-              for (int c = 0; c <= P; ++c) {
-                aa[c] = fmaf(b[c], qa, aa[c]);
-                ab[c] = fmaf(b[c], qb, ab[c]);
-              }
+              for (int c = 0; c <= P; ++c) acc[c] = __ffma2_rn(make_float2(b[c], b[c]), q2, acc[c]);
             }
           }
           if (MODE != B32_RESIDUAL) {
             // complete, or this segment's part of a straddling control point
-            xa[s] = aa[0];
-            if (two) xb[s] = ab[0];
+            xa[s] = acc[0].x;
+            if (two) xb[s] = acc[0].y;
 #pragma unroll
-            for (int c = 0; c < P; ++c) {
-              aa[c] = aa[c + 1];
-              ab[c] = ab[c + 1];
-            }
-            aa[P] = ab[P] = 0.f;
+            for (int c = 0; c < P; ++c) acc[c] = acc[c + 1];
+            acc[P] = make_float2(0.f, 0.f);
           }
         }
         if (MODE != B32_RESIDUAL) {
           if (gb == ns0) {
 #pragma unroll
             for (int c = 0; c < P; ++c) {
-              xa[ns0 + c] = aa[c];
-              if (two) xb[ns0 + c] = ab[c];
+              xa[ns0 + c] = acc[c].x;
+              if (two) xb[ns0 + c] = acc[c].y;
             }
           } else {  // S > 1: one task per lane (row pairs x S <= 32)
             have_left = true;
             left2 = two;
 #pragma unroll
             for (int c = 0; c < P; ++c) {
-              la[c] = aa[c];
-              lb[c] = ab[c];
+              la[c] = acc[c].x;
+              lb[c] = acc[c].y;
             }
             lpa = ia * n0s + gb;
             lpb = ib * n0s + gb;
