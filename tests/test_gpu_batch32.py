@@ -166,3 +166,44 @@ def test_fp32_batch_refuses_what_it_does_not_cover():
         assert e.value.code == mfa.MFA_ERR_UNSUPPORTED
     finally:
         h.close()
+
+
+def _grid_field(npts, rng):
+    x = [np.linspace(-3, 3, m) for m in npts]
+    grids = np.meshgrid(*reversed(x), indexing="ij")
+    f = np.ones(grids[0].shape)
+    for g in grids:
+        f = f * np.sinc(g / 2)
+    return (f + 0.05 * rng.standard_normal(f.shape)).astype(np.float32).ravel()
+
+
+def test_fp32_batch_edge_shapes():
+    """Degrees 1, 6 and 7; the longest row the staging takes (1023 points);
+    256 x control points (eight column groups of open y control points);
+    single-span axes; interpolation (as many points as control points);
+    small 3-D planes several to a chunk; a 2-D instance whose y spans split
+    over warps with the fewest spans per warp (p)."""
+    rng = np.random.default_rng(8)
+    shapes = [
+        (1, (1023,), 3, None), (2, (1023, 9), 4, None), (2, (1023, 12), 2, [253, 3]),
+        (1, (60,), 1, None), (2, (40, 37), 6, None), (3, (30, 28, 26), 7, None),
+        (2, (16, 16), 5, [1, 1]), (3, (12, 10, 40), 2, None), (2, (9, 9), 3, [6, 6]),
+        (2, (200, 300), 5, [5 * 8, 5 * 8]), (1, (7,), 6, [1]),
+    ]
+    specs, chunks, off = [], [], 0
+    for d, npts, p, ns in shapes:
+        n = int(np.prod(npts))
+        chunks.append(_grid_field(npts, rng))
+        nspans = ns if ns is not None else [max(p + 1, m // 4) - p for m in npts]
+        specs.append({"dim": d, "degree": p, "npts": list(npts), "nspans": list(nspans), "q_offset": off})
+        off += n
+    data = np.concatenate(chunks)
+    h = mfa.Handle(0)
+    try:
+        b = h.encode_batch(specs, _dev(data), FP32)
+        _check_batch(specs, data, b)
+        b.refit(_dev(data))  # autotune + captured graph on the same shapes
+        _check_batch(specs, data, b)
+        b.free()
+    finally:
+        h.close()
