@@ -817,9 +817,10 @@ __global__ void __launch_bounds__(kDecThreads, (P >= 4 ? 3 : 4)) k_decode3d(Layo
   static_assert(sizeof(V) == sizeof(ff), "float-float control points");
   constexpr int W = P + 1;
   extern __shared__ __align__(128) unsigned char smem[];
-  const int ntx = (int)((L.M[0] + kDecTX - 1) / kDecTX), nty = (int)((L.M[1] + kDecTY - 1) / kDecTY);
-  const int tile = blockIdx.x;
-  const int tx = tile % ntx, ty = (tile / ntx) % nty, tz = tile / (ntx * nty);
+  // one CTA per tile on a 3-D grid of tiles; the linear tile index names the
+  // tile's residual partials
+  const int tx = blockIdx.x, ty = blockIdx.y, tz = blockIdx.z;
+  const int tile = tx + gridDim.x * (ty + gridDim.y * tz);
   const int x0 = tx * kDecTX, y0 = ty * kDecTY, z0 = tz * kDecTZ;
   const int x1 = min(x0 + kDecTX, (int)L.M[0]), y1 = min(y0 + kDecTY, (int)L.M[1]), z1 = min(z0 + kDecTZ, (int)L.M[2]);
   const int nx = x1 - x0, ny = y1 - y0, nz = z1 - z0;
@@ -885,8 +886,10 @@ __global__ void __launch_bounds__(kDecThreads, (P >= 4 ? 3 : 4)) k_decode3d(Layo
   // (z, y) rows of the block
   const long long n0 = L.ncp[0], n01 = L.ncp[0] * L.ncp[1];
   const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;  // 8 groups of 32
+  const bool small_rows = ncz * ncy < 1024 && ncy <= 128;  // div_small's range
+  const unsigned rcy = div_magic(ncy);
   for (int row = grp; row < ncz * ncy; row += kDecThreads / 32) {
-    const int cz = row / ncy, cy = row - cz * ncy;
+    const int cz = small_rows ? div_small(row, rcy) : row / ncy, cy = row - cz * ncy;
     const ff* src = Pf + (long long)cx0 + n0 * (cy0 + cy) + n01 * (cz0 + cz);
     for (int cx = lane; cx < ncxp; cx += 32) {
       const ff v = cx < ncx ? src[cx] : ff(0.f, 0.f);
@@ -990,13 +993,16 @@ __global__ void __launch_bounds__(kDecThreads, (P >= 4 ? 3 : 4)) k_decode3d(Layo
   float s2 = 0.f, emax = 0.f, qmin = INFINITY, qmax = -INFINITY;
   const long long M0 = L.M[0], M01 = L.M[0] * L.M[1];
   const int xt = threadIdx.x & (kDecTX - 1), yt = threadIdx.x / kDecTX;
-  auto emit = [&](const ff2& acc, int z) {
+  // offset of this thread's point (x0 + xt, y0 + yt, z0 + z) in the grid:
+  // a base at z = 0, plus a plane step per z and kDecYH rows for the second row
+  const long long g0 = (long long)(x0 + xt) + M0 * (y0 + yt) + M01 * z0, gy = M0 * kDecYH;
+  auto emit = [&](const ff2& acc, int z, long long gz) {
 #pragma unroll
     for (int hh = 0; hh < 2; ++hh) {
       const int y = yt + hh * kDecYH;
       if (y >= ny) continue;
       const ff v = hh ? fast_two_sum(acc.hi.y, acc.lo.y) : fast_two_sum(acc.hi.x, acc.lo.x);
-      const long long g = (long long)(x0 + xt) + M0 * (y0 + y) + M01 * (z0 + z);
+      const long long g = hh ? gz + gy : gz;
       if constexpr (RESID) {
         const float q = (float)Q[g];
         // E = q - (hi + lo): q - hi is exact when the fit is close (Sterbenz)
@@ -1024,7 +1030,8 @@ __global__ void __launch_bounds__(kDecThreads, (P >= 4 ? 3 : 4)) k_decode3d(Layo
       bl[r] = dup2(nxl[xt * W + r]);
     }
     const int sxx = sx[xt];
-    for (int z = 0; z < nz; z += 2) {
+    long long gz = g0;  // offset at plane z
+    for (int z = 0; z < nz; z += 2, gz += 2 * M01) {
       const int z2 = min(z + 1, nz - 1);
       const float4* sa = Ty + (z * kDecYH + yt) * ncx + sxx;
       const float4* sb = Ty + (z2 * kDecYH + yt) * ncx + sxx;
@@ -1035,8 +1042,8 @@ __global__ void __launch_bounds__(kDecThreads, (P >= 4 ? 3 : 4)) k_decode3d(Layo
         ff2_add_v(A, bh[r], bn[r], bl[r], make_float2(ta.x, ta.y), make_float2(ta.z, ta.w));
         ff2_add_v(B, bh[r], bn[r], bl[r], make_float2(tb.x, tb.y), make_float2(tb.z, tb.w));
       }
-      emit(A, z);
-      if (z + 1 < nz) emit(B, z + 1);
+      emit(A, z, gz);
+      if (z + 1 < nz) emit(B, z + 1, gz + M01);
     }
   }
   if constexpr (RESID) {
@@ -1104,10 +1111,13 @@ bool launch_decode3d(const LayoutDev& L, const V* P, const TQ* Q, TOut* out, dou
   if (L.dim != 3 || L.ax[1].p != p || L.ax[2].p != p) return false;
   const int ncx = tile_cps(L.ax[0], kDecTX), ncy = tile_cps(L.ax[1], kDecTY), ncz = tile_cps(L.ax[2], kDecTZ);
   const long long tiles = decode3d_tiles(L);
-  if (tiles > (1LL << 31) - 1) return false;
+  const long long ntx = (L.M[0] + kDecTX - 1) / kDecTX, nty = (L.M[1] + kDecTY - 1) / kDecTY,
+                  ntz = (L.M[2] + kDecTZ - 1) / kDecTZ;
+  if (tiles > (1LL << 31) - 1 || ntx > INT32_MAX || nty > 65535 || ntz > 65535) return false;
+  const dim3 grid((unsigned)ntx, (unsigned)nty, (unsigned)ntz);
   auto go = [&](auto kernel, size_t smem) {
     ensure_smem(kernel, smem);
-    kernel<<<(unsigned)tiles, kDecThreads, smem, st>>>(L, P, Q, out, partials);
+    kernel<<<grid, kDecThreads, smem, st>>>(L, P, Q, out, partials);
   };
 #define MFA_DEC_CASE(PP)                                                    \
   case PP: {                                                                \
