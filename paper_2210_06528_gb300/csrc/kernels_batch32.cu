@@ -146,15 +146,21 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
   };
   // y emission: 3-D xy-reduced planes; 2-D control points, or the partial
   // sums at this warp's boundary spans sa / sb when warps split the instance
-  auto emit = [&](int kk2, int j1, int j0, float v) {
-    if (D.dim == 3) {
-      R[D.r_off + ((long long)kk2 * n1 + j1) * n0 + j0] = v;
+  // (descriptor fields in registers: D lives in shared memory, and stores
+  // through these pointers would otherwise make every emission reload it)
+  const int dim = D.dim;
+  float* const Rb = dim == 3 ? R + D.r_off : nullptr;
+  float* const Zb = dim == 2 ? Z + it.z_off : nullptr;
+  ff* const Xb = MODE != B32_RESIDUAL ? X + D.x_off : nullptr;
+  auto emit = [=](int kk2, int j1, int j0, float v) {
+    if (dim == 3) {
+      Rb[((long long)kk2 * n1 + j1) * n0 + j0] = v;
     } else if (sa > 0 && j1 < sa + P) {
-      Z[it.z_off + ((long long)(2 * w) * P + (j1 - sa)) * n0 + j0] = v;
+      Zb[(2 * w * P + (j1 - sa)) * n0 + j0] = v;
     } else if (sb < ns1 && j1 >= sb) {
-      Z[it.z_off + ((long long)(2 * w + 1) * P + (j1 - sb)) * n0 + j0] = v;
+      Zb[((2 * w + 1) * P + (j1 - sb)) * n0 + j0] = v;
     } else {
-      X[D.x_off + (long long)j1 * n0 + j0] = ff(v);
+      Xb[(long long)j1 * n0 + j0] = ff(v);
     }
   };
   auto yvals = [&](int kk1, float* v) {
@@ -371,7 +377,8 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
 #pragma unroll
           for (int c = 0; c <= P; ++c) a[c] = 0.f;
           int cc = 0;
-          for (int kk = 0; kk < M1; ++kk) {
+          for (int kk = 0; kk < M1;) {
+            // the rows of span sr, after the control points before it are emitted
             const int sr = T.ysp[kk];
             while (cc < sr) {
               if (ok) emit(k2 + pl, cc, j0, a[0]);
@@ -380,11 +387,15 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
               a[P] = 0.f;
               ++cc;
             }
-            const float x = xc[kk * n0s];
-            float v[W];
-            yvals(kk, v);
+            const int ke = max(kk + 1, T.sy[sr + 1]);
+#pragma unroll 2
+            for (; kk < ke; ++kk) {
+              const float x = xc[kk * n0s];
+              float v[W];
+              yvals(kk, v);
 #pragma unroll
-            for (int c = 0; c <= P; ++c) a[c] = fmaf(v[c], x, a[c]);
+              for (int c = 0; c <= P; ++c) a[c] = fmaf(v[c], x, a[c]);
+            }
           }
           if (ok) {
 #pragma unroll
@@ -404,7 +415,7 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
           for (int c = 0; c <= P; ++c)
             a[c] = NC == 1 ? ay[c] : (fresh ? 0.f : L.ring[(m * (P + 1) + c) * 32 + lane]);
           cc = cur;
-          for (int rr = 0; rr < rc; ++rr) {
+          for (int rr = 0; rr < rc;) {
             const int sr = T.ysp[k1 + rr];
             while (cc < sr) {
               if (ok) emit(k2, cc, j0, a[0]);
@@ -413,11 +424,15 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
               a[P] = 0.f;
               ++cc;
             }
-            const float x = ok ? L.xr[rr * n0s + j0] : 0.f;
-            float v[W];
-            yvals(k1 + rr, v);
+            const int re = min(rc, max(rr + 1, T.sy[sr + 1] - k1));
+#pragma unroll 2
+            for (; rr < re; ++rr) {
+              const float x = ok ? L.xr[rr * n0s + j0] : 0.f;
+              float v[W];
+              yvals(k1 + rr, v);
 #pragma unroll
-            for (int c = 0; c <= P; ++c) a[c] = fmaf(v[c], x, a[c]);
+              for (int c = 0; c <= P; ++c) a[c] = fmaf(v[c], x, a[c]);
+            }
           }
           if (pend) {
 #pragma unroll
@@ -447,12 +462,12 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
   }
 }
 
+// (refinement at degree >= 4 needs more than 128 registers: one CTA per SM)
 template <int P, int MODE>
-__global__ void __launch_bounds__(kB32Threads, MODE == B32_REFINE ? 1 : 2) k_b32(const B32Inst* __restrict__ insts,
-                                                        const B32Item* __restrict__ items, int base, B32Caps cap,
-                                                        const float* __restrict__ Q, const float* __restrict__ P32,
-                                                        ff* __restrict__ X, float* __restrict__ R,
-                                                        float* __restrict__ Z, double* __restrict__ part) {
+__global__ void __launch_bounds__(kB32Threads, MODE == B32_REFINE && P >= 4 ? 1 : 2)
+    k_b32(const B32Inst* __restrict__ insts, const B32Item* __restrict__ items, int base, B32Caps cap,
+          const float* __restrict__ Q, const float* __restrict__ P32, ff* __restrict__ X, float* __restrict__ R,
+          float* __restrict__ Z, double* __restrict__ part) {
   extern __shared__ __align__(16) float sm[];
   __shared__ double red[kB32Threads / 32][2];
   __shared__ B32Inst Ds;
