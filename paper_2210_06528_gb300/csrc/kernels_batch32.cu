@@ -25,9 +25,10 @@
 //  for the solves); 3-D instances write their xy-reduced planes and a second
 //  kernel contracts z.
 //  Refinement projects r = q - (N P32) instead of q, P32 the FP32 copy of
-//  the control points: per chunk the z- and y-expanded control points of its
-//  rows, then every lane decodes its points in the same walk (one step of
-//  iterative refinement; its rounding is relative to |r|).
+//  the control points: per chunk the y-expanded control points of its rows
+//  (from the z-expanded planes DZ of a 3-D instance, which k_b32_zexpand
+//  writes beforehand), then every lane decodes its points in the same walk
+//  (one step of iterative refinement; its rounding is relative to |r|).
 //
 // Residual.  The same walk with the decode only: E = q - value, sum of E^2
 // and max |E| per lane (FP32), per warp and CTA in FP64 in fixed order.
@@ -81,7 +82,7 @@ __device__ __forceinline__ unsigned fmagic(unsigned d) { return d <= 1 ? 0u : 0x
 __host__ __device__ inline int b32_warp_floats(const B32Caps& c, int mode) {
   int f = 2 * r4(c.stage);  // staged rows, two buffers
   if (mode != B32_RESIDUAL) f += r4(c.xr) + r4(c.ring);
-  if (mode != B32_PROJECT) f += r4(c.xr) + r4(c.dz);
+  if (mode != B32_PROJECT) f += r4(c.xr);
   return f;
 }
 // Floats of the CTA's tables: x basis values (W per point), x span starts, y
@@ -95,7 +96,6 @@ struct B32Warp {
   float* xr;     // [row of the chunk][n0 | 1]: x-reduced rows
   float* ring;   // streamed planes with n0 > 32: open y control points between chunks
   float* dzy;    // [row of the chunk][n0 | 1]: z- and y-expanded control points
-  float* dz;     // [plane of the chunk][n1][n0]: z-expanded control points
 };
 
 struct B32Tables {
@@ -111,8 +111,8 @@ template <int P, int MODE>
 __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, const B32Warp& L, const B32Tables& T,
                                          int w, int ra, int rb, int sa, int sb, int cap_stage,
                                          const float* __restrict__ Q, const float* __restrict__ P32,
-                                         ff* __restrict__ X, float* __restrict__ R, float* __restrict__ Z, float& s2,
-                                         float& emax) {
+                                         const float* __restrict__ DZ, ff* __restrict__ X, float* __restrict__ R,
+                                         float* __restrict__ Z, float& s2, float& emax) {
   constexpr int W = P < 4 ? 4 : 8;  // basis values per point / row in shared memory (padded)
   const int lane = threadIdx.x & 31;
   const int M0 = D.M[0], M1 = D.M[1], n0 = D.n[0], n1 = D.n[1];
@@ -126,7 +126,9 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
   const unsigned mgS = fmagic(S);
   const bool whole = D.mode == 0;
   const int plane_cp = n1 * n0;
-  const float* Pi = MODE != B32_PROJECT ? P32 + D.x_off : nullptr;
+  // control points the decode expands along y: the instance's own (2-D), or
+  // its z-expanded planes (3-D)
+  const float* Pi = MODE == B32_PROJECT ? nullptr : D.dim == 3 ? DZ + D.r_off : P32 + D.x_off;
 
   int row = ra;
   int k2 = row / M1, k1 = row - k2 * M1;
@@ -187,7 +189,6 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
   float ay[P + 1];
 #pragma unroll
   for (int c = 0; c <= P; ++c) ay[c] = 0.f;
-  int dz_k2 = -1;  // plane whose z-expansion is in dz (streamed planes)
 
   while (row < rb) {
     const float* stage = L.stage + buf * scap;
@@ -209,38 +210,33 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
     }
     __syncwarp();
     if (MODE != B32_PROJECT) {
-      // z- and y-expanded control points of the chunk's rows
-      const int npl = whole ? (int)fdiv(rc, M1, mg1) : 1;
-      if (D.dim == 3 && (whole || dz_k2 != k2)) {
-        for (int pl = 0; pl < npl; ++pl) {
-          const long long gk = (long long)D.kbase[2] + k2 + pl;
-          const int sz = __ldg(D.span[2] + gk) - D.cbase[2];
-          float vz[P + 1];
+      // z- and y-expanded control points of the chunk's rows, K per lane at a
+      // time: their loads (from L2) all in flight before the first sum
+      constexpr int K = P <= 3 ? 4 : 2;
+      const int ne = rc * n0;
+      for (int t0 = 0; t0 < ne; t0 += 32 * K) {
+        float g[K][P + 1];
+        int kk[K], at[K];
 #pragma unroll
-          for (int c = 0; c <= P; ++c) vz[c] = __ldg(D.vals[2] + gk * (P + 1) + c);
-          const float* src = Pi + (long long)sz * plane_cp;
-          for (int e = lane; e < plane_cp; e += 32) {
-            float a = 0.f;
+        for (int u = 0; u < K; ++u) {
+          const int t = min(t0 + 32 * u + lane, ne - 1);
+          const int rr = (int)fdiv(t, n0, mgn0), j0 = t - rr * n0;
+          const int pl = whole ? (int)fdiv(rr, M1, mg1) : 0;
+          kk[u] = whole ? rr - pl * M1 : k1 + rr;
+          at[u] = rr * n0s + j0;
+          const float* src = (D.dim == 3 ? Pi + (long long)(k2 + pl) * plane_cp : Pi) + T.ysp[kk[u]] * n0 + j0;
 #pragma unroll
-            for (int c = 0; c <= P; ++c) a = fmaf(vz[c], __ldg(src + (long long)c * plane_cp + e), a);
-            L.dz[pl * plane_cp + e] = a;
-          }
+          for (int c = 0; c <= P; ++c) g[u][c] = c <= py ? __ldg(src + c * n0) : 0.f;
         }
-        dz_k2 = k2;
-        __syncwarp();
-      }
-      for (int t = lane; t < rc * n0; t += 32) {
-        const int rr = (int)fdiv(t, n0, mgn0), j0 = t - rr * n0;
-        const int pl = whole ? (int)fdiv(rr, M1, mg1) : 0;
-        const int kk1 = whole ? rr - pl * M1 : k1 + rr;
-        const float* src = D.dim == 3 ? L.dz + pl * plane_cp : Pi;
-        const float* v = T.vy + kk1 * W;
-        const int s1 = T.ysp[kk1];
-        float a = 0.f;
 #pragma unroll
-        for (int c = 0; c <= P; ++c)
-          if (c <= py) a = fmaf(v[c], src[(s1 + c) * n0 + j0], a);
-        L.dzy[rr * n0s + j0] = a;
+        for (int u = 0; u < K; ++u) {
+          const float* v = T.vy + kk[u] * W;
+          float a = 0.f;
+#pragma unroll
+          for (int c = 0; c <= P; ++c)
+            if (c <= py) a = fmaf(v[c], g[u][c], a);
+          if (t0 + 32 * u + lane < ne) L.dzy[at[u]] = a;
+        }
       }
       __syncwarp();
     }
@@ -462,12 +458,12 @@ __device__ __forceinline__ void b32_warp(const B32Inst& D, const B32Item& it, co
   }
 }
 
-// (refinement at degree >= 4 needs more than 128 registers: one CTA per SM)
+// (refinement at degree >= 6 needs well over 128 registers: one CTA per SM)
 template <int P, int MODE>
-__global__ void __launch_bounds__(kB32Threads, MODE == B32_REFINE && P >= 4 ? 1 : 2)
+__global__ void __launch_bounds__(kB32Threads, MODE == B32_REFINE && P >= 6 ? 1 : 2)
     k_b32(const B32Inst* __restrict__ insts, const B32Item* __restrict__ items, int base, B32Caps cap,
-          const float* __restrict__ Q, const float* __restrict__ P32, ff* __restrict__ X, float* __restrict__ R,
-          float* __restrict__ Z, double* __restrict__ part) {
+          const float* __restrict__ Q, const float* __restrict__ P32, const float* __restrict__ DZ,
+          ff* __restrict__ X, float* __restrict__ R, float* __restrict__ Z, double* __restrict__ part) {
   extern __shared__ __align__(16) float sm[];
   __shared__ double red[kB32Threads / 32][2];
   __shared__ B32Inst Ds;
@@ -500,8 +496,6 @@ __global__ void __launch_bounds__(kB32Threads, MODE == B32_REFINE && P >= 4 ? 1 
   }
   if (MODE != B32_PROJECT) {
     L.dzy = f;
-    f += r4(cap.xr);
-    L.dz = f;
   }
   {
     const float* v0 = D.vals[0] + (long long)D.kbase[0] * (P + 1);
@@ -543,7 +537,7 @@ __global__ void __launch_bounds__(kB32Threads, MODE == B32_REFINE && P >= 4 ? 1 
     }
   }
   float s2 = 0.f, emax = 0.f;
-  if (ra < rb) b32_warp<P, MODE>(D, it, L, T, w, ra, rb, sa, sb, cap.stage, Q, P32, X, R, Z, s2, emax);
+  if (ra < rb) b32_warp<P, MODE>(D, it, L, T, w, ra, rb, sa, sb, cap.stage, Q, P32, DZ, X, R, Z, s2, emax);
   if (MODE == B32_RESIDUAL) {
     double a = s2, b = emax;
     for (int o = 16; o > 0; o >>= 1) {
@@ -581,16 +575,15 @@ __global__ void __launch_bounds__(kB32Threads, MODE == B32_REFINE && P >= 4 ? 1 
 
 template <int MODE>
 void launch_mode(const B32Inst* insts, const B32Item* items, const int* first, const B32Caps* caps, const float* Q,
-                 const float* P32, ff* X, float* R, float* Z, double* part, cudaStream_t st, const cudaStream_t* sides,
-                 int nsides, int& k) {
-#define MFA_B32_LAUNCH(PP)                                                                                   \
-  if (first[PP] > first[PP - 1]) {                                                                          \
-    const size_t smem = b32_smem_bytes(caps[PP], MODE);                                                     \
-    ensure_smem(k_b32<PP, MODE>, smem);                                                                     \
-    cudaStream_t s_ = nsides > 0 ? sides[k++ % nsides] : st;                                                \
-    k_b32<PP, MODE><<<first[PP] - first[PP - 1], kB32Threads, smem, s_>>>(insts, items + first[PP - 1],      \
-                                                                          first[PP - 1], caps[PP], Q, P32, X, \
-                                                                          R, Z, part);                      \
+                 const float* P32, const float* DZ, ff* X, float* R, float* Z, double* part, cudaStream_t st,
+                 const cudaStream_t* sides, int nsides, int& k) {
+#define MFA_B32_LAUNCH(PP)                                                                            \
+  if (first[PP] > first[PP - 1]) {                                                                   \
+    const size_t smem = b32_smem_bytes(caps[PP], MODE);                                              \
+    ensure_smem(k_b32<PP, MODE>, smem);                                                              \
+    cudaStream_t s_ = nsides > 0 ? sides[k++ % nsides] : st;                                         \
+    k_b32<PP, MODE><<<first[PP] - first[PP - 1], kB32Threads, smem, s_>>>(                           \
+        insts, items + first[PP - 1], first[PP - 1], caps[PP], Q, P32, DZ, X, R, Z, part);           \
   }
   MFA_B32_LAUNCH(1) MFA_B32_LAUNCH(2) MFA_B32_LAUNCH(3) MFA_B32_LAUNCH(4) MFA_B32_LAUNCH(5) MFA_B32_LAUNCH(6)
   MFA_B32_LAUNCH(7)
@@ -604,17 +597,47 @@ size_t b32_smem_bytes(const B32Caps& cap, int mode) {
 }
 
 void launch_b32(int mode, const B32Inst* insts, const B32Item* items, const int* first, const B32Caps* caps,
-                const float* Q, const float* P32, ff* X, float* R, float* Z, double* part, cudaStream_t st,
-                const cudaStream_t* sides, int nsides, int* next_side) {
+                const float* Q, const float* P32, const float* DZ, ff* X, float* R, float* Z, double* part,
+                cudaStream_t st, const cudaStream_t* sides, int nsides, int* next_side) {
   int k0 = next_side ? *next_side : 0;
   int& k = next_side ? *next_side : k0;
   if (mode == B32_PROJECT)
-    launch_mode<B32_PROJECT>(insts, items, first, caps, Q, nullptr, X, R, Z, nullptr, st, sides, nsides, k);
+    launch_mode<B32_PROJECT>(insts, items, first, caps, Q, nullptr, nullptr, X, R, Z, nullptr, st, sides, nsides, k);
   else if (mode == B32_REFINE)
-    launch_mode<B32_REFINE>(insts, items, first, caps, Q, P32, X, R, Z, nullptr, st, sides, nsides, k);
+    launch_mode<B32_REFINE>(insts, items, first, caps, Q, P32, DZ, X, R, Z, nullptr, st, sides, nsides, k);
   else
-    launch_mode<B32_RESIDUAL>(insts, items, first, caps, Q, P32, nullptr, nullptr, nullptr, part, st, sides, nsides,
-                              k);
+    launch_mode<B32_RESIDUAL>(insts, items, first, caps, Q, P32, DZ, nullptr, nullptr, nullptr, part, st, sides,
+                              nsides, k);
+}
+
+// z expansion of the FP32 control points of 3-D instances for the decode of
+// the refinement and the residual: DZ[k2][j1][j0] = sum over c of
+// N_{s+c}(u_{k2}) P32[s + c][j1][j0], s the z span of point k2 (FP32 in c
+// order, as the decode's own expansion would take it), in the layout of R.
+__global__ void __launch_bounds__(256) k_b32_zexpand(const B32Inst* __restrict__ insts,
+                                                     const int* __restrict__ tile_inst,
+                                                     const long long* __restrict__ tile_base,
+                                                     const float* __restrict__ P32, float* __restrict__ DZ) {
+  const B32Inst& D = insts[tile_inst[blockIdx.x]];
+  const long long plane_cp = (long long)D.n[1] * D.n[0];
+  const long long total = (long long)D.M[2] * plane_cp;
+  const long long e = tile_base[blockIdx.x] + threadIdx.x;
+  if (e >= total) return;
+  const long long k2 =
+      total <= 0xffffffffLL ? (long long)((unsigned)e / (unsigned)plane_cp) : e / plane_cp;
+  const long long gk = D.kbase[2] + k2;
+  const int sz = __ldg(D.span[2] + gk) - D.cbase[2];
+  const float* src = P32 + D.x_off + sz * plane_cp + (e - k2 * plane_cp);
+  const float* vz = D.vals[2] + gk * (D.p + 1);
+  float a = 0.f;
+  for (int c = 0; c <= D.p; ++c) a = fmaf(__ldg(vz + c), __ldg(src + c * plane_cp), a);
+  DZ[D.r_off + e] = a;
+}
+
+void launch_b32_zexpand(const B32Inst* insts, const int* tile_inst, const long long* tile_base, int ntiles,
+                        const float* P32, float* DZ, cudaStream_t st) {
+  if (ntiles <= 0) return;
+  k_b32_zexpand<<<ntiles, 256, 0, st>>>(insts, tile_inst, tile_base, P32, DZ);
 }
 
 // X += dX over n float-float values (the refinement's correction of the
@@ -641,7 +664,7 @@ __global__ void __launch_bounds__(256) k_b32_zcontract(const B32Inst* __restrict
                                                        const float* __restrict__ R, ff* __restrict__ X) {
   const B32Inst& D = insts[tile_inst[blockIdx.x]];
   const int n0 = D.n[0], n1 = D.n[1], n2 = D.n[2], p = D.p;
-  const unsigned idx = (unsigned)(tile_base[blockIdx.x] + threadIdx.x);  // < n0 n1 n2 <= 2^20
+  const unsigned idx = (unsigned)(tile_base[blockIdx.x] + threadIdx.x);  // < n0 n1 n2 < 2^31
   if (idx >= (unsigned)(n0 * n1 * n2)) return;
   const unsigned rest = fdiv(idx, n0, fmagic(n0));
   const int j0 = (int)(idx - rest * n0);

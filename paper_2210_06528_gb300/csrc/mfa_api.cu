@@ -2338,6 +2338,14 @@ struct mfa_batch {
   long long* b32_ftile_base = nullptr;
   ff* b32_dX = nullptr;
   int n_fitems = 0, n_ftiles = 0, n_refined = 0;
+  // the decode's z expansion of 3-D instances (all of them, and the refined
+  // ones) into DZ, laid out like R
+  int* b32_etile_inst = nullptr;
+  long long* b32_etile_base = nullptr;
+  int* b32_fetile_inst = nullptr;
+  long long* b32_fetile_base = nullptr;
+  float* b32_DZ = nullptr;
+  int n_etiles = 0, n_fetiles = 0;
   // side streams on which the groups' independent work runs side by side
   // (forked from and joined back into the handle's stream; a captured refit
   // records them as parallel branches)
@@ -2726,7 +2734,7 @@ void b32_pass(mfa_batch* b, int mode, const B32Item* items, int first[2][MFA_MAX
   int k = 0;
   if (ns > 1) batch_fork(b);
   for (int c = 0; c < 2; ++c)
-    launch_b32(mode, b->b32_inst, items, first[c], b->caps[c], q, b->b32_P32, X, b->b32_R, b->b32_Z, part,
+    launch_b32(mode, b->b32_inst, items, first[c], b->caps[c], q, b->b32_P32, b->b32_DZ, X, b->b32_R, b->b32_Z, part,
                h->stream, ns > 1 ? b->side : nullptr, ns > 1 ? ns : 0, &k);
   if (ns > 1) batch_join(b);
 }
@@ -2761,7 +2769,11 @@ void batch_fit32(mfa_batch* b, const float* q) {
     // one step of iterative refinement for the badly conditioned instances:
     // project r = q - N P32, solve, add the correction
     cudaMemsetAsync(b->b32_dX, 0, (size_t)ncp * sizeof(ff), h->stream);
-    TRACED(h, TR_REFINE_DATA, b32_pass(b, B32_REFINE, b->b32_fitems, b->ffirst, q, b->b32_dX, nullptr));
+    TRACED(h, TR_REFINE_DATA, {
+      launch_b32_zexpand(b->b32_inst, b->b32_fetile_inst, b->b32_fetile_base, b->n_fetiles, b->b32_P32, b->b32_DZ,
+                         h->stream);
+      b32_pass(b, B32_REFINE, b->b32_fitems, b->ffirst, q, b->b32_dX, nullptr);
+    });
     if (b->n_ftiles)
       TRACED(h, TR_PROJECT_REDUCED,
              launch_b32_zcontract(b->b32_inst, b->b32_ftile_inst, b->b32_ftile_base, b->n_ftiles, b->b32_R,
@@ -2784,8 +2796,8 @@ void batch_fit_any(mfa_batch* b, const void* q, int q_dtype) {
 // Limits of the FP32 data-pass kernels for one instance: a row (padded to
 // an odd pitch) fits one warp's staging buffer, the x basis values fit the
 // CTA's table, the open y control points of a streamed plane fit eight
-// column groups, and a 3-D instance's z-expanded control-point plane fits a
-// warp's buffer.
+// column groups, and the z contraction's 32-bit index divisions of a 3-D
+// instance stay exact.
 bool b32_supported(const mfa_instance& in) {
   const int p = in.degree;
   const long long M0 = in.npts[0], n0 = (long long)in.nspans[0] + p;
@@ -2793,7 +2805,7 @@ bool b32_supported(const mfa_instance& in) {
   if ((M0 | 1) > kB32Stage || n0 > kB32Threads || W * M0 > 8192) return false;
   if (in.dim == 3) {
     const long long n1 = (long long)in.nspans[1] + p, n2 = (long long)in.nspans[2] + p;
-    if (n0 * n1 > 4096 || n0 * n1 * n2 * std::max(n0, n1) >= (1LL << 32)) return false;
+    if (n0 * n1 * n2 * std::max(n0, n1) >= (1LL << 32)) return false;
   }
   return true;
 }
@@ -2967,7 +2979,6 @@ int build_b32(mfa_batch* b) {
     c.stage = std::max(c.stage, rows * pitch);
     c.xr = std::max(c.xr, rows * n0s);
     if (d.mode == 1 && n0 > 32) c.ring = std::max(c.ring, (p + 1) * ((n0 + 31) / 32) * 32);
-    if (d.dim == 3) c.dz = std::max(c.dz, d.np * n1 * n0);
   }
   for (int k = 0; k < 2; ++k)
     for (int p = 1; p <= MFA_MAX_DEGREE; ++p)
@@ -3020,14 +3031,20 @@ int build_b32(mfa_batch* b) {
       }
   };
   firsts(pit, b->pfirst);
-  std::vector<int> zti;
-  std::vector<long long> ztb;
+  std::vector<int> zti, eti;
+  std::vector<long long> ztb, etb;
   for (int i = 0; i < count; ++i)
     if (D[i].dim == 3) {
       const long long n = (long long)D[i].n[0] * D[i].n[1] * D[i].n[2];
       for (long long e = 0; e < n; e += 256) {
         zti.push_back(i);
         ztb.push_back(e);
+      }
+      // z expansion for the decode: 256 values of DZ (M2 x n1 x n0) per tile
+      const long long nz = (long long)D[i].M[2] * D[i].n[1] * D[i].n[0];
+      for (long long e = 0; e < nz; e += 256) {
+        eti.push_back(i);
+        etb.push_back(e);
       }
     }
   // a refinement step where the FP32 error bound 2^-24 prod_a sqrt(cond(N_a^T N_a))
@@ -3061,12 +3078,17 @@ int build_b32(mfa_batch* b) {
   for (const B32Item& x : pit)
     if (refine[x.inst]) fit.push_back(x);
   firsts(fit, b->ffirst);
-  std::vector<int> fti;
-  std::vector<long long> ftb;
+  std::vector<int> fti, feti;
+  std::vector<long long> ftb, fetb;
   for (size_t k = 0; k < zti.size(); ++k)
     if (refine[zti[k]]) {
       fti.push_back(zti[k]);
       ftb.push_back(ztb[k]);
+    }
+  for (size_t k = 0; k < eti.size(); ++k)
+    if (refine[eti[k]]) {
+      feti.push_back(eti[k]);
+      fetb.push_back(etb[k]);
     }
   int nref = 0;
   for (int i = 0; i < count; ++i) nref += refine[i];
@@ -3075,10 +3097,13 @@ int build_b32(mfa_batch* b) {
   const size_t o_inst = ar.take<B32Inst>(count), o_pit = ar.take<B32Item>(pit.size()),
                o_rf = ar.take<int>(2 * (size_t)count), o_zi = ar.take<int>(zti.size()),
                o_zb = ar.take<long long>(ztb.size()), o_fit = ar.take<B32Item>(fit.size()),
-               o_fti = ar.take<int>(fti.size()), o_ftb = ar.take<long long>(ftb.size());
+               o_fti = ar.take<int>(fti.size()), o_ftb = ar.take<long long>(ftb.size()),
+               o_ei = ar.take<int>(eti.size()), o_eb = ar.take<long long>(etb.size()),
+               o_fei = ar.take<int>(feti.size()), o_feb = ar.take<long long>(fetb.size());
   const size_t host_bytes = ar.used;
   const size_t o_R = ar.take<float>(rsize), o_Z = ar.take<float>(zsize), o_P = ar.take<float>(b->cp_off[count]),
-               o_part = ar.take<double>(2 * pit.size()), o_dX = ar.take<ff>(nref ? b->cp_off[count] : 0);
+               o_part = ar.take<double>(2 * pit.size()), o_dX = ar.take<ff>(nref ? b->cp_off[count] : 0),
+               o_DZ = ar.take<float>(rsize);
   void* mem = nullptr;
   int rc = pool_alloc(h, &mem, ar.used);
   if (rc != MFA_OK) return rc;
@@ -3106,6 +3131,10 @@ int build_b32(mfa_batch* b) {
   std::memcpy(img + o_fit, fit.data(), sizeof(B32Item) * fit.size());
   std::memcpy(img + o_fti, fti.data(), sizeof(int) * fti.size());
   std::memcpy(img + o_ftb, ftb.data(), sizeof(long long) * ftb.size());
+  std::memcpy(img + o_ei, eti.data(), sizeof(int) * eti.size());
+  std::memcpy(img + o_eb, etb.data(), sizeof(long long) * etb.size());
+  std::memcpy(img + o_fei, feti.data(), sizeof(int) * feti.size());
+  std::memcpy(img + o_feb, fetb.data(), sizeof(long long) * fetb.size());
   cudaError_t e = cudaMemcpyAsync(mem, img, host_bytes, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaEventRecord(h->stage32_done, h->stream);
   if (e != cudaSuccess) {
@@ -3127,10 +3156,17 @@ int build_b32(mfa_batch* b) {
   b->b32_ftile_inst = at_off<int>(mem, o_fti);
   b->b32_ftile_base = at_off<long long>(mem, o_ftb);
   b->b32_dX = nref ? at_off<ff>(mem, o_dX) : nullptr;
+  b->b32_etile_inst = at_off<int>(mem, o_ei);
+  b->b32_etile_base = at_off<long long>(mem, o_eb);
+  b->b32_fetile_inst = at_off<int>(mem, o_fei);
+  b->b32_fetile_base = at_off<long long>(mem, o_feb);
+  b->b32_DZ = at_off<float>(mem, o_DZ);
   b->n_pitems = (int)pit.size();
   b->n_ztiles = (int)zti.size();
   b->n_fitems = (int)fit.size();
   b->n_ftiles = (int)fti.size();
+  b->n_etiles = (int)eti.size();
+  b->n_fetiles = (int)feti.size();
   b->n_refined = nref;
   return MFA_OK;
 }
@@ -3241,8 +3277,8 @@ int batch_autotune(mfa_batch* b, const void* q, int q_dtype) {
       if (rc != MFA_OK) break;
       const float ms = timed([&] {
         for (int c = 0; c < 2; ++c)
-          launch_b32(B32_PROJECT, b->b32_inst, b->b32_pitems, b->pfirst[c], b->caps[c], qf, nullptr, (ff*)b->buf,
-                     b->b32_R, b->b32_Z, nullptr, h->stream);
+          launch_b32(B32_PROJECT, b->b32_inst, b->b32_pitems, b->pfirst[c], b->caps[c], qf, nullptr, nullptr,
+                     (ff*)b->buf, b->b32_R, b->b32_Z, nullptr, h->stream);
       });
       for (mfa_model* md : b->groups) md->tune_ms[3 + k] = ms;
       if (ms < best) {
@@ -3633,8 +3669,11 @@ int mfa_batch_residual(mfa_handle* h, const mfa_batch* bc, const void* q, int q_
   if (rc == MFA_OK && e == cudaSuccess && b->prec == MFA_PREC_FP32 && q_dtype != MFA_F32) rc = MFA_ERR_UNSUPPORTED;
   if (rc == MFA_OK && e == cudaSuccess) {
     if (b->prec == MFA_PREC_FP32) {
-      TRACED(h, TR_RESIDUAL, b32_pass(b, B32_RESIDUAL, b->b32_pitems, b->pfirst, (const float*)q, nullptr,
-                                      b->b32_part));
+      TRACED(h, TR_RESIDUAL, {
+        launch_b32_zexpand(b->b32_inst, b->b32_etile_inst, b->b32_etile_base, b->n_etiles, b->b32_P32, b->b32_DZ,
+                           h->stream);
+        b32_pass(b, B32_RESIDUAL, b->b32_pitems, b->pfirst, (const float*)q, nullptr, b->b32_part);
+      });
       TRACED(h, TR_REDUCE, launch_b32_reduce(b->b32_rfirst, b->count, b->b32_part, (double*)res, h->stream));
     } else if (b->prec == MFA_PREC_FP64)
       rc = q_dtype == MFA_F64 ? batch_residual_into<double, double>(b, (const double*)q, (double*)res)

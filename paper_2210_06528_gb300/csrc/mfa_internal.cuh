@@ -270,11 +270,11 @@ struct B32Item {
 // Shared-memory capacities (elements) of one launch, the maxima over its
 // instances: per CTA the x basis values (W per point), the x and y span
 // starts, the y basis values (W per row) and the y span of every row; per
-// warp the staged rows, the x-reduced rows, the y accumulators of a streamed
-// plane and the z-expanded control points.
+// warp the staged rows, the x-reduced rows (and as many y-expanded control
+// points for the decode) and the y accumulators of a streamed plane.
 struct B32Caps {
   int vb, sx, sy, vy, ysp;
-  int stage, xr, ring, dz;
+  int stage, xr, ring;
 };
 constexpr int kB32Threads = 256;
 constexpr int kB32Stage = 1024;  // data values a warp stages per chunk (rows padded to odd pitch)
@@ -285,11 +285,17 @@ size_t b32_smem_bytes(const B32Caps& cap, int mode);
 //  B32_PROJECT: N^T q into X (2-D, 1-D) or R (3-D, xy-reduced planes);
 //  B32_REFINE: the same for r = q - N P32 (dX in X);
 //  B32_RESIDUAL: per item sum of E^2 and max |E|, E = q - N P32, in part.
+//  The decode of both takes a 3-D instance's z-expanded control points from
+//  DZ (launch_b32_zexpand of the same P32, layout of R).
 // With sides (nsides > 0), the launches of successive degrees go to
 // sides[(*next_side)++ % nsides] instead of st (the caller forks and joins).
 void launch_b32(int mode, const B32Inst* insts, const B32Item* items, const int* first, const B32Caps* caps,
-                const float* Q, const float* P32, ff* X, float* R, float* Z, double* part, cudaStream_t st,
-                const cudaStream_t* sides = nullptr, int nsides = 0, int* next_side = nullptr);
+                const float* Q, const float* P32, const float* DZ, ff* X, float* R, float* Z, double* part,
+                cudaStream_t st, const cudaStream_t* sides = nullptr, int nsides = 0, int* next_side = nullptr);
+// DZ (layout of R) = the control points P32 of the tiles' 3-D instances
+// expanded along z at every point plane (tiles of 256 values of DZ).
+void launch_b32_zexpand(const B32Inst* insts, const int* tile_inst, const long long* tile_base, int ntiles,
+                        const float* P32, float* DZ, cudaStream_t st);
 void launch_b32_add(ff* X, const ff* dX, long long n, cudaStream_t st);
 void launch_b32_zcontract(const B32Inst* insts, const int* tile_inst, const long long* tile_base, int ntiles,
                           const float* R, ff* X, cudaStream_t st);
