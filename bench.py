@@ -396,13 +396,23 @@ def bench_batched(h, torch, mfa, stream, steps, count=4096, seed=0):
     mix = bench_batch(h, torch, mfa, stream, steps, mfa.MFA_PREC_MIXED, count, seed, decode=False)
     r32, rmx = f32.pop("rms"), mix.pop("rms")
     rel = np.abs(r32 - rmx) / np.maximum(rmx, 1e-300)
-    specs, _ = inputs.batch_instances(count, seed=seed)
+    specs, data = inputs.batch_instances(count, seed=seed)
     d2 = sum(1 for sp in specs if sp["dim"] == 2)
+    # FP32 data passes meet the 1 % bar where the decoded RMS is at least
+    # 100 x 2^-24 x the data range; elsewhere the RMS agrees to that amount
+    rng = np.array([float(np.ptp(data[sp["q_offset"]:sp["q_offset"] + int(np.prod(sp["npts"]))])) for sp in specs])
+    floor = 100.0 * 2.0 ** -24 * rng
+    rule = rmx >= floor
     return {"workload": f"{count} independent fits ({d2} 2-D 32..512^2, {count - d2} 3-D 16..128^3 log-uniform, "
                         "degree 2..5, control points max(p+1, M/4) per axis, sinc / Gaussian sums)",
             "fp32": f32, "mixed": mix,
             "fp32_vs_mixed_rms": {"max_rel": float(rel.max()), "median_rel": float(np.median(rel)),
-                                  "within_1pct": int((rel <= 0.01).sum()), "instances": count},
+                                  "within_1pct": int((rel <= 0.01).sum()), "instances": count,
+                                  "rms_at_least_100_fp32_ulps_of_range": int(rule.sum()),
+                                  "of_those_within_1pct": int((rule & (rel <= 0.01)).sum()),
+                                  "others_within_100_fp32_ulps_of_range":
+                                      int((~rule & (np.abs(r32 - rmx) <= floor)).sum()),
+                                  "others": int((~rule).sum())},
             "refit": "one CUDA graph per batch (projection, z contraction and solves of every group)"}
 
 
