@@ -93,9 +93,7 @@ enum { MFA_F32 = 0, MFA_F64 = 1 };
  *                 and MFA_ERR_UNSUPPORTED for an instance outside the
  *                 kernels' staging limits (points along axis 0 <= 1023,
  *                 control points along axis 0 <= 256, W x points along axis 0
- *                 <= 8192 with W = 4 for degree <= 3 and 8 above, and for 3-D
- *                 n0 n1 n2 max(n0, n1) < 2^32, n_a the control points along
- *                 axis a). */
+ *                 <= 8192 with W = 4 for degree <= 3 and 8 above). */
 enum { MFA_PREC_FP64 = 0, MFA_PREC_MIXED = 1, MFA_PREC_FP32 = 2 };
 
 #define MFA_MAX_DIM 3

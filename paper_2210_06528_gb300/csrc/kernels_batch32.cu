@@ -629,8 +629,14 @@ __global__ void __launch_bounds__(256) k_b32_zexpand(const B32Inst* __restrict__
   const int sz = __ldg(D.span[2] + gk) - D.cbase[2];
   const float* src = P32 + D.x_off + sz * plane_cp + (e - k2 * plane_cp);
   const float* vz = D.vals[2] + gk * (D.p + 1);
+  constexpr int PM = MFA_MAX_DEGREE;
+  float g[PM + 1];  // every load in flight before the first product
+#pragma unroll
+  for (int c = 0; c <= PM; ++c) g[c] = c <= D.p ? __ldg(src + c * plane_cp) : 0.f;
   float a = 0.f;
-  for (int c = 0; c <= D.p; ++c) a = fmaf(__ldg(vz + c), __ldg(src + c * plane_cp), a);
+#pragma unroll
+  for (int c = 0; c <= PM; ++c)
+    if (c <= D.p) a = fmaf(__ldg(vz + c), g[c], a);
   DZ[D.r_off + e] = a;
 }
 
@@ -655,41 +661,64 @@ void launch_b32_add(ff* X, const ff* dX, long long n, cudaStream_t st) {
   k_b32_add<<<(unsigned)blocks, 256, 0, st>>>(X, dX, n);
 }
 
-// z contraction of the xy-reduced planes of 3-D instances: control point
-// (j0, j1, j2) sums N_{j2}(u_{k2}) R[k2][j1][j0] over the planes of its
-// support (FP32), written as float-float.
-__global__ void __launch_bounds__(256) k_b32_zcontract(const B32Inst* __restrict__ insts,
-                                                       const int* __restrict__ tile_inst,
-                                                       const long long* __restrict__ tile_base,
-                                                       const float* __restrict__ R, ff* __restrict__ X) {
+// z contraction of the xy-reduced planes of 3-D instances: one thread per
+// (j1, j0) column walks the planes k2 in order with the p + 1 z control
+// points that plane touches open in registers, and writes each one (as
+// float-float) once no later plane touches it, so every plane value is read
+// once.  Control point (j0, j1, j2) = sum over planes k2 of
+// N_{j2}(u_{k2}) R[k2][j1][j0] (FP32, planes in order).
+__global__ void __launch_bounds__(kB32ZThreads) k_b32_zcontract(const B32Inst* __restrict__ insts,
+                                                                const int* __restrict__ tile_inst,
+                                                                const long long* __restrict__ tile_base,
+                                                                const float* __restrict__ R, ff* __restrict__ X) {
+  constexpr int PM = MFA_MAX_DEGREE;
   const B32Inst& D = insts[tile_inst[blockIdx.x]];
-  const int n0 = D.n[0], n1 = D.n[1], n2 = D.n[2], p = D.p;
-  const unsigned idx = (unsigned)(tile_base[blockIdx.x] + threadIdx.x);  // < n0 n1 n2 < 2^31
-  if (idx >= (unsigned)(n0 * n1 * n2)) return;
-  const unsigned rest = fdiv(idx, n0, fmagic(n0));
-  const int j0 = (int)(idx - rest * n0);
-  const int j2 = (int)fdiv(rest, n1, fmagic(n1)), j1 = (int)rest - j2 * n1;
-  const int* ss = D.sstart[2] + D.cbase[2];
-  const float* vz = D.vals[2];
-  const float* Rp = R + D.r_off + (long long)j1 * n0 + j0;
-  const long long pstride = (long long)n1 * n0;
-  const int ns2 = n2 - p;
-  float acc = 0.f;
-  for (int r = 0; r <= p; ++r) {
-    const int s = j2 - r;
-    if (s < 0) break;
-    if (s >= ns2) continue;
-    const int kb = ss[s] - D.kbase[2], ke = s + 1 == ns2 ? D.M[2] : ss[s + 1] - D.kbase[2];
-    for (int k = kb; k < ke; ++k)
-      acc = fmaf(vz[(long long)(D.kbase[2] + k) * (p + 1) + r], __ldg(Rp + (long long)k * pstride), acc);
+  const long long plane = (long long)D.n[0] * D.n[1];
+  const long long col = tile_base[blockIdx.x] + threadIdx.x;
+  if (col >= plane) return;
+  const int p = D.p, n2 = D.n[2], M2 = D.M[2];
+  const int* sp = D.span[2] + D.kbase[2];
+  const float* vz = D.vals[2] + (long long)D.kbase[2] * (p + 1);
+  const float* Rp = R + D.r_off + col;
+  ff* Xp = X + D.x_off + col;
+  float a[PM + 1];
+#pragma unroll
+  for (int c = 0; c <= PM; ++c) a[c] = 0.f;
+  int cc = 0;  // first open z control point
+  // planes in groups of kZGroup, the group's values loaded before its first
+  // use (one column's planes are a stride apart: each load waits on DRAM)
+  constexpr int kZGroup = 8;
+  for (int k0 = 0; k0 < M2; k0 += kZGroup) {
+    float rq[kZGroup];
+#pragma unroll
+    for (int u = 0; u < kZGroup; ++u) rq[u] = k0 + u < M2 ? __ldg(Rp + (long long)(k0 + u) * plane) : 0.f;
+#pragma unroll
+    for (int u = 0; u < kZGroup; ++u) {
+      const int k = k0 + u;
+      if (k >= M2) break;
+      const int sk = __ldg(sp + k) - D.cbase[2];
+      while (cc < sk) {
+        Xp[(long long)cc * plane] = ff(a[0]);
+#pragma unroll
+        for (int c = 0; c < PM; ++c) a[c] = a[c + 1];
+        a[PM] = 0.f;
+        ++cc;
+      }
+      const float* v = vz + (long long)k * (p + 1);
+#pragma unroll
+      for (int c = 0; c <= PM; ++c)
+        if (c <= p) a[c] = fmaf(__ldg(v + c), rq[u], a[c]);
+    }
   }
-  X[D.x_off + idx] = ff(acc);
+#pragma unroll
+  for (int c = 0; c <= PM; ++c)
+    if (c <= p && cc + c < n2) Xp[(long long)(cc + c) * plane] = ff(a[c]);
 }
 
 void launch_b32_zcontract(const B32Inst* insts, const int* tile_inst, const long long* tile_base, int ntiles,
                           const float* R, ff* X, cudaStream_t st) {
   if (ntiles <= 0) return;
-  k_b32_zcontract<<<ntiles, 256, 0, st>>>(insts, tile_inst, tile_base, R, X);
+  k_b32_zcontract<<<ntiles, kB32ZThreads, 0, st>>>(insts, tile_inst, tile_base, R, X);
 }
 
 // Per instance, its items' totals in item order: out[2 i] = sum E^2,

@@ -2795,19 +2795,13 @@ void batch_fit_any(mfa_batch* b, const void* q, int q_dtype) {
 
 // Limits of the FP32 data-pass kernels for one instance: a row (padded to
 // an odd pitch) fits one warp's staging buffer, the x basis values fit the
-// CTA's table, the open y control points of a streamed plane fit eight
-// column groups, and the z contraction's 32-bit index divisions of a 3-D
-// instance stay exact.
+// CTA's table, and the open y control points of a streamed plane fit eight
+// column groups.
 bool b32_supported(const mfa_instance& in) {
   const int p = in.degree;
   const long long M0 = in.npts[0], n0 = (long long)in.nspans[0] + p;
   const int W = p < 4 ? 4 : 8;  // basis values per point in shared memory
-  if ((M0 | 1) > kB32Stage || n0 > kB32Threads || W * M0 > 8192) return false;
-  if (in.dim == 3) {
-    const long long n1 = (long long)in.nspans[1] + p, n2 = (long long)in.nspans[2] + p;
-    if (n0 * n1 * n2 * std::max(n0, n1) >= (1LL << 32)) return false;
-  }
-  return true;
+  return (M0 | 1) <= kB32Stage && n0 <= kB32Threads && W * M0 <= 8192;
 }
 
 // Condition number of the normal matrix N^T N of one axis (M points
@@ -3035,8 +3029,9 @@ int build_b32(mfa_batch* b) {
   std::vector<long long> ztb, etb;
   for (int i = 0; i < count; ++i)
     if (D[i].dim == 3) {
-      const long long n = (long long)D[i].n[0] * D[i].n[1] * D[i].n[2];
-      for (long long e = 0; e < n; e += 256) {
+      // z contraction: kB32ZThreads (j1, j0) columns per tile
+      const long long n = (long long)D[i].n[0] * D[i].n[1];
+      for (long long e = 0; e < n; e += kB32ZThreads) {
         zti.push_back(i);
         ztb.push_back(e);
       }

@@ -277,6 +277,7 @@ struct B32Caps {
   int stage, xr, ring;
 };
 constexpr int kB32Threads = 256;
+constexpr int kB32ZThreads = 128;  // z contraction: (j1, j0) columns per tile
 constexpr int kB32Stage = 1024;  // data values a warp stages per chunk (rows padded to odd pitch)
 enum { B32_PROJECT = 0, B32_REFINE = 1, B32_RESIDUAL = 2 };
 size_t b32_smem_bytes(const B32Caps& cap, int mode);
@@ -297,6 +298,8 @@ void launch_b32(int mode, const B32Inst* insts, const B32Item* items, const int*
 void launch_b32_zexpand(const B32Inst* insts, const int* tile_inst, const long long* tile_base, int ntiles,
                         const float* P32, float* DZ, cudaStream_t st);
 void launch_b32_add(ff* X, const ff* dX, long long n, cudaStream_t st);
+// z contraction of the xy-reduced planes R of 3-D instances into X (tiles of
+// kB32ZThreads (j1, j0) columns of an instance).
 void launch_b32_zcontract(const B32Inst* insts, const int* tile_inst, const long long* tile_base, int ntiles,
                           const float* R, ff* X, cudaStream_t st);
 void launch_b32_reduce(const int* range, int count, const double* part, double* out, cudaStream_t st);

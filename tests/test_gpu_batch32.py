@@ -182,13 +182,15 @@ def test_fp32_batch_edge_shapes():
     256 x control points (eight column groups of open y control points);
     single-span axes; interpolation (as many points as control points);
     small 3-D planes several to a chunk; a 2-D instance whose y spans split
-    over warps with the fewest spans per warp (p)."""
+    over warps with the fewest spans per warp (p); a 3-D instance with 100 x
+    50 control points per plane (its z-expanded planes larger than a warp's
+    share of shared memory)."""
     rng = np.random.default_rng(8)
     shapes = [
         (1, (1023,), 3, None), (2, (1023, 9), 4, None), (2, (1023, 12), 2, [253, 3]),
         (1, (60,), 1, None), (2, (40, 37), 6, None), (3, (30, 28, 26), 7, None),
         (2, (16, 16), 5, [1, 1]), (3, (12, 10, 40), 2, None), (2, (9, 9), 3, [6, 6]),
-        (2, (200, 300), 5, [5 * 8, 5 * 8]), (1, (7,), 6, [1]),
+        (2, (200, 300), 5, [5 * 8, 5 * 8]), (1, (7,), 6, [1]), (3, (400, 200, 6), 3, None),
     ]
     specs, chunks, off = [], [], 0
     for d, npts, p, ns in shapes:
