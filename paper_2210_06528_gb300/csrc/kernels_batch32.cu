@@ -713,6 +713,7 @@ __global__ void __launch_bounds__(kB32ZThreads) k_b32_zcontract(const B32Inst* _
 #pragma unroll
   for (int c = 0; c <= PM; ++c)
     if (c <= p && cc + c < n2) Xp[(long long)(cc + c) * plane] = ff(a[c]);
+  for (int j = cc + p + 1; j < n2; ++j) Xp[(long long)j * plane] = ff(0.f);  // spans without planes
 }
 
 void launch_b32_zcontract(const B32Inst* insts, const int* tile_inst, const long long* tile_base, int ntiles,
