@@ -1946,15 +1946,23 @@ namespace mfa {
 
 void ensure_smem_attr(const void* kernel, size_t bytes, bool carveout) {
   // the limit the kernel has in the current context right now (a context
-  // created again after a reset starts from the default), raised only when
-  // too small
+  // created again after a reset starts from the default), only ever raised:
+  // host threads launching the same kernel with different sizes (the
+  // server's workers) check and raise it one at a time, so no thread lowers
+  // the limit another thread's launch relies on
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lk(mu);
   cudaFuncAttributes fa{};
-  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && (size_t)fa.maxDynamicSharedSizeBytes >= bytes &&
-      (!carveout || fa.preferredShmemCarveout == 100))
-    return;
-  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
+  if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
+    cudaGetLastError();
+    fa.maxDynamicSharedSizeBytes = 0;
+    fa.preferredShmemCarveout = -1;
+  }
+  if ((size_t)fa.maxDynamicSharedSizeBytes < bytes &&
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
     cudaGetLastError();  // the launch reports the problem
-  if (carveout && cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
+  if (carveout && fa.preferredShmemCarveout != 100 &&
+      cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100) != cudaSuccess)
     cudaGetLastError();
 }
 

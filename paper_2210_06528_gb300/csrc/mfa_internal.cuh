@@ -142,9 +142,10 @@ struct TileMap {
 int device_sm_count();
 
 // Dynamic shared-memory limit (and, with `carveout`, the preferred shared
-// memory share) of a kernel, set once per kernel, device and size: the
-// attribute persists, and setting it again on every launch costs host time on
-// the launch path.
+// memory share) of a kernel in the current context, raised to at least
+// `bytes` and never lowered, under a process-wide lock (host threads may
+// launch the same kernel with different sizes at once).  The attribute
+// persists, so a launch that fits the current limit sets nothing.
 void ensure_smem_attr(const void* kernel, size_t bytes, bool carveout = false);
 template <typename K>
 inline void ensure_smem(K kernel, size_t bytes, bool carveout = false) {
