@@ -165,3 +165,36 @@ def test_fp32_encodes_alone_equal_the_mix_and_meet_the_bar():
             srv.release(m)
     finally:
         srv.close()
+
+
+_FIRST_ENCODES = r"""
+import sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2210_06528_gb300 import inputs, mfa
+specs, data = inputs.batch_instances(12, seed=41, size2=(64, 400), size3=(32, 160), degrees=(2, 5))
+srv = mfa.Server(0, workers=3, mem_budget=16 << 30, max_batch=1)
+try:
+    rids = [srv.encode(sp, data[sp["q_offset"]:sp["q_offset"] + int(np.prod(sp["npts"]))], mfa.MFA_PREC_FP32)
+            for sp in specs]
+    codes = [srv.wait(r, 300.0)[0] for r in rids]
+finally:
+    srv.close()
+print(codes)
+sys.exit(0 if all(c == mfa.MFA_OK for c in codes) else 1)
+"""
+
+
+def test_first_fp32_encodes_of_different_sizes_at_once():
+    """A fresh process whose first launches are served FP32 encodes of
+    different sizes on three workers at once, one instance per job: every
+    launch raises its kernel's shared-memory limit as needed while other
+    workers launch the same kernels with other sizes, and every encode
+    succeeds."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FIRST_ENCODES, root], cwd=root, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
