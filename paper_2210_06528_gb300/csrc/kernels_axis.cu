@@ -147,7 +147,6 @@ __device__ __forceinline__ T expand_one(const AxisDev& ax, const AxisOp& op, con
 template <typename T, typename TOut, int AXIS>
 __global__ void k_expand(LayoutDev L, const AxisOp* ops, const T* __restrict__ in, TOut* __restrict__ out,
                          TileMap tm) {
-  constexpr int axis = AXIS;
   int opi;
   long long idx0;
   tile_of(tm, opi, idx0);
@@ -348,7 +347,6 @@ void launch_expand_residual_tiles(const LayoutDev& L, int axis, const AxisOp* op
 template <typename T, typename TQ, int AXIS>
 __global__ void k_expand_residual(LayoutDev L, const AxisOp* opp, const T* __restrict__ in,
                                   const TQ* __restrict__ q, double* partials) {
-  constexpr int axis = AXIS;
   const AxisOp& op = block_op(opp, 0);
   const long long nout = (long long)op.out.n[0] * op.out.n[1] * op.out.n[2];
   const long long stride = (long long)gridDim.x * blockDim.x;

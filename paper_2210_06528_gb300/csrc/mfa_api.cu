@@ -3566,7 +3566,7 @@ int mfa_batch_refit(mfa_handle* h, mfa_batch* b, const void* q, int q_dtype) {
   return st < 0 ? st : MFA_OK;
 }
 
-int64_t mfa_batch_num_ctrl(const mfa_batch* b) { return b ? (int64_t)b->cp_off[b->count] : MFA_ERR_ARG; }
+int64_t mfa_batch_num_ctrl(const mfa_batch* b) { return b ? (int64_t)b->cp_off[b->count] : (int64_t)MFA_ERR_ARG; }
 
 int mfa_batch_ctrl_offsets(const mfa_batch* b, int64_t* host_off) {
   if (!b || !host_off) return MFA_ERR_ARG;
