@@ -263,7 +263,6 @@ struct ResidAcc<ff, float> {
 template <typename T, typename TQ, int AXIS>
 __global__ void k_expand_residual_tiles(LayoutDev L, const AxisOp* ops, const T* __restrict__ in,
                                         const TQ* __restrict__ q, TileMap tm, double* __restrict__ tile_part) {
-  constexpr int axis = AXIS;
   int opi;
   long long idx;
   tile_of(tm, opi, idx);
@@ -533,8 +532,8 @@ void launch_expand(const LayoutDev& L, int axis, const AxisOp* ops, int nops, lo
 }
 
 template <typename T, typename TQ>
-void launch_expand_residual(const LayoutDev& L, int axis, const AxisOp* op, long long nout, const T* in, const TQ* q,
-                            double* partials, int nblocks, cudaStream_t st) {
+void launch_expand_residual(const LayoutDev& L, int axis, const AxisOp* op, long long /*nout*/, const T* in,
+                            const TQ* q, double* partials, int nblocks, cudaStream_t st) {
   MFA_AXIS_DISPATCH(axis, (k_expand_residual<T, TQ, AX><<<nblocks, 256, 0, st>>>(L, op, in, q, partials)));
 }
 
