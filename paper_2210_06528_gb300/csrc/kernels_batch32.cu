@@ -576,9 +576,9 @@ __global__ void __launch_bounds__(kB32Threads, MODE == B32_REFINE && P >= 6 ? 1 
 template <int MODE>
 void launch_mode(const B32Inst* insts, const B32Item* items, const int* first, const B32Caps* caps, const float* Q,
                  const float* P32, const float* DZ, ff* X, float* R, float* Z, double* part, cudaStream_t st,
-                 const cudaStream_t* sides, int nsides, int& k) {
+                 const cudaStream_t* sides, int nsides, int& k, int only) {
 #define MFA_B32_LAUNCH(PP)                                                                            \
-  if (first[PP] > first[PP - 1]) {                                                                   \
+  if ((only == 0 || only == PP) && first[PP] > first[PP - 1]) {                                      \
     const size_t smem = b32_smem_bytes(caps[PP], MODE);                                              \
     ensure_smem(k_b32<PP, MODE>, smem);                                                              \
     cudaStream_t s_ = nsides > 0 ? sides[k++ % nsides] : st;                                         \
@@ -598,16 +598,41 @@ size_t b32_smem_bytes(const B32Caps& cap, int mode) {
 
 void launch_b32(int mode, const B32Inst* insts, const B32Item* items, const int* first, const B32Caps* caps,
                 const float* Q, const float* P32, const float* DZ, ff* X, float* R, float* Z, double* part,
-                cudaStream_t st, const cudaStream_t* sides, int nsides, int* next_side) {
+                cudaStream_t st, const cudaStream_t* sides, int nsides, int* next_side, int only_degree) {
   int k0 = next_side ? *next_side : 0;
   int& k = next_side ? *next_side : k0;
   if (mode == B32_PROJECT)
-    launch_mode<B32_PROJECT>(insts, items, first, caps, Q, nullptr, nullptr, X, R, Z, nullptr, st, sides, nsides, k);
+    launch_mode<B32_PROJECT>(insts, items, first, caps, Q, nullptr, nullptr, X, R, Z, nullptr, st, sides, nsides, k,
+                             only_degree);
   else if (mode == B32_REFINE)
-    launch_mode<B32_REFINE>(insts, items, first, caps, Q, P32, DZ, X, R, Z, nullptr, st, sides, nsides, k);
+    launch_mode<B32_REFINE>(insts, items, first, caps, Q, P32, DZ, X, R, Z, nullptr, st, sides, nsides, k,
+                            only_degree);
   else
     launch_mode<B32_RESIDUAL>(insts, items, first, caps, Q, P32, DZ, nullptr, nullptr, nullptr, part, st, sides,
-                              nsides, k);
+                              nsides, k, only_degree);
+}
+
+// Over tiles of control points (first value, count): P32 = float(X), after
+// X += dX where dX is given (the refinement's correction).  The same
+// operations as k_b32_add followed by the whole-buffer cast.
+__global__ void k_b32_cast_tiles(const long long* __restrict__ off, const int* __restrict__ len,
+                                 ff* __restrict__ X, const ff* __restrict__ dX, float* __restrict__ P32) {
+  const long long o = off[blockIdx.x];
+  const int n = len[blockIdx.x];
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    ff x = X[o + t];
+    if (dX) {
+      x = x + dX[o + t];
+      X[o + t] = x;
+    }
+    P32[o + t] = (float)x;
+  }
+}
+
+void launch_b32_cast_tiles(const long long* off, const int* len, int ntiles, ff* X, const ff* dX, float* P32,
+                           cudaStream_t st) {
+  if (ntiles <= 0) return;
+  k_b32_cast_tiles<<<ntiles, 256, 0, st>>>(off, len, X, dX, P32);
 }
 
 // z expansion of the FP32 control points of 3-D instances for the decode of

@@ -2346,6 +2346,17 @@ struct mfa_batch {
   long long* b32_fetile_base = nullptr;
   float* b32_DZ = nullptr;
   int n_etiles = 0, n_fetiles = 0;
+  // the per-unit fit pipeline: unit u = class * (MFA_MAX_DEGREE + 1) +
+  // degree; its z-contraction tiles (all, refined), refined z-expansion tiles
+  // and control-point tiles (all, refined) are ranges [u_x[u], u_x[u + 1])
+  // of the unit-sorted lists
+  static constexpr int kUnits = 2 * (MFA_MAX_DEGREE + 1);
+  int u_zt[kUnits + 1] = {}, u_ft[kUnits + 1] = {}, u_fe[kUnits + 1] = {}, u_ct[kUnits + 1] = {},
+      u_rt[kUnits + 1] = {};
+  long long* b32_ct_off = nullptr;
+  int* b32_ct_len = nullptr;
+  long long* b32_rt_off = nullptr;
+  int* b32_rt_len = nullptr;
   // side streams on which the groups' independent work runs side by side
   // (forked from and joined back into the handle's stream; a captured refit
   // records them as parallel branches)
@@ -2739,8 +2750,61 @@ void b32_pass(mfa_batch* b, int mode, const B32Item* items, int first[2][MFA_MAX
   if (ns > 1) batch_join(b);
 }
 
+// The FP32 fit as one pipeline per (class, degree) unit, the units side by
+// side on the batch's side streams: a unit's projection, z contraction,
+// solves and FP32 copy, then its refinement step (z expansion, refinement
+// projection, z contraction, solves, correction and FP32 copy), each unit in
+// order on its own stream.  The units' instances, tiles and control points
+// are disjoint, so one unit's latency-bound solves run beside other units'
+// data passes.  The operations are those of the pass-by-pass order.
+void batch_fit32_units(mfa_batch* b, const float* q) {
+  mfa_handle* h = b->h;
+  ff* X = (ff*)b->buf;
+  const int ns = batch_sides(b);
+  const long long ncp = b->cp_off[b->count];
+  if (b->n_fitems) cudaMemsetAsync(b->b32_dX, 0, (size_t)ncp * sizeof(ff), h->stream);
+  batch_fork(b);
+  int k = 0;
+  for (int c = 0; c < 2; ++c)
+    for (int p = 1; p <= MFA_MAX_DEGREE; ++p) {
+      if (b->pfirst[c][p] == b->pfirst[c][p - 1]) continue;
+      const int u = c * (MFA_MAX_DEGREE + 1) + p;
+      cudaStream_t st = b->side[k++ % ns];
+      auto solves = [&](ff* x) {
+        for (mfa_model* md : b->groups)
+          if ((md->dim == 3) == (c == 1) && md->degree == p)
+            for (int a = 0; a < md->dim; ++a)
+              launch_band_solve<ff>(md->L, a, false, md->ops + (size_t)(OP_SOLVEL0 + a) * md->nsub, md->nsub,
+                                    md->maxFibL[a], x, st, &md->tm_solve[a]);
+      };
+      launch_b32(B32_PROJECT, b->b32_inst, b->b32_pitems, b->pfirst[c], b->caps[c], q, nullptr, nullptr, X,
+                 b->b32_R, b->b32_Z, nullptr, st, nullptr, 0, nullptr, p);
+      launch_b32_zcontract(b->b32_inst, b->b32_ztile_inst + b->u_zt[u], b->b32_ztile_base + b->u_zt[u],
+                           b->u_zt[u + 1] - b->u_zt[u], b->b32_R, X, st);
+      solves(X);
+      launch_b32_cast_tiles(b->b32_ct_off + b->u_ct[u], b->b32_ct_len + b->u_ct[u], b->u_ct[u + 1] - b->u_ct[u], X,
+                            nullptr, b->b32_P32, st);
+      if (b->ffirst[c][p] == b->ffirst[c][p - 1]) continue;
+      launch_b32_zexpand(b->b32_inst, b->b32_fetile_inst + b->u_fe[u], b->b32_fetile_base + b->u_fe[u],
+                         b->u_fe[u + 1] - b->u_fe[u], b->b32_P32, b->b32_DZ, st);
+      launch_b32(B32_REFINE, b->b32_inst, b->b32_fitems, b->ffirst[c], b->caps[c], q, b->b32_P32, b->b32_DZ,
+                 b->b32_dX, b->b32_R, b->b32_Z, nullptr, st, nullptr, 0, nullptr, p);
+      launch_b32_zcontract(b->b32_inst, b->b32_ftile_inst + b->u_ft[u], b->b32_ftile_base + b->u_ft[u],
+                           b->u_ft[u + 1] - b->u_ft[u], b->b32_R, b->b32_dX, st);
+      solves(b->b32_dX);
+      launch_b32_cast_tiles(b->b32_rt_off + b->u_rt[u], b->b32_rt_len + b->u_rt[u], b->u_rt[u + 1] - b->u_rt[u], X,
+                            b->b32_dX, b->b32_P32, st);
+    }
+  batch_join(b);
+}
+
 void batch_fit32(mfa_batch* b, const float* q) {
   mfa_handle* h = b->h;
+  // a traced fit runs pass by pass, so that each pass is timed on its own
+  if (!h->trace_on && batch_sides(b) > 1) {
+    batch_fit32_units(b, q);
+    return;
+  }
   ff* X = (ff*)b->buf;
   TRACED(h, TR_PROJECT_DATA, b32_pass(b, B32_PROJECT, b->b32_pitems, b->pfirst, q, X, nullptr));
   if (b->n_ztiles)
@@ -3025,9 +3089,15 @@ int build_b32(mfa_batch* b) {
       }
   };
   firsts(pit, b->pfirst);
+  // tile lists in (class, degree) unit order, so that every unit's tiles are
+  // one range (the per-unit fit pipeline launches them unit by unit)
+  auto unit_of = [&](int i) { return cls_of(i) * (MFA_MAX_DEGREE + 1) + D[i].p; };
+  std::vector<int> uord(count);
+  for (int i = 0; i < count; ++i) uord[i] = i;
+  std::stable_sort(uord.begin(), uord.end(), [&](int x, int y) { return unit_of(x) < unit_of(y); });
   std::vector<int> zti, eti;
   std::vector<long long> ztb, etb;
-  for (int i = 0; i < count; ++i)
+  for (int i : uord)
     if (D[i].dim == 3) {
       // z contraction: kB32ZThreads (j1, j0) columns per tile
       const long long n = (long long)D[i].n[0] * D[i].n[1];
@@ -3085,6 +3155,35 @@ int build_b32(mfa_batch* b) {
       feti.push_back(eti[k]);
       fetb.push_back(etb[k]);
     }
+  // control-point tiles of every instance and of the refined ones, unit by unit
+  std::vector<long long> cto, rto;
+  std::vector<int> ctl, rtl;
+  constexpr int NU = mfa_batch::kUnits;
+  int u_ct[NU + 1] = {}, u_rt[NU + 1] = {}, u_zt[NU + 1] = {}, u_ft[NU + 1] = {}, u_fe[NU + 1] = {};
+  for (int i : uord) {
+    const int u = unit_of(i);
+    for (long long o = b->cp_off[i]; o < b->cp_off[i + 1]; o += kB32CastTile) {
+      const int n = (int)std::min<long long>(kB32CastTile, b->cp_off[i + 1] - o);
+      cto.push_back(o);
+      ctl.push_back(n);
+      u_ct[u + 1]++;
+      if (refine[i]) {
+        rto.push_back(o);
+        rtl.push_back(n);
+        u_rt[u + 1]++;
+      }
+    }
+  }
+  for (int t : zti) u_zt[unit_of(t) + 1]++;
+  for (int t : fti) u_ft[unit_of(t) + 1]++;
+  for (int t : feti) u_fe[unit_of(t) + 1]++;
+  for (int u = 0; u < NU; ++u) {
+    u_ct[u + 1] += u_ct[u];
+    u_rt[u + 1] += u_rt[u];
+    u_zt[u + 1] += u_zt[u];
+    u_ft[u + 1] += u_ft[u];
+    u_fe[u + 1] += u_fe[u];
+  }
   int nref = 0;
   for (int i = 0; i < count; ++i) nref += refine[i];
   std::memcpy(b->caps, caps, sizeof(caps));
@@ -3094,7 +3193,9 @@ int build_b32(mfa_batch* b) {
                o_zb = ar.take<long long>(ztb.size()), o_fit = ar.take<B32Item>(fit.size()),
                o_fti = ar.take<int>(fti.size()), o_ftb = ar.take<long long>(ftb.size()),
                o_ei = ar.take<int>(eti.size()), o_eb = ar.take<long long>(etb.size()),
-               o_fei = ar.take<int>(feti.size()), o_feb = ar.take<long long>(fetb.size());
+               o_fei = ar.take<int>(feti.size()), o_feb = ar.take<long long>(fetb.size()),
+               o_cto = ar.take<long long>(cto.size()), o_ctl = ar.take<int>(ctl.size()),
+               o_rto = ar.take<long long>(rto.size()), o_rtl = ar.take<int>(rtl.size());
   const size_t host_bytes = ar.used;
   const size_t o_R = ar.take<float>(rsize), o_Z = ar.take<float>(zsize), o_P = ar.take<float>(b->cp_off[count]),
                o_part = ar.take<double>(2 * pit.size()), o_dX = ar.take<ff>(nref ? b->cp_off[count] : 0),
@@ -3130,6 +3231,10 @@ int build_b32(mfa_batch* b) {
   std::memcpy(img + o_eb, etb.data(), sizeof(long long) * etb.size());
   std::memcpy(img + o_fei, feti.data(), sizeof(int) * feti.size());
   std::memcpy(img + o_feb, fetb.data(), sizeof(long long) * fetb.size());
+  std::memcpy(img + o_cto, cto.data(), sizeof(long long) * cto.size());
+  std::memcpy(img + o_ctl, ctl.data(), sizeof(int) * ctl.size());
+  std::memcpy(img + o_rto, rto.data(), sizeof(long long) * rto.size());
+  std::memcpy(img + o_rtl, rtl.data(), sizeof(int) * rtl.size());
   cudaError_t e = cudaMemcpyAsync(mem, img, host_bytes, cudaMemcpyHostToDevice, h->stream);
   if (e == cudaSuccess) e = cudaEventRecord(h->stage32_done, h->stream);
   if (e != cudaSuccess) {
@@ -3156,6 +3261,15 @@ int build_b32(mfa_batch* b) {
   b->b32_fetile_inst = at_off<int>(mem, o_fei);
   b->b32_fetile_base = at_off<long long>(mem, o_feb);
   b->b32_DZ = at_off<float>(mem, o_DZ);
+  b->b32_ct_off = at_off<long long>(mem, o_cto);
+  b->b32_ct_len = at_off<int>(mem, o_ctl);
+  b->b32_rt_off = at_off<long long>(mem, o_rto);
+  b->b32_rt_len = at_off<int>(mem, o_rtl);
+  std::memcpy(b->u_ct, u_ct, sizeof(u_ct));
+  std::memcpy(b->u_rt, u_rt, sizeof(u_rt));
+  std::memcpy(b->u_zt, u_zt, sizeof(u_zt));
+  std::memcpy(b->u_ft, u_ft, sizeof(u_ft));
+  std::memcpy(b->u_fe, u_fe, sizeof(u_fe));
   b->n_pitems = (int)pit.size();
   b->n_ztiles = (int)zti.size();
   b->n_fitems = (int)fit.size();

@@ -291,9 +291,16 @@ size_t b32_smem_bytes(const B32Caps& cap, int mode);
 //  DZ (launch_b32_zexpand of the same P32, layout of R).
 // With sides (nsides > 0), the launches of successive degrees go to
 // sides[(*next_side)++ % nsides] instead of st (the caller forks and joins).
+// With only_degree > 0, the launch of that degree alone.
 void launch_b32(int mode, const B32Inst* insts, const B32Item* items, const int* first, const B32Caps* caps,
                 const float* Q, const float* P32, const float* DZ, ff* X, float* R, float* Z, double* part,
-                cudaStream_t st, const cudaStream_t* sides = nullptr, int nsides = 0, int* next_side = nullptr);
+                cudaStream_t st, const cudaStream_t* sides = nullptr, int nsides = 0, int* next_side = nullptr,
+                int only_degree = 0);
+// P32 = float(X) over tiles of control points (first value, count; at most
+// 2^31 values each), after X += dX where dX is not null.
+constexpr int kB32CastTile = 4096;
+void launch_b32_cast_tiles(const long long* off, const int* len, int ntiles, ff* X, const ff* dX, float* P32,
+                           cudaStream_t st);
 // DZ (layout of R) = the control points P32 of the tiles' 3-D instances
 // expanded along z at every point plane (tiles of 256 values of DZ).
 void launch_b32_zexpand(const B32Inst* insts, const int* tile_inst, const long long* tile_base, int ntiles,

@@ -209,3 +209,26 @@ def test_fp32_batch_edge_shapes():
         b.free()
     finally:
         h.close()
+
+
+def test_fp32_unit_pipeline_equals_the_pass_by_pass_fit():
+    """The fit as one pipeline per (class, degree) unit on side streams (the
+    untraced path) gives the same control points, bit for bit, as the fit
+    run pass by pass (the traced path), refined and unrefined instances of
+    every degree and of both classes included."""
+    specs, data = inputs.batch_instances(48, seed=17, size2=(20, 120), size3=(12, 40), degrees=(1, 5),
+                                         dims=(1, 2, 3))
+    h = mfa.Handle(0)
+    try:
+        b1 = h.encode_batch(specs, _dev(data), FP32)
+        P1 = b1.ctrl()
+        mfa.mfa_trace_enable(h.h, True)
+        b2 = h.encode_batch(specs, _dev(data), FP32)
+        mfa.mfa_trace_enable(h.h, False)
+        P2 = b2.ctrl()
+        assert b1.info()["refined"] > 0
+        assert np.array_equal(P1, P2)
+        b1.free()
+        b2.free()
+    finally:
+        h.close()
