@@ -349,6 +349,20 @@ const char* mfa_status_string(int status);
 int mfa_axis_layout(int64_t npts, int32_t nspans, int32_t degree, int32_t nsub, const int32_t* core_spans,
                     int32_t overlap, int32_t knots, int32_t* out, int32_t cap, int32_t* owner);
 
+/* Condition number of one axis's normal matrix N^T N (Sec. 2.3.1), as the
+ * FP32 data passes estimate it on the host: npts points u_k = k / (npts - 1),
+ * a clamped uniform knot vector of nspans spans, B-spline basis of the given
+ * degree (Sec. 2.1).  An MFA_PREC_FP32 batch gives an instance one
+ * refinement step when 2^-24 times the product over its axes of the square
+ * root of this value exceeds 2e-6.  The estimate: the banded matrix in FP64,
+ * 30 power iterations for its largest eigenvalue and 30 inverse iterations
+ * (banded Cholesky solves) for its smallest.  Host only; no GPU is used.
+ *   *out  the estimate; 1e300 where N^T N is not positive definite (a span
+ *         without enough points)
+ * Returns MFA_OK; MFA_ERR_ARG for npts < 1, nspans < 1, a degree outside
+ * 1..MFA_MAX_DEGREE or a NULL out (nothing written). */
+int mfa_gram_condition(int64_t npts, int32_t nspans, int32_t degree, double* out);
+
 /* Grid decode that allocates nothing.
  *
  * The paper has no counterpart to this call; it exists for callers that

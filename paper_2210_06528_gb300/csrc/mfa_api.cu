@@ -3456,6 +3456,12 @@ int batch_autotune(mfa_batch* b, const void* q, int q_dtype) {
 }
 }  // namespace
 
+int mfa_gram_condition(int64_t npts, int32_t nspans, int32_t degree, double* out) {
+  if (!out || npts < 1 || nspans < 1 || degree < 1 || degree > MFA_MAX_DEGREE) return MFA_ERR_ARG;
+  *out = host_gram_cond((long long)npts, nspans, degree);
+  return MFA_OK;
+}
+
 int mfa_batch_info(const mfa_batch* b, mfa_batch_info_t* out) {
   if (!b || !out) return MFA_ERR_ARG;
   std::memset(out, 0, sizeof(*out));

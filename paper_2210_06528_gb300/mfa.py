@@ -158,6 +158,8 @@ def load(path: Optional[str] = None) -> ctypes.CDLL:
     lib.mfa_batch_tile_sizes.restype = ctypes.c_int
     lib.mfa_batch_info.argtypes = [P, P]
     lib.mfa_batch_info.restype = ctypes.c_int
+    lib.mfa_gram_condition.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, P]
+    lib.mfa_gram_condition.restype = ctypes.c_int
     lib.mfa_batch_group_tuning.argtypes = [P, ctypes.c_int32, P]
     lib.mfa_batch_group_tuning.restype = ctypes.c_int
     lib.mfa_batch_decode_points.argtypes = [P, P, ctypes.c_int32, P, P, P, P, ctypes.c_int]
@@ -406,6 +408,14 @@ class MfaBatchInfo(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("groups", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("refined", ctypes.c_int32), ("items", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("points", ctypes.c_int64), ("ctrl", ctypes.c_int64)]
+
+
+def mfa_gram_condition(npts: int, nspans: int, degree: int) -> float:
+    """Host estimate of one axis's cond(N^T N) (the FP32 refinement rule's input)."""
+    out = ctypes.c_double()
+    _check(load().mfa_gram_condition(ctypes.c_int64(npts), ctypes.c_int32(nspans), ctypes.c_int32(degree),
+                                     ctypes.byref(out)), "mfa_gram_condition")
+    return out.value
 
 
 def mfa_batch_info(b: int) -> dict:
