@@ -34,3 +34,31 @@ def test_arguments_out_of_range_are_refused(args):
     with pytest.raises(mfa.MFAError) as e:
         mfa.mfa_gram_condition(*args)
     assert e.value.code == mfa.MFA_ERR_ARG
+
+
+def test_rule_on_the_batched_workload():
+    """2^-24 x the product of sqrt(cond) over an instance's axes above 2e-6
+    marks 2514 of the 4096 instances of the batched workload for a
+    refinement step (the count the GPU batch reports): every 3-D instance of
+    degree >= 4 and 2-D instance of degree 5, none of degree 2 in 3-D or
+    degree <= 3 in 2-D; 3-D degree 3 and 2-D degree 4 depend on the shape."""
+    from paper_2210_06528_gb300 import inputs
+    specs, _ = inputs.batch_instances(4096, seed=0)
+    cache = {}
+    refined = 0
+    kinds = set()
+    for sp in specs:
+        g = 2.0 ** -24
+        for M, ns in zip(sp["npts"], sp["nspans"]):
+            key = (M, ns, sp["degree"])
+            if key not in cache:
+                cache[key] = mfa.mfa_gram_condition(M, ns, sp["degree"])
+            g *= np.sqrt(cache[key])
+        refined += g > 2e-6
+        kinds.add((sp["dim"], sp["degree"], bool(g > 2e-6)))
+    assert refined == 2514
+    for d, p, r in kinds:
+        if (d == 3 and p >= 4) or (d == 2 and p == 5):
+            assert r, (d, p)
+        if (d == 3 and p == 2) or (d == 2 and p <= 3):
+            assert not r, (d, p)
